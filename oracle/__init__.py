@@ -1,0 +1,294 @@
+"""Plain FP64 CPU oracle for the Wilson twisted-mass operator and its even/odd CG.
+
+TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` use this package; the library under
+``paper_0905_3331_gb300`` never imports it and it never imports that library.
+
+The arithmetic lives in ``tm_oracle.c`` (C99 complex, FP64), written from the
+paper's definitions: eq. eo0 for M, App. A for the gamma matrices, Sec. 2.4 for
+the fermion boundary phases, eq. eo2-eo4 for the even/odd blocks, App. B.2 for
+the two inversion steps and Sec. 4.4 for the stopping rule.  This module only
+compiles it (gcc) and marshals numpy arrays.
+
+Array conventions (canonical order t, z, y, x, spin, colour; Sec. 4.7.2):
+  spinor field  complex128, shape (T, Lz, Ly, Lx, 4, 3)
+  gauge field   complex128, shape (T, Lz, Ly, Lx, 4, 3, 3), direction mu = t, x, y, z
+Half-lattice vectors are full-lattice arrays that are zero on the other parity.
+
+Parity pins: every function here is pinned by the CPU tests in
+tests/test_oracle_pins.py (closed forms, invariants, dense brute force and a
+hand-derived worked example).  Agreement with the original tmLQCD program's own
+outputs is "parity unpinned": no code or data of that program exist here.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "tm_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libtm_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+# Plain IEEE arithmetic on every host: no FMA contraction, textbook complex multiply.
+CFLAGS = ["-O2", "-std=gnu11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+          "-fcx-limited-range"]
+
+
+def build(force: bool = False) -> str:
+    """Compile tm_oracle.c into _build/libtm_oracle.so (gcc); returns the path."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    subprocess.run(["gcc", *CFLAGS, _SRC, "-o", tmp, "-lm"], check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.c_void_p
+            I = ctypes.c_int
+            D = ctypes.c_double
+            L = ctypes.c_long
+            lib.orc_gamma.argtypes = [I, P]
+            lib.orc_hopping.argtypes = [P, P, I, P, P, P, I]
+            lib.orc_apply_M.argtypes = [P, P, I, D, D, I, P, P, P]
+            lib.orc_apply_M_sites.argtypes = [P, P, I, D, D, I, P, P, P, L, P]
+            lib.orc_apply_Mdiag.argtypes = [P, D, I, I, P, P]
+            lib.orc_apply_Mdiag_inv.argtypes = [P, D, I, I, P, P]
+            lib.orc_apply_Moff.argtypes = [P, P, I, D, P, I, P, P]
+            lib.orc_schur.argtypes = [P, P, I, D, D, I, P, P, P, I]
+            lib.orc_normal_op.argtypes = [P, P, I, D, D, I, P, P, P]
+            lib.orc_cg.argtypes = [P, P, I, D, D, I, P, P, P, D, I,
+                                   ctypes.POINTER(I), ctypes.POINTER(D)]
+            lib.orc_cg.restype = I
+            lib.orc_eo_prepare.argtypes = [P, P, I, D, D, I, P, P, P]
+            lib.orc_eo_reconstruct.argtypes = [P, P, I, D, D, I, P, P, P]
+            lib.orc_solve.argtypes = [P, P, I, D, D, I, P, P, P, D, I, ctypes.POINTER(I),
+                                      ctypes.POINTER(D), ctypes.POINTER(D)]
+            lib.orc_solve.restype = I
+            lib.orc_num_threads.restype = I
+            _lib = lib
+    return _lib
+
+
+# ------------------------------------------------------------------ helpers ---
+@dataclass(frozen=True)
+class Lattice:
+    """Extents and boundary phases.  dims are in direction order (T, Lx, Ly, Lz)."""
+    T: int
+    Lx: int
+    Ly: int
+    Lz: int
+    theta: tuple = (1.0, 0.0, 0.0, 0.0)  # antiperiodic in time (Sec. 2.4, theta = 1)
+    spread: bool = False                  # phase on every hop (Sec. 4.1.2) instead
+
+    @classmethod
+    def cubic(cls, T: int, L: int, **kw) -> "Lattice":
+        return cls(T, L, L, L, **kw)
+
+    @property
+    def V(self) -> int:
+        return self.T * self.Lx * self.Ly * self.Lz
+
+    @property
+    def spinor_shape(self):
+        return (self.T, self.Lz, self.Ly, self.Lx, 4, 3)
+
+    @property
+    def gauge_shape(self):
+        return (self.T, self.Lz, self.Ly, self.Lx, 4, 3, 3)
+
+    def _dims(self):
+        return np.array([self.T, self.Lx, self.Ly, self.Lz], dtype=np.int32)
+
+    def _theta(self):
+        return np.array(self.theta, dtype=np.float64)
+
+    def parity_mask(self) -> np.ndarray:
+        """Boolean array (T, Lz, Ly, Lx): True on odd sites."""
+        t, z, y, x = np.indices((self.T, self.Lz, self.Ly, self.Lx))
+        return ((t + z + y + x) & 1).astype(bool)
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c(a: np.ndarray, shape) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    if a.shape != tuple(shape):
+        raise ValueError(f"expected shape {tuple(shape)}, got {a.shape}")
+    return a
+
+
+def num_threads() -> int:
+    """OpenMP threads used by the operator's site loops."""
+    return int(_load().orc_num_threads())
+
+
+def gamma(k: int) -> np.ndarray:
+    """gamma_k (k = 0..3) or gamma_5 (k = 4) as typed from App. A."""
+    out = np.zeros((4, 4), dtype=np.complex128)
+    _load().orc_gamma(k, _ptr(out))
+    return out
+
+
+# ---------------------------------------------------------------- operator ---
+def hopping(lat: Lattice, U, psi, out_parity: int = -1) -> np.ndarray:
+    """Pure hopping sum H (eq. eo0 bracket, no -kappa); out_parity 0/1 gives H_eo/H_oe."""
+    U = _c(U, lat.gauge_shape)
+    psi = _c(psi, lat.spinor_shape)
+    out = np.empty_like(psi)
+    _load().orc_hopping(_ptr(lat._dims()), _ptr(lat._theta()), int(lat.spread), _ptr(U),
+                        _ptr(psi), _ptr(out), int(out_parity))
+    return out
+
+
+def apply_M(lat: Lattice, U, psi, kappa: float, mu: float, f: int = 1) -> np.ndarray:
+    """M psi of eq. eo0 on the full lattice (mu~ = 2 kappa mu, flavour sign f)."""
+    U = _c(U, lat.gauge_shape)
+    psi = _c(psi, lat.spinor_shape)
+    out = np.empty_like(psi)
+    _load().orc_apply_M(_ptr(lat._dims()), _ptr(lat._theta()), int(lat.spread), kappa, mu,
+                        int(f), _ptr(U), _ptr(psi), _ptr(out))
+    return out
+
+
+def apply_M_sites(lat: Lattice, U, psi, kappa: float, mu: float, sites, f: int = 1):
+    """(M psi) at the given lexicographic site indices: array (len(sites), 4, 3)."""
+    U = _c(U, lat.gauge_shape)
+    psi = _c(psi, lat.spinor_shape)
+    sites = np.ascontiguousarray(sites, dtype=np.int64)
+    out = np.empty((len(sites), 4, 3), dtype=np.complex128)
+    _load().orc_apply_M_sites(_ptr(lat._dims()), _ptr(lat._theta()), int(lat.spread), kappa,
+                              mu, int(f), _ptr(U), _ptr(psi), _ptr(sites), len(sites),
+                              _ptr(out))
+    return out
+
+
+def apply_Mdiag(lat: Lattice, psi, mut: float, f: int, parity: int) -> np.ndarray:
+    """(1 + i f mu~ gamma5) psi on the sites of one parity (eq. eo2)."""
+    psi = _c(psi, lat.spinor_shape)
+    out = np.empty_like(psi)
+    _load().orc_apply_Mdiag(_ptr(lat._dims()), mut, int(f), int(parity), _ptr(psi), _ptr(out))
+    return out
+
+
+def apply_Mdiag_inv(lat: Lattice, psi, mut: float, f: int, parity: int) -> np.ndarray:
+    """(1 - i f mu~ gamma5)/(1 + mu~^2) psi on the sites of one parity (eq. eo3)."""
+    psi = _c(psi, lat.spinor_shape)
+    out = np.empty_like(psi)
+    _load().orc_apply_Mdiag_inv(_ptr(lat._dims()), mut, int(f), int(parity), _ptr(psi),
+                                _ptr(out))
+    return out
+
+
+def apply_Moff(lat: Lattice, U, psi, kappa: float, out_parity: int) -> np.ndarray:
+    """M_eo (out_parity 0) or M_oe (out_parity 1) = -kappa H restricted (eq. eo2)."""
+    U = _c(U, lat.gauge_shape)
+    psi = _c(psi, lat.spinor_shape)
+    out = np.empty_like(psi)
+    _load().orc_apply_Moff(_ptr(lat._dims()), _ptr(lat._theta()), int(lat.spread), kappa,
+                           _ptr(U), int(out_parity), _ptr(psi), _ptr(out))
+    return out
+
+
+def schur(lat: Lattice, U, v, kappa: float, mu: float, f: int = 1, gamma5: bool = False):
+    """Mhat^f v (or Qhat^f v = gamma5 Mhat^f v) on odd sites, eq. eo2/eo4."""
+    U = _c(U, lat.gauge_shape)
+    v = _c(v, lat.spinor_shape)
+    out = np.empty_like(v)
+    _load().orc_schur(_ptr(lat._dims()), _ptr(lat._theta()), int(lat.spread), kappa, mu,
+                      int(f), _ptr(U), _ptr(v), _ptr(out), int(gamma5))
+    return out
+
+
+def normal_op(lat: Lattice, U, v, kappa: float, mu: float, f: int = 1) -> np.ndarray:
+    """Qhat^f Qhat^-f v on odd sites (eq. eo6)."""
+    U = _c(U, lat.gauge_shape)
+    v = _c(v, lat.spinor_shape)
+    out = np.empty_like(v)
+    _load().orc_normal_op(_ptr(lat._dims()), _ptr(lat._theta()), int(lat.spread), kappa, mu,
+                          int(f), _ptr(U), _ptr(v), _ptr(out))
+    return out
+
+
+@dataclass
+class CGResult:
+    x: np.ndarray
+    converged: bool
+    iters: int
+    relres: float
+
+
+def cg(lat: Lattice, U, b, kappa: float, mu: float, f: int = 1, tol: float = 1e-10,
+       max_iter: int = 10000, x0=None) -> CGResult:
+    """CG on Qhat^f Qhat^-f X = b (odd-site vectors), relative stop ||r||/||b|| < tol."""
+    U = _c(U, lat.gauge_shape)
+    b = _c(b, lat.spinor_shape)
+    x = np.zeros_like(b) if x0 is None else _c(x0, lat.spinor_shape).copy()
+    it = ctypes.c_int(0)
+    rr = ctypes.c_double(0)
+    st = _load().orc_cg(_ptr(lat._dims()), _ptr(lat._theta()), int(lat.spread), kappa, mu,
+                        int(f), _ptr(U), _ptr(b), _ptr(x), tol, int(max_iter),
+                        ctypes.byref(it), ctypes.byref(rr))
+    return CGResult(x, st == 0, it.value, rr.value)
+
+
+def eo_prepare(lat: Lattice, U, phi, kappa: float, mu: float, f: int = 1) -> np.ndarray:
+    """varphi_e = (M_ee)^-1 phi_e, varphi_o = phi_o - M_oe varphi_e (App. B.2)."""
+    U = _c(U, lat.gauge_shape)
+    phi = _c(phi, lat.spinor_shape)
+    out = np.empty_like(phi)
+    _load().orc_eo_prepare(_ptr(lat._dims()), _ptr(lat._theta()), int(lat.spread), kappa, mu,
+                           int(f), _ptr(U), _ptr(phi), _ptr(out))
+    return out
+
+
+def eo_reconstruct(lat: Lattice, U, varphi, psi_o, kappa: float, mu: float,
+                   f: int = 1) -> np.ndarray:
+    """psi_e = varphi_e - (M_ee)^-1 M_eo psi_o (App. B.2); returns psi with both parities."""
+    U = _c(U, lat.gauge_shape)
+    varphi = _c(varphi, lat.spinor_shape)
+    psi = _c(psi_o, lat.spinor_shape).copy()
+    _load().orc_eo_reconstruct(_ptr(lat._dims()), _ptr(lat._theta()), int(lat.spread), kappa,
+                               mu, int(f), _ptr(U), _ptr(varphi), _ptr(psi))
+    return psi
+
+
+@dataclass
+class SolveResult:
+    psi: np.ndarray
+    converged: bool
+    iters: int
+    relres_normal: float
+    relres_full: float
+
+
+def solve(lat: Lattice, U, phi, kappa: float, mu: float, f: int = 1, tol: float = 1e-10,
+          max_iter: int = 10000) -> SolveResult:
+    """M^f psi = phi by even/odd preconditioning + CG (App. B.2, eq. eo6)."""
+    U = _c(U, lat.gauge_shape)
+    phi = _c(phi, lat.spinor_shape)
+    psi = np.zeros_like(phi)
+    it = ctypes.c_int(0)
+    rn = ctypes.c_double(0)
+    rf = ctypes.c_double(0)
+    st = _load().orc_solve(_ptr(lat._dims()), _ptr(lat._theta()), int(lat.spread), kappa, mu,
+                           int(f), _ptr(U), _ptr(phi), _ptr(psi), tol, int(max_iter),
+                           ctypes.byref(it), ctypes.byref(rn), ctypes.byref(rf))
+    return SolveResult(psi, st == 0, it.value, rn.value, rf.value)

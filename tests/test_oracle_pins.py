@@ -1,0 +1,365 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+None of these compares the oracle with itself or with a retyped copy of its own
+formulas.  Each pin is one of: a closed form (free-field spectrum), an algebraic
+identity (Clifford algebra, gauge covariance, gamma5-hermiticity, Schur
+complement), a library routine on a special case (dense inverse, dense solve,
+dense Schur complement) or a worked example derived by hand from the paper
+(tests/golden/point_source_unit_gauge.txt).  Together they are chosen so that a
+dropped term, a wrong sign, a wrong link orientation, a transposed operand or a
+misplaced boundary phase in the oracle fails at least one of them.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import Lattice
+from paper_0905_3331_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "point_source_unit_gauge.txt")
+
+
+# ------------------------------------------------------------------ helpers ---
+def dense_from(apply, lat: Lattice, rows_mask=None, cols_mask=None):
+    """Dense matrix of a linear map on spinor fields, built column by column."""
+    n = 12 * lat.V
+    cols = np.arange(n) if cols_mask is None else np.flatnonzero(cols_mask)
+    rows = np.arange(n) if rows_mask is None else np.flatnonzero(rows_mask)
+    A = np.empty((len(rows), len(cols)), dtype=np.complex128)
+    e = np.zeros(lat.spinor_shape, dtype=np.complex128)
+    flat = e.reshape(-1)
+    for k, j in enumerate(cols):
+        flat[j] = 1.0
+        A[:, k] = apply(e).reshape(-1)[rows]
+        flat[j] = 0.0
+    return A
+
+
+def component_mask(lat: Lattice, parity: int) -> np.ndarray:
+    """Boolean mask over the 12 V spinor components: True on sites of the parity."""
+    odd = lat.parity_mask()
+    m = odd if parity == 1 else ~odd
+    return np.broadcast_to(m[..., None, None], lat.spinor_shape).reshape(-1)
+
+
+def free_field_momenta(lat: Lattice):
+    """Allowed momenta p_nu = (2 n + theta_nu) pi / L_nu (boundary phase of Sec. 2.4)."""
+    ext = (lat.T, lat.Lx, lat.Ly, lat.Lz)
+    grids = [(2 * np.arange(n) + th) * np.pi / n for n, th in zip(ext, lat.theta)]
+    P = np.stack(np.meshgrid(*grids, indexing="ij"), axis=-1).reshape(-1, 4)
+    return P
+
+
+def rel(a, b):
+    return np.linalg.norm(np.ravel(a - b)) / max(np.linalg.norm(np.ravel(b)), 1e-300)
+
+
+def rand_spinor(lat, seed):
+    return inputs.gaussian_spinor(lat.T, lat.Lx, seed)
+
+
+# ------------------------------------------------------------- App. A ---
+def test_gamma_matrices_clifford_algebra():
+    """{gamma_mu, gamma_nu} = 2 delta, each Hermitian, gamma0 gamma1 gamma2 gamma3 = gamma5 = diag(1,1,-1,-1)."""
+    g = [oracle.gamma(k) for k in range(5)]
+    for m in range(4):
+        assert np.allclose(g[m], g[m].conj().T, atol=0)
+        for n in range(4):
+            ac = g[m] @ g[n] + g[n] @ g[m]
+            assert np.array_equal(ac, 2.0 * (m == n) * np.eye(4))
+    assert np.array_equal(g[0] @ g[1] @ g[2] @ g[3], g[4])
+    assert np.array_equal(g[4], np.diag([1.0, 1.0, -1.0, -1.0]).astype(complex))
+    for m in range(4):
+        assert np.array_equal(g[4] @ g[m], -g[m] @ g[4])
+
+
+# --------------------------------------------------- hand-derived example ---
+def _read_golden():
+    hops, diag = [], {}
+    with open(GOLDEN) as fh:
+        for line in fh:
+            line = line.split("#", 1)[0].strip()
+            if not line:
+                continue
+            tok = line.split()
+            if tok[0] == "diag":
+                diag[int(tok[1])] = complex(float(tok[2]), float(tok[3]))
+            else:
+                s0, mu, side = int(tok[0]), int(tok[1]), tok[2]
+                v = np.array([complex(float(tok[3 + 2 * k]), float(tok[4 + 2 * k]))
+                              for k in range(4)])
+                hops.append((s0, mu, side, v))
+    return hops, diag
+
+
+def test_point_source_worked_example():
+    """H and M on a point source over a unit gauge field match the hand-derived values."""
+    lat = Lattice.cubic(4, 4)
+    U = inputs.unit_gauge(4, 4)
+    x0 = (0, 1, 2, 3)  # (t, z, y, x)
+    hops, diag = _read_golden()
+    kappa, mu = 0.125, 0.2
+    c0 = 1
+    for s0 in (0, 2):
+        src = inputs.point_source(4, 4, s0, c0, x0)
+        H = oracle.hopping(lat, U, src)
+        M = oracle.apply_M(lat, U, src, kappa, mu)
+        expect = np.zeros(lat.spinor_shape, dtype=complex)
+        for (s, mu_dir, side, v) in hops:
+            if s != s0:
+                continue
+            # axis of the array for direction mu: t -> 0, x -> 3, y -> 2, z -> 1
+            axis = {0: 0, 1: 3, 2: 2, 3: 1}[mu_dir]
+            site = list(x0)
+            site[axis] = (site[axis] + (-1 if side == "fwd" else 1)) % 4
+            expect[tuple(site)][:, c0] = v
+        assert np.array_equal(H, expect), f"s0={s0}"
+        expect_M = -kappa * expect
+        for s in range(4):
+            if s == s0:
+                expect_M[x0][s, c0] = diag[s0]
+        assert np.allclose(M, expect_M, rtol=0, atol=1e-15)
+
+
+# ------------------------------------------------------ free-field closed form ---
+@pytest.mark.parametrize("T,L", [(2, 2), (4, 2)])
+def test_free_field_eigenvalues_of_M(T, L):
+    """Unit gauge: eigenvalues of M are 1 - 2k sum cos p +- i sqrt(mu~^2 + 4k^2 sum sin^2 p), 6-fold."""
+    lat = Lattice.cubic(T, L)
+    kappa, mu = 0.13, 0.35
+    mut = 2 * kappa * mu
+    U = inputs.unit_gauge(T, L)
+    M = dense_from(lambda v: oracle.apply_M(lat, U, v, kappa, mu), lat)
+    ev = np.linalg.eigvals(M)
+    P = free_field_momenta(lat)
+    a = 1 - 2 * kappa * np.cos(P).sum(1)
+    w = np.sqrt(mut ** 2 + 4 * kappa ** 2 * (np.sin(P) ** 2).sum(1))
+    expect = np.concatenate([np.repeat(a + 1j * w, 6), np.repeat(a - 1j * w, 6)])
+    key = lambda z: np.lexsort((np.round(z.imag, 9), np.round(z.real, 9)))
+    assert np.allclose(ev[key(ev)], expect[key(expect)], atol=1e-10)
+
+
+@pytest.mark.parametrize("T,L,theta", [(4, 4, (1.0, 0.0, 0.0, 0.0)), (4, 2, (0.0, 0.0, 0.0, 0.0)),
+                                       (2, 4, (1.0, 0.5, 0.0, 0.25))])
+def test_free_field_spectrum_of_MdagM(T, L, theta):
+    """Unit gauge: eigenvalues of M^dag M are (1 - 2k sum cos p)^2 + 4k^2 sum sin^2 p + mu~^2, 12-fold."""
+    lat = Lattice(T, L, L, L, theta=theta)
+    kappa, mu = 0.16, 0.01
+    mut = 2 * kappa * mu
+    U = inputs.unit_gauge(T, L)
+    M = dense_from(lambda v: oracle.apply_M(lat, U, v, kappa, mu), lat)
+    ev = np.linalg.eigvalsh(M.conj().T @ M)
+    P = free_field_momenta(lat)
+    lam = (1 - 2 * kappa * np.cos(P).sum(1)) ** 2 + 4 * kappa ** 2 * (np.sin(P) ** 2).sum(1) + mut ** 2
+    assert np.allclose(np.sort(ev), np.sort(np.repeat(lam, 12)), rtol=0, atol=1e-12)
+
+
+# ----------------------------------------------------------- link dependence ---
+def test_gauge_covariance():
+    """U_mu(x) -> G(x) U_mu(x) G(x+mu)^dag, psi -> G psi  implies  M psi -> G M psi."""
+    T, L = 4, 4
+    lat = Lattice.cubic(T, L)
+    U = inputs.random_gauge(T, L, 0.7, seed=11)
+    G = inputs.random_su3(lat.V, 2.0, seed=12).reshape(T, L, L, L, 3, 3)
+    axis = {0: 0, 1: 3, 2: 2, 3: 1}
+    Ug = np.empty_like(U)
+    for mu in range(4):
+        Gfwd = np.roll(G, -1, axis=axis[mu])  # G(x + mu^)
+        Ug[..., mu, :, :] = G @ U[..., mu, :, :] @ np.conj(np.swapaxes(Gfwd, -1, -2))
+    psi = rand_spinor(lat, 13)
+    psig = np.einsum("tzyxab,tzyxsb->tzyxsa", G, psi)
+    kappa, mu = 0.16, 0.05
+    lhs = oracle.apply_M(lat, Ug, psig, kappa, mu)
+    rhs = np.einsum("tzyxab,tzyxsb->tzyxsa", G, oracle.apply_M(lat, U, psi, kappa, mu))
+    assert rel(lhs, rhs) < 1e-13
+
+
+# ------------------------------------------------------- adjoint structure ---
+def test_gamma5_hermiticity_with_twisted_mass():
+    """<chi, g5 M(mu) g5 psi> = <M(-mu) chi, psi>, i.e. g5 M(mu) g5 = M(-mu)^dag."""
+    T, L = 4, 4
+    lat = Lattice.cubic(T, L)
+    U = inputs.random_gauge(T, L, 0.6, seed=21)
+    psi, chi = rand_spinor(lat, 22), rand_spinor(lat, 23)
+    g5 = np.array([1, 1, -1, -1])[:, None]
+    kappa, mu = 0.16, 0.07
+    lhs = np.vdot(chi, g5 * oracle.apply_M(lat, U, g5 * psi, kappa, mu))
+    rhs = np.vdot(oracle.apply_M(lat, U, chi, kappa, -mu), psi)
+    assert abs(lhs - rhs) < 1e-12 * abs(rhs)
+    # and the plain identity at mu = 0; f = -1 is mu -> -mu
+    lhs0 = np.vdot(chi, g5 * oracle.apply_M(lat, U, g5 * psi, kappa, 0.0))
+    rhs0 = np.vdot(oracle.apply_M(lat, U, chi, kappa, 0.0), psi)
+    assert abs(lhs0 - rhs0) < 1e-12 * abs(rhs0)
+    assert np.allclose(oracle.apply_M(lat, U, psi, kappa, mu, f=-1),
+                       oracle.apply_M(lat, U, psi, kappa, -mu), rtol=0, atol=1e-15)
+
+
+# ------------------------------------------------------- boundary phases ---
+@pytest.mark.parametrize("theta", [(1.0, 0.0, 0.0, 0.0), (1.0, 0.3, 0.0, 0.7)])
+def test_boundary_phase_placement_equivalence(theta):
+    """Spread phases (Sec. 4.1.2) = W^dag M W with boundary phases (Sec. 2.4), W = exp(i pi sum theta x/L)."""
+    T, L = 4, 4
+    lb = Lattice(T, L, L, L, theta=theta)
+    ls = Lattice(T, L, L, L, theta=theta, spread=True)
+    U = inputs.random_gauge(T, L, 0.5, seed=31)
+    psi = rand_spinor(lb, 32)
+    t, z, y, x = np.indices((T, L, L, L))
+    ph = np.exp(1j * np.pi * (theta[0] * t / T + theta[1] * x / L + theta[2] * y / L
+                              + theta[3] * z / L))[..., None, None]
+    lhs = oracle.apply_M(ls, U, psi, 0.15, 0.02)
+    rhs = np.conj(ph) * oracle.apply_M(lb, U, ph * psi, 0.15, 0.02)
+    assert rel(lhs, rhs) < 1e-13
+    # and the phase is really there: the periodic operator differs
+    lp = Lattice(T, L, L, L, theta=(0.0, 0.0, 0.0, 0.0))
+    assert rel(oracle.apply_M(lp, U, psi, 0.15, 0.02), oracle.apply_M(lb, U, psi, 0.15, 0.02)) > 1e-3
+
+
+# --------------------------------------------------- even/odd blocks (B.1) ---
+def test_site_diagonal_inverse_is_the_inverse():
+    """(M_ee)^-1 of eq. eo3 equals numpy's inverse of the 12x12 site block and inverts M_ee."""
+    lat = Lattice.cubic(2, 2)
+    mut = 0.37
+    even_site = (0, 0, 0, 0)
+    for f in (+1, -1):
+        blk = np.zeros((12, 12), complex)
+        blk_inv = np.zeros((12, 12), complex)
+        for j in range(12):
+            e = np.zeros(lat.spinor_shape, complex)
+            e[even_site].reshape(-1)[j] = 1.0
+            blk[:, j] = oracle.apply_Mdiag(lat, e, mut, f, 0)[even_site].reshape(-1)
+            blk_inv[:, j] = oracle.apply_Mdiag_inv(lat, e, mut, f, 0)[even_site].reshape(-1)
+        assert np.allclose(blk_inv, np.linalg.inv(blk), rtol=0, atol=1e-15)
+        # M_ee = 1 + i f mu~ gamma5 (x) 1_colour
+        g5 = np.diag([1, 1, -1, -1]).astype(complex)
+        assert np.allclose(blk, np.kron(np.eye(4) + 1j * f * mut * g5, np.eye(3)), atol=1e-16)
+    psi = rand_spinor(lat, 41)
+    back = oracle.apply_Mdiag(lat, oracle.apply_Mdiag_inv(lat, psi, mut, 1, 1), mut, 1, 1)
+    odd = lat.parity_mask()[..., None, None]
+    assert rel(back, np.where(odd, psi, 0)) < 1e-15
+
+
+def test_even_odd_blocks_tile_the_operator():
+    """M = diag - kappa (H_eo + H_oe): the parity-restricted hoppings add up to the full one."""
+    T, L = 4, 4
+    lat = Lattice.cubic(T, L)
+    U = inputs.random_gauge(T, L, 0.5, seed=51)
+    psi = rand_spinor(lat, 52)
+    H = oracle.hopping(lat, U, psi)
+    He = oracle.hopping(lat, U, psi, out_parity=0)
+    Ho = oracle.hopping(lat, U, psi, out_parity=1)
+    assert np.array_equal(He + Ho, H)
+    odd = lat.parity_mask()[..., None, None]
+    # H_eo reads only odd sites: zeroing the even input changes nothing
+    assert np.array_equal(oracle.hopping(lat, U, np.where(odd, psi, 0), out_parity=0), He)
+    kappa, mu = 0.15, 0.03
+    M = oracle.apply_M(lat, U, psi, kappa, mu)
+    D = oracle.apply_Mdiag(lat, psi, 2 * kappa * mu, 1, 0) + oracle.apply_Mdiag(lat, psi, 2 * kappa * mu, 1, 1)
+    assert rel(M, D - kappa * H) < 1e-15
+    assert np.allclose(oracle.apply_Moff(lat, U, psi, kappa, 1), -kappa * Ho, atol=0)
+
+
+@pytest.mark.parametrize("T,L", [(2, 2), (4, 4)])
+def test_schur_operator_is_the_dense_schur_complement(T, L):
+    """Mhat = M_oo - M_oe M_ee^-1 M_eo, computed with numpy from dense blocks of M (eq. eo2/eo4),
+    and det M = det M_ee det Mhat."""
+    lat = Lattice.cubic(T, L)
+    U = inputs.random_gauge(T, L, 0.6, seed=61)
+    kappa, mu = 0.16, 0.04
+    for f in (+1, -1):
+        M = dense_from(lambda v: oracle.apply_M(lat, U, v, kappa, mu, f), lat)
+        e, o = component_mask(lat, 0), component_mask(lat, 1)
+        Mee, Meo = M[np.ix_(e, e)], M[np.ix_(e, o)]
+        Moe, Moo = M[np.ix_(o, e)], M[np.ix_(o, o)]
+        S = Moo - Moe @ np.linalg.solve(Mee, Meo)
+        Mhat = dense_from(lambda v: oracle.schur(lat, U, v, kappa, mu, f), lat,
+                          rows_mask=o, cols_mask=o)
+        assert np.abs(Mhat - S).max() < 1e-13
+        s1, l1 = np.linalg.slogdet(M)
+        s2, l2 = np.linalg.slogdet(Mee)
+        s3, l3 = np.linalg.slogdet(Mhat)
+        assert abs(l1 - (l2 + l3)) < 1e-9 and abs(s1 - s2 * s3) < 1e-9
+        # Qhat = gamma5 Mhat and (Qhat^f)^dag = Qhat^-f (eq. eo6)
+        Q = dense_from(lambda v: oracle.schur(lat, U, v, kappa, mu, f, gamma5=True), lat,
+                       rows_mask=o, cols_mask=o)
+        Qm = dense_from(lambda v: oracle.schur(lat, U, v, kappa, mu, -f, gamma5=True), lat,
+                        rows_mask=o, cols_mask=o)
+        g5 = np.tile(np.repeat([1.0, 1.0, -1.0, -1.0], 3), lat.V // 2)
+        assert np.abs(Q - g5[:, None] * Mhat).max() == 0
+        assert np.abs(Q.conj().T - Qm).max() < 1e-14
+
+
+@pytest.mark.parametrize("T,L", [(2, 2), (4, 4)])
+def test_even_odd_solve_equals_dense_solve(T, L):
+    """The even/odd Schur + CG solve (App. B.2) equals numpy's dense solve of M psi = phi."""
+    lat = Lattice.cubic(T, L)
+    w = inputs.WORKLOADS["4^4"]
+    U = inputs.random_gauge(T, L, w.eps, seed=w.gauge_seed)
+    phi = inputs.gaussian_spinor(T, L, w.source_seed)
+    M = dense_from(lambda v: oracle.apply_M(lat, U, v, w.kappa, w.mu), lat)
+    psi_dense = np.linalg.solve(M, phi.reshape(-1)).reshape(lat.spinor_shape)
+    res = oracle.solve(lat, U, phi, w.kappa, w.mu, tol=1e-13, max_iter=5000)
+    assert res.converged
+    assert rel(res.psi, psi_dense) < 1e-10
+    # residual identities: even part of phi - M psi vanishes, full = normal residual
+    r = phi - oracle.apply_M(lat, U, res.psi, w.kappa, w.mu)
+    odd = lat.parity_mask()[..., None, None]
+    assert np.linalg.norm(np.where(odd, 0, r)) < 1e-14 * np.linalg.norm(phi)
+    varphi = oracle.eo_prepare(lat, U, phi, w.kappa, w.mu)
+    bnorm = np.linalg.norm(np.where(odd, varphi, 0))
+    assert abs(res.relres_full * np.linalg.norm(phi) - res.relres_normal * bnorm) < 1e-13 * bnorm
+
+
+def test_cg_reaches_tolerance_on_4x4x4x4():
+    """4^4 workload (kappa 0.160, mu 0.01, eps 0.3): CG stops with a true relative residual below 1e-10."""
+    w = inputs.WORKLOADS["4^4"]
+    lat = Lattice.cubic(w.T, w.L)
+    U = w.gauge()
+    phi = w.source()
+    res = oracle.solve(lat, U, phi, w.kappa, w.mu, tol=1e-10)
+    assert res.converged and res.relres_normal < 1e-10
+    r = phi - oracle.apply_M(lat, U, res.psi, w.kappa, w.mu)
+    assert np.linalg.norm(r) / np.linalg.norm(phi) < 1e-10
+    # flavour -1 solves M(-mu)
+    res_m = oracle.solve(lat, U, phi, w.kappa, w.mu, f=-1, tol=1e-10)
+    r = phi - oracle.apply_M(lat, U, res_m.psi, w.kappa, -w.mu)
+    assert np.linalg.norm(r) / np.linalg.norm(phi) < 1e-10
+
+
+def test_cg_on_normal_equations_matches_dense():
+    """orc_cg solves Qhat+ Qhat- X = b: compare X with numpy's solve of the dense normal operator."""
+    lat = Lattice.cubic(2, 2)
+    U = inputs.random_gauge(2, 2, 0.5, seed=71)
+    kappa, mu = 0.16, 0.05
+    o = component_mask(lat, 1)
+    A = dense_from(lambda v: oracle.normal_op(lat, U, v, kappa, mu), lat, rows_mask=o, cols_mask=o)
+    assert np.abs(A - A.conj().T).max() < 1e-14
+    b = np.where(lat.parity_mask()[..., None, None], inputs.gaussian_spinor(2, 2, 72), 0)
+    res = oracle.cg(lat, U, b, kappa, mu, tol=1e-13)
+    X = np.linalg.solve(A, b.reshape(-1)[o])
+    assert res.converged and rel(res.x.reshape(-1)[o], X) < 1e-10
+
+
+def test_lambda_min_bound():
+    """M^dag M = W^dag W + mu~^2 >= mu~^2 on a rough random gauge field."""
+    lat = Lattice.cubic(4, 4)
+    U = inputs.random_gauge(4, 4, 0.9, seed=81)
+    kappa, mu = 0.17, 0.05
+    mut = 2 * kappa * mu
+    M = dense_from(lambda v: oracle.apply_M(lat, U, v, kappa, mu), lat)
+    lam = np.linalg.eigvalsh(M.conj().T @ M)
+    assert lam.min() >= mut ** 2 * (1 - 1e-9)
+    M0 = dense_from(lambda v: oracle.apply_M(lat, U, v, kappa, 0.0), lat)
+    lam0 = np.linalg.eigvalsh(M0.conj().T @ M0)
+    assert np.allclose(lam, lam0 + mut ** 2, atol=1e-11)
+
+
+def test_sampled_sites_match_full_application():
+    lat = Lattice.cubic(4, 4)
+    U = inputs.random_gauge(4, 4, 0.5, seed=91)
+    psi = rand_spinor(lat, 92)
+    full = oracle.apply_M(lat, U, psi, 0.16, 0.01).reshape(lat.V, 4, 3)
+    sites = np.array([0, 5, 77, 255, 128])
+    part = oracle.apply_M_sites(lat, U, psi, 0.16, 0.01, sites)
+    assert np.array_equal(part, full[sites])
