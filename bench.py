@@ -1,0 +1,393 @@
+#!/usr/bin/env python3
+"""Benchmark: even/odd CG solves/s to an FP64 true residual of 1e-10 (mixed precision vs
+FP64) and the hopping kernel's bandwidth against the measured HBM roofline.
+
+Workload (default): the 16^3 x 32 lattice, random SU(3) links exp(i eps H) with eps = 0.5,
+kappa = 0.1632, mu = 0.004 (mu~ = 2 kappa mu), Gaussian source.  One step = one complete
+solve of M x = b through the C ABI: packing, source preparation, CG on Qhat+ Qhat- with the
+sloppy operator and FP64 reliable updates, reconstruction and the FP64 true-residual check.
+The L2 cache is flushed (a 512 MB write) before every step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank solves its own system (a different
+source) with no collective on the data path: weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Dslash GB/s & % HBM roofline; CG solves/sec to 1e-10 FP64 residual, mixed vs FP64"
+HOP_FLOPS = 1320  # per output site per hopping application (8 hops x 168 flops - 24)
+
+
+def hop_bytes_per_site(prec: int, nreal: int) -> int:
+    """Algorithmic bytes per output site of one half-lattice hopping application: one input
+    spinor, eight links (4 forward + 4 backward), one output spinor."""
+    spinor = {0: 192, 1: 96, 2: 52}[prec]
+    elem = {0: 8, 1: 4, 2: 2}[prec]
+    return 2 * spinor + 8 * nreal * elem
+
+
+def parse_sloppy(s: str):
+    p, l = s.split(":")
+    return {"f32": 1, "f16": 2}[p], int(l)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def __enter__(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.file is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 8:
+                    rows.append(parts)
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[4 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ GPU arm ---
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_0905_3331_gb300 import (CG_FP64, CG_RELIABLE, F32, F64, LINK18, Lattice, inputs,
+                                       launch_count)
+    from paper_0905_3331_gb300 import build as libbuild
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    libbuild.build()
+
+    w = inputs.WORKLOADS[args.workload]
+    sp, sl = parse_sloppy(args.sloppy)
+    U = w.gauge()
+    phi = w.source(rank)
+    lat = Lattice(w.T, w.L, w.kappa, w.mu)
+    lat.set_gauge(torch.from_numpy(U).to(dev))
+    b = torch.from_numpy(phi).to(dev)
+    x = torch.zeros_like(b)
+    flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    mixed_kw = dict(mode=CG_RELIABLE, sloppy_prec=sp, sloppy_link=sl, delta=args.delta)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max_over_ranks(v: float) -> float:
+        if world == 1:
+            return v
+        import torch.distributed as dist
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def timed_solves(n, kw, host=False):
+        """n solves, each after an L2 flush, timed with CUDA events (device side)."""
+        infos = []
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * n)]
+        if host:
+            bh = torch.from_numpy(phi).pin_memory()
+            xh = torch.zeros_like(bh).pin_memory()
+        total = 0.0
+        for k in range(n):
+            flush.zero_()
+            barrier()
+            torch.cuda.synchronize()
+            ev[2 * k].record(stream)
+            if host:
+                infos.append(lat.solve_cg(xh, bh, tol=1e-10, **kw))
+            else:
+                infos.append(lat.solve_cg(x, b, tol=1e-10, **kw))
+            ev[2 * k + 1].record(stream)
+            torch.cuda.synchronize()
+            total += ev[2 * k].elapsed_time(ev[2 * k + 1]) / 1e3
+        return total, infos
+
+    # warm-up (allocations, gauge copies of every form used)
+    for _ in range(args.warmup):
+        timed_solves(1, mixed_kw)
+
+    # ---- timed region: K mixed-precision solves
+    launches0 = launch_count()
+    with ClockSampler(local) as clk:
+        t_mixed, infos = timed_solves(args.steps, mixed_kw)
+    launches = launch_count() - launches0
+    clocks = clk.summary()
+    t_mixed = max_over_ranks(t_mixed)
+    worst_res = max(i.true_rel_residual for i in infos)
+
+    # ---- FP64 CG on the same system (the comparison the metric asks for)
+    timed_solves(1, dict(mode=CG_FP64))
+    n64 = max(1, min(args.steps, args.fp64_steps))
+    t64, infos64 = timed_solves(n64, dict(mode=CG_FP64))
+    t64 = max_over_ranks(t64)
+
+    # ---- end to end: same solve through the C ABI with pinned HOST buffers
+    timed_solves(1, mixed_kw, host=True)
+    t_e2e, _ = timed_solves(max(1, min(args.steps, 10)), mixed_kw, host=True)
+    n_e2e = max(1, min(args.steps, 10))
+    t_e2e = max_over_ranks(t_e2e)
+
+    # ---- hopping kernel: per-launch CUDA events, L2 flushed before each launch
+    def hop_time(prec, nreal, n, cold=True):
+        nb = lat.half_field_bytes(prec)
+        din = torch.empty(nb, dtype=torch.uint8, device=dev)
+        dout = torch.empty(nb, dtype=torch.uint8, device=dev)
+        half = torch.from_numpy(np.ascontiguousarray(
+            phi.reshape(-1, 4, 3)[: w.V // 2])).to(dev)
+        lat.pack_half(prec, din, half)
+        lat.apply_hopping_eo(1, dout, din, prec, nreal)
+        torch.cuda.synchronize()
+        if cold:
+            ts = []
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            for k in range(n):
+                flush.zero_()
+                e0.record(stream)
+                lat.apply_hopping_eo(k & 1, dout, din, prec, nreal)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1) / 1e3)
+            return statistics.mean(ts)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(n):
+            lat.apply_hopping_eo(k & 1, dout, din, prec, nreal)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / n
+
+    h = w.V // 2
+    peak, peak_kind = peaks()
+    dslash = {}
+    for name, (prec, nreal) in {"f64_18": (F64, 18), "f32_18": (F32, LINK18),
+                                f"{args.sloppy.replace(':', '_')}": (sp, sl)}.items():
+        tc = hop_time(prec, nreal, args.hop_iters)
+        tw = hop_time(prec, nreal, 1000, cold=False)
+        by = hop_bytes_per_site(prec, nreal) * h
+        dslash[name] = {"bytes_per_site": hop_bytes_per_site(prec, nreal),
+                        "us_cold": tc * 1e6, "gbs_cold": by / tc / 1e9,
+                        "frac_hbm_cold": by / tc / 1e9 / peak,
+                        "gflops_cold": HOP_FLOPS * h / tc / 1e9,
+                        "us_l2_resident": tw * 1e6, "gbs_l2_resident": by / tw / 1e9,
+                        "gflops_l2_resident": HOP_FLOPS * h / tw / 1e9}
+    skey = args.sloppy.replace(":", "_")
+    top = dslash[skey]
+    roofline = {"bound": "hbm", "kernel": f"hop_kernel ({args.sloppy} sloppy form)",
+                "achieved": round(top["gbs_cold"], 1), "peak": peak, "unit": "GB/s",
+                "frac": round(top["gbs_cold"] / peak, 4),
+                "traffic": args.traffic, "peak_kind": peak_kind,
+                "timing": "per-launch CUDA events, L2 flushed before each launch"}
+
+    n_units = args.steps * world
+    value = n_units / t_mixed
+    result = {
+        "metric": METRIC, "value": round(value, 3), "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(t_mixed / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"{w.name} lattice, eps {w.eps}, kappa {w.kappa}, mu {w.mu}, "
+                               "Gaussian source; even/odd CG to FP64 true residual 1e-10",
+                   "lattice": w.name, "solver": f"reliable-update CG, sloppy {args.sloppy}, "
+                   f"delta {args.delta}", "l2": "flushed (512 MB write) before every step",
+                   "parallelism": f"replicas x{world} (independent systems)"},
+        "mixed_cg": {"solves_per_s": round(value, 3), "iters": infos[-1].iters,
+                     "reliable_updates": infos[-1].reliable_updates,
+                     "true_rel_residual": worst_res},
+        "fp64_cg": {"solves_per_s": round(n64 * world / t64, 3), "iters": infos64[-1].iters,
+                    "true_rel_residual": infos64[-1].true_rel_residual},
+        "speedup_mixed_vs_fp64": round((n_units / t_mixed) / (n64 * world / t64), 3),
+        "dslash": {k: {kk: (round(vv, 3) if isinstance(vv, float) else vv)
+                       for kk, vv in v.items()} for k, v in dslash.items()},
+        "roofline": roofline,
+        "e2e": {"value": round(n_e2e * world / t_e2e, 3), "unit": "solves/s",
+                "h2d_bytes_per_step": int(phi.nbytes), "d2h_bytes_per_step": int(phi.nbytes)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(w, U, phi, infos64[-1].iters, args.cpu_seconds)
+    lat.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(result))
+
+
+# -------------------------------------------------------------- CPU oracle ---
+def oracle_cg_rate(w, U, phi, seconds: float):
+    """Time the oracle's CG iterations (as it stands) on a bounded sample: returns
+    (seconds per iteration, iterations timed, seconds for prepare + reconstruct)."""
+    import numpy as np
+
+    import oracle
+    lat = oracle.Lattice.cubic(w.T, w.L)
+    t0 = time.perf_counter()
+    varphi = oracle.eo_prepare(lat, U, phi, w.kappa, w.mu)
+    odd = lat.parity_mask()[..., None, None]
+    b = np.where(odd, varphi, 0) * np.array([1, 1, -1, -1])[:, None]
+    t_prep = time.perf_counter() - t0
+    n, t = 0, 0.0
+    k = 1
+    x = None
+    while t < seconds:
+        t1 = time.perf_counter()
+        res = oracle.cg(lat, U, b, w.kappa, w.mu, tol=1e-30, max_iter=k, x0=x)
+        t += time.perf_counter() - t1
+        n += res.iters
+        x = res.x
+        k = min(2 * k, 64)
+    t2 = time.perf_counter()
+    oracle.eo_reconstruct(lat, U, varphi, np.where(odd, x, 0), w.kappa, w.mu)
+    t_rec = time.perf_counter() - t2
+    return t / n, n, t_prep + 2 * t_rec
+
+
+def cpu_baseline(w, U, phi, iters, seconds):
+    import oracle
+    t_it, n, t_fixed = oracle_cg_rate(w, U, phi, seconds)
+    per_solve = t_it * iters + t_fixed
+    return {"value": round(1.0 / per_solve, 6), "unit": "solves/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"oracle FP64 CG on {w.name}: {n} iterations timed ({t_it * 1e3:.1f} ms "
+                      f"each), extrapolated to the {iters} iterations of the GPU FP64 CG, plus "
+                      "one source preparation and reconstruction"}
+
+
+def run_reference(args):
+    """The reference arm: the CPU oracle as it stands, each step a bounded sample."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_0905_3331_gb300 import inputs
+    w = inputs.WORKLOADS[args.workload]
+    U, phi = w.gauge(), w.source()
+    iters = args.ref_iters
+    for _ in range(args.warmup):
+        oracle_cg_rate(w, U, phi, 0.0)
+    per_step = []
+    for _ in range(args.steps):
+        t_it, n, t_fixed = oracle_cg_rate(w, U, phi, args.ref_seconds)
+        per_step.append(t_it * iters + t_fixed)
+    tot = sum(per_step)
+    value = args.steps / tot
+    cb = {"value": round(value, 6), "unit": "solves/s", "cores": oracle.num_threads(),
+          "kind": "oracle",
+          "sample": f"each step: oracle FP64 CG on {w.name} timed for ~{args.ref_seconds} s, "
+                    f"extrapolated to {iters} iterations per solve"}
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "solves/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(tot / args.steps * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{w.name} lattice, eps {w.eps}, kappa {w.kappa}, mu {w.mu}, "
+                               "Gaussian source; even/odd CG to FP64 true residual 1e-10",
+                   "lattice": w.name},
+        "cpu_baseline": cb,
+        "e2e": {"value": round(value, 6), "unit": "solves/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="16^3x32")
+    ap.add_argument("--sloppy", default="f16:12", help="sloppy storage:links, e.g. f32:12, f16:8")
+    ap.add_argument("--delta", type=float, default=0.1)
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--hop-iters", type=int, default=200)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-seconds", type=float, default=8.0)
+    ap.add_argument("--ref-iters", type=int, default=1500,
+                    help="CG iterations per solve used to scale the reference arm's sample")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="ncu dram bytes per launch of the sloppy hopping kernel, if measured")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)  # at least 3 warm-up steps, always
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,200 @@
+/*
+ * tm.h -- C ABI of the GB300 (sm_103a) library for the one-flavour Wilson
+ * twisted-mass Dirac operator and its even/odd-preconditioned CG solve,
+ * following Jansen & Urbach, "tmLQCD: a program suite to simulate Wilson
+ * twisted mass lattice QCD" (arXiv:0905.3331).
+ *
+ * The operator (eq. eo0, App. B.1, hopping-parameter form, Wilson r = 1):
+ *
+ *   (M psi)(x) = [1 + i f mu~ gamma5] psi(x)
+ *                - kappa sum_{mu=t,x,y,z} [ U_mu(x) (1 + gamma_mu) psi(x + mu^)
+ *                                          + U_mu(x - mu^)^dag (1 - gamma_mu) psi(x - mu^) ]
+ *
+ * with mu~ = 2 kappa mu (mu = bare twisted mass mu_q), flavour sign f = +1
+ * ("up", tau3 = +1) or -1, gamma matrices of App. A (chiral basis,
+ * gamma5 = diag(1, 1, -1, -1)).  M relates to D_tm of eq. Dtm by
+ * D_tm = M / (2 kappa) with m0 = 1/(2 kappa) - 4.  Gauge links are periodic;
+ * fermions are antiperiodic in time and periodic in space (Sec. 2.4 with
+ * theta = (1, 0, 0, 0)): the whole phase -1 sits on the hop across t = T-1 <-> 0.
+ *
+ * Conventions shared by all entry points
+ * --------------------------------------
+ * Lattice   T x L^3, T and L even and >= 2.  Site index lex = ((t L + z) L + y) L + x
+ *           (index order t, z, y, x, spin, colour of Sec. 4.7.2).  Direction mu = 0:t,
+ *           1:x, 2:y, 3:z.  Parity (t + x + y + z) mod 2, even = 0.  V = T L^3, h = V/2.
+ * Canonical full field   V x 4 x 3 complex FP64 (24 doubles per site, re then im),
+ *           [lex][spin][colour].  nrhs fields are stacked back to back.
+ * Canonical gauge field  V x 4 x 3 x 3 complex FP64, [lex][mu][row][col] (72 doubles/site).
+ * Half field (device layout) -- one parity p, site index cb = lex / 2 over the
+ *           sites of parity p in lexicographic order (0 <= cb < h):
+ *   TM_F64  double2 blocks [12][h]: block k = complex component 3*spin + colour.   192 h bytes
+ *   TM_F32  float4  blocks [6][h]: block j = components 2j, 2j+1 (re, im, re, im). 96 h bytes
+ *   TM_F16  uint4   blocks [3][h]: block j = components 4j..4j+3 as 8 IEEE halves
+ *           (re, im, ...), then float norm[h]; value = half * norm[cb], where norm is
+ *           the site's largest |re| or |im|.                                     52 h bytes
+ *   nrhs half fields are stacked back to back (stride tm_half_field_bytes()).
+ * Pointers  "device" pointers are CUDA device (or managed) memory of the current
+ *           device.  Arguments named "host or device" are classified with
+ *           cudaPointerGetAttributes: host memory (pinned or pageable) is staged through
+ *           lattice-owned device buffers, with both copies ordered on `stream`.
+ * Streams   `stream` is a cudaStream_t (NULL = legacy default stream).  Every call is
+ *           ordered on it; calls return once the work is enqueued unless stated
+ *           otherwise.  The caller owns every buffer it passes; the lattice owns its
+ *           gauge copies and work space.  One lattice must not be used from two host
+ *           threads or two streams at the same time.
+ * Errors    Every call returns a tm_status and never aborts or exits; on failure
+ *           tm_last_error() gives a message (per host thread).  Device-side conditions
+ *           (non-finite values, a solver that did not converge, a device wait that ran
+ *           out) are reported through status words that the library reads back.
+ */
+#ifndef TM_H
+#define TM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tm_lattice_s *tm_lattice;
+
+typedef enum {
+  TM_OK = 0,
+  TM_ERR_ARG = 1,           /* invalid argument (null pointer, bad enum, aliasing, ...) */
+  TM_ERR_ODD_EXTENT = 2,    /* T or L odd or < 2 */
+  TM_ERR_NO_GAUGE = 3,      /* operator requested before tm_set_gauge */
+  TM_ERR_NOT_SU3 = 4,       /* a link fails |U^dag U - 1| or |det U - 1| <= 1e-10 */
+  TM_ERR_NONFINITE = 5,     /* NaN or Inf in an input */
+  TM_ERR_CUDA = 6,          /* a CUDA runtime call failed */
+  TM_ERR_NOT_CONVERGED = 7, /* max_iter reached; the last iterate is returned */
+  TM_ERR_TIMEOUT = 8,       /* a bounded device-side wait gave up */
+  TM_ERR_OOM = 9,           /* device allocation failed */
+  TM_ERR_UNSUPPORTED = 10   /* a precision / link-format combination that is not built */
+} tm_status;
+
+typedef enum { TM_F64 = 0, TM_F32 = 1, TM_F16 = 2 } tm_prec; /* spinor storage precision */
+
+/* Gauge-link storage: 18 reals, 12 (rows 1-2; row 3 = conj(row1 x row2)) or 8
+ * (a 2-row/column parametrisation of SU(3), reconstructed in registers).  Links
+ * are stored in the precision of the spinors they act on (FP64, FP32, FP16). */
+typedef enum { TM_LINK18 = 18, TM_LINK12 = 12, TM_LINK8 = 8 } tm_link;
+
+/* ---------------------------------------------------------------- lattice --- */
+
+/* Creates a T x L^3 lattice with hopping parameter kappa and bare twisted mass mu
+ * (mu~ = 2 kappa mu; eq. eo0).  No gauge field yet.  Errors: TM_ERR_ODD_EXTENT,
+ * TM_ERR_ARG (out == NULL, non-finite kappa/mu), TM_ERR_CUDA. */
+tm_status tm_lattice_create(int T, int L, double kappa, double mu, tm_lattice *out);
+
+/* Frees every device buffer of the lattice (synchronises the device first). NULL is a no-op. */
+tm_status tm_lattice_destroy(tm_lattice lat);
+
+/* Changes kappa and mu (the gauge copies stay valid). */
+tm_status tm_lattice_set_params(tm_lattice lat, double kappa, double mu);
+
+/* Sizes: V, and the bytes of one half field of precision `prec` (see the layout above). */
+size_t tm_volume(tm_lattice lat);
+size_t tm_half_field_bytes(tm_lattice lat, tm_prec prec);
+
+/* Copies the canonical FP64 gauge field U (host or device; 72 V doubles) into the
+ * lattice, checks that every link is SU(3) (|U^dag U - 1|_max and |det U - 1| <= 1e-10,
+ * all entries finite) and builds the parity-split "gauge copy" of Sec. 4.1 in device
+ * memory: per output parity, per site, the 4 forward links U_mu(x) and the 4 backward
+ * links U_mu(x - mu^)^dag, in the order the hopping kernel reads them.  Reduced-precision
+ * and compressed copies are built on first use.  Synchronises `stream`.
+ * Errors: TM_ERR_NOT_SU3 (nothing is changed), TM_ERR_NONFINITE, TM_ERR_ARG, TM_ERR_CUDA, TM_ERR_OOM. */
+tm_status tm_set_gauge(tm_lattice lat, const double *U, void *stream);
+
+/* ------------------------------------------------------- field conversion --- */
+
+/* Canonical FP64 half field(s) -> device half field(s) of precision `prec`.
+ * src: host or device, nrhs x h x 24 doubles, site order cb (= lex/2 over one parity).
+ * dst: device, nrhs x tm_half_field_bytes(prec).  FP32 / FP16 round to nearest. */
+tm_status tm_pack_half(tm_lattice lat, tm_prec prec, void *dst, const double *src, int nrhs,
+                       void *stream);
+/* Inverse of tm_pack_half: device half field(s) -> canonical FP64 (host or device). */
+tm_status tm_unpack_half(tm_lattice lat, tm_prec prec, double *dst, const void *src, int nrhs,
+                         void *stream);
+
+/* ---------------------------------------------------------------- operator --- */
+
+/* out = M(f) in on the full lattice (eq. eo0), or M(f)^dag in if dagger != 0
+ * (M^dag = gamma5 M(-f) gamma5).  in, out: canonical full fields, host or device,
+ * nrhs x 24 V doubles; out must not overlap in.  Computed in FP64 with 18-real links.
+ * Errors: TM_ERR_NO_GAUGE, TM_ERR_ARG (flavour not +-1, aliasing), TM_ERR_CUDA. */
+tm_status tm_apply_D(tm_lattice lat, double *out, const double *in, int flavour, int dagger,
+                     int nrhs, void *stream);
+
+/* out_p = H_{p,1-p} in: the pure hopping sum of eq. eo0 (without -kappa) onto the sites
+ * of parity out_parity, from the half field of the other parity (H_eo / H_oe of eq. eo2;
+ * M_eo = -kappa H_eo).  in, out: device half fields of precision `prec`, nrhs of them;
+ * out must not overlap in.  Links in format `link` (built on first use).  Arithmetic is
+ * FP64 for TM_F64 and FP32 otherwise.  The spin projection (1 +- gamma_mu) is applied
+ * before the SU(3) multiply (Sec. 4.1), so each hop multiplies two colour vectors.
+ * Errors: TM_ERR_NO_GAUGE, TM_ERR_ARG, TM_ERR_UNSUPPORTED, TM_ERR_CUDA. */
+tm_status tm_apply_hopping_eo(tm_lattice lat, int out_parity, void *out, const void *in,
+                              tm_prec prec, tm_link link, int nrhs, void *stream);
+
+/* out = (M_ee^f)^{-1} in = (1 - i f mu~ gamma5) / (1 + mu~^2) in, site by site (eq. eo3).
+ * in, out: device half fields of precision `prec` (either parity: M_ee = M_oo), nrhs of
+ * them; in == out is allowed.  Errors: TM_ERR_ARG, TM_ERR_CUDA. */
+tm_status tm_apply_Mee_inv(tm_lattice lat, void *out, const void *in, int flavour, tm_prec prec,
+                           int nrhs, void *stream);
+
+/* ------------------------------------------------------------------ solver --- */
+
+typedef enum {
+  TM_CG_FP64 = 0,     /* CG in FP64 throughout */
+  TM_CG_SQRT_EPS = 1, /* Sec. 4.4: FP64 until ||r|| < sqrt(tol) ||b||, then the sloppy
+                         operator; a final FP64 defect correction keeps the true residual */
+  TM_CG_RELIABLE = 2  /* sloppy CG with reliable updates: FP64 true residual and FP64
+                         solution accumulation whenever ||r|| falls by a factor delta */
+} tm_cg_mode;
+
+typedef struct {
+  double tol;           /* relative: stop when ||b - A X|| / ||b|| < tol, b = gamma5 varphi_o */
+  int max_iter;         /* total CG iterations (all precisions) */
+  int mode;             /* tm_cg_mode */
+  int sloppy_prec;      /* tm_prec of the sloppy operator (modes 1, 2) */
+  int sloppy_link;      /* tm_link of the sloppy operator (modes 1, 2) */
+  double delta;         /* reliable-update trigger (mode 2), e.g. 0.1 */
+  int use_x0;           /* nonzero: x holds the initial guess (full field) */
+  int flavour;          /* +1 solves M(+mu) x = b, -1 solves M(-mu) x = b; 0 means +1 */
+} tm_cg_params;
+
+typedef struct {
+  int iters;                 /* CG iterations performed (all precisions) */
+  int reliable_updates;      /* FP64 residual recomputations inside the loop */
+  double true_rel_residual;  /* ||b - M x|| / ||b|| on the full lattice, FP64, recomputed */
+  double schur_rel_residual; /* ||b_o - A X|| / ||b_o|| of the normal equations, FP64 */
+  double seconds;            /* wall time of the call */
+  int status;                /* tm_status of the solve */
+} tm_cg_info;
+
+/* Solves M(f) x = b on the full lattice by even/odd preconditioning (App. B.2): source
+ * preparation varphi_o = b_o - M_oe (M_ee)^{-1} b_e, CG on Qhat^f Qhat^-f X = gamma5 varphi_o
+ * (eq. eo6), x_o = Qhat^-f X, x_e = (M_ee)^{-1}(b_e - M_eo x_o).  x, b: canonical full
+ * fields, host or device, nrhs x 24 V doubles, solved one after another.  Synchronises
+ * `stream` to fill `info` (may be NULL; with nrhs > 1 it describes the worst system).
+ * Errors: TM_ERR_NOT_CONVERGED (x holds the last iterate), TM_ERR_NO_GAUGE, TM_ERR_ARG,
+ * TM_ERR_NONFINITE, TM_ERR_CUDA, TM_ERR_OOM. */
+tm_status tm_solve_cg(tm_lattice lat, double *x, const double *b, int nrhs,
+                      const tm_cg_params *params, tm_cg_info *info, void *stream);
+
+/* Fills params with the defaults: tol 1e-10, max_iter 100000, TM_CG_FP64, sloppy
+ * TM_F32 / TM_LINK12, delta 0.1, use_x0 0, flavour +1. */
+void tm_cg_params_default(tm_cg_params *params);
+
+/* ------------------------------------------------------------------- misc --- */
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char *tm_last_error(void);
+
+/* Kernels the library has launched since tm_reset_launch_count() (all threads). */
+unsigned long long tm_launch_count(void);
+void tm_reset_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TM_H */

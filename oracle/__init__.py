@@ -67,6 +67,7 @@ def _load():
             lib.orc_hopping.argtypes = [P, P, I, P, P, P, I]
             lib.orc_apply_M.argtypes = [P, P, I, D, D, I, P, P, P]
             lib.orc_apply_M_sites.argtypes = [P, P, I, D, D, I, P, P, P, L, P]
+            lib.orc_hopping_sites.argtypes = [P, P, I, P, P, P, L, P]
             lib.orc_apply_Mdiag.argtypes = [P, D, I, I, P, P]
             lib.orc_apply_Mdiag_inv.argtypes = [P, D, I, I, P, P]
             lib.orc_apply_Moff.argtypes = [P, P, I, D, P, I, P, P]
@@ -177,6 +178,17 @@ def apply_M_sites(lat: Lattice, U, psi, kappa: float, mu: float, sites, f: int =
     _load().orc_apply_M_sites(_ptr(lat._dims()), _ptr(lat._theta()), int(lat.spread), kappa,
                               mu, int(f), _ptr(U), _ptr(psi), _ptr(sites), len(sites),
                               _ptr(out))
+    return out
+
+
+def hopping_sites(lat: Lattice, U, psi, sites) -> np.ndarray:
+    """(H psi) at the given lexicographic site indices: array (len(sites), 4, 3)."""
+    U = _c(U, lat.gauge_shape)
+    psi = _c(psi, lat.spinor_shape)
+    sites = np.ascontiguousarray(sites, dtype=np.int64)
+    out = np.empty((len(sites), 4, 3), dtype=np.complex128)
+    _load().orc_hopping_sites(_ptr(lat._dims()), _ptr(lat._theta()), int(lat.spread), _ptr(U),
+                              _ptr(psi), _ptr(sites), len(sites), _ptr(out))
     return out
 
 

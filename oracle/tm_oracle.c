@@ -491,3 +491,16 @@ int orc_num_threads(void) { return omp_get_max_threads(); }
 #else
 int orc_num_threads(void) { return 1; }
 #endif
+
+/* Pure hopping sum H at the listed sites only (same arithmetic as orc_hopping). */
+void orc_hopping_sites(const int dims[4], const double theta[4], int spread, const cplx *U,
+                       const cplx *in, const long *sites, long nsites, cplx *out) {
+  geo_t g = make_geo(dims);
+#pragma omp parallel for schedule(static)
+  for (long k = 0; k < nsites; ++k) {
+    cplx acc[4][3];
+    hopping_site(&g, theta, spread, U, in, sites[k], acc);
+    for (int s = 0; s < 4; ++s)
+      for (int a = 0; a < 3; ++a) out[12 * k + 3 * s + a] = acc[s][a];
+  }
+}

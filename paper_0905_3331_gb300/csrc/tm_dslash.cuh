@@ -1,0 +1,228 @@
+// tm_dslash.cuh -- the hopping kernel H_{p,1-p} (eq. eo0 bracket, Sec. 4.1) with fused
+// site-diagonal epilogues (eq. eo2, eo3) and fused FP64 reductions.
+//
+// One thread computes one output site of one right-hand side:
+//   out(x) = sum_mu [ U_mu(x) (1 + gamma_mu) in(x + mu^) + U_mu(x - mu^)^dag (1 - gamma_mu) in(x - mu^) ]
+// For each of the 8 hops the neighbour spinor is projected onto two spin components first
+// (Sec. 4.1: (1 +- gamma_mu) psi has two independent spin components), the two colour
+// vectors are multiplied by the link, and the lower two spin components are rebuilt from
+// the upper two.  The projections below follow from the gamma matrices of App. A, with
+// s = +1 for the forward hop (1 + gamma_mu) and s = -1 for the backward hop (1 - gamma_mu):
+//   mu = t: h0 = p0 - s p2,   h1 = p1 - s p3;   out2 += -s U h0,  out3 += -s U h1
+//   mu = x: h0 = p0 - i s p3, h1 = p1 - i s p2; out2 += i s U h1, out3 += i s U h0
+//   mu = y: h0 = p0 - s p3,   h1 = p1 + s p2;   out2 += s U h1,   out3 += -s U h0
+//   mu = z: h0 = p0 - i s p2, h1 = p1 + i s p3; out2 += i s U h0, out3 += -i s U h1
+// and out0 += U h0, out1 += U h1 in every direction.  Fermions are antiperiodic in time
+// (Sec. 2.4): the hop across t = T-1 <-> 0 is multiplied by -1.
+#pragma once
+
+#include "tm_internal.cuh"
+
+namespace tmq {
+
+constexpr int HOP_NT = 128;  // threads per block
+
+template <typename R, int MU, int S>
+__device__ __forceinline__ void project(const cpx<R> p[12], cpx<R> h0[3], cpx<R> h1[3]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const cpx<R> p0 = p[c], p1 = p[3 + c], p2 = p[6 + c], p3 = p[9 + c];
+    if (MU == 0) {
+      h0[c] = (S > 0) ? p0 - p2 : p0 + p2;
+      h1[c] = (S > 0) ? p1 - p3 : p1 + p3;
+    } else if (MU == 1) {
+      h0[c] = (S > 0) ? p0 - times_i(p3) : p0 + times_i(p3);
+      h1[c] = (S > 0) ? p1 - times_i(p2) : p1 + times_i(p2);
+    } else if (MU == 2) {
+      h0[c] = (S > 0) ? p0 - p3 : p0 + p3;
+      h1[c] = (S > 0) ? p1 + p2 : p1 - p2;
+    } else {
+      h0[c] = (S > 0) ? p0 - times_i(p2) : p0 + times_i(p2);
+      h1[c] = (S > 0) ? p1 + times_i(p3) : p1 - times_i(p3);
+    }
+  }
+}
+
+template <typename R, int MU, int S>
+__device__ __forceinline__ void accumulate(cpx<R> acc[12], const cpx<R> u0[3], const cpx<R> u1[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    acc[a] = acc[a] + u0[a];
+    acc[3 + a] = acc[3 + a] + u1[a];
+    if (MU == 0) {
+      acc[6 + a] = (S > 0) ? acc[6 + a] - u0[a] : acc[6 + a] + u0[a];
+      acc[9 + a] = (S > 0) ? acc[9 + a] - u1[a] : acc[9 + a] + u1[a];
+    } else if (MU == 1) {
+      acc[6 + a] = (S > 0) ? acc[6 + a] + times_i(u1[a]) : acc[6 + a] - times_i(u1[a]);
+      acc[9 + a] = (S > 0) ? acc[9 + a] + times_i(u0[a]) : acc[9 + a] - times_i(u0[a]);
+    } else if (MU == 2) {
+      acc[6 + a] = (S > 0) ? acc[6 + a] + u1[a] : acc[6 + a] - u1[a];
+      acc[9 + a] = (S > 0) ? acc[9 + a] - u0[a] : acc[9 + a] + u0[a];
+    } else {
+      acc[6 + a] = (S > 0) ? acc[6 + a] + times_i(u0[a]) : acc[6 + a] - times_i(u0[a]);
+      acc[9 + a] = (S > 0) ? acc[9 + a] - times_i(u1[a]) : acc[9 + a] + times_i(u1[a]);
+    }
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void su3_mul2(const Mat3<R>& U, const cpx<R> h0[3], const cpx<R> h1[3],
+                                         cpx<R> u0[3], cpx<R> u1[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    u0[a] = U.m[a][0] * h0[0] + U.m[a][1] * h0[1] + U.m[a][2] * h0[2];
+    u1[a] = U.m[a][0] * h1[0] + U.m[a][1] * h1[1] + U.m[a][2] * h1[2];
+  }
+}
+
+template <int PREC, int NREAL, int MU, int S>
+__device__ __forceinline__ void hop_dir(cpx<typename SpinorFmt<PREC>::real> acc[12], const void* in, int h,
+                                        int nbi, const char* slab, int cb, bool negate) {
+  typedef typename SpinorFmt<PREC>::real R;
+  typedef typename LinkStore<PREC>::type St;
+  constexpr int BYTES = NREAL * LinkStore<PREC>::size;
+  RawWords<BYTES> raw = load_raw<BYTES>(slab, h, cb);
+  cpx<R> p[12];
+  SpinorFmt<PREC>::load(in, h, nbi, p);
+  cpx<R> h0[3], h1[3];
+  project<R, MU, S>(p, h0, h1);
+  if (MU == 0 && negate) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      h0[c] = R(-1) * h0[c];
+      h1[c] = R(-1) * h1[c];
+    }
+  }
+  Mat3<R> U;
+  LinkRecon<R, St, NREAL>::unpack(raw, U);
+  cpx<R> u0[3], u1[3];
+  su3_mul2(U, h0, h1, u0, u1);
+  accumulate<R, MU, S>(acc, u0, u1);
+}
+
+// MODE 0: out = epi(hop).  MODE 1: same plus sum ||out||^2.
+// MODE 2: out buffer holds r (FP64 for FP64 storage, FP32 otherwise); r <- r - alpha * epi(hop),
+// plus sum ||r||^2.
+template <int PREC, int NREAL, bool HAS_Y, int MODE>
+__global__ void __launch_bounds__(HOP_NT) hop_kernel(const Geom g, const int out_parity,
+                                                     const char* __restrict__ links, const void* in,
+                                                     size_t in_stride, void* out, size_t out_stride,
+                                                     const void* y, size_t y_stride, const EpiCoef coef,
+                                                     const CGState* alpha_src, const double alpha_sign,
+                                                     const Reduce red, const int* skip) {
+  typedef typename SpinorFmt<PREC>::real R;
+  __shared__ double sh[HOP_NT / 32];
+  if (skip != nullptr && *skip != 0) return;
+  const int rhs = blockIdx.y;
+  const int cb = blockIdx.x * HOP_NT + threadIdx.x;
+  const bool active = cb < g.h;
+  double nrm = 0.0;
+  if (active) {
+    const SiteCoord c = site_of(g, cb, out_parity);
+    int nb[8];
+    neighbours(g, cb, c, nb);
+    const char* inr = static_cast<const char*>(in) + (size_t)rhs * in_stride;
+    const size_t slab = link_bytes(PREC, NREAL) * (size_t)g.h;
+    const char* lb = links + (size_t)(out_parity * 8) * slab;
+    cpx<R> acc[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = mk<R>(R(0), R(0));
+    const bool tfwd = (c.t == g.T - 1), tbwd = (c.t == 0);
+    hop_dir<PREC, NREAL, 0, +1>(acc, inr, g.h, nb[0], lb + 0 * slab, cb, tfwd);
+    hop_dir<PREC, NREAL, 0, -1>(acc, inr, g.h, nb[4], lb + 4 * slab, cb, tbwd);
+    hop_dir<PREC, NREAL, 1, +1>(acc, inr, g.h, nb[1], lb + 1 * slab, cb, false);
+    hop_dir<PREC, NREAL, 1, -1>(acc, inr, g.h, nb[5], lb + 5 * slab, cb, false);
+    hop_dir<PREC, NREAL, 2, +1>(acc, inr, g.h, nb[2], lb + 2 * slab, cb, false);
+    hop_dir<PREC, NREAL, 2, -1>(acc, inr, g.h, nb[6], lb + 6 * slab, cb, false);
+    hop_dir<PREC, NREAL, 3, +1>(acc, inr, g.h, nb[3], lb + 3 * slab, cb, false);
+    hop_dir<PREC, NREAL, 3, -1>(acc, inr, g.h, nb[7], lb + 7 * slab, cb, false);
+
+    // epilogue: o_s = D_s (c acc_s + E_s y_s)
+    const R cc = (R)coef.c;
+    const cpx<R> Du = mk<R>((R)coef.d_up_re, (R)coef.d_up_im), Dl = mk<R>((R)coef.d_lo_re, (R)coef.d_lo_im);
+    cpx<R> o[12];
+    if (HAS_Y) {
+      const cpx<R> Eu = mk<R>((R)coef.e_up_re, (R)coef.e_up_im), El = mk<R>((R)coef.e_lo_re, (R)coef.e_lo_im);
+      cpx<R> yv[12];
+      SpinorFmt<PREC>::load(static_cast<const char*>(y) + (size_t)rhs * y_stride, g.h, cb, yv);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        const cpx<R> E = (k < 6) ? Eu : El;
+        const cpx<R> D = (k < 6) ? Du : Dl;
+        o[k] = D * (cc * acc[k] + E * yv[k]);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 12; ++k) o[k] = ((k < 6) ? Du : Dl) * (cc * acc[k]);
+    }
+    char* outr = static_cast<char*>(out) + (size_t)rhs * out_stride;
+    if (MODE == 2) {
+      const R al = (R)(alpha_src ? alpha_sign * alpha_src[rhs].alpha : alpha_sign);
+      constexpr int PR = ResidPrec<PREC>::value;
+      cpx<R> r[12];
+      SpinorFmt<PR>::load(outr, g.h, cb, r);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        r[k] = r[k] - al * o[k];
+        nrm += (double)norm2(r[k]);
+      }
+      SpinorFmt<PR>::store(outr, g.h, cb, r);
+    } else {
+      if (MODE == 1) {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) nrm += (double)norm2(o[k]);
+      }
+      SpinorFmt<PREC>::store(outr, g.h, cb, o);
+    }
+  }
+  if (MODE >= 1) {
+    const double bs = block_sum<HOP_NT>(nrm, sh);
+    grid_reduce<HOP_NT>(red, rhs, gridDim.x, blockIdx.x, bs, sh);
+  }
+}
+
+template <int PREC, int NREAL>
+tm_status hop_launch_t(tm_lattice lat, const HopArgs& a, cudaStream_t s) {
+  const Geom& g = lat->geom;
+  dim3 grid((g.h + HOP_NT - 1) / HOP_NT, a.nrhs);
+  const char* links = static_cast<const char*>(lat->links[PREC][link_index(NREAL)]);
+  const bool has_y = a.y != nullptr;
+#define TM_HOP_ARGS                                                                                      \
+  g, a.out_parity, links, a.in, a.in_stride, a.out, a.out_stride, a.y, a.y_stride, a.coef, a.alpha_src, \
+      a.alpha_sign, a.red, a.skip
+  if (!has_y && a.mode == 0)
+    hop_kernel<PREC, NREAL, false, 0><<<grid, HOP_NT, 0, s>>>(TM_HOP_ARGS);
+  else if (!has_y && a.mode == 1)
+    hop_kernel<PREC, NREAL, false, 1><<<grid, HOP_NT, 0, s>>>(TM_HOP_ARGS);
+  else if (has_y && a.mode == 0)
+    hop_kernel<PREC, NREAL, true, 0><<<grid, HOP_NT, 0, s>>>(TM_HOP_ARGS);
+  else if (has_y && a.mode == 1)
+    hop_kernel<PREC, NREAL, true, 1><<<grid, HOP_NT, 0, s>>>(TM_HOP_ARGS);
+  else if (has_y && a.mode == 2)
+    hop_kernel<PREC, NREAL, true, 2><<<grid, HOP_NT, 0, s>>>(TM_HOP_ARGS);
+  else
+    return set_error(TM_ERR_ARG, "hopping: unsupported epilogue combination");
+#undef TM_HOP_ARGS
+  count_launch();
+  return cuda_check(cudaGetLastError(), "hopping kernel launch");
+}
+
+template <int PREC>
+tm_status hop_launch_prec(tm_lattice lat, const HopArgs& a, cudaStream_t s) {
+  switch (a.nreal) {
+    case 18:
+      return hop_launch_t<PREC, 18>(lat, a, s);
+    case 12:
+      return hop_launch_t<PREC, 12>(lat, a, s);
+    case 8:
+      return hop_launch_t<PREC, 8>(lat, a, s);
+    default:
+      return set_error(TM_ERR_ARG, "hopping: link format %d not one of 18, 12, 8", a.nreal);
+  }
+}
+
+tm_status hop_launch_f64(tm_lattice lat, const HopArgs& a, cudaStream_t s);
+tm_status hop_launch_f32(tm_lattice lat, const HopArgs& a, cudaStream_t s);
+tm_status hop_launch_f16(tm_lattice lat, const HopArgs& a, cudaStream_t s);
+
+}  // namespace tmq

@@ -1,0 +1,667 @@
+// tm_internal.cuh -- types and device helpers shared by the library's translation units.
+//
+// Layouts (see include/tm.h for the public part):
+//   half spinor field  per precision, blocks of 16 bytes, block-major ("SoA"): block k of
+//                      site cb at byte offset (k * h + cb) * 16, so a warp reading block k of
+//                      32 consecutive sites issues one fully coalesced 512-byte request.
+//   gauge copy         per output parity p (2), per direction d (8: d = mu forward link
+//                      U_mu(x), d = 4 + mu backward link U_mu(x - mu^)^dag), per 16-byte
+//                      block, per site cb; a link of R reals in storage type S takes
+//                      R * sizeof(S) bytes = NB full 16-byte blocks plus a tail of 0, 4 or 8
+//                      bytes stored in its own block-major array after the full blocks.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "tm.h"
+
+namespace tmq {
+
+// ------------------------------------------------------------------ complex ---
+template <typename R>
+struct cpx {
+  R re, im;
+};
+
+template <typename R>
+__host__ __device__ __forceinline__ cpx<R> mk(R a, R b) {
+  return {a, b};
+}
+template <typename R>
+__device__ __forceinline__ cpx<R> operator+(cpx<R> a, cpx<R> b) {
+  return {a.re + b.re, a.im + b.im};
+}
+template <typename R>
+__device__ __forceinline__ cpx<R> operator-(cpx<R> a, cpx<R> b) {
+  return {a.re - b.re, a.im - b.im};
+}
+template <typename R>
+__device__ __forceinline__ cpx<R> operator*(cpx<R> a, cpx<R> b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename R>
+__device__ __forceinline__ cpx<R> operator*(R s, cpx<R> a) {
+  return {s * a.re, s * a.im};
+}
+template <typename R>
+__device__ __forceinline__ cpx<R> cj(cpx<R> a) {
+  return {a.re, -a.im};
+}
+// conj(a) * b
+template <typename R>
+__device__ __forceinline__ cpx<R> cjmul(cpx<R> a, cpx<R> b) {
+  return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re};
+}
+template <typename R>
+__device__ __forceinline__ cpx<R> times_i(cpx<R> a) {
+  return {-a.im, a.re};
+}
+template <typename R>
+__device__ __forceinline__ cpx<R> times_mi(cpx<R> a) {
+  return {a.im, -a.re};
+}
+template <typename R>
+__device__ __forceinline__ R norm2(cpx<R> a) {
+  return a.re * a.re + a.im * a.im;
+}
+
+// ------------------------------------------------------------------ geometry ---
+// T x L^3 lattice, checkerboard index cb = lex / 2 within one parity.
+struct Geom {
+  int T, L, Lh;      // Lh = L / 2
+  int h;             // sites per parity
+  int sy, sz, st;    // cb strides of y, z, t: Lh, L*Lh, L*L*Lh
+};
+
+struct SiteCoord {
+  int t, z, y, x;
+};
+
+__device__ __forceinline__ SiteCoord site_of(const Geom& g, int cb, int parity) {
+  SiteCoord c;
+  int xh = cb % g.Lh;
+  int r = cb / g.Lh;
+  c.y = r % g.L;
+  r /= g.L;
+  c.z = r % g.L;
+  c.t = r / g.L;
+  c.x = 2 * xh + ((c.t + c.z + c.y + parity) & 1);
+  return c;
+}
+
+// cb indices of the 8 neighbours: nb[mu] = x + mu^, nb[4 + mu] = x - mu^ (periodic wrap).
+__device__ __forceinline__ void neighbours(const Geom& g, int cb, const SiteCoord& c, int nb[8]) {
+  const int row = cb - (c.x >> 1);  // cb of (t, z, y, x = 0 or 1)
+  // t
+  nb[0] = (c.t == g.T - 1) ? cb - (g.T - 1) * g.st : cb + g.st;
+  nb[4] = (c.t == 0) ? cb + (g.T - 1) * g.st : cb - g.st;
+  // x
+  const int xp = (c.x == g.L - 1) ? 0 : c.x + 1;
+  const int xm = (c.x == 0) ? g.L - 1 : c.x - 1;
+  nb[1] = row + (xp >> 1);
+  nb[5] = row + (xm >> 1);
+  // y
+  nb[2] = (c.y == g.L - 1) ? cb - (g.L - 1) * g.sy : cb + g.sy;
+  nb[6] = (c.y == 0) ? cb + (g.L - 1) * g.sy : cb - g.sy;
+  // z
+  nb[3] = (c.z == g.L - 1) ? cb - (g.L - 1) * g.sz : cb + g.sz;
+  nb[7] = (c.z == 0) ? cb + (g.L - 1) * g.sz : cb - g.sz;
+}
+
+// --------------------------------------------------------------- precisions ---
+template <int PREC>
+struct SpinorFmt;
+
+// FP64: double2 blocks [12][h]
+template <>
+struct SpinorFmt<TM_F64> {
+  typedef double real;
+  static constexpr size_t bytes_per_site = 192;
+  template <typename R>
+  __device__ static __forceinline__ void load(const void* base, int h, int i, cpx<R> s[12]) {
+    const double2* p = static_cast<const double2*>(base);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      double2 v = __ldg(p + (size_t)k * h + i);
+      s[k] = mk<R>((R)v.x, (R)v.y);
+    }
+  }
+  template <typename R>
+  __device__ static __forceinline__ void store(void* base, int h, int i, const cpx<R> s[12]) {
+    double2* p = static_cast<double2*>(base);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) p[(size_t)k * h + i] = make_double2((double)s[k].re, (double)s[k].im);
+  }
+};
+
+// FP32: float4 blocks [6][h]
+template <>
+struct SpinorFmt<TM_F32> {
+  typedef float real;
+  static constexpr size_t bytes_per_site = 96;
+  template <typename R>
+  __device__ static __forceinline__ void load(const void* base, int h, int i, cpx<R> s[12]) {
+    const float4* p = static_cast<const float4*>(base);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      float4 v = __ldg(p + (size_t)k * h + i);
+      s[2 * k] = mk<R>((R)v.x, (R)v.y);
+      s[2 * k + 1] = mk<R>((R)v.z, (R)v.w);
+    }
+  }
+  template <typename R>
+  __device__ static __forceinline__ void store(void* base, int h, int i, const cpx<R> s[12]) {
+    float4* p = static_cast<float4*>(base);
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+      p[(size_t)k * h + i] = make_float4((float)s[2 * k].re, (float)s[2 * k].im,
+                                         (float)s[2 * k + 1].re, (float)s[2 * k + 1].im);
+  }
+};
+
+// FP16 + per-site FP32 norm: uint4 blocks [3][h] (8 halves each), then float norm[h].
+template <>
+struct SpinorFmt<TM_F16> {
+  typedef float real;
+  static constexpr size_t bytes_per_site = 52;
+  __device__ static __forceinline__ float2 h2f(unsigned int w) {
+    __half2 hv = *reinterpret_cast<__half2*>(&w);
+    return __half22float2(hv);
+  }
+  __device__ static __forceinline__ unsigned int f2h(float a, float b) {
+    __half2 hv = __floats2half2_rn(a, b);
+    return *reinterpret_cast<unsigned int*>(&hv);
+  }
+  template <typename R>
+  __device__ static __forceinline__ void load(const void* base, int h, int i, cpx<R> s[12]) {
+    const uint4* p = static_cast<const uint4*>(base);
+    const float* nrm = reinterpret_cast<const float*>(p + (size_t)3 * h);
+    const float n = __ldg(nrm + i);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      uint4 v = __ldg(p + (size_t)k * h + i);
+      float2 a = h2f(v.x), b = h2f(v.y), c = h2f(v.z), d = h2f(v.w);
+      s[4 * k + 0] = mk<R>((R)(a.x * n), (R)(a.y * n));
+      s[4 * k + 1] = mk<R>((R)(b.x * n), (R)(b.y * n));
+      s[4 * k + 2] = mk<R>((R)(c.x * n), (R)(c.y * n));
+      s[4 * k + 3] = mk<R>((R)(d.x * n), (R)(d.y * n));
+    }
+  }
+  template <typename R>
+  __device__ static __forceinline__ void store(void* base, int h, int i, const cpx<R> s[12]) {
+    uint4* p = static_cast<uint4*>(base);
+    float* nrm = reinterpret_cast<float*>(p + (size_t)3 * h);
+    float m = 0.f;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) m = fmaxf(m, fmaxf(fabsf((float)s[k].re), fabsf((float)s[k].im)));
+    const float inv = (m > 0.f) ? 1.0f / m : 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      uint4 v;
+      v.x = f2h((float)s[4 * k + 0].re * inv, (float)s[4 * k + 0].im * inv);
+      v.y = f2h((float)s[4 * k + 1].re * inv, (float)s[4 * k + 1].im * inv);
+      v.z = f2h((float)s[4 * k + 2].re * inv, (float)s[4 * k + 2].im * inv);
+      v.w = f2h((float)s[4 * k + 3].re * inv, (float)s[4 * k + 3].im * inv);
+      p[(size_t)k * h + i] = v;
+    }
+    nrm[i] = m;
+  }
+};
+
+// Precision of the iterated residual that goes with an operator storage precision.
+template <int PREC>
+struct ResidPrec {
+  static constexpr int value = (PREC == TM_F64) ? TM_F64 : TM_F32;
+};
+
+__host__ __device__ inline size_t spinor_bytes_per_site(int prec) {
+  return prec == TM_F64 ? 192 : (prec == TM_F32 ? 96 : 52);
+}
+
+// -------------------------------------------------------------------- links ---
+// Storage type per spinor precision: FP64 -> double, FP32 -> float, FP16 -> half.
+template <int PREC>
+struct LinkStore;
+template <>
+struct LinkStore<TM_F64> {
+  typedef double type;
+  static constexpr int size = 8;
+};
+template <>
+struct LinkStore<TM_F32> {
+  typedef float type;
+  static constexpr int size = 4;
+};
+template <>
+struct LinkStore<TM_F16> {
+  typedef __half type;
+  static constexpr int size = 2;
+};
+
+__host__ __device__ inline int link_elem_size(int prec) {
+  return prec == TM_F64 ? 8 : (prec == TM_F32 ? 4 : 2);
+}
+__host__ __device__ inline size_t link_bytes(int prec, int nreal) {
+  return (size_t)nreal * link_elem_size(prec);
+}
+// byte offset of the (parity, dir) slab inside a gauge copy
+__host__ __device__ inline size_t link_slab_offset(int prec, int nreal, int h, int parity, int dir) {
+  return (size_t)(parity * 8 + dir) * link_bytes(prec, nreal) * (size_t)h;
+}
+
+// Load the R raw reals (as 32-bit words) of link (slab, i).
+template <int BYTES>
+struct RawWords {
+  unsigned int w[BYTES / 4];
+};
+
+template <int BYTES>
+__device__ __forceinline__ RawWords<BYTES> load_raw(const char* slab, int h, int i) {
+  RawWords<BYTES> r;
+  constexpr int NB = BYTES / 16;
+  constexpr int TAIL = BYTES % 16;
+  const uint4* blk = reinterpret_cast<const uint4*>(slab);
+#pragma unroll
+  for (int j = 0; j < NB; ++j) {
+    uint4 q = __ldg(blk + (size_t)j * h + i);
+    r.w[4 * j + 0] = q.x;
+    r.w[4 * j + 1] = q.y;
+    r.w[4 * j + 2] = q.z;
+    r.w[4 * j + 3] = q.w;
+  }
+  if (TAIL == 8) {
+    const uint2* t = reinterpret_cast<const uint2*>(slab + (size_t)NB * 16 * h);
+    uint2 q = __ldg(t + i);
+    r.w[4 * NB + 0] = q.x;
+    r.w[4 * NB + 1] = q.y;
+  } else if (TAIL == 4) {
+    const unsigned int* t = reinterpret_cast<const unsigned int*>(slab + (size_t)NB * 16 * h);
+    r.w[4 * NB] = __ldg(t + i);
+  }
+  return r;
+}
+
+template <int BYTES>
+__device__ __forceinline__ void store_raw(char* slab, int h, int i, const RawWords<BYTES>& r) {
+  constexpr int NB = BYTES / 16;
+  constexpr int TAIL = BYTES % 16;
+  uint4* blk = reinterpret_cast<uint4*>(slab);
+#pragma unroll
+  for (int j = 0; j < NB; ++j)
+    blk[(size_t)j * h + i] = make_uint4(r.w[4 * j], r.w[4 * j + 1], r.w[4 * j + 2], r.w[4 * j + 3]);
+  if (TAIL == 8) {
+    uint2* t = reinterpret_cast<uint2*>(slab + (size_t)NB * 16 * h);
+    t[i] = make_uint2(r.w[4 * NB], r.w[4 * NB + 1]);
+  } else if (TAIL == 4) {
+    unsigned int* t = reinterpret_cast<unsigned int*>(slab + (size_t)NB * 16 * h);
+    t[i] = r.w[4 * NB];
+  }
+}
+
+// real number k of a raw link in storage type S
+template <typename S, int BYTES>
+struct RawGet;
+template <int BYTES>
+struct RawGet<double, BYTES> {
+  __device__ static __forceinline__ double get(const RawWords<BYTES>& r, int k) {
+    return __hiloint2double((int)r.w[2 * k + 1], (int)r.w[2 * k]);
+  }
+  __device__ static __forceinline__ void put(RawWords<BYTES>& r, int k, double v) {
+    r.w[2 * k] = (unsigned)__double2loint(v);
+    r.w[2 * k + 1] = (unsigned)__double2hiint(v);
+  }
+};
+template <int BYTES>
+struct RawGet<float, BYTES> {
+  __device__ static __forceinline__ float get(const RawWords<BYTES>& r, int k) {
+    return __uint_as_float(r.w[k]);
+  }
+  __device__ static __forceinline__ void put(RawWords<BYTES>& r, int k, float v) {
+    r.w[k] = __float_as_uint(v);
+  }
+};
+template <int BYTES>
+struct RawGet<__half, BYTES> {
+  __device__ static __forceinline__ float get(const RawWords<BYTES>& r, int k) {
+    unsigned short bits = (unsigned short)((r.w[k >> 1] >> (16 * (k & 1))) & 0xffffu);
+    return __half2float(__ushort_as_half(bits));
+  }
+  __device__ static __forceinline__ void put(RawWords<BYTES>& r, int k, float v) {
+    unsigned int bits = (unsigned int)__half_as_ushort(__float2half_rn(v));
+    unsigned int sh = 16 * (k & 1);
+    r.w[k >> 1] = (r.w[k >> 1] & ~(0xffffu << sh)) | (bits << sh);
+  }
+};
+
+// 3x3 complex matrix in registers, row-major
+template <typename R>
+struct Mat3 {
+  cpx<R> m[3][3];
+};
+
+// Reconstruct a link from its stored reals.
+//  18: all 9 entries, row-major (re, im).
+//  12: rows 0 and 1; row 2 = conj(row0 x row1) (det = 1).
+//   8: a1, a2 (row 0, columns 1, 2), b0 (row 1, column 0), arg(a0)/pi, arg(c0)/pi, where
+//      a, b, c are rows 0, 1, 2.  |a0| follows from the unit norm of row 0, |c0| from the
+//      unit norm of column 0, b1 and b2 from orthogonality of rows 0 and 1 together with
+//      c0 = conj(a1 b2 - a2 b1), and row 2 from c = conj(a x b).
+template <typename R, typename S, int NREAL>
+struct LinkRecon;
+
+template <typename R, typename S>
+struct LinkRecon<R, S, 18> {
+  static constexpr int BYTES = 18 * (int)sizeof(S);
+  __device__ static __forceinline__ void unpack(const RawWords<BYTES>& r, Mat3<R>& U) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+        U.m[a][b] = mk<R>((R)RawGet<S, BYTES>::get(r, 2 * (3 * a + b)),
+                          (R)RawGet<S, BYTES>::get(r, 2 * (3 * a + b) + 1));
+  }
+  __device__ static __forceinline__ void pack(RawWords<BYTES>& r, const Mat3<double>& U) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        RawGet<S, BYTES>::put(r, 2 * (3 * a + b), (S)U.m[a][b].re);
+        RawGet<S, BYTES>::put(r, 2 * (3 * a + b) + 1, (S)U.m[a][b].im);
+      }
+  }
+};
+
+template <typename R>
+__device__ __forceinline__ void third_row(Mat3<R>& U) {
+  U.m[2][0] = cj(U.m[0][1] * U.m[1][2] - U.m[0][2] * U.m[1][1]);
+  U.m[2][1] = cj(U.m[0][2] * U.m[1][0] - U.m[0][0] * U.m[1][2]);
+  U.m[2][2] = cj(U.m[0][0] * U.m[1][1] - U.m[0][1] * U.m[1][0]);
+}
+
+template <typename R, typename S>
+struct LinkRecon<R, S, 12> {
+  static constexpr int BYTES = 12 * (int)sizeof(S);
+  __device__ static __forceinline__ void unpack(const RawWords<BYTES>& r, Mat3<R>& U) {
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+        U.m[a][b] = mk<R>((R)RawGet<S, BYTES>::get(r, 2 * (3 * a + b)),
+                          (R)RawGet<S, BYTES>::get(r, 2 * (3 * a + b) + 1));
+    third_row(U);
+  }
+  __device__ static __forceinline__ void pack(RawWords<BYTES>& r, const Mat3<double>& U) {
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        RawGet<S, BYTES>::put(r, 2 * (3 * a + b), (S)U.m[a][b].re);
+        RawGet<S, BYTES>::put(r, 2 * (3 * a + b) + 1, (S)U.m[a][b].im);
+      }
+  }
+};
+
+template <typename R>
+__device__ __forceinline__ R sqrt_nonneg(R v) {
+  return sqrt(v > R(0) ? v : R(0));
+}
+
+template <typename R, typename S>
+struct LinkRecon<R, S, 8> {
+  static constexpr int BYTES = 8 * (int)sizeof(S);
+  __device__ static __forceinline__ void unpack(const RawWords<BYTES>& r, Mat3<R>& U) {
+    typedef RawGet<S, BYTES> G;
+    const cpx<R> a1 = mk<R>((R)G::get(r, 0), (R)G::get(r, 1));
+    const cpx<R> a2 = mk<R>((R)G::get(r, 2), (R)G::get(r, 3));
+    const cpx<R> b0 = mk<R>((R)G::get(r, 4), (R)G::get(r, 5));
+    const R tha = (R)G::get(r, 6), thc = (R)G::get(r, 7);  // phases / pi
+    const R N = norm2(a1) + norm2(a2);                       // = 1 - |a0|^2
+    const R ma0 = sqrt_nonneg(R(1) - N);
+    const R mc0 = sqrt_nonneg(N - norm2(b0));                // = 1 - |a0|^2 - |b0|^2
+    R sa, ca, sc, cc;
+    sincospi_(tha, &sa, &ca);
+    sincospi_(thc, &sc, &cc);
+    const cpx<R> a0 = mk<R>(ma0 * ca, ma0 * sa);
+    const cpx<R> c0 = mk<R>(mc0 * cc, mc0 * sc);
+    const R invN = R(1) / N;
+    // b1 = -(b0 conj(a0) a1 + conj(a2) conj(c0)) / N ;  b2 = (conj(a1) conj(c0) - a2 b0 conj(a0)) / N
+    const cpx<R> b0ca0 = cjmul(a0, b0);  // conj(a0) b0
+    const cpx<R> b1 = (-invN) * (b0ca0 * a1 + cj(a2 * c0));
+    const cpx<R> b2 = invN * (cj(a1 * c0) - a2 * b0ca0);
+    U.m[0][0] = a0;
+    U.m[0][1] = a1;
+    U.m[0][2] = a2;
+    U.m[1][0] = b0;
+    U.m[1][1] = b1;
+    U.m[1][2] = b2;
+    third_row(U);
+  }
+  __device__ static __forceinline__ void sincospi_(float v, float* s, float* c) { sincospif(v, s, c); }
+  __device__ static __forceinline__ void sincospi_(double v, double* s, double* c) { sincospi(v, s, c); }
+  __device__ static __forceinline__ void pack(RawWords<BYTES>& r, const Mat3<double>& U) {
+    typedef RawGet<S, BYTES> G;
+    G::put(r, 0, (S)U.m[0][1].re);
+    G::put(r, 1, (S)U.m[0][1].im);
+    G::put(r, 2, (S)U.m[0][2].re);
+    G::put(r, 3, (S)U.m[0][2].im);
+    G::put(r, 4, (S)U.m[1][0].re);
+    G::put(r, 5, (S)U.m[1][0].im);
+    G::put(r, 6, (S)(atan2(U.m[0][0].im, U.m[0][0].re) / 3.14159265358979323846));
+    G::put(r, 7, (S)(atan2(U.m[2][0].im, U.m[2][0].re) / 3.14159265358979323846));
+  }
+};
+
+// ---------------------------------------------------------------- epilogue ---
+// out_s = D_s (c * hop_s + E_s * y_s), D and E complex per chirality (s = 0, 1 upper; 2, 3 lower).
+struct EpiCoef {
+  double c;
+  double d_up_re, d_up_im, d_lo_re, d_lo_im;
+  double e_up_re, e_up_im, e_lo_re, e_lo_im;
+};
+
+// Epilogue coefficient sets used by the operators (eq. eo0, eo2, eo3, App. B.2).
+EpiCoef epi_plain();                                    // out = H in
+EpiCoef epi_mdiag_inv_hop(double mut, int f);           // out = (M_ee^f)^-1 H in
+EpiCoef epi_scaled_minv(double mut, int f, double c);   // out = (M_ee^f)^-1 (c H in + y)
+EpiCoef epi_full_M(double kappa, double mut, int f);    // out = (1 + i f mut g5) y - kappa H in
+EpiCoef epi_schur_q(double kappa, double mut, int f);   // out = g5 [(1 + i f mut g5) y - kappa^2 H in]
+EpiCoef epi_g5_y_plus(double c);                        // out = g5 (y + c H in)
+
+// ----------------------------------------------------------------- CG state ---
+// Scalars of one CG system, kept in device memory so that the iteration never
+// needs the host.  Written only by the last block of the kernel that finishes a
+// reduction ("last block done" pattern), read by the following kernels.
+struct CGState {
+  double rr;        // ||r||^2 of the iterated residual
+  double pAp;       // <p, A p> = ||Qhat^-f p||^2
+  double alpha, beta;
+  double stop2;     // stop when rr < stop2 (= tol^2 ||b||^2 for the active stage)
+  double rr_ref;    // reliable updates: ||r||^2 at the last update
+  double delta2;    // reliable updates: trigger when rr < delta2 * rr_ref
+  int iter;         // iterations done in this stage
+  int max_iter;
+  int done;         // iteration loop finished (converged, out of iterations, or failed)
+  int applied;      // iteration count whose solution/direction update has been applied
+  int converged;
+  int nonfinite;
+  int want_update;  // reliable updates: the sloppy residual fell below the trigger
+  int pad;
+};
+
+// What the last block does with the sum of a reduction.
+enum FinKind : int {
+  FIN_STORE = 0,     // result[sys] = sum
+  FIN_CG_ALPHA = 1,  // st.pAp = sum; st.alpha = st.rr / sum
+  FIN_CG_RR = 2      // st.beta = sum / st.rr; st.rr = sum; st.iter++; convergence / trigger tests
+};
+
+struct Reduce {
+  double* partials;    // [nsys][nblocks]
+  unsigned* counters;  // [nsys], zero between uses
+  double* result;      // [nsys] (FIN_STORE)
+  CGState* st;         // [nsys] (FIN_CG_*)
+  int kind;
+};
+
+__device__ __forceinline__ void fin_apply(const Reduce& red, int sys, double sum) {
+  if (red.kind == FIN_STORE) {
+    red.result[sys] = sum;
+  } else if (red.kind == FIN_CG_ALPHA) {
+    CGState& s = red.st[sys];
+    s.pAp = sum;
+    if (!(sum > 0.0) || !isfinite(sum) || !isfinite(s.rr)) {
+      s.nonfinite = (!isfinite(sum) || !isfinite(s.rr)) ? 1 : s.nonfinite;
+      s.alpha = 0.0;
+      s.done = 1;
+    } else {
+      s.alpha = s.rr / sum;
+    }
+  } else if (red.kind == FIN_CG_RR) {
+    CGState& s = red.st[sys];
+    if (!isfinite(sum)) {
+      s.nonfinite = 1;
+      s.done = 1;
+      s.beta = 0.0;
+      return;
+    }
+    s.beta = sum / s.rr;
+    s.rr = sum;
+    s.iter += 1;
+    if (sum < s.stop2) {
+      s.converged = 1;
+      s.done = 1;
+    } else if (s.iter >= s.max_iter) {
+      s.done = 1;
+    } else if (s.delta2 > 0.0 && sum < s.delta2 * s.rr_ref) {
+      s.want_update = 1;
+      s.done = 1;
+    }
+  }
+}
+
+// Deterministic block sum of a double (fixed shuffle tree, then warps in order).
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int w = 0; w < NT / 32; ++w) s += sh[w];
+  }
+  return s;  // valid in thread 0
+}
+
+// Called by every thread of every block with the block's contribution (valid in thread 0).
+// The last block of system `sys` to arrive sums the partials in fixed order and finalises.
+template <int NT>
+__device__ __forceinline__ void grid_reduce(const Reduce& red, int sys, int nblocks, int bid, double bsum,
+                                            double* sh) {
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    red.partials[(size_t)sys * nblocks + bid] = bsum;
+    __threadfence();
+    unsigned prev = atomicAdd(red.counters + sys, 1u);
+    last = (prev == (unsigned)nblocks - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double v = 0.0;
+  const volatile double* parts = red.partials + (size_t)sys * nblocks;
+  for (int k = threadIdx.x; k < nblocks; k += NT) v += parts[k];
+  __syncthreads();
+  double tot = block_sum<NT>(v, sh);
+  if (threadIdx.x == 0) {
+    fin_apply(red, sys, tot);
+    red.counters[sys] = 0u;
+  }
+}
+
+// -------------------------------------------------------------- host side ---
+void count_launch(unsigned n = 1);
+tm_status set_error(tm_status st, const char* fmt, ...);
+tm_status cuda_check(cudaError_t e, const char* what);
+
+}  // namespace tmq
+
+// The lattice object (host side).
+struct tm_lattice_s {
+  int T, L;
+  double kappa, mu;
+  tmq::Geom geom;
+  size_t V, h;
+  int device;
+  bool has_gauge;
+  double* U_canon;          // 72 V doubles, canonical copy on the device
+  void* links[3][3];        // gauge copies [prec][0:18, 1:12, 2:8], built on demand
+  // work space
+  void* ws[32];             // half-field buffers, allocated on demand
+  size_t ws_bytes[32];
+  double* partials;         // reduction partials
+  size_t partials_count;
+  unsigned* counters;       // reduction counters (zeroed)
+  size_t counters_count;
+  double* dscalars;         // small device scalar scratch
+  tmq::CGState* cgstate;     // device CG state array
+  size_t cgstate_count;
+  tmq::CGState* cgstate_host;  // pinned host mirror
+  double* stage;            // device staging buffer for host in/out of full fields
+  size_t stage_bytes;
+  int* flag_host;           // pinned host word
+};
+
+namespace tmq {
+inline int link_index(int nreal) { return nreal == 18 ? 0 : (nreal == 12 ? 1 : 2); }
+tm_status ensure_links(tm_lattice lat, int prec, int nreal, cudaStream_t s);
+void* workspace(tm_lattice lat, int slot, size_t bytes, tm_status* st);
+tm_status ensure_reduce(tm_lattice lat, size_t nparts, size_t ncounters);
+tm_status ensure_cgstate(tm_lattice lat, size_t n);
+bool is_device_pointer(const void* p);
+
+// Hopping launch description (one parity, nrhs fields).
+struct HopArgs {
+  int out_parity;
+  int prec;
+  int nreal;
+  int nrhs;
+  const void* in;
+  size_t in_stride;   // bytes between rhs fields
+  void* out;
+  size_t out_stride;
+  const void* y;      // site-local input (same format as out), or null
+  size_t y_stride;
+  EpiCoef coef;
+  int mode;           // 0 store, 1 store + norm, 2 r -= alpha * out (r = out buffer) + norm
+  const CGState* alpha_src;  // mode 2: alpha = alpha_sign * st[sys].alpha (alpha_sign if null)
+  double alpha_sign;
+  Reduce red;         // modes 1, 2
+  const int* skip;    // if non-null and *skip != 0 the kernel does nothing
+};
+tm_status hop_launch(tm_lattice lat, const HopArgs& a, cudaStream_t s);
+
+// Field conversions (tm_fields.cu)
+tm_status pack_full_parity(tm_lattice lat, int prec, void* dst, const double* src_full, int parity,
+                           int g5, cudaStream_t s);
+tm_status unpack_full_parity(tm_lattice lat, int prec, double* dst_full, const void* src, int parity,
+                             int g5, cudaStream_t s);
+tm_status convert_half(tm_lattice lat, int prec_out, void* dst, int prec_in, const void* src,
+                       cudaStream_t s);
+tm_status apply_M_halves(tm_lattice lat, void* out_e, void* out_o, const void* in_e, const void* in_o, int f,
+                         cudaStream_t s);
+tm_status diag_apply(tm_lattice lat, int prec, void* out, const void* in, int nrhs, double dur, double dui,
+                     double dlr, double dli, cudaStream_t s);
+// Workspace slots: 0..15 solver, 16..19 tm_apply_D, 20 staged input, 21 staged output.
+enum { WS_APPLY_D = 16, WS_STAGE_IN = 20, WS_STAGE_OUT = 21 };
+// host-buffer staging through workspace slots
+const void* stage_in(tm_lattice lat, int slot, const void* src, size_t bytes, cudaStream_t s, tm_status* st);
+void* stage_out(tm_lattice lat, int slot, void* dst, size_t bytes, tm_status* st);
+tm_status stage_out_finish(void* dst, const void* dev, size_t bytes, cudaStream_t s);
+}  // namespace tmq

@@ -1,0 +1,414 @@
+// tm_lattice.cu -- lattice object, error reporting, device buffers, gauge field
+// validation and the parity-split gauge copy (Sec. 4.1: links stored again in the
+// order the operator reads them; here per output parity: 4 forward links U_mu(x)
+// and 4 backward links U_mu(x - mu^)^dag per site, in FP64/FP32/FP16 and with
+// 18, 12 or 8 stored reals).
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+
+#include "tm_dslash.cuh"
+#include "tm_internal.cuh"
+
+namespace tmq {
+
+static thread_local char g_err[1024] = "";
+static std::atomic<unsigned long long> g_launches{0};
+
+void count_launch(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+tm_status set_error(tm_status st, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+tm_status cuda_check(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return TM_OK;
+  if (e == cudaErrorMemoryAllocation)
+    return set_error(TM_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+  return set_error(TM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool is_device_pointer(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// ------------------------------------------------------- epilogue coefficients ---
+EpiCoef epi_plain() {
+  EpiCoef e{};
+  e.c = 1.0;
+  e.d_up_re = e.d_lo_re = 1.0;
+  return e;
+}
+EpiCoef epi_mdiag_inv_hop(double mut, int f) {  // (1 - i f mut g5) / (1 + mut^2) H
+  EpiCoef e{};
+  const double n = 1.0 / (1.0 + mut * mut);
+  e.c = 1.0;
+  e.d_up_re = n;
+  e.d_up_im = -f * mut * n;
+  e.d_lo_re = n;
+  e.d_lo_im = f * mut * n;
+  return e;
+}
+EpiCoef epi_scaled_minv(double mut, int f, double c) {  // (M_ee^f)^-1 (c H + y)
+  EpiCoef e = epi_mdiag_inv_hop(mut, f);
+  e.c = c;
+  e.e_up_re = e.e_lo_re = 1.0;
+  return e;
+}
+EpiCoef epi_full_M(double kappa, double mut, int f) {  // (1 + i f mut g5) y - kappa H
+  EpiCoef e{};
+  e.c = -kappa;
+  e.d_up_re = e.d_lo_re = 1.0;
+  e.e_up_re = 1.0;
+  e.e_up_im = f * mut;
+  e.e_lo_re = 1.0;
+  e.e_lo_im = -f * mut;
+  return e;
+}
+EpiCoef epi_schur_q(double kappa, double mut, int f) {  // g5 [(1 + i f mut g5) y - kappa^2 H]
+  EpiCoef e = epi_full_M(kappa * kappa, mut, f);
+  e.c = -kappa * kappa;
+  e.d_up_re = 1.0;
+  e.d_lo_re = -1.0;
+  return e;
+}
+EpiCoef epi_g5_y_plus(double c) {  // g5 (y + c H)
+  EpiCoef e{};
+  e.c = c;
+  e.d_up_re = 1.0;
+  e.d_lo_re = -1.0;
+  e.e_up_re = e.e_lo_re = 1.0;
+  return e;
+}
+
+// ------------------------------------------------------------------ buffers ---
+void* workspace(tm_lattice lat, int slot, size_t bytes, tm_status* st) {
+  *st = TM_OK;
+  if (slot < 0 || slot >= 32) {
+    *st = set_error(TM_ERR_ARG, "internal: workspace slot %d", slot);
+    return nullptr;
+  }
+  if (lat->ws_bytes[slot] >= bytes && lat->ws[slot] != nullptr) return lat->ws[slot];
+  if (lat->ws[slot]) cudaFree(lat->ws[slot]);
+  lat->ws[slot] = nullptr;
+  lat->ws_bytes[slot] = 0;
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    *st = cuda_check(e, "workspace allocation");
+    return nullptr;
+  }
+  lat->ws[slot] = p;
+  lat->ws_bytes[slot] = bytes;
+  return p;
+}
+
+tm_status ensure_reduce(tm_lattice lat, size_t nparts, size_t ncounters) {
+  if (nparts > lat->partials_count) {
+    if (lat->partials) cudaFree(lat->partials);
+    lat->partials = nullptr;
+    lat->partials_count = 0;
+    tm_status st = cuda_check(cudaMalloc(&lat->partials, nparts * sizeof(double)), "reduction buffer");
+    if (st != TM_OK) return st;
+    lat->partials_count = nparts;
+  }
+  if (ncounters > lat->counters_count) {
+    if (lat->counters) cudaFree(lat->counters);
+    lat->counters = nullptr;
+    lat->counters_count = 0;
+    tm_status st = cuda_check(cudaMalloc(&lat->counters, ncounters * sizeof(unsigned)), "reduction counters");
+    if (st != TM_OK) return st;
+    st = cuda_check(cudaMemset(lat->counters, 0, ncounters * sizeof(unsigned)), "reduction counters");
+    if (st != TM_OK) return st;
+    lat->counters_count = ncounters;
+  }
+  return TM_OK;
+}
+
+tm_status ensure_cgstate(tm_lattice lat, size_t n) {
+  if (n <= lat->cgstate_count) return TM_OK;
+  if (lat->cgstate) cudaFree(lat->cgstate);
+  if (lat->cgstate_host) cudaFreeHost(lat->cgstate_host);
+  lat->cgstate = nullptr;
+  lat->cgstate_host = nullptr;
+  lat->cgstate_count = 0;
+  tm_status st = cuda_check(cudaMalloc(&lat->cgstate, n * sizeof(CGState)), "CG state");
+  if (st != TM_OK) return st;
+  st = cuda_check(cudaMallocHost(&lat->cgstate_host, n * sizeof(CGState)), "CG state (host)");
+  if (st != TM_OK) return st;
+  lat->cgstate_count = n;
+  return TM_OK;
+}
+
+// --------------------------------------------------------- gauge validation ---
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, double v) {
+  atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+}
+
+// dev[0] = max |U^dag U - 1|, dev[1] = max |det U - 1|, dev[2] = number of non-finite entries
+__global__ void check_su3_kernel(const double* __restrict__ U, size_t nlinks, unsigned long long* dev) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nlinks) return;
+  Mat3<double> m;
+  bool finite = true;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      double re = U[18 * i + 6 * a + 2 * b], im = U[18 * i + 6 * a + 2 * b + 1];
+      finite = finite && isfinite(re) && isfinite(im);
+      m.m[a][b] = mk(re, im);
+    }
+  if (!finite) {
+    atomicAdd(dev + 2, 1ull);
+    return;
+  }
+  double du = 0.0;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      cpx<double> s = mk(0.0, 0.0);
+      for (int k = 0; k < 3; ++k) s = s + cjmul(m.m[k][a], m.m[k][b]);
+      s.re -= (a == b) ? 1.0 : 0.0;
+      du = fmax(du, fmax(fabs(s.re), fabs(s.im)));
+    }
+  cpx<double> det = m.m[0][0] * (m.m[1][1] * m.m[2][2] - m.m[1][2] * m.m[2][1]) -
+                    m.m[0][1] * (m.m[1][0] * m.m[2][2] - m.m[1][2] * m.m[2][0]) +
+                    m.m[0][2] * (m.m[1][0] * m.m[2][1] - m.m[1][1] * m.m[2][0]);
+  det.re -= 1.0;
+  atomic_max_nonneg(dev + 0, du);
+  atomic_max_nonneg(dev + 1, sqrt(norm2(det)));
+}
+
+// ------------------------------------------------------------ gauge copies ---
+// Per output parity p and site cb: slab d = mu holds U_mu(x), slab d = 4 + mu holds
+// U_mu(x - mu^)^dag, compressed to NREAL reals of type S.
+template <typename S, int NREAL>
+__global__ void build_links_kernel(Geom g, const double* __restrict__ U, char* __restrict__ out) {
+  const int p = blockIdx.y;
+  const int cb = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cb >= g.h) return;
+  constexpr int BYTES = NREAL * (int)sizeof(S);
+  const SiteCoord c = site_of(g, cb, p);
+  const int n[4] = {g.T, g.L, g.L, g.L};
+  const int xc[4] = {c.t, c.x, c.y, c.z};
+  const size_t lex = (((size_t)c.t * g.L + c.z) * g.L + c.y) * g.L + c.x;
+  const size_t slab = (size_t)BYTES * g.h;
+  for (int mu = 0; mu < 4; ++mu) {
+    int yc[4] = {xc[0], xc[1], xc[2], xc[3]};
+    yc[mu] = (xc[mu] + n[mu] - 1) % n[mu];
+    const size_t lexm = (((size_t)yc[0] * g.L + yc[3]) * g.L + yc[2]) * g.L + yc[1];
+    Mat3<double> F, B;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        const double* uf = U + 72 * lex + 18 * mu + 6 * a + 2 * b;
+        F.m[a][b] = mk(uf[0], uf[1]);
+        const double* ub = U + 72 * lexm + 18 * mu + 6 * b + 2 * a;  // (b, a) entry
+        B.m[a][b] = mk(ub[0], -ub[1]);                             // conjugate transpose
+      }
+    RawWords<BYTES> rf, rb;
+    LinkRecon<double, S, NREAL>::pack(rf, F);
+    LinkRecon<double, S, NREAL>::pack(rb, B);
+    store_raw<BYTES>(out + (size_t)(p * 8 + mu) * slab, g.h, cb, rf);
+    store_raw<BYTES>(out + (size_t)(p * 8 + 4 + mu) * slab, g.h, cb, rb);
+  }
+}
+
+template <typename S, int NREAL>
+static void launch_build(tm_lattice lat, char* out, cudaStream_t s) {
+  dim3 grid((lat->geom.h + 127) / 128, 2);
+  build_links_kernel<S, NREAL><<<grid, 128, 0, s>>>(lat->geom, lat->U_canon, out);
+  count_launch();
+}
+
+tm_status ensure_links(tm_lattice lat, int prec, int nreal, cudaStream_t s) {
+  if (!lat->has_gauge) return set_error(TM_ERR_NO_GAUGE, "no gauge field: call tm_set_gauge first");
+  if (prec < 0 || prec > 2) return set_error(TM_ERR_ARG, "precision %d not one of TM_F64/F32/F16", prec);
+  if (nreal != 18 && nreal != 12 && nreal != 8)
+    return set_error(TM_ERR_ARG, "link format %d not one of 18, 12, 8", nreal);
+  void*& slot = lat->links[prec][link_index(nreal)];
+  if (slot) return TM_OK;
+  const size_t bytes = 16 * link_bytes(prec, nreal) * lat->h;
+  tm_status st = cuda_check(cudaMalloc(&slot, bytes), "gauge copy allocation");
+  if (st != TM_OK) {
+    slot = nullptr;
+    return st;
+  }
+  char* out = static_cast<char*>(slot);
+  if (prec == TM_F64) {
+    if (nreal == 18) launch_build<double, 18>(lat, out, s);
+    if (nreal == 12) launch_build<double, 12>(lat, out, s);
+    if (nreal == 8) launch_build<double, 8>(lat, out, s);
+  } else if (prec == TM_F32) {
+    if (nreal == 18) launch_build<float, 18>(lat, out, s);
+    if (nreal == 12) launch_build<float, 12>(lat, out, s);
+    if (nreal == 8) launch_build<float, 8>(lat, out, s);
+  } else {
+    if (nreal == 18) launch_build<__half, 18>(lat, out, s);
+    if (nreal == 12) launch_build<__half, 12>(lat, out, s);
+    if (nreal == 8) launch_build<__half, 8>(lat, out, s);
+  }
+  return cuda_check(cudaGetLastError(), "gauge copy build");
+}
+
+tm_status hop_launch(tm_lattice lat, const HopArgs& a, cudaStream_t s) {
+  tm_status st = ensure_links(lat, a.prec, a.nreal, s);
+  if (st != TM_OK) return st;
+  switch (a.prec) {
+    case TM_F64:
+      return hop_launch_f64(lat, a, s);
+    case TM_F32:
+      return hop_launch_f32(lat, a, s);
+    case TM_F16:
+      return hop_launch_f16(lat, a, s);
+    default:
+      return set_error(TM_ERR_ARG, "precision %d", a.prec);
+  }
+}
+
+}  // namespace tmq
+
+using namespace tmq;
+
+// ================================================================== C ABI ===
+extern "C" {
+
+const char* tm_last_error(void) { return tmq::g_err; }
+
+unsigned long long tm_launch_count(void) { return tmq::g_launches.load(); }
+void tm_reset_launch_count(void) { tmq::g_launches.store(0); }
+
+tm_status tm_lattice_create(int T, int L, double kappa, double mu, tm_lattice* out) {
+  tmq::g_err[0] = 0;
+  if (!out) return set_error(TM_ERR_ARG, "tm_lattice_create: out is NULL");
+  *out = nullptr;
+  if (T < 2 || L < 2 || (T & 1) || (L & 1))
+    return set_error(TM_ERR_ODD_EXTENT, "tm_lattice_create: T=%d, L=%d must be even and >= 2", T, L);
+  if (!std::isfinite(kappa) || !std::isfinite(mu))
+    return set_error(TM_ERR_ARG, "tm_lattice_create: kappa and mu must be finite");
+  const double Vd = (double)T * L * L * L;
+  if (Vd / 2 > 2.0e9) return set_error(TM_ERR_ARG, "tm_lattice_create: lattice too large");
+  tm_lattice lat = static_cast<tm_lattice>(calloc(1, sizeof(tm_lattice_s)));
+  if (!lat) return set_error(TM_ERR_OOM, "tm_lattice_create: host allocation");
+  lat->T = T;
+  lat->L = L;
+  lat->kappa = kappa;
+  lat->mu = mu;
+  lat->V = (size_t)T * L * L * L;
+  lat->h = lat->V / 2;
+  lat->geom.T = T;
+  lat->geom.L = L;
+  lat->geom.Lh = L / 2;
+  lat->geom.h = (int)lat->h;
+  lat->geom.sy = L / 2;
+  lat->geom.sz = L * (L / 2);
+  lat->geom.st = L * L * (L / 2);
+  tm_status st = cuda_check(cudaGetDevice(&lat->device), "cudaGetDevice");
+  if (st == TM_OK) st = cuda_check(cudaMalloc(&lat->dscalars, 64 * sizeof(double)), "scalar scratch");
+  if (st == TM_OK) st = cuda_check(cudaMallocHost(&lat->flag_host, 64 * sizeof(int)), "host flag");
+  // reduction buffers sized once for every kernel of the library (a hopping launch uses
+  // ceil(h / 128) blocks, the vector kernels at most 152 * 16), so nothing is reallocated
+  // while kernels that use them may be in flight
+  if (st == TM_OK) st = ensure_reduce(lat, (lat->h + 127) / 128 + 152 * 16, 64);
+  if (st == TM_OK) st = ensure_cgstate(lat, 2);
+  if (st != TM_OK) {
+    tm_lattice_destroy(lat);
+    return st;
+  }
+  *out = lat;
+  return TM_OK;
+}
+
+tm_status tm_lattice_destroy(tm_lattice lat) {
+  if (!lat) return TM_OK;
+  cudaDeviceSynchronize();
+  cudaFree(lat->U_canon);
+  for (int p = 0; p < 3; ++p)
+    for (int l = 0; l < 3; ++l) cudaFree(lat->links[p][l]);
+  for (int k = 0; k < 32; ++k) cudaFree(lat->ws[k]);
+  cudaFree(lat->partials);
+  cudaFree(lat->counters);
+  cudaFree(lat->dscalars);
+  cudaFree(lat->cgstate);
+  cudaFree(lat->stage);
+  if (lat->cgstate_host) cudaFreeHost(lat->cgstate_host);
+  if (lat->flag_host) cudaFreeHost(lat->flag_host);
+  free(lat);
+  return TM_OK;
+}
+
+tm_status tm_lattice_set_params(tm_lattice lat, double kappa, double mu) {
+  if (!lat) return set_error(TM_ERR_ARG, "tm_lattice_set_params: lattice is NULL");
+  if (!std::isfinite(kappa) || !std::isfinite(mu))
+    return set_error(TM_ERR_ARG, "tm_lattice_set_params: kappa and mu must be finite");
+  lat->kappa = kappa;
+  lat->mu = mu;
+  return TM_OK;
+}
+
+size_t tm_volume(tm_lattice lat) { return lat ? lat->V : 0; }
+
+size_t tm_half_field_bytes(tm_lattice lat, tm_prec prec) {
+  if (!lat || prec < 0 || prec > 2) return 0;
+  return spinor_bytes_per_site(prec) * lat->h;
+}
+
+tm_status tm_set_gauge(tm_lattice lat, const double* U, void* stream) {
+  tmq::g_err[0] = 0;
+  if (!lat || !U) return set_error(TM_ERR_ARG, "tm_set_gauge: NULL argument");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t n = 72 * lat->V;
+  double* tmp = nullptr;
+  tm_status st = cuda_check(cudaMalloc(&tmp, n * sizeof(double)), "tm_set_gauge: allocation");
+  if (st != TM_OK) return st;
+  st = cuda_check(cudaMemcpyAsync(tmp, U, n * sizeof(double), cudaMemcpyDefault, s), "tm_set_gauge: copy");
+  unsigned long long* dev = reinterpret_cast<unsigned long long*>(lat->dscalars);
+  if (st == TM_OK) st = cuda_check(cudaMemsetAsync(dev, 0, 3 * sizeof(unsigned long long), s), "memset");
+  if (st == TM_OK) {
+    const size_t nl = 4 * lat->V;
+    check_su3_kernel<<<(unsigned)((nl + 255) / 256), 256, 0, s>>>(tmp, nl, dev);
+    count_launch();
+    st = cuda_check(cudaGetLastError(), "tm_set_gauge: check kernel");
+  }
+  unsigned long long hv[3] = {0, 0, 0};
+  if (st == TM_OK) st = cuda_check(cudaMemcpyAsync(hv, dev, sizeof(hv), cudaMemcpyDeviceToHost, s), "readback");
+  if (st == TM_OK) st = cuda_check(cudaStreamSynchronize(s), "tm_set_gauge: synchronise");
+  if (st != TM_OK) {
+    cudaFree(tmp);
+    return st;
+  }
+  double du, dd;
+  memcpy(&du, &hv[0], sizeof(double));
+  memcpy(&dd, &hv[1], sizeof(double));
+  if (hv[2] != 0) {
+    cudaFree(tmp);
+    return set_error(TM_ERR_NONFINITE, "tm_set_gauge: %llu links have non-finite entries", hv[2]);
+  }
+  if (du > 1e-10 || dd > 1e-10) {
+    cudaFree(tmp);
+    return set_error(TM_ERR_NOT_SU3, "tm_set_gauge: max |U^dag U - 1| = %.3e, max |det U - 1| = %.3e", du, dd);
+  }
+  // accept: replace the canonical copy and drop every derived copy
+  cudaFree(lat->U_canon);
+  lat->U_canon = tmp;
+  for (int p = 0; p < 3; ++p)
+    for (int l = 0; l < 3; ++l) {
+      cudaFree(lat->links[p][l]);
+      lat->links[p][l] = nullptr;
+    }
+  lat->has_gauge = true;
+  st = ensure_links(lat, TM_F64, 18, s);
+  if (st != TM_OK) return st;
+  return cuda_check(cudaStreamSynchronize(s), "tm_set_gauge: build");
+}
+
+}  // extern "C"

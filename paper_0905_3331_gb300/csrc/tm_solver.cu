@@ -1,0 +1,668 @@
+// tm_solver.cu -- even/odd-preconditioned CG (App. B.2, eq. eo6) on the device.
+//
+// System:  M^f x = b.  Source preparation varphi_o = b_o - M_oe (M_ee^f)^{-1} b_e, then CG on
+// the Hermitian positive-definite normal operator A = Qhat^f Qhat^{-f} (eq. eo6) with right-
+// hand side b' = gamma5 varphi_o; x_o = Qhat^{-f} X, x_e = (M_ee^f)^{-1}(b_e - M_eo x_o).
+//
+// One CG iteration is five kernels, all on the caller's stream, none of them waiting for the
+// host: the scalars alpha, beta and ||r||^2 live in a device-side CGState written by the last
+// block of the kernel that completes each reduction (deterministic, fixed summation order):
+//   K1  T = (M_ee^{-f})^{-1} H_eo p
+//   K2  W = Qhat^{-f} p = gamma5 [(1 - i f mu~ gamma5) p - kappa^2 H_oe T],  sum ||W||^2 = <p, A p>,
+//       alpha = ||r||^2 / <p, A p>
+//   K3  T = (M_ee^{f})^{-1} H_eo W
+//   K4  r -= alpha Qhat^f W  (= alpha A p, never stored),  sum ||r||^2, beta, convergence test
+//   U   x += alpha p,  p = r + beta p
+// Kernels K1..K4 return at once when the state says "done"; U applies each iteration once.
+// The host enqueues chunks of iterations and checks the state of the previous chunk while the
+// next one runs, so the device does not wait for the host between chunks.
+//
+// Mixed precision: the sloppy operator stores p, T, W in FP32 or FP16 (+ per-site norm) with
+// 12- or 8-real links and FP32 arithmetic; r and the solution increment are FP32; every
+// reduction is FP64.  Reliable updates (TM_CG_RELIABLE): whenever the iterated ||r|| falls by
+// the factor delta since the last update, the increment is added to the FP64 solution X and
+// the FP64 residual b' - A X is recomputed with the FP64 operator and replaces r.  The
+// TM_CG_SQRT_EPS mode follows Sec. 4.4: FP64 until ||r|| / ||b'|| < sqrt(tol), then the sloppy
+// operator; the FP64 recomputation at the end (and further reliable updates if needed)
+// guarantees the requested true residual.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "tm_internal.cuh"
+
+namespace tmq {
+
+constexpr int BNT = 256;
+constexpr int CHUNK = 8;  // CG iterations enqueued per host check
+
+static unsigned blas_blocks(int h) {
+  int nb = (h + BNT - 1) / BNT;
+  return (unsigned)(nb < 152 * 8 ? nb : 152 * 8);
+}
+
+// ------------------------------------------------------------- BLAS kernels ---
+// x += alpha p ; p = r + beta p, once per CG iteration (see `applied`).
+template <int PX, int PP, int PR>
+__global__ void __launch_bounds__(BNT) cg_update_kernel(int h, char* x, char* p, const char* r, CGState* st,
+                                                        unsigned* counter) {
+  CGState& S = st[0];
+  const int iter = S.iter;
+  if (iter == S.applied) return;
+  const double alpha = S.alpha, beta = S.beta;
+  typedef typename SpinorFmt<PX>::real RX;
+  typedef typename SpinorFmt<PP>::real RP;
+  for (int i = blockIdx.x * BNT + threadIdx.x; i < h; i += gridDim.x * BNT) {
+    cpx<RX> xv[12];
+    cpx<RP> pv[12], rv[12];
+    SpinorFmt<PX>::load(x, h, i, xv);
+    SpinorFmt<PP>::load(p, h, i, pv);
+    SpinorFmt<PR>::load(r, h, i, rv);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      xv[k] = xv[k] + (RX)alpha * mk<RX>((RX)pv[k].re, (RX)pv[k].im);
+      pv[k] = rv[k] + (RP)beta * pv[k];
+    }
+    SpinorFmt<PX>::store(x, h, i, xv);
+    SpinorFmt<PP>::store(p, h, i, pv);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    unsigned prev = atomicAdd(counter, 1u);
+    if (prev == gridDim.x - 1) {
+      S.applied = iter;
+      *counter = 0u;
+    }
+  }
+}
+
+template <int P>
+__global__ void __launch_bounds__(BNT) norm2_kernel(int h, const char* x, Reduce red) {
+  __shared__ double sh[BNT / 32];
+  typedef typename SpinorFmt<P>::real R;
+  double v = 0.0;
+  for (int i = blockIdx.x * BNT + threadIdx.x; i < h; i += gridDim.x * BNT) {
+    cpx<R> s[12];
+    SpinorFmt<P>::load(x, h, i, s);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) v += (double)norm2(s[k]);
+  }
+  const double bs = block_sum<BNT>(v, sh);
+  grid_reduce<BNT>(red, 0, gridDim.x, blockIdx.x, bs, sh);
+}
+
+// sum ||a - b||^2 over FP64 half fields
+__global__ void __launch_bounds__(BNT) diffnorm2_kernel(int h, const char* a, const char* b, Reduce red) {
+  __shared__ double sh[BNT / 32];
+  double v = 0.0;
+  for (int i = blockIdx.x * BNT + threadIdx.x; i < h; i += gridDim.x * BNT) {
+    cpx<double> s[12], t[12];
+    SpinorFmt<TM_F64>::load(a, h, i, s);
+    SpinorFmt<TM_F64>::load(b, h, i, t);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) v += norm2(s[k] - t[k]);
+  }
+  const double bs = block_sum<BNT>(v, sh);
+  grid_reduce<BNT>(red, 0, gridDim.x, blockIdx.x, bs, sh);
+}
+
+// X (FP64) += xs (precision PL); xs = 0
+template <int PL>
+__global__ void __launch_bounds__(BNT) accumulate_kernel(int h, char* X, char* xs) {
+  typedef typename SpinorFmt<PL>::real RL;
+  for (int i = blockIdx.x * BNT + threadIdx.x; i < h; i += gridDim.x * BNT) {
+    cpx<double> a[12];
+    cpx<RL> b[12];
+    SpinorFmt<TM_F64>::load(X, h, i, a);
+    SpinorFmt<PL>::load(xs, h, i, b);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      a[k] = a[k] + mk<double>((double)b[k].re, (double)b[k].im);
+      b[k] = mk<RL>(RL(0), RL(0));
+    }
+    SpinorFmt<TM_F64>::store(X, h, i, a);
+    SpinorFmt<PL>::store(xs, h, i, b);
+  }
+}
+
+// y = a x + b y on canonical full fields (n doubles)
+__global__ void axpby_kernel(size_t n, double a, const double* x, double b, double* y) {
+  for (size_t i = (size_t)blockIdx.x * BNT + threadIdx.x; i < n; i += (size_t)gridDim.x * BNT) y[i] = a * x[i] + b * y[i];
+}
+
+// sum of squares of n doubles
+__global__ void __launch_bounds__(BNT) full_norm2_kernel(size_t n, const double* x, Reduce red) {
+  __shared__ double sh[BNT / 32];
+  double v = 0.0;
+  for (size_t i = (size_t)blockIdx.x * BNT + threadIdx.x; i < n; i += (size_t)gridDim.x * BNT) v += x[i] * x[i];
+  const double bs = block_sum<BNT>(v, sh);
+  grid_reduce<BNT>(red, 0, gridDim.x, blockIdx.x, bs, sh);
+}
+
+// ------------------------------------------------------------ host helpers ---
+static tm_status full_norm2(tm_lattice lat, const double* x, double* out, cudaStream_t s) {
+  const size_t n = lat->V * 24;
+  const unsigned nb = (unsigned)std::min<size_t>((n + BNT - 1) / BNT, 152 * 8);
+  tm_status st = ensure_reduce(lat, nb, 4);
+  if (st != TM_OK) return st;
+  Reduce red{lat->partials, lat->counters, lat->dscalars, nullptr, FIN_STORE};
+  full_norm2_kernel<<<nb, BNT, 0, s>>>(n, x, red);
+  count_launch();
+  if ((st = cuda_check(cudaMemcpyAsync(out, lat->dscalars, sizeof(double), cudaMemcpyDeviceToHost, s), "readback")) !=
+      TM_OK)
+    return st;
+  return cuda_check(cudaStreamSynchronize(s), "synchronise");
+}
+
+struct Solver {
+  tm_lattice lat;
+  cudaStream_t s;
+  int f;
+  double mut;
+  size_t hb[3];  // half-field bytes per precision
+};
+
+static tm_status norm2_half(const Solver& S, int prec, const void* x, double* out_host) {
+  tm_lattice lat = S.lat;
+  const unsigned nb = blas_blocks(lat->geom.h);
+  tm_status st = ensure_reduce(lat, nb, 4);
+  if (st != TM_OK) return st;
+  Reduce red{lat->partials, lat->counters, lat->dscalars, nullptr, FIN_STORE};
+  const char* xp = static_cast<const char*>(x);
+  if (prec == TM_F64)
+    norm2_kernel<TM_F64><<<nb, BNT, 0, S.s>>>(lat->geom.h, xp, red);
+  else if (prec == TM_F32)
+    norm2_kernel<TM_F32><<<nb, BNT, 0, S.s>>>(lat->geom.h, xp, red);
+  else
+    norm2_kernel<TM_F16><<<nb, BNT, 0, S.s>>>(lat->geom.h, xp, red);
+  count_launch();
+  if ((st = cuda_check(cudaGetLastError(), "norm kernel")) != TM_OK) return st;
+  if ((st = cuda_check(cudaMemcpyAsync(out_host, lat->dscalars, sizeof(double), cudaMemcpyDeviceToHost, S.s),
+                       "readback")) != TM_OK)
+    return st;
+  return cuda_check(cudaStreamSynchronize(S.s), "synchronise");
+}
+
+// A = Qhat^f Qhat^{-f} applied to `in` (precision prec, links nreal), result folded into
+// `r` as r -= alpha A in.  With `state` the iteration form is used (skip when done, alpha from
+// the state, FIN_CG_ALPHA / FIN_CG_RR); without it alpha = 1 and ||r||^2 goes to dscalars[0].
+static tm_status normal_apply(const Solver& S, int prec, int nreal, const void* in, void* T, void* W, void* r,
+                              CGState* state) {
+  tm_lattice lat = S.lat;
+  const int h = lat->geom.h;
+  const unsigned nb = (unsigned)((h + 127) / 128);
+  tm_status st = ensure_reduce(lat, nb, 4);
+  if (st != TM_OK) return st;
+  HopArgs a{};
+  a.prec = prec;
+  a.nreal = nreal;
+  a.nrhs = 1;
+  a.skip = state ? &state->done : nullptr;
+  // K1: T = (M_ee^{-f})^-1 H_eo in
+  a.out_parity = 0;
+  a.in = in;
+  a.out = T;
+  a.coef = epi_mdiag_inv_hop(S.mut, -S.f);
+  a.mode = 0;
+  if ((st = hop_launch(lat, a, S.s)) != TM_OK) return st;
+  // K2: W = Qhat^{-f} in, <in, A in> = ||W||^2
+  a.out_parity = 1;
+  a.in = T;
+  a.y = in;
+  a.out = W;
+  a.coef = epi_schur_q(lat->kappa, S.mut, -S.f);
+  if (state) {
+    a.mode = 1;
+    a.red = Reduce{lat->partials, lat->counters, nullptr, state, FIN_CG_ALPHA};
+  } else {
+    a.mode = 0;
+  }
+  if ((st = hop_launch(lat, a, S.s)) != TM_OK) return st;
+  // K3: T = (M_ee^{f})^-1 H_eo W
+  a.out_parity = 0;
+  a.in = W;
+  a.y = nullptr;
+  a.out = T;
+  a.coef = epi_mdiag_inv_hop(S.mut, S.f);
+  a.mode = 0;
+  if ((st = hop_launch(lat, a, S.s)) != TM_OK) return st;
+  // K4: r -= alpha Qhat^f W
+  a.out_parity = 1;
+  a.in = T;
+  a.y = W;
+  a.out = r;
+  a.coef = epi_schur_q(lat->kappa, S.mut, S.f);
+  a.mode = 2;
+  if (state) {
+    a.alpha_src = state;
+    a.alpha_sign = 1.0;
+    a.red = Reduce{lat->partials, lat->counters, nullptr, state, FIN_CG_RR};
+  } else {
+    a.alpha_src = nullptr;
+    a.alpha_sign = 1.0;
+    a.red = Reduce{lat->partials, lat->counters, lat->dscalars, nullptr, FIN_STORE};
+  }
+  return hop_launch(lat, a, S.s);
+}
+
+static tm_status launch_update(const Solver& S, int px, int pp, void* x, void* p, const void* r, CGState* state) {
+  tm_lattice lat = S.lat;
+  const unsigned nb = blas_blocks(lat->geom.h);
+  char* xc = static_cast<char*>(x);
+  char* pc = static_cast<char*>(p);
+  const char* rc = static_cast<const char*>(r);
+  unsigned* ctr = lat->counters + 2;
+  if (px == TM_F64)
+    cg_update_kernel<TM_F64, TM_F64, TM_F64><<<nb, BNT, 0, S.s>>>(lat->geom.h, xc, pc, rc, state, ctr);
+  else if (pp == TM_F32)
+    cg_update_kernel<TM_F32, TM_F32, TM_F32><<<nb, BNT, 0, S.s>>>(lat->geom.h, xc, pc, rc, state, ctr);
+  else
+    cg_update_kernel<TM_F32, TM_F16, TM_F32><<<nb, BNT, 0, S.s>>>(lat->geom.h, xc, pc, rc, state, ctr);
+  count_launch();
+  return cuda_check(cudaGetLastError(), "CG update kernel");
+}
+
+// The vectors of one CG stage: x (PX), r (ResidPrec of op), p / T / W (op precision).
+struct Stage {
+  int prec;   // operator storage precision
+  int nreal;  // link format
+  int px;     // precision of x
+  void *x, *r, *p, *T, *W;
+};
+
+static tm_status enqueue_iterations(const Solver& S, const Stage& v, CGState* dst, int n) {
+  tm_status st = TM_OK;
+  for (int k = 0; k < n && st == TM_OK; ++k) {
+    st = normal_apply(S, v.prec, v.nreal, v.p, v.T, v.W, v.r, dst);
+    if (st == TM_OK) st = launch_update(S, v.px, v.prec, v.x, v.p, v.r, dst);
+  }
+  return st;
+}
+
+// Runs CG iterations from `init` until the device state says done (and the last update has
+// been applied).  Two chunks are in flight: the host reads the state after chunk k while
+// chunk k + 1 runs; chunks after the end cost only empty launches.
+static tm_status run_stage(const Solver& S, const Stage& v, const CGState& init, CGState* out) {
+  tm_lattice lat = S.lat;
+  tm_status st = ensure_cgstate(lat, 2);
+  if (st != TM_OK) return st;
+  CGState* dst = lat->cgstate;
+  CGState* hst = lat->cgstate_host;
+  hst[0] = init;
+  if ((st = cuda_check(cudaMemcpyAsync(dst, &hst[0], sizeof(CGState), cudaMemcpyHostToDevice, S.s), "state"))
+      != TM_OK)
+    return st;
+  if ((st = cuda_check(cudaStreamSynchronize(S.s), "state upload")) != TM_OK) return st;
+  cudaEvent_t ev[2];
+  cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming);
+  cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming);
+  int cur = 0;
+  st = enqueue_iterations(S, v, dst, CHUNK);
+  if (st == TM_OK) st = cuda_check(cudaMemcpyAsync(&hst[cur], dst, sizeof(CGState), cudaMemcpyDeviceToHost, S.s), "state");
+  if (st == TM_OK) st = cuda_check(cudaEventRecord(ev[cur], S.s), "event");
+  while (st == TM_OK) {
+    const int nxt = cur ^ 1;
+    st = enqueue_iterations(S, v, dst, CHUNK);
+    if (st == TM_OK)
+      st = cuda_check(cudaMemcpyAsync(&hst[nxt], dst, sizeof(CGState), cudaMemcpyDeviceToHost, S.s), "state");
+    if (st == TM_OK) st = cuda_check(cudaEventRecord(ev[nxt], S.s), "event");
+    if (st == TM_OK) st = cuda_check(cudaEventSynchronize(ev[cur]), "CG chunk");
+    if (st != TM_OK) break;
+    const CGState c = hst[cur];
+    if (c.done && c.applied == c.iter) {
+      st = cuda_check(cudaEventSynchronize(ev[nxt]), "CG chunk");
+      *out = hst[nxt];
+      break;
+    }
+    cur = nxt;
+  }
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  return st;
+}
+
+// r = b' - A X in FP64 (r, X, b' FP64 odd fields; T, W FP64 temporaries); returns ||r||^2.
+static tm_status true_residual(const Solver& S, void* r, const void* X, const void* bp, void* T, void* W,
+                               double* rr) {
+  tm_status st = cuda_check(cudaMemcpyAsync(r, bp, S.hb[TM_F64], cudaMemcpyDeviceToDevice, S.s), "copy");
+  if (st != TM_OK) return st;
+  if ((st = normal_apply(S, TM_F64, 18, X, T, W, r, nullptr)) != TM_OK) return st;
+  if ((st = cuda_check(cudaMemcpyAsync(rr, S.lat->dscalars, sizeof(double), cudaMemcpyDeviceToHost, S.s),
+                       "readback")) != TM_OK)
+    return st;
+  return cuda_check(cudaStreamSynchronize(S.s), "synchronise");
+}
+
+static CGState fresh_state(double rr, double stop2, int max_iter, int iter0, double delta2) {
+  CGState c;
+  memset(&c, 0, sizeof(c));
+  c.rr = rr;
+  c.rr_ref = rr;
+  c.stop2 = stop2;
+  c.max_iter = max_iter;
+  c.iter = iter0;
+  c.applied = iter0;
+  c.delta2 = delta2;
+  return c;
+}
+
+// Solves M^f x = b for one canonical full field (device pointers).
+static tm_status solve_one(tm_lattice lat, double* x, const double* b, const tm_cg_params& P, tm_cg_info* info,
+                           cudaStream_t s) {
+  Solver S{lat, s, P.flavour, 2.0 * lat->kappa * lat->mu, {0, 0, 0}};
+  for (int p = 0; p < 3; ++p) S.hb[p] = spinor_bytes_per_site(p) * lat->h;
+  tm_status st = TM_OK;
+  // FP64 fields: 0 b_e, 1 b_o, 2 b', 3 X, 4 R, 5 P, 6 T, 7 W
+  void* w[8];
+  for (int k = 0; k < 8; ++k) {
+    w[k] = workspace(lat, k, S.hb[TM_F64], &st);
+    if (st != TM_OK) return st;
+  }
+  void *be = w[0], *bo = w[1], *bp = w[2], *X = w[3], *R = w[4], *Pv = w[5], *T = w[6], *W = w[7];
+
+  // ---- source preparation (App. B.2): b' = gamma5 (b_o + kappa H_oe (M_ee^f)^-1 b_e)
+  if ((st = pack_full_parity(lat, TM_F64, be, b, 0, 0, s)) != TM_OK) return st;
+  if ((st = pack_full_parity(lat, TM_F64, bo, b, 1, 0, s)) != TM_OK) return st;
+  {
+    const double n = 1.0 / (1.0 + S.mut * S.mut);
+    if ((st = diag_apply(lat, TM_F64, T, be, 1, n, -S.f * S.mut * n, n, S.f * S.mut * n, s)) != TM_OK) return st;
+    HopArgs a{};
+    a.prec = TM_F64;
+    a.nreal = 18;
+    a.nrhs = 1;
+    a.out_parity = 1;
+    a.in = T;
+    a.y = bo;
+    a.out = bp;
+    a.coef = epi_g5_y_plus(lat->kappa);
+    if ((st = hop_launch(lat, a, s)) != TM_OK) return st;
+  }
+  double bb = 0.0, bfull = 0.0, tmp = 0.0;
+  if ((st = norm2_half(S, TM_F64, bp, &bb)) != TM_OK) return st;
+  if ((st = norm2_half(S, TM_F64, be, &tmp)) != TM_OK) return st;
+  bfull = tmp;
+  if ((st = norm2_half(S, TM_F64, bo, &tmp)) != TM_OK) return st;
+  bfull += tmp;
+  if (!std::isfinite(bb) || !std::isfinite(bfull))
+    return set_error(TM_ERR_NONFINITE, "tm_solve_cg: the source has non-finite entries");
+  info->iters = 0;
+  info->reliable_updates = 0;
+  if (bfull == 0.0) {
+    st = cuda_check(cudaMemsetAsync(x, 0, lat->V * 24 * sizeof(double), s), "memset");
+    info->true_rel_residual = 0.0;
+    info->schur_rel_residual = 0.0;
+    info->status = TM_OK;
+    return st;
+  }
+  const double tol2 = P.tol * P.tol;
+  const double stop2 = tol2 * bb;
+  int iters = 0, updates = 0;
+  bool converged = false;
+  double rr_true = bb;
+  if ((st = cuda_check(cudaMemsetAsync(X, 0, S.hb[TM_F64], s), "memset")) != TM_OK) return st;
+
+  if (P.mode == TM_CG_FP64) {
+    // ---- plain FP64 CG, restarted from the recomputed residual if the iterated one drifted
+    if ((st = cuda_check(cudaMemcpyAsync(R, bp, S.hb[TM_F64], cudaMemcpyDeviceToDevice, s), "copy")) != TM_OK)
+      return st;
+    if ((st = cuda_check(cudaMemcpyAsync(Pv, bp, S.hb[TM_F64], cudaMemcpyDeviceToDevice, s), "copy")) != TM_OK)
+      return st;
+    Stage v{TM_F64, 18, TM_F64, X, R, Pv, T, W};
+    double rr = bb;
+    for (;;) {
+      CGState fin;
+      if ((st = run_stage(S, v, fresh_state(rr, stop2, P.max_iter, iters, 0.0), &fin)) != TM_OK) return st;
+      if (fin.nonfinite) return set_error(TM_ERR_NONFINITE, "tm_solve_cg: non-finite value in the iteration");
+      const bool progress = fin.iter > iters;
+      iters = fin.iter;
+      if ((st = true_residual(S, R, X, bp, T, W, &rr_true)) != TM_OK) return st;
+      ++updates;
+      if (rr_true < stop2) {
+        converged = true;
+        break;
+      }
+      if (iters >= P.max_iter || !fin.converged || !progress) break;
+      // restart: p = r = b' - A X
+      if ((st = cuda_check(cudaMemcpyAsync(Pv, R, S.hb[TM_F64], cudaMemcpyDeviceToDevice, s), "copy")) != TM_OK)
+        return st;
+      rr = rr_true;
+    }
+  } else {
+    // ---- mixed precision
+    const int sp = P.sloppy_prec, sl = P.sloppy_link;
+    void *rs = nullptr, *xs = nullptr, *ps = nullptr, *Ts = nullptr, *Ws = nullptr;
+    rs = workspace(lat, 8, S.hb[TM_F32], &st);
+    if (st == TM_OK) xs = workspace(lat, 9, S.hb[TM_F32], &st);
+    if (st == TM_OK) ps = workspace(lat, 10, S.hb[sp], &st);
+    if (st == TM_OK) Ts = workspace(lat, 11, S.hb[sp], &st);
+    if (st == TM_OK) Ws = workspace(lat, 12, S.hb[sp], &st);
+    if (st != TM_OK) return st;
+    Stage v{sp, sl, TM_F32, xs, rs, ps, Ts, Ws};
+    if ((st = cuda_check(cudaMemsetAsync(xs, 0, S.hb[TM_F32], s), "memset")) != TM_OK) return st;
+    double rr = bb;
+    if (P.mode == TM_CG_SQRT_EPS) {
+      // FP64 until ||r||^2 < tol ||b'||^2 (i.e. ||r|| / ||b'|| < sqrt(tol)), Sec. 4.4
+      if ((st = cuda_check(cudaMemcpyAsync(R, bp, S.hb[TM_F64], cudaMemcpyDeviceToDevice, s), "copy")) != TM_OK)
+        return st;
+      if ((st = cuda_check(cudaMemcpyAsync(Pv, bp, S.hb[TM_F64], cudaMemcpyDeviceToDevice, s), "copy")) != TM_OK)
+        return st;
+      Stage v64{TM_F64, 18, TM_F64, X, R, Pv, T, W};
+      CGState fin;
+      const double stop_sw = std::fmax(P.tol * bb, stop2);
+      if ((st = run_stage(S, v64, fresh_state(rr, stop_sw, P.max_iter, 0, 0.0), &fin)) != TM_OK) return st;
+      iters = fin.iter;
+      if (fin.nonfinite) return set_error(TM_ERR_NONFINITE, "tm_solve_cg: non-finite value in the iteration");
+      rr = fin.rr;
+      // continue with the sloppy operator from the current r and p
+      if ((st = convert_half(lat, TM_F32, rs, TM_F64, R, s)) != TM_OK) return st;
+      if ((st = convert_half(lat, sp, ps, TM_F64, Pv, s)) != TM_OK) return st;
+      // first sloppy stage runs without reliable updates (the paper's switch)
+      if ((st = run_stage(S, v, fresh_state(rr, stop2, P.max_iter, iters, 0.0), &fin)) != TM_OK) return st;
+      iters = fin.iter;
+      if (fin.nonfinite) return set_error(TM_ERR_NONFINITE, "tm_solve_cg: non-finite value in the iteration");
+      {
+        const unsigned nbb = blas_blocks(lat->geom.h);
+        accumulate_kernel<TM_F32><<<nbb, BNT, 0, s>>>(lat->geom.h, static_cast<char*>(X), static_cast<char*>(xs));
+        count_launch();
+      }
+      if ((st = true_residual(S, R, X, bp, T, W, &rr_true)) != TM_OK) return st;
+      ++updates;
+      converged = rr_true < stop2;
+      rr = rr_true;
+      if (!converged && iters < P.max_iter) {
+        if ((st = convert_half(lat, TM_F32, rs, TM_F64, R, s)) != TM_OK) return st;
+      }
+    } else {
+      if ((st = convert_half(lat, TM_F32, rs, TM_F64, bp, s)) != TM_OK) return st;
+      if ((st = convert_half(lat, sp, ps, TM_F64, bp, s)) != TM_OK) return st;
+    }
+    // reliable-update loop (also the defect correction of the sqrt(eps) mode)
+    const double delta2 = P.delta * P.delta;
+    while (!converged && iters < P.max_iter) {
+      CGState fin;
+      if ((st = run_stage(S, v, fresh_state(rr, stop2, P.max_iter, iters, delta2), &fin)) != TM_OK) return st;
+      if (fin.nonfinite) return set_error(TM_ERR_NONFINITE, "tm_solve_cg: non-finite value in the iteration");
+      if (fin.iter == iters) break;  // no progress (breakdown of <p, A p>): stop, report not converged
+      iters = fin.iter;
+      const unsigned nbb = blas_blocks(lat->geom.h);
+      accumulate_kernel<TM_F32><<<nbb, BNT, 0, s>>>(lat->geom.h, static_cast<char*>(X), static_cast<char*>(xs));
+      count_launch();
+      if ((st = cuda_check(cudaGetLastError(), "accumulate kernel")) != TM_OK) return st;
+      if ((st = true_residual(S, R, X, bp, T, W, &rr_true)) != TM_OK) return st;
+      ++updates;
+      if (rr_true < stop2) {
+        converged = true;
+        break;
+      }
+      if (!(rr_true < 1e300)) return set_error(TM_ERR_NONFINITE, "tm_solve_cg: residual diverged");
+      if ((st = convert_half(lat, TM_F32, rs, TM_F64, R, s)) != TM_OK) return st;
+      rr = rr_true;
+    }
+  }
+  info->iters = iters;
+  info->reliable_updates = updates;
+  info->schur_rel_residual = std::sqrt(rr_true / bb);
+
+  // ---- reconstruction: x_o = Qhat^{-f} X, x_e = (M_ee^f)^-1 (b_e + kappa H_eo x_o)
+  {
+    HopArgs a{};
+    a.prec = TM_F64;
+    a.nreal = 18;
+    a.nrhs = 1;
+    a.out_parity = 0;
+    a.in = X;
+    a.out = T;
+    a.coef = epi_mdiag_inv_hop(S.mut, -S.f);
+    if ((st = hop_launch(lat, a, s)) != TM_OK) return st;
+    a.out_parity = 1;
+    a.in = T;
+    a.y = X;
+    a.out = W;  // x_o
+    a.coef = epi_schur_q(lat->kappa, S.mut, -S.f);
+    if ((st = hop_launch(lat, a, s)) != TM_OK) return st;
+    a.out_parity = 0;
+    a.in = W;
+    a.y = be;
+    a.out = T;  // x_e
+    a.coef = epi_scaled_minv(S.mut, S.f, lat->kappa);
+    if ((st = hop_launch(lat, a, s)) != TM_OK) return st;
+  }
+  // ---- true residual of the full system: ||b - M x|| / ||b|| (FP64)
+  {
+    double rre = 0.0, rro = 0.0;
+    if ((st = apply_M_halves(lat, R, Pv, T, W, S.f, s)) != TM_OK) return st;  // R = (M x)_e, Pv = (M x)_o
+    const unsigned nb = blas_blocks(lat->geom.h);
+    if ((st = ensure_reduce(lat, nb, 4)) != TM_OK) return st;
+    Reduce red{lat->partials, lat->counters, lat->dscalars, nullptr, FIN_STORE};
+    diffnorm2_kernel<<<nb, BNT, 0, s>>>(lat->geom.h, static_cast<const char*>(be), static_cast<const char*>(R), red);
+    count_launch();
+    if ((st = cuda_check(cudaMemcpyAsync(&lat->flag_host[0], lat->dscalars, sizeof(double), cudaMemcpyDeviceToHost, s),
+                         "readback")) != TM_OK)
+      return st;
+    if ((st = cuda_check(cudaStreamSynchronize(s), "synchronise")) != TM_OK) return st;
+    memcpy(&rre, &lat->flag_host[0], sizeof(double));
+    diffnorm2_kernel<<<nb, BNT, 0, s>>>(lat->geom.h, static_cast<const char*>(bo), static_cast<const char*>(Pv), red);
+    count_launch();
+    if ((st = cuda_check(cudaMemcpyAsync(&lat->flag_host[0], lat->dscalars, sizeof(double), cudaMemcpyDeviceToHost, s),
+                         "readback")) != TM_OK)
+      return st;
+    if ((st = cuda_check(cudaStreamSynchronize(s), "synchronise")) != TM_OK) return st;
+    memcpy(&rro, &lat->flag_host[0], sizeof(double));
+    info->true_rel_residual = std::sqrt((rre + rro) / bfull);
+  }
+  if ((st = unpack_full_parity(lat, TM_F64, x, T, 0, 0, s)) != TM_OK) return st;
+  if ((st = unpack_full_parity(lat, TM_F64, x, W, 1, 0, s)) != TM_OK) return st;
+  info->status = converged ? TM_OK : TM_ERR_NOT_CONVERGED;
+  if (!converged)
+    return set_error(TM_ERR_NOT_CONVERGED, "tm_solve_cg: not converged after %d iterations (||r||/||b|| = %.3e)",
+                     iters, info->schur_rel_residual);
+  return TM_OK;
+}
+
+}  // namespace tmq
+
+using namespace tmq;
+
+extern "C" {
+
+void tm_cg_params_default(tm_cg_params* p) {
+  if (!p) return;
+  p->tol = 1e-10;
+  p->max_iter = 100000;
+  p->mode = TM_CG_FP64;
+  p->sloppy_prec = TM_F32;
+  p->sloppy_link = TM_LINK12;
+  p->delta = 0.1;
+  p->use_x0 = 0;
+  p->flavour = 1;
+}
+
+tm_status tm_solve_cg(tm_lattice lat, double* x, const double* b, int nrhs, const tm_cg_params* params,
+                      tm_cg_info* info, void* stream) {
+  const auto t0 = std::chrono::steady_clock::now();
+  if (!lat || !x || !b || nrhs < 1) return set_error(TM_ERR_ARG, "tm_solve_cg: bad argument");
+  if (!lat->has_gauge) return set_error(TM_ERR_NO_GAUGE, "tm_solve_cg: no gauge field");
+  tm_cg_params P;
+  if (params)
+    P = *params;
+  else
+    tm_cg_params_default(&P);
+  if (P.flavour == 0) P.flavour = 1;
+  if (P.flavour != 1 && P.flavour != -1) return set_error(TM_ERR_ARG, "tm_solve_cg: flavour must be +1 or -1");
+  if (!(P.tol > 0.0) || P.max_iter < 1) return set_error(TM_ERR_ARG, "tm_solve_cg: tol > 0 and max_iter >= 1");
+  if (P.mode < TM_CG_FP64 || P.mode > TM_CG_RELIABLE) return set_error(TM_ERR_ARG, "tm_solve_cg: mode %d", P.mode);
+  if (P.mode != TM_CG_FP64) {
+    if (P.sloppy_prec != TM_F32 && P.sloppy_prec != TM_F16)
+      return set_error(TM_ERR_ARG, "tm_solve_cg: sloppy precision must be TM_F32 or TM_F16");
+    if (P.sloppy_link != 18 && P.sloppy_link != 12 && P.sloppy_link != 8)
+      return set_error(TM_ERR_ARG, "tm_solve_cg: sloppy link format %d", P.sloppy_link);
+    if (!(P.delta > 0.0 && P.delta < 1.0)) return set_error(TM_ERR_ARG, "tm_solve_cg: delta must be in (0, 1)");
+  }
+  const size_t fbytes = lat->V * 24 * sizeof(double);
+  if (x == b) return set_error(TM_ERR_ARG, "tm_solve_cg: x and b must differ");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  tm_status st;
+  const double* db = static_cast<const double*>(stage_in(lat, WS_STAGE_IN, b, fbytes * nrhs, s, &st));
+  if (st != TM_OK) return st;
+  double* dx = static_cast<double*>(stage_out(lat, WS_STAGE_OUT, x, fbytes * nrhs, &st));
+  if (st != TM_OK) return st;
+  if (P.use_x0 && dx != x) {
+    st = cuda_check(cudaMemcpyAsync(dx, x, fbytes * nrhs, cudaMemcpyHostToDevice, s), "x0 copy");
+    if (st != TM_OK) return st;
+  }
+  tm_cg_info worst{};
+  worst.status = TM_OK;
+  tm_status result = TM_OK;
+  for (int r = 0; r < nrhs; ++r) {
+    double* xr = dx + (size_t)r * lat->V * 24;
+    const double* br = db + (size_t)r * lat->V * 24;
+    tm_cg_info one{};
+    if (P.use_x0) {
+      // defect correction from the initial guess: x = x0 + M^-1 (b - M x0)
+      double* d = static_cast<double*>(workspace(lat, 13, 2 * fbytes, &st));
+      if (st != TM_OK) return st;
+      double* r0 = d;
+      double* delta = d + lat->V * 24;
+      const size_t n = lat->V * 24;
+      const unsigned nb = (unsigned)std::min<size_t>((n + BNT - 1) / BNT, 152 * 16);
+      if ((st = tm_apply_D(lat, r0, xr, P.flavour, 0, 1, stream)) != TM_OK) return st;
+      axpby_kernel<<<nb, BNT, 0, s>>>(n, 1.0, br, -1.0, r0);  // r0 = b - M x0
+      count_launch();
+      st = solve_one(lat, delta, r0, P, &one, s);
+      if (st != TM_OK && st != TM_ERR_NOT_CONVERGED) return st;
+      axpby_kernel<<<nb, BNT, 0, s>>>(n, 1.0, delta, 1.0, xr);  // x = x0 + delta
+      count_launch();
+      tm_status st2 = cuda_check(cudaGetLastError(), "axpby kernel");
+      if (st2 != TM_OK) return st2;
+      {
+        // true residual relative to b
+        double* rfull = r0;
+        if ((st2 = tm_apply_D(lat, rfull, xr, P.flavour, 0, 1, stream)) != TM_OK) return st2;
+        axpby_kernel<<<nb, BNT, 0, s>>>(n, 1.0, br, -1.0, rfull);
+        count_launch();
+        double num = 0.0, den = 0.0;
+        if ((st2 = full_norm2(lat, rfull, &num, s)) != TM_OK) return st2;
+        if ((st2 = full_norm2(lat, br, &den, s)) != TM_OK) return st2;
+        one.true_rel_residual = den > 0 ? std::sqrt(num / den) : 0.0;
+      }
+    } else {
+      st = solve_one(lat, xr, br, P, &one, s);
+    }
+    if (st != TM_OK && st != TM_ERR_NOT_CONVERGED) return st;
+    if (st == TM_ERR_NOT_CONVERGED) result = st;
+    if (r == 0 || one.true_rel_residual > worst.true_rel_residual) worst = one;
+    if (one.iters > worst.iters) worst.iters = one.iters;
+  }
+  if (dx != x) {
+    if ((st = stage_out_finish(x, dx, fbytes * nrhs, s)) != TM_OK) return st;
+  }
+  if ((st = cuda_check(cudaStreamSynchronize(s), "tm_solve_cg: synchronise")) != TM_OK) return st;
+  worst.status = result;
+  worst.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (info) *info = worst;
+  return result;
+}
+
+}  // extern "C"

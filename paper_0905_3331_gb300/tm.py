@@ -1,0 +1,232 @@
+"""Python binding of the C ABI in include/tm.h (ctypes; argument marshalling only).
+
+Every operation runs in the CUDA library libtmqcd.so built from csrc/ for sm_103a.
+There is no fallback: if the library is missing or no GPU is present the calls
+raise.  Buffers may be torch tensors (CUDA or CPU), numpy arrays or raw integer
+addresses; streams default to torch's current CUDA stream.
+
+Canonical arrays (complex128, order t, z, y, x, spin, colour):
+  spinor (T, L, L, L, 4, 3)   gauge (T, L, L, L, 4, 3, 3)   half field (h, 4, 3), h = V / 2
+Device half fields of a given precision are opaque byte buffers of
+``half_field_bytes(prec)`` bytes each (layout documented in include/tm.h).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+F64, F32, F16 = 0, 1, 2
+LINK18, LINK12, LINK8 = 18, 12, 8
+CG_FP64, CG_SQRT_EPS, CG_RELIABLE = 0, 1, 2
+
+STATUS = {0: "TM_OK", 1: "TM_ERR_ARG", 2: "TM_ERR_ODD_EXTENT", 3: "TM_ERR_NO_GAUGE",
+          4: "TM_ERR_NOT_SU3", 5: "TM_ERR_NONFINITE", 6: "TM_ERR_CUDA",
+          7: "TM_ERR_NOT_CONVERGED", 8: "TM_ERR_TIMEOUT", 9: "TM_ERR_OOM",
+          10: "TM_ERR_UNSUPPORTED"}
+
+_lib = None
+
+
+class TMError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        self.status = status
+        self.status_name = STATUS.get(status, str(status))
+        super().__init__(f"{where}: {self.status_name}: {message}")
+
+
+class CGParams(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("mode", ctypes.c_int),
+                ("sloppy_prec", ctypes.c_int), ("sloppy_link", ctypes.c_int),
+                ("delta", ctypes.c_double), ("use_x0", ctypes.c_int), ("flavour", ctypes.c_int)]
+
+
+class CGInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("reliable_updates", ctypes.c_int),
+                ("true_rel_residual", ctypes.c_double), ("schur_rel_residual", ctypes.c_double),
+                ("seconds", ctypes.c_double), ("status", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libtmqcd.so (it must have been built: ``paper_0905_3331_gb300.build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"the CUDA library {path} is not built; run "
+                           "paper_0905_3331_gb300.build.build() (or __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    P, I, D, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    sig = {
+        "tm_lattice_create": ([I, I, D, D, ctypes.POINTER(P)], I),
+        "tm_lattice_destroy": ([P], I),
+        "tm_lattice_set_params": ([P, D, D], I),
+        "tm_volume": ([P], S),
+        "tm_half_field_bytes": ([P, I], S),
+        "tm_set_gauge": ([P, P, P], I),
+        "tm_pack_half": ([P, I, P, P, I, P], I),
+        "tm_unpack_half": ([P, I, P, P, I, P], I),
+        "tm_apply_D": ([P, P, P, I, I, I, P], I),
+        "tm_apply_hopping_eo": ([P, I, P, P, I, I, I, P], I),
+        "tm_apply_Mee_inv": ([P, P, P, I, I, I, P], I),
+        "tm_solve_cg": ([P, P, P, I, ctypes.POINTER(CGParams), ctypes.POINTER(CGInfo), P], I),
+        "tm_cg_params_default": ([ctypes.POINTER(CGParams)], None),
+        "tm_last_error": ([], ctypes.c_char_p),
+        "tm_launch_count": ([], ctypes.c_ulonglong),
+        "tm_reset_launch_count": ([], None),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    """Names of the ABI functions this binding binds (all must exist in the library)."""
+    return ["tm_lattice_create", "tm_lattice_destroy", "tm_lattice_set_params", "tm_volume",
+            "tm_half_field_bytes", "tm_set_gauge", "tm_pack_half", "tm_unpack_half", "tm_apply_D",
+            "tm_apply_hopping_eo", "tm_apply_Mee_inv", "tm_solve_cg", "tm_cg_params_default",
+            "tm_last_error", "tm_launch_count", "tm_reset_launch_count"]
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        msg = load().tm_last_error()
+        raise TMError(status, where, msg.decode() if msg else "")
+
+
+def _addr(buf) -> int:
+    """Address of a torch tensor, numpy array or integer address."""
+    if buf is None:
+        return 0
+    if isinstance(buf, int):
+        return buf
+    if isinstance(buf, np.ndarray):
+        if not buf.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return buf.ctypes.data
+    if hasattr(buf, "data_ptr"):
+        if not buf.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return buf.data_ptr()
+    raise TypeError(f"unsupported buffer type {type(buf)}")
+
+
+def _stream(stream) -> int:
+    if stream is not None:
+        return int(stream if isinstance(stream, int) else stream.cuda_stream)
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return int(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return 0
+
+
+def launch_count() -> int:
+    return int(load().tm_launch_count())
+
+
+def reset_launch_count():
+    load().tm_reset_launch_count()
+
+
+@dataclass
+class SolveInfo:
+    iters: int
+    reliable_updates: int
+    true_rel_residual: float
+    schur_rel_residual: float
+    seconds: float
+    status: int
+
+
+class Lattice:
+    """A T x L^3 lattice with hopping parameter kappa and bare twisted mass mu (mu~ = 2 kappa mu)."""
+
+    def __init__(self, T: int, L: int, kappa: float, mu: float):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.tm_lattice_create(T, L, kappa, mu, ctypes.byref(h)), "tm_lattice_create")
+        self._h = h
+        self.T, self.L, self.kappa, self.mu = T, L, kappa, mu
+        self.V = T * L ** 3
+        self.h = self.V // 2
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().tm_lattice_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_params(self, kappa: float, mu: float):
+        _check(load().tm_lattice_set_params(self._h, kappa, mu), "tm_lattice_set_params")
+        self.kappa, self.mu = kappa, mu
+
+    def half_field_bytes(self, prec: int) -> int:
+        return int(load().tm_half_field_bytes(self._h, prec))
+
+    def set_gauge(self, U, stream=None):
+        _check(load().tm_set_gauge(self._h, _addr(U), _stream(stream)), "tm_set_gauge")
+
+    def pack_half(self, prec: int, dst, src, nrhs: int = 1, stream=None):
+        _check(load().tm_pack_half(self._h, prec, _addr(dst), _addr(src), nrhs, _stream(stream)),
+               "tm_pack_half")
+
+    def unpack_half(self, prec: int, dst, src, nrhs: int = 1, stream=None):
+        _check(load().tm_unpack_half(self._h, prec, _addr(dst), _addr(src), nrhs, _stream(stream)),
+               "tm_unpack_half")
+
+    def apply_D(self, out, inp, flavour: int = 1, dagger: bool = False, nrhs: int = 1, stream=None):
+        _check(load().tm_apply_D(self._h, _addr(out), _addr(inp), flavour, int(dagger), nrhs,
+                                 _stream(stream)), "tm_apply_D")
+
+    def apply_hopping_eo(self, out_parity: int, out, inp, prec: int = F64, link: int = LINK18,
+                         nrhs: int = 1, stream=None):
+        _check(load().tm_apply_hopping_eo(self._h, out_parity, _addr(out), _addr(inp), prec, link,
+                                          nrhs, _stream(stream)), "tm_apply_hopping_eo")
+
+    def apply_Mee_inv(self, out, inp, flavour: int = 1, prec: int = F64, nrhs: int = 1,
+                      stream=None):
+        _check(load().tm_apply_Mee_inv(self._h, _addr(out), _addr(inp), flavour, prec, nrhs,
+                                       _stream(stream)), "tm_apply_Mee_inv")
+
+    def solve_cg(self, x, b, nrhs: int = 1, tol: float = 1e-10, max_iter: int = 100000,
+                 mode: int = CG_FP64, sloppy_prec: int = F32, sloppy_link: int = LINK12,
+                 delta: float = 0.1, use_x0: bool = False, flavour: int = 1, stream=None,
+                 check: bool = True) -> SolveInfo:
+        p = CGParams(tol, max_iter, mode, sloppy_prec, sloppy_link, delta, int(use_x0), flavour)
+        info = CGInfo()
+        st = load().tm_solve_cg(self._h, _addr(x), _addr(b), nrhs, ctypes.byref(p),
+                                ctypes.byref(info), _stream(stream))
+        if check:
+            _check(st, "tm_solve_cg")
+        d = info.as_dict()
+        d["status"] = st
+        return SolveInfo(**d)

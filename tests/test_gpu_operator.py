@@ -1,0 +1,242 @@
+"""GPU parity of the operator entry points against the CPU oracle (through the C ABI).
+
+Tolerances (relative 2-norm error against the FP64 oracle on the same FP64 input):
+  FP64 storage, any link format ........ 1e-13   (FP64 arithmetic; the 8-real
+                                                  reconstruction divides by
+                                                  |a1|^2 + |a2|^2 and is held to 1e-12)
+  FP32 storage, 18/12-real links ....... 1e-6    (24-bit mantissa: input rounding
+                                                  6e-8 plus ~100 accumulated FP32 ops)
+  FP32 storage, 8-real links ........... 1e-5
+  FP16 storage + FP32 norm ............. 2e-3    (11-bit mantissa: 4.9e-4 per stored value)
+Sizes run from 2^4 (h = 8; the +mu and -mu neighbours coincide) through ragged
+tails (h = 432, not a multiple of the 128-thread block) to the full 16^3 x 32
+lattice; the 32^3 x 64 and 48^3 x 96 lattices are checked on sampled sites.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0905_3331_gb300 import F16, F32, F64, Lattice, TMError, inputs
+
+from _util import from_half, lex_of_half, rel, to_half
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {(F64, 18): 1e-13, (F64, 12): 1e-13, (F64, 8): 1e-12,
+       (F32, 18): 1e-6, (F32, 12): 1e-6, (F32, 8): 1e-5,
+       (F16, 18): 2e-3, (F16, 12): 2e-3, (F16, 8): 2e-3}
+
+SIZES = [(2, 2), (4, 4), (4, 6), (8, 4), (32, 16)]
+
+
+def dev():
+    return torch.device("cuda:0")
+
+
+def make(T, L, eps=0.5, kappa=0.1632, mu=0.004, seed=1):
+    U = inputs.random_gauge(T, L, eps, seed)
+    lat = Lattice(T, L, kappa, mu)
+    lat.set_gauge(torch.from_numpy(U).to(dev()))
+    return lat, U
+
+
+@pytest.mark.parametrize("T,L", SIZES)
+def test_apply_D_matches_oracle(T, L):
+    lat, U = make(T, L)
+    psi = inputs.gaussian_spinor(T, L, 7)
+    olat = oracle.Lattice.cubic(T, L)
+    for f in (1, -1):
+        ref = oracle.apply_M(olat, U, psi, lat.kappa, lat.mu, f)
+        out = torch.empty(psi.shape, dtype=torch.complex128, device=dev())
+        lat.apply_D(out, torch.from_numpy(psi).to(dev()), flavour=f)
+        assert rel(out.cpu().numpy(), ref) < 1e-13
+    # dagger: M^dag = g5 M(-mu) g5 (gamma5-hermiticity, eq. eo6 remark)
+    g5 = np.array([1, 1, -1, -1])[:, None]
+    ref = g5 * oracle.apply_M(olat, U, g5 * psi, lat.kappa, -lat.mu)
+    out = torch.empty(psi.shape, dtype=torch.complex128, device=dev())
+    lat.apply_D(out, torch.from_numpy(psi).to(dev()), dagger=True)
+    assert rel(out.cpu().numpy(), ref) < 1e-13
+    lat.close()
+
+
+@pytest.mark.parametrize("T,L", SIZES)
+@pytest.mark.parametrize("prec,link", sorted(TOL))
+def test_hopping_eo_matches_oracle(T, L, prec, link):
+    lat, U = make(T, L)
+    olat = oracle.Lattice.cubic(T, L)
+    psi = inputs.gaussian_spinor(T, L, 8)
+    nb = lat.half_field_bytes(prec)
+    for p in (0, 1):
+        src = to_half(psi, 1 - p)
+        ref = to_half(oracle.hopping(olat, U, from_half(src, 1 - p, T, L), out_parity=p), p)
+        din = torch.empty(nb, dtype=torch.uint8, device=dev())
+        dout = torch.empty(nb, dtype=torch.uint8, device=dev())
+        lat.pack_half(prec, din, torch.from_numpy(src).to(dev()))
+        lat.apply_hopping_eo(p, dout, din, prec, link)
+        got = torch.empty(src.shape, dtype=torch.complex128, device=dev())
+        lat.unpack_half(prec, got, dout)
+        err = rel(got.cpu().numpy(), ref)
+        assert err < TOL[(prec, link)], f"parity {p}: {err:.3e}"
+    lat.close()
+
+
+def test_hopping_multi_rhs_equals_single():
+    T, L = 8, 4
+    lat, U = make(T, L)
+    nrhs = 3
+    src = np.stack([to_half(inputs.gaussian_spinor(T, L, 20 + k), 1) for k in range(nrhs)])
+    for prec in (F64, F32, F16):
+        nb = lat.half_field_bytes(prec)
+        din = torch.empty(nrhs * nb, dtype=torch.uint8, device=dev())
+        dout = torch.empty(nrhs * nb, dtype=torch.uint8, device=dev())
+        lat.pack_half(prec, din, torch.from_numpy(src).to(dev()), nrhs=nrhs)
+        lat.apply_hopping_eo(0, dout, din, prec, 12, nrhs=nrhs)
+        many = torch.empty(src.shape, dtype=torch.complex128, device=dev())
+        lat.unpack_half(prec, many, dout, nrhs=nrhs)
+        for k in range(nrhs):
+            one_in = torch.empty(nb, dtype=torch.uint8, device=dev())
+            one_out = torch.empty(nb, dtype=torch.uint8, device=dev())
+            lat.pack_half(prec, one_in, torch.from_numpy(src[k]).to(dev()))
+            lat.apply_hopping_eo(0, one_out, one_in, prec, 12)
+            one = torch.empty(src[k].shape, dtype=torch.complex128, device=dev())
+            lat.unpack_half(prec, one, one_out)
+            assert torch.equal(one, many[k])
+    lat.close()
+
+
+def test_pack_unpack_round_trip():
+    T, L = 4, 6
+    lat, _ = make(T, L)
+    src = to_half(inputs.gaussian_spinor(T, L, 9), 0)
+    for prec, tol in ((F64, 0.0), (F32, 6e-8), (F16, 5e-4)):
+        buf = torch.empty(lat.half_field_bytes(prec), dtype=torch.uint8, device=dev())
+        lat.pack_half(prec, buf, torch.from_numpy(src).to(dev()))
+        back = torch.empty(src.shape, dtype=torch.complex128, device=dev())
+        lat.unpack_half(prec, back, buf)
+        b = back.cpu().numpy()
+        if tol == 0.0:
+            assert np.array_equal(b, src)
+        else:
+            # per site, relative to the site's largest component (the FP16 norm)
+            scale = np.maximum(np.abs(src.real), np.abs(src.imag)).reshape(len(src), -1).max(1)
+            err = np.abs(b - src).reshape(len(src), -1).max(1) / scale
+            assert err.max() <= tol
+    # host buffers (numpy) work the same as device buffers
+    buf = torch.empty(lat.half_field_bytes(F64), dtype=torch.uint8, device=dev())
+    lat.pack_half(F64, buf, src)
+    back = np.empty_like(src)
+    lat.unpack_half(F64, back, buf)
+    torch.cuda.synchronize()
+    assert np.array_equal(back, src)
+    lat.close()
+
+
+def test_Mee_inv_matches_oracle():
+    T, L = 4, 4
+    lat, _ = make(T, L, kappa=0.16, mu=0.3)
+    olat = oracle.Lattice.cubic(T, L)
+    psi = inputs.gaussian_spinor(T, L, 10)
+    mut = 2 * lat.kappa * lat.mu
+    for f in (1, -1):
+        for p in (0, 1):
+            src = to_half(psi, p)
+            ref = to_half(oracle.apply_Mdiag_inv(olat, psi, mut, f, p), p)
+            buf = torch.empty(lat.half_field_bytes(F64), dtype=torch.uint8, device=dev())
+            lat.pack_half(F64, buf, torch.from_numpy(src).to(dev()))
+            lat.apply_Mee_inv(buf, buf, flavour=f, prec=F64)  # in place
+            got = torch.empty(src.shape, dtype=torch.complex128, device=dev())
+            lat.unpack_half(F64, got, buf)
+            assert rel(got.cpu().numpy(), ref) < 1e-15
+    lat.close()
+
+
+def test_host_buffers_equal_device_buffers():
+    T, L = 4, 4
+    lat, U = make(T, L)
+    psi = inputs.gaussian_spinor(T, L, 11)
+    out_h = np.empty_like(psi)
+    lat.apply_D(out_h, psi)
+    torch.cuda.synchronize()
+    out_d = torch.empty(psi.shape, dtype=torch.complex128, device=dev())
+    lat.apply_D(out_d, torch.from_numpy(psi).to(dev()))
+    assert np.array_equal(out_h, out_d.cpu().numpy())
+    lat.close()
+
+
+def test_set_gauge_rejects_non_su3_and_nonfinite():
+    T, L = 4, 4
+    U = inputs.random_gauge(T, L, 0.5, 1)
+    lat = Lattice(T, L, 0.16, 0.01)
+    bad = U.copy()
+    bad[1, 2, 3, 0, 2] *= 1.001
+    with pytest.raises(TMError) as e:
+        lat.set_gauge(torch.from_numpy(bad).to(dev()))
+    assert e.value.status_name == "TM_ERR_NOT_SU3"
+    bad = U.copy()
+    bad[0, 0, 0, 1, 1, 2, 2] = np.nan
+    with pytest.raises(TMError) as e:
+        lat.set_gauge(bad)
+    assert e.value.status_name == "TM_ERR_NONFINITE"
+    # nothing was installed: operators still refuse
+    out = torch.empty((T, L, L, L, 4, 3), dtype=torch.complex128, device=dev())
+    with pytest.raises(TMError) as e:
+        lat.apply_D(out, torch.zeros_like(out))
+    assert e.value.status_name == "TM_ERR_NO_GAUGE"
+    lat.set_gauge(U)
+    lat.apply_D(out, torch.zeros_like(out))
+    lat.close()
+
+
+def test_argument_errors():
+    T, L = 4, 4
+    lat, _ = make(T, L)
+    buf = torch.zeros(lat.half_field_bytes(F64), dtype=torch.uint8, device=dev())
+    with pytest.raises(TMError) as e:
+        lat.apply_hopping_eo(0, buf, buf, F64, 18)
+    assert e.value.status_name == "TM_ERR_ARG"  # out overlaps in
+    with pytest.raises(TMError):
+        lat.apply_hopping_eo(2, buf, buf.clone(), F64, 18)
+    with pytest.raises(TMError):
+        lat.apply_hopping_eo(0, buf, buf.clone(), F64, 10)
+    with pytest.raises(TMError):
+        lat.apply_Mee_inv(buf, buf, flavour=0)
+    lat.close()
+
+
+@pytest.mark.parametrize("name,prec,link", [("32^3x64", F32, 12), ("48^3x96", F16, 8)])
+def test_full_size_sampled_sites(name, prec, link):
+    """Full 32^3 x 64 and 48^3 x 96 lattices: apply_D (FP64) and the hopping kernel in the
+    sloppy form of that workload, against the oracle at 4096 sampled sites."""
+    w = inputs.WORKLOADS[name]
+    T, L = w.T, w.L
+    U = w.gauge()
+    psi = w.source()
+    lat = Lattice(T, L, w.kappa, w.mu)
+    lat.set_gauge(U)
+    olat = oracle.Lattice.cubic(T, L)
+    rng = np.random.default_rng(0)
+    src = torch.from_numpy(psi).to(dev())
+    out = torch.empty_like(src)
+    lat.apply_D(out, src)
+    sites = np.sort(rng.choice(w.V, 4096, replace=False))
+    got = out.reshape(w.V, 4, 3)[torch.from_numpy(sites).to(dev())].cpu().numpy()
+    ref = oracle.apply_M_sites(olat, U, psi, w.kappa, w.mu, sites)
+    assert rel(got, ref) < 1e-13
+    del out
+    p = 1
+    lexs = lex_of_half(T, L, p)
+    half_in = torch.from_numpy(to_half(psi, 1 - p)).to(dev())
+    nb = lat.half_field_bytes(prec)
+    din = torch.empty(nb, dtype=torch.uint8, device=dev())
+    dout = torch.empty(nb, dtype=torch.uint8, device=dev())
+    lat.pack_half(prec, din, half_in)
+    lat.apply_hopping_eo(p, dout, din, prec, link)
+    full = torch.empty(half_in.shape, dtype=torch.complex128, device=dev())
+    lat.unpack_half(prec, full, dout)
+    idx = np.sort(rng.choice(len(lexs), 4096, replace=False))
+    got = full[torch.from_numpy(idx).to(dev())].cpu().numpy()
+    masked = from_half(to_half(psi, 1 - p), 1 - p, T, L)
+    ref = oracle.hopping_sites(olat, U, masked, lexs[idx])
+    assert rel(got, ref) < TOL[(prec, link)]
+    lat.close()

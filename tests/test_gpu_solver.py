@@ -1,0 +1,171 @@
+"""GPU even/odd CG against the CPU oracle (through the C ABI).
+
+The bar for every solve is the spec one: the FP64 true residual
+||phi - M x|| / ||phi||, recomputed by the ORACLE's operator on the GPU solution,
+is below 1e-10.  On 4^4 the GPU solution is also compared with the oracle's own
+even/odd solve.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0905_3331_gb300 import (CG_FP64, CG_RELIABLE, CG_SQRT_EPS, F16, F32, LINK8, LINK12,
+                                   LINK18, Lattice, TMError, inputs)
+
+from _util import rel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+MODES = [
+    ("fp64", dict(mode=CG_FP64)),
+    ("sqrt_eps_f32_12", dict(mode=CG_SQRT_EPS, sloppy_prec=F32, sloppy_link=LINK12)),
+    ("reliable_f32_18", dict(mode=CG_RELIABLE, sloppy_prec=F32, sloppy_link=LINK18)),
+    ("reliable_f32_12", dict(mode=CG_RELIABLE, sloppy_prec=F32, sloppy_link=LINK12)),
+    ("reliable_f16_12", dict(mode=CG_RELIABLE, sloppy_prec=F16, sloppy_link=LINK12)),
+    ("reliable_f16_8", dict(mode=CG_RELIABLE, sloppy_prec=F16, sloppy_link=LINK8)),
+]
+
+
+def dev():
+    return torch.device("cuda:0")
+
+
+def oracle_true_residual(w, U, phi, x, f=1):
+    olat = oracle.Lattice.cubic(w.T, w.L)
+    r = phi - oracle.apply_M(olat, U, x, w.kappa, w.mu if f == 1 else -w.mu)
+    return np.linalg.norm(r) / np.linalg.norm(phi)
+
+
+@pytest.mark.parametrize("name,kw", MODES)
+def test_solve_4x4x4x4(name, kw):
+    w = inputs.WORKLOADS["4^4"]
+    U, phi = w.gauge(), w.source()
+    lat = Lattice(w.T, w.L, w.kappa, w.mu)
+    lat.set_gauge(torch.from_numpy(U).to(dev()))
+    b = torch.from_numpy(phi).to(dev())
+    x = torch.zeros_like(b)
+    info = lat.solve_cg(x, b, tol=1e-10, **kw)
+    xn = x.cpu().numpy()
+    assert oracle_true_residual(w, U, phi, xn) < 1e-10
+    assert info.true_rel_residual < 1e-10 and info.schur_rel_residual < 1e-10
+    # agreement with the oracle's own even/odd solve (both at 1e-12)
+    lat.solve_cg(x, b, tol=1e-12, **kw)
+    ref = oracle.solve(oracle.Lattice.cubic(w.T, w.L), U, phi, w.kappa, w.mu, tol=1e-12)
+    assert rel(x.cpu().numpy(), ref.psi) < 1e-9
+    lat.close()
+
+
+@pytest.mark.parametrize("name,kw", [MODES[0], MODES[3], MODES[4]])
+def test_solve_16x16x16x32(name, kw):
+    """The 16^3 x 32 workload (eps 0.5, kappa 0.1632, mu 0.004), Gaussian source seed 2."""
+    w = inputs.WORKLOADS["16^3x32"]
+    U, phi = w.gauge(), w.source()
+    lat = Lattice(w.T, w.L, w.kappa, w.mu)
+    lat.set_gauge(U)
+    b = torch.from_numpy(phi).to(dev())
+    x = torch.zeros_like(b)
+    info = lat.solve_cg(x, b, tol=1e-10, **kw)
+    assert oracle_true_residual(w, U, phi, x.cpu().numpy()) < 1e-10
+    assert info.iters > 0
+    lat.close()
+
+
+def test_flavour_minus_and_multiple_rhs():
+    w = inputs.WORKLOADS["4^4"]
+    U = w.gauge()
+    phis = np.stack([w.source(k) for k in range(2)])
+    lat = Lattice(w.T, w.L, w.kappa, w.mu)
+    lat.set_gauge(U)
+    b = torch.from_numpy(phis).to(dev())
+    x = torch.zeros_like(b)
+    lat.solve_cg(x, b, nrhs=2, flavour=-1)
+    xs = x.cpu().numpy()
+    for k in range(2):
+        assert oracle_true_residual(w, U, phis[k], xs[k], f=-1) < 1e-10
+    # each system equals its own single solve
+    x1 = torch.zeros_like(b[1])
+    lat.solve_cg(x1, b[1].contiguous(), flavour=-1)
+    assert torch.equal(x1, x[1])
+    lat.close()
+
+
+def test_deterministic_and_host_buffers():
+    w = inputs.WORKLOADS["4^4"]
+    U, phi = w.gauge(), w.source()
+    lat = Lattice(w.T, w.L, w.kappa, w.mu)
+    lat.set_gauge(U)
+    b = torch.from_numpy(phi).to(dev())
+    x1, x2 = torch.zeros_like(b), torch.zeros_like(b)
+    i1 = lat.solve_cg(x1, b, mode=CG_RELIABLE, sloppy_prec=F16)
+    i2 = lat.solve_cg(x2, b, mode=CG_RELIABLE, sloppy_prec=F16)
+    assert torch.equal(x1, x2) and i1.iters == i2.iters
+    xh = np.zeros_like(phi)
+    i3 = lat.solve_cg(xh, phi, mode=CG_RELIABLE, sloppy_prec=F16)
+    assert np.array_equal(xh, x1.cpu().numpy()) and i3.iters == i1.iters
+    lat.close()
+
+
+def test_initial_guess_defect_correction():
+    w = inputs.WORKLOADS["4^4"]
+    U, phi = w.gauge(), w.source()
+    lat = Lattice(w.T, w.L, w.kappa, w.mu)
+    lat.set_gauge(U)
+    b = torch.from_numpy(phi).to(dev())
+    x = torch.zeros_like(b)
+    lat.solve_cg(x, b, tol=1e-4)
+    info = lat.solve_cg(x, b, tol=1e-10, use_x0=True)
+    assert oracle_true_residual(w, U, phi, x.cpu().numpy()) < 1e-10
+    assert info.true_rel_residual < 1e-10
+    lat.close()
+
+
+def test_edge_cases():
+    w = inputs.WORKLOADS["4^4"]
+    U, phi = w.gauge(), w.source()
+    lat = Lattice(w.T, w.L, w.kappa, w.mu)
+    lat.set_gauge(U)
+    b = torch.from_numpy(phi).to(dev())
+    # zero source gives x = 0
+    x = torch.ones_like(b)
+    info = lat.solve_cg(x, torch.zeros_like(b))
+    assert torch.count_nonzero(x) == 0 and info.iters == 0
+    # max_iter reached: TM_ERR_NOT_CONVERGED, info filled, last iterate returned
+    x = torch.zeros_like(b)
+    info = lat.solve_cg(x, b, max_iter=5, check=False)
+    assert info.status == 7 and info.iters >= 5 and info.schur_rel_residual > 1e-10
+    assert torch.count_nonzero(x) > 0
+    with pytest.raises(TMError) as e:
+        lat.solve_cg(x, b, max_iter=5)
+    assert e.value.status_name == "TM_ERR_NOT_CONVERGED"
+    # non-finite source
+    bad = b.clone()
+    bad[0, 0, 0, 0, 0, 0] = float("nan")
+    with pytest.raises(TMError) as e:
+        lat.solve_cg(x, bad)
+    assert e.value.status_name == "TM_ERR_NONFINITE"
+    # bad parameters
+    for kw in (dict(tol=0.0), dict(mode=7), dict(mode=CG_RELIABLE, delta=1.5),
+               dict(flavour=3), dict(mode=CG_RELIABLE, sloppy_prec=0)):
+        with pytest.raises(TMError) as e:
+            lat.solve_cg(x, b, **kw)
+        assert e.value.status_name == "TM_ERR_ARG"
+    with pytest.raises(TMError):
+        lat.solve_cg(b, b)
+    lat.close()
+
+
+def test_smallest_lattice_2x2x2x2():
+    """2^4: the +mu and -mu neighbours of every site coincide."""
+    U = inputs.random_gauge(2, 2, 0.6, 3)
+    phi = inputs.gaussian_spinor(2, 2, 4)
+    lat = Lattice(2, 2, 0.15, 0.05)
+    lat.set_gauge(U)
+    b = torch.from_numpy(phi).to(dev())
+    for name, kw in MODES:
+        x = torch.zeros_like(b)
+        lat.solve_cg(x, b, **kw)
+        olat = oracle.Lattice.cubic(2, 2)
+        r = phi - oracle.apply_M(olat, U, x.cpu().numpy(), 0.15, 0.05)
+        assert np.linalg.norm(r) / np.linalg.norm(phi) < 1e-10, name
+    lat.close()
