@@ -185,6 +185,32 @@ tm_status tm_solve_cg(tm_lattice lat, double *x, const double *b, int nrhs,
  * TM_F32 / TM_LINK12, delta 0.1, use_x0 0, flavour +1. */
 void tm_cg_params_default(tm_cg_params *params);
 
+/* ------------------------------------------------------ allocation-free variant --- */
+
+/* The paper has no counterpart to this entry point.  Same result as tm_apply_D, for callers
+ * that must not allocate device memory during the call: code running under a fixed
+ * device-memory budget (a framework whose caching allocator already holds the memory, a
+ * process with a hard memory limit) or in a latency-critical loop where a cudaMalloc or
+ * cudaFree would synchronise the device.  tm_apply_D takes its four half-field work buffers
+ * from lattice-owned memory allocated on first use; this variant takes them from one static
+ * 64 MiB device array that is part of the library's device code, so the call itself calls no
+ * cudaMalloc, cudaFree or other allocating routine.  Every GPU that loads the library holds
+ * those 64 MiB until the process exits.
+ *   Limit: 4 x 192 x V/2 bytes of scratch must fit in 64 MiB, i.e. V = T L^3 <= 174762
+ *          sites (16^3 x 32 fits, 24^3 x 48 does not); larger lattices get TM_ERR_ARG.
+ *   in, out: canonical full fields in DEVICE memory of the lattice's device (host pointers
+ *          get TM_ERR_ARG: staging them would need a buffer); nrhs x 24 V doubles; no overlap.
+ *   Set-up: the first call on a device looks up the array's device address
+ *          (cudaGetSymbolAddress, with that device current) and caches it; make that first
+ *          call before any stream capture.
+ *   Sharing: every call uses the same array.  The array keeps the previous call's contents
+ *          (each call writes every scratch byte it reads before reading it), and calls that
+ *          overlap on the GPU -- on different streams, or from different host threads --
+ *          race on it: order them on one stream.
+ * Errors: as tm_apply_D, plus TM_ERR_ARG for the limits above. */
+tm_status tm_apply_D_noalloc(tm_lattice lat, double *out, const double *in, int flavour, int dagger,
+                             int nrhs, void *stream);
+
 /* ------------------------------------------------------------------- misc --- */
 
 /* Message of the last failed call on this host thread ("" if none). */
