@@ -370,8 +370,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="16^3x32")
-    ap.add_argument("--sloppy", default="f16:12", help="sloppy storage:links, e.g. f32:12, f16:8")
-    ap.add_argument("--delta", type=float, default=0.1)
+    ap.add_argument("--sloppy", default="f32:12", help="sloppy storage:links, e.g. f32:12, f16:8")
+    ap.add_argument("--delta", type=float, default=0.001)
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--hop-iters", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -99,9 +99,10 @@ size_t tm_half_field_bytes(tm_lattice lat, tm_prec prec);
 /* Copies the canonical FP64 gauge field U (host or device; 72 V doubles) into the
  * lattice, checks that every link is SU(3) (|U^dag U - 1|_max and |det U - 1| <= 1e-10,
  * all entries finite) and builds the parity-split "gauge copy" of Sec. 4.1 in device
- * memory: per output parity, per site, the 4 forward links U_mu(x) and the 4 backward
- * links U_mu(x - mu^)^dag, in the order the hopping kernel reads them.  Reduced-precision
- * and compressed copies are built on first use.  Synchronises `stream`.
+ * memory: per parity and direction, the links U_mu(x) of the sites of that parity in the
+ * order the hopping kernel reads them (the backward hop reads U_mu(x - mu^) of the
+ * neighbour, of the other parity, and applies its adjoint).  Reduced-precision and
+ * compressed copies are built on first use.  Synchronises `stream`.
  * Errors: TM_ERR_NOT_SU3 (nothing is changed), TM_ERR_NONFINITE, TM_ERR_ARG, TM_ERR_CUDA, TM_ERR_OOM. */
 tm_status tm_set_gauge(tm_lattice lat, const double *U, void *stream);
 

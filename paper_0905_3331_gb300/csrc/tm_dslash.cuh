@@ -12,8 +12,8 @@
 //   mu = x: h0 = p0 - i s p3, h1 = p1 - i s p2; out2 += i s U h1, out3 += i s U h0
 //   mu = y: h0 = p0 - s p3,   h1 = p1 + s p2;   out2 += s U h1,   out3 += -s U h0
 //   mu = z: h0 = p0 - i s p2, h1 = p1 + i s p3; out2 += i s U h0, out3 += -i s U h1
-// and out0 += U h0, out1 += U h1 in every direction.  Fermions are antiperiodic in time
-// (Sec. 2.4): the hop across t = T-1 <-> 0 is multiplied by -1.
+// and out0 += U h0, out1 += U h1 in every direction (U^dag for the backward hops).  Fermions
+// are antiperiodic in time (Sec. 2.4): the hop across t = T-1 <-> 0 is multiplied by -1.
 #pragma once
 
 #include "tm_internal.cuh"
@@ -75,18 +75,42 @@ __device__ __forceinline__ void su3_mul2(const Mat3<R>& U, const cpx<R> h0[3], c
   }
 }
 
+// u = U^dag h for two colour vectors
+template <typename R>
+__device__ __forceinline__ void su3_adj_mul2(const Mat3<R>& U, const cpx<R> h0[3], const cpx<R> h1[3],
+                                             cpx<R> u0[3], cpx<R> u1[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    u0[a] = cjmul(U.m[0][a], h0[0]) + cjmul(U.m[1][a], h0[1]) + cjmul(U.m[2][a], h0[2]);
+    u1[a] = cjmul(U.m[0][a], h1[0]) + cjmul(U.m[1][a], h1[1]) + cjmul(U.m[2][a], h1[2]);
+  }
+}
+
+// One hop.  Forward (S = +1): link U_mu(x) from the output parity's slab at the output site.
+// Backward (S = -1): link U_mu(x - mu^) from the other parity's slab at the neighbour's index,
+// applied as its adjoint -- the same stored link serves both hops, so the operator keeps
+// gamma5-hermiticity exactly in every storage format.
 template <int PREC, int NREAL, int MU, int S>
 __device__ __forceinline__ void hop_dir(cpx<typename SpinorFmt<PREC>::real> acc[12], const void* in, int h,
-                                        int nbi, const char* slab, int cb, bool negate) {
+                                        int nbi, const char* slab, int link_index, bool negate) {
   typedef typename SpinorFmt<PREC>::real R;
   typedef typename LinkStore<PREC>::type St;
   constexpr int BYTES = NREAL * LinkStore<PREC>::size;
-  RawWords<BYTES> raw = load_raw<BYTES>(slab, h, cb);
+  RawWords<BYTES> raw = load_raw<BYTES>(slab, h, link_index);
   cpx<R> p[12];
-  SpinorFmt<PREC>::load(in, h, nbi, p);
+  R scale;
+  SpinorFmt<PREC>::load_unscaled(in, h, nbi, p, scale);
   cpx<R> h0[3], h1[3];
   project<R, MU, S>(p, h0, h1);
-  if (MU == 0 && negate) {
+  if (SpinorFmt<PREC>::has_norm) {
+    // FP16 per-site norm and the boundary sign, applied to the 6 projected components
+    const R f = (MU == 0 && negate) ? -scale : scale;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      h0[c] = f * h0[c];
+      h1[c] = f * h1[c];
+    }
+  } else if (MU == 0 && negate) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       h0[c] = R(-1) * h0[c];
@@ -96,7 +120,10 @@ __device__ __forceinline__ void hop_dir(cpx<typename SpinorFmt<PREC>::real> acc[
   Mat3<R> U;
   LinkRecon<R, St, NREAL>::unpack(raw, U);
   cpx<R> u0[3], u1[3];
-  su3_mul2(U, h0, h1, u0, u1);
+  if (S > 0)
+    su3_mul2(U, h0, h1, u0, u1);
+  else
+    su3_adj_mul2(U, h0, h1, u0, u1);
   accumulate<R, MU, S>(acc, u0, u1);
 }
 
@@ -123,19 +150,20 @@ __global__ void __launch_bounds__(HOP_NT) hop_kernel(const Geom g, const int out
     neighbours(g, cb, c, nb);
     const char* inr = static_cast<const char*>(in) + (size_t)rhs * in_stride;
     const size_t slab = link_bytes(PREC, NREAL) * (size_t)g.h;
-    const char* lb = links + (size_t)(out_parity * 8) * slab;
+    const char* lf = links + (size_t)(out_parity * 4) * slab;        // U_mu(x), x of this parity
+    const char* lo = links + (size_t)((1 - out_parity) * 4) * slab;  // U_mu(y), y of the other parity
     cpx<R> acc[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) acc[k] = mk<R>(R(0), R(0));
     const bool tfwd = (c.t == g.T - 1), tbwd = (c.t == 0);
-    hop_dir<PREC, NREAL, 0, +1>(acc, inr, g.h, nb[0], lb + 0 * slab, cb, tfwd);
-    hop_dir<PREC, NREAL, 0, -1>(acc, inr, g.h, nb[4], lb + 4 * slab, cb, tbwd);
-    hop_dir<PREC, NREAL, 1, +1>(acc, inr, g.h, nb[1], lb + 1 * slab, cb, false);
-    hop_dir<PREC, NREAL, 1, -1>(acc, inr, g.h, nb[5], lb + 5 * slab, cb, false);
-    hop_dir<PREC, NREAL, 2, +1>(acc, inr, g.h, nb[2], lb + 2 * slab, cb, false);
-    hop_dir<PREC, NREAL, 2, -1>(acc, inr, g.h, nb[6], lb + 6 * slab, cb, false);
-    hop_dir<PREC, NREAL, 3, +1>(acc, inr, g.h, nb[3], lb + 3 * slab, cb, false);
-    hop_dir<PREC, NREAL, 3, -1>(acc, inr, g.h, nb[7], lb + 7 * slab, cb, false);
+    hop_dir<PREC, NREAL, 0, +1>(acc, inr, g.h, nb[0], lf + 0 * slab, cb, tfwd);
+    hop_dir<PREC, NREAL, 0, -1>(acc, inr, g.h, nb[4], lo + 0 * slab, nb[4], tbwd);
+    hop_dir<PREC, NREAL, 1, +1>(acc, inr, g.h, nb[1], lf + 1 * slab, cb, false);
+    hop_dir<PREC, NREAL, 1, -1>(acc, inr, g.h, nb[5], lo + 1 * slab, nb[5], false);
+    hop_dir<PREC, NREAL, 2, +1>(acc, inr, g.h, nb[2], lf + 2 * slab, cb, false);
+    hop_dir<PREC, NREAL, 2, -1>(acc, inr, g.h, nb[6], lo + 2 * slab, nb[6], false);
+    hop_dir<PREC, NREAL, 3, +1>(acc, inr, g.h, nb[3], lf + 3 * slab, cb, false);
+    hop_dir<PREC, NREAL, 3, -1>(acc, inr, g.h, nb[7], lo + 3 * slab, nb[7], false);
 
     // epilogue: o_s = D_s (c acc_s + E_s y_s)
     const R cc = (R)coef.c;

@@ -4,9 +4,10 @@
 //   half spinor field  per precision, blocks of 16 bytes, block-major ("SoA"): block k of
 //                      site cb at byte offset (k * h + cb) * 16, so a warp reading block k of
 //                      32 consecutive sites issues one fully coalesced 512-byte request.
-//   gauge copy         per output parity p (2), per direction d (8: d = mu forward link
-//                      U_mu(x), d = 4 + mu backward link U_mu(x - mu^)^dag), per 16-byte
-//                      block, per site cb; a link of R reals in storage type S takes
+//   gauge copy         per parity p (2), per direction mu (4): the link U_mu(x) of every
+//                      site x of parity p, per 16-byte block, per site cb (the backward hop
+//                      of a site reads its neighbour's link from the other parity's slabs
+//                      and applies the adjoint); a link of R reals in storage type S takes
 //                      R * sizeof(S) bytes = NB full 16-byte blocks plus a tail of 0, 4 or 8
 //                      bytes stored in its own block-major array after the full blocks.
 #pragma once
@@ -116,11 +117,20 @@ __device__ __forceinline__ void neighbours(const Geom& g, int cb, const SiteCoor
 template <int PREC>
 struct SpinorFmt;
 
+// Each format provides load/store of the 12 complex components of site i, and
+// load_unscaled(), which leaves out the FP16 per-site norm (returned in `scale`, 1 for the
+// other formats) so that a caller can apply it after a linear map that halves the data.
 // FP64: double2 blocks [12][h]
 template <>
 struct SpinorFmt<TM_F64> {
   typedef double real;
+  static constexpr bool has_norm = false;
   static constexpr size_t bytes_per_site = 192;
+  template <typename R>
+  __device__ static __forceinline__ void load_unscaled(const void* base, int h, int i, cpx<R> s[12], R& scale) {
+    load(base, h, i, s);
+    scale = R(1);
+  }
   template <typename R>
   __device__ static __forceinline__ void load(const void* base, int h, int i, cpx<R> s[12]) {
     const double2* p = static_cast<const double2*>(base);
@@ -142,7 +152,13 @@ struct SpinorFmt<TM_F64> {
 template <>
 struct SpinorFmt<TM_F32> {
   typedef float real;
+  static constexpr bool has_norm = false;
   static constexpr size_t bytes_per_site = 96;
+  template <typename R>
+  __device__ static __forceinline__ void load_unscaled(const void* base, int h, int i, cpx<R> s[12], R& scale) {
+    load(base, h, i, s);
+    scale = R(1);
+  }
   template <typename R>
   __device__ static __forceinline__ void load(const void* base, int h, int i, cpx<R> s[12]) {
     const float4* p = static_cast<const float4*>(base);
@@ -167,7 +183,23 @@ struct SpinorFmt<TM_F32> {
 template <>
 struct SpinorFmt<TM_F16> {
   typedef float real;
+  static constexpr bool has_norm = true;
   static constexpr size_t bytes_per_site = 52;
+  template <typename R>
+  __device__ static __forceinline__ void load_unscaled(const void* base, int h, int i, cpx<R> s[12], R& scale) {
+    const uint4* p = static_cast<const uint4*>(base);
+    const float* nrm = reinterpret_cast<const float*>(p + (size_t)3 * h);
+    scale = (R)__ldg(nrm + i);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      uint4 v = __ldg(p + (size_t)k * h + i);
+      float2 a = h2f(v.x), b = h2f(v.y), c = h2f(v.z), d = h2f(v.w);
+      s[4 * k + 0] = mk<R>((R)a.x, (R)a.y);
+      s[4 * k + 1] = mk<R>((R)b.x, (R)b.y);
+      s[4 * k + 2] = mk<R>((R)c.x, (R)c.y);
+      s[4 * k + 3] = mk<R>((R)d.x, (R)d.y);
+    }
+  }
   __device__ static __forceinline__ float2 h2f(unsigned int w) {
     __half2 hv = *reinterpret_cast<__half2*>(&w);
     return __half22float2(hv);
@@ -248,9 +280,9 @@ __host__ __device__ inline int link_elem_size(int prec) {
 __host__ __device__ inline size_t link_bytes(int prec, int nreal) {
   return (size_t)nreal * link_elem_size(prec);
 }
-// byte offset of the (parity, dir) slab inside a gauge copy
-__host__ __device__ inline size_t link_slab_offset(int prec, int nreal, int h, int parity, int dir) {
-  return (size_t)(parity * 8 + dir) * link_bytes(prec, nreal) * (size_t)h;
+// byte offset of the (parity, mu) slab inside a gauge copy
+__host__ __device__ inline size_t link_slab_offset(int prec, int nreal, int h, int parity, int mu) {
+  return (size_t)(parity * 4 + mu) * link_bytes(prec, nreal) * (size_t)h;
 }
 
 // Load the R raw reals (as 32-bit words) of link (slab, i).
@@ -482,6 +514,8 @@ struct CGState {
   double stop2;     // stop when rr < stop2 (= tol^2 ||b||^2 for the active stage)
   double rr_ref;    // reliable updates: ||r||^2 at the last update
   double delta2;    // reliable updates: trigger when rr < delta2 * rr_ref
+  double rr_min;    // smallest ||r||^2 of this stage
+  double grow2;     // divergence guard: stop the stage when rr > grow2 * rr_min (0: off)
   int iter;         // iterations done in this stage
   int max_iter;
   int done;         // iteration loop finished (converged, out of iterations, or failed)
@@ -489,7 +523,9 @@ struct CGState {
   int converged;
   int nonfinite;
   int want_update;  // reliable updates: the sloppy residual fell below the trigger
-  int pad;
+  int diverged;     // the stage ended because the iterated residual grew (restart p)
+  int loops;        // graph loop: iteration bodies executed in this stage
+  int loop_cap;     // graph loop: hard bound on loops (the loop always ends)
 };
 
 // What the last block does with the sum of a reduction.
@@ -531,6 +567,7 @@ __device__ __forceinline__ void fin_apply(const Reduce& red, int sys, double sum
     s.beta = sum / s.rr;
     s.rr = sum;
     s.iter += 1;
+    if (sum < s.rr_min) s.rr_min = sum;
     if (sum < s.stop2) {
       s.converged = 1;
       s.done = 1;
@@ -538,6 +575,10 @@ __device__ __forceinline__ void fin_apply(const Reduce& red, int sys, double sum
       s.done = 1;
     } else if (s.delta2 > 0.0 && sum < s.delta2 * s.rr_ref) {
       s.want_update = 1;
+      s.done = 1;
+    } else if (s.grow2 > 0.0 && sum > s.grow2 * s.rr_min) {
+      s.want_update = 1;
+      s.diverged = 1;
       s.done = 1;
     }
   }
@@ -616,6 +657,15 @@ struct tm_lattice_s {
   double* stage;            // device staging buffer for host in/out of full fields
   size_t stage_bytes;
   int* flag_host;           // pinned host word
+  struct StageGraph {       // instantiated CUDA graphs of one CG stage loop (see tm_solver.cu)
+    bool valid;
+    int prec, nreal, px, f;
+    const void *x, *r, *p, *T, *W;
+    double kappa, mu;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+  } graphs[8];
+  int graph_next;           // round-robin replacement slot
 };
 
 namespace tmq {

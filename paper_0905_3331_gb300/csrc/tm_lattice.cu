@@ -190,8 +190,9 @@ __global__ void check_su3_kernel(const double* __restrict__ U, size_t nlinks, un
 }
 
 // ------------------------------------------------------------ gauge copies ---
-// Per output parity p and site cb: slab d = mu holds U_mu(x), slab d = 4 + mu holds
-// U_mu(x - mu^)^dag, compressed to NREAL reals of type S.
+// Per parity p and site cb of that parity, slab mu holds U_mu(x) compressed to NREAL reals of
+// type S.  The hopping kernel reads the forward link of an output site from its own parity's
+// slab and the backward link U_mu(x - mu^) from the other parity's slab at the neighbour.
 template <typename S, int NREAL>
 __global__ void build_links_kernel(Geom g, const double* __restrict__ U, char* __restrict__ out) {
   const int p = blockIdx.y;
@@ -199,27 +200,18 @@ __global__ void build_links_kernel(Geom g, const double* __restrict__ U, char* _
   if (cb >= g.h) return;
   constexpr int BYTES = NREAL * (int)sizeof(S);
   const SiteCoord c = site_of(g, cb, p);
-  const int n[4] = {g.T, g.L, g.L, g.L};
-  const int xc[4] = {c.t, c.x, c.y, c.z};
   const size_t lex = (((size_t)c.t * g.L + c.z) * g.L + c.y) * g.L + c.x;
   const size_t slab = (size_t)BYTES * g.h;
   for (int mu = 0; mu < 4; ++mu) {
-    int yc[4] = {xc[0], xc[1], xc[2], xc[3]};
-    yc[mu] = (xc[mu] + n[mu] - 1) % n[mu];
-    const size_t lexm = (((size_t)yc[0] * g.L + yc[3]) * g.L + yc[2]) * g.L + yc[1];
-    Mat3<double> F, B;
+    Mat3<double> F;
     for (int a = 0; a < 3; ++a)
       for (int b = 0; b < 3; ++b) {
         const double* uf = U + 72 * lex + 18 * mu + 6 * a + 2 * b;
         F.m[a][b] = mk(uf[0], uf[1]);
-        const double* ub = U + 72 * lexm + 18 * mu + 6 * b + 2 * a;  // (b, a) entry
-        B.m[a][b] = mk(ub[0], -ub[1]);                             // conjugate transpose
       }
-    RawWords<BYTES> rf, rb;
+    RawWords<BYTES> rf;
     LinkRecon<double, S, NREAL>::pack(rf, F);
-    LinkRecon<double, S, NREAL>::pack(rb, B);
-    store_raw<BYTES>(out + (size_t)(p * 8 + mu) * slab, g.h, cb, rf);
-    store_raw<BYTES>(out + (size_t)(p * 8 + 4 + mu) * slab, g.h, cb, rb);
+    store_raw<BYTES>(out + (size_t)(p * 4 + mu) * slab, g.h, cb, rf);
   }
 }
 
@@ -237,7 +229,7 @@ tm_status ensure_links(tm_lattice lat, int prec, int nreal, cudaStream_t s) {
     return set_error(TM_ERR_ARG, "link format %d not one of 18, 12, 8", nreal);
   void*& slot = lat->links[prec][link_index(nreal)];
   if (slot) return TM_OK;
-  const size_t bytes = 16 * link_bytes(prec, nreal) * lat->h;
+  const size_t bytes = 8 * link_bytes(prec, nreal) * lat->h;  // 2 parities x 4 directions
   tm_status st = cuda_check(cudaMalloc(&slot, bytes), "gauge copy allocation");
   if (st != TM_OK) {
     slot = nullptr;
@@ -342,6 +334,11 @@ tm_status tm_lattice_destroy(tm_lattice lat) {
   cudaFree(lat->stage);
   if (lat->cgstate_host) cudaFreeHost(lat->cgstate_host);
   if (lat->flag_host) cudaFreeHost(lat->flag_host);
+  for (int k = 0; k < 8; ++k)
+    if (lat->graphs[k].valid) {
+      cudaGraphExecDestroy(lat->graphs[k].exec);
+      cudaGraphDestroy(lat->graphs[k].graph);
+    }
   free(lat);
   return TM_OK;
 }

@@ -28,6 +28,8 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "tm_internal.cuh"
@@ -44,12 +46,22 @@ static unsigned blas_blocks(int h) {
 
 // ------------------------------------------------------------- BLAS kernels ---
 // x += alpha p ; p = r + beta p, once per CG iteration (see `applied`).
+// Inside a graph loop (use_cond) the kernel also decides whether the loop runs again: the
+// last block continues it only while the state is not done and the loop count is below its
+// cap; when there is nothing to apply the state is done and block 0 ends the loop.
 template <int PX, int PP, int PR>
 __global__ void __launch_bounds__(BNT) cg_update_kernel(int h, char* x, char* p, const char* r, CGState* st,
-                                                        unsigned* counter) {
+                                                        unsigned* counter, cudaGraphConditionalHandle cond,
+                                                        int use_cond) {
   CGState& S = st[0];
   const int iter = S.iter;
-  if (iter == S.applied) return;
+  if (iter == S.applied) {
+    if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) {
+      S.loops += 1;
+      cudaGraphSetConditional(cond, 0u);
+    }
+    return;
+  }
   const double alpha = S.alpha, beta = S.beta;
   typedef typename SpinorFmt<PX>::real RX;
   typedef typename SpinorFmt<PP>::real RP;
@@ -74,6 +86,11 @@ __global__ void __launch_bounds__(BNT) cg_update_kernel(int h, char* x, char* p,
     if (prev == gridDim.x - 1) {
       S.applied = iter;
       *counter = 0u;
+      if (use_cond) {
+        S.loops += 1;
+        const bool again = !S.done && S.loops < S.loop_cap;
+        cudaGraphSetConditional(cond, again ? 1u : 0u);
+      }
     }
   }
 }
@@ -247,7 +264,8 @@ static tm_status normal_apply(const Solver& S, int prec, int nreal, const void* 
   return hop_launch(lat, a, S.s);
 }
 
-static tm_status launch_update(const Solver& S, int px, int pp, void* x, void* p, const void* r, CGState* state) {
+static tm_status launch_update(const Solver& S, int px, int pp, void* x, void* p, const void* r, CGState* state,
+                               cudaGraphConditionalHandle cond = 0, int use_cond = 0) {
   tm_lattice lat = S.lat;
   const unsigned nb = blas_blocks(lat->geom.h);
   char* xc = static_cast<char*>(x);
@@ -255,11 +273,11 @@ static tm_status launch_update(const Solver& S, int px, int pp, void* x, void* p
   const char* rc = static_cast<const char*>(r);
   unsigned* ctr = lat->counters + 2;
   if (px == TM_F64)
-    cg_update_kernel<TM_F64, TM_F64, TM_F64><<<nb, BNT, 0, S.s>>>(lat->geom.h, xc, pc, rc, state, ctr);
+    cg_update_kernel<TM_F64, TM_F64, TM_F64><<<nb, BNT, 0, S.s>>>(lat->geom.h, xc, pc, rc, state, ctr, cond, use_cond);
   else if (pp == TM_F32)
-    cg_update_kernel<TM_F32, TM_F32, TM_F32><<<nb, BNT, 0, S.s>>>(lat->geom.h, xc, pc, rc, state, ctr);
+    cg_update_kernel<TM_F32, TM_F32, TM_F32><<<nb, BNT, 0, S.s>>>(lat->geom.h, xc, pc, rc, state, ctr, cond, use_cond);
   else
-    cg_update_kernel<TM_F32, TM_F16, TM_F32><<<nb, BNT, 0, S.s>>>(lat->geom.h, xc, pc, rc, state, ctr);
+    cg_update_kernel<TM_F32, TM_F16, TM_F32><<<nb, BNT, 0, S.s>>>(lat->geom.h, xc, pc, rc, state, ctr, cond, use_cond);
   count_launch();
   return cuda_check(cudaGetLastError(), "CG update kernel");
 }
@@ -281,10 +299,125 @@ static tm_status enqueue_iterations(const Solver& S, const Stage& v, CGState* ds
   return st;
 }
 
+static bool use_graphs() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("TM_NO_GRAPH");
+    v = (e && *e && *e != '0') ? 0 : 1;
+  }
+  return v == 1;
+}
+
+// The CUDA graph of one CG stage: a WHILE conditional node whose body is one iteration
+// (K1..K4 and the update, which sets the loop condition from the device-side state).
+// Graphs are cached per lattice and stage (vectors, precision, flavour, kappa, mu).
+static tm_status stage_graph(const Solver& S, const Stage& v, cudaGraphExec_t* out) {
+  tm_lattice lat = S.lat;
+  for (int k = 0; k < 8; ++k) {
+    const auto& e = lat->graphs[k];
+    if (e.valid && e.prec == v.prec && e.nreal == v.nreal && e.px == v.px && e.f == S.f && e.x == v.x &&
+        e.r == v.r && e.p == v.p && e.T == v.T && e.W == v.W && e.kappa == lat->kappa && e.mu == lat->mu) {
+      *out = e.exec;
+      return TM_OK;
+    }
+  }
+  tm_status st = ensure_links(lat, v.prec, v.nreal, S.s);
+  if (st != TM_OK) return st;
+  if ((st = cuda_check(cudaStreamSynchronize(S.s), "synchronise")) != TM_OK) return st;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  cudaStream_t cs = nullptr;
+  cudaGraphConditionalHandle cond;
+  cudaGraphNode_t node;
+  cudaGraphNodeParams cp = {};
+  const unsigned long long before = tm_launch_count();
+  if ((st = cuda_check(cudaGraphCreate(&g, 0), "cudaGraphCreate")) != TM_OK) return st;
+  st = cuda_check(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault), "conditional handle");
+  if (st == TM_OK) {
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    st = cuda_check(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp), "conditional node");
+  }
+  if (st == TM_OK) st = cuda_check(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream");
+  if (st == TM_OK) {
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    st = cuda_check(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal),
+                    "begin capture");
+    if (st == TM_OK) {
+      Solver C = S;
+      C.s = cs;
+      tm_status st1 = normal_apply(C, v.prec, v.nreal, v.p, v.T, v.W, v.r, lat->cgstate);
+      if (st1 == TM_OK) st1 = launch_update(C, v.px, v.prec, v.x, v.p, v.r, lat->cgstate, cond, 1);
+      cudaGraph_t captured = nullptr;
+      tm_status st2 = cuda_check(cudaStreamEndCapture(cs, &captured), "end capture");
+      st = st1 != TM_OK ? st1 : st2;
+    }
+  }
+  if (st == TM_OK) st = cuda_check(cudaGraphInstantiate(&ex, g, 0), "graph instantiate");
+  if (cs) cudaStreamDestroy(cs);
+  tm_reset_launch_count();
+  count_launch((unsigned)before);  // capture enqueues nothing; keep the launch count unchanged
+  if (st != TM_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  auto& e = lat->graphs[lat->graph_next];
+  if (e.valid) {
+    cudaGraphExecDestroy(e.exec);
+    cudaGraphDestroy(e.graph);
+  }
+  e.valid = true;
+  e.prec = v.prec;
+  e.nreal = v.nreal;
+  e.px = v.px;
+  e.f = S.f;
+  e.x = v.x;
+  e.r = v.r;
+  e.p = v.p;
+  e.T = v.T;
+  e.W = v.W;
+  e.kappa = lat->kappa;
+  e.mu = lat->mu;
+  e.graph = g;
+  e.exec = ex;
+  lat->graph_next = (lat->graph_next + 1) % 8;
+  *out = ex;
+  return TM_OK;
+}
+
+// Graph form of a stage: upload the state, launch the loop graph once, read the state back.
+static tm_status run_stage_graph(const Solver& S, const Stage& v, const CGState& init, CGState* out) {
+  tm_lattice lat = S.lat;
+  tm_status st = ensure_cgstate(lat, 2);
+  if (st != TM_OK) return st;
+  cudaGraphExec_t ex;
+  if ((st = stage_graph(S, v, &ex)) != TM_OK) return st;
+  CGState* hst = lat->cgstate_host;
+  hst[0] = init;
+  hst[0].loops = 0;
+  hst[0].loop_cap = (init.max_iter - init.iter) + 2;
+  if ((st = cuda_check(cudaMemcpyAsync(lat->cgstate, &hst[0], sizeof(CGState), cudaMemcpyHostToDevice, S.s),
+                       "state")) != TM_OK)
+    return st;
+  if ((st = cuda_check(cudaGraphLaunch(ex, S.s), "graph launch")) != TM_OK) return st;
+  if ((st = cuda_check(cudaMemcpyAsync(&hst[1], lat->cgstate, sizeof(CGState), cudaMemcpyDeviceToHost, S.s),
+                       "state")) != TM_OK)
+    return st;
+  if ((st = cuda_check(cudaStreamSynchronize(S.s), "CG stage")) != TM_OK) return st;
+  *out = hst[1];
+  count_launch(5u * (unsigned)hst[1].loops);
+  if (!(hst[1].done)) return set_error(TM_ERR_TIMEOUT, "tm_solve_cg: stage loop reached its bound without finishing");
+  return TM_OK;
+}
+
 // Runs CG iterations from `init` until the device state says done (and the last update has
-// been applied).  Two chunks are in flight: the host reads the state after chunk k while
-// chunk k + 1 runs; chunks after the end cost only empty launches.
+// been applied).  Graph form by default (TM_NO_GRAPH=1 selects the host loop below).  Host
+// loop: two chunks are in flight, the host reads the state after chunk k while chunk k + 1
+// runs; chunks after the end cost only empty launches.
 static tm_status run_stage(const Solver& S, const Stage& v, const CGState& init, CGState* out) {
+  if (use_graphs()) return run_stage_graph(S, v, init, out);
   tm_lattice lat = S.lat;
   tm_status st = ensure_cgstate(lat, 2);
   if (st != TM_OK) return st;
@@ -335,17 +468,42 @@ static tm_status true_residual(const Solver& S, void* r, const void* X, const vo
   return cuda_check(cudaStreamSynchronize(S.s), "synchronise");
 }
 
-static CGState fresh_state(double rr, double stop2, int max_iter, int iter0, double delta2) {
+// Sloppy stages stop when the iterated ||r|| grows by this factor over its minimum.
+constexpr double SLOPPY_GROWTH = 100.0;
+
+static CGState fresh_state(double rr, double stop2, int max_iter, int iter0, double delta2, double growth = 0.0) {
   CGState c;
   memset(&c, 0, sizeof(c));
   c.rr = rr;
   c.rr_ref = rr;
+  c.rr_min = rr;
   c.stop2 = stop2;
   c.max_iter = max_iter;
   c.iter = iter0;
   c.applied = iter0;
   c.delta2 = delta2;
+  c.grow2 = growth * growth;
   return c;
+}
+
+static bool verbose() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("TM_VERBOSE");
+    v = (e && *e && *e != '0') ? 1 : 0;
+  }
+  return v == 1;
+}
+
+static void trace_stage(const char* what, const CGState& c, double bb) {
+  if (!verbose()) return;
+  fprintf(stderr, "[tm_solve_cg] %s: iter %d  |r|/|b| %.3e  converged %d  update %d  diverged %d  nonfinite %d\n",
+          what, c.iter, std::sqrt(c.rr / bb), c.converged, c.want_update, c.diverged, c.nonfinite);
+}
+
+static void trace_update(int k, double rr_true, double bb) {
+  if (!verbose()) return;
+  fprintf(stderr, "[tm_solve_cg] reliable update %d: true |r|/|b| %.3e\n", k, std::sqrt(rr_true / bb));
 }
 
 // Solves M^f x = b for one canonical full field (device pointers).
@@ -414,11 +572,13 @@ static tm_status solve_one(tm_lattice lat, double* x, const double* b, const tm_
     for (;;) {
       CGState fin;
       if ((st = run_stage(S, v, fresh_state(rr, stop2, P.max_iter, iters, 0.0), &fin)) != TM_OK) return st;
+      trace_stage("fp64 stage", fin, bb);
       if (fin.nonfinite) return set_error(TM_ERR_NONFINITE, "tm_solve_cg: non-finite value in the iteration");
       const bool progress = fin.iter > iters;
       iters = fin.iter;
       if ((st = true_residual(S, R, X, bp, T, W, &rr_true)) != TM_OK) return st;
       ++updates;
+      trace_update(updates, rr_true, bb);
       if (rr_true < stop2) {
         converged = true;
         break;
@@ -452,27 +612,35 @@ static tm_status solve_one(tm_lattice lat, double* x, const double* b, const tm_
       CGState fin;
       const double stop_sw = std::fmax(P.tol * bb, stop2);
       if ((st = run_stage(S, v64, fresh_state(rr, stop_sw, P.max_iter, 0, 0.0), &fin)) != TM_OK) return st;
+      trace_stage("fp64 stage (to sqrt(tol))", fin, bb);
       iters = fin.iter;
       if (fin.nonfinite) return set_error(TM_ERR_NONFINITE, "tm_solve_cg: non-finite value in the iteration");
       rr = fin.rr;
       // continue with the sloppy operator from the current r and p
       if ((st = convert_half(lat, TM_F32, rs, TM_F64, R, s)) != TM_OK) return st;
       if ((st = convert_half(lat, sp, ps, TM_F64, Pv, s)) != TM_OK) return st;
-      // first sloppy stage runs without reliable updates (the paper's switch)
-      if ((st = run_stage(S, v, fresh_state(rr, stop2, P.max_iter, iters, 0.0), &fin)) != TM_OK) return st;
+      // first sloppy stage runs without reliable updates (the paper's switch); only the
+      // divergence guard can end it early
+      if ((st = run_stage(S, v, fresh_state(rr, stop2, P.max_iter, iters, 0.0, SLOPPY_GROWTH), &fin)) != TM_OK)
+        return st;
+      trace_stage("sloppy stage", fin, bb);
       iters = fin.iter;
-      if (fin.nonfinite) return set_error(TM_ERR_NONFINITE, "tm_solve_cg: non-finite value in the iteration");
-      {
+      if (fin.nonfinite) {  // drop the overflowed increment; continue from the FP64 solution
+        if ((st = cuda_check(cudaMemsetAsync(xs, 0, S.hb[TM_F32], s), "memset")) != TM_OK) return st;
+        fin.diverged = 1;
+      } else {
         const unsigned nbb = blas_blocks(lat->geom.h);
         accumulate_kernel<TM_F32><<<nbb, BNT, 0, s>>>(lat->geom.h, static_cast<char*>(X), static_cast<char*>(xs));
         count_launch();
       }
       if ((st = true_residual(S, R, X, bp, T, W, &rr_true)) != TM_OK) return st;
       ++updates;
+      trace_update(updates, rr_true, bb);
       converged = rr_true < stop2;
       rr = rr_true;
       if (!converged && iters < P.max_iter) {
         if ((st = convert_half(lat, TM_F32, rs, TM_F64, R, s)) != TM_OK) return st;
+        if (fin.diverged && (st = convert_half(lat, sp, ps, TM_F64, R, s)) != TM_OK) return st;
       }
     } else {
       if ((st = convert_half(lat, TM_F32, rs, TM_F64, bp, s)) != TM_OK) return st;
@@ -480,24 +648,38 @@ static tm_status solve_one(tm_lattice lat, double* x, const double* b, const tm_
     }
     // reliable-update loop (also the defect correction of the sqrt(eps) mode)
     const double delta2 = P.delta * P.delta;
+    int bad_stages = 0;
     while (!converged && iters < P.max_iter) {
       CGState fin;
-      if ((st = run_stage(S, v, fresh_state(rr, stop2, P.max_iter, iters, delta2), &fin)) != TM_OK) return st;
-      if (fin.nonfinite) return set_error(TM_ERR_NONFINITE, "tm_solve_cg: non-finite value in the iteration");
-      if (fin.iter == iters) break;  // no progress (breakdown of <p, A p>): stop, report not converged
-      iters = fin.iter;
-      const unsigned nbb = blas_blocks(lat->geom.h);
-      accumulate_kernel<TM_F32><<<nbb, BNT, 0, s>>>(lat->geom.h, static_cast<char*>(X), static_cast<char*>(xs));
-      count_launch();
+      if ((st = run_stage(S, v, fresh_state(rr, stop2, P.max_iter, iters, delta2, SLOPPY_GROWTH), &fin)) != TM_OK)
+        return st;
+      trace_stage("sloppy stage", fin, bb);
+      if (fin.nonfinite) {
+        // the sloppy iteration overflowed: drop its increment, restart from the FP64 solution
+        if (++bad_stages > 3) return set_error(TM_ERR_NONFINITE, "tm_solve_cg: non-finite value in the iteration");
+        iters = fin.iter;
+        if ((st = cuda_check(cudaMemsetAsync(xs, 0, S.hb[TM_F32], s), "memset")) != TM_OK) return st;
+        fin.diverged = 1;
+      } else {
+        bad_stages = 0;
+        if (fin.iter == iters) break;  // no progress (breakdown of <p, A p>): stop, report not converged
+        iters = fin.iter;
+        const unsigned nbb = blas_blocks(lat->geom.h);
+        accumulate_kernel<TM_F32><<<nbb, BNT, 0, s>>>(lat->geom.h, static_cast<char*>(X), static_cast<char*>(xs));
+        count_launch();
+      }
       if ((st = cuda_check(cudaGetLastError(), "accumulate kernel")) != TM_OK) return st;
       if ((st = true_residual(S, R, X, bp, T, W, &rr_true)) != TM_OK) return st;
       ++updates;
+      trace_update(updates, rr_true, bb);
       if (rr_true < stop2) {
         converged = true;
         break;
       }
       if (!(rr_true < 1e300)) return set_error(TM_ERR_NONFINITE, "tm_solve_cg: residual diverged");
       if ((st = convert_half(lat, TM_F32, rs, TM_F64, R, s)) != TM_OK) return st;
+      // after a divergent stage the search direction restarts from the true residual
+      if (fin.diverged && (st = convert_half(lat, sp, ps, TM_F64, R, s)) != TM_OK) return st;
       rr = rr_true;
     }
   }

@@ -1,0 +1,75 @@
+"""Runs the hopping kernel on one workload in one storage form and prints its timing.
+
+A small driver for timing and for ncu captures of a single kernel:
+
+  python -m paper_0905_3331_gb300.profile_hop --workload 32^3x64 --form f16:12 --iters 5
+
+It sets up the lattice (gauge copy), packs a Gaussian half field, runs
+tm_apply_hopping_eo `iters` times (alternating output parity) and reports the mean
+launch time from CUDA events (L2 flushed before each launch unless --warm), the
+algorithmic bytes and GB/s.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import statistics
+
+import numpy as np
+
+
+def main():
+    import torch
+
+    from . import Lattice, inputs
+    from . import build as libbuild
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="32^3x64")
+    ap.add_argument("--form", default="f16:12", help="storage:links, storage in f64/f32/f16")
+    ap.add_argument("--iters", type=int, default=5)
+    ap.add_argument("--nrhs", type=int, default=1)
+    ap.add_argument("--warm", action="store_true", help="do not flush L2 between launches")
+    args = ap.parse_args()
+    libbuild.build()
+    prec = {"f64": 0, "f32": 1, "f16": 2}[args.form.split(":")[0]]
+    nreal = int(args.form.split(":")[1])
+    w = inputs.WORKLOADS[args.workload]
+    dev = torch.device("cuda:0")
+    lat = Lattice(w.T, w.L, w.kappa, w.mu)
+    lat.set_gauge(w.gauge())
+    h = w.V // 2
+    nb = lat.half_field_bytes(prec)
+    src = inputs.gaussian_spinor(w.T, w.L, w.source_seed, shape_prefix=(args.nrhs,))
+    half = np.ascontiguousarray(src.reshape(args.nrhs, -1, 4, 3)[:, :h])
+    din = torch.empty(args.nrhs * nb, dtype=torch.uint8, device=dev)
+    dout = torch.empty(args.nrhs * nb, dtype=torch.uint8, device=dev)
+    lat.pack_half(prec, din, torch.from_numpy(half).to(dev), nrhs=args.nrhs)
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    lat.apply_hopping_eo(1, dout, din, prec, nreal, nrhs=args.nrhs)
+    torch.cuda.synchronize()
+    times = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for k in range(args.iters):
+        if not args.warm:
+            flush.zero_()
+        e0.record(stream)
+        lat.apply_hopping_eo(k & 1, dout, din, prec, nreal, nrhs=args.nrhs)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    spinor = {0: 192, 1: 96, 2: 52}[prec]
+    elem = {0: 8, 1: 4, 2: 2}[prec]
+    per_site = args.nrhs * 2 * spinor + 8 * nreal * elem
+    t = statistics.mean(times)
+    print(json.dumps({"workload": w.name, "form": args.form, "nrhs": args.nrhs, "h": h,
+                      "us": t * 1e6, "bytes_per_site": per_site,
+                      "gbs": per_site * h / t / 1e9,
+                      "gflops": 1320 * args.nrhs * h / t / 1e9,
+                      "l2": "warm" if args.warm else "flushed"}))
+    lat.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -169,3 +169,44 @@ def test_smallest_lattice_2x2x2x2():
         r = phi - oracle.apply_M(olat, U, x.cpu().numpy(), 0.15, 0.05)
         assert np.linalg.norm(r) / np.linalg.norm(phi) < 1e-10, name
     lat.close()
+
+
+_SUBPROCESS_SOLVE = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, {root!r})
+from paper_0905_3331_gb300 import Lattice, inputs, CG_RELIABLE, F16
+w = inputs.WORKLOADS["4^4"]
+lat = Lattice(w.T, w.L, w.kappa, w.mu)
+lat.set_gauge(w.gauge())
+b = torch.from_numpy(w.source()).cuda()
+x = torch.zeros_like(b)
+info = lat.solve_cg(x, b, mode=CG_RELIABLE, sloppy_prec=F16)
+np.save({out!r}, x.cpu().numpy())
+print("ITERS", info.iters)
+"""
+
+
+@pytest.mark.parametrize("env", [{"TM_NO_GRAPH": "1"}, {"TM_VERBOSE": "1"}])
+def test_host_loop_fallback_and_tracing(env, tmp_path):
+    """The host-driven stage loop (TM_NO_GRAPH=1) gives bitwise the same solution as the
+    CUDA-graph loop (all reductions have a fixed order); TM_VERBOSE=1 traces the stages."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = str(tmp_path / "x.npy")
+    code = _SUBPROCESS_SOLVE.format(root=root, out=out)
+    r = subprocess.run([sys.executable, "-c", code], env={**os.environ, **env}, capture_output=True,
+                       text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    w = inputs.WORKLOADS["4^4"]
+    lat = Lattice(w.T, w.L, w.kappa, w.mu)
+    lat.set_gauge(w.gauge())
+    b = torch.from_numpy(w.source()).to(dev())
+    x = torch.zeros_like(b)
+    info = lat.solve_cg(x, b, mode=CG_RELIABLE, sloppy_prec=F16)
+    assert np.array_equal(np.load(out), x.cpu().numpy())
+    assert f"ITERS {info.iters}" in r.stdout
+    if "TM_VERBOSE" in env:
+        assert "[tm_solve_cg] sloppy stage" in r.stderr and "reliable update" in r.stderr
+    lat.close()
