@@ -237,6 +237,7 @@ def run_gpu(args):
         tw = hop_time(prec, nreal, 1000, cold=False)
         by = hop_bytes_per_site(prec, nreal) * h
         dslash[name] = {"bytes_per_site": hop_bytes_per_site(prec, nreal),
+                        "threads_per_site": lat.hop_threads(prec, nreal),
                         "us_cold": tc * 1e6, "gbs_cold": by / tc / 1e9,
                         "frac_hbm_cold": by / tc / 1e9 / peak,
                         "gflops_cold": HOP_FLOPS * h / tc / 1e9,

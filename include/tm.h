@@ -96,6 +96,17 @@ tm_status tm_lattice_set_params(tm_lattice lat, double kappa, double mu);
 size_t tm_volume(tm_lattice lat);
 size_t tm_half_field_bytes(tm_lattice lat, tm_prec prec);
 
+/* Launch configuration of the hopping kernel for one storage form (a tuning knob; no paper
+ * counterpart).  Each output site's 8 hops are shared by 1, 2 or 4 threads (the partial sums
+ * are added in a fixed order); more threads per site keep more memory requests in flight on
+ * lattices too small to fill the GPU.  By default the library times the three choices when
+ * the form's gauge copy is first built and keeps the fastest (the environment variable
+ * TM_HOP_TPS=1|2|4 overrides that for every form).  tm_set_hop_threads fixes the choice
+ * (0 = tune again); tm_get_hop_threads reports it.  Results for different choices agree to
+ * rounding; for one fixed choice they are bitwise reproducible.  Errors: TM_ERR_ARG. */
+tm_status tm_set_hop_threads(tm_lattice lat, tm_prec prec, tm_link link, int threads_per_site);
+int tm_get_hop_threads(tm_lattice lat, tm_prec prec, tm_link link);
+
 /* Copies the canonical FP64 gauge field U (host or device; 72 V doubles) into the
  * lattice, checks that every link is SU(3) (|U^dag U - 1|_max and |det U - 1| <= 1e-10,
  * all entries finite) and builds the parity-split "gauge copy" of Sec. 4.1 in device

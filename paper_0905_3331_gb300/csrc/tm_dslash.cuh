@@ -130,7 +130,37 @@ __device__ __forceinline__ void hop_dir(cpx<typename SpinorFmt<PREC>::real> acc[
 // MODE 0: out = epi(hop).  MODE 1: same plus sum ||out||^2.
 // MODE 2: out buffer holds r (FP64 for FP64 storage, FP32 otherwise); r <- r - alpha * epi(hop),
 // plus sum ||r||^2.
-template <int PREC, int NREAL, bool HAS_Y, int MODE>
+//
+// TPS (threads per site) = 1, 2 or 4.  With TPS > 1 the 8 hops of a site are split over TPS
+// warps of the block (part q takes the directions q*4/TPS .. (q+1)*4/TPS - 1, both hops of
+// each), so the branch on the part is warp-uniform; the partial sums meet in shared memory,
+// are added in part order 0, 1, ..., and part q finishes the storage blocks
+// [NBLK q / TPS, NBLK (q + 1) / TPS) of the site.  More threads per site give more memory
+// requests in flight for lattices too small to fill the GPU with one thread per site.
+template <int PREC, int NREAL, int TPS>
+__device__ __forceinline__ void hop_part(cpx<typename SpinorFmt<PREC>::real> acc[12], const Geom& g, int cb,
+                                         const SiteCoord& c, const int nb[8], const char* inr, const char* lf,
+                                         const char* lo, size_t slab, int part) {
+  const bool tfwd = (c.t == g.T - 1), tbwd = (c.t == 0);
+  if (TPS == 1 || part == 0 || (TPS == 2 && part == 0)) {
+    hop_dir<PREC, NREAL, 0, +1>(acc, inr, g.h, nb[0], lf + 0 * slab, cb, tfwd);
+    hop_dir<PREC, NREAL, 0, -1>(acc, inr, g.h, nb[4], lo + 0 * slab, nb[4], tbwd);
+  }
+  if (TPS == 1 || (TPS == 2 && part == 0) || (TPS == 4 && part == 1)) {
+    hop_dir<PREC, NREAL, 1, +1>(acc, inr, g.h, nb[1], lf + 1 * slab, cb, false);
+    hop_dir<PREC, NREAL, 1, -1>(acc, inr, g.h, nb[5], lo + 1 * slab, nb[5], false);
+  }
+  if (TPS == 1 || (TPS == 2 && part == 1) || (TPS == 4 && part == 2)) {
+    hop_dir<PREC, NREAL, 2, +1>(acc, inr, g.h, nb[2], lf + 2 * slab, cb, false);
+    hop_dir<PREC, NREAL, 2, -1>(acc, inr, g.h, nb[6], lo + 2 * slab, nb[6], false);
+  }
+  if (TPS == 1 || (TPS == 2 && part == 1) || (TPS == 4 && part == 3)) {
+    hop_dir<PREC, NREAL, 3, +1>(acc, inr, g.h, nb[3], lf + 3 * slab, cb, false);
+    hop_dir<PREC, NREAL, 3, -1>(acc, inr, g.h, nb[7], lo + 3 * slab, nb[7], false);
+  }
+}
+
+template <int PREC, int NREAL, bool HAS_Y, int MODE, int TPS>
 __global__ void __launch_bounds__(HOP_NT) hop_kernel(const Geom g, const int out_parity,
                                                      const char* __restrict__ links, const void* in,
                                                      size_t in_stride, void* out, size_t out_stride,
@@ -138,12 +168,23 @@ __global__ void __launch_bounds__(HOP_NT) hop_kernel(const Geom g, const int out
                                                      const CGState* alpha_src, const double alpha_sign,
                                                      const Reduce red, const int* skip) {
   typedef typename SpinorFmt<PREC>::real R;
+  typedef SpinorFmt<PREC> F;
+  constexpr int SPB = HOP_NT / TPS;         // sites per block
+  constexpr int WPP = (HOP_NT / 32) / TPS;  // warps per part
+  constexpr int STRIDE = 25;                // 24 reals per site, padded against bank conflicts
   __shared__ double sh[HOP_NT / 32];
+  __shared__ R part_acc[TPS > 1 ? TPS * SPB * STRIDE : 1];
+  __shared__ float part_max[(TPS > 1 && F::has_norm) ? TPS * SPB : 1];
   if (skip != nullptr && *skip != 0) return;
   const int rhs = blockIdx.y;
-  const int cb = blockIdx.x * HOP_NT + threadIdx.x;
+  const int warp = threadIdx.x >> 5;
+  const int part = (TPS == 1) ? 0 : warp / WPP;
+  const int sib = (TPS == 1) ? threadIdx.x : (warp % WPP) * 32 + (threadIdx.x & 31);
+  const int cb = blockIdx.x * SPB + sib;
   const bool active = cb < g.h;
-  double nrm = 0.0;
+  cpx<R> acc[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc[k] = mk<R>(R(0), R(0));
   if (active) {
     const SiteCoord c = site_of(g, cb, out_parity);
     int nb[8];
@@ -152,55 +193,87 @@ __global__ void __launch_bounds__(HOP_NT) hop_kernel(const Geom g, const int out
     const size_t slab = link_bytes(PREC, NREAL) * (size_t)g.h;
     const char* lf = links + (size_t)(out_parity * 4) * slab;        // U_mu(x), x of this parity
     const char* lo = links + (size_t)((1 - out_parity) * 4) * slab;  // U_mu(y), y of the other parity
-    cpx<R> acc[12];
+    hop_part<PREC, NREAL, TPS>(acc, g, cb, c, nb, inr, lf, lo, slab, part);
+  }
+  // this thread's share of the site's storage blocks
+  const int kb = (TPS == 1) ? 0 : F::CPB * ((F::NBLK * part) / TPS);
+  const int ke = (TPS == 1) ? 12 : F::CPB * ((F::NBLK * (part + 1)) / TPS);
+  if (TPS > 1) {
+    R* mine = part_acc + (part * SPB + sib) * STRIDE;
 #pragma unroll
-    for (int k = 0; k < 12; ++k) acc[k] = mk<R>(R(0), R(0));
-    const bool tfwd = (c.t == g.T - 1), tbwd = (c.t == 0);
-    hop_dir<PREC, NREAL, 0, +1>(acc, inr, g.h, nb[0], lf + 0 * slab, cb, tfwd);
-    hop_dir<PREC, NREAL, 0, -1>(acc, inr, g.h, nb[4], lo + 0 * slab, nb[4], tbwd);
-    hop_dir<PREC, NREAL, 1, +1>(acc, inr, g.h, nb[1], lf + 1 * slab, cb, false);
-    hop_dir<PREC, NREAL, 1, -1>(acc, inr, g.h, nb[5], lo + 1 * slab, nb[5], false);
-    hop_dir<PREC, NREAL, 2, +1>(acc, inr, g.h, nb[2], lf + 2 * slab, cb, false);
-    hop_dir<PREC, NREAL, 2, -1>(acc, inr, g.h, nb[6], lo + 2 * slab, nb[6], false);
-    hop_dir<PREC, NREAL, 3, +1>(acc, inr, g.h, nb[3], lf + 3 * slab, cb, false);
-    hop_dir<PREC, NREAL, 3, -1>(acc, inr, g.h, nb[7], lo + 3 * slab, nb[7], false);
-
-    // epilogue: o_s = D_s (c acc_s + E_s y_s)
-    const R cc = (R)coef.c;
-    const cpx<R> Du = mk<R>((R)coef.d_up_re, (R)coef.d_up_im), Dl = mk<R>((R)coef.d_lo_re, (R)coef.d_lo_im);
-    cpx<R> o[12];
-    if (HAS_Y) {
-      const cpx<R> Eu = mk<R>((R)coef.e_up_re, (R)coef.e_up_im), El = mk<R>((R)coef.e_lo_re, (R)coef.e_lo_im);
-      cpx<R> yv[12];
-      SpinorFmt<PREC>::load(static_cast<const char*>(y) + (size_t)rhs * y_stride, g.h, cb, yv);
-#pragma unroll
-      for (int k = 0; k < 12; ++k) {
-        const cpx<R> E = (k < 6) ? Eu : El;
-        const cpx<R> D = (k < 6) ? Du : Dl;
-        o[k] = D * (cc * acc[k] + E * yv[k]);
-      }
-    } else {
-#pragma unroll
-      for (int k = 0; k < 12; ++k) o[k] = ((k < 6) ? Du : Dl) * (cc * acc[k]);
+    for (int k = 0; k < 12; ++k) {
+      mine[2 * k] = acc[k].re;
+      mine[2 * k + 1] = acc[k].im;
     }
-    char* outr = static_cast<char*>(out) + (size_t)rhs * out_stride;
-    if (MODE == 2) {
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 12; ++k)
+      if (k >= kb && k < ke) {
+        cpx<R> sum = mk<R>(part_acc[sib * STRIDE + 2 * k], part_acc[sib * STRIDE + 2 * k + 1]);
+#pragma unroll
+        for (int q = 1; q < TPS; ++q) {
+          const R* o = part_acc + (q * SPB + sib) * STRIDE;
+          sum = sum + mk<R>(o[2 * k], o[2 * k + 1]);
+        }
+        acc[k] = sum;
+      }
+  }
+  double nrm = 0.0;
+  // epilogue: o_s = D_s (c acc_s + E_s y_s) on components [kb, ke)
+  const R cc = (R)coef.c;
+  const cpx<R> Du = mk<R>((R)coef.d_up_re, (R)coef.d_up_im), Dl = mk<R>((R)coef.d_lo_re, (R)coef.d_lo_im);
+  cpx<R> o[12];
+  if (HAS_Y) {
+    const cpx<R> Eu = mk<R>((R)coef.e_up_re, (R)coef.e_up_im), El = mk<R>((R)coef.e_lo_re, (R)coef.e_lo_im);
+    cpx<R> yv[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) yv[k] = mk<R>(R(0), R(0));
+    if (active) F::load_range(static_cast<const char*>(y) + (size_t)rhs * y_stride, g.h, cb, yv, kb, ke);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      const cpx<R> E = (k < 6) ? Eu : El;
+      const cpx<R> D = (k < 6) ? Du : Dl;
+      o[k] = D * (cc * acc[k] + E * yv[k]);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) o[k] = ((k < 6) ? Du : Dl) * (cc * acc[k]);
+  }
+  char* outr = static_cast<char*>(out) + (size_t)rhs * out_stride;
+  if (MODE == 2) {
+    if (active) {
       const R al = (R)(alpha_src ? alpha_sign * alpha_src[rhs].alpha : alpha_sign);
       constexpr int PR = ResidPrec<PREC>::value;
       cpx<R> r[12];
-      SpinorFmt<PR>::load(outr, g.h, cb, r);
+      SpinorFmt<PR>::load_range(outr, g.h, cb, r, kb, ke);
 #pragma unroll
-      for (int k = 0; k < 12; ++k) {
-        r[k] = r[k] - al * o[k];
-        nrm += (double)norm2(r[k]);
+      for (int k = 0; k < 12; ++k)
+        if (k >= kb && k < ke) {
+          r[k] = r[k] - al * o[k];
+          nrm += (double)norm2(r[k]);
+        }
+      SpinorFmt<PR>::store_range(outr, g.h, cb, r, kb, ke, 0.f, false);
+    }
+  } else {
+    float m = 0.f;
+    if (F::has_norm) {  // the site's FP16 norm needs all of its components
+#pragma unroll
+      for (int k = 0; k < 12; ++k)
+        if (k >= kb && k < ke) m = fmaxf(m, fmaxf(fabsf((float)o[k].re), fabsf((float)o[k].im)));
+      if (TPS > 1) {
+        part_max[part * SPB + sib] = m;
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < TPS; ++q) m = fmaxf(m, part_max[q * SPB + sib]);
       }
-      SpinorFmt<PR>::store(outr, g.h, cb, r);
-    } else {
+    }
+    if (active) {
       if (MODE == 1) {
 #pragma unroll
-        for (int k = 0; k < 12; ++k) nrm += (double)norm2(o[k]);
+        for (int k = 0; k < 12; ++k)
+          if (k >= kb && k < ke) nrm += (double)norm2(o[k]);
       }
-      SpinorFmt<PREC>::store(outr, g.h, cb, o);
+      F::store_range(outr, g.h, cb, o, kb, ke, m, part == 0);
     }
   }
   if (MODE >= 1) {
@@ -209,30 +282,43 @@ __global__ void __launch_bounds__(HOP_NT) hop_kernel(const Geom g, const int out
   }
 }
 
-template <int PREC, int NREAL>
-tm_status hop_launch_t(tm_lattice lat, const HopArgs& a, cudaStream_t s) {
+template <int PREC, int NREAL, int TPS>
+tm_status hop_launch_tps(tm_lattice lat, const HopArgs& a, cudaStream_t s) {
   const Geom& g = lat->geom;
-  dim3 grid((g.h + HOP_NT - 1) / HOP_NT, a.nrhs);
+  constexpr int SPB = HOP_NT / TPS;
+  dim3 grid((g.h + SPB - 1) / SPB, a.nrhs);
   const char* links = static_cast<const char*>(lat->links[PREC][link_index(NREAL)]);
   const bool has_y = a.y != nullptr;
 #define TM_HOP_ARGS                                                                                      \
   g, a.out_parity, links, a.in, a.in_stride, a.out, a.out_stride, a.y, a.y_stride, a.coef, a.alpha_src, \
       a.alpha_sign, a.red, a.skip
   if (!has_y && a.mode == 0)
-    hop_kernel<PREC, NREAL, false, 0><<<grid, HOP_NT, 0, s>>>(TM_HOP_ARGS);
+    hop_kernel<PREC, NREAL, false, 0, TPS><<<grid, HOP_NT, 0, s>>>(TM_HOP_ARGS);
   else if (!has_y && a.mode == 1)
-    hop_kernel<PREC, NREAL, false, 1><<<grid, HOP_NT, 0, s>>>(TM_HOP_ARGS);
+    hop_kernel<PREC, NREAL, false, 1, TPS><<<grid, HOP_NT, 0, s>>>(TM_HOP_ARGS);
   else if (has_y && a.mode == 0)
-    hop_kernel<PREC, NREAL, true, 0><<<grid, HOP_NT, 0, s>>>(TM_HOP_ARGS);
+    hop_kernel<PREC, NREAL, true, 0, TPS><<<grid, HOP_NT, 0, s>>>(TM_HOP_ARGS);
   else if (has_y && a.mode == 1)
-    hop_kernel<PREC, NREAL, true, 1><<<grid, HOP_NT, 0, s>>>(TM_HOP_ARGS);
+    hop_kernel<PREC, NREAL, true, 1, TPS><<<grid, HOP_NT, 0, s>>>(TM_HOP_ARGS);
   else if (has_y && a.mode == 2)
-    hop_kernel<PREC, NREAL, true, 2><<<grid, HOP_NT, 0, s>>>(TM_HOP_ARGS);
+    hop_kernel<PREC, NREAL, true, 2, TPS><<<grid, HOP_NT, 0, s>>>(TM_HOP_ARGS);
   else
     return set_error(TM_ERR_ARG, "hopping: unsupported epilogue combination");
 #undef TM_HOP_ARGS
   count_launch();
   return cuda_check(cudaGetLastError(), "hopping kernel launch");
+}
+
+template <int PREC, int NREAL>
+tm_status hop_launch_t(tm_lattice lat, const HopArgs& a, cudaStream_t s) {
+  switch (lat->hop_tps[PREC][link_index(NREAL)]) {
+    case 2:
+      return hop_launch_tps<PREC, NREAL, 2>(lat, a, s);
+    case 4:
+      return hop_launch_tps<PREC, NREAL, 4>(lat, a, s);
+    default:
+      return hop_launch_tps<PREC, NREAL, 1>(lat, a, s);
+  }
 }
 
 template <int PREC>

@@ -146,6 +146,26 @@ struct SpinorFmt<TM_F64> {
 #pragma unroll
     for (int k = 0; k < 12; ++k) p[(size_t)k * h + i] = make_double2((double)s[k].re, (double)s[k].im);
   }
+  // components [kb, ke) only (block-aligned)
+  static constexpr int NBLK = 12, CPB = 1;
+  template <typename R>
+  __device__ static __forceinline__ void load_range(const void* base, int h, int i, cpx<R> s[12], int kb, int ke) {
+    const double2* p = static_cast<const double2*>(base);
+#pragma unroll
+    for (int k = 0; k < 12; ++k)
+      if (k >= kb && k < ke) {
+        double2 v = __ldg(p + (size_t)k * h + i);
+        s[k] = mk<R>((R)v.x, (R)v.y);
+      }
+  }
+  template <typename R>
+  __device__ static __forceinline__ void store_range(void* base, int h, int i, const cpx<R> s[12], int kb, int ke,
+                                                     float, bool) {
+    double2* p = static_cast<double2*>(base);
+#pragma unroll
+    for (int k = 0; k < 12; ++k)
+      if (k >= kb && k < ke) p[(size_t)k * h + i] = make_double2((double)s[k].re, (double)s[k].im);
+  }
 };
 
 // FP32: float4 blocks [6][h]
@@ -176,6 +196,28 @@ struct SpinorFmt<TM_F32> {
     for (int k = 0; k < 6; ++k)
       p[(size_t)k * h + i] = make_float4((float)s[2 * k].re, (float)s[2 * k].im,
                                          (float)s[2 * k + 1].re, (float)s[2 * k + 1].im);
+  }
+  static constexpr int NBLK = 6, CPB = 2;
+  template <typename R>
+  __device__ static __forceinline__ void load_range(const void* base, int h, int i, cpx<R> s[12], int kb, int ke) {
+    const float4* p = static_cast<const float4*>(base);
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+      if (2 * k >= kb && 2 * k < ke) {
+        float4 v = __ldg(p + (size_t)k * h + i);
+        s[2 * k] = mk<R>((R)v.x, (R)v.y);
+        s[2 * k + 1] = mk<R>((R)v.z, (R)v.w);
+      }
+  }
+  template <typename R>
+  __device__ static __forceinline__ void store_range(void* base, int h, int i, const cpx<R> s[12], int kb, int ke,
+                                                     float, bool) {
+    float4* p = static_cast<float4*>(base);
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+      if (2 * k >= kb && 2 * k < ke)
+        p[(size_t)k * h + i] = make_float4((float)s[2 * k].re, (float)s[2 * k].im, (float)s[2 * k + 1].re,
+                                           (float)s[2 * k + 1].im);
   }
 };
 
@@ -241,6 +283,42 @@ struct SpinorFmt<TM_F16> {
       p[(size_t)k * h + i] = v;
     }
     nrm[i] = m;
+  }
+  static constexpr int NBLK = 3, CPB = 4;
+  template <typename R>
+  __device__ static __forceinline__ void load_range(const void* base, int h, int i, cpx<R> s[12], int kb, int ke) {
+    const uint4* p = static_cast<const uint4*>(base);
+    const float* nrm = reinterpret_cast<const float*>(p + (size_t)3 * h);
+    const float n = __ldg(nrm + i);
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      if (4 * k >= kb && 4 * k < ke) {
+        uint4 v = __ldg(p + (size_t)k * h + i);
+        float2 a = h2f(v.x), b = h2f(v.y), c = h2f(v.z), d = h2f(v.w);
+        s[4 * k + 0] = mk<R>((R)(a.x * n), (R)(a.y * n));
+        s[4 * k + 1] = mk<R>((R)(b.x * n), (R)(b.y * n));
+        s[4 * k + 2] = mk<R>((R)(c.x * n), (R)(c.y * n));
+        s[4 * k + 3] = mk<R>((R)(d.x * n), (R)(d.y * n));
+      }
+  }
+  // m: the site's norm (largest |re| or |im| over all 12 components), computed by the caller
+  template <typename R>
+  __device__ static __forceinline__ void store_range(void* base, int h, int i, const cpx<R> s[12], int kb, int ke,
+                                                     float m, bool write_norm) {
+    uint4* p = static_cast<uint4*>(base);
+    float* nrm = reinterpret_cast<float*>(p + (size_t)3 * h);
+    const float inv = (m > 0.f) ? 1.0f / m : 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      if (4 * k >= kb && 4 * k < ke) {
+        uint4 v;
+        v.x = f2h((float)s[4 * k + 0].re * inv, (float)s[4 * k + 0].im * inv);
+        v.y = f2h((float)s[4 * k + 1].re * inv, (float)s[4 * k + 1].im * inv);
+        v.z = f2h((float)s[4 * k + 2].re * inv, (float)s[4 * k + 2].im * inv);
+        v.w = f2h((float)s[4 * k + 3].re * inv, (float)s[4 * k + 3].im * inv);
+        p[(size_t)k * h + i] = v;
+      }
+    if (write_norm) nrm[i] = m;
   }
 };
 
@@ -643,6 +721,8 @@ struct tm_lattice_s {
   bool has_gauge;
   double* U_canon;          // 72 V doubles, canonical copy on the device
   void* links[3][3];        // gauge copies [prec][0:18, 1:12, 2:8], built on demand
+  int hop_tps[3][3];        // threads per site of the hopping kernel per form (autotuned; 1, 2, 4)
+  int hop_tps_forced[3][3]; // set by tm_set_hop_threads: the tuner keeps hands off
   // work space
   void* ws[32];             // half-field buffers, allocated on demand
   size_t ws_bytes[32];
@@ -696,6 +776,10 @@ struct HopArgs {
   const int* skip;    // if non-null and *skip != 0 the kernel does nothing
 };
 tm_status hop_launch(tm_lattice lat, const HopArgs& a, cudaStream_t s);
+tm_status hop_launch_dispatch(tm_lattice lat, const HopArgs& a, cudaStream_t s);  // no gauge-copy check
+// blocks of a hopping launch with `tps` threads per site (128-thread blocks)
+inline unsigned hop_grid_blocks(size_t h, int tps) { return (unsigned)((h + 128 / tps - 1) / (128 / tps)); }
+void invalidate_graphs(tm_lattice lat);
 
 // Field conversions (tm_fields.cu)
 tm_status pack_full_parity(tm_lattice lat, int prec, void* dst, const double* src_full, int parity,

@@ -215,6 +215,8 @@ __global__ void build_links_kernel(Geom g, const double* __restrict__ U, char* _
   }
 }
 
+static tm_status tune_hop(tm_lattice lat, int prec, int nreal, cudaStream_t s);
+
 template <typename S, int NREAL>
 static void launch_build(tm_lattice lat, char* out, cudaStream_t s) {
   dim3 grid((lat->geom.h + 127) / 128, 2);
@@ -249,12 +251,89 @@ tm_status ensure_links(tm_lattice lat, int prec, int nreal, cudaStream_t s) {
     if (nreal == 12) launch_build<__half, 12>(lat, out, s);
     if (nreal == 8) launch_build<__half, 8>(lat, out, s);
   }
-  return cuda_check(cudaGetLastError(), "gauge copy build");
+  if ((st = cuda_check(cudaGetLastError(), "gauge copy build")) != TM_OK) return st;
+  return tune_hop(lat, prec, nreal, s);
+}
+
+// ---------------------------------------------------------------- autotuner ---
+// Picks the hopping kernel's threads per site (1, 2 or 4) for one storage form of this lattice
+// by timing each choice (one warm-up and three timed launches, CUDA events, fastest of three)
+// on scratch buffers.  TM_HOP_TPS=1|2|4 in the environment fixes the choice for every form;
+// tm_set_hop_threads fixes it for one form.  Runs when the form's gauge copy is built.
+static int env_tps() {
+  const char* e = getenv("TM_HOP_TPS");
+  if (!e) return 0;
+  const int v = atoi(e);
+  return (v == 1 || v == 2 || v == 4) ? v : 0;
+}
+
+static tm_status tune_hop(tm_lattice lat, int prec, int nreal, cudaStream_t s) {
+  const int li = link_index(nreal);
+  if (lat->hop_tps_forced[prec][li]) return TM_OK;
+  if (const int e = env_tps()) {
+    lat->hop_tps[prec][li] = e;
+    return TM_OK;
+  }
+  const size_t hb = spinor_bytes_per_site(prec) * lat->h;
+  void *din = nullptr, *dout = nullptr;
+  tm_status st = cuda_check(cudaMalloc(&din, hb), "tuner buffer");
+  if (st == TM_OK) st = cuda_check(cudaMalloc(&dout, hb), "tuner buffer");
+  if (st == TM_OK) st = cuda_check(cudaMemsetAsync(din, 0, hb, s), "tuner buffer");
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (st == TM_OK) st = cuda_check(cudaEventCreate(&e0), "event");
+  if (st == TM_OK) st = cuda_check(cudaEventCreate(&e1), "event");
+  int best = 1;
+  float best_ms = 1e30f;
+  HopArgs a{};
+  a.prec = prec;
+  a.nreal = nreal;
+  a.nrhs = 1;
+  a.in = din;
+  a.out = dout;
+  a.coef = epi_plain();
+  const int cands[3] = {1, 2, 4};
+  for (int c = 0; c < 3 && st == TM_OK; ++c) {
+    lat->hop_tps[prec][li] = cands[c];
+    float tmin = 1e30f;
+    for (int k = 0; k < 4 && st == TM_OK; ++k) {
+      a.out_parity = k & 1;
+      st = cuda_check(cudaEventRecord(e0, s), "event");
+      if (st == TM_OK) st = hop_launch_dispatch(lat, a, s);
+      if (st == TM_OK) st = cuda_check(cudaEventRecord(e1, s), "event");
+      if (st == TM_OK) st = cuda_check(cudaEventSynchronize(e1), "tuner");
+      float ms = 0.f;
+      if (st == TM_OK) st = cuda_check(cudaEventElapsedTime(&ms, e0, e1), "event");
+      if (k > 0 && ms < tmin) tmin = ms;  // launch 0 is the warm-up
+    }
+    if (st == TM_OK && tmin < best_ms) {
+      best_ms = tmin;
+      best = cands[c];
+    }
+  }
+  lat->hop_tps[prec][li] = best;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(din);
+  cudaFree(dout);
+  return st;
+}
+
+void invalidate_graphs(tm_lattice lat) {
+  for (int k = 0; k < 8; ++k)
+    if (lat->graphs[k].valid) {
+      cudaGraphExecDestroy(lat->graphs[k].exec);
+      cudaGraphDestroy(lat->graphs[k].graph);
+      lat->graphs[k].valid = false;
+    }
 }
 
 tm_status hop_launch(tm_lattice lat, const HopArgs& a, cudaStream_t s) {
   tm_status st = ensure_links(lat, a.prec, a.nreal, s);
   if (st != TM_OK) return st;
+  return hop_launch_dispatch(lat, a, s);
+}
+
+tm_status hop_launch_dispatch(tm_lattice lat, const HopArgs& a, cudaStream_t s) {
   switch (a.prec) {
     case TM_F64:
       return hop_launch_f64(lat, a, s);
@@ -307,10 +386,10 @@ tm_status tm_lattice_create(int T, int L, double kappa, double mu, tm_lattice* o
   tm_status st = cuda_check(cudaGetDevice(&lat->device), "cudaGetDevice");
   if (st == TM_OK) st = cuda_check(cudaMalloc(&lat->dscalars, 64 * sizeof(double)), "scalar scratch");
   if (st == TM_OK) st = cuda_check(cudaMallocHost(&lat->flag_host, 64 * sizeof(int)), "host flag");
-  // reduction buffers sized once for every kernel of the library (a hopping launch uses
-  // ceil(h / 128) blocks, the vector kernels at most 152 * 16), so nothing is reallocated
+  // reduction buffers sized once for every kernel of the library (a hopping launch uses at
+  // most ceil(h / 32) blocks, the vector kernels at most 152 * 16), so nothing is reallocated
   // while kernels that use them may be in flight
-  if (st == TM_OK) st = ensure_reduce(lat, (lat->h + 127) / 128 + 152 * 16, 64);
+  if (st == TM_OK) st = ensure_reduce(lat, hop_grid_blocks(lat->h, 4) + 152 * 16, 64);
   if (st == TM_OK) st = ensure_cgstate(lat, 2);
   if (st != TM_OK) {
     tm_lattice_destroy(lat);
@@ -334,11 +413,7 @@ tm_status tm_lattice_destroy(tm_lattice lat) {
   cudaFree(lat->stage);
   if (lat->cgstate_host) cudaFreeHost(lat->cgstate_host);
   if (lat->flag_host) cudaFreeHost(lat->flag_host);
-  for (int k = 0; k < 8; ++k)
-    if (lat->graphs[k].valid) {
-      cudaGraphExecDestroy(lat->graphs[k].exec);
-      cudaGraphDestroy(lat->graphs[k].graph);
-    }
+  invalidate_graphs(lat);
   free(lat);
   return TM_OK;
 }
@@ -353,6 +428,29 @@ tm_status tm_lattice_set_params(tm_lattice lat, double kappa, double mu) {
 }
 
 size_t tm_volume(tm_lattice lat) { return lat ? lat->V : 0; }
+
+tm_status tm_set_hop_threads(tm_lattice lat, tm_prec prec, tm_link link, int threads_per_site) {
+  if (!lat || prec < TM_F64 || prec > TM_F16 || (link != 18 && link != 12 && link != 8))
+    return set_error(TM_ERR_ARG, "tm_set_hop_threads: bad argument");
+  if (threads_per_site != 0 && threads_per_site != 1 && threads_per_site != 2 && threads_per_site != 4)
+    return set_error(TM_ERR_ARG, "tm_set_hop_threads: threads_per_site must be 0 (tune), 1, 2 or 4");
+  const int li = link_index(link);
+  invalidate_graphs(lat);  // captured graphs hold the previous kernel choice
+  if (threads_per_site == 0) {
+    lat->hop_tps_forced[prec][li] = 0;
+    if (lat->links[prec][li]) return tune_hop(lat, prec, link, nullptr);
+    return TM_OK;
+  }
+  lat->hop_tps_forced[prec][li] = 1;
+  lat->hop_tps[prec][li] = threads_per_site;
+  return TM_OK;
+}
+
+int tm_get_hop_threads(tm_lattice lat, tm_prec prec, tm_link link) {
+  if (!lat || prec < TM_F64 || prec > TM_F16 || (link != 18 && link != 12 && link != 8)) return 0;
+  const int v = lat->hop_tps[prec][link_index(link)];
+  return v == 0 ? 1 : v;
+}
 
 size_t tm_half_field_bytes(tm_lattice lat, tm_prec prec) {
   if (!lat || prec < 0 || prec > 2) return 0;

@@ -208,8 +208,7 @@ static tm_status norm2_half(const Solver& S, int prec, const void* x, double* ou
 static tm_status normal_apply(const Solver& S, int prec, int nreal, const void* in, void* T, void* W, void* r,
                               CGState* state) {
   tm_lattice lat = S.lat;
-  const int h = lat->geom.h;
-  const unsigned nb = (unsigned)((h + 127) / 128);
+  const unsigned nb = hop_grid_blocks(lat->h, 4);  // enough for every threads-per-site choice
   tm_status st = ensure_reduce(lat, nb, 4);
   if (st != TM_OK) return st;
   HopArgs a{};

@@ -30,6 +30,7 @@ def main():
     ap.add_argument("--iters", type=int, default=5)
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--warm", action="store_true", help="do not flush L2 between launches")
+    ap.add_argument("--tps", type=int, default=0, help="threads per site 1/2/4 (0: autotuned)")
     args = ap.parse_args()
     libbuild.build()
     prec = {"f64": 0, "f32": 1, "f16": 2}[args.form.split(":")[0]]
@@ -37,6 +38,8 @@ def main():
     w = inputs.WORKLOADS[args.workload]
     dev = torch.device("cuda:0")
     lat = Lattice(w.T, w.L, w.kappa, w.mu)
+    if args.tps:
+        lat.set_hop_threads(prec, nreal, args.tps)
     lat.set_gauge(w.gauge())
     h = w.V // 2
     nb = lat.half_field_bytes(prec)
@@ -64,6 +67,7 @@ def main():
     per_site = args.nrhs * 2 * spinor + 8 * nreal * elem
     t = statistics.mean(times)
     print(json.dumps({"workload": w.name, "form": args.form, "nrhs": args.nrhs, "h": h,
+                      "threads_per_site": lat.hop_threads(prec, nreal),
                       "us": t * 1e6, "bytes_per_site": per_site,
                       "gbs": per_site * h / t / 1e9,
                       "gflops": 1320 * args.nrhs * h / t / 1e9,

@@ -75,6 +75,8 @@ def load():
         "tm_lattice_set_params": ([P, D, D], I),
         "tm_volume": ([P], S),
         "tm_half_field_bytes": ([P, I], S),
+        "tm_set_hop_threads": ([P, I, I, I], I),
+        "tm_get_hop_threads": ([P, I, I], I),
         "tm_set_gauge": ([P, P, P], I),
         "tm_pack_half": ([P, I, P, P, I, P], I),
         "tm_unpack_half": ([P, I, P, P, I, P], I),
@@ -98,7 +100,7 @@ def load():
 def exported_symbols():
     """Names of the ABI functions this binding binds (all must exist in the library)."""
     return ["tm_lattice_create", "tm_lattice_destroy", "tm_lattice_set_params", "tm_volume",
-            "tm_half_field_bytes", "tm_set_gauge", "tm_pack_half", "tm_unpack_half", "tm_apply_D",
+            "tm_half_field_bytes", "tm_set_hop_threads", "tm_get_hop_threads", "tm_set_gauge", "tm_pack_half", "tm_unpack_half", "tm_apply_D",
             "tm_apply_hopping_eo", "tm_apply_Mee_inv", "tm_solve_cg", "tm_cg_params_default",
             "tm_last_error", "tm_launch_count", "tm_reset_launch_count"]
 
@@ -191,6 +193,14 @@ class Lattice:
 
     def half_field_bytes(self, prec: int) -> int:
         return int(load().tm_half_field_bytes(self._h, prec))
+
+    def set_hop_threads(self, prec: int, link: int, threads_per_site: int):
+        """Fix the hopping kernel's threads per site (1, 2, 4) for one form; 0 re-tunes."""
+        _check(load().tm_set_hop_threads(self._h, prec, link, threads_per_site),
+               "tm_set_hop_threads")
+
+    def hop_threads(self, prec: int, link: int) -> int:
+        return int(load().tm_get_hop_threads(self._h, prec, link))
 
     def set_gauge(self, U, stream=None):
         _check(load().tm_set_gauge(self._h, _addr(U), _stream(stream)), "tm_set_gauge")

@@ -55,6 +55,8 @@ def test_host_side_argument_checks(lib):
     assert lib.tm_solve_cg(None, None, None, 1, None, None, None) == 1
     assert lib.tm_lattice_destroy(None) == 0
     assert lib.tm_volume(None) == 0
+    assert lib.tm_set_hop_threads(None, 0, 18, 2) == 1
+    assert lib.tm_get_hop_threads(None, 0, 18) == 0
 
 
 def test_cg_params_defaults(lib):

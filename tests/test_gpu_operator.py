@@ -240,3 +240,33 @@ def test_full_size_sampled_sites(name, prec, link):
     ref = oracle.hopping_sites(olat, U, masked, lexs[idx])
     assert rel(got, ref) < TOL[(prec, link)]
     lat.close()
+
+
+@pytest.mark.parametrize("tps", [1, 2, 4])
+@pytest.mark.parametrize("T,L", [(2, 2), (4, 6), (32, 16)])
+@pytest.mark.parametrize("prec,link", [(F64, 18), (F32, 12), (F16, 12), (F16, 8)])
+def test_hopping_each_threads_per_site(tps, T, L, prec, link):
+    """The 1-, 2- and 4-threads-per-site kernels all match the oracle (ragged tails included)."""
+    lat = Lattice(T, L, 0.1632, 0.004)
+    lat.set_hop_threads(prec, link, tps)
+    U = inputs.random_gauge(T, L, 0.5, 1)
+    lat.set_gauge(U)
+    assert lat.hop_threads(prec, link) == tps
+    olat = oracle.Lattice.cubic(T, L)
+    psi = inputs.gaussian_spinor(T, L, 8)
+    nb = lat.half_field_bytes(prec)
+    for p in (0, 1):
+        src = to_half(psi, 1 - p)
+        ref = to_half(oracle.hopping(olat, U, from_half(src, 1 - p, T, L), out_parity=p), p)
+        din = torch.empty(nb, dtype=torch.uint8, device=dev())
+        dout = torch.empty(nb, dtype=torch.uint8, device=dev())
+        lat.pack_half(prec, din, torch.from_numpy(src).to(dev()))
+        lat.apply_hopping_eo(p, dout, din, prec, link)
+        got = torch.empty(src.shape, dtype=torch.complex128, device=dev())
+        lat.unpack_half(prec, got, dout)
+        assert rel(got.cpu().numpy(), ref) < TOL[(prec, link)]
+    # D itself (FP64) with this configuration
+    out = torch.empty(psi.shape, dtype=torch.complex128, device=dev())
+    lat.apply_D(out, torch.from_numpy(psi).to(dev()))
+    assert rel(out.cpu().numpy(), oracle.apply_M(olat, U, psi, lat.kappa, lat.mu)) < 1e-13
+    lat.close()

@@ -177,6 +177,8 @@ sys.path.insert(0, {root!r})
 from paper_0905_3331_gb300 import Lattice, inputs, CG_RELIABLE, F16
 w = inputs.WORKLOADS["4^4"]
 lat = Lattice(w.T, w.L, w.kappa, w.mu)
+for prec, link in ((0, 18), (2, 12)):
+    lat.set_hop_threads(prec, link, 2)
 lat.set_gauge(w.gauge())
 b = torch.from_numpy(w.source()).cuda()
 x = torch.zeros_like(b)
@@ -201,6 +203,8 @@ def test_host_loop_fallback_and_tracing(env, tmp_path):
     assert r.returncode == 0, r.stderr
     w = inputs.WORKLOADS["4^4"]
     lat = Lattice(w.T, w.L, w.kappa, w.mu)
+    for prec, link in ((0, 18), (2, 12)):  # same kernel choice as the subprocess
+        lat.set_hop_threads(prec, link, 2)
     lat.set_gauge(w.gauge())
     b = torch.from_numpy(w.source()).to(dev())
     x = torch.zeros_like(b)
@@ -209,4 +213,23 @@ def test_host_loop_fallback_and_tracing(env, tmp_path):
     assert f"ITERS {info.iters}" in r.stdout
     if "TM_VERBOSE" in env:
         assert "[tm_solve_cg] sloppy stage" in r.stderr and "reliable update" in r.stderr
+    lat.close()
+
+
+@pytest.mark.parametrize("tps", [1, 2, 4])
+def test_solve_with_each_threads_per_site(tps):
+    """Every launch configuration of the hopping kernel gives a solve that meets the bar."""
+    w = inputs.WORKLOADS["4^4"]
+    U, phi = w.gauge(), w.source()
+    lat = Lattice(w.T, w.L, w.kappa, w.mu)
+    for prec, link in ((0, 18), (1, 12), (2, 12)):
+        lat.set_hop_threads(prec, link, tps)
+    lat.set_gauge(U)
+    b = torch.from_numpy(phi).to(dev())
+    for kw in (dict(mode=CG_FP64), dict(mode=CG_RELIABLE, sloppy_prec=F32, sloppy_link=LINK12),
+               dict(mode=CG_RELIABLE, sloppy_prec=F16, sloppy_link=LINK12)):
+        x = torch.zeros_like(b)
+        lat.solve_cg(x, b, **kw)
+        assert oracle_true_residual(w, U, phi, x.cpu().numpy()) < 1e-10
+    assert lat.hop_threads(0, 18) == tps
     lat.close()
