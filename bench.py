@@ -35,8 +35,8 @@ HOP_FLOPS = 1320  # per output site per hopping application (8 hops x 168 flops 
 def hop_bytes_per_site(prec: int, nreal: int) -> int:
     """Algorithmic bytes per output site of one half-lattice hopping application: one input
     spinor, eight links (4 forward + 4 backward), one output spinor."""
-    spinor = {0: 192, 1: 96, 2: 52}[prec]
-    elem = {0: 8, 1: 4, 2: 2}[prec]
+    spinor = {0: 192, 1: 96, 2: 52, 3: 192}[prec]
+    elem = {0: 8, 1: 4, 2: 2, 3: 8}[prec]
     return 2 * spinor + 8 * nreal * elem
 
 

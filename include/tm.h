@@ -32,6 +32,8 @@
  *   TM_F16  uint4   blocks [3][h]: block j = components 4j..4j+3 as 8 IEEE halves
  *           (re, im, ...), then float norm[h]; value = half * norm[cb], where norm is
  *           the site's largest |re| or |im|.                                     52 h bytes
+ *   TM_DF64 float4  blocks [12][h]: block k = (re.hi, re.lo, im.hi, im.lo) of component k,
+ *           value = hi + lo.                                                   192 h bytes
  *   nrhs half fields are stacked back to back (stride tm_half_field_bytes()).
  * Pointers  "device" pointers are CUDA device (or managed) memory of the current
  *           device.  Arguments named "host or device" are classified with
@@ -72,11 +74,16 @@ typedef enum {
   TM_ERR_UNSUPPORTED = 10   /* a precision / link-format combination that is not built */
 } tm_status;
 
-typedef enum { TM_F64 = 0, TM_F32 = 1, TM_F16 = 2 } tm_prec; /* spinor storage precision */
+/* Spinor storage precision.  TM_DF64 ("double-float") stores each real as two FP32 numbers
+ * hi + lo and computes in double-word arithmetic on the FP32 units (about 48 significant
+ * bits); a form of this library with no counterpart in the paper.  (Measured on GB300 the
+ * double-word kernel is not faster than native FP64: 226 vs 173 us on 16^3 x 32.) */
+typedef enum { TM_F64 = 0, TM_F32 = 1, TM_F16 = 2, TM_DF64 = 3 } tm_prec;
 
 /* Gauge-link storage: 18 reals, 12 (rows 1-2; row 3 = conj(row1 x row2)) or 8
  * (a 2-row/column parametrisation of SU(3), reconstructed in registers).  Links
- * are stored in the precision of the spinors they act on (FP64, FP32, FP16). */
+ * are stored in the precision of the spinors they act on (FP64, FP32, FP16, double-float;
+ * double-float supports 18 reals only, with one thread per site). */
 typedef enum { TM_LINK18 = 18, TM_LINK12 = 12, TM_LINK8 = 8 } tm_link;
 
 /* ---------------------------------------------------------------- lattice --- */
@@ -172,6 +179,10 @@ typedef struct {
   double delta;         /* reliable-update trigger (mode 2), e.g. 0.1 */
   int use_x0;           /* nonzero: x holds the initial guess (full field) */
   int flavour;          /* +1 solves M(+mu) x = b, -1 solves M(-mu) x = b; 0 means +1 */
+  int update_prec;      /* modes 1, 2: arithmetic of the residual recomputations inside the
+                           loop, TM_F64 or TM_DF64 (double-float; about 48 bits, on the FP32
+                           units).  Convergence is always confirmed by an FP64 recomputation;
+                           if that fails the solve continues with FP64 recomputations. */
 } tm_cg_params;
 
 typedef struct {
@@ -194,7 +205,7 @@ tm_status tm_solve_cg(tm_lattice lat, double *x, const double *b, int nrhs,
                       const tm_cg_params *params, tm_cg_info *info, void *stream);
 
 /* Fills params with the defaults: tol 1e-10, max_iter 100000, TM_CG_FP64, sloppy
- * TM_F32 / TM_LINK12, delta 0.1, use_x0 0, flavour +1. */
+ * TM_F32 / TM_LINK12, delta 0.1, use_x0 0, flavour +1, update_prec TM_F64. */
 void tm_cg_params_default(tm_cg_params *params);
 
 /* ------------------------------------------------------ allocation-free variant --- */

@@ -336,6 +336,7 @@ tm_status hop_launch_prec(tm_lattice lat, const HopArgs& a, cudaStream_t s) {
 }
 
 tm_status hop_launch_f64(tm_lattice lat, const HopArgs& a, cudaStream_t s);
+tm_status hop_launch_df64(tm_lattice lat, const HopArgs& a, cudaStream_t s);
 tm_status hop_launch_f32(tm_lattice lat, const HopArgs& a, cudaStream_t s);
 tm_status hop_launch_f16(tm_lattice lat, const HopArgs& a, cudaStream_t s);
 

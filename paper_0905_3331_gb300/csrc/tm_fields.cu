@@ -104,6 +104,10 @@ __global__ void diag_kernel(int h, const char* in, size_t istride, char* out, si
       constexpr int P = TM_F32;        \
       F;                               \
     } break;                           \
+    case TM_DF64: {                    \
+      constexpr int P = TM_DF64;       \
+      F;                               \
+    } break;                           \
     default: {                         \
       constexpr int P = TM_F16;        \
       F;                               \
@@ -145,6 +149,11 @@ tm_status convert_half(tm_lattice lat, int prec_out, void* dst, int prec_in, con
   TM_CONV(TM_F16, TM_F64)
   TM_CONV(TM_F16, TM_F32)
   TM_CONV(TM_F16, TM_F16)
+  TM_CONV(TM_F64, TM_DF64)
+  TM_CONV(TM_DF64, TM_F64)
+  TM_CONV(TM_DF64, TM_F32)
+  TM_CONV(TM_F32, TM_DF64)
+  TM_CONV(TM_DF64, TM_DF64)
 #undef TM_CONV
   count_launch();
   return cuda_check(cudaGetLastError(), "convert kernel");
@@ -189,7 +198,7 @@ extern "C" {
 
 tm_status tm_pack_half(tm_lattice lat, tm_prec prec, void* dst, const double* src, int nrhs, void* stream) {
   if (!lat || !dst || !src || nrhs < 1) return set_error(TM_ERR_ARG, "tm_pack_half: bad argument");
-  if (prec < TM_F64 || prec > TM_F16) return set_error(TM_ERR_ARG, "tm_pack_half: precision %d", (int)prec);
+  if (prec < TM_F64 || prec > TM_DF64) return set_error(TM_ERR_ARG, "tm_pack_half: precision %d", (int)prec);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   tm_status st;
   const void* d = stage_in(lat, WS_STAGE_IN, src, (size_t)nrhs * lat->h * 24 * sizeof(double), s, &st);
@@ -205,7 +214,7 @@ tm_status tm_pack_half(tm_lattice lat, tm_prec prec, void* dst, const double* sr
 
 tm_status tm_unpack_half(tm_lattice lat, tm_prec prec, double* dst, const void* src, int nrhs, void* stream) {
   if (!lat || !dst || !src || nrhs < 1) return set_error(TM_ERR_ARG, "tm_unpack_half: bad argument");
-  if (prec < TM_F64 || prec > TM_F16) return set_error(TM_ERR_ARG, "tm_unpack_half: precision %d", (int)prec);
+  if (prec < TM_F64 || prec > TM_DF64) return set_error(TM_ERR_ARG, "tm_unpack_half: precision %d", (int)prec);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   tm_status st;
   const size_t bytes = (size_t)nrhs * lat->h * 24 * sizeof(double);
@@ -226,7 +235,7 @@ tm_status tm_apply_Mee_inv(tm_lattice lat, void* out, const void* in, int flavou
                            void* stream) {
   if (!lat || !out || !in || nrhs < 1) return set_error(TM_ERR_ARG, "tm_apply_Mee_inv: bad argument");
   if (flavour != 1 && flavour != -1) return set_error(TM_ERR_ARG, "tm_apply_Mee_inv: flavour must be +1 or -1");
-  if (prec < TM_F64 || prec > TM_F16) return set_error(TM_ERR_ARG, "tm_apply_Mee_inv: precision %d", (int)prec);
+  if (prec < TM_F64 || prec > TM_DF64) return set_error(TM_ERR_ARG, "tm_apply_Mee_inv: precision %d", (int)prec);
   const double mut = 2.0 * lat->kappa * lat->mu;
   const double n = 1.0 / (1.0 + mut * mut);
   return diag_apply(lat, prec, out, in, nrhs, n, -flavour * mut * n, n, flavour * mut * n,

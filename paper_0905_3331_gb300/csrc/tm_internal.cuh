@@ -70,6 +70,63 @@ __device__ __forceinline__ R norm2(cpx<R> a) {
   return a.re * a.re + a.im * a.im;
 }
 
+// ------------------------------------------------------------- double-float ---
+// A real number held as the unevaluated sum hi + lo of two FP32 numbers ("double-word"
+// arithmetic, Dekker 1971).  The building blocks are the error-free transformations TwoSum
+// (Knuth; exact: s + e = a + b) and TwoProd via FMA (exact: p + e = a * b), and the addition
+// and multiplication of double-word numbers as analysed by Joldes, Muller and Popescu (ACM
+// TOMS 2017): relative error about 3 * 2^-48 and 5 * 2^-48, so about 48 significant bits,
+// with the FP32 exponent range.  All of it runs on the FP32 pipes, which on GB300 issue
+// about 58 times the FP64 rate.
+struct dd {
+  float hi, lo;
+  dd() = default;
+  __host__ __device__ constexpr dd(float h, float l) : hi(h), lo(l) {}
+  __device__ dd(float f) : hi(f), lo(0.f) {}
+  __device__ dd(int i) : hi((float)i), lo(0.f) {}
+  __device__ dd(double d) {
+    hi = __double2float_rn(d);
+    lo = __double2float_rn(d - (double)hi);
+  }
+  __device__ explicit operator double() const { return (double)hi + (double)lo; }
+  __device__ explicit operator float() const { return hi + lo; }
+};
+
+__device__ __forceinline__ float dd_two_sum(float a, float b, float& e) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return s;
+}
+__device__ __forceinline__ float dd_fast_two_sum(float a, float b, float& e) {  // needs |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+  return s;
+}
+__device__ __forceinline__ dd operator+(dd x, dd y) {
+  float e, f;
+  float s = dd_two_sum(x.hi, y.hi, e);
+  const float t = dd_two_sum(x.lo, y.lo, f);
+  e = __fadd_rn(e, t);
+  float g;
+  s = dd_fast_two_sum(s, e, g);
+  g = __fadd_rn(g, f);
+  float lo;
+  s = dd_fast_two_sum(s, g, lo);
+  return dd(s, lo);
+}
+__device__ __forceinline__ dd operator-(dd x) { return dd(-x.hi, -x.lo); }
+__device__ __forceinline__ dd operator-(dd x, dd y) { return x + (-y); }
+__device__ __forceinline__ dd operator*(dd x, dd y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  float lo;
+  const float s = dd_fast_two_sum(p, e, lo);
+  return dd(s, lo);
+}
+
 // ------------------------------------------------------------------ geometry ---
 // T x L^3 lattice, checkerboard index cb = lex / 2 within one parity.
 struct Geom {
@@ -325,11 +382,64 @@ struct SpinorFmt<TM_F16> {
 // Precision of the iterated residual that goes with an operator storage precision.
 template <int PREC>
 struct ResidPrec {
-  static constexpr int value = (PREC == TM_F64) ? TM_F64 : TM_F32;
+  static constexpr int value = (PREC == TM_F64 || PREC == TM_DF64) ? PREC : TM_F32;
+};
+
+// Double-float (TM_DF64): float4 blocks [12][h], block k = (re.hi, re.lo, im.hi, im.lo) of
+// complex component k.  Same footprint as FP64, double-float arithmetic.
+template <>
+struct SpinorFmt<TM_DF64> {
+  typedef dd real;
+  static constexpr bool has_norm = false;
+  static constexpr size_t bytes_per_site = 192;
+  static constexpr int NBLK = 12, CPB = 1;
+  template <typename R>
+  __device__ static __forceinline__ void load(const void* base, int h, int i, cpx<R> s[12]) {
+    const float4* p = static_cast<const float4*>(base);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) s[k] = conv<R>(__ldg(p + (size_t)k * h + i));
+  }
+  template <typename R>
+  __device__ static __forceinline__ void load_unscaled(const void* base, int h, int i, cpx<R> s[12], R& scale) {
+    load(base, h, i, s);
+    scale = R(1);
+  }
+  template <typename R>
+  __device__ static __forceinline__ void store(void* base, int h, int i, const cpx<R> s[12]) {
+    float4* p = static_cast<float4*>(base);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) p[(size_t)k * h + i] = pack(s[k]);
+  }
+  template <typename R>
+  __device__ static __forceinline__ void load_range(const void* base, int h, int i, cpx<R> s[12], int kb, int ke) {
+    const float4* p = static_cast<const float4*>(base);
+#pragma unroll
+    for (int k = 0; k < 12; ++k)
+      if (k >= kb && k < ke) s[k] = conv<R>(__ldg(p + (size_t)k * h + i));
+  }
+  template <typename R>
+  __device__ static __forceinline__ void store_range(void* base, int h, int i, const cpx<R> s[12], int kb, int ke,
+                                                     float, bool) {
+    float4* p = static_cast<float4*>(base);
+#pragma unroll
+    for (int k = 0; k < 12; ++k)
+      if (k >= kb && k < ke) p[(size_t)k * h + i] = pack(s[k]);
+  }
+  // conversions: the (hi, lo) pair to the arithmetic type R, and any R to a (hi, lo) pair
+  template <typename R>
+  __device__ static __forceinline__ cpx<R> conv(float4 v) {
+    return mk<R>(R(dd(v.x, v.y)), R(dd(v.z, v.w)));
+  }
+  __device__ static __forceinline__ float4 pack(const cpx<dd>& z) { return make_float4(z.re.hi, z.re.lo, z.im.hi, z.im.lo); }
+  __device__ static __forceinline__ float4 pack(const cpx<double>& z) {
+    const dd a(z.re), b(z.im);
+    return make_float4(a.hi, a.lo, b.hi, b.lo);
+  }
+  __device__ static __forceinline__ float4 pack(const cpx<float>& z) { return make_float4(z.re, 0.f, z.im, 0.f); }
 };
 
 __host__ __device__ inline size_t spinor_bytes_per_site(int prec) {
-  return prec == TM_F64 ? 192 : (prec == TM_F32 ? 96 : 52);
+  return prec == TM_F64 ? 192 : (prec == TM_F32 ? 96 : (prec == TM_F16 ? 52 : 192));
 }
 
 // -------------------------------------------------------------------- links ---
@@ -351,9 +461,14 @@ struct LinkStore<TM_F16> {
   typedef __half type;
   static constexpr int size = 2;
 };
+template <>
+struct LinkStore<TM_DF64> {
+  typedef dd type;
+  static constexpr int size = 8;
+};
 
 __host__ __device__ inline int link_elem_size(int prec) {
-  return prec == TM_F64 ? 8 : (prec == TM_F32 ? 4 : 2);
+  return (prec == TM_F64 || prec == TM_DF64) ? 8 : (prec == TM_F32 ? 4 : 2);
 }
 __host__ __device__ inline size_t link_bytes(int prec, int nreal) {
   return (size_t)nreal * link_elem_size(prec);
@@ -432,6 +547,16 @@ struct RawGet<float, BYTES> {
   }
   __device__ static __forceinline__ void put(RawWords<BYTES>& r, int k, float v) {
     r.w[k] = __float_as_uint(v);
+  }
+};
+template <int BYTES>
+struct RawGet<dd, BYTES> {
+  __device__ static __forceinline__ dd get(const RawWords<BYTES>& r, int k) {
+    return dd(__uint_as_float(r.w[2 * k]), __uint_as_float(r.w[2 * k + 1]));
+  }
+  __device__ static __forceinline__ void put(RawWords<BYTES>& r, int k, dd v) {
+    r.w[2 * k] = __float_as_uint(v.hi);
+    r.w[2 * k + 1] = __float_as_uint(v.lo);
   }
 };
 template <int BYTES>
@@ -720,9 +845,9 @@ struct tm_lattice_s {
   int device;
   bool has_gauge;
   double* U_canon;          // 72 V doubles, canonical copy on the device
-  void* links[3][3];        // gauge copies [prec][0:18, 1:12, 2:8], built on demand
-  int hop_tps[3][3];        // threads per site of the hopping kernel per form (autotuned; 1, 2, 4)
-  int hop_tps_forced[3][3]; // set by tm_set_hop_threads: the tuner keeps hands off
+  void* links[4][3];        // gauge copies [prec][0:18, 1:12, 2:8], built on demand
+  int hop_tps[4][3];        // threads per site of the hopping kernel per form (autotuned; 1, 2, 4)
+  int hop_tps_forced[4][3]; // set by tm_set_hop_threads: the tuner keeps hands off
   // work space
   void* ws[32];             // half-field buffers, allocated on demand
   size_t ws_bytes[32];
@@ -792,8 +917,9 @@ tm_status apply_M_halves(tm_lattice lat, void* out_e, void* out_o, const void* i
                          cudaStream_t s);
 tm_status diag_apply(tm_lattice lat, int prec, void* out, const void* in, int nrhs, double dur, double dui,
                      double dlr, double dli, cudaStream_t s);
-// Workspace slots: 0..15 solver, 16..19 tm_apply_D, 20 staged input, 21 staged output.
-enum { WS_APPLY_D = 16, WS_STAGE_IN = 20, WS_STAGE_OUT = 21 };
+// Workspace slots: 0..17 solver, 22..25 tm_apply_D, 26 staged input, 27 staged output,
+// 28 initial-guess work space.
+enum { WS_APPLY_D = 22, WS_STAGE_IN = 26, WS_STAGE_OUT = 27, WS_X0 = 28 };
 // host-buffer staging through workspace slots
 const void* stage_in(tm_lattice lat, int slot, const void* src, size_t bytes, cudaStream_t s, tm_status* st);
 void* stage_out(tm_lattice lat, int slot, void* dst, size_t bytes, tm_status* st);

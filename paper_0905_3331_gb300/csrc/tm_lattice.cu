@@ -226,9 +226,11 @@ static void launch_build(tm_lattice lat, char* out, cudaStream_t s) {
 
 tm_status ensure_links(tm_lattice lat, int prec, int nreal, cudaStream_t s) {
   if (!lat->has_gauge) return set_error(TM_ERR_NO_GAUGE, "no gauge field: call tm_set_gauge first");
-  if (prec < 0 || prec > 2) return set_error(TM_ERR_ARG, "precision %d not one of TM_F64/F32/F16", prec);
+  if (prec < 0 || prec > 3) return set_error(TM_ERR_ARG, "precision %d not one of TM_F64/F32/F16/DF64", prec);
   if (nreal != 18 && nreal != 12 && nreal != 8)
     return set_error(TM_ERR_ARG, "link format %d not one of 18, 12, 8", nreal);
+  if (prec == TM_DF64 && nreal != 18)
+    return set_error(TM_ERR_UNSUPPORTED, "double-float storage supports 18-real links only");
   void*& slot = lat->links[prec][link_index(nreal)];
   if (slot) return TM_OK;
   const size_t bytes = 8 * link_bytes(prec, nreal) * lat->h;  // 2 parities x 4 directions
@@ -246,6 +248,8 @@ tm_status ensure_links(tm_lattice lat, int prec, int nreal, cudaStream_t s) {
     if (nreal == 18) launch_build<float, 18>(lat, out, s);
     if (nreal == 12) launch_build<float, 12>(lat, out, s);
     if (nreal == 8) launch_build<float, 8>(lat, out, s);
+  } else if (prec == TM_DF64) {
+    launch_build<dd, 18>(lat, out, s);
   } else {
     if (nreal == 18) launch_build<__half, 18>(lat, out, s);
     if (nreal == 12) launch_build<__half, 12>(lat, out, s);
@@ -270,6 +274,10 @@ static int env_tps() {
 static tm_status tune_hop(tm_lattice lat, int prec, int nreal, cudaStream_t s) {
   const int li = link_index(nreal);
   if (lat->hop_tps_forced[prec][li]) return TM_OK;
+  if (prec == TM_DF64) {  // built with one thread per site only
+    lat->hop_tps[prec][li] = 1;
+    return TM_OK;
+  }
   if (const int e = env_tps()) {
     lat->hop_tps[prec][li] = e;
     return TM_OK;
@@ -341,6 +349,8 @@ tm_status hop_launch_dispatch(tm_lattice lat, const HopArgs& a, cudaStream_t s) 
       return hop_launch_f32(lat, a, s);
     case TM_F16:
       return hop_launch_f16(lat, a, s);
+    case TM_DF64:
+      return hop_launch_df64(lat, a, s);
     default:
       return set_error(TM_ERR_ARG, "precision %d", a.prec);
   }
@@ -403,7 +413,7 @@ tm_status tm_lattice_destroy(tm_lattice lat) {
   if (!lat) return TM_OK;
   cudaDeviceSynchronize();
   cudaFree(lat->U_canon);
-  for (int p = 0; p < 3; ++p)
+  for (int p = 0; p < 4; ++p)
     for (int l = 0; l < 3; ++l) cudaFree(lat->links[p][l]);
   for (int k = 0; k < 32; ++k) cudaFree(lat->ws[k]);
   cudaFree(lat->partials);
@@ -430,7 +440,7 @@ tm_status tm_lattice_set_params(tm_lattice lat, double kappa, double mu) {
 size_t tm_volume(tm_lattice lat) { return lat ? lat->V : 0; }
 
 tm_status tm_set_hop_threads(tm_lattice lat, tm_prec prec, tm_link link, int threads_per_site) {
-  if (!lat || prec < TM_F64 || prec > TM_F16 || (link != 18 && link != 12 && link != 8))
+  if (!lat || prec < TM_F64 || prec > TM_DF64 || (link != 18 && link != 12 && link != 8))
     return set_error(TM_ERR_ARG, "tm_set_hop_threads: bad argument");
   if (threads_per_site != 0 && threads_per_site != 1 && threads_per_site != 2 && threads_per_site != 4)
     return set_error(TM_ERR_ARG, "tm_set_hop_threads: threads_per_site must be 0 (tune), 1, 2 or 4");
@@ -441,19 +451,21 @@ tm_status tm_set_hop_threads(tm_lattice lat, tm_prec prec, tm_link link, int thr
     if (lat->links[prec][li]) return tune_hop(lat, prec, link, nullptr);
     return TM_OK;
   }
+  if (prec == TM_DF64 && threads_per_site != 1)
+    return set_error(TM_ERR_UNSUPPORTED, "tm_set_hop_threads: double-float runs with one thread per site");
   lat->hop_tps_forced[prec][li] = 1;
   lat->hop_tps[prec][li] = threads_per_site;
   return TM_OK;
 }
 
 int tm_get_hop_threads(tm_lattice lat, tm_prec prec, tm_link link) {
-  if (!lat || prec < TM_F64 || prec > TM_F16 || (link != 18 && link != 12 && link != 8)) return 0;
+  if (!lat || prec < TM_F64 || prec > TM_DF64 || (link != 18 && link != 12 && link != 8)) return 0;
   const int v = lat->hop_tps[prec][link_index(link)];
   return v == 0 ? 1 : v;
 }
 
 size_t tm_half_field_bytes(tm_lattice lat, tm_prec prec) {
-  if (!lat || prec < 0 || prec > 2) return 0;
+  if (!lat || prec < 0 || prec > 3) return 0;
   return spinor_bytes_per_site(prec) * lat->h;
 }
 
@@ -495,7 +507,7 @@ tm_status tm_set_gauge(tm_lattice lat, const double* U, void* stream) {
   // accept: replace the canonical copy and drop every derived copy
   cudaFree(lat->U_canon);
   lat->U_canon = tmp;
-  for (int p = 0; p < 3; ++p)
+  for (int p = 0; p < 4; ++p)
     for (int l = 0; l < 3; ++l) {
       cudaFree(lat->links[p][l]);
       lat->links[p][l] = nullptr;

@@ -44,7 +44,7 @@ tm_status tm_apply_hopping_eo(tm_lattice lat, int out_parity, void* out, const v
   if (!lat || !out || !in || nrhs < 1) return set_error(TM_ERR_ARG, "tm_apply_hopping_eo: bad argument");
   if (out_parity != 0 && out_parity != 1)
     return set_error(TM_ERR_ARG, "tm_apply_hopping_eo: out_parity must be 0 or 1");
-  if (prec < TM_F64 || prec > TM_F16) return set_error(TM_ERR_ARG, "tm_apply_hopping_eo: precision %d", (int)prec);
+  if (prec < TM_F64 || prec > TM_DF64) return set_error(TM_ERR_ARG, "tm_apply_hopping_eo: precision %d", (int)prec);
   if (link != TM_LINK18 && link != TM_LINK12 && link != TM_LINK8)
     return set_error(TM_ERR_ARG, "tm_apply_hopping_eo: link format %d", (int)link);
   const size_t fb = tm_half_field_bytes(lat, prec);

@@ -178,7 +178,7 @@ struct Solver {
   cudaStream_t s;
   int f;
   double mut;
-  size_t hb[3];  // half-field bytes per precision
+  size_t hb[4];  // half-field bytes per precision
 };
 
 static tm_status norm2_half(const Solver& S, int prec, const void* x, double* out_host) {
@@ -192,6 +192,8 @@ static tm_status norm2_half(const Solver& S, int prec, const void* x, double* ou
     norm2_kernel<TM_F64><<<nb, BNT, 0, S.s>>>(lat->geom.h, xp, red);
   else if (prec == TM_F32)
     norm2_kernel<TM_F32><<<nb, BNT, 0, S.s>>>(lat->geom.h, xp, red);
+  else if (prec == TM_DF64)
+    norm2_kernel<TM_DF64><<<nb, BNT, 0, S.s>>>(lat->geom.h, xp, red);
   else
     norm2_kernel<TM_F16><<<nb, BNT, 0, S.s>>>(lat->geom.h, xp, red);
   count_launch();
@@ -470,6 +472,21 @@ static tm_status true_residual(const Solver& S, void* r, const void* X, const vo
 // Sloppy stages stop when the iterated ||r|| grows by this factor over its minimum.
 constexpr double SLOPPY_GROWTH = 100.0;
 
+// The same in double-float: X (FP64) is converted to Xd, r = b' - A Xd with the double-float
+// operator (all fields TM_DF64); returns ||r||^2.
+static tm_status true_residual_dd(const Solver& S, void* rd, const void* X, const void* bpd, void* Td, void* Wd,
+                                  void* Xd, double* rr) {
+  tm_status st = convert_half(S.lat, TM_DF64, Xd, TM_F64, X, S.s);
+  if (st != TM_OK) return st;
+  if ((st = cuda_check(cudaMemcpyAsync(rd, bpd, S.hb[TM_DF64], cudaMemcpyDeviceToDevice, S.s), "copy")) != TM_OK)
+    return st;
+  if ((st = normal_apply(S, TM_DF64, 18, Xd, Td, Wd, rd, nullptr)) != TM_OK) return st;
+  if ((st = cuda_check(cudaMemcpyAsync(rr, S.lat->dscalars, sizeof(double), cudaMemcpyDeviceToHost, S.s),
+                       "readback")) != TM_OK)
+    return st;
+  return cuda_check(cudaStreamSynchronize(S.s), "synchronise");
+}
+
 static CGState fresh_state(double rr, double stop2, int max_iter, int iter0, double delta2, double growth = 0.0) {
   CGState c;
   memset(&c, 0, sizeof(c));
@@ -508,8 +525,8 @@ static void trace_update(int k, double rr_true, double bb) {
 // Solves M^f x = b for one canonical full field (device pointers).
 static tm_status solve_one(tm_lattice lat, double* x, const double* b, const tm_cg_params& P, tm_cg_info* info,
                            cudaStream_t s) {
-  Solver S{lat, s, P.flavour, 2.0 * lat->kappa * lat->mu, {0, 0, 0}};
-  for (int p = 0; p < 3; ++p) S.hb[p] = spinor_bytes_per_site(p) * lat->h;
+  Solver S{lat, s, P.flavour, 2.0 * lat->kappa * lat->mu, {0, 0, 0, 0}};
+  for (int p = 0; p < 4; ++p) S.hb[p] = spinor_bytes_per_site(p) * lat->h;
   tm_status st = TM_OK;
   // FP64 fields: 0 b_e, 1 b_o, 2 b', 3 X, 4 R, 5 P, 6 T, 7 W
   void* w[8];
@@ -648,6 +665,17 @@ static tm_status solve_one(tm_lattice lat, double* x, const double* b, const tm_
     // reliable-update loop (also the defect correction of the sqrt(eps) mode)
     const double delta2 = P.delta * P.delta;
     int bad_stages = 0;
+    bool dd_updates = P.update_prec == TM_DF64;
+    void *bpd = nullptr, *Rd = nullptr, *Xd = nullptr, *Td = nullptr, *Wd = nullptr;
+    if (dd_updates) {
+      bpd = workspace(lat, 13, S.hb[TM_DF64], &st);
+      if (st == TM_OK) Rd = workspace(lat, 14, S.hb[TM_DF64], &st);
+      if (st == TM_OK) Xd = workspace(lat, 15, S.hb[TM_DF64], &st);
+      if (st == TM_OK) Td = workspace(lat, 16, S.hb[TM_DF64], &st);
+      if (st == TM_OK) Wd = workspace(lat, 17, S.hb[TM_DF64], &st);
+      if (st == TM_OK) st = convert_half(lat, TM_DF64, bpd, TM_F64, bp, s);
+      if (st != TM_OK) return st;
+    }
     while (!converged && iters < P.max_iter) {
       CGState fin;
       if ((st = run_stage(S, v, fresh_state(rr, stop2, P.max_iter, iters, delta2, SLOPPY_GROWTH), &fin)) != TM_OK)
@@ -668,17 +696,38 @@ static tm_status solve_one(tm_lattice lat, double* x, const double* b, const tm_
         count_launch();
       }
       if ((st = cuda_check(cudaGetLastError(), "accumulate kernel")) != TM_OK) return st;
-      if ((st = true_residual(S, R, X, bp, T, W, &rr_true)) != TM_OK) return st;
+      const void* rsrc = R;
+      int rprec = TM_F64;
+      if (dd_updates) {
+        if ((st = true_residual_dd(S, Rd, X, bpd, Td, Wd, Xd, &rr_true)) != TM_OK) return st;
+        rsrc = Rd;
+        rprec = TM_DF64;
+      } else {
+        if ((st = true_residual(S, R, X, bp, T, W, &rr_true)) != TM_OK) return st;
+      }
       ++updates;
       trace_update(updates, rr_true, bb);
       if (rr_true < stop2) {
-        converged = true;
-        break;
+        if (!dd_updates) {
+          converged = true;
+          break;
+        }
+        // confirm in FP64; if the double-float residual was too optimistic, carry on in FP64
+        if ((st = true_residual(S, R, X, bp, T, W, &rr_true)) != TM_OK) return st;
+        ++updates;
+        trace_update(updates, rr_true, bb);
+        if (rr_true < stop2) {
+          converged = true;
+          break;
+        }
+        dd_updates = false;
+        rsrc = R;
+        rprec = TM_F64;
       }
       if (!(rr_true < 1e300)) return set_error(TM_ERR_NONFINITE, "tm_solve_cg: residual diverged");
-      if ((st = convert_half(lat, TM_F32, rs, TM_F64, R, s)) != TM_OK) return st;
+      if ((st = convert_half(lat, TM_F32, rs, rprec, rsrc, s)) != TM_OK) return st;
       // after a divergent stage the search direction restarts from the true residual
-      if (fin.diverged && (st = convert_half(lat, sp, ps, TM_F64, R, s)) != TM_OK) return st;
+      if (fin.diverged && (st = convert_half(lat, sp, ps, rprec, rsrc, s)) != TM_OK) return st;
       rr = rr_true;
     }
   }
@@ -758,6 +807,7 @@ void tm_cg_params_default(tm_cg_params* p) {
   p->delta = 0.1;
   p->use_x0 = 0;
   p->flavour = 1;
+  p->update_prec = TM_F64;
 }
 
 tm_status tm_solve_cg(tm_lattice lat, double* x, const double* b, int nrhs, const tm_cg_params* params,
@@ -780,6 +830,8 @@ tm_status tm_solve_cg(tm_lattice lat, double* x, const double* b, int nrhs, cons
     if (P.sloppy_link != 18 && P.sloppy_link != 12 && P.sloppy_link != 8)
       return set_error(TM_ERR_ARG, "tm_solve_cg: sloppy link format %d", P.sloppy_link);
     if (!(P.delta > 0.0 && P.delta < 1.0)) return set_error(TM_ERR_ARG, "tm_solve_cg: delta must be in (0, 1)");
+    if (P.update_prec != TM_F64 && P.update_prec != TM_DF64)
+      return set_error(TM_ERR_ARG, "tm_solve_cg: update_prec must be TM_F64 or TM_DF64");
   }
   const size_t fbytes = lat->V * 24 * sizeof(double);
   if (x == b) return set_error(TM_ERR_ARG, "tm_solve_cg: x and b must differ");
@@ -802,7 +854,7 @@ tm_status tm_solve_cg(tm_lattice lat, double* x, const double* b, int nrhs, cons
     tm_cg_info one{};
     if (P.use_x0) {
       // defect correction from the initial guess: x = x0 + M^-1 (b - M x0)
-      double* d = static_cast<double*>(workspace(lat, 13, 2 * fbytes, &st));
+      double* d = static_cast<double*>(workspace(lat, WS_X0, 2 * fbytes, &st));
       if (st != TM_OK) return st;
       double* r0 = d;
       double* delta = d + lat->V * 24;

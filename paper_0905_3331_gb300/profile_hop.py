@@ -33,7 +33,7 @@ def main():
     ap.add_argument("--tps", type=int, default=0, help="threads per site 1/2/4 (0: autotuned)")
     args = ap.parse_args()
     libbuild.build()
-    prec = {"f64": 0, "f32": 1, "f16": 2}[args.form.split(":")[0]]
+    prec = {"f64": 0, "f32": 1, "f16": 2, "df64": 3}[args.form.split(":")[0]]
     nreal = int(args.form.split(":")[1])
     w = inputs.WORKLOADS[args.workload]
     dev = torch.device("cuda:0")
@@ -62,8 +62,8 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1) / 1e3)
-    spinor = {0: 192, 1: 96, 2: 52}[prec]
-    elem = {0: 8, 1: 4, 2: 2}[prec]
+    spinor = {0: 192, 1: 96, 2: 52, 3: 192}[prec]
+    elem = {0: 8, 1: 4, 2: 2, 3: 8}[prec]
     per_site = args.nrhs * 2 * spinor + 8 * nreal * elem
     t = statistics.mean(times)
     print(json.dumps({"workload": w.name, "form": args.form, "nrhs": args.nrhs, "h": h,

@@ -20,7 +20,7 @@ import numpy as np
 
 from . import build as _build
 
-F64, F32, F16 = 0, 1, 2
+F64, F32, F16, DF64 = 0, 1, 2, 3
 LINK18, LINK12, LINK8 = 18, 12, 8
 CG_FP64, CG_SQRT_EPS, CG_RELIABLE = 0, 1, 2
 
@@ -42,7 +42,8 @@ class TMError(RuntimeError):
 class CGParams(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("mode", ctypes.c_int),
                 ("sloppy_prec", ctypes.c_int), ("sloppy_link", ctypes.c_int),
-                ("delta", ctypes.c_double), ("use_x0", ctypes.c_int), ("flavour", ctypes.c_int)]
+                ("delta", ctypes.c_double), ("use_x0", ctypes.c_int), ("flavour", ctypes.c_int),
+                ("update_prec", ctypes.c_int)]
 
 
 class CGInfo(ctypes.Structure):
@@ -229,9 +230,10 @@ class Lattice:
 
     def solve_cg(self, x, b, nrhs: int = 1, tol: float = 1e-10, max_iter: int = 100000,
                  mode: int = CG_FP64, sloppy_prec: int = F32, sloppy_link: int = LINK12,
-                 delta: float = 0.1, use_x0: bool = False, flavour: int = 1, stream=None,
-                 check: bool = True) -> SolveInfo:
-        p = CGParams(tol, max_iter, mode, sloppy_prec, sloppy_link, delta, int(use_x0), flavour)
+                 delta: float = 0.1, use_x0: bool = False, flavour: int = 1,
+                 update_prec: int = F64, stream=None, check: bool = True) -> SolveInfo:
+        p = CGParams(tol, max_iter, mode, sloppy_prec, sloppy_link, delta, int(use_x0), flavour,
+                     update_prec)
         info = CGInfo()
         st = load().tm_solve_cg(self._h, _addr(x), _addr(b), nrhs, ctypes.byref(p),
                                 ctypes.byref(info), _stream(stream))

@@ -63,7 +63,7 @@ def test_cg_params_defaults(lib):
     p = tm.CGParams()
     lib.tm_cg_params_default(ctypes.byref(p))
     assert (p.tol, p.max_iter, p.mode, p.sloppy_prec, p.sloppy_link, p.delta, p.use_x0,
-            p.flavour) == (1e-10, 100000, 0, 1, 12, 0.1, 0, 1)
+            p.flavour, p.update_prec) == (1e-10, 100000, 0, 1, 12, 0.1, 0, 1, 0)
 
 
 def test_launch_counter(lib):

@@ -8,6 +8,7 @@ Tolerances (relative 2-norm error against the FP64 oracle on the same FP64 input
                                                   6e-8 plus ~100 accumulated FP32 ops)
   FP32 storage, 8-real links ........... 1e-5
   FP16 storage + FP32 norm ............. 2e-3    (11-bit mantissa: 4.9e-4 per stored value)
+  double-float (FP32 pair), 18-real .... 1e-13   (about 48 significant bits per operation)
 Sizes run from 2^4 (h = 8; the +mu and -mu neighbours coincide) through ragged
 tails (h = 432, not a multiple of the 128-thread block) to the full 16^3 x 32
 lattice; the 32^3 x 64 and 48^3 x 96 lattices are checked on sampled sites.
@@ -16,7 +17,7 @@ import numpy as np
 import pytest
 
 import oracle
-from paper_0905_3331_gb300 import F16, F32, F64, Lattice, TMError, inputs
+from paper_0905_3331_gb300 import DF64, F16, F32, F64, Lattice, TMError, inputs
 
 from _util import from_half, lex_of_half, rel, to_half
 
@@ -25,7 +26,7 @@ pytestmark = pytest.mark.gpu
 
 TOL = {(F64, 18): 1e-13, (F64, 12): 1e-13, (F64, 8): 1e-12,
        (F32, 18): 1e-6, (F32, 12): 1e-6, (F32, 8): 1e-5,
-       (F16, 18): 2e-3, (F16, 12): 2e-3, (F16, 8): 2e-3}
+       (F16, 18): 2e-3, (F16, 12): 2e-3, (F16, 8): 2e-3, (DF64, 18): 1e-13}
 
 SIZES = [(2, 2), (4, 4), (4, 6), (8, 4), (32, 16)]
 
@@ -109,7 +110,7 @@ def test_pack_unpack_round_trip():
     T, L = 4, 6
     lat, _ = make(T, L)
     src = to_half(inputs.gaussian_spinor(T, L, 9), 0)
-    for prec, tol in ((F64, 0.0), (F32, 6e-8), (F16, 5e-4)):
+    for prec, tol in ((F64, 0.0), (F32, 6e-8), (F16, 5e-4), (DF64, 1e-14)):
         buf = torch.empty(lat.half_field_bytes(prec), dtype=torch.uint8, device=dev())
         lat.pack_half(prec, buf, torch.from_numpy(src).to(dev()))
         back = torch.empty(src.shape, dtype=torch.complex128, device=dev())
@@ -269,4 +270,19 @@ def test_hopping_each_threads_per_site(tps, T, L, prec, link):
     out = torch.empty(psi.shape, dtype=torch.complex128, device=dev())
     lat.apply_D(out, torch.from_numpy(psi).to(dev()))
     assert rel(out.cpu().numpy(), oracle.apply_M(olat, U, psi, lat.kappa, lat.mu)) < 1e-13
+    lat.close()
+
+
+def test_double_float_link_formats():
+    """Double-float storage is built with 18-real links only; the others are refused."""
+    lat, _ = make(4, 4)
+    buf = torch.zeros(lat.half_field_bytes(DF64), dtype=torch.uint8, device=dev())
+    out = torch.zeros_like(buf)
+    lat.apply_hopping_eo(0, out, buf, DF64, 18)
+    for link in (12, 8):
+        with pytest.raises(TMError) as e:
+            lat.apply_hopping_eo(0, out, buf, DF64, link)
+        assert e.value.status_name == "TM_ERR_UNSUPPORTED"
+    with pytest.raises(TMError):
+        lat.set_hop_threads(DF64, 18, 2)
     lat.close()

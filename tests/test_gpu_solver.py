@@ -9,8 +9,8 @@ import numpy as np
 import pytest
 
 import oracle
-from paper_0905_3331_gb300 import (CG_FP64, CG_RELIABLE, CG_SQRT_EPS, F16, F32, LINK8, LINK12,
-                                   LINK18, Lattice, TMError, inputs)
+from paper_0905_3331_gb300 import (CG_FP64, CG_RELIABLE, CG_SQRT_EPS, DF64, F16, F32, F64, LINK8,
+                                   LINK12, LINK18, Lattice, TMError, inputs)
 
 from _util import rel
 
@@ -24,6 +24,8 @@ MODES = [
     ("reliable_f32_12", dict(mode=CG_RELIABLE, sloppy_prec=F32, sloppy_link=LINK12)),
     ("reliable_f16_12", dict(mode=CG_RELIABLE, sloppy_prec=F16, sloppy_link=LINK12)),
     ("reliable_f16_8", dict(mode=CG_RELIABLE, sloppy_prec=F16, sloppy_link=LINK8)),
+    ("reliable_f32_12_df64_updates", dict(mode=CG_RELIABLE, sloppy_prec=F32, sloppy_link=LINK12,
+                                          update_prec=DF64)),
 ]
 
 
@@ -56,7 +58,7 @@ def test_solve_4x4x4x4(name, kw):
     lat.close()
 
 
-@pytest.mark.parametrize("name,kw", [MODES[0], MODES[3], MODES[4]])
+@pytest.mark.parametrize("name,kw", [MODES[0], MODES[3], MODES[4], MODES[6]])
 def test_solve_16x16x16x32(name, kw):
     """The 16^3 x 32 workload (eps 0.5, kappa 0.1632, mu 0.004), Gaussian source seed 2."""
     w = inputs.WORKLOADS["16^3x32"]
@@ -146,7 +148,8 @@ def test_edge_cases():
     assert e.value.status_name == "TM_ERR_NONFINITE"
     # bad parameters
     for kw in (dict(tol=0.0), dict(mode=7), dict(mode=CG_RELIABLE, delta=1.5),
-               dict(flavour=3), dict(mode=CG_RELIABLE, sloppy_prec=0)):
+               dict(flavour=3), dict(mode=CG_RELIABLE, sloppy_prec=0),
+               dict(mode=CG_RELIABLE, update_prec=F32)):
         with pytest.raises(TMError) as e:
             lat.solve_cg(x, b, **kw)
         assert e.value.status_name == "TM_ERR_ARG"
