@@ -204,6 +204,32 @@ typedef struct {
 tm_status tm_solve_cg(tm_lattice lat, double *x, const double *b, int nrhs,
                       const tm_cg_params *params, tm_cg_info *info, void *stream);
 
+/* One system of a batched solve: M(f; mu) x = b on the lattice `lat` (its gauge field and
+ * kappa), with this system's own bare twisted mass mu (mu~ = 2 kappa mu). */
+typedef struct {
+  tm_lattice lat;
+  double mu;
+  int flavour;     /* +1 or -1 (0 means +1) */
+  double *x;       /* solution: canonical full field, device memory */
+  const double *b; /* source: canonical full field, device memory */
+} tm_system;
+
+/* Solves many systems together (the paper's inversions of many sources, e.g. the 12 spin-
+ * colour point sources of a propagator, Sec. 4.7.2, or sources on several lattices): the
+ * mixed-precision reliable-update CG of tm_solve_cg (params->mode must be TM_CG_RELIABLE;
+ * FP32 or FP16 sloppy storage; FP64 updates), with the sloppy iterations of every system in
+ * the same kernel launches -- blocks of systems that share a lattice interleaved so each
+ * link is read from HBM once per iteration for all of them -- and each stage (iterations
+ * until every system has reached its reliable-update trigger) one CUDA graph launch.  Every
+ * system keeps its own CG scalars and stops on its own residual; infos[k] (may be NULL)
+ * receives system k's result (seconds = the whole call).  Systems may share lattices and
+ * differ in mu, flavour and source.  Synchronises `stream`.  Allocates its work space
+ * (about 1.7 kB per site per system) for the duration of the call.
+ * Errors: TM_ERR_NOT_CONVERGED (some systems; their x holds the last iterate), TM_ERR_ARG,
+ * TM_ERR_UNSUPPORTED, TM_ERR_NO_GAUGE, TM_ERR_NONFINITE, TM_ERR_CUDA, TM_ERR_OOM. */
+tm_status tm_solve_cg_batch(const tm_system *systems, int nsys, const tm_cg_params *params,
+                            tm_cg_info *infos, void *stream);
+
 /* Fills params with the defaults: tol 1e-10, max_iter 100000, TM_CG_FP64, sloppy
  * TM_F32 / TM_LINK12, delta 0.1, use_x0 0, flavour +1, update_prec TM_F64. */
 void tm_cg_params_default(tm_cg_params *params);

@@ -1,0 +1,565 @@
+// tm_batch.cu -- many systems M_s^f x_s = b_s solved together (tm_solve_cg_batch).
+//
+// Systems may differ in source, twisted mass and lattice (geometry and gauge field).  Every
+// system runs the mixed-precision reliable-update CG of tm_solver.cu, but the sloppy
+// iterations of all systems go through the same kernels: one launch of K1..K4 and of the
+// update covers every system, its blocks mapped to (system, block of sites) by a table, with
+// the blocks of systems that share a lattice interleaved so that each link is fetched from
+// HBM once and served to the other systems from L2.  Each system keeps its own device-side
+// CG state and reductions; a system that reaches its reliable-update trigger (or converges)
+// idles while the others continue.  A stage -- iterations until every system has reached its
+// trigger -- is one CUDA graph launch (a WHILE node over one batched iteration).  Between
+// stages the host performs the FP64 reliable updates of the systems that need them.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "tm_dslash.cuh"
+#include "tm_solver.cuh"
+
+namespace tmq {
+
+// Per-system descriptor (device memory).
+struct BatchSys {
+  Geom g;
+  const char* links;   // sloppy gauge copy of the system's lattice
+  EpiCoef coef[4];     // epilogues of K1..K4 (this system's mu)
+  void* vec[5];        // 0 p, 1 T, 2 W (sloppy storage), 3 r, 4 x increment (FP32)
+  CGState* st;
+  double* partials;    // reduction partials of this system (nblocks entries)
+  unsigned* counters;  // [0] reductions, [1] update kernel
+  int nblocks;         // hopping blocks (HOP_NT sites each)
+  int nblocks_upd;     // update-kernel blocks
+};
+
+struct BatchGlobal {
+  int active;        // systems still iterating in this stage
+  int loops;         // iteration bodies executed
+  int loop_cap;      // hard bound on loops
+  unsigned counter;  // update-kernel blocks arrived
+};
+
+// Same site computation as hop_kernel (one thread per site), the system taken from the table.
+template <int PREC, int NREAL, bool HAS_Y, int MODE>
+__global__ void __launch_bounds__(HOP_NT) hop_batch_kernel(const BatchSys* __restrict__ systems,
+                                                           const int2* __restrict__ map, int in_sel, int y_sel,
+                                                           int out_sel, int k, int out_parity) {
+  typedef typename SpinorFmt<PREC>::real R;
+  typedef SpinorFmt<PREC> F;
+  __shared__ double sh[HOP_NT / 32];
+  const int2 m = map[blockIdx.x];
+  const BatchSys& B = systems[m.x];
+  CGState* st = B.st;
+  if (st->done) return;
+  const Geom g = B.g;
+  const int cb = m.y * HOP_NT + threadIdx.x;
+  const bool active = cb < g.h;
+  cpx<R> acc[12];
+#pragma unroll
+  for (int q = 0; q < 12; ++q) acc[q] = mk<R>(R(0), R(0));
+  if (active) {
+    const SiteCoord c = site_of(g, cb, out_parity);
+    int nb[8];
+    neighbours(g, cb, c, nb);
+    const size_t slab = link_bytes(PREC, NREAL) * (size_t)g.h;
+    const char* lf = B.links + (size_t)(out_parity * 4) * slab;
+    const char* lo = B.links + (size_t)((1 - out_parity) * 4) * slab;
+    hop_part<PREC, NREAL, 1>(acc, g, cb, c, nb, static_cast<const char*>(B.vec[in_sel]), lf, lo, slab, 0);
+  }
+  const EpiCoef coef = B.coef[k];
+  const R cc = (R)coef.c;
+  const cpx<R> Du = mk<R>((R)coef.d_up_re, (R)coef.d_up_im), Dl = mk<R>((R)coef.d_lo_re, (R)coef.d_lo_im);
+  cpx<R> o[12];
+  if (HAS_Y) {
+    const cpx<R> Eu = mk<R>((R)coef.e_up_re, (R)coef.e_up_im), El = mk<R>((R)coef.e_lo_re, (R)coef.e_lo_im);
+    cpx<R> yv[12];
+#pragma unroll
+    for (int q = 0; q < 12; ++q) yv[q] = mk<R>(R(0), R(0));
+    if (active) F::load(B.vec[y_sel], g.h, cb, yv);
+#pragma unroll
+    for (int q = 0; q < 12; ++q) o[q] = ((q < 6) ? Du : Dl) * (cc * acc[q] + ((q < 6) ? Eu : El) * yv[q]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 12; ++q) o[q] = ((q < 6) ? Du : Dl) * (cc * acc[q]);
+  }
+  double nrm = 0.0;
+  void* outp = B.vec[out_sel];
+  if (MODE == 2) {
+    if (active) {
+      const R al = (R)st->alpha;
+      constexpr int PR = ResidPrec<PREC>::value;
+      cpx<R> r[12];
+      SpinorFmt<PR>::load(outp, g.h, cb, r);
+#pragma unroll
+      for (int q = 0; q < 12; ++q) {
+        r[q] = r[q] - al * o[q];
+        nrm += (double)norm2(r[q]);
+      }
+      SpinorFmt<PR>::store(outp, g.h, cb, r);
+    }
+  } else if (active) {
+    if (MODE == 1) {
+#pragma unroll
+      for (int q = 0; q < 12; ++q) nrm += (double)norm2(o[q]);
+    }
+    F::store(outp, g.h, cb, o);
+  }
+  if (MODE >= 1) {
+    const Reduce red{B.partials, B.counters, nullptr, st, MODE == 1 ? FIN_CG_ALPHA : FIN_CG_RR};
+    const double bs = block_sum<HOP_NT>(nrm, sh);
+    grid_reduce<HOP_NT>(red, 0, B.nblocks, m.y, bs, sh);
+  }
+}
+
+// x += alpha p, p = r + beta p per system; the last block of all sets the loop condition.
+template <int PP>
+__global__ void __launch_bounds__(BNT) cg_update_batch_kernel(const BatchSys* __restrict__ systems,
+                                                              const int2* __restrict__ map, BatchGlobal* gl,
+                                                              cudaGraphConditionalHandle cond, int use_cond) {
+  typedef typename SpinorFmt<PP>::real RP;
+  const int2 m = map[blockIdx.x];
+  const BatchSys& B = systems[m.x];
+  CGState& S = *B.st;
+  const int iter = S.iter;
+  const bool work = iter != S.applied;
+  if (work) {
+    const double alpha = S.alpha, beta = S.beta;
+    const int h = B.g.h;
+    char* x = static_cast<char*>(B.vec[4]);
+    char* p = static_cast<char*>(B.vec[0]);
+    const char* r = static_cast<const char*>(B.vec[3]);
+    for (int i = m.y * BNT + threadIdx.x; i < h; i += B.nblocks_upd * BNT) {
+      cpx<float> xv[12], rv[12];
+      cpx<RP> pv[12];
+      SpinorFmt<TM_F32>::load(x, h, i, xv);
+      SpinorFmt<PP>::load(p, h, i, pv);
+      SpinorFmt<TM_F32>::load(r, h, i, rv);
+#pragma unroll
+      for (int q = 0; q < 12; ++q) {
+        xv[q] = xv[q] + (float)alpha * mk<float>((float)pv[q].re, (float)pv[q].im);
+        pv[q] = rv[q] + (RP)beta * pv[q];
+      }
+      SpinorFmt<TM_F32>::store(x, h, i, xv);
+      SpinorFmt<PP>::store(p, h, i, pv);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (work) {
+      __threadfence();
+      const unsigned prev = atomicAdd(B.counters + 1, 1u);
+      if (prev == (unsigned)B.nblocks_upd - 1) {
+        S.applied = iter;
+        B.counters[1] = 0u;
+        if (S.done && !S.retired) {
+          S.retired = 1;
+          atomicSub(&gl->active, 1);
+        }
+      }
+    } else if (m.y == 0 && S.done && !S.retired) {  // stopped without a step to apply
+      S.retired = 1;
+      atomicSub(&gl->active, 1);
+    }
+    __threadfence();
+    const unsigned g = atomicAdd(&gl->counter, 1u);
+    if (g == gridDim.x - 1) {
+      gl->counter = 0u;
+      gl->loops += 1;
+      const bool again = atomicAdd(&gl->active, 0) > 0 && gl->loops < gl->loop_cap;
+      if (use_cond) cudaGraphSetConditional(cond, again ? 1u : 0u);
+    }
+  }
+}
+
+template <int PREC, int NREAL>
+static tm_status launch_hop_batch(const BatchSys* d_sys, const int2* d_map, int nblocks, int in_sel, int y_sel,
+                                  int out_sel, int k, int parity, int mode, bool has_y, cudaStream_t s) {
+  if (!has_y && mode == 0)
+    hop_batch_kernel<PREC, NREAL, false, 0><<<nblocks, HOP_NT, 0, s>>>(d_sys, d_map, in_sel, y_sel, out_sel, k, parity);
+  else if (has_y && mode == 1)
+    hop_batch_kernel<PREC, NREAL, true, 1><<<nblocks, HOP_NT, 0, s>>>(d_sys, d_map, in_sel, y_sel, out_sel, k, parity);
+  else
+    hop_batch_kernel<PREC, NREAL, true, 2><<<nblocks, HOP_NT, 0, s>>>(d_sys, d_map, in_sel, y_sel, out_sel, k, parity);
+  count_launch();
+  return cuda_check(cudaGetLastError(), "batched hopping kernel");
+}
+
+static tm_status hop_batch(int prec, int nreal, const BatchSys* d_sys, const int2* d_map, int nblocks, int in_sel,
+                           int y_sel, int out_sel, int k, int parity, int mode, bool has_y, cudaStream_t s) {
+#define TM_B(P, N) \
+  if (prec == P && nreal == N) return launch_hop_batch<P, N>(d_sys, d_map, nblocks, in_sel, y_sel, out_sel, k, parity, mode, has_y, s);
+  TM_B(TM_F32, 18) TM_B(TM_F32, 12) TM_B(TM_F32, 8) TM_B(TM_F16, 18) TM_B(TM_F16, 12) TM_B(TM_F16, 8)
+#undef TM_B
+  return set_error(TM_ERR_UNSUPPORTED, "batched solve: sloppy form not supported");
+}
+
+// One batched CG iteration: K1..K4 of every system, then the update.
+static tm_status batch_iteration(int prec, int nreal, const BatchSys* d_sys, const int2* d_hmap, int nh,
+                                 const int2* d_umap, int nu, BatchGlobal* d_gl, cudaGraphConditionalHandle cond,
+                                 int use_cond, cudaStream_t s) {
+  tm_status st;
+  // K1: T = (M_ee^-f)^-1 H_eo p ; K2: W = Qhat^-f p, <p,Ap> ; K3: T = (M_ee^f)^-1 H_eo W ; K4: r -= alpha Qhat^f W
+  if ((st = hop_batch(prec, nreal, d_sys, d_hmap, nh, 0, 0, 1, 0, 0, 0, false, s)) != TM_OK) return st;
+  if ((st = hop_batch(prec, nreal, d_sys, d_hmap, nh, 1, 0, 2, 1, 1, 1, true, s)) != TM_OK) return st;
+  if ((st = hop_batch(prec, nreal, d_sys, d_hmap, nh, 2, 0, 1, 2, 0, 0, false, s)) != TM_OK) return st;
+  if ((st = hop_batch(prec, nreal, d_sys, d_hmap, nh, 1, 2, 3, 3, 1, 2, true, s)) != TM_OK) return st;
+  if (prec == TM_F32)
+    cg_update_batch_kernel<TM_F32><<<nu, BNT, 0, s>>>(d_sys, d_umap, d_gl, cond, use_cond);
+  else
+    cg_update_batch_kernel<TM_F16><<<nu, BNT, 0, s>>>(d_sys, d_umap, d_gl, cond, use_cond);
+  count_launch();
+  return cuda_check(cudaGetLastError(), "batched update kernel");
+}
+
+namespace {
+
+struct SysWork {
+  Solver S;
+  tm_lattice lat;
+  double mu;
+  double* x;
+  const double* b;
+  // FP64 half fields
+  void *be, *bo, *bp, *X;
+  // FP32 and sloppy
+  void *rs, *xs, *ps, *Ts, *Ws;
+  double bb, bfull, rr, stop2;
+  int iters, updates;
+  bool converged, failed;
+  int lat_index;
+};
+
+struct LatWork {
+  tm_lattice lat;
+  void *R, *Pv, *T, *W;  // FP64 scratch for reliable updates and the final check
+};
+
+}  // namespace
+
+}  // namespace tmq
+
+using namespace tmq;
+
+extern "C" tm_status tm_solve_cg_batch(const tm_system* systems, int nsys, const tm_cg_params* params,
+                                       tm_cg_info* infos, void* stream) {
+  const auto t0 = std::chrono::steady_clock::now();
+  if (!systems || nsys < 1) return set_error(TM_ERR_ARG, "tm_solve_cg_batch: no systems");
+  tm_cg_params P;
+  if (params)
+    P = *params;
+  else
+    tm_cg_params_default(&P);
+  if (P.mode != TM_CG_RELIABLE) return set_error(TM_ERR_UNSUPPORTED, "tm_solve_cg_batch: mode must be TM_CG_RELIABLE");
+  if (P.sloppy_prec != TM_F32 && P.sloppy_prec != TM_F16)
+    return set_error(TM_ERR_ARG, "tm_solve_cg_batch: sloppy precision must be TM_F32 or TM_F16");
+  if (P.sloppy_link != 18 && P.sloppy_link != 12 && P.sloppy_link != 8)
+    return set_error(TM_ERR_ARG, "tm_solve_cg_batch: sloppy link format %d", P.sloppy_link);
+  if (!(P.tol > 0.0) || P.max_iter < 1 || !(P.delta > 0.0 && P.delta < 1.0))
+    return set_error(TM_ERR_ARG, "tm_solve_cg_batch: tol > 0, max_iter >= 1, 0 < delta < 1");
+  if (P.use_x0) return set_error(TM_ERR_UNSUPPORTED, "tm_solve_cg_batch: initial guesses are not supported");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int sp = P.sloppy_prec, sl = P.sloppy_link;
+
+  // ---- validate systems, group by lattice
+  std::vector<LatWork> lats;
+  std::vector<SysWork> W(nsys);
+  for (int k = 0; k < nsys; ++k) {
+    const tm_system& y = systems[k];
+    if (!y.lat || !y.x || !y.b) return set_error(TM_ERR_ARG, "tm_solve_cg_batch: system %d has a NULL member", k);
+    if (!y.lat->has_gauge) return set_error(TM_ERR_NO_GAUGE, "tm_solve_cg_batch: system %d has no gauge field", k);
+    const int f = y.flavour == 0 ? 1 : y.flavour;
+    if (f != 1 && f != -1) return set_error(TM_ERR_ARG, "tm_solve_cg_batch: system %d flavour", k);
+    if (!std::isfinite(y.mu)) return set_error(TM_ERR_ARG, "tm_solve_cg_batch: system %d mu", k);
+    if (!is_device_pointer(y.x) || !is_device_pointer(y.b))
+      return set_error(TM_ERR_ARG, "tm_solve_cg_batch: system %d: x and b must be device memory", k);
+    int li = -1;
+    for (size_t q = 0; q < lats.size(); ++q)
+      if (lats[q].lat == y.lat) li = (int)q;
+    if (li < 0) {
+      lats.push_back(LatWork{y.lat, nullptr, nullptr, nullptr, nullptr});
+      li = (int)lats.size() - 1;
+    }
+    SysWork& w = W[k];
+    memset(&w, 0, sizeof(w));
+    w.lat = y.lat;
+    w.mu = y.mu;
+    w.x = y.x;
+    w.b = y.b;
+    w.lat_index = li;
+    w.S = Solver{y.lat, s, f, 2.0 * y.lat->kappa * y.mu, {0, 0, 0, 0}};
+    for (int q = 0; q < 4; ++q) w.S.hb[q] = spinor_bytes_per_site(q) * y.lat->h;
+  }
+  tm_status st = TM_OK;
+  for (auto& L : lats) {
+    if ((st = ensure_links(L.lat, sp, sl, s)) != TM_OK) return st;
+    if ((st = ensure_links(L.lat, TM_F64, 18, s)) != TM_OK) return st;
+  }
+
+  // ---- one allocation for every work field
+  size_t total = 0;
+  auto add = [&](size_t bytes) {
+    const size_t off = total;
+    total += (bytes + 255) / 256 * 256;
+    return off;
+  };
+  std::vector<size_t> offs;
+  for (auto& L : lats)
+    for (int q = 0; q < 4; ++q) offs.push_back(add(spinor_bytes_per_site(TM_F64) * L.lat->h));
+  for (auto& w : W) {
+    const size_t h = w.lat->h;
+    for (int q = 0; q < 4; ++q) offs.push_back(add(192 * h));
+    for (int q = 0; q < 2; ++q) offs.push_back(add(96 * h));
+    for (int q = 0; q < 3; ++q) offs.push_back(add(spinor_bytes_per_site(sp) * h));
+  }
+  // device tables
+  int nh = 0, nu = 0;
+  for (auto& w : W) {
+    nh += (int)hop_grid_blocks(w.lat->h, 1);
+    nu += (int)blas_blocks(w.lat->geom.h);
+  }
+  const size_t off_sys = add(sizeof(BatchSys) * nsys);
+  const size_t off_hmap = add(sizeof(int2) * nh);
+  const size_t off_umap = add(sizeof(int2) * nu);
+  const size_t off_state = add(sizeof(CGState) * nsys);
+  const size_t off_gl = add(sizeof(BatchGlobal));
+  const size_t off_part = add(sizeof(double) * nh);
+  const size_t off_ctr = add(sizeof(unsigned) * 2 * nsys);
+  char* base = nullptr;
+  if ((st = cuda_check(cudaMalloc(&base, total), "tm_solve_cg_batch: work space")) != TM_OK) return st;
+  std::vector<BatchSys> hsys(nsys);
+  std::vector<CGState> hst(nsys);
+  BatchGlobal hgl{};
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cs = nullptr;
+  tm_status result = TM_OK;
+  {
+    size_t oi = 0;
+    for (auto& L : lats) {
+      L.R = base + offs[oi++];
+      L.Pv = base + offs[oi++];
+      L.T = base + offs[oi++];
+      L.W = base + offs[oi++];
+    }
+    for (auto& w : W) {
+      w.be = base + offs[oi++];
+      w.bo = base + offs[oi++];
+      w.bp = base + offs[oi++];
+      w.X = base + offs[oi++];
+      w.rs = base + offs[oi++];
+      w.xs = base + offs[oi++];
+      w.ps = base + offs[oi++];
+      w.Ts = base + offs[oi++];
+      w.Ws = base + offs[oi++];
+    }
+  }
+  BatchSys* d_sys = reinterpret_cast<BatchSys*>(base + off_sys);
+  int2* d_hmap = reinterpret_cast<int2*>(base + off_hmap);
+  int2* d_umap = reinterpret_cast<int2*>(base + off_umap);
+  CGState* d_st = reinterpret_cast<CGState*>(base + off_state);
+  BatchGlobal* d_gl = reinterpret_cast<BatchGlobal*>(base + off_gl);
+  double* d_part = reinterpret_cast<double*>(base + off_part);
+  unsigned* d_ctr = reinterpret_cast<unsigned*>(base + off_ctr);
+
+  do {
+    // ---- per system: source preparation (FP64), initial vectors
+    for (int k = 0; k < nsys && st == TM_OK; ++k) {
+      SysWork& w = W[k];
+      LatWork& L = lats[w.lat_index];
+      st = prepare_source(w.S, w.b, w.be, w.bo, w.bp, L.T, &w.bb, &w.bfull);
+      if (st != TM_OK) break;
+      if (!std::isfinite(w.bb) || !std::isfinite(w.bfull)) {
+        st = set_error(TM_ERR_NONFINITE, "tm_solve_cg_batch: system %d has a non-finite source", k);
+        break;
+      }
+      w.stop2 = P.tol * P.tol * w.bb;
+      w.rr = w.bb;
+      st = cuda_check(cudaMemsetAsync(w.X, 0, w.S.hb[TM_F64], s), "memset");
+      if (st == TM_OK) st = cuda_check(cudaMemsetAsync(w.xs, 0, w.S.hb[TM_F32], s), "memset");
+      if (st == TM_OK) st = convert_half(w.lat, TM_F32, w.rs, TM_F64, w.bp, s);
+      if (st == TM_OK) st = convert_half(w.lat, sp, w.ps, TM_F64, w.bp, s);
+      if (w.bfull == 0.0) w.converged = true;
+    }
+    if (st != TM_OK) break;
+    // ---- descriptor tables; blocks of systems on the same lattice interleaved site-block by site-block
+    {
+      std::vector<int2> hmap, umap;
+      int pfirst = 0;
+      std::vector<int> first(nsys);
+      for (int k = 0; k < nsys; ++k) {
+        first[k] = pfirst;
+        pfirst += (int)hop_grid_blocks(W[k].lat->h, 1);
+      }
+      for (size_t li = 0; li < lats.size(); ++li) {
+        const int nbl = (int)hop_grid_blocks(lats[li].lat->h, 1);
+        for (int blk = 0; blk < nbl; ++blk)
+          for (int k = 0; k < nsys; ++k)
+            if (W[k].lat_index == (int)li) hmap.push_back(make_int2(k, blk));
+        const int nub = (int)blas_blocks(lats[li].lat->geom.h);
+        for (int blk = 0; blk < nub; ++blk)
+          for (int k = 0; k < nsys; ++k)
+            if (W[k].lat_index == (int)li) umap.push_back(make_int2(k, blk));
+      }
+      for (int k = 0; k < nsys; ++k) {
+        SysWork& w = W[k];
+        BatchSys& B = hsys[k];
+        memset(&B, 0, sizeof(B));
+        B.g = w.lat->geom;
+        B.links = static_cast<const char*>(w.lat->links[sp][link_index(sl)]);
+        B.coef[0] = epi_mdiag_inv_hop(w.S.mut, -w.S.f);
+        B.coef[1] = epi_schur_q(w.lat->kappa, w.S.mut, -w.S.f);
+        B.coef[2] = epi_mdiag_inv_hop(w.S.mut, w.S.f);
+        B.coef[3] = epi_schur_q(w.lat->kappa, w.S.mut, w.S.f);
+        B.vec[0] = w.ps;
+        B.vec[1] = w.Ts;
+        B.vec[2] = w.Ws;
+        B.vec[3] = w.rs;
+        B.vec[4] = w.xs;
+        B.st = d_st + k;
+        B.partials = d_part + first[k];
+        B.counters = d_ctr + 2 * k;
+        B.nblocks = (int)hop_grid_blocks(w.lat->h, 1);
+        B.nblocks_upd = (int)blas_blocks(w.lat->geom.h);
+      }
+      st = cuda_check(cudaMemcpyAsync(d_sys, hsys.data(), sizeof(BatchSys) * nsys, cudaMemcpyHostToDevice, s), "table");
+      if (st == TM_OK)
+        st = cuda_check(cudaMemcpyAsync(d_hmap, hmap.data(), sizeof(int2) * nh, cudaMemcpyHostToDevice, s), "table");
+      if (st == TM_OK)
+        st = cuda_check(cudaMemcpyAsync(d_umap, umap.data(), sizeof(int2) * nu, cudaMemcpyHostToDevice, s), "table");
+      if (st == TM_OK) st = cuda_check(cudaMemsetAsync(d_ctr, 0, sizeof(unsigned) * 2 * nsys, s), "memset");
+      if (st == TM_OK) st = cuda_check(cudaStreamSynchronize(s), "tables");
+    }
+    if (st != TM_OK) break;
+    // ---- the stage graph: WHILE (any system active) { one batched iteration }
+    {
+      cudaGraphConditionalHandle cond;
+      cudaGraphNode_t node;
+      cudaGraphNodeParams cp = {};
+      const unsigned long long before = tm_launch_count();
+      st = cuda_check(cudaGraphCreate(&graph, 0), "cudaGraphCreate");
+      if (st == TM_OK)
+        st = cuda_check(cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault), "conditional");
+      if (st == TM_OK) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = cond;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        st = cuda_check(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp), "conditional node");
+      }
+      if (st == TM_OK) st = cuda_check(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream");
+      if (st == TM_OK) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        st = cuda_check(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal),
+                        "begin capture");
+        if (st == TM_OK) {
+          tm_status st1 = batch_iteration(sp, sl, d_sys, d_hmap, nh, d_umap, nu, d_gl, cond, 1, cs);
+          cudaGraph_t captured = nullptr;
+          tm_status st2 = cuda_check(cudaStreamEndCapture(cs, &captured), "end capture");
+          st = st1 != TM_OK ? st1 : st2;
+        }
+      }
+      if (st == TM_OK) st = cuda_check(cudaGraphInstantiate(&exec, graph, 0), "graph instantiate");
+      tm_reset_launch_count();
+      count_launch((unsigned)before);
+    }
+    if (st != TM_OK) break;
+    // ---- stages
+    const double delta2 = P.delta * P.delta;
+    for (;;) {
+      int active = 0, cap = 0;
+      for (int k = 0; k < nsys; ++k) {
+        SysWork& w = W[k];
+        const bool run = !w.converged && !w.failed && w.iters < P.max_iter;
+        hst[k] = fresh_state(w.rr, w.stop2, P.max_iter, w.iters, delta2, SLOPPY_GROWTH);
+        if (!run) {
+          hst[k].done = 1;
+          hst[k].retired = 1;
+        } else {
+          ++active;
+          cap = std::max(cap, P.max_iter - w.iters + 2);
+        }
+      }
+      if (active == 0) break;
+      hgl = BatchGlobal{active, 0, cap, 0u};
+      st = cuda_check(cudaMemcpyAsync(d_st, hst.data(), sizeof(CGState) * nsys, cudaMemcpyHostToDevice, s), "state");
+      if (st == TM_OK) st = cuda_check(cudaMemcpyAsync(d_gl, &hgl, sizeof(hgl), cudaMemcpyHostToDevice, s), "state");
+      if (st == TM_OK) st = cuda_check(cudaGraphLaunch(exec, s), "graph launch");
+      if (st == TM_OK)
+        st = cuda_check(cudaMemcpyAsync(hst.data(), d_st, sizeof(CGState) * nsys, cudaMemcpyDeviceToHost, s), "state");
+      if (st == TM_OK) st = cuda_check(cudaMemcpyAsync(&hgl, d_gl, sizeof(hgl), cudaMemcpyDeviceToHost, s), "state");
+      if (st == TM_OK) st = cuda_check(cudaStreamSynchronize(s), "batched stage");
+      if (st != TM_OK) break;
+      count_launch(5u * (unsigned)hgl.loops);
+      // ---- reliable updates (FP64) of every system that stopped
+      for (int k = 0; k < nsys && st == TM_OK; ++k) {
+        SysWork& w = W[k];
+        if (w.converged || w.failed || w.iters >= P.max_iter) continue;
+        const CGState& c = hst[k];
+        if (!c.done) {  // the loop bound ended the stage first
+          w.iters = c.iter;
+          continue;
+        }
+        LatWork& L = lats[w.lat_index];
+        if (c.nonfinite) {
+          st = cuda_check(cudaMemsetAsync(w.xs, 0, w.S.hb[TM_F32], s), "memset");
+          w.failed = (++w.updates > 1000);
+        } else {
+          if (c.iter == w.iters) {  // breakdown without progress
+            w.failed = true;
+            continue;
+          }
+          st = launch_accumulate(w.S, w.X, w.xs);
+        }
+        w.iters = c.iter;
+        double rr_true = 0.0;
+        if (st == TM_OK) st = true_residual(w.S, L.R, w.X, w.bp, L.T, L.W, &rr_true);
+        if (st != TM_OK) break;
+        ++w.updates;
+        if (rr_true < w.stop2) {
+          w.converged = true;
+          w.rr = rr_true;
+          continue;
+        }
+        if (!(rr_true < 1e300)) {
+          w.failed = true;
+          continue;
+        }
+        st = convert_half(w.lat, TM_F32, w.rs, TM_F64, L.R, s);
+        if (st == TM_OK && (c.diverged || c.nonfinite)) st = convert_half(w.lat, sp, w.ps, TM_F64, L.R, s);
+        w.rr = rr_true;
+      }
+      if (st != TM_OK) break;
+    }
+    if (st != TM_OK) break;
+    // ---- reconstruction and FP64 check per system
+    for (int k = 0; k < nsys && st == TM_OK; ++k) {
+      SysWork& w = W[k];
+      LatWork& L = lats[w.lat_index];
+      tm_cg_info info{};
+      info.iters = w.iters;
+      info.reliable_updates = w.updates;
+      info.schur_rel_residual = w.bb > 0.0 ? std::sqrt(w.rr / w.bb) : 0.0;
+      if (w.bfull == 0.0) {
+        st = cuda_check(cudaMemsetAsync(w.x, 0, w.lat->V * 24 * sizeof(double), s), "memset");
+      } else {
+        st = reconstruct_check(w.S, w.X, w.be, w.bo, w.bfull, w.x, L.T, L.W, L.R, L.Pv, &info.true_rel_residual);
+      }
+      info.status = w.converged ? TM_OK : TM_ERR_NOT_CONVERGED;
+      if (!w.converged) result = TM_ERR_NOT_CONVERGED;
+      if (infos) infos[k] = info;
+    }
+    if (st == TM_OK) st = cuda_check(cudaStreamSynchronize(s), "synchronise");
+  } while (false);
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  if (cs) cudaStreamDestroy(cs);
+  cudaFree(base);
+  if (st != TM_OK) return st;
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (infos)
+    for (int k = 0; k < nsys; ++k) infos[k].seconds = secs;
+  if (result != TM_OK) return set_error(result, "tm_solve_cg_batch: some systems did not converge");
+  return TM_OK;
+}

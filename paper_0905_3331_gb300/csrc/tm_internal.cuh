@@ -729,6 +729,8 @@ struct CGState {
   int diverged;     // the stage ended because the iterated residual grew (restart p)
   int loops;        // graph loop: iteration bodies executed in this stage
   int loop_cap;     // graph loop: hard bound on loops (the loop always ends)
+  int retired;      // batched solves: this system no longer counts as active in the stage
+  int pad;
 };
 
 // What the last block does with the sum of a reduction.

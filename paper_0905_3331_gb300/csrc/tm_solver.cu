@@ -33,13 +33,13 @@
 #include <cstring>
 
 #include "tm_internal.cuh"
+#include "tm_solver.cuh"
 
 namespace tmq {
 
-constexpr int BNT = 256;
 constexpr int CHUNK = 8;  // CG iterations enqueued per host check
 
-static unsigned blas_blocks(int h) {
+unsigned blas_blocks(int h) {
   int nb = (h + BNT - 1) / BNT;
   return (unsigned)(nb < 152 * 8 ? nb : 152 * 8);
 }
@@ -173,15 +173,8 @@ static tm_status full_norm2(tm_lattice lat, const double* x, double* out, cudaSt
   return cuda_check(cudaStreamSynchronize(s), "synchronise");
 }
 
-struct Solver {
-  tm_lattice lat;
-  cudaStream_t s;
-  int f;
-  double mut;
-  size_t hb[4];  // half-field bytes per precision
-};
 
-static tm_status norm2_half(const Solver& S, int prec, const void* x, double* out_host) {
+tm_status norm2_half(const Solver& S, int prec, const void* x, double* out_host) {
   tm_lattice lat = S.lat;
   const unsigned nb = blas_blocks(lat->geom.h);
   tm_status st = ensure_reduce(lat, nb, 4);
@@ -207,8 +200,8 @@ static tm_status norm2_half(const Solver& S, int prec, const void* x, double* ou
 // A = Qhat^f Qhat^{-f} applied to `in` (precision prec, links nreal), result folded into
 // `r` as r -= alpha A in.  With `state` the iteration form is used (skip when done, alpha from
 // the state, FIN_CG_ALPHA / FIN_CG_RR); without it alpha = 1 and ||r||^2 goes to dscalars[0].
-static tm_status normal_apply(const Solver& S, int prec, int nreal, const void* in, void* T, void* W, void* r,
-                              CGState* state) {
+tm_status normal_apply(const Solver& S, int prec, int nreal, const void* in, void* T, void* W, void* r,
+                       CGState* state) {
   tm_lattice lat = S.lat;
   const unsigned nb = hop_grid_blocks(lat->h, 4);  // enough for every threads-per-site choice
   tm_status st = ensure_reduce(lat, nb, 4);
@@ -458,7 +451,7 @@ static tm_status run_stage(const Solver& S, const Stage& v, const CGState& init,
 }
 
 // r = b' - A X in FP64 (r, X, b' FP64 odd fields; T, W FP64 temporaries); returns ||r||^2.
-static tm_status true_residual(const Solver& S, void* r, const void* X, const void* bp, void* T, void* W,
+tm_status true_residual(const Solver& S, void* r, const void* X, const void* bp, void* T, void* W,
                                double* rr) {
   tm_status st = cuda_check(cudaMemcpyAsync(r, bp, S.hb[TM_F64], cudaMemcpyDeviceToDevice, S.s), "copy");
   if (st != TM_OK) return st;
@@ -469,8 +462,6 @@ static tm_status true_residual(const Solver& S, void* r, const void* X, const vo
   return cuda_check(cudaStreamSynchronize(S.s), "synchronise");
 }
 
-// Sloppy stages stop when the iterated ||r|| grows by this factor over its minimum.
-constexpr double SLOPPY_GROWTH = 100.0;
 
 // The same in double-float: X (FP64) is converted to Xd, r = b' - A Xd with the double-float
 // operator (all fields TM_DF64); returns ||r||^2.
@@ -487,7 +478,7 @@ static tm_status true_residual_dd(const Solver& S, void* rd, const void* X, cons
   return cuda_check(cudaStreamSynchronize(S.s), "synchronise");
 }
 
-static CGState fresh_state(double rr, double stop2, int max_iter, int iter0, double delta2, double growth = 0.0) {
+CGState fresh_state(double rr, double stop2, int max_iter, int iter0, double delta2, double growth) {
   CGState c;
   memset(&c, 0, sizeof(c));
   c.rr = rr;
@@ -522,6 +513,104 @@ static void trace_update(int k, double rr_true, double bb) {
   fprintf(stderr, "[tm_solve_cg] reliable update %d: true |r|/|b| %.3e\n", k, std::sqrt(rr_true / bb));
 }
 
+// b' = gamma5 (b_o + kappa H_oe (M_ee^f)^-1 b_e) (App. B.2), with ||b'||^2 and ||b||^2.
+tm_status prepare_source(const Solver& S, const double* b, void* be, void* bo, void* bp, void* T, double* bb,
+                         double* bfull) {
+  tm_lattice lat = S.lat;
+  cudaStream_t s = S.s;
+  tm_status st;
+  if ((st = pack_full_parity(lat, TM_F64, be, b, 0, 0, s)) != TM_OK) return st;
+  if ((st = pack_full_parity(lat, TM_F64, bo, b, 1, 0, s)) != TM_OK) return st;
+  const double n = 1.0 / (1.0 + S.mut * S.mut);
+  if ((st = diag_apply(lat, TM_F64, T, be, 1, n, -S.f * S.mut * n, n, S.f * S.mut * n, s)) != TM_OK) return st;
+  HopArgs a{};
+  a.prec = TM_F64;
+  a.nreal = 18;
+  a.nrhs = 1;
+  a.out_parity = 1;
+  a.in = T;
+  a.y = bo;
+  a.out = bp;
+  a.coef = epi_g5_y_plus(lat->kappa);
+  if ((st = hop_launch(lat, a, s)) != TM_OK) return st;
+  double tmp = 0.0;
+  if ((st = norm2_half(S, TM_F64, bp, bb)) != TM_OK) return st;
+  if ((st = norm2_half(S, TM_F64, be, &tmp)) != TM_OK) return st;
+  *bfull = tmp;
+  if ((st = norm2_half(S, TM_F64, bo, &tmp)) != TM_OK) return st;
+  *bfull += tmp;
+  return TM_OK;
+}
+
+// x_o = Qhat^{-f} X, x_e = (M_ee^f)^-1 (b_e + kappa H_eo x_o) (eq. eo6, App. B.2), written to
+// the canonical field x; then ||b - M x|| / ||b|| in FP64 (R, Pv, T, W are FP64 scratch).
+tm_status reconstruct_check(const Solver& S, const void* X, const void* be, const void* bo, double bfull, double* x,
+                            void* T, void* W, void* R, void* Pv, double* true_rel) {
+  tm_lattice lat = S.lat;
+  cudaStream_t s = S.s;
+  tm_status st;
+  HopArgs a{};
+  a.prec = TM_F64;
+  a.nreal = 18;
+  a.nrhs = 1;
+  a.out_parity = 0;
+  a.in = X;
+  a.out = T;
+  a.coef = epi_mdiag_inv_hop(S.mut, -S.f);
+  if ((st = hop_launch(lat, a, s)) != TM_OK) return st;
+  a.out_parity = 1;
+  a.in = T;
+  a.y = X;
+  a.out = W;  // x_o
+  a.coef = epi_schur_q(lat->kappa, S.mut, -S.f);
+  if ((st = hop_launch(lat, a, s)) != TM_OK) return st;
+  a.out_parity = 0;
+  a.in = W;
+  a.y = be;
+  a.out = T;  // x_e
+  a.coef = epi_scaled_minv(S.mut, S.f, lat->kappa);
+  if ((st = hop_launch(lat, a, s)) != TM_OK) return st;
+  // (M x)_e into R, (M x)_o into Pv
+  a.coef = epi_full_M(lat->kappa, S.mut, S.f);
+  a.out_parity = 0;
+  a.in = W;
+  a.y = T;
+  a.out = R;
+  if ((st = hop_launch(lat, a, s)) != TM_OK) return st;
+  a.out_parity = 1;
+  a.in = T;
+  a.y = W;
+  a.out = Pv;
+  if ((st = hop_launch(lat, a, s)) != TM_OK) return st;
+  double rre = 0.0, rro = 0.0;
+  const unsigned nb = blas_blocks(lat->geom.h);
+  Reduce red{lat->partials, lat->counters, lat->dscalars, nullptr, FIN_STORE};
+  diffnorm2_kernel<<<nb, BNT, 0, s>>>(lat->geom.h, static_cast<const char*>(be), static_cast<const char*>(R), red);
+  count_launch();
+  if ((st = cuda_check(cudaMemcpyAsync(&lat->flag_host[0], lat->dscalars, sizeof(double), cudaMemcpyDeviceToHost, s),
+                       "readback")) != TM_OK)
+    return st;
+  if ((st = cuda_check(cudaStreamSynchronize(s), "synchronise")) != TM_OK) return st;
+  memcpy(&rre, &lat->flag_host[0], sizeof(double));
+  diffnorm2_kernel<<<nb, BNT, 0, s>>>(lat->geom.h, static_cast<const char*>(bo), static_cast<const char*>(Pv), red);
+  count_launch();
+  if ((st = cuda_check(cudaMemcpyAsync(&lat->flag_host[0], lat->dscalars, sizeof(double), cudaMemcpyDeviceToHost, s),
+                       "readback")) != TM_OK)
+    return st;
+  if ((st = cuda_check(cudaStreamSynchronize(s), "synchronise")) != TM_OK) return st;
+  memcpy(&rro, &lat->flag_host[0], sizeof(double));
+  *true_rel = bfull > 0.0 ? std::sqrt((rre + rro) / bfull) : 0.0;
+  if ((st = unpack_full_parity(lat, TM_F64, x, T, 0, 0, s)) != TM_OK) return st;
+  return unpack_full_parity(lat, TM_F64, x, W, 1, 0, s);
+}
+
+tm_status launch_accumulate(const Solver& S, void* X, void* xs) {
+  const unsigned nb = blas_blocks(S.lat->geom.h);
+  accumulate_kernel<TM_F32><<<nb, BNT, 0, S.s>>>(S.lat->geom.h, static_cast<char*>(X), static_cast<char*>(xs));
+  count_launch();
+  return cuda_check(cudaGetLastError(), "accumulate kernel");
+}
+
 // Solves M^f x = b for one canonical full field (device pointers).
 static tm_status solve_one(tm_lattice lat, double* x, const double* b, const tm_cg_params& P, tm_cg_info* info,
                            cudaStream_t s) {
@@ -537,28 +626,8 @@ static tm_status solve_one(tm_lattice lat, double* x, const double* b, const tm_
   void *be = w[0], *bo = w[1], *bp = w[2], *X = w[3], *R = w[4], *Pv = w[5], *T = w[6], *W = w[7];
 
   // ---- source preparation (App. B.2): b' = gamma5 (b_o + kappa H_oe (M_ee^f)^-1 b_e)
-  if ((st = pack_full_parity(lat, TM_F64, be, b, 0, 0, s)) != TM_OK) return st;
-  if ((st = pack_full_parity(lat, TM_F64, bo, b, 1, 0, s)) != TM_OK) return st;
-  {
-    const double n = 1.0 / (1.0 + S.mut * S.mut);
-    if ((st = diag_apply(lat, TM_F64, T, be, 1, n, -S.f * S.mut * n, n, S.f * S.mut * n, s)) != TM_OK) return st;
-    HopArgs a{};
-    a.prec = TM_F64;
-    a.nreal = 18;
-    a.nrhs = 1;
-    a.out_parity = 1;
-    a.in = T;
-    a.y = bo;
-    a.out = bp;
-    a.coef = epi_g5_y_plus(lat->kappa);
-    if ((st = hop_launch(lat, a, s)) != TM_OK) return st;
-  }
-  double bb = 0.0, bfull = 0.0, tmp = 0.0;
-  if ((st = norm2_half(S, TM_F64, bp, &bb)) != TM_OK) return st;
-  if ((st = norm2_half(S, TM_F64, be, &tmp)) != TM_OK) return st;
-  bfull = tmp;
-  if ((st = norm2_half(S, TM_F64, bo, &tmp)) != TM_OK) return st;
-  bfull += tmp;
+  double bb = 0.0, bfull = 0.0;
+  if ((st = prepare_source(S, b, be, bo, bp, T, &bb, &bfull)) != TM_OK) return st;
   if (!std::isfinite(bb) || !std::isfinite(bfull))
     return set_error(TM_ERR_NONFINITE, "tm_solve_cg: the source has non-finite entries");
   info->iters = 0;
@@ -735,55 +804,8 @@ static tm_status solve_one(tm_lattice lat, double* x, const double* b, const tm_
   info->reliable_updates = updates;
   info->schur_rel_residual = std::sqrt(rr_true / bb);
 
-  // ---- reconstruction: x_o = Qhat^{-f} X, x_e = (M_ee^f)^-1 (b_e + kappa H_eo x_o)
-  {
-    HopArgs a{};
-    a.prec = TM_F64;
-    a.nreal = 18;
-    a.nrhs = 1;
-    a.out_parity = 0;
-    a.in = X;
-    a.out = T;
-    a.coef = epi_mdiag_inv_hop(S.mut, -S.f);
-    if ((st = hop_launch(lat, a, s)) != TM_OK) return st;
-    a.out_parity = 1;
-    a.in = T;
-    a.y = X;
-    a.out = W;  // x_o
-    a.coef = epi_schur_q(lat->kappa, S.mut, -S.f);
-    if ((st = hop_launch(lat, a, s)) != TM_OK) return st;
-    a.out_parity = 0;
-    a.in = W;
-    a.y = be;
-    a.out = T;  // x_e
-    a.coef = epi_scaled_minv(S.mut, S.f, lat->kappa);
-    if ((st = hop_launch(lat, a, s)) != TM_OK) return st;
-  }
-  // ---- true residual of the full system: ||b - M x|| / ||b|| (FP64)
-  {
-    double rre = 0.0, rro = 0.0;
-    if ((st = apply_M_halves(lat, R, Pv, T, W, S.f, s)) != TM_OK) return st;  // R = (M x)_e, Pv = (M x)_o
-    const unsigned nb = blas_blocks(lat->geom.h);
-    if ((st = ensure_reduce(lat, nb, 4)) != TM_OK) return st;
-    Reduce red{lat->partials, lat->counters, lat->dscalars, nullptr, FIN_STORE};
-    diffnorm2_kernel<<<nb, BNT, 0, s>>>(lat->geom.h, static_cast<const char*>(be), static_cast<const char*>(R), red);
-    count_launch();
-    if ((st = cuda_check(cudaMemcpyAsync(&lat->flag_host[0], lat->dscalars, sizeof(double), cudaMemcpyDeviceToHost, s),
-                         "readback")) != TM_OK)
-      return st;
-    if ((st = cuda_check(cudaStreamSynchronize(s), "synchronise")) != TM_OK) return st;
-    memcpy(&rre, &lat->flag_host[0], sizeof(double));
-    diffnorm2_kernel<<<nb, BNT, 0, s>>>(lat->geom.h, static_cast<const char*>(bo), static_cast<const char*>(Pv), red);
-    count_launch();
-    if ((st = cuda_check(cudaMemcpyAsync(&lat->flag_host[0], lat->dscalars, sizeof(double), cudaMemcpyDeviceToHost, s),
-                         "readback")) != TM_OK)
-      return st;
-    if ((st = cuda_check(cudaStreamSynchronize(s), "synchronise")) != TM_OK) return st;
-    memcpy(&rro, &lat->flag_host[0], sizeof(double));
-    info->true_rel_residual = std::sqrt((rre + rro) / bfull);
-  }
-  if ((st = unpack_full_parity(lat, TM_F64, x, T, 0, 0, s)) != TM_OK) return st;
-  if ((st = unpack_full_parity(lat, TM_F64, x, W, 1, 0, s)) != TM_OK) return st;
+  // ---- reconstruction and the FP64 residual of the full system
+  if ((st = reconstruct_check(S, X, be, bo, bfull, x, T, W, R, Pv, &info->true_rel_residual)) != TM_OK) return st;
   info->status = converged ? TM_OK : TM_ERR_NOT_CONVERGED;
   if (!converged)
     return set_error(TM_ERR_NOT_CONVERGED, "tm_solve_cg: not converged after %d iterations (||r||/||b|| = %.3e)",

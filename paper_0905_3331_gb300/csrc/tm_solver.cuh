@@ -1,0 +1,34 @@
+// tm_solver.cuh -- pieces of the even/odd CG shared by the single-system and batched solvers.
+#pragma once
+
+#include "tm_internal.cuh"
+
+namespace tmq {
+
+constexpr int BNT = 256;                // threads per block of the vector kernels
+constexpr double SLOPPY_GROWTH = 100.0;  // a sloppy stage ends when ||r|| grows this much over its minimum
+
+// One system's solver context: lattice, stream, flavour sign f and mu~ = 2 kappa mu.
+struct Solver {
+  tm_lattice lat;
+  cudaStream_t s;
+  int f;
+  double mut;
+  size_t hb[4];  // half-field bytes per precision
+};
+
+unsigned blas_blocks(int h);
+tm_status norm2_half(const Solver& S, int prec, const void* x, double* out_host);
+// r -= alpha Qhat^f Qhat^{-f} in (iteration form with `state`, else alpha = 1 and ||r||^2 in dscalars[0])
+tm_status normal_apply(const Solver& S, int prec, int nreal, const void* in, void* T, void* W, void* r,
+                       CGState* state);
+// r = b' - A X in FP64; ||r||^2 returned
+tm_status true_residual(const Solver& S, void* r, const void* X, const void* bp, void* T, void* W, double* rr);
+CGState fresh_state(double rr, double stop2, int max_iter, int iter0, double delta2, double growth = 0.0);
+tm_status prepare_source(const Solver& S, const double* b, void* be, void* bo, void* bp, void* T, double* bb,
+                         double* bfull);
+tm_status reconstruct_check(const Solver& S, const void* X, const void* be, const void* bo, double bfull, double* x,
+                            void* T, void* W, void* R, void* Pv, double* true_rel);
+tm_status launch_accumulate(const Solver& S, void* X, void* xs);  // X (FP64) += xs (FP32); xs = 0
+
+}  // namespace tmq

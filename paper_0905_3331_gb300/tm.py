@@ -46,6 +46,11 @@ class CGParams(ctypes.Structure):
                 ("update_prec", ctypes.c_int)]
 
 
+class TmSystem(ctypes.Structure):
+    _fields_ = [("lat", ctypes.c_void_p), ("mu", ctypes.c_double), ("flavour", ctypes.c_int),
+                ("x", ctypes.c_void_p), ("b", ctypes.c_void_p)]
+
+
 class CGInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("reliable_updates", ctypes.c_int),
                 ("true_rel_residual", ctypes.c_double), ("schur_rel_residual", ctypes.c_double),
@@ -86,6 +91,8 @@ def load():
         "tm_apply_Mee_inv": ([P, P, P, I, I, I, P], I),
         "tm_solve_cg": ([P, P, P, I, ctypes.POINTER(CGParams), ctypes.POINTER(CGInfo), P], I),
         "tm_cg_params_default": ([ctypes.POINTER(CGParams)], None),
+        "tm_solve_cg_batch": ([ctypes.POINTER(TmSystem), I, ctypes.POINTER(CGParams),
+                               ctypes.POINTER(CGInfo), P], I),
         "tm_last_error": ([], ctypes.c_char_p),
         "tm_launch_count": ([], ctypes.c_ulonglong),
         "tm_reset_launch_count": ([], None),
@@ -102,7 +109,8 @@ def exported_symbols():
     """Names of the ABI functions this binding binds (all must exist in the library)."""
     return ["tm_lattice_create", "tm_lattice_destroy", "tm_lattice_set_params", "tm_volume",
             "tm_half_field_bytes", "tm_set_hop_threads", "tm_get_hop_threads", "tm_set_gauge", "tm_pack_half", "tm_unpack_half", "tm_apply_D",
-            "tm_apply_hopping_eo", "tm_apply_Mee_inv", "tm_solve_cg", "tm_cg_params_default",
+            "tm_apply_hopping_eo", "tm_apply_Mee_inv", "tm_solve_cg", "tm_solve_cg_batch",
+            "tm_cg_params_default",
             "tm_last_error", "tm_launch_count", "tm_reset_launch_count"]
 
 
@@ -242,3 +250,26 @@ class Lattice:
         d = info.as_dict()
         d["status"] = st
         return SolveInfo(**d)
+
+
+def solve_cg_batch(systems, tol: float = 1e-10, max_iter: int = 100000, sloppy_prec: int = F32,
+                   sloppy_link: int = LINK12, delta: float = 0.1, stream=None, check: bool = True):
+    """Solve many systems together.  `systems` is a list of (lattice, mu, x, b) or
+    (lattice, mu, x, b, flavour) with x, b device buffers (canonical full fields).
+    Returns one SolveInfo per system."""
+    n = len(systems)
+    arr = (TmSystem * n)()
+    for k, sysk in enumerate(systems):
+        lat, mu, x, b = sysk[:4]
+        flavour = sysk[4] if len(sysk) > 4 else 1
+        arr[k] = TmSystem(lat._h, mu, flavour, _addr(x), _addr(b))
+    p = CGParams(tol, max_iter, CG_RELIABLE, sloppy_prec, sloppy_link, delta, 0, 1, F64)
+    infos = (CGInfo * n)()
+    st = load().tm_solve_cg_batch(arr, n, ctypes.byref(p), infos, _stream(stream))
+    if check:
+        _check(st, "tm_solve_cg_batch")
+    out = []
+    for k in range(n):
+        d = infos[k].as_dict()
+        out.append(SolveInfo(**d))
+    return out

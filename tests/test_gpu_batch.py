@@ -1,0 +1,105 @@
+"""GPU batched solves (tm_solve_cg_batch) against the CPU oracle.
+
+Every system of a batch must reach the same bar as a single solve: the oracle's own M
+applied to the GPU solution gives ||phi - M x|| / ||phi|| < 1e-10.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0905_3331_gb300 import F16, F32, LINK12, LINK18, Lattice, TMError, inputs, solve_cg_batch
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def dev():
+    return torch.device("cuda:0")
+
+
+def oracle_rel_residual(T, L, U, phi, x, kappa, mu, f=1):
+    olat = oracle.Lattice.cubic(T, L)
+    r = phi - oracle.apply_M(olat, U, x, kappa, mu if f == 1 else -mu)
+    return np.linalg.norm(r) / np.linalg.norm(phi)
+
+
+@pytest.mark.parametrize("sloppy", [(F32, LINK12), (F16, LINK12), (F32, LINK18)])
+def test_mixed_batch_of_lattices_masses_and_sources(sloppy):
+    """Two lattices (4^4 and 4^3 x 6... as 6 x 4^3) with different gauge fields, three twisted
+    masses and several sources, in one batched solve."""
+    specs = [(4, 4, 0.3, 0.160, 11), (6, 4, 0.5, 0.1632, 12)]
+    lats, gauges = [], []
+    for T, L, eps, kappa, seed in specs:
+        U = inputs.random_gauge(T, L, eps, seed)
+        lat = Lattice(T, L, kappa, 0.01)
+        lat.set_gauge(U)
+        lats.append(lat)
+        gauges.append(U)
+    systems, meta = [], []
+    for li, (T, L, eps, kappa, seed) in enumerate(specs):
+        for mu in (0.002, 0.005, 0.01):
+            for src in range(2):
+                phi = inputs.gaussian_spinor(T, L, 100 + 10 * li + src)
+                b = torch.from_numpy(phi).to(dev())
+                x = torch.zeros_like(b)
+                f = 1 if src == 0 else -1
+                systems.append((lats[li], mu, x, b, f))
+                meta.append((li, mu, phi, f))
+    infos = solve_cg_batch(systems, sloppy_prec=sloppy[0], sloppy_link=sloppy[1], delta=0.1)
+    for (lat, mu, x, b, f), (li, mu_, phi, f_), info in zip(systems, meta, infos):
+        T, L, eps, kappa, seed = specs[li]
+        res = oracle_rel_residual(T, L, gauges[li], phi, x.cpu().numpy(), kappa, mu, f)
+        assert res < 1e-10, (li, mu, f, res)
+        assert info.status == 0 and info.true_rel_residual < 1e-10 and info.iters > 0
+    # the batched solution equals the single solve to within the solver tolerance
+    lat, mu, x, b, f = systems[3]
+    lat.set_params(lat.kappa, mu)
+    x1 = torch.zeros_like(b)
+    lat.solve_cg(x1, b, mode=2, sloppy_prec=sloppy[0], sloppy_link=sloppy[1], flavour=f, tol=1e-10)
+    assert float(torch.linalg.vector_norm(x1 - x) / torch.linalg.vector_norm(x1)) < 1e-7
+    for lat in lats:
+        lat.close()
+
+
+def test_twelve_point_sources_8x8x8x8():
+    """The 12 spin-colour point sources of a propagator on one 8^4 lattice."""
+    w = inputs.WORKLOADS["8^4"]
+    U = w.gauge()
+    lat = Lattice(w.T, w.L, w.kappa, w.mu)
+    lat.set_gauge(U)
+    systems, phis = [], []
+    for s in range(4):
+        for c in range(3):
+            phi = inputs.point_source(w.T, w.L, s, c)
+            b = torch.from_numpy(phi).to(dev())
+            systems.append((lat, w.mu, torch.zeros_like(b), b))
+            phis.append(phi)
+    infos = solve_cg_batch(systems, sloppy_prec=F32, sloppy_link=LINK12, delta=1e-3)
+    for (l, mu, x, b), phi, info in zip(systems, phis, infos):
+        assert oracle_rel_residual(w.T, w.L, U, phi, x.cpu().numpy(), w.kappa, w.mu) < 1e-10
+        assert info.true_rel_residual < 1e-10
+    lat.close()
+
+
+def test_batch_edge_cases():
+    w = inputs.WORKLOADS["4^4"]
+    U = w.gauge()
+    lat = Lattice(w.T, w.L, w.kappa, w.mu)
+    lat.set_gauge(U)
+    phi = w.source()
+    b = torch.from_numpy(phi).to(dev())
+    zero = torch.zeros_like(b)
+    x0, x1 = torch.ones_like(b), torch.zeros_like(b)
+    infos = solve_cg_batch([(lat, w.mu, x0, zero), (lat, w.mu, x1, b)])
+    assert torch.count_nonzero(x0) == 0 and infos[0].iters == 0
+    assert oracle_rel_residual(w.T, w.L, U, phi, x1.cpu().numpy(), w.kappa, w.mu) < 1e-10
+    infos = solve_cg_batch([(lat, w.mu, x1, b)], max_iter=3, check=False)
+    assert infos[0].status == 7
+    with pytest.raises(TMError) as e:
+        solve_cg_batch([(lat, w.mu, x1, b)], max_iter=3)
+    assert e.value.status_name == "TM_ERR_NOT_CONVERGED"
+    host = np.zeros_like(phi)
+    with pytest.raises(TMError) as e:
+        solve_cg_batch([(lat, w.mu, host, b)])
+    assert e.value.status_name == "TM_ERR_ARG"
+    lat.close()
