@@ -30,6 +30,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Dslash GB/s & % HBM roofline; CG solves/sec to 1e-10 FP64 residual, mixed vs FP64"
 HOP_FLOPS = 1320  # per output site per hopping application (8 hops x 168 flops - 24)
+# dram__bytes_read.sum + dram__bytes_write.sum of one hop_kernel<FP32, 12-real> launch on the
+# 16^3 x 32 lattice, ncu --set full capture (profiles/hop_f32_12_16x32_and_32x64_full.md)
+NCU_TRAFFIC = {("f32:12", "16^3x32"): 31488768.0}
 
 
 def hop_bytes_per_site(prec: int, nreal: int) -> int:
@@ -180,8 +183,10 @@ def run_gpu(args):
 
     # ---- timed region: K mixed-precision solves
     launches0 = launch_count()
+    torch.cuda.nvtx.range_push("timed_region")  # ncu --nvtx --nvtx-include "timed_region/"
     with ClockSampler(local) as clk:
         t_mixed, infos = timed_solves(args.steps, mixed_kw)
+    torch.cuda.nvtx.range_pop()
     launches = launch_count() - launches0
     clocks = clk.summary()
     t_mixed = max_over_ranks(t_mixed)
@@ -244,12 +249,18 @@ def run_gpu(args):
                         "us_l2_resident": tw * 1e6, "gbs_l2_resident": by / tw / 1e9,
                         "gflops_l2_resident": HOP_FLOPS * h / tw / 1e9}
     skey = args.sloppy.replace(":", "_")
+    # DRAM bytes of one launch of the sloppy kernel from an ncu capture (profiles/), valid
+    # while that kernel is unchanged; other forms or lattices report null
+    if args.traffic is None and (args.sloppy, w.name) in NCU_TRAFFIC:
+        args.traffic = NCU_TRAFFIC[(args.sloppy, w.name)]
     top = dslash[skey]
     roofline = {"bound": "hbm", "kernel": f"hop_kernel ({args.sloppy} sloppy form)",
                 "achieved": round(top["gbs_cold"], 1), "peak": peak, "unit": "GB/s",
                 "frac": round(top["gbs_cold"] / peak, 4),
                 "traffic": args.traffic, "peak_kind": peak_kind,
                 "timing": "per-launch CUDA events, L2 flushed before each launch"}
+
+    batched = None if args.no_batched else batched_measurement(args, dev)
 
     n_units = args.steps * world
     value = n_units / t_mixed
@@ -276,6 +287,7 @@ def run_gpu(args):
         "e2e": {"value": round(n_e2e * world / t_e2e, 3), "unit": "solves/s",
                 "h2d_bytes_per_step": int(phi.nbytes), "d2h_bytes_per_step": int(phi.nbytes)},
         "gpu_launches": int(launches),
+        "batched": batched,
         "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -286,6 +298,65 @@ def run_gpu(args):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(result))
+
+
+# --------------------------------------------------------------- batched ---
+def batched_measurement(args, dev):
+    """The batched workload: 12 spin-colour point sources on 24^3 x 48 (eps 0.6, kappa 0.1615,
+    mu 0.003) plus 8^4, 12^3 x 24 and 16^3 x 32 lattices (eps 0.5, kappa 0.1632) with 4
+    Gaussian sources for each mu in {0.002, 0.005, 0.01}: 48 systems in one batched solve,
+    against the same systems solved one at a time.  Same solver settings as the main line."""
+    import torch
+
+    from paper_0905_3331_gb300 import CG_RELIABLE, Lattice, inputs, solve_cg_batch
+    sp, sl = parse_sloppy(args.sloppy)
+    big = inputs.WORKLOADS["24^3x48"]
+    lats, systems = [], []
+    lat = Lattice(big.T, big.L, big.kappa, big.mu)
+    lat.set_gauge(big.gauge())
+    lats.append(lat)
+    for s in range(4):
+        for c in range(3):
+            b = torch.from_numpy(inputs.point_source(big.T, big.L, s, c)).to(dev)
+            systems.append((lat, big.mu, torch.zeros_like(b), b))
+    for name in ("8^4", "12^3x24", "16^3x32"):
+        w = inputs.WORKLOADS[name]
+        lat = Lattice(w.T, w.L, 0.1632, 0.002)
+        lat.set_gauge(inputs.random_gauge(w.T, w.L, 0.5, w.gauge_seed))
+        lats.append(lat)
+        for mu in (0.002, 0.005, 0.01):
+            for k in range(4):
+                b = torch.from_numpy(inputs.gaussian_spinor(w.T, w.L, 2 + k)).to(dev)
+                systems.append((lat, mu, torch.zeros_like(b), b))
+    kw = dict(sloppy_prec=sp, sloppy_link=sl, delta=args.delta)
+    solve_cg_batch(systems, **kw)  # warm-up (gauge copies, allocations)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    infos = solve_cg_batch(systems, **kw)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    t_single = 0.0
+    iters_single = 0
+    for lat_, mu, x, b in systems:
+        lat_.set_params(lat_.kappa, mu)
+        x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = lat_.solve_cg(x, b, mode=CG_RELIABLE, **kw)
+        torch.cuda.synchronize()
+        t_single += time.perf_counter() - t0
+        iters_single += info.iters
+    for lat_ in lats:
+        lat_.close()
+    n = len(systems)
+    return {"workload": "12 point sources on 24^3x48 + {8^4, 12^3x24, 16^3x32} x 3 mu x 4 sources",
+            "systems": n, "systems_per_s": round(n / t_batch, 3),
+            "unbatched_systems_per_s": round(n / t_single, 3),
+            "speedup": round(t_single / t_batch, 3),
+            "max_true_rel_residual": max(i.true_rel_residual for i in infos),
+            "iters_batched": sum(i.iters for i in infos), "iters_unbatched": iters_single,
+            "timing": "host wall clock around one synchronised call (batched) / the sum of "
+                      "the single solves (unbatched)"}
 
 
 # -------------------------------------------------------------- CPU oracle ---
@@ -377,6 +448,7 @@ def main():
     ap.add_argument("--hop-iters", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-solve measurement")
     ap.add_argument("--ref-seconds", type=float, default=8.0)
     ap.add_argument("--ref-iters", type=int, default=1500,
                     help="CG iterations per solve used to scale the reference arm's sample")
