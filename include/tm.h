@@ -230,6 +230,19 @@ typedef struct {
 tm_status tm_solve_cg_batch(const tm_system *systems, int nsys, const tm_cg_params *params,
                             tm_cg_info *infos, void *stream);
 
+/* ---------------------------------------------------------------- contractions --- */
+
+/* Meson contraction of a point-source propagator, for the correlators of Sec. 4.5 (one-end
+ * trick; gamma5-hermiticity G_u(0,x) = gamma5 G_d(x,0)^dag gamma5):
+ *   C_PG(t) = sum_{x, x_t = t} tr[ G(x,0)^dag G(x,0) Gamma gamma5 ]   (Gamma on source spin),
+ * with G(x,0) the d-quark propagator of a source at the origin (solutions of M(-mu) x = b).
+ * props: 12 canonical full fields, host or device, back to back; field j = 3 s + c is the
+ * solution for the source of spin s and colour c.  out: T x 12 x 12 complex doubles (host or
+ * device), out[t][j][k] = sum_{x, x_t = t} <psi_j(x), psi_k(x)> (conjugate on psi_j); then
+ * C_PG(t) = sum_{s, s', c} out[t][3s+c][3s'+c] (Gamma gamma5)[s'][s], e.g. C_PP(t) = trace.
+ * FP64, deterministic.  Errors: TM_ERR_ARG, TM_ERR_CUDA. */
+tm_status tm_meson_contract(tm_lattice lat, const double *props, double *out, void *stream);
+
 /* Fills params with the defaults: tol 1e-10, max_iter 100000, TM_CG_FP64, sloppy
  * TM_F32 / TM_LINK12, delta 0.1, use_x0 0, flavour +1, update_prec TM_F64. */
 void tm_cg_params_default(tm_cg_params *params);

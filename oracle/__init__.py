@@ -54,36 +54,55 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
+def compile_variant(src_text: str, path: str) -> str:
+    """Compile C source text with the oracle's flags into `path` (for tests that plant a
+    mistake in a copy of the oracle and check that the pins catch it)."""
+    csrc = path[:-3] + ".c"
+    with open(csrc, "w") as fh:
+        fh.write(src_text)
+    subprocess.run(["gcc", *CFLAGS, csrc, "-o", path, "-lm"], check=True)
+    return path
+
+
+def load_library(path: str):
+    """Load and configure a compiled oracle library (the default one is loaded lazily)."""
+    return _configure(ctypes.CDLL(path))
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
-            P = ctypes.c_void_p
-            I = ctypes.c_int
-            D = ctypes.c_double
-            L = ctypes.c_long
-            lib.orc_gamma.argtypes = [I, P]
-            lib.orc_hopping.argtypes = [P, P, I, P, P, P, I]
-            lib.orc_apply_M.argtypes = [P, P, I, D, D, I, P, P, P]
-            lib.orc_apply_M_sites.argtypes = [P, P, I, D, D, I, P, P, P, L, P]
-            lib.orc_hopping_sites.argtypes = [P, P, I, P, P, P, L, P]
-            lib.orc_apply_Mdiag.argtypes = [P, D, I, I, P, P]
-            lib.orc_apply_Mdiag_inv.argtypes = [P, D, I, I, P, P]
-            lib.orc_apply_Moff.argtypes = [P, P, I, D, P, I, P, P]
-            lib.orc_schur.argtypes = [P, P, I, D, D, I, P, P, P, I]
-            lib.orc_normal_op.argtypes = [P, P, I, D, D, I, P, P, P]
-            lib.orc_cg.argtypes = [P, P, I, D, D, I, P, P, P, D, I,
-                                   ctypes.POINTER(I), ctypes.POINTER(D)]
-            lib.orc_cg.restype = I
-            lib.orc_eo_prepare.argtypes = [P, P, I, D, D, I, P, P, P]
-            lib.orc_eo_reconstruct.argtypes = [P, P, I, D, D, I, P, P, P]
-            lib.orc_solve.argtypes = [P, P, I, D, D, I, P, P, P, D, I, ctypes.POINTER(I),
-                                      ctypes.POINTER(D), ctypes.POINTER(D)]
-            lib.orc_solve.restype = I
-            lib.orc_num_threads.restype = I
-            _lib = lib
+            _lib = _configure(ctypes.CDLL(build()))
     return _lib
+
+
+def _configure(lib):
+    """Set the ctypes signatures of every oracle entry point."""
+    P = ctypes.c_void_p
+    I = ctypes.c_int
+    D = ctypes.c_double
+    L = ctypes.c_long
+    lib.orc_gamma.argtypes = [I, P]
+    lib.orc_hopping.argtypes = [P, P, I, P, P, P, I]
+    lib.orc_apply_M.argtypes = [P, P, I, D, D, I, P, P, P]
+    lib.orc_apply_M_sites.argtypes = [P, P, I, D, D, I, P, P, P, L, P]
+    lib.orc_hopping_sites.argtypes = [P, P, I, P, P, P, L, P]
+    lib.orc_apply_Mdiag.argtypes = [P, D, I, I, P, P]
+    lib.orc_apply_Mdiag_inv.argtypes = [P, D, I, I, P, P]
+    lib.orc_apply_Moff.argtypes = [P, P, I, D, P, I, P, P]
+    lib.orc_schur.argtypes = [P, P, I, D, D, I, P, P, P, I]
+    lib.orc_normal_op.argtypes = [P, P, I, D, D, I, P, P, P]
+    lib.orc_cg.argtypes = [P, P, I, D, D, I, P, P, P, D, I,
+                           ctypes.POINTER(I), ctypes.POINTER(D)]
+    lib.orc_cg.restype = I
+    lib.orc_eo_prepare.argtypes = [P, P, I, D, D, I, P, P, P]
+    lib.orc_eo_reconstruct.argtypes = [P, P, I, D, D, I, P, P, P]
+    lib.orc_solve.argtypes = [P, P, I, D, D, I, P, P, P, D, I, ctypes.POINTER(I),
+                              ctypes.POINTER(D), ctypes.POINTER(D)]
+    lib.orc_solve.restype = I
+    lib.orc_num_threads.restype = I
+    return lib
 
 
 # ------------------------------------------------------------------ helpers ---
@@ -304,3 +323,21 @@ def solve(lat: Lattice, U, phi, kappa: float, mu: float, f: int = 1, tol: float 
                            int(f), _ptr(U), _ptr(phi), _ptr(psi), tol, int(max_iter),
                            ctypes.byref(it), ctypes.byref(rn), ctypes.byref(rf))
     return SolveResult(psi, st == 0, it.value, rn.value, rf.value)
+
+
+# ------------------------------------------------------------- contractions ---
+def meson_contract(props) -> np.ndarray:
+    """Timeslice sums of the Gram matrix of a 12-column point-source propagator:
+    A[t][j][k] = sum_{x, x_t = t} <psi_j(x), psi_k(x)> (conjugate on psi_j), the building
+    block of the correlators C_PG(t) = sum_x tr[G^dag G Gamma gamma5] of Sec. 4.5.
+    props: (12, T, L, L, L, 4, 3).  Plain numpy definition."""
+    P = np.asarray(props, dtype=np.complex128)
+    return np.einsum("jtzyxsc,ktzyxsc->tjk", P.conj(), P)
+
+
+def correlator(A, G) -> np.ndarray:
+    """C(t) = tr[A_t (G (x) 1_colour)] with G = Gamma gamma5 acting on source spin."""
+    A = np.asarray(A)
+    T = A.shape[0]
+    big = np.kron(np.asarray(G, dtype=np.complex128), np.eye(3))
+    return np.array([np.trace(A[t] @ big) for t in range(T)])

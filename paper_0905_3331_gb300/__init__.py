@@ -7,4 +7,4 @@ The compute path is the CUDA library built from csrc/ (C ABI in include/tm.h);
 from . import build  # noqa: F401  (the module; build.build() compiles the library)
 from .tm import (CG_FP64, CG_RELIABLE, CG_SQRT_EPS, DF64, F16, F32, F64, LINK8, LINK12,  # noqa: F401
                  LINK18, Lattice, SolveInfo, TMError, launch_count, load, reset_launch_count,
-                 solve_cg_batch)
+                 correlator, solve_cg_batch)

@@ -93,6 +93,7 @@ def load():
         "tm_cg_params_default": ([ctypes.POINTER(CGParams)], None),
         "tm_solve_cg_batch": ([ctypes.POINTER(TmSystem), I, ctypes.POINTER(CGParams),
                                ctypes.POINTER(CGInfo), P], I),
+        "tm_meson_contract": ([P, P, P, P], I),
         "tm_last_error": ([], ctypes.c_char_p),
         "tm_launch_count": ([], ctypes.c_ulonglong),
         "tm_reset_launch_count": ([], None),
@@ -110,7 +111,7 @@ def exported_symbols():
     return ["tm_lattice_create", "tm_lattice_destroy", "tm_lattice_set_params", "tm_volume",
             "tm_half_field_bytes", "tm_set_hop_threads", "tm_get_hop_threads", "tm_set_gauge", "tm_pack_half", "tm_unpack_half", "tm_apply_D",
             "tm_apply_hopping_eo", "tm_apply_Mee_inv", "tm_solve_cg", "tm_solve_cg_batch",
-            "tm_cg_params_default",
+            "tm_cg_params_default", "tm_meson_contract",
             "tm_last_error", "tm_launch_count", "tm_reset_launch_count"]
 
 
@@ -236,6 +237,22 @@ class Lattice:
         _check(load().tm_apply_Mee_inv(self._h, _addr(out), _addr(inp), flavour, prec, nrhs,
                                        _stream(stream)), "tm_apply_Mee_inv")
 
+    def meson_contract(self, props, out=None, stream=None):
+        """Timeslice Gram matrices of a 12-column point-source propagator (tm_meson_contract).
+        props: (12, T, L, L, L, 4, 3) complex128 (device or host).  Returns (T, 12, 12)."""
+        if out is None:
+            out = np.zeros((self.T, 12, 12), dtype=np.complex128)
+        _check(load().tm_meson_contract(self._h, _addr(props), _addr(out), _stream(stream)),
+               "tm_meson_contract")
+        if isinstance(out, np.ndarray):
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    torch.cuda.synchronize()
+            except ImportError:
+                pass
+        return out
+
     def solve_cg(self, x, b, nrhs: int = 1, tol: float = 1e-10, max_iter: int = 100000,
                  mode: int = CG_FP64, sloppy_prec: int = F32, sloppy_link: int = LINK12,
                  delta: float = 0.1, use_x0: bool = False, flavour: int = 1,
@@ -273,3 +290,11 @@ def solve_cg_batch(systems, tol: float = 1e-10, max_iter: int = 100000, sloppy_p
         d = infos[k].as_dict()
         out.append(SolveInfo(**d))
     return out
+
+
+def correlator(A, gamma_source_times_g5):
+    """C(t) = sum_{s, s', c} A[t][3s+c][3s'+c] G[s'][s] for G = Gamma gamma5 (4 x 4); A from
+    Lattice.meson_contract.  C_PP uses G = identity."""
+    A = np.asarray(A).reshape(-1, 4, 3, 4, 3)
+    G = np.asarray(gamma_source_times_g5)
+    return np.einsum("tacbc,ba->t", A, G)

@@ -1,0 +1,97 @@
+"""The pins catch plausible mistakes in the oracle.
+
+Each case plants one mistake in a copy of oracle/tm_oracle.c (a dropped term, a wrong sign,
+a missing adjoint, a transposed operand, a misplaced boundary phase, a wrong inverse, a typo
+in a gamma matrix ...), compiles it, swaps it in for the real oracle and runs the pins of
+tests/test_oracle_pins.py at their smallest sizes: at least one pin must fail.  The CPU only.
+"""
+import os
+
+import pytest
+
+import oracle
+import test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "tm_oracle.c")
+
+MUTATIONS = [
+    ("projector sign swapped (1 - gamma) forward",
+     "(s == t ? 1.0 : 0.0) + (double)dir * GAMMA[mu][s][t]",
+     "(s == t ? 1.0 : 0.0) - (double)dir * GAMMA[mu][s][t]"),
+    ("backward link not daggered",
+     "link[a][b] = conj(u[3 * b + a]);", "link[a][b] = u[3 * a + b];"),
+    ("backward link taken at x instead of x - mu",
+     "const cplx *u = U + 36 * ln + 9 * mu;", "const cplx *u = U + 36 * lex + 9 * mu;"),
+    ("forward link transposed",
+     "for (int b = 0; b < 3; ++b) link[a][b] = u[3 * a + b];",
+     "for (int b = 0; b < 3; ++b) link[a][b] = u[3 * b + a];"),
+    ("antiperiodic phase dropped",
+     "if (dir > 0 && c[mu] == g->n[mu] - 1) return unit_phase(theta[mu]);",
+     "if (dir > 0 && c[mu] == g->n[mu] - 1) return 1.0;"),
+    ("neighbour direction reversed",
+     "cn[mu] = (c[mu] + dir + g->n[mu]) % g->n[mu];", "cn[mu] = (c[mu] - dir + g->n[mu]) % g->n[mu];"),
+    ("twisted mass sign flipped",
+     "cplx m = (s == t ? 1.0 : 0.0) + I * (double)f * mut * GAMMA[4][s][t];",
+     "cplx m = (s == t ? 1.0 : 0.0) - I * (double)f * mut * GAMMA[4][s][t];"),
+    ("twisted mass without gamma5",
+     "cplx m = (s == t ? 1.0 : 0.0) + I * (double)f * mut * GAMMA[4][s][t];",
+     "cplx m = (s == t ? 1.0 + I * (double)f * mut : 0.0);"),
+    ("site-diagonal inverse with 1 - mu~^2",
+     "out[12 * lex + k] = tmp[k] / (1.0 + mut * mut);", "out[12 * lex + k] = tmp[k] / (1.0 - mut * mut);"),
+    ("kappa dropped from the hopping term of M",
+     "out[12 * lex + 3 * s + a] = d[3 * s + a] - kappa * acc[s][a];",
+     "out[12 * lex + 3 * s + a] = d[3 * s + a] - acc[s][a];"),
+    ("Schur complement sign",
+     "for (long k = 0; k < n; ++k) t4[k] -= t3[k];", "for (long k = 0; k < n; ++k) t4[k] += t3[k];"),
+    ("source preparation sign",
+     "varphi[i] = parity_of(c) == 0 ? ve[i] : phi[i] - t[i];",
+     "varphi[i] = parity_of(c) == 0 ? ve[i] : phi[i] + t[i];"),
+    ("reconstruction sign",
+     "psi[12 * lex + k] = varphi[12 * lex + k] - u[12 * lex + k];",
+     "psi[12 * lex + k] = varphi[12 * lex + k] + u[12 * lex + k];"),
+    ("gamma_2 typo", "{{0, 0, 0, -1}, {0, 0, +1, 0}, {0, +1, 0, 0}, {-1, 0, 0, 0}},",
+     "{{0, 0, 0, -1}, {0, 0, -1, 0}, {0, +1, 0, 0}, {-1, 0, 0, 0}},"),
+    ("CG step length from <p, p>",
+     "double alpha = rr / creal(dot(n, p, q));", "double alpha = rr / creal(dot(n, p, p));"),
+    ("CG direction update without beta",
+     "for (long i = 0; i < n; ++i) p[i] = r[i] + beta * p[i];",
+     "for (long i = 0; i < n; ++i) p[i] = r[i];"),
+]
+
+# the pins, at their smallest sizes
+PIN_CALLS = [
+    ("gamma", lambda: pins.test_gamma_matrices_clifford_algebra()),
+    ("worked example", lambda: pins.test_point_source_worked_example()),
+    ("free field M", lambda: pins.test_free_field_eigenvalues_of_M(2, 2)),
+    ("free field MdagM", lambda: pins.test_free_field_spectrum_of_MdagM(4, 2, (0.0, 0.0, 0.0, 0.0))),
+    ("gauge covariance", lambda: pins.test_gauge_covariance()),
+    ("gamma5 hermiticity", lambda: pins.test_gamma5_hermiticity_with_twisted_mass()),
+    ("boundary phases", lambda: pins.test_boundary_phase_placement_equivalence((1.0, 0.0, 0.0, 0.0))),
+    ("diagonal inverse", lambda: pins.test_site_diagonal_inverse_is_the_inverse()),
+    ("schur dense", lambda: pins.test_schur_operator_is_the_dense_schur_complement(2, 2)),
+    ("solve dense", lambda: pins.test_even_odd_solve_equals_dense_solve(2, 2)),
+    ("cg dense", lambda: pins.test_cg_on_normal_equations_matches_dense()),
+]
+
+
+@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_a_planted_mistake_fails_a_pin(name, old, new, tmp_path, monkeypatch):
+    src = open(SRC).read()
+    assert src.count(old) >= 1, f"mutation site not found: {old}"
+    variant = oracle.load_library(oracle.compile_variant(src.replace(old, new, 1),
+                                                         str(tmp_path / "libvariant.so")))
+    monkeypatch.setattr(oracle, "_lib", variant)
+    failed = []
+    for pin, call in PIN_CALLS:
+        try:
+            call()
+        except Exception:  # an assertion, a non-convergence, a numpy error: the pin caught it
+            failed.append(pin)
+    assert failed, f"no pin caught: {name}"
+
+
+def test_the_unmutated_copy_passes_every_pin(tmp_path, monkeypatch):
+    variant = oracle.load_library(oracle.compile_variant(open(SRC).read(), str(tmp_path / "libsame.so")))
+    monkeypatch.setattr(oracle, "_lib", variant)
+    for pin, call in PIN_CALLS:
+        call()

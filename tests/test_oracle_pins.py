@@ -339,6 +339,8 @@ def test_cg_on_normal_equations_matches_dense():
     res = oracle.cg(lat, U, b, kappa, mu, tol=1e-13)
     X = np.linalg.solve(A, b.reshape(-1)[o])
     assert res.converged and rel(res.x.reshape(-1)[o], X) < 1e-10
+    # conjugate gradients end within the dimension of the system (here 12 V / 2 = 96)
+    assert res.iters <= A.shape[0]
 
 
 def test_lambda_min_bound():
@@ -363,3 +365,38 @@ def test_sampled_sites_match_full_application():
     sites = np.array([0, 5, 77, 255, 128])
     part = oracle.apply_M_sites(lat, U, psi, 0.16, 0.01, sites)
     assert np.array_equal(part, full[sites])
+
+
+# ------------------------------------------------------ correlators (Sec. 4.5) ---
+def test_free_field_pion_correlator_from_momentum_space():
+    """C_PP(t) = sum_x ||G(x,0)||^2 of the oracle's 12 point-source solves on a unit gauge field
+    equals the closed form G(x,0) = (1/V) sum_p e^{ipx} M(p)^-1, M(p) = (1 - 2k sum cos p)
+    + i mu~ g5 - 2ik sum g_mu sin p_mu (antiperiodic p_t), summed over each timeslice."""
+    T, L = 4, 4
+    lat = Lattice.cubic(T, L)
+    U = inputs.unit_gauge(T, L)
+    kappa, mu = 0.12, 0.05
+    mut = 2 * kappa * mu
+    props = []
+    for s in range(4):
+        for c in range(3):
+            res = oracle.solve(lat, U, inputs.point_source(T, L, s, c), kappa, mu, tol=1e-13)
+            assert res.converged
+            props.append(res.psi)
+    A = oracle.meson_contract(np.stack(props))
+    C = oracle.correlator(A, np.eye(4)).real
+    g = [oracle.gamma(k) for k in range(5)]
+    P = free_field_momenta(lat)  # (p_t, p_x, p_y, p_z)
+    t, z, y, x = np.indices((T, L, L, L))
+    G = np.zeros((T, L, L, L, 4, 4), dtype=complex)
+    for p in P:
+        Mp = (1 - 2 * kappa * np.cos(p).sum()) * np.eye(4) + 1j * mut * g[4] \
+            - 2j * kappa * sum(g[m] * np.sin(p[m]) for m in range(4))
+        phase = np.exp(1j * (p[0] * t + p[1] * x + p[2] * y + p[3] * z))
+        G += phase[..., None, None] * np.linalg.inv(Mp)
+    G /= lat.V
+    C_closed = 3 * (np.abs(G) ** 2).sum(axis=(1, 2, 3, 4, 5))  # colour identity: 3 copies
+    assert np.allclose(C, C_closed, rtol=1e-9, atol=0)
+    # the point-source propagator itself, spin block of colour 0, at every site
+    Gsolve = np.stack(props).reshape(4, 3, T, L, L, L, 4, 3)[:, 0, ..., 0]  # [s_src, ..., s_sink]
+    assert np.allclose(np.moveaxis(Gsolve, 0, -1), G, rtol=0, atol=1e-10)
