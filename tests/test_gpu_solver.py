@@ -236,3 +236,25 @@ def test_solve_with_each_threads_per_site(tps):
         assert oracle_true_residual(w, U, phi, x.cpu().numpy()) < 1e-10
     assert lat.hop_threads(0, 18) == tps
     lat.close()
+
+
+@pytest.mark.parametrize("name,sloppy,link,delta", [
+    ("32^3x64", F32, LINK12, 1e-3),    # precision form: FP32 storage, 12-real links
+    ("32^3x64", F16, LINK12, 0.1),     # precision form: FP16 + norm storage, 12-real links
+    ("48^3x96", F16, LINK8, 0.3),      # large volume: FP16 storage, 8-real links (half)
+])
+def test_full_size_precision_forms(name, sloppy, link, delta):
+    """The 32^3 x 64 and 48^3 x 96 workloads solved to an FP64 true residual of 1e-10 with the
+    reliable-update CG; the oracle recomputes the residual of the GPU solution on the host."""
+    w = inputs.WORKLOADS[name]
+    U, phi = w.gauge(), w.source()
+    lat = Lattice(w.T, w.L, w.kappa, w.mu)
+    lat.set_gauge(U)
+    b = torch.from_numpy(phi).to(dev())
+    x = torch.zeros_like(b)
+    info = lat.solve_cg(x, b, mode=CG_RELIABLE, sloppy_prec=sloppy, sloppy_link=link, delta=delta,
+                        max_iter=20000)
+    res = oracle_true_residual(w, U, phi, x.cpu().numpy())
+    assert res < 1e-10 and info.true_rel_residual < 1e-10
+    assert abs(res - info.true_rel_residual) < 1e-3 * res
+    lat.close()
