@@ -110,6 +110,23 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+# -------------------------------------------------------- multi-rank logic ---
+def reduce_max(v: float, world: int, device) -> float:
+    """Max of a per-rank value over all ranks (the slowest rank's time)."""
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, world: int, t_max: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * world / t_max
+
+
 # ------------------------------------------------------------------ GPU arm ---
 def run_gpu(args):
     import numpy as np
@@ -148,12 +165,7 @@ def run_gpu(args):
             dist.barrier()
 
     def max_over_ranks(v: float) -> float:
-        if world == 1:
-            return v
-        import torch.distributed as dist
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(v, world, dev)
 
     def timed_solves(n, kw, host=False):
         """n solves, each after an L2 flush, timed with CUDA events (device side)."""
@@ -263,7 +275,7 @@ def run_gpu(args):
     batched = None if args.no_batched else batched_measurement(args, dev)
 
     n_units = args.steps * world
-    value = n_units / t_mixed
+    value = whole_job_rate(args.steps, world, t_mixed)
     result = {
         "metric": METRIC, "value": round(value, 3), "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
@@ -375,7 +387,7 @@ def oracle_cg_rate(w, U, phi, seconds: float):
     n, t = 0, 0.0
     k = 1
     x = None
-    while t < seconds:
+    while n == 0 or t < seconds:
         t1 = time.perf_counter()
         res = oracle.cg(lat, U, b, w.kappa, w.mu, tol=1e-30, max_iter=k, x0=x)
         t += time.perf_counter() - t1

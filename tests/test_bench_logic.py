@@ -1,0 +1,57 @@
+"""bench.py host logic on the CPU: the multi-rank reduction (gloo, 2 ranks), the whole-job
+rate, and the reference arm's JSON line (the CPU oracle on the 4^4 workload)."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+torch = pytest.importorskip("torch")
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, out):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    t = bench.reduce_max(1.0 + rank, world, "cpu")  # rank r was r + 1 seconds slow
+    dist.barrier()
+    with open(out + f".{rank}", "w") as fh:
+        fh.write(repr(t))
+    dist.destroy_process_group()
+
+
+def test_two_rank_max_and_weak_scaling(tmp_path):
+    import torch.multiprocessing as mp
+    port = _free_port()
+    out = str(tmp_path / "r")
+    mp.spawn(_rank, args=(2, port, out), nprocs=2, join=True)
+    vals = [float(open(out + f".{r}").read()) for r in range(2)]
+    assert vals == [2.0, 2.0]  # both ranks see the slowest rank's time
+    # 10 solves per rank on 2 ranks in 2 s (the slowest rank) is 10 solves/s for the job
+    assert bench.whole_job_rate(10, 2, 2.0) == 10.0
+    assert bench.reduce_max(3.5, 1, "cpu") == 3.5
+
+
+def test_reference_arm_json_line():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--workload", "4^4", "--steps", "2", "--warmup", "3", "--ref-seconds", "0.2",
+                        "--ref-iters", "40"], capture_output=True, text=True, timeout=300,
+                       cwd=ROOT)
+    assert r.returncode == 0, r.stderr
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == "solves/s" and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["higher_is_better"] is True
+    assert line["metric"] == bench.METRIC and line["warmup"] == 3 and line["steps"] == 2
