@@ -230,9 +230,37 @@ typedef struct {
 tm_status tm_solve_cg_batch(const tm_system *systems, int nsys, const tm_cg_params *params,
                             tm_cg_info *infos, void *stream);
 
+/* Solves the normal equations of the odd-site Schur operator directly (eq. eo6),
+ *   A X = phi,   A = Qhat^f Qhat^-f = gamma5 Mhat^f gamma5 Mhat^-f,  Qhat^f = gamma5 Mhat^f,
+ * the solve that the HMC force of the twisted-mass pseudofermion needs (X = (Qhat^+ Qhat^-)^-1
+ * phi, App. B.1), with the CG and the mixed-precision modes of tm_solve_cg.
+ * X, phi: FP64 odd-parity half fields in DEVICE memory (the layout of tm_pack_half, TM_F64),
+ * distinct.  params->use_x0 nonzero: X holds the initial guess (e.g. from tm_chrono_guess);
+ * otherwise X is overwritten from zero.  params->flavour picks f (0 means +1).  tol is relative
+ * to ||phi||.  info (may be NULL): iters, reliable_updates, schur_rel_residual =
+ * true_rel_residual = ||phi - A X|| / ||phi||, recomputed in FP64.  Synchronises `stream`.
+ * Errors: TM_ERR_NOT_CONVERGED (X holds the last iterate), TM_ERR_NO_GAUGE, TM_ERR_ARG,
+ * TM_ERR_NONFINITE, TM_ERR_CUDA, TM_ERR_OOM. */
+tm_status tm_solve_normal(tm_lattice lat, void *X, const void *phi, const tm_cg_params *params,
+                          tm_cg_info *info, void *stream);
+
+/* Chronological solver guess (Sec. 4.2, eq. chrono): from n earlier solutions chi_i of
+ * A X = phi (A as in tm_solve_normal, flavour f), solves
+ *   sum_i <chi_j, A chi_i> c_i = <chi_j, phi>    (j = 0 .. n-1; conjugate on chi_j)
+ * for the c_i -- the X0 in the span of the chi_i that minimises the A-norm of the error, the
+ * functional CG minimises -- and writes X0 = sum_i c_i chi_i.  The n x n system (hermitian)
+ * is solved on the host in FP64 by Gaussian elimination with partial pivoting; a direction
+ * whose pivot falls below 1e-13 max|G| (a linearly dependent history) gets c = 0.
+ * X0, phi, chi[i]: FP64 odd half fields in DEVICE memory; chi is a HOST array of n pointers;
+ * 0 <= n <= 64 (n = 0 gives X0 = 0).  X0 must not alias any chi[i].  Costs n applications
+ * of A and n(n+1)/2 + n inner products.  Synchronises `stream` once (to read the n x n
+ * matrix).  Errors: TM_ERR_ARG, TM_ERR_NO_GAUGE, TM_ERR_NONFINITE, TM_ERR_CUDA. */
+tm_status tm_chrono_guess(tm_lattice lat, void *X0, const void *const *chi, int n, const void *phi,
+                          int flavour, void *stream);
+
 /* ---------------------------------------------------------------- contractions --- */
 
-/* Meson contraction of a point-source propagator, for the correlators of Sec. 4.5 (one-end
+/* Meson contraction of a point-source propagator, for the correlators of Sec. 4.3 (one-end
  * trick; gamma5-hermiticity G_u(0,x) = gamma5 G_d(x,0)^dag gamma5):
  *   C_PG(t) = sum_{x, x_t = t} tr[ G(x,0)^dag G(x,0) Gamma gamma5 ]   (Gamma on source spin),
  * with G(x,0) the d-quark propagator of a source at the origin (solutions of M(-mu) x = b).

@@ -329,7 +329,7 @@ def solve(lat: Lattice, U, phi, kappa: float, mu: float, f: int = 1, tol: float 
 def meson_contract(props) -> np.ndarray:
     """Timeslice sums of the Gram matrix of a 12-column point-source propagator:
     A[t][j][k] = sum_{x, x_t = t} <psi_j(x), psi_k(x)> (conjugate on psi_j), the building
-    block of the correlators C_PG(t) = sum_x tr[G^dag G Gamma gamma5] of Sec. 4.5.
+    block of the correlators C_PG(t) = sum_x tr[G^dag G Gamma gamma5] of Sec. 4.3.
     props: (12, T, L, L, L, 4, 3).  Plain numpy definition."""
     P = np.asarray(props, dtype=np.complex128)
     return np.einsum("jtzyxsc,ktzyxsc->tjk", P.conj(), P)
@@ -341,3 +341,27 @@ def correlator(A, G) -> np.ndarray:
     T = A.shape[0]
     big = np.kron(np.asarray(G, dtype=np.complex128), np.eye(3))
     return np.array([np.trace(A[t] @ big) for t in range(T)])
+
+
+# ------------------------------------------------------- chronological guess ---
+def chrono_guess(lat: Lattice, U, chis, phi, kappa: float, mu: float, f: int = 1):
+    """Chronological solver guess (Sec. 4.2, eq. chrono) for A X = phi, A = Qhat^f Qhat^-f
+    (eq. eo6): the coefficients c solve sum_i <chi_j, A chi_i> c_i = <chi_j, phi> and the
+    guess is X0 = sum_i c_i chi_i.  chis: list of odd-site vectors.  Returns (X0, c).
+    Plain numpy: the matrix by its definition, numpy.linalg.solve for the n x n system."""
+    phi = _c(phi, lat.spinor_shape)
+    n = len(chis)
+    if n == 0:
+        return np.zeros_like(phi), np.zeros(0, dtype=np.complex128)
+    chis = [_c(c, lat.spinor_shape) for c in chis]
+    Achi = [normal_op(lat, U, chi, kappa, mu, f) for chi in chis]
+    G = np.empty((n, n), dtype=np.complex128)
+    for j in range(n):
+        for i in range(n):
+            G[j, i] = np.vdot(chis[j], Achi[i])
+    rhs = np.array([np.vdot(chis[j], phi) for j in range(n)])
+    c = np.linalg.solve(G, rhs)
+    X0 = np.zeros_like(phi)
+    for i in range(n):
+        X0 += c[i] * chis[i]
+    return X0, c

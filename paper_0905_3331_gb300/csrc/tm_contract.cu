@@ -1,6 +1,6 @@
 // tm_contract.cu -- meson contraction of a point-source propagator (tm_meson_contract).
 //
-// The correlators of Sec. 4.5 (one-end trick) are, for a point source at the origin,
+// The correlators of Sec. 4.3 (one-end trick) are, for a point source at the origin,
 //   C_PG(t) = sum_{x, x_t = t} tr[ G(x,0)^dag G(x,0) G~ ]  with G~ = Gamma gamma5 on source spin,
 // where G(x,0) is the 12 x 12 spin-colour propagator (column j = the solution for the source
 // of spin-colour j).  This file computes the timeslice sums of its Gram matrix

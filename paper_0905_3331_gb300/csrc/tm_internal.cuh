@@ -920,8 +920,8 @@ tm_status apply_M_halves(tm_lattice lat, void* out_e, void* out_o, const void* i
 tm_status diag_apply(tm_lattice lat, int prec, void* out, const void* in, int nrhs, double dur, double dui,
                      double dlr, double dli, cudaStream_t s);
 // Workspace slots: 0..17 solver, 22..25 tm_apply_D, 26 staged input, 27 staged output,
-// 28 initial-guess work space.
-enum { WS_APPLY_D = 22, WS_STAGE_IN = 26, WS_STAGE_OUT = 27, WS_X0 = 28 };
+// 28 initial-guess work space, 29 contraction partials, 30 chronological-guess scalars.
+enum { WS_APPLY_D = 22, WS_STAGE_IN = 26, WS_STAGE_OUT = 27, WS_X0 = 28, WS_CHRONO = 30 };
 // host-buffer staging through workspace slots
 const void* stage_in(tm_lattice lat, int slot, const void* src, size_t bytes, cudaStream_t s, tm_status* st);
 void* stage_out(tm_lattice lat, int slot, void* dst, size_t bytes, tm_status* st);

@@ -611,50 +611,39 @@ tm_status launch_accumulate(const Solver& S, void* X, void* xs) {
   return cuda_check(cudaGetLastError(), "accumulate kernel");
 }
 
-// Solves M^f x = b for one canonical full field (device pointers).
-static tm_status solve_one(tm_lattice lat, double* x, const double* b, const tm_cg_params& P, tm_cg_info* info,
-                           cudaStream_t s) {
-  Solver S{lat, s, P.flavour, 2.0 * lat->kappa * lat->mu, {0, 0, 0, 0}};
-  for (int p = 0; p < 4; ++p) S.hb[p] = spinor_bytes_per_site(p) * lat->h;
+// CG on A X = bp, A = Qhat^f Qhat^-f on the odd sites (eq. eo6), FP64 or mixed precision per
+// P.mode; X holds an initial guess if `guess`, else it starts at 0.  bp, X, R, Pv, T, W are FP64
+// half fields (R, Pv, T, W work space); bb = ||bp||^2.  The result is converged when the
+// recomputed FP64 residual satisfies ||bp - A X||^2 < tol^2 bb.
+tm_status cg_normal(const Solver& S, const tm_cg_params& P, const void* bp, double bb, void* X, bool guess, void* R,
+                    void* Pv, void* T, void* W, NormalResult* res) {
+  tm_lattice lat = S.lat;
+  cudaStream_t s = S.s;
   tm_status st = TM_OK;
-  // FP64 fields: 0 b_e, 1 b_o, 2 b', 3 X, 4 R, 5 P, 6 T, 7 W
-  void* w[8];
-  for (int k = 0; k < 8; ++k) {
-    w[k] = workspace(lat, k, S.hb[TM_F64], &st);
-    if (st != TM_OK) return st;
-  }
-  void *be = w[0], *bo = w[1], *bp = w[2], *X = w[3], *R = w[4], *Pv = w[5], *T = w[6], *W = w[7];
-
-  // ---- source preparation (App. B.2): b' = gamma5 (b_o + kappa H_oe (M_ee^f)^-1 b_e)
-  double bb = 0.0, bfull = 0.0;
-  if ((st = prepare_source(S, b, be, bo, bp, T, &bb, &bfull)) != TM_OK) return st;
-  if (!std::isfinite(bb) || !std::isfinite(bfull))
-    return set_error(TM_ERR_NONFINITE, "tm_solve_cg: the source has non-finite entries");
-  info->iters = 0;
-  info->reliable_updates = 0;
-  if (bfull == 0.0) {
-    st = cuda_check(cudaMemsetAsync(x, 0, lat->V * 24 * sizeof(double), s), "memset");
-    info->true_rel_residual = 0.0;
-    info->schur_rel_residual = 0.0;
-    info->status = TM_OK;
-    return st;
-  }
   const double tol2 = P.tol * P.tol;
   const double stop2 = tol2 * bb;
   int iters = 0, updates = 0;
   bool converged = false;
   double rr_true = bb;
-  if ((st = cuda_check(cudaMemsetAsync(X, 0, S.hb[TM_F64], s), "memset")) != TM_OK) return st;
+  // starting residual R = b' - A X (X = 0 unless a guess is given)
+  if (guess) {
+    if ((st = true_residual(S, R, X, bp, T, W, &rr_true)) != TM_OK) return st;
+  } else {
+    if ((st = cuda_check(cudaMemsetAsync(X, 0, S.hb[TM_F64], s), "memset")) != TM_OK) return st;
+    if ((st = cuda_check(cudaMemcpyAsync(R, bp, S.hb[TM_F64], cudaMemcpyDeviceToDevice, s), "copy")) != TM_OK)
+      return st;
+  }
+  if (!std::isfinite(rr_true)) return set_error(TM_ERR_NONFINITE, "tm_solve_cg: non-finite initial residual");
+  if (rr_true < stop2) converged = true;
+  const double rr0 = rr_true;
 
   if (P.mode == TM_CG_FP64) {
     // ---- plain FP64 CG, restarted from the recomputed residual if the iterated one drifted
-    if ((st = cuda_check(cudaMemcpyAsync(R, bp, S.hb[TM_F64], cudaMemcpyDeviceToDevice, s), "copy")) != TM_OK)
-      return st;
-    if ((st = cuda_check(cudaMemcpyAsync(Pv, bp, S.hb[TM_F64], cudaMemcpyDeviceToDevice, s), "copy")) != TM_OK)
+    if ((st = cuda_check(cudaMemcpyAsync(Pv, R, S.hb[TM_F64], cudaMemcpyDeviceToDevice, s), "copy")) != TM_OK)
       return st;
     Stage v{TM_F64, 18, TM_F64, X, R, Pv, T, W};
-    double rr = bb;
-    for (;;) {
+    double rr = rr0;
+    while (!converged) {
       CGState fin;
       if ((st = run_stage(S, v, fresh_state(rr, stop2, P.max_iter, iters, 0.0), &fin)) != TM_OK) return st;
       trace_stage("fp64 stage", fin, bb);
@@ -686,12 +675,10 @@ static tm_status solve_one(tm_lattice lat, double* x, const double* b, const tm_
     if (st != TM_OK) return st;
     Stage v{sp, sl, TM_F32, xs, rs, ps, Ts, Ws};
     if ((st = cuda_check(cudaMemsetAsync(xs, 0, S.hb[TM_F32], s), "memset")) != TM_OK) return st;
-    double rr = bb;
-    if (P.mode == TM_CG_SQRT_EPS) {
+    double rr = rr0;
+    if (P.mode == TM_CG_SQRT_EPS && !converged) {
       // FP64 until ||r||^2 < tol ||b'||^2 (i.e. ||r|| / ||b'|| < sqrt(tol)), Sec. 4.4
-      if ((st = cuda_check(cudaMemcpyAsync(R, bp, S.hb[TM_F64], cudaMemcpyDeviceToDevice, s), "copy")) != TM_OK)
-        return st;
-      if ((st = cuda_check(cudaMemcpyAsync(Pv, bp, S.hb[TM_F64], cudaMemcpyDeviceToDevice, s), "copy")) != TM_OK)
+      if ((st = cuda_check(cudaMemcpyAsync(Pv, R, S.hb[TM_F64], cudaMemcpyDeviceToDevice, s), "copy")) != TM_OK)
         return st;
       Stage v64{TM_F64, 18, TM_F64, X, R, Pv, T, W};
       CGState fin;
@@ -728,8 +715,8 @@ static tm_status solve_one(tm_lattice lat, double* x, const double* b, const tm_
         if (fin.diverged && (st = convert_half(lat, sp, ps, TM_F64, R, s)) != TM_OK) return st;
       }
     } else {
-      if ((st = convert_half(lat, TM_F32, rs, TM_F64, bp, s)) != TM_OK) return st;
-      if ((st = convert_half(lat, sp, ps, TM_F64, bp, s)) != TM_OK) return st;
+      if ((st = convert_half(lat, TM_F32, rs, TM_F64, R, s)) != TM_OK) return st;
+      if ((st = convert_half(lat, sp, ps, TM_F64, R, s)) != TM_OK) return st;
     }
     // reliable-update loop (also the defect correction of the sqrt(eps) mode)
     const double delta2 = P.delta * P.delta;
@@ -800,6 +787,46 @@ static tm_status solve_one(tm_lattice lat, double* x, const double* b, const tm_
       rr = rr_true;
     }
   }
+  res->iters = iters;
+  res->updates = updates;
+  res->converged = converged;
+  res->rr_true = rr_true;
+  return TM_OK;
+}
+
+// Solves M^f x = b for one canonical full field (device pointers).
+static tm_status solve_one(tm_lattice lat, double* x, const double* b, const tm_cg_params& P, tm_cg_info* info,
+                           cudaStream_t s) {
+  Solver S{lat, s, P.flavour, 2.0 * lat->kappa * lat->mu, {0, 0, 0, 0}};
+  for (int p = 0; p < 4; ++p) S.hb[p] = spinor_bytes_per_site(p) * lat->h;
+  tm_status st = TM_OK;
+  // FP64 fields: 0 b_e, 1 b_o, 2 b', 3 X, 4 R, 5 P, 6 T, 7 W
+  void* w[8];
+  for (int k = 0; k < 8; ++k) {
+    w[k] = workspace(lat, k, S.hb[TM_F64], &st);
+    if (st != TM_OK) return st;
+  }
+  void *be = w[0], *bo = w[1], *bp = w[2], *X = w[3], *R = w[4], *Pv = w[5], *T = w[6], *W = w[7];
+
+  // ---- source preparation (App. B.2): b' = gamma5 (b_o + kappa H_oe (M_ee^f)^-1 b_e)
+  double bb = 0.0, bfull = 0.0;
+  if ((st = prepare_source(S, b, be, bo, bp, T, &bb, &bfull)) != TM_OK) return st;
+  if (!std::isfinite(bb) || !std::isfinite(bfull))
+    return set_error(TM_ERR_NONFINITE, "tm_solve_cg: the source has non-finite entries");
+  info->iters = 0;
+  info->reliable_updates = 0;
+  if (bfull == 0.0) {
+    st = cuda_check(cudaMemsetAsync(x, 0, lat->V * 24 * sizeof(double), s), "memset");
+    info->true_rel_residual = 0.0;
+    info->schur_rel_residual = 0.0;
+    info->status = TM_OK;
+    return st;
+  }
+  NormalResult nr{};
+  if ((st = cg_normal(S, P, bp, bb, X, false, R, Pv, T, W, &nr)) != TM_OK) return st;
+  const int iters = nr.iters, updates = nr.updates;
+  const bool converged = nr.converged;
+  const double rr_true = nr.rr_true;
   info->iters = iters;
   info->reliable_updates = updates;
   info->schur_rel_residual = std::sqrt(rr_true / bb);

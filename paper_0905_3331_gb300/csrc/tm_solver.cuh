@@ -31,4 +31,12 @@ tm_status reconstruct_check(const Solver& S, const void* X, const void* be, cons
                             void* T, void* W, void* R, void* Pv, double* true_rel);
 tm_status launch_accumulate(const Solver& S, void* X, void* xs);  // X (FP64) += xs (FP32); xs = 0
 
+struct NormalResult {
+  int iters, updates;
+  bool converged;
+  double rr_true;  // ||bp - A X||^2, recomputed in FP64
+};
+tm_status cg_normal(const Solver& S, const tm_cg_params& P, const void* bp, double bb, void* X, bool guess, void* R,
+                    void* Pv, void* T, void* W, NormalResult* res);
+
 }  // namespace tmq

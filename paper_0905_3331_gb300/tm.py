@@ -94,6 +94,8 @@ def load():
         "tm_solve_cg_batch": ([ctypes.POINTER(TmSystem), I, ctypes.POINTER(CGParams),
                                ctypes.POINTER(CGInfo), P], I),
         "tm_meson_contract": ([P, P, P, P], I),
+        "tm_solve_normal": ([P, P, P, ctypes.POINTER(CGParams), ctypes.POINTER(CGInfo), P], I),
+        "tm_chrono_guess": ([P, P, ctypes.POINTER(P), I, P, I, P], I),
         "tm_last_error": ([], ctypes.c_char_p),
         "tm_launch_count": ([], ctypes.c_ulonglong),
         "tm_reset_launch_count": ([], None),
@@ -111,7 +113,7 @@ def exported_symbols():
     return ["tm_lattice_create", "tm_lattice_destroy", "tm_lattice_set_params", "tm_volume",
             "tm_half_field_bytes", "tm_set_hop_threads", "tm_get_hop_threads", "tm_set_gauge", "tm_pack_half", "tm_unpack_half", "tm_apply_D",
             "tm_apply_hopping_eo", "tm_apply_Mee_inv", "tm_solve_cg", "tm_solve_cg_batch",
-            "tm_cg_params_default", "tm_meson_contract",
+            "tm_cg_params_default", "tm_meson_contract", "tm_solve_normal", "tm_chrono_guess",
             "tm_last_error", "tm_launch_count", "tm_reset_launch_count"]
 
 
@@ -267,6 +269,31 @@ class Lattice:
         d = info.as_dict()
         d["status"] = st
         return SolveInfo(**d)
+
+    def solve_normal(self, X, phi, tol: float = 1e-10, max_iter: int = 100000,
+                     mode: int = CG_FP64, sloppy_prec: int = F32, sloppy_link: int = LINK12,
+                     delta: float = 0.1, use_x0: bool = False, flavour: int = 1,
+                     update_prec: int = F64, stream=None, check: bool = True) -> SolveInfo:
+        """Solve Qhat^f Qhat^-f X = phi (FP64 odd half fields on the device); with use_x0 the
+        content of X is the initial guess."""
+        p = CGParams(tol, max_iter, mode, sloppy_prec, sloppy_link, delta, int(use_x0), flavour,
+                     update_prec)
+        info = CGInfo()
+        st = load().tm_solve_normal(self._h, _addr(X), _addr(phi), ctypes.byref(p),
+                                    ctypes.byref(info), _stream(stream))
+        if check:
+            _check(st, "tm_solve_normal")
+        d = info.as_dict()
+        d["status"] = st
+        return SolveInfo(**d)
+
+    def chrono_guess(self, X0, chi, phi, flavour: int = 1, stream=None):
+        """X0 = sum_i c_i chi_i with the c_i of the chronological guess (Galerkin condition on
+        Qhat^f Qhat^-f); chi is a list of FP64 odd half fields on the device."""
+        n = len(chi)
+        arr = (ctypes.c_void_p * max(n, 1))(*[_addr(c) for c in chi])
+        _check(load().tm_chrono_guess(self._h, _addr(X0), arr, n, _addr(phi), flavour,
+                                      _stream(stream)), "tm_chrono_guess")
 
 
 def solve_cg_batch(systems, tol: float = 1e-10, max_iter: int = 100000, sloppy_prec: int = F32,

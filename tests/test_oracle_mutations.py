@@ -95,3 +95,37 @@ def test_the_unmutated_copy_passes_every_pin(tmp_path, monkeypatch):
     monkeypatch.setattr(oracle, "_lib", variant)
     for pin, call in PIN_CALLS:
         call()
+
+
+# The chronological guess is plain numpy in oracle/__init__.py: its mistakes are planted in a
+# copy of that function's source, and the chronological-guess pins must catch each.
+CHRONO_MUTATIONS = [
+    ("Galerkin matrix transposed", "G[j, i] = np.vdot(chis[j], Achi[i])", "G[i, j] = np.vdot(chis[j], Achi[i])"),
+    ("right-hand side conjugated", "np.vdot(chis[j], phi)", "np.vdot(phi, chis[j])"),
+    ("operator of the other flavour", "normal_op(lat, U, chi, kappa, mu, f)", "normal_op(lat, U, chi, kappa, mu, -f)"),
+    ("coefficients conjugated in the guess", "X0 += c[i] * chis[i]", "X0 += np.conj(c[i]) * chis[i]"),
+]
+
+CHRONO_PINS = [
+    ("exact on span", lambda: pins.test_chrono_guess_is_exact_on_its_span()),
+    ("krylov = cg", lambda: pins.test_chrono_guess_with_a_krylov_history_is_the_cg_iterate()),
+    ("minimises", lambda: pins.test_chrono_guess_minimises_the_error_functional()),
+]
+
+
+@pytest.mark.parametrize("name,old,new", CHRONO_MUTATIONS, ids=[m[0] for m in CHRONO_MUTATIONS])
+def test_a_planted_mistake_in_the_chrono_guess_fails_a_pin(name, old, new, monkeypatch):
+    import inspect
+    import textwrap
+    src = textwrap.dedent(inspect.getsource(oracle.chrono_guess))
+    assert src.count(old) == 1, f"mutation site not found: {old}"
+    ns = dict(vars(oracle))
+    exec(compile(src.replace(old, new), "<mutated chrono_guess>", "exec"), ns)
+    monkeypatch.setattr(oracle, "chrono_guess", ns["chrono_guess"])
+    failed = []
+    for pin, call in CHRONO_PINS:
+        try:
+            call()
+        except Exception:
+            failed.append(pin)
+    assert failed, f"no pin caught: {name}"

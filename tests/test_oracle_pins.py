@@ -367,7 +367,7 @@ def test_sampled_sites_match_full_application():
     assert np.array_equal(part, full[sites])
 
 
-# ------------------------------------------------------ correlators (Sec. 4.5) ---
+# ------------------------------------------------------ correlators (Sec. 4.3) ---
 def test_free_field_pion_correlator_from_momentum_space():
     """C_PP(t) = sum_x ||G(x,0)||^2 of the oracle's 12 point-source solves on a unit gauge field
     equals the closed form G(x,0) = (1/V) sum_p e^{ipx} M(p)^-1, M(p) = (1 - 2k sum cos p)
@@ -400,3 +400,70 @@ def test_free_field_pion_correlator_from_momentum_space():
     # the point-source propagator itself, spin block of colour 0, at every site
     Gsolve = np.stack(props).reshape(4, 3, T, L, L, L, 4, 3)[:, 0, ..., 0]  # [s_src, ..., s_sink]
     assert np.allclose(np.moveaxis(Gsolve, 0, -1), G, rtol=0, atol=1e-10)
+
+
+# ------------------------------------------- chronological guess (Sec. 4.2) ---
+def _odd(lat, seed):
+    return np.where(lat.parity_mask()[..., None, None], rand_spinor(lat, seed), 0)
+
+
+def test_chrono_guess_is_exact_on_its_span():
+    """phi = A X* with X* = sum_i a_i chi_i: the Galerkin system has the unique solution a,
+    so the guess reproduces X* and the coefficients a."""
+    lat = Lattice.cubic(4, 2)
+    U = inputs.random_gauge(4, 2, 0.5, seed=91)
+    kappa, mu = 0.16, 0.04
+    chis = [_odd(lat, 92 + i) for i in range(4)]
+    a = np.array([0.7 - 0.2j, -1.1 + 0.4j, 0.05j, 2.0])
+    Xs = sum(ai * c for ai, c in zip(a, chis))
+    phi = oracle.normal_op(lat, U, Xs, kappa, mu, f=-1)
+    X0, c = oracle.chrono_guess(lat, U, chis, phi, kappa, mu, f=-1)
+    assert np.allclose(c, a, rtol=0, atol=1e-11)
+    assert rel(X0, Xs) < 1e-11
+
+
+def test_chrono_guess_with_a_krylov_history_is_the_cg_iterate():
+    """CG from X = 0 minimises the A-norm of the error over the Krylov space
+    span{phi, A phi, ..., A^(k-1) phi}; the guess minimises the same functional over the span
+    of its history, so with that Krylov basis as history it equals the k-th CG iterate."""
+    lat = Lattice.cubic(4, 2)
+    U = inputs.random_gauge(4, 2, 0.6, seed=93)
+    kappa, mu = 0.15, 0.03
+    phi = _odd(lat, 94)
+    for k in (1, 3):
+        basis = [phi]
+        for _ in range(k - 1):
+            v = oracle.normal_op(lat, U, basis[-1], kappa, mu)
+            basis.append(v / np.linalg.norm(v))
+        X0, _ = oracle.chrono_guess(lat, U, basis, phi, kappa, mu)
+        res = oracle.cg(lat, U, phi, kappa, mu, tol=1e-30, max_iter=k)
+        assert res.iters == k
+        assert rel(X0, res.x) < 1e-9
+
+
+def test_chrono_guess_minimises_the_error_functional():
+    """Galerkin orthogonality <chi_j, phi - A X0> = 0 for every j, and every other
+    combination of the history has a larger A-norm error than X0 (dense solve for X*)."""
+    lat = Lattice.cubic(2, 2)
+    U = inputs.random_gauge(2, 2, 0.5, seed=95)
+    kappa, mu = 0.16, 0.05
+    o = component_mask(lat, 1)
+    A = dense_from(lambda v: oracle.normal_op(lat, U, v, kappa, mu), lat, rows_mask=o, cols_mask=o)
+    phi = _odd(lat, 96)
+    chis = [_odd(lat, 97 + i) for i in range(3)]
+    X0, c = oracle.chrono_guess(lat, U, chis, phi, kappa, mu)
+    r = phi.reshape(-1)[o] - A @ X0.reshape(-1)[o]
+    for chi in chis:
+        assert abs(np.vdot(chi.reshape(-1)[o], r)) < 1e-11 * np.linalg.norm(phi)
+    Xs = np.linalg.solve(A, phi.reshape(-1)[o])
+    B = np.stack([chi.reshape(-1)[o] for chi in chis], axis=1)
+
+    def err(cc):
+        e = B @ cc - Xs
+        return np.vdot(e, A @ e).real
+
+    e0 = err(c)
+    rng = np.random.default_rng(98)
+    for _ in range(20):
+        d = 1e-3 * (rng.standard_normal(3) + 1j * rng.standard_normal(3))
+        assert err(c + d) > e0
