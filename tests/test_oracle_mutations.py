@@ -56,6 +56,15 @@ MUTATIONS = [
     ("CG direction update without beta",
      "for (long i = 0; i < n; ++i) p[i] = r[i] + beta * p[i];",
      "for (long i = 0; i < n; ++i) p[i] = r[i];"),
+    ("BiCGstab omega conjugated", "cplx omega = tt > 0 ? dot(n, t, s) / tt : 0;",
+     "cplx omega = tt > 0 ? dot(n, s, t) / tt : 0;"),
+    ("BiCGstab beta without alpha / omega", "cplx beta = (rho_new / rho) * (alpha / omega);",
+     "cplx beta = (rho_new / rho);"),
+    ("BiCGstab direction update without omega v",
+     "p[i] = r[i] + beta * (p[i] - omega * v[i]);", "p[i] = r[i] + beta * p[i];"),
+    ("BiCGstab on Qhat instead of Mhat", "orc_schur(dims, theta, spread, kappa, mu, f, U, p, v, 0);",
+     "orc_schur(dims, theta, spread, kappa, mu, f, U, p, v, 1);"),
+    ("BiCGstab shadow residual not conjugated", "cplx rv = dot(n, rh, v);", "cplx rv = dot(n, v, rh);"),
 ]
 
 # the pins, at their smallest sizes
@@ -71,6 +80,8 @@ PIN_CALLS = [
     ("schur dense", lambda: pins.test_schur_operator_is_the_dense_schur_complement(2, 2)),
     ("solve dense", lambda: pins.test_even_odd_solve_equals_dense_solve(2, 2)),
     ("cg dense", lambda: pins.test_cg_on_normal_equations_matches_dense()),
+    ("bicgstab = scipy", lambda: pins.test_bicgstab_iterates_match_scipy()),
+    ("bicgstab dense", lambda: pins.test_bicgstab_solve_equals_dense_solve(2, 2)),
 ]
 
 

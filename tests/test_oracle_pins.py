@@ -467,3 +467,52 @@ def test_chrono_guess_minimises_the_error_functional():
     for _ in range(20):
         d = 1e-3 * (rng.standard_normal(3) + 1j * rng.standard_normal(3))
         assert err(c + d) > e0
+
+
+# ------------------------------------------------- BiCGstab on Mhat (Sec. 4.4) ---
+def test_bicgstab_iterates_match_scipy():
+    """The oracle's BiCGstab on the Schur operator produces the same iterates as SciPy's
+    bicgstab (a library routine) on the dense Schur matrix, iteration by iteration."""
+    from scipy.sparse.linalg import bicgstab as scipy_bicgstab
+    lat = Lattice.cubic(4, 2)
+    U = inputs.random_gauge(4, 2, 0.5, seed=101)
+    kappa, mu = 0.15, 0.05
+    o = component_mask(lat, 1)
+    Mh = dense_from(lambda v: oracle.schur(lat, U, v, kappa, mu, f=-1), lat, rows_mask=o, cols_mask=o)
+    b = _odd(lat, 102)
+    iterates = []
+    scipy_bicgstab(Mh, b.reshape(-1)[o], rtol=1e-30, atol=0.0, maxiter=6,
+                   callback=lambda xk: iterates.append(np.array(xk)))
+    assert len(iterates) == 6
+    for k in (1, 2, 3, 6):
+        res = oracle.bicgstab(lat, U, b, kappa, mu, f=-1, tol=1e-30, max_iter=k)
+        assert res.iters == k
+        assert rel(res.x.reshape(-1)[o], iterates[k - 1]) < 1e-12, k
+
+
+@pytest.mark.parametrize("T,L", [(2, 2), (4, 2)])
+def test_bicgstab_solve_equals_dense_solve(T, L):
+    """Even/odd + BiCGstab on Mhat gives the solution of the dense full system M psi = phi,
+    for both flavours, and the same solution as the CG path."""
+    lat = Lattice.cubic(T, L)
+    U = inputs.random_gauge(T, L, 0.5, seed=103)
+    kappa, mu = 0.16, 0.04
+    phi = rand_spinor(lat, 104)
+    for f in (1, -1):
+        M = dense_from(lambda v: oracle.apply_M(lat, U, v, kappa, mu, f), lat)
+        psi = np.linalg.solve(M, phi.reshape(-1))
+        res = oracle.solve_bicgstab(lat, U, phi, kappa, mu, f, tol=1e-12)
+        assert res.converged and res.relres_full < 1e-11
+        assert rel(res.psi.reshape(-1), psi) < 1e-10
+        cg = oracle.solve(lat, U, phi, kappa, mu, f, tol=1e-12)
+        assert rel(res.psi, cg.psi) < 1e-10
+
+
+def test_bicgstab_reaches_tolerance_on_4x4x4x4():
+    w = inputs.WORKLOADS["4^4"]
+    lat = Lattice.cubic(w.T, w.L)
+    U, phi = w.gauge(), w.source()
+    res = oracle.solve_bicgstab(lat, U, phi, w.kappa, w.mu, tol=1e-10)
+    assert res.converged and res.relres_full < 1e-10
+    resid = phi - oracle.apply_M(lat, U, res.psi, w.kappa, w.mu)
+    assert np.linalg.norm(resid) / np.linalg.norm(phi) < 1e-10
