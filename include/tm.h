@@ -204,6 +204,23 @@ typedef struct {
 tm_status tm_solve_cg(tm_lattice lat, double *x, const double *b, int nrhs,
                       const tm_cg_params *params, tm_cg_info *info, void *stream);
 
+/* Solves M(f) x = b like tm_solve_cg, with the stabilised bi-conjugate gradient method
+ * (BiCGstab, one of the solvers of Sec. 4.4) applied directly to the non-hermitian Schur
+ * system of eq. eo4 instead of CG on the normal equations:
+ *   Mhat^f x_o = varphi_o,  Mhat^f = (1 + i f mu~ gamma5) - kappa^2 H_oe (M_ee^f)^{-1} H_eo,
+ * varphi_o = b_o - M_oe (M_ee^f)^{-1} b_e, x_e = (M_ee^f)^{-1}(b_e - M_eo x_o) (App. B.2).
+ * One iteration applies Mhat twice, the cost of one CG iteration on Qhat^f Qhat^-f.
+ * Arguments, staging, nrhs and use_x0 as tm_solve_cg; params->mode TM_CG_FP64 (BiCGstab in
+ * FP64, restarted from the recomputed residual if the iterated one drifted) or TM_CG_RELIABLE
+ * (sloppy storage and FP32 arithmetic with FP64 reliable updates every factor delta; p and
+ * the shadow residual carry across updates); max_iter counts BiCGstab iterations.  tol is
+ * relative to ||varphi_o|| (info->schur_rel_residual) and the full-lattice residual is
+ * reported as in tm_solve_cg.  Breakdowns (a vanishing <r^, v>, omega or rho) restart the
+ * method from the FP64 residual.
+ * Errors: as tm_solve_cg, plus TM_ERR_UNSUPPORTED for TM_CG_SQRT_EPS or TM_DF64 updates. */
+tm_status tm_solve_bicgstab(tm_lattice lat, double *x, const double *b, int nrhs,
+                            const tm_cg_params *params, tm_cg_info *info, void *stream);
+
 /* One system of a batched solve: M(f; mu) x = b on the lattice `lat` (its gauge field and
  * kappa), with this system's own bare twisted mass mu (mu~ = 2 kappa mu). */
 typedef struct {

@@ -873,6 +873,13 @@ struct tm_lattice_s {
     cudaGraphExec_t exec;
   } graphs[8];
   int graph_next;           // round-robin replacement slot
+  struct AuxGraph {         // graphs of the other solvers' stage loops, keyed by 16 words
+    bool valid;
+    unsigned long long key[16];
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+  } aux_graphs[8];
+  int aux_next;
 };
 
 namespace tmq {
@@ -919,9 +926,10 @@ tm_status apply_M_halves(tm_lattice lat, void* out_e, void* out_o, const void* i
                          cudaStream_t s);
 tm_status diag_apply(tm_lattice lat, int prec, void* out, const void* in, int nrhs, double dur, double dui,
                      double dlr, double dli, cudaStream_t s);
-// Workspace slots: 0..17 solver, 22..25 tm_apply_D, 26 staged input, 27 staged output,
-// 28 initial-guess work space, 29 contraction partials, 30 chronological-guess scalars.
-enum { WS_APPLY_D = 22, WS_STAGE_IN = 26, WS_STAGE_OUT = 27, WS_X0 = 28, WS_CHRONO = 30 };
+// Workspace slots: 0..17 CG solver, 22..25 tm_apply_D, 26 staged input, 27 staged output,
+// 28 initial-guess work space, 29 contraction partials, 30 chronological-guess scalars,
+// 31 BiCGstab state; 18..20 BiCGstab vectors.
+enum { WS_APPLY_D = 22, WS_STAGE_IN = 26, WS_STAGE_OUT = 27, WS_X0 = 28, WS_CHRONO = 30, WS_BISTATE = 31 };
 // host-buffer staging through workspace slots
 const void* stage_in(tm_lattice lat, int slot, const void* src, size_t bytes, cudaStream_t s, tm_status* st);
 void* stage_out(tm_lattice lat, int slot, void* dst, size_t bytes, tm_status* st);

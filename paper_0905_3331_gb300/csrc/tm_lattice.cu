@@ -327,12 +327,18 @@ static tm_status tune_hop(tm_lattice lat, int prec, int nreal, cudaStream_t s) {
 }
 
 void invalidate_graphs(tm_lattice lat) {
-  for (int k = 0; k < 8; ++k)
+  for (int k = 0; k < 8; ++k) {
     if (lat->graphs[k].valid) {
       cudaGraphExecDestroy(lat->graphs[k].exec);
       cudaGraphDestroy(lat->graphs[k].graph);
       lat->graphs[k].valid = false;
     }
+    if (lat->aux_graphs[k].valid) {
+      cudaGraphExecDestroy(lat->aux_graphs[k].exec);
+      cudaGraphDestroy(lat->aux_graphs[k].graph);
+      lat->aux_graphs[k].valid = false;
+    }
+  }
 }
 
 tm_status hop_launch(tm_lattice lat, const HopArgs& a, cudaStream_t s) {

@@ -293,7 +293,7 @@ static tm_status enqueue_iterations(const Solver& S, const Stage& v, CGState* ds
   return st;
 }
 
-static bool use_graphs() {
+bool use_graphs() {
   static int v = -1;
   if (v < 0) {
     const char* e = getenv("TM_NO_GRAPH");
@@ -547,7 +547,6 @@ tm_status prepare_source(const Solver& S, const double* b, void* be, void* bo, v
 tm_status reconstruct_check(const Solver& S, const void* X, const void* be, const void* bo, double bfull, double* x,
                             void* T, void* W, void* R, void* Pv, double* true_rel) {
   tm_lattice lat = S.lat;
-  cudaStream_t s = S.s;
   tm_status st;
   HopArgs a{};
   a.prec = TM_F64;
@@ -557,13 +556,28 @@ tm_status reconstruct_check(const Solver& S, const void* X, const void* be, cons
   a.in = X;
   a.out = T;
   a.coef = epi_mdiag_inv_hop(S.mut, -S.f);
-  if ((st = hop_launch(lat, a, s)) != TM_OK) return st;
+  if ((st = hop_launch(lat, a, S.s)) != TM_OK) return st;
   a.out_parity = 1;
   a.in = T;
   a.y = X;
   a.out = W;  // x_o
   a.coef = epi_schur_q(lat->kappa, S.mut, -S.f);
-  if ((st = hop_launch(lat, a, s)) != TM_OK) return st;
+  if ((st = hop_launch(lat, a, S.s)) != TM_OK) return st;
+  return reconstruct_xo(S, W, be, bo, bfull, x, T, R, Pv, true_rel);
+}
+
+// x_e = (M_ee^f)^-1 (b_e + kappa H_eo x_o) from the odd solution xo, written with xo to the
+// canonical field x; then ||b - M x|| / ||b|| in FP64 (T, R, Pv are FP64 scratch).
+tm_status reconstruct_xo(const Solver& S, const void* xo, const void* be, const void* bo, double bfull, double* x,
+                         void* T, void* R, void* Pv, double* true_rel) {
+  tm_lattice lat = S.lat;
+  cudaStream_t s = S.s;
+  tm_status st;
+  void* W = const_cast<void*>(xo);
+  HopArgs a{};
+  a.prec = TM_F64;
+  a.nreal = 18;
+  a.nrhs = 1;
   a.out_parity = 0;
   a.in = W;
   a.y = be;
@@ -861,29 +875,43 @@ void tm_cg_params_default(tm_cg_params* p) {
 
 tm_status tm_solve_cg(tm_lattice lat, double* x, const double* b, int nrhs, const tm_cg_params* params,
                       tm_cg_info* info, void* stream) {
+  return solve_driver(lat, x, b, nrhs, params, info, stream, SOLVER_CG);
+}
+
+}  // extern "C"
+
+namespace tmq {
+
+// Validation, host staging, the loop over right-hand sides and the defect correction from an
+// initial guess, shared by tm_solve_cg and tm_solve_bicgstab.
+tm_status solve_driver(tm_lattice lat, double* x, const double* b, int nrhs, const tm_cg_params* params,
+                       tm_cg_info* info, void* stream, int kind) {
   const auto t0 = std::chrono::steady_clock::now();
-  if (!lat || !x || !b || nrhs < 1) return set_error(TM_ERR_ARG, "tm_solve_cg: bad argument");
-  if (!lat->has_gauge) return set_error(TM_ERR_NO_GAUGE, "tm_solve_cg: no gauge field");
+  const char* nm = kind == SOLVER_CG ? "tm_solve_cg" : "tm_solve_bicgstab";
+  if (!lat || !x || !b || nrhs < 1) return set_error(TM_ERR_ARG, "%s: bad argument", nm);
+  if (!lat->has_gauge) return set_error(TM_ERR_NO_GAUGE, "%s: no gauge field", nm);
   tm_cg_params P;
   if (params)
     P = *params;
   else
     tm_cg_params_default(&P);
   if (P.flavour == 0) P.flavour = 1;
-  if (P.flavour != 1 && P.flavour != -1) return set_error(TM_ERR_ARG, "tm_solve_cg: flavour must be +1 or -1");
-  if (!(P.tol > 0.0) || P.max_iter < 1) return set_error(TM_ERR_ARG, "tm_solve_cg: tol > 0 and max_iter >= 1");
-  if (P.mode < TM_CG_FP64 || P.mode > TM_CG_RELIABLE) return set_error(TM_ERR_ARG, "tm_solve_cg: mode %d", P.mode);
+  if (P.flavour != 1 && P.flavour != -1) return set_error(TM_ERR_ARG, "%s: flavour must be +1 or -1", nm);
+  if (!(P.tol > 0.0) || P.max_iter < 1) return set_error(TM_ERR_ARG, "%s: tol > 0 and max_iter >= 1", nm);
+  if (P.mode < TM_CG_FP64 || P.mode > TM_CG_RELIABLE) return set_error(TM_ERR_ARG, "%s: mode %d", nm, P.mode);
   if (P.mode != TM_CG_FP64) {
     if (P.sloppy_prec != TM_F32 && P.sloppy_prec != TM_F16)
-      return set_error(TM_ERR_ARG, "tm_solve_cg: sloppy precision must be TM_F32 or TM_F16");
+      return set_error(TM_ERR_ARG, "%s: sloppy precision must be TM_F32 or TM_F16", nm);
     if (P.sloppy_link != 18 && P.sloppy_link != 12 && P.sloppy_link != 8)
-      return set_error(TM_ERR_ARG, "tm_solve_cg: sloppy link format %d", P.sloppy_link);
-    if (!(P.delta > 0.0 && P.delta < 1.0)) return set_error(TM_ERR_ARG, "tm_solve_cg: delta must be in (0, 1)");
+      return set_error(TM_ERR_ARG, "%s: sloppy link format %d", nm, P.sloppy_link);
+    if (!(P.delta > 0.0 && P.delta < 1.0)) return set_error(TM_ERR_ARG, "%s: delta must be in (0, 1)", nm);
     if (P.update_prec != TM_F64 && P.update_prec != TM_DF64)
-      return set_error(TM_ERR_ARG, "tm_solve_cg: update_prec must be TM_F64 or TM_DF64");
+      return set_error(TM_ERR_ARG, "%s: update_prec must be TM_F64 or TM_DF64", nm);
   }
+  if (kind != SOLVER_CG && (P.mode == TM_CG_SQRT_EPS || (P.mode == TM_CG_RELIABLE && P.update_prec != TM_F64)))
+    return set_error(TM_ERR_UNSUPPORTED, "%s: modes TM_CG_FP64 and TM_CG_RELIABLE with FP64 updates only", nm);
   const size_t fbytes = lat->V * 24 * sizeof(double);
-  if (x == b) return set_error(TM_ERR_ARG, "tm_solve_cg: x and b must differ");
+  if (x == b) return set_error(TM_ERR_ARG, "%s: x and b must differ", nm);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   tm_status st;
   const double* db = static_cast<const double*>(stage_in(lat, WS_STAGE_IN, b, fbytes * nrhs, s, &st));
@@ -912,7 +940,7 @@ tm_status tm_solve_cg(tm_lattice lat, double* x, const double* b, int nrhs, cons
       if ((st = tm_apply_D(lat, r0, xr, P.flavour, 0, 1, stream)) != TM_OK) return st;
       axpby_kernel<<<nb, BNT, 0, s>>>(n, 1.0, br, -1.0, r0);  // r0 = b - M x0
       count_launch();
-      st = solve_one(lat, delta, r0, P, &one, s);
+      st = kind == SOLVER_CG ? solve_one(lat, delta, r0, P, &one, s) : solve_one_bicgstab(lat, delta, r0, P, &one, s);
       if (st != TM_OK && st != TM_ERR_NOT_CONVERGED) return st;
       axpby_kernel<<<nb, BNT, 0, s>>>(n, 1.0, delta, 1.0, xr);  // x = x0 + delta
       count_launch();
@@ -930,7 +958,7 @@ tm_status tm_solve_cg(tm_lattice lat, double* x, const double* b, int nrhs, cons
         one.true_rel_residual = den > 0 ? std::sqrt(num / den) : 0.0;
       }
     } else {
-      st = solve_one(lat, xr, br, P, &one, s);
+      st = kind == SOLVER_CG ? solve_one(lat, xr, br, P, &one, s) : solve_one_bicgstab(lat, xr, br, P, &one, s);
     }
     if (st != TM_OK && st != TM_ERR_NOT_CONVERGED) return st;
     if (st == TM_ERR_NOT_CONVERGED) result = st;
@@ -940,11 +968,11 @@ tm_status tm_solve_cg(tm_lattice lat, double* x, const double* b, int nrhs, cons
   if (dx != x) {
     if ((st = stage_out_finish(x, dx, fbytes * nrhs, s)) != TM_OK) return st;
   }
-  if ((st = cuda_check(cudaStreamSynchronize(s), "tm_solve_cg: synchronise")) != TM_OK) return st;
+  if ((st = cuda_check(cudaStreamSynchronize(s), "solve: synchronise")) != TM_OK) return st;
   worst.status = result;
   worst.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (info) *info = worst;
   return result;
 }
 
-}  // extern "C"
+}  // namespace tmq

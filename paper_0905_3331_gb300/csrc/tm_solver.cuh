@@ -29,6 +29,8 @@ tm_status prepare_source(const Solver& S, const double* b, void* be, void* bo, v
                          double* bfull);
 tm_status reconstruct_check(const Solver& S, const void* X, const void* be, const void* bo, double bfull, double* x,
                             void* T, void* W, void* R, void* Pv, double* true_rel);
+tm_status reconstruct_xo(const Solver& S, const void* xo, const void* be, const void* bo, double bfull, double* x,
+                         void* T, void* R, void* Pv, double* true_rel);
 tm_status launch_accumulate(const Solver& S, void* X, void* xs);  // X (FP64) += xs (FP32); xs = 0
 
 struct NormalResult {
@@ -38,5 +40,14 @@ struct NormalResult {
 };
 tm_status cg_normal(const Solver& S, const tm_cg_params& P, const void* bp, double bb, void* X, bool guess, void* R,
                     void* Pv, void* T, void* W, NormalResult* res);
+
+bool use_graphs();  // CUDA-graph stage loops (TM_NO_GRAPH=1 selects host-driven chunks)
+
+enum { SOLVER_CG = 0, SOLVER_BICGSTAB = 1 };
+tm_status solve_driver(tm_lattice lat, double* x, const double* b, int nrhs, const tm_cg_params* params,
+                       tm_cg_info* info, void* stream, int kind);
+// BiCGstab on Mhat^f x_o = varphi_o for one canonical full field (tm_bicgstab.cu)
+tm_status solve_one_bicgstab(tm_lattice lat, double* x, const double* b, const tm_cg_params& P, tm_cg_info* info,
+                             cudaStream_t s);
 
 }  // namespace tmq

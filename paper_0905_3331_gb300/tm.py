@@ -94,6 +94,7 @@ def load():
         "tm_solve_cg_batch": ([ctypes.POINTER(TmSystem), I, ctypes.POINTER(CGParams),
                                ctypes.POINTER(CGInfo), P], I),
         "tm_meson_contract": ([P, P, P, P], I),
+        "tm_solve_bicgstab": ([P, P, P, I, ctypes.POINTER(CGParams), ctypes.POINTER(CGInfo), P], I),
         "tm_solve_normal": ([P, P, P, ctypes.POINTER(CGParams), ctypes.POINTER(CGInfo), P], I),
         "tm_chrono_guess": ([P, P, ctypes.POINTER(P), I, P, I, P], I),
         "tm_last_error": ([], ctypes.c_char_p),
@@ -113,7 +114,7 @@ def exported_symbols():
     return ["tm_lattice_create", "tm_lattice_destroy", "tm_lattice_set_params", "tm_volume",
             "tm_half_field_bytes", "tm_set_hop_threads", "tm_get_hop_threads", "tm_set_gauge", "tm_pack_half", "tm_unpack_half", "tm_apply_D",
             "tm_apply_hopping_eo", "tm_apply_Mee_inv", "tm_solve_cg", "tm_solve_cg_batch",
-            "tm_cg_params_default", "tm_meson_contract", "tm_solve_normal", "tm_chrono_guess",
+            "tm_cg_params_default", "tm_meson_contract", "tm_solve_bicgstab", "tm_solve_normal", "tm_chrono_guess",
             "tm_last_error", "tm_launch_count", "tm_reset_launch_count"]
 
 
@@ -266,6 +267,22 @@ class Lattice:
                                 ctypes.byref(info), _stream(stream))
         if check:
             _check(st, "tm_solve_cg")
+        d = info.as_dict()
+        d["status"] = st
+        return SolveInfo(**d)
+
+    def solve_bicgstab(self, x, b, nrhs: int = 1, tol: float = 1e-10, max_iter: int = 100000,
+                       mode: int = CG_FP64, sloppy_prec: int = F32, sloppy_link: int = LINK12,
+                       delta: float = 0.1, use_x0: bool = False, flavour: int = 1, stream=None,
+                       check: bool = True) -> SolveInfo:
+        """Solve M^f x = b with BiCGstab on the even/odd Schur system (iters = BiCGstab
+        iterations, two Schur applications each)."""
+        p = CGParams(tol, max_iter, mode, sloppy_prec, sloppy_link, delta, int(use_x0), flavour, F64)
+        info = CGInfo()
+        st = load().tm_solve_bicgstab(self._h, _addr(x), _addr(b), nrhs, ctypes.byref(p),
+                                      ctypes.byref(info), _stream(stream))
+        if check:
+            _check(st, "tm_solve_bicgstab")
         d = info.as_dict()
         d["status"] = st
         return SolveInfo(**d)

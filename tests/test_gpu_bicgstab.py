@@ -1,0 +1,190 @@
+"""GPU BiCGstab on the even/odd Schur system against the CPU oracle (through the C ABI).
+
+The bar is the same as for CG: the FP64 true residual ||phi - M x|| / ||phi||, recomputed by
+the ORACLE's operator on the GPU solution, is below 1e-10; on small lattices the solution is
+also compared element by element with the oracle's own even/odd BiCGstab solve.
+
+BiCGstab converges where the spectrum of Mhat lies in Re > 0.  On the synthetic gauge fields
+that holds at kappa = 0.13 (dense spectrum of the 4^4 Schur matrix: min Re 0.19), not at the
+workloads' own kappa 0.16 - 0.1632, where some eigenvalues have Re < 0 and BiCGstab stagnates
+(checked below: it stops cleanly with TM_ERR_NOT_CONVERGED).  The tests therefore run the
+workloads' gauge fields and sources at KAPPA = 0.13.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0905_3331_gb300 import (CG_FP64, CG_RELIABLE, CG_SQRT_EPS, DF64, F16, F32, LINK8, LINK12,
+                                   LINK18, Lattice, TMError, inputs)
+
+from _util import rel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+MODES = [
+    ("fp64", dict(mode=CG_FP64)),
+    ("reliable_f32_18", dict(mode=CG_RELIABLE, sloppy_prec=F32, sloppy_link=LINK18)),
+    ("reliable_f32_12", dict(mode=CG_RELIABLE, sloppy_prec=F32, sloppy_link=LINK12)),
+    ("reliable_f16_12", dict(mode=CG_RELIABLE, sloppy_prec=F16, sloppy_link=LINK12)),
+    ("reliable_f16_8", dict(mode=CG_RELIABLE, sloppy_prec=F16, sloppy_link=LINK8)),
+]
+
+
+def dev():
+    return torch.device("cuda:0")
+
+
+KAPPA = 0.13
+
+
+def oracle_true_residual(w, U, phi, x, f=1, kappa=KAPPA):
+    olat = oracle.Lattice.cubic(w.T, w.L)
+    r = phi - oracle.apply_M(olat, U, x, kappa, w.mu if f == 1 else -w.mu)
+    return np.linalg.norm(r) / np.linalg.norm(phi)
+
+
+def setup(name, kappa=KAPPA):
+    w = inputs.WORKLOADS[name]
+    U, phi = w.gauge(), w.source()
+    lat = Lattice(w.T, w.L, kappa, w.mu)
+    lat.set_gauge(torch.from_numpy(U).to(dev()))
+    return w, U, phi, lat
+
+
+@pytest.mark.parametrize("name,kw", MODES)
+@pytest.mark.parametrize("flavour", [1, -1])
+def test_bicgstab_4x4x4x4(name, kw, flavour):
+    w, U, phi, lat = setup("4^4")
+    b = torch.from_numpy(phi).to(dev())
+    x = torch.zeros_like(b)
+    info = lat.solve_bicgstab(x, b, tol=1e-10, flavour=flavour, **kw)
+    assert oracle_true_residual(w, U, phi, x.cpu().numpy(), flavour) < 1e-10
+    assert info.true_rel_residual < 1e-10 and info.schur_rel_residual < 1e-10 and info.iters > 0
+    # agreement with the oracle's own even/odd BiCGstab solve (both at 1e-12)
+    lat.solve_bicgstab(x, b, tol=1e-12, flavour=flavour, **kw)
+    ref = oracle.solve_bicgstab(oracle.Lattice.cubic(w.T, w.L), U, phi, KAPPA, w.mu, flavour, tol=1e-12)
+    assert ref.converged and rel(x.cpu().numpy(), ref.psi) < 1e-9
+    lat.close()
+
+
+@pytest.mark.parametrize("name,kw", [MODES[0], MODES[2], MODES[3]])
+@pytest.mark.parametrize("workload", ["8^4", "12^3x24", "16^3x32"])
+def test_bicgstab_larger_lattices(name, kw, workload):
+    """12^3 x 24 has h = 20736 odd sites, not a multiple of the 256-thread vector blocks."""
+    w, U, phi, lat = setup(workload)
+    b = torch.from_numpy(phi).to(dev())
+    x = torch.zeros_like(b)
+    info = lat.solve_bicgstab(x, b, tol=1e-10, **kw)
+    res = oracle_true_residual(w, U, phi, x.cpu().numpy())
+    assert res < 1e-10 and info.true_rel_residual < 1e-10
+    assert abs(res - info.true_rel_residual) < 1e-3 * res
+    lat.close()
+
+
+def test_bicgstab_needs_fewer_operator_applications_than_cg():
+    """Both solvers apply four hopping kernels per iteration; with the spectrum of Mhat in
+    Re > 0 (16^3 x 32 gauge field at kappa 0.13) BiCGstab on Mhat reaches the same bar in fewer
+    iterations than CG on the normal equations."""
+    w, U, phi, lat = setup("16^3x32")
+    b = torch.from_numpy(phi).to(dev())
+    x = torch.zeros_like(b)
+    bi = lat.solve_bicgstab(x, b, tol=1e-10)
+    cg = lat.solve_cg(x, b, tol=1e-10)
+    assert bi.iters < cg.iters, (bi.iters, cg.iters)
+    lat.close()
+
+
+@pytest.mark.parametrize("kw", [MODES[0][1], MODES[3][1]])
+def test_bicgstab_stops_cleanly_where_it_stagnates(kw):
+    """At the 8^4 workload's own kappa (0.1632) part of the spectrum of Mhat has Re < 0 and
+    BiCGstab does not converge in 300 iterations (nor does the oracle's): the call returns
+    TM_ERR_NOT_CONVERGED with a finite last iterate and its residual, and CG still solves it."""
+    w, U, phi, lat = setup("8^4", kappa=0.1632)
+    b = torch.from_numpy(phi).to(dev())
+    x = torch.zeros_like(b)
+    info = lat.solve_bicgstab(x, b, tol=1e-10, max_iter=300, check=False, **kw)
+    assert info.status == 7  # TM_ERR_NOT_CONVERGED
+    assert torch.isfinite(x).all() and np.isfinite(info.true_rel_residual)
+    lat.solve_cg(x, b, tol=1e-10)
+    assert oracle_true_residual(w, U, phi, x.cpu().numpy(), kappa=0.1632) < 1e-10
+    lat.close()
+
+
+def test_bicgstab_multiple_rhs_host_buffers_and_determinism():
+    w, U, _, lat = setup("4^4")
+    phis = np.stack([w.source(k) for k in range(2)])
+    xh = np.zeros_like(phis)
+    lat.solve_bicgstab(xh, phis, nrhs=2, mode=CG_RELIABLE, sloppy_prec=F16)
+    for k in range(2):
+        assert oracle_true_residual(w, U, phis[k], xh[k]) < 1e-10
+    b = torch.from_numpy(phis[1].copy()).to(dev())
+    x1, x2 = torch.zeros_like(b), torch.zeros_like(b)
+    i1 = lat.solve_bicgstab(x1, b, mode=CG_RELIABLE, sloppy_prec=F16)
+    i2 = lat.solve_bicgstab(x2, b, mode=CG_RELIABLE, sloppy_prec=F16)
+    assert torch.equal(x1, x2) and i1.iters == i2.iters
+    assert np.array_equal(x1.cpu().numpy(), xh[1])
+    lat.close()
+
+
+def test_bicgstab_initial_guess_and_zero_source():
+    w, U, phi, lat = setup("4^4")
+    b = torch.from_numpy(phi).to(dev())
+    x = torch.zeros_like(b)
+    lat.solve_bicgstab(x, b, tol=1e-4)
+    info = lat.solve_bicgstab(x, b, tol=1e-10, use_x0=True)
+    assert oracle_true_residual(w, U, phi, x.cpu().numpy()) < 1e-10 and info.true_rel_residual < 1e-10
+    z = torch.zeros_like(b)
+    x.fill_(1.0)
+    info = lat.solve_bicgstab(x, z)
+    assert info.iters == 0 and float(x.abs().max()) == 0.0
+    lat.close()
+
+
+def test_bicgstab_rejects_unsupported_modes():
+    w, U, phi, lat = setup("4^4")
+    b = torch.from_numpy(phi).to(dev())
+    x = torch.zeros_like(b)
+    with pytest.raises(TMError):
+        lat.solve_bicgstab(x, b, mode=CG_SQRT_EPS)
+    with pytest.raises(TMError):
+        lat.solve_bicgstab(x, x)
+    lat.close()
+
+
+_CHILD = """
+import numpy as np, torch
+from paper_0905_3331_gb300 import Lattice, inputs, CG_RELIABLE, F16
+w = inputs.WORKLOADS["4^4"]
+lat = Lattice(w.T, w.L, 0.13, w.mu)
+for prec, link in ((0, 18), (2, 12)):  # fixed kernel choice: no timing-dependent tuning
+    lat.set_hop_threads(prec, link, 2)
+lat.set_gauge(w.gauge())
+b = torch.from_numpy(w.source()).cuda()
+x = torch.zeros_like(b)
+info = lat.solve_bicgstab(x, b, mode=CG_RELIABLE, sloppy_prec=F16)
+np.save({out!r}, x.cpu().numpy())
+print("ITERS", info.iters)
+"""
+
+
+@pytest.mark.parametrize("env", [{"TM_NO_GRAPH": "1"}, {"TM_VERBOSE": "1"}])
+def test_bicgstab_host_loop_fallback_and_tracing(env, tmp_path):
+    """The host-driven chunk loop (TM_NO_GRAPH=1) gives bitwise the solution of the graph loop
+    (fixed-order sums); TM_VERBOSE=1 traces the stages.  Child processes read the environment
+    afresh."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    outs = []
+    for k, e in enumerate(({}, env)):
+        out = str(tmp_path / f"x{k}.npy")
+        r = subprocess.run([sys.executable, "-c", _CHILD.format(out=out)], cwd=root,
+                           env={**os.environ, **e}, capture_output=True, text=True, timeout=300)
+        assert r.returncode == 0, r.stderr
+        outs.append((np.load(out), r.stdout, r.stderr))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert outs[0][1] == outs[1][1]
+    if "TM_VERBOSE" in env:
+        assert "[tm_solve_bicgstab] stage" in outs[1][2] and "update" in outs[1][2]
