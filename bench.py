@@ -273,6 +273,7 @@ def run_gpu(args):
                 "timing": "per-launch CUDA events, L2 flushed before each launch"}
 
     batched = None if args.no_batched else batched_measurement(args, dev)
+    extras = None if args.no_extras else extra_measurements(args, dev, w, U, phi)
 
     n_units = args.steps * world
     value = whole_job_rate(args.steps, world, t_mixed)
@@ -300,6 +301,7 @@ def run_gpu(args):
                 "h2d_bytes_per_step": int(phi.nbytes), "d2h_bytes_per_step": int(phi.nbytes)},
         "gpu_launches": int(launches),
         "batched": batched,
+        "solver_variants": extras,
         "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -347,6 +349,33 @@ def batched_measurement(args, dev):
     infos = solve_cg_batch(systems, **kw)
     torch.cuda.synchronize()
     t_batch = time.perf_counter() - t0
+    # meson contraction of the 12 point-source solutions (the correlators' building block)
+    props = torch.stack([systems[k][2] for k in range(12)])
+    Aout = torch.empty((big.T, 12, 12, 2), dtype=torch.float64, device=dev)
+    lats[0].meson_contract(props, Aout)
+    stream = torch.cuda.current_stream()
+    t_con = 0.0
+    flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev)
+    for _ in range(5):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lats[0].meson_contract(props, Aout)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_con += e0.elapsed_time(e1) / 1e3 / 5
+    con_bytes = props.numel() * props.element_size() + Aout.numel() * Aout.element_size()
+    hbm, _ = peaks()
+    # FP64 flops: 78 hermitian pairs x 12 components x 8 flop per site (conj(a) b accumulated)
+    con_flops = 78 * 12 * 8 * big.T * big.L ** 3
+    contraction = {"workload": f"12 point-source propagators on {big.name} ({con_bytes / 1e9:.2f} GB)",
+                   "ms": round(t_con * 1e3, 4), "gbs": round(con_bytes / t_con / 1e9, 1),
+                   "frac_hbm": round(con_bytes / t_con / 1e9 / hbm, 4),
+                   "fp64_tflops": round(con_flops / t_con / 1e12, 4), "bytes": int(con_bytes),
+                   "flops": int(con_flops), "bound": "fp64 alu (about 3.3 flop per byte)",
+                   "timing": "mean of 5 calls, CUDA events, L2 flushed before each"}
+    del props
     t_single = 0.0
     iters_single = 0
     for lat_, mu, x, b in systems:
@@ -368,7 +397,105 @@ def batched_measurement(args, dev):
             "max_true_rel_residual": max(i.true_rel_residual for i in infos),
             "iters_batched": sum(i.iters for i in infos), "iters_unbatched": iters_single,
             "timing": "host wall clock around one synchronised call (batched) / the sum of "
-                      "the single solves (unbatched)"}
+                      "the single solves (unbatched)",
+            "meson_contract": contraction}
+
+
+# ------------------------------------------------------ the other solvers ---
+def _timed(fn, n, dev):
+    """n calls of fn, each after an L2 flush, CUDA events on the current stream; (seconds, infos)."""
+    import torch
+    flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    total, infos = 0.0, []
+    for _ in range(n):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        infos.append(fn())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        total += e0.elapsed_time(e1) / 1e3
+    return total, infos
+
+
+def extra_measurements(args, dev, w, U, phi):
+    """BiCGstab on Mhat against CG on the normal equations, the chronological guess along a
+    sequence of slowly varying sources, and the meson contraction.  Same gauge field and source
+    as the main line."""
+    import numpy as np
+    import torch
+
+    from paper_0905_3331_gb300 import CG_FP64, CG_RELIABLE, F64, Lattice, inputs
+    sp, sl = parse_sloppy(args.sloppy)
+    out = {}
+    b = torch.from_numpy(phi).to(dev)
+    x = torch.zeros_like(b)
+    # ---- BiCGstab vs CG.  BiCGstab needs the spectrum of Mhat in Re > 0: kappa 0.13 on this
+    # gauge field; at the workload's kappa it stagnates (shown with a bounded run).
+    kb = 0.13
+    lat = Lattice(w.T, w.L, kb, w.mu)
+    lat.set_gauge(torch.from_numpy(U).to(dev))
+    mixed = dict(mode=CG_RELIABLE, sloppy_prec=sp, sloppy_link=sl, delta=0.1)
+    rows = {}
+    for name, fn, kw in (("cg_fp64", lat.solve_cg, dict(mode=CG_FP64)),
+                         ("bicgstab_fp64", lat.solve_bicgstab, dict(mode=CG_FP64)),
+                         ("cg_mixed", lat.solve_cg, mixed),
+                         ("bicgstab_mixed", lat.solve_bicgstab, mixed)):
+        fn(x, b, tol=1e-10, **kw)  # warm-up
+        t, infos = _timed(lambda: fn(x, b, tol=1e-10, **kw), 3, dev)
+        rows[name] = {"solves_per_s": round(3 / t, 3), "iters": infos[-1].iters,
+                      "true_rel_residual": infos[-1].true_rel_residual}
+    lat.set_params(w.kappa, w.mu)
+    info = lat.solve_bicgstab(x, b, tol=1e-10, max_iter=500, check=False)
+    rows["bicgstab_fp64_at_workload_kappa"] = {
+        "kappa": w.kappa, "converged": info.status == 0, "iters": info.iters,
+        "schur_rel_residual": info.schur_rel_residual}
+    lat.close()
+    out["bicgstab"] = {"workload": f"{w.name} gauge field and source at kappa {kb} "
+                                   "(spectrum of Mhat in Re > 0), mu " + str(w.mu),
+                       "sloppy": f"{args.sloppy}, delta 0.1", **rows,
+                       "timing": "3 solves each, CUDA events, L2 flushed before each"}
+    # ---- chronological guess: 8 sources phi_k = phi + 0.02 k eta1 + 0.0005 k^2 eta2, normal
+    # equations solved cold and from the guess of the last 4 solutions
+    lat = Lattice(w.T, w.L, w.kappa, w.mu)
+    lat.set_gauge(torch.from_numpy(U).to(dev))
+    hb = lat.half_field_bytes(F64) // 8
+    base, d1, d2 = (inputs.gaussian_spinor(w.T, w.L, s_) for s_ in (51, 52, 53))
+    odd = ((np.indices((w.T, w.L, w.L, w.L)).sum(axis=0) & 1) == 1).reshape(-1)
+    srcs = []
+    for k in range(8):
+        full = (base + 0.02 * k * d1 + 0.0005 * k * k * d2).reshape(-1, 4, 3)[odd]
+        h = torch.from_numpy(np.ascontiguousarray(full).view(np.float64).reshape(-1)).to(dev)
+        dsrc = torch.empty(hb, dtype=torch.float64, device=dev)
+        lat.pack_half(F64, dsrc, h)
+        srcs.append(dsrc)
+    X = torch.zeros(hb, dtype=torch.float64, device=dev)
+    lat.solve_normal(X, srcs[0], tol=1e-10)  # warm-up
+    cold_iters = warm_iters = 0
+    t_cold = t_warm = 0.0
+    history = []
+    for dsrc in srcs:
+        X.zero_()
+        t, (i,) = _timed(lambda: lat.solve_normal(X, dsrc, tol=1e-10), 1, dev)
+        t_cold += t
+        cold_iters += i.iters
+
+        def warm():
+            lat.chrono_guess(X, history[-4:], dsrc)
+            return lat.solve_normal(X, dsrc, tol=1e-10, use_x0=True)
+        t, (i,) = _timed(warm, 1, dev)
+        t_warm += t
+        warm_iters += i.iters
+        history.append(X.clone())
+    lat.close()
+    out["chrono_guess"] = {"workload": f"{w.name}, 8 slowly varying sources, N_CSG = 4, FP64 CG on "
+                                       "Qhat^+ Qhat^- to 1e-10",
+                           "iters_cold": cold_iters, "iters_with_guess": warm_iters,
+                           "seconds_cold": round(t_cold, 4), "seconds_with_guess": round(t_warm, 4),
+                           "speedup": round(t_cold / t_warm, 3)}
+    return out
 
 
 # -------------------------------------------------------------- CPU oracle ---
@@ -461,6 +588,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-solve measurement")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the BiCGstab, chronological-guess and contraction measurements")
     ap.add_argument("--ref-seconds", type=float, default=8.0)
     ap.add_argument("--ref-iters", type=int, default=1500,
                     help="CG iterations per solve used to scale the reference arm's sample")

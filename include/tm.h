@@ -285,7 +285,9 @@ tm_status tm_chrono_guess(tm_lattice lat, void *X0, const void *const *chi, int 
  * solution for the source of spin s and colour c.  out: T x 12 x 12 complex doubles (host or
  * device), out[t][j][k] = sum_{x, x_t = t} <psi_j(x), psi_k(x)> (conjugate on psi_j); then
  * C_PG(t) = sum_{s, s', c} out[t][3s+c][3s'+c] (Gamma gamma5)[s'][s], e.g. C_PP(t) = trace.
- * FP64, deterministic.  Errors: TM_ERR_ARG, TM_ERR_CUDA. */
+ * FP64, deterministic; exactly hermitian (the 78 entries j <= k are summed, the others are
+ * their conjugates).  Device props must be 16-byte aligned (host props are staged).
+ * Errors: TM_ERR_ARG, TM_ERR_CUDA. */
 tm_status tm_meson_contract(tm_lattice lat, const double *props, double *out, void *stream);
 
 /* Fills params with the defaults: tol 1e-10, max_iter 100000, TM_CG_FP64, sloppy
