@@ -105,6 +105,11 @@ def _configure(lib):
                               ctypes.POINTER(D), ctypes.POINTER(D)]
     lib.orc_solve.restype = I
     lib.orc_num_threads.restype = I
+    lib.orc_pauli.argtypes = [I, P]
+    lib.orc_apply_Mh.argtypes = [P, P, I, D, D, D, P, P, P]
+    lib.orc_apply_Mh_dag.argtypes = [P, P, I, D, D, D, P, P, P]
+    lib.orc_solve_Mh.argtypes = [P, P, I, D, D, D, P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D)]
+    lib.orc_solve_Mh.restype = I
     return lib
 
 
@@ -399,3 +404,45 @@ def chrono_guess(lat: Lattice, U, chis, phi, kappa: float, mu: float, f: int = 1
     for i in range(n):
         X0 += c[i] * chis[i]
     return X0, c
+
+
+# ------------------------------------------------------ non-degenerate doublet ---
+def pauli(k: int) -> np.ndarray:
+    """tau_k (k = 1, 2, 3; 0 is the flavour identity) as typed from App. A."""
+    out = np.zeros((2, 2), dtype=np.complex128)
+    _load().orc_pauli(int(k), _ptr(out))
+    return out
+
+
+def apply_Mh(lat: Lattice, U, psi, kappa: float, mubar: float, epsbar: float) -> np.ndarray:
+    """M_h psi for the doublet of eq. Dh, hopping-parameter form (psi: (2,) + spinor shape)."""
+    U = _c(U, lat.gauge_shape)
+    psi = _c(psi, (2,) + lat.spinor_shape)
+    out = np.empty_like(psi)
+    _load().orc_apply_Mh(_ptr(lat._dims()), _ptr(lat._theta()), int(lat.spread), kappa, mubar, epsbar,
+                         _ptr(U), _ptr(psi), _ptr(out))
+    return out
+
+
+def apply_Mh_dag(lat: Lattice, U, psi, kappa: float, mubar: float, epsbar: float) -> np.ndarray:
+    """M_h^dag psi = tau1 gamma5 M_h gamma5 tau1 psi."""
+    U = _c(U, lat.gauge_shape)
+    psi = _c(psi, (2,) + lat.spinor_shape)
+    out = np.empty_like(psi)
+    _load().orc_apply_Mh_dag(_ptr(lat._dims()), _ptr(lat._theta()), int(lat.spread), kappa, mubar,
+                             epsbar, _ptr(U), _ptr(psi), _ptr(out))
+    return out
+
+
+def solve_Mh(lat: Lattice, U, phi, kappa: float, mubar: float, epsbar: float, tol: float = 1e-10,
+             max_iter: int = 20000) -> CGResult:
+    """M_h psi = phi on the full lattice by CG on the normal equations (CGNR)."""
+    U = _c(U, lat.gauge_shape)
+    phi = _c(phi, (2,) + lat.spinor_shape)
+    psi = np.zeros_like(phi)
+    it = ctypes.c_int(0)
+    rr = ctypes.c_double(0)
+    st = _load().orc_solve_Mh(_ptr(lat._dims()), _ptr(lat._theta()), int(lat.spread), kappa, mubar,
+                              epsbar, _ptr(U), _ptr(phi), _ptr(psi), tol, int(max_iter),
+                              ctypes.byref(it), ctypes.byref(rr))
+    return CGResult(psi, st == 0, it.value, rr.value)

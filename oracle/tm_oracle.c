@@ -610,3 +610,135 @@ void orc_hopping_sites(const int dims[4], const double theta[4], int spread, con
       for (int a = 0; a < 3; ++a) out[12 * k + 3 * s + a] = acc[s][a];
   }
 }
+
+/* ------------------------------------------- non-degenerate doublet --- */
+/*
+ * The mass non-degenerate flavour doublet of eq. Dh, D_h = D_W 1_f + i mubar gamma5 tau3 +
+ * epsbar tau1, in the hopping-parameter form of eq. eo0 (M = 2 kappa D):
+ *   (M_h psi)(x) = [1_f + i mb gamma5 tau3 + eb tau1] psi(x) - kappa (H psi)(x),
+ *   mb = 2 kappa mubar, eb = 2 kappa epsbar,
+ * with H the hopping sum of eq. eo0 acting on each flavour alike.  The Pauli matrices are
+ * those of App. A.  A doublet field is two one-flavour fields back to back: component
+ * [f][lex][spin][colour], f = 0 the upper (tau3 = +1) flavour.
+ */
+static const cplx PAULI[4][2][2] = {
+    {{1, 0}, {0, 1}},   /* 1_f    */
+    {{0, 1}, {1, 0}},   /* tau^1  */
+    {{0, -I}, {I, 0}},  /* tau^2  */
+    {{1, 0}, {0, -1}},  /* tau^3  */
+};
+
+void orc_pauli(int k, cplx *out) {
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) out[2 * a + b] = PAULI[k][a][b];
+}
+
+void orc_apply_Mh(const int dims[4], const double theta[4], int spread, double kappa, double mubar,
+                  double epsbar, const cplx *U, const cplx *in, cplx *out) {
+  geo_t g = make_geo(dims);
+  long n = 12 * g.V;
+  double mb = 2.0 * kappa * mubar, eb = 2.0 * kappa * epsbar;
+  cplx *hop = calloc(2 * n, sizeof(cplx));
+  orc_hopping(dims, theta, spread, U, in, hop, -1);         /* H psi_0 */
+  orc_hopping(dims, theta, spread, U, in + n, hop + n, -1); /* H psi_1 */
+#pragma omp parallel for schedule(static)
+  for (long lex = 0; lex < g.V; ++lex) {
+    for (int f = 0; f < 2; ++f)
+      for (int s = 0; s < 4; ++s)
+        for (int a = 0; a < 3; ++a) {
+          /* site matrix (1_f x 1) + i mb (tau3 x gamma5) + eb (tau1 x 1), row (f, s) */
+          cplx v = 0;
+          for (int f2 = 0; f2 < 2; ++f2)
+            for (int t = 0; t < 4; ++t) {
+              cplx m = PAULI[0][f][f2] * (s == t ? 1.0 : 0.0) + I * mb * PAULI[3][f][f2] * GAMMA[4][s][t] +
+                       eb * PAULI[1][f][f2] * (s == t ? 1.0 : 0.0);
+              v += m * in[f2 * n + 12 * lex + 3 * t + a];
+            }
+          out[f * n + 12 * lex + 3 * s + a] = v - kappa * hop[f * n + 12 * lex + 3 * s + a];
+        }
+  }
+  free(hop);
+}
+
+/* M_h^dag psi = tau1 gamma5 M_h gamma5 tau1 psi (the adjoint relation stated with the PHMC,
+ * Sec. 2.3; a CPU test checks it against <chi, M_h psi> = <M_h^dag chi, psi>). */
+static void apply_Mh_dag(const int dims[4], const double theta[4], int spread, double kappa,
+                         double mubar, double epsbar, const cplx *U, const cplx *in, cplx *out) {
+  geo_t g = make_geo(dims);
+  long n = 12 * g.V;
+  cplx *t1 = calloc(2 * n, sizeof(cplx)), *t2 = calloc(2 * n, sizeof(cplx));
+  /* t1 = gamma5 tau1 in: flavours swapped, gamma5 on each */
+  gamma5_apply(g.V, in + n, t1);
+  gamma5_apply(g.V, in, t1 + n);
+  orc_apply_Mh(dims, theta, spread, kappa, mubar, epsbar, U, t1, t2);
+  gamma5_apply(g.V, t2 + n, out);
+  gamma5_apply(g.V, t2, out + n);
+  free(t1);
+  free(t2);
+}
+
+void orc_apply_Mh_dag(const int dims[4], const double theta[4], int spread, double kappa, double mubar,
+                      double epsbar, const cplx *U, const cplx *in, cplx *out) {
+  apply_Mh_dag(dims, theta, spread, kappa, mubar, epsbar, U, in, out);
+}
+
+/*
+ * Solves M_h psi = phi on the full lattice by CG on the normal equations
+ * M_h^dag M_h psi = M_h^dag phi (CGNR: the residual r = phi - M_h psi is carried along and
+ * tested), relative stop ||r|| / ||phi|| < tol (Sec. 4.4), confirmed on the recomputed
+ * residual.  psi holds the initial guess.  Returns 0 if converged, 1 otherwise.
+ */
+int orc_solve_Mh(const int dims[4], const double theta[4], int spread, double kappa, double mubar,
+                 double epsbar, const cplx *U, const cplx *phi, cplx *psi, double tol, int max_iter,
+                 int *iters_out, double *relres_out) {
+  geo_t g = make_geo(dims);
+  long n = 24 * g.V;
+  cplx *r = calloc(n, sizeof(cplx)), *z = calloc(n, sizeof(cplx)), *p = calloc(n, sizeof(cplx));
+  cplx *w = calloc(n, sizeof(cplx));
+  double bb = norm2(n, phi), rr = 0;
+  int converged = 0, k = 0, restart = 1;
+  double zz = 0;
+  if (bb == 0.0) {
+    for (long i = 0; i < n; ++i) psi[i] = 0;
+    converged = 1;
+    goto done;
+  }
+  while (k < max_iter) {
+    if (restart) { /* r = phi - M psi, z = M^dag r, p = z */
+      orc_apply_Mh(dims, theta, spread, kappa, mubar, epsbar, U, psi, w);
+      for (long i = 0; i < n; ++i) r[i] = phi[i] - w[i];
+      rr = norm2(n, r);
+      if (rr < tol * tol * bb) {
+        converged = 1;
+        break;
+      }
+      apply_Mh_dag(dims, theta, spread, kappa, mubar, epsbar, U, r, z);
+      memcpy(p, z, n * sizeof(cplx));
+      zz = norm2(n, z);
+      restart = 0;
+    }
+    orc_apply_Mh(dims, theta, spread, kappa, mubar, epsbar, U, p, w); /* w = M p */
+    double alpha = zz / norm2(n, w);
+    for (long i = 0; i < n; ++i) psi[i] += alpha * p[i];
+    for (long i = 0; i < n; ++i) r[i] -= alpha * w[i];
+    ++k;
+    rr = norm2(n, r);
+    if (rr < tol * tol * bb) {
+      restart = 1; /* confirm on the recomputed residual */
+      continue;
+    }
+    apply_Mh_dag(dims, theta, spread, kappa, mubar, epsbar, U, r, z);
+    double zz_new = norm2(n, z);
+    double beta = zz_new / zz;
+    for (long i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
+    zz = zz_new;
+  }
+done:
+  if (iters_out) *iters_out = k;
+  if (relres_out) *relres_out = bb > 0 ? sqrt(rr / bb) : 0.0;
+  free(r);
+  free(z);
+  free(p);
+  free(w);
+  return converged ? 0 : 1;
+}

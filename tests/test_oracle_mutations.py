@@ -65,6 +65,15 @@ MUTATIONS = [
     ("BiCGstab on Qhat instead of Mhat", "orc_schur(dims, theta, spread, kappa, mu, f, U, p, v, 0);",
      "orc_schur(dims, theta, spread, kappa, mu, f, U, p, v, 1);"),
     ("BiCGstab shadow residual not conjugated", "cplx rv = dot(n, rh, v);", "cplx rv = dot(n, v, rh);"),
+    ("doublet splitting with tau3 instead of tau1", "eb * PAULI[1][f][f2] * (s == t ? 1.0 : 0.0);",
+     "eb * PAULI[3][f][f2] * (s == t ? 1.0 : 0.0);"),
+    ("doublet twisted mass without tau3", "I * mb * PAULI[3][f][f2] * GAMMA[4][s][t]",
+     "I * mb * PAULI[0][f][f2] * GAMMA[4][s][t]"),
+    ("doublet hopping on the other flavour", "v - kappa * hop[f * n + 12 * lex + 3 * s + a];",
+     "v - kappa * hop[(1 - f) * n + 12 * lex + 3 * s + a];"),
+    ("doublet adjoint without the flavour swap", "  gamma5_apply(g.V, in + n, t1);\n  gamma5_apply(g.V, in, t1 + n);",
+     "  gamma5_apply(g.V, in, t1);\n  gamma5_apply(g.V, in + n, t1 + n);"),
+    ("tau2 typo", "{{0, -I}, {I, 0}},  /* tau^2  */", "{{0, I}, {-I, 0}},  /* tau^2  */"),
 ]
 
 # the pins, at their smallest sizes
@@ -82,6 +91,11 @@ PIN_CALLS = [
     ("cg dense", lambda: pins.test_cg_on_normal_equations_matches_dense()),
     ("bicgstab = scipy", lambda: pins.test_bicgstab_iterates_match_scipy()),
     ("bicgstab dense", lambda: pins.test_bicgstab_solve_equals_dense_solve(2, 2)),
+    ("pauli", lambda: pins.test_pauli_matrices_algebra()),
+    ("doublet eps 0", lambda: pins.test_doublet_without_splitting_is_two_twisted_flavours()),
+    ("doublet free field", lambda: pins.test_doublet_free_field_spectrum()),
+    ("doublet adjoint", lambda: pins.test_doublet_adjoint_relation()),
+    ("doublet dense", lambda: pins.test_doublet_solve_equals_dense_solve(2, 2)),
 ]
 
 

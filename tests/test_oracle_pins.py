@@ -516,3 +516,87 @@ def test_bicgstab_reaches_tolerance_on_4x4x4x4():
     assert res.converged and res.relres_full < 1e-10
     resid = phi - oracle.apply_M(lat, U, res.psi, w.kappa, w.mu)
     assert np.linalg.norm(resid) / np.linalg.norm(phi) < 1e-10
+
+
+# ------------------------------------- non-degenerate doublet (eq. Dh, Sec. 2.3) ---
+def _doublet(lat, seed):
+    return np.stack([rand_spinor(lat, seed), rand_spinor(lat, seed + 1)])
+
+
+def dense_doublet(apply, lat):
+    n = 24 * lat.V
+    A = np.empty((n, n), dtype=np.complex128)
+    e = np.zeros((2,) + lat.spinor_shape, dtype=np.complex128)
+    flat = e.reshape(-1)
+    for j in range(n):
+        flat[j] = 1.0
+        A[:, j] = apply(e).reshape(-1)
+        flat[j] = 0.0
+    return A
+
+
+def test_pauli_matrices_algebra():
+    """tau_a tau_b = delta_ab + i eps_abc tau_c for the App. A matrices (exact)."""
+    t = [oracle.pauli(k) for k in range(4)]
+    assert np.array_equal(t[0], np.eye(2))
+    eps = np.zeros((3, 3, 3))
+    eps[0, 1, 2] = eps[1, 2, 0] = eps[2, 0, 1] = 1
+    eps[0, 2, 1] = eps[2, 1, 0] = eps[1, 0, 2] = -1
+    for a in range(3):
+        for b in range(3):
+            rhs = (a == b) * np.eye(2) + 1j * sum(eps[a, b, c] * t[c + 1] for c in range(3))
+            assert np.array_equal(t[a + 1] @ t[b + 1], rhs)
+
+
+def test_doublet_without_splitting_is_two_twisted_flavours():
+    """epsbar = 0: M_h = diag(M(+mubar), M(-mubar)), the pinned one-flavour operator."""
+    lat = Lattice.cubic(4, 2)
+    U = inputs.random_gauge(4, 2, 0.5, seed=111)
+    kappa, mubar = 0.15, 0.07
+    psi = _doublet(lat, 112)
+    out = oracle.apply_Mh(lat, U, psi, kappa, mubar, 0.0)
+    assert rel(out[0], oracle.apply_M(lat, U, psi[0], kappa, mubar, 1)) < 1e-15
+    assert rel(out[1], oracle.apply_M(lat, U, psi[1], kappa, mubar, -1)) < 1e-15
+
+
+def test_doublet_free_field_spectrum():
+    """Unit gauge: per momentum, M_h^dag M_h = c0 + 2 eb (w0 tau1 + mb gamma5 tau2) with
+    c0 = w0^2 + sum s^2 + mb^2 + eb^2, so its eigenvalues are c0 +- 2 eb sqrt(w0^2 + mb^2),
+    twelve of each, w0 = 1 - 2 kappa sum cos p, s = 2 kappa sin p (antiperiodic p_t)."""
+    T, L = 4, 2
+    lat = Lattice.cubic(T, L)
+    U = inputs.unit_gauge(T, L)
+    kappa, mubar, epsbar = 0.13, 0.4, 0.3
+    mb, eb = 2 * kappa * mubar, 2 * kappa * epsbar
+    M = dense_doublet(lambda v: oracle.apply_Mh(lat, U, v, kappa, mubar, epsbar), lat)
+    lam = np.sort(np.linalg.eigvalsh(M.conj().T @ M))
+    expect = []
+    for p in free_field_momenta(lat):
+        w0 = 1 - 2 * kappa * np.cos(p).sum()
+        c0 = w0 ** 2 + (2 * kappa * np.sin(p)) @ (2 * kappa * np.sin(p)) + mb ** 2 + eb ** 2
+        d = 2 * eb * np.sqrt(w0 ** 2 + mb ** 2)
+        expect += [c0 + d] * 12 + [c0 - d] * 12
+    assert np.allclose(lam, np.sort(expect), rtol=0, atol=1e-12)
+
+
+def test_doublet_adjoint_relation():
+    """<chi, M_h psi> = <M_h^dag chi, psi> with M_h^dag = tau1 gamma5 M_h gamma5 tau1."""
+    lat = Lattice.cubic(4, 4)
+    U = inputs.random_gauge(4, 4, 0.7, seed=113)
+    kappa, mubar, epsbar = 0.16, 0.02, 0.03
+    psi, chi = _doublet(lat, 114), _doublet(lat, 116)
+    lhs = np.vdot(chi, oracle.apply_Mh(lat, U, psi, kappa, mubar, epsbar))
+    rhs = np.vdot(oracle.apply_Mh_dag(lat, U, chi, kappa, mubar, epsbar), psi)
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+
+
+@pytest.mark.parametrize("T,L", [(2, 2), (4, 2)])
+def test_doublet_solve_equals_dense_solve(T, L):
+    lat = Lattice.cubic(T, L)
+    U = inputs.random_gauge(T, L, 0.5, seed=117)
+    kappa, mubar, epsbar = 0.16, 0.05, 0.07
+    phi = _doublet(lat, 118)
+    M = dense_doublet(lambda v: oracle.apply_Mh(lat, U, v, kappa, mubar, epsbar), lat)
+    psi = np.linalg.solve(M, phi.reshape(-1))
+    res = oracle.solve_Mh(lat, U, phi, kappa, mubar, epsbar, tol=1e-12)
+    assert res.converged and rel(res.x.reshape(-1), psi) < 1e-10
