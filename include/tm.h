@@ -275,6 +275,37 @@ tm_status tm_solve_normal(tm_lattice lat, void *X, const void *phi, const tm_cg_
 tm_status tm_chrono_guess(tm_lattice lat, void *X0, const void *const *chi, int n, const void *phi,
                           int flavour, void *stream);
 
+/* ------------------------------------------------ non-degenerate doublet --- */
+
+/* The mass non-degenerate flavour doublet of eq. Dh, D_h = D_W 1_f + i mubar gamma5 tau3 +
+ * epsbar tau1, in the hopping-parameter form of eq. eo0 (M_h = 2 kappa D_h, m0 = 1/(2 kappa) - 4):
+ *   (M_h psi)(x) = [1 + i mb gamma5 tau3 + eb tau1] psi(x) - kappa (H psi)(x),
+ *   mb = 2 kappa mubar, eb = 2 kappa epsbar (mubar, epsbar bare, like mu in tm_lattice_create),
+ * H the hopping sum of eq. eo0 on each flavour; tau_k the Pauli matrices of App. A.  A doublet
+ * field is two canonical full fields back to back (2 x 24 V doubles): the upper flavour
+ * (tau3 = +1) first.  Uses the lattice's kappa and gauge field (its mu is ignored).
+ * Requires 1 + mb^2 - eb^2 > 0 (the site term is invertible), else TM_ERR_ARG.
+ * in, out: host or device, nrhs doublet fields, no overlap.  Computed in FP64 on both parities.
+ * Errors: TM_ERR_NO_GAUGE, TM_ERR_ARG, TM_ERR_CUDA. */
+tm_status tm_apply_Dh(tm_lattice lat, double *out, const double *in, double mubar, double epsbar,
+                      int nrhs, void *stream);
+
+/* Solves M_h x = b for one doublet field (host or device) by even/odd preconditioning (the block
+ * elimination of App. B.1 with the doublet's site term D = 1 + i mb gamma5 tau3 + eb tau1,
+ * D^{-1} = (1 - i mb gamma5 tau3 - eb tau1) / (1 + mb^2 - eb^2)):
+ *   Mhat_h = D - kappa^2 H_oe D^{-1} H_eo (odd sites),  varphi_o = b_o + kappa H_oe D^{-1} b_e,
+ *   CG on Qhat_h^2 y = gamma5 tau1 varphi_o with the hermitian Qhat_h = gamma5 tau1 Mhat_h
+ *   (Mhat_h^dag = tau1 gamma5 Mhat_h gamma5 tau1, Sec. 2.3), x_o = Qhat_h y,
+ *   x_e = D^{-1}(b_e + kappa H_eo x_o).
+ * params: tol, max_iter, mode TM_CG_FP64 or TM_CG_RELIABLE with sloppy_prec TM_F32 (18/12/8
+ * links) and FP64 reliable updates; use_x0 must be 0 (TM_ERR_UNSUPPORTED otherwise).
+ * info as for tm_solve_cg (schur_rel_residual relative to ||varphi_o||, true_rel_residual the
+ * full-lattice FP64 residual).  Synchronises `stream`.
+ * Errors: TM_ERR_NOT_CONVERGED (x holds the last iterate), TM_ERR_NO_GAUGE, TM_ERR_ARG,
+ * TM_ERR_UNSUPPORTED, TM_ERR_NONFINITE, TM_ERR_CUDA, TM_ERR_OOM. */
+tm_status tm_solve_doublet(tm_lattice lat, double *x, const double *b, double mubar, double epsbar,
+                           const tm_cg_params *params, tm_cg_info *info, void *stream);
+
 /* ---------------------------------------------------------------- contractions --- */
 
 /* Meson contraction of a point-source propagator, for the correlators of Sec. 4.3 (one-end

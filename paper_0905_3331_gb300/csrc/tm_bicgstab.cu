@@ -457,66 +457,13 @@ static tm_status bi_graph(const Solver& S, const BiVecs& v, BiState* dst, cudaGr
   const void* ptrs[10] = {v.x, v.r, v.rh, v.p, v.s, v.v, v.t, v.T, dst, lat->partials};
   for (int k = 0; k < 10; ++k) key[4 + k] = (unsigned long long)(uintptr_t)ptrs[k];
   key[14] = (unsigned long long)(uintptr_t)lat->counters;
-  for (int k = 0; k < 8; ++k) {
-    const auto& e = lat->aux_graphs[k];
-    if (e.valid && memcmp(e.key, key, sizeof(key)) == 0) {
-      *out = e.exec;
-      return TM_OK;
-    }
-  }
   tm_status st = ensure_links(lat, v.pp, v.nreal, S.s);
   if (st != TM_OK) return st;
-  if ((st = cuda_check(cudaStreamSynchronize(S.s), "synchronise")) != TM_OK) return st;
-  cudaGraph_t g = nullptr;
-  cudaGraphExec_t ex = nullptr;
-  cudaStream_t cs = nullptr;
-  cudaGraphConditionalHandle cond;
-  cudaGraphNode_t node;
-  cudaGraphNodeParams cp = {};
-  const unsigned long long before = tm_launch_count();
-  if ((st = cuda_check(cudaGraphCreate(&g, 0), "cudaGraphCreate")) != TM_OK) return st;
-  st = cuda_check(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault), "conditional handle");
-  if (st == TM_OK) {
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = cond;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    st = cuda_check(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp), "conditional node");
-  }
-  if (st == TM_OK) st = cuda_check(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream");
-  if (st == TM_OK) {
-    cudaGraph_t body = cp.conditional.phGraph_out[0];
-    st = cuda_check(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal),
-                    "begin capture");
-    if (st == TM_OK) {
-      Solver C = S;
-      C.s = cs;
-      tm_status st1 = enqueue_iteration(C, v, dst, cond, 1);
-      cudaGraph_t captured = nullptr;
-      tm_status st2 = cuda_check(cudaStreamEndCapture(cs, &captured), "end capture");
-      st = st1 != TM_OK ? st1 : st2;
-    }
-  }
-  if (st == TM_OK) st = cuda_check(cudaGraphInstantiate(&ex, g, 0), "graph instantiate");
-  if (cs) cudaStreamDestroy(cs);
-  tm_reset_launch_count();
-  count_launch((unsigned)before);  // capture enqueues nothing
-  if (st != TM_OK) {
-    if (g) cudaGraphDestroy(g);
-    return st;
-  }
-  auto& e = lat->aux_graphs[lat->aux_next];
-  if (e.valid) {
-    cudaGraphExecDestroy(e.exec);
-    cudaGraphDestroy(e.graph);
-  }
-  e.valid = true;
-  memcpy(e.key, key, sizeof(key));
-  e.graph = g;
-  e.exec = ex;
-  lat->aux_next = (lat->aux_next + 1) % 8;
-  *out = ex;
-  return TM_OK;
+  return aux_loop_graph(lat, key, S.s, [&](cudaStream_t cs, cudaGraphConditionalHandle cond) {
+    Solver C = S;
+    C.s = cs;
+    return enqueue_iteration(C, v, dst, cond, 1);
+  }, out);
 }
 
 // Runs one stage: uploads `init`, recomputes rho and ||r||^2 on the device, iterates until the

@@ -175,20 +175,24 @@ static tm_status full_norm2(tm_lattice lat, const double* x, double* out, cudaSt
 
 
 tm_status norm2_half(const Solver& S, int prec, const void* x, double* out_host) {
+  return norm2_n(S, prec, S.lat->geom.h, x, out_host);
+}
+
+tm_status norm2_n(const Solver& S, int prec, int n, const void* x, double* out_host) {
   tm_lattice lat = S.lat;
-  const unsigned nb = blas_blocks(lat->geom.h);
+  const unsigned nb = blas_blocks(n);
   tm_status st = ensure_reduce(lat, nb, 4);
   if (st != TM_OK) return st;
   Reduce red{lat->partials, lat->counters, lat->dscalars, nullptr, FIN_STORE};
   const char* xp = static_cast<const char*>(x);
   if (prec == TM_F64)
-    norm2_kernel<TM_F64><<<nb, BNT, 0, S.s>>>(lat->geom.h, xp, red);
+    norm2_kernel<TM_F64><<<nb, BNT, 0, S.s>>>(n, xp, red);
   else if (prec == TM_F32)
-    norm2_kernel<TM_F32><<<nb, BNT, 0, S.s>>>(lat->geom.h, xp, red);
+    norm2_kernel<TM_F32><<<nb, BNT, 0, S.s>>>(n, xp, red);
   else if (prec == TM_DF64)
-    norm2_kernel<TM_DF64><<<nb, BNT, 0, S.s>>>(lat->geom.h, xp, red);
+    norm2_kernel<TM_DF64><<<nb, BNT, 0, S.s>>>(n, xp, red);
   else
-    norm2_kernel<TM_F16><<<nb, BNT, 0, S.s>>>(lat->geom.h, xp, red);
+    norm2_kernel<TM_F16><<<nb, BNT, 0, S.s>>>(n, xp, red);
   count_launch();
   if ((st = cuda_check(cudaGetLastError(), "norm kernel")) != TM_OK) return st;
   if ((st = cuda_check(cudaMemcpyAsync(out_host, lat->dscalars, sizeof(double), cudaMemcpyDeviceToHost, S.s),
@@ -258,22 +262,27 @@ tm_status normal_apply(const Solver& S, int prec, int nreal, const void* in, voi
   return hop_launch(lat, a, S.s);
 }
 
-static tm_status launch_update(const Solver& S, int px, int pp, void* x, void* p, const void* r, CGState* state,
-                               cudaGraphConditionalHandle cond = 0, int use_cond = 0) {
+tm_status launch_update_n(const Solver& S, int n, int px, int pp, void* x, void* p, const void* r, CGState* state,
+                          cudaGraphConditionalHandle cond, int use_cond) {
   tm_lattice lat = S.lat;
-  const unsigned nb = blas_blocks(lat->geom.h);
+  const unsigned nb = blas_blocks(n);
   char* xc = static_cast<char*>(x);
   char* pc = static_cast<char*>(p);
   const char* rc = static_cast<const char*>(r);
   unsigned* ctr = lat->counters + 2;
   if (px == TM_F64)
-    cg_update_kernel<TM_F64, TM_F64, TM_F64><<<nb, BNT, 0, S.s>>>(lat->geom.h, xc, pc, rc, state, ctr, cond, use_cond);
+    cg_update_kernel<TM_F64, TM_F64, TM_F64><<<nb, BNT, 0, S.s>>>(n, xc, pc, rc, state, ctr, cond, use_cond);
   else if (pp == TM_F32)
-    cg_update_kernel<TM_F32, TM_F32, TM_F32><<<nb, BNT, 0, S.s>>>(lat->geom.h, xc, pc, rc, state, ctr, cond, use_cond);
+    cg_update_kernel<TM_F32, TM_F32, TM_F32><<<nb, BNT, 0, S.s>>>(n, xc, pc, rc, state, ctr, cond, use_cond);
   else
-    cg_update_kernel<TM_F32, TM_F16, TM_F32><<<nb, BNT, 0, S.s>>>(lat->geom.h, xc, pc, rc, state, ctr, cond, use_cond);
+    cg_update_kernel<TM_F32, TM_F16, TM_F32><<<nb, BNT, 0, S.s>>>(n, xc, pc, rc, state, ctr, cond, use_cond);
   count_launch();
   return cuda_check(cudaGetLastError(), "CG update kernel");
+}
+
+static tm_status launch_update(const Solver& S, int px, int pp, void* x, void* p, const void* r, CGState* state,
+                               cudaGraphConditionalHandle cond = 0, int use_cond = 0) {
+  return launch_update_n(S, S.lat->geom.h, px, pp, x, p, r, state, cond, use_cond);
 }
 
 // The vectors of one CG stage: x (PX), r (ResidPrec of op), p / T / W (op precision).
@@ -377,6 +386,67 @@ static tm_status stage_graph(const Solver& S, const Stage& v, cudaGraphExec_t* o
   e.graph = g;
   e.exec = ex;
   lat->graph_next = (lat->graph_next + 1) % 8;
+  *out = ex;
+  return TM_OK;
+}
+
+tm_status aux_loop_graph(tm_lattice lat, const unsigned long long key[16], cudaStream_t s, const LoopBody& body,
+                         cudaGraphExec_t* out) {
+  for (int k = 0; k < 8; ++k) {
+    const auto& e = lat->aux_graphs[k];
+    if (e.valid && memcmp(e.key, key, 16 * sizeof(unsigned long long)) == 0) {
+      *out = e.exec;
+      return TM_OK;
+    }
+  }
+  tm_status st = cuda_check(cudaStreamSynchronize(s), "synchronise");
+  if (st != TM_OK) return st;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  cudaStream_t cs = nullptr;
+  cudaGraphConditionalHandle cond;
+  cudaGraphNode_t node;
+  cudaGraphNodeParams cp = {};
+  const unsigned long long before = tm_launch_count();
+  if ((st = cuda_check(cudaGraphCreate(&g, 0), "cudaGraphCreate")) != TM_OK) return st;
+  st = cuda_check(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault), "conditional handle");
+  if (st == TM_OK) {
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    st = cuda_check(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp), "conditional node");
+  }
+  if (st == TM_OK) st = cuda_check(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream");
+  if (st == TM_OK) {
+    cudaGraph_t bodyg = cp.conditional.phGraph_out[0];
+    st = cuda_check(cudaStreamBeginCaptureToGraph(cs, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal),
+                    "begin capture");
+    if (st == TM_OK) {
+      tm_status st1 = body(cs, cond);
+      cudaGraph_t captured = nullptr;
+      tm_status st2 = cuda_check(cudaStreamEndCapture(cs, &captured), "end capture");
+      st = st1 != TM_OK ? st1 : st2;
+    }
+  }
+  if (st == TM_OK) st = cuda_check(cudaGraphInstantiate(&ex, g, 0), "graph instantiate");
+  if (cs) cudaStreamDestroy(cs);
+  tm_reset_launch_count();
+  count_launch((unsigned)before);  // capture enqueues nothing; keep the launch count unchanged
+  if (st != TM_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  auto& e = lat->aux_graphs[lat->aux_next];
+  if (e.valid) {
+    cudaGraphExecDestroy(e.exec);
+    cudaGraphDestroy(e.graph);
+  }
+  e.valid = true;
+  memcpy(e.key, key, 16 * sizeof(unsigned long long));
+  e.graph = g;
+  e.exec = ex;
+  lat->aux_next = (lat->aux_next + 1) % 8;
   *out = ex;
   return TM_OK;
 }

@@ -1,6 +1,8 @@
 // tm_solver.cuh -- pieces of the even/odd CG shared by the single-system and batched solvers.
 #pragma once
 
+#include <functional>
+
 #include "tm_internal.cuh"
 
 namespace tmq {
@@ -42,6 +44,21 @@ tm_status cg_normal(const Solver& S, const tm_cg_params& P, const void* bp, doub
                     void* Pv, void* T, void* W, NormalResult* res);
 
 bool use_graphs();  // CUDA-graph stage loops (TM_NO_GRAPH=1 selects host-driven chunks)
+
+// A cached CUDA graph whose only node is a WHILE conditional; its body is whatever `body`
+// enqueues on the capture stream (the body's last kernel sets the condition).  Graphs are
+// cached on the lattice under the 16-word key (the caller includes every buffer address and
+// parameter the body bakes in).
+typedef std::function<tm_status(cudaStream_t, cudaGraphConditionalHandle)> LoopBody;
+tm_status aux_loop_graph(tm_lattice lat, const unsigned long long key[16], cudaStream_t s, const LoopBody& body,
+                         cudaGraphExec_t* out);
+
+// x += alpha p; p = r + beta p over n "sites" of the given formats (n = h for one half field;
+// 2h for two stacked half fields of the same formats), once per iteration (see cg_update_kernel)
+tm_status launch_update_n(const Solver& S, int n, int px, int pp, void* x, void* p, const void* r, CGState* state,
+                          cudaGraphConditionalHandle cond, int use_cond);
+// sum of |x|^2 over n sites of format prec into *out_host (synchronises)
+tm_status norm2_n(const Solver& S, int prec, int n, const void* x, double* out_host);
 
 enum { SOLVER_CG = 0, SOLVER_BICGSTAB = 1 };
 tm_status solve_driver(tm_lattice lat, double* x, const double* b, int nrhs, const tm_cg_params* params,

@@ -95,6 +95,8 @@ def load():
                                ctypes.POINTER(CGInfo), P], I),
         "tm_meson_contract": ([P, P, P, P], I),
         "tm_solve_bicgstab": ([P, P, P, I, ctypes.POINTER(CGParams), ctypes.POINTER(CGInfo), P], I),
+        "tm_apply_Dh": ([P, P, P, D, D, I, P], I),
+        "tm_solve_doublet": ([P, P, P, D, D, ctypes.POINTER(CGParams), ctypes.POINTER(CGInfo), P], I),
         "tm_solve_normal": ([P, P, P, ctypes.POINTER(CGParams), ctypes.POINTER(CGInfo), P], I),
         "tm_chrono_guess": ([P, P, ctypes.POINTER(P), I, P, I, P], I),
         "tm_last_error": ([], ctypes.c_char_p),
@@ -114,7 +116,8 @@ def exported_symbols():
     return ["tm_lattice_create", "tm_lattice_destroy", "tm_lattice_set_params", "tm_volume",
             "tm_half_field_bytes", "tm_set_hop_threads", "tm_get_hop_threads", "tm_set_gauge", "tm_pack_half", "tm_unpack_half", "tm_apply_D",
             "tm_apply_hopping_eo", "tm_apply_Mee_inv", "tm_solve_cg", "tm_solve_cg_batch",
-            "tm_cg_params_default", "tm_meson_contract", "tm_solve_bicgstab", "tm_solve_normal", "tm_chrono_guess",
+            "tm_cg_params_default", "tm_meson_contract", "tm_solve_bicgstab", "tm_solve_normal", "tm_chrono_guess", "tm_apply_Dh",
+            "tm_solve_doublet",
             "tm_last_error", "tm_launch_count", "tm_reset_launch_count"]
 
 
@@ -283,6 +286,34 @@ class Lattice:
                                       ctypes.byref(info), _stream(stream))
         if check:
             _check(st, "tm_solve_bicgstab")
+        d = info.as_dict()
+        d["status"] = st
+        return SolveInfo(**d)
+
+    def apply_Dh(self, out, inp, mubar: float, epsbar: float, nrhs: int = 1, stream=None):
+        """out = M_h inp for the non-degenerate doublet (fields (2, T, L, L, L, 4, 3) per rhs)."""
+        _check(load().tm_apply_Dh(self._h, _addr(out), _addr(inp), mubar, epsbar, nrhs,
+                                  _stream(stream)), "tm_apply_Dh")
+        if isinstance(out, np.ndarray):
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    torch.cuda.synchronize()
+            except ImportError:
+                pass
+        return out
+
+    def solve_doublet(self, x, b, mubar: float, epsbar: float, tol: float = 1e-10,
+                      max_iter: int = 100000, mode: int = CG_FP64, sloppy_link: int = LINK12,
+                      delta: float = 0.1, stream=None, check: bool = True) -> SolveInfo:
+        """Solve M_h x = b for the doublet (even/odd CG; mode CG_FP64 or CG_RELIABLE with FP32
+        sloppy storage)."""
+        p = CGParams(tol, max_iter, mode, F32, sloppy_link, delta, 0, 1, F64)
+        info = CGInfo()
+        st = load().tm_solve_doublet(self._h, _addr(x), _addr(b), mubar, epsbar, ctypes.byref(p),
+                                     ctypes.byref(info), _stream(stream))
+        if check:
+            _check(st, "tm_solve_doublet")
         d = info.as_dict()
         d["status"] = st
         return SolveInfo(**d)
