@@ -490,6 +490,27 @@ def extra_measurements(args, dev, w, U, phi):
         warm_iters += i.iters
         history.append(X.clone())
     lat.close()
+    # ---- non-degenerate doublet (eq. Dh): mubar 0.15, epsbar 0.19 on the same gauge field
+    lat = Lattice(w.T, w.L, w.kappa, w.mu)
+    lat.set_gauge(torch.from_numpy(U).to(dev))
+    bd = torch.from_numpy(np.stack([phi, inputs.gaussian_spinor(w.T, w.L, 3)])).to(dev)
+    xd = torch.zeros_like(bd)
+    drows = {}
+    for name, kw in (("fp64", dict(mode=CG_FP64)),
+                     ("mixed", dict(mode=CG_RELIABLE, sloppy_link=sl, delta=0.1))):
+        lat.solve_doublet(xd, bd, 0.15, 0.19, tol=1e-10, **kw)  # warm-up
+        t, infos = _timed(lambda: lat.solve_doublet(xd, bd, 0.15, 0.19, tol=1e-10, **kw), 3, dev)
+        drows[name] = {"solves_per_s": round(3 / t, 3), "iters": infos[-1].iters,
+                       "true_rel_residual": infos[-1].true_rel_residual}
+    od = torch.empty_like(bd)
+    lat.apply_Dh(od, bd, 0.15, 0.19)
+    t, _ = _timed(lambda: lat.apply_Dh(od, bd, 0.15, 0.19), 5, dev)
+    lat.close()
+    out["doublet"] = {"workload": f"{w.name} gauge field, mubar 0.15, epsbar 0.19, kappa {w.kappa}, two "
+                                  "Gaussian flavour sources; even/odd CG to 1e-10",
+                      "sloppy": f"f32:{sl}, delta 0.1", **drows,
+                      "apply_Dh_ms": round(t / 5 * 1e3, 4),
+                      "timing": "3 solves / 5 applications, CUDA events, L2 flushed before each"}
     out["chrono_guess"] = {"workload": f"{w.name}, 8 slowly varying sources, N_CSG = 4, FP64 CG on "
                                        "Qhat^+ Qhat^- to 1e-10",
                            "iters_cold": cold_iters, "iters_with_guess": warm_iters,
