@@ -437,7 +437,7 @@ def extra_measurements(args, dev, w, U, phi):
     kb = 0.13
     lat = Lattice(w.T, w.L, kb, w.mu)
     lat.set_gauge(torch.from_numpy(U).to(dev))
-    mixed = dict(mode=CG_RELIABLE, sloppy_prec=sp, sloppy_link=sl, delta=0.1)
+    mixed = dict(mode=CG_RELIABLE, sloppy_prec=sp, sloppy_link=sl, delta=args.delta)
     rows = {}
     for name, fn, kw in (("cg_fp64", lat.solve_cg, dict(mode=CG_FP64)),
                          ("bicgstab_fp64", lat.solve_bicgstab, dict(mode=CG_FP64)),
@@ -446,6 +446,7 @@ def extra_measurements(args, dev, w, U, phi):
         fn(x, b, tol=1e-10, **kw)  # warm-up
         t, infos = _timed(lambda: fn(x, b, tol=1e-10, **kw), 3, dev)
         rows[name] = {"solves_per_s": round(3 / t, 3), "iters": infos[-1].iters,
+                      "reliable_updates": infos[-1].reliable_updates,
                       "true_rel_residual": infos[-1].true_rel_residual}
     lat.set_params(w.kappa, w.mu)
     info = lat.solve_bicgstab(x, b, tol=1e-10, max_iter=500, check=False)
@@ -455,7 +456,7 @@ def extra_measurements(args, dev, w, U, phi):
     lat.close()
     out["bicgstab"] = {"workload": f"{w.name} gauge field and source at kappa {kb} "
                                    "(spectrum of Mhat in Re > 0), mu " + str(w.mu),
-                       "sloppy": f"{args.sloppy}, delta 0.1", **rows,
+                       "sloppy": f"{args.sloppy}, delta {args.delta}", **rows,
                        "timing": "3 solves each, CUDA events, L2 flushed before each"}
     # ---- chronological guess: 8 sources phi_k = phi + 0.02 k eta1 + 0.0005 k^2 eta2, normal
     # equations solved cold and from the guess of the last 4 solutions
@@ -497,10 +498,11 @@ def extra_measurements(args, dev, w, U, phi):
     xd = torch.zeros_like(bd)
     drows = {}
     for name, kw in (("fp64", dict(mode=CG_FP64)),
-                     ("mixed", dict(mode=CG_RELIABLE, sloppy_link=sl, delta=0.1))):
+                     ("mixed", dict(mode=CG_RELIABLE, sloppy_link=sl, delta=args.delta))):
         lat.solve_doublet(xd, bd, 0.15, 0.19, tol=1e-10, **kw)  # warm-up
         t, infos = _timed(lambda: lat.solve_doublet(xd, bd, 0.15, 0.19, tol=1e-10, **kw), 3, dev)
         drows[name] = {"solves_per_s": round(3 / t, 3), "iters": infos[-1].iters,
+                       "reliable_updates": infos[-1].reliable_updates,
                        "true_rel_residual": infos[-1].true_rel_residual}
     od = torch.empty_like(bd)
     lat.apply_Dh(od, bd, 0.15, 0.19)
@@ -508,7 +510,7 @@ def extra_measurements(args, dev, w, U, phi):
     lat.close()
     out["doublet"] = {"workload": f"{w.name} gauge field, mubar 0.15, epsbar 0.19, kappa {w.kappa}, two "
                                   "Gaussian flavour sources; even/odd CG to 1e-10",
-                      "sloppy": f"f32:{sl}, delta 0.1", **drows,
+                      "sloppy": f"f32:{sl}, delta {args.delta}", **drows,
                       "apply_Dh_ms": round(t / 5 * 1e3, 4),
                       "timing": "3 solves / 5 applications, CUDA events, L2 flushed before each"}
     out["chrono_guess"] = {"workload": f"{w.name}, 8 slowly varying sources, N_CSG = 4, FP64 CG on "
@@ -603,7 +605,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="16^3x32")
     ap.add_argument("--sloppy", default="f32:12", help="sloppy storage:links, e.g. f32:12, f16:8")
-    ap.add_argument("--delta", type=float, default=0.001)
+    ap.add_argument("--delta", type=float, default=1e-5)
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--hop-iters", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

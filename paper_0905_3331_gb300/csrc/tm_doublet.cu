@@ -15,9 +15,10 @@
 // whose residual G (varphi_o - Mhat_h x_o) has the norm of the Schur residual.
 //
 // Fields: a doublet half field is two one-flavour half fields back to back (upper flavour,
-// tau3 = +1, first), each in the library's half-field layout.  The hopping term runs as the
-// one-flavour kernel with two right-hand sides; the flavour-mixing site terms, the gamma5 tau1
-// swap and the CG reductions run in one site kernel that holds both flavours of a site.
+// tau3 = +1, first), each in the library's half-field layout.  The hopping term runs in the
+// two-flavour kernel of tm_dslash_doublet.cu (both flavours of a site in one thread, each link
+// loaded once), whose epilogue applies the flavour-mixing site term, the gamma5 tau1 swap and
+// the fused CG reductions; purely site-local steps use the site kernel below.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -25,16 +26,10 @@
 #include <cstdlib>
 #include <cstring>
 
+#include "tm_doublet.cuh"
 #include "tm_solver.cuh"
 
 namespace tmq {
-
-// out = G^swap [ P a + Q b ], P and Q 2x2 flavour matrices per chirality (complex)
-struct DCoef {
-  double P[2][2][2][2];  // [chirality][f_out][f_in][re, im]
-  double Q[2][2][2][2];
-  int swap;              // apply G = gamma5 tau1 to the result
-};
 
 static DCoef dcoef_zero() {
   DCoef c;
@@ -161,80 +156,82 @@ static tm_status dsite(const DSolver& D, int prec, int mode, const void* a, cons
   char* rc = static_cast<char*>(r);
 #define DSITE_LAUNCH(PP, MM) \
   dsite_kernel<PP, MM><<<nb, BNT, 0, D.S.s>>>(h, ac, bc, oc, st, rc, rst, co, red, skip, alpha_src)
-  if (prec == TM_F64) {
-    if (mode == 0) DSITE_LAUNCH(TM_F64, 0);
-    else if (mode == 1) DSITE_LAUNCH(TM_F64, 1);
-    else DSITE_LAUNCH(TM_F64, 2);
-  } else {
-    if (mode == 0) DSITE_LAUNCH(TM_F32, 0);
-    else if (mode == 1) DSITE_LAUNCH(TM_F32, 1);
-    else DSITE_LAUNCH(TM_F32, 2);
-  }
+  if (mode != 0) return set_error(TM_ERR_ARG, "internal: doublet site kernel mode %d", mode);
+  if (prec == TM_F64)
+    DSITE_LAUNCH(TM_F64, 0);
+  else
+    DSITE_LAUNCH(TM_F32, 0);
 #undef DSITE_LAUNCH
   count_launch();
   return cuda_check(cudaGetLastError(), "doublet site kernel");
 }
 
-// out (both flavours, parity out_parity) = H in, the one-flavour kernel with two right-hand sides
-static tm_status dhop(const DSolver& D, int prec, int nreal, int out_parity, const void* in, void* out,
-                      const int* skip = nullptr) {
-  HopArgs a{};
+// Fused two-flavour hopping: out = [G] (P y + Q H_{p,1-p} in), see tm_doublet.cuh.
+static tm_status dhop(const DSolver& D, int prec, int nreal, int out_parity, const void* in, const void* y,
+                      void* out, const DCoef& co, int mode = 0, const Reduce& red = Reduce{},
+                      const int* skip = nullptr, const CGState* alpha_src = nullptr) {
+  DHopArgs a{};
   a.prec = prec;
   a.nreal = nreal;
-  a.nrhs = 2;
-  a.in = in;
-  a.in_stride = D.S.hb[prec];
-  a.out = out;
-  a.out_stride = D.S.hb[prec];
   a.out_parity = out_parity;
-  a.coef = epi_plain();
-  a.mode = 0;
+  a.in = in;
+  a.stride = D.S.hb[prec];
+  a.out = out;
+  a.out_stride = mode == 2 ? D.S.hb[prec == TM_F64 ? TM_F64 : TM_F32] : D.S.hb[prec];
+  a.y = y;
+  a.co = co;
+  a.mode = mode;
+  a.alpha_src = alpha_src;
+  a.red = red;
   a.skip = skip;
-  return hop_launch(D.S.lat, a, D.S.s);
+  return dhop_launch(D.S.lat, a, D.S.s);
+}
+
+// the coefficient sets of the operator
+static DCoef co_dinv_hop(const DSolver& D) {  // D^-1 H in
+  DCoef c = dcoef_zero();
+  set_Dinv(c.Q, D.mb, D.eb, 1.0);
+  return c;
+}
+static DCoef co_schur_g(const DSolver& D) {  // G (D y - kappa^2 H in)
+  DCoef c = dcoef_zero();
+  set_D(c.P, D.mb, D.eb, 1.0);
+  set_I(c.Q, -D.S.lat->kappa * D.S.lat->kappa);
+  c.swap = 1;
+  return c;
 }
 
 // r -= alpha Qhat_h^2 p  (Qhat_h = G Mhat_h), iteration form with `state` (alpha from the state,
 // <p, A p> = ||Qhat_h p||^2 finalised into alpha, ||r||^2 into beta and the tests); without it
-// alpha = 1 and ||r||^2 goes to dscalars[0].  T, W, Z: work fields of format prec.
-static tm_status dnormal_apply(const DSolver& D, int prec, int nreal, const void* p, void* T, void* W, void* Z,
-                               void* r, CGState* state) {
+// alpha = 1 and ||r||^2 goes to dscalars[0].  T, W: work fields of format prec.  Four launches.
+static tm_status dnormal_apply(const DSolver& D, int prec, int nreal, const void* p, void* T, void* W, void* r,
+                               CGState* state) {
   tm_lattice lat = D.S.lat;
-  tm_status st = ensure_reduce(lat, blas_blocks(lat->geom.h), 4);
+  tm_status st = ensure_reduce(lat, (lat->geom.h + 127) / 128, 4);
   if (st != TM_OK) return st;
   const int* skip = state ? &state->done : nullptr;
-  const double k2 = lat->kappa * lat->kappa;
-  DCoef dinv = dcoef_zero();
-  set_Dinv(dinv.P, D.mb, D.eb, 1.0);
-  DCoef comb = dcoef_zero();  // G (D y - kappa^2 z)
-  set_D(comb.P, D.mb, D.eb, 1.0);
-  set_I(comb.Q, -k2);
-  comb.swap = 1;
-  const Reduce none{};
-  // W = Qhat_h p
-  if ((st = dhop(D, prec, nreal, 0, p, T, skip)) != TM_OK) return st;
-  if ((st = dsite(D, prec, 0, T, nullptr, T, nullptr, dinv, none, skip)) != TM_OK) return st;
-  if ((st = dhop(D, prec, nreal, 1, T, Z, skip)) != TM_OK) return st;
+  const DCoef dinv = co_dinv_hop(D), comb = co_schur_g(D);
+  // W = Qhat_h p = G (D p - kappa^2 H_oe D^-1 H_eo p)
+  if ((st = dhop(D, prec, nreal, 0, p, nullptr, T, dinv, 0, Reduce{}, skip)) != TM_OK) return st;
   if (state) {
     const Reduce ra{lat->partials, lat->counters, nullptr, state, FIN_CG_ALPHA};
-    if ((st = dsite(D, prec, 1, p, Z, W, nullptr, comb, ra, skip)) != TM_OK) return st;
-  } else {
-    if ((st = dsite(D, prec, 0, p, Z, W, nullptr, comb, none)) != TM_OK) return st;
+    if ((st = dhop(D, prec, nreal, 1, T, p, W, comb, 1, ra, skip)) != TM_OK) return st;
+  } else if ((st = dhop(D, prec, nreal, 1, T, p, W, comb)) != TM_OK) {
+    return st;
   }
   // r -= alpha Qhat_h W
-  if ((st = dhop(D, prec, nreal, 0, W, T, skip)) != TM_OK) return st;
-  if ((st = dsite(D, prec, 0, T, nullptr, T, nullptr, dinv, none, skip)) != TM_OK) return st;
-  if ((st = dhop(D, prec, nreal, 1, T, Z, skip)) != TM_OK) return st;
+  if ((st = dhop(D, prec, nreal, 0, W, nullptr, T, dinv, 0, Reduce{}, skip)) != TM_OK) return st;
   const Reduce rr = state ? Reduce{lat->partials, lat->counters, nullptr, state, FIN_CG_RR}
                           : Reduce{lat->partials, lat->counters, lat->dscalars, nullptr, FIN_STORE};
-  return dsite(D, prec, 2, W, Z, nullptr, r, comb, rr, skip, state);
+  return dhop(D, prec, nreal, 1, T, W, r, comb, 2, rr, skip, state);
 }
 
 // r = b' - Qhat_h^2 X in FP64; ||r||^2 returned (synchronises)
-static tm_status dtrue_residual(const DSolver& D, void* r, const void* X, const void* bp, void* T, void* W, void* Z,
+static tm_status dtrue_residual(const DSolver& D, void* r, const void* X, const void* bp, void* T, void* W,
                                 double* rr) {
   tm_status st = cuda_check(cudaMemcpyAsync(r, bp, 2 * D.S.hb[TM_F64], cudaMemcpyDeviceToDevice, D.S.s), "copy");
   if (st != TM_OK) return st;
-  if ((st = dnormal_apply(D, TM_F64, 18, X, T, W, Z, r, nullptr)) != TM_OK) return st;
+  if ((st = dnormal_apply(D, TM_F64, 18, X, T, W, r, nullptr)) != TM_OK) return st;
   if ((st = cuda_check(cudaMemcpyAsync(rr, D.S.lat->dscalars, sizeof(double), cudaMemcpyDeviceToHost, D.S.s),
                        "readback")) != TM_OK)
     return st;
@@ -242,13 +239,13 @@ static tm_status dtrue_residual(const DSolver& D, void* r, const void* X, const 
 }
 
 struct DVecs {
-  int prec, nreal;  // operator storage (p, T, W, Z); x and r are FP64 (prec F64) or FP32
-  void *x, *r, *p, *T, *W, *Z;
+  int prec, nreal;  // operator storage (p, T, W); x and r are FP64 (prec F64) or FP32
+  void *x, *r, *p, *T, *W;
 };
 
 static tm_status enqueue_diter(const DSolver& D, const DVecs& v, CGState* state, cudaGraphConditionalHandle cond,
                                int use_cond) {
-  tm_status st = dnormal_apply(D, v.prec, v.nreal, v.p, v.T, v.W, v.Z, v.r, state);
+  tm_status st = dnormal_apply(D, v.prec, v.nreal, v.p, v.T, v.W, v.r, state);
   if (st != TM_OK) return st;
   const int px = v.prec == TM_F64 ? TM_F64 : TM_F32;
   return launch_update_n(D.S, 2 * D.S.lat->geom.h, px, v.prec, v.x, v.p, v.r, state, cond, use_cond);
@@ -275,8 +272,8 @@ static tm_status run_dstage(const DSolver& D, const DVecs& v, const CGState& ini
     memcpy(&key[2], &lat->kappa, sizeof(double));
     memcpy(&key[3], &D.mb, sizeof(double));
     memcpy(&key[4], &D.eb, sizeof(double));
-    const void* ptrs[9] = {v.x, v.r, v.p, v.T, v.W, v.Z, dst, lat->partials, lat->counters};
-    for (int k = 0; k < 9; ++k) key[5 + k] = (unsigned long long)(uintptr_t)ptrs[k];
+    const void* ptrs[8] = {v.x, v.r, v.p, v.T, v.W, dst, lat->partials, lat->counters};
+    for (int k = 0; k < 8; ++k) key[5 + k] = (unsigned long long)(uintptr_t)ptrs[k];
     cudaGraphExec_t ex;
     st = aux_loop_graph(lat, key, D.S.s, [&](cudaStream_t cs, cudaGraphConditionalHandle cond) {
       DSolver C = D;
@@ -289,7 +286,7 @@ static tm_status run_dstage(const DSolver& D, const DVecs& v, const CGState& ini
         TM_OK)
       return st;
     if ((st = cuda_check(cudaStreamSynchronize(D.S.s), "doublet CG stage")) != TM_OK) return st;
-    count_launch(9u * (unsigned)hst[1].loops);
+    count_launch(5u * (unsigned)hst[1].loops);
     if (!hst[1].done) return set_error(TM_ERR_TIMEOUT, "tm_solve_doublet: stage loop reached its bound");
     *out = hst[1];
     return TM_OK;
@@ -332,7 +329,7 @@ static bool dverbose() {
 
 // CG on Qhat_h^2 y = bp (FP64 or reliable-update mixed precision); y starts at 0.
 static tm_status dcg(const DSolver& D, const tm_cg_params& P, const void* bp, double bb, void* Y, void* R, void* Pv,
-                     void* T, void* W, void* Z, int* iters_out, int* updates_out, bool* conv_out, double* rr_out) {
+                     void* T, void* W, int* iters_out, int* updates_out, bool* conv_out, double* rr_out) {
   tm_lattice lat = D.S.lat;
   cudaStream_t s = D.S.s;
   const size_t hb64 = 2 * D.S.hb[TM_F64];
@@ -345,7 +342,7 @@ static tm_status dcg(const DSolver& D, const tm_cg_params& P, const void* bp, do
   if ((st = cuda_check(cudaMemcpyAsync(R, bp, hb64, cudaMemcpyDeviceToDevice, s), "copy")) != TM_OK) return st;
   if (P.mode == TM_CG_FP64) {
     if ((st = cuda_check(cudaMemcpyAsync(Pv, R, hb64, cudaMemcpyDeviceToDevice, s), "copy")) != TM_OK) return st;
-    DVecs v{TM_F64, 18, Y, R, Pv, T, W, Z};
+    DVecs v{TM_F64, 18, Y, R, Pv, T, W};
     double rr = bb;
     while (!converged) {
       CGState fin;
@@ -353,7 +350,7 @@ static tm_status dcg(const DSolver& D, const tm_cg_params& P, const void* bp, do
       if (fin.nonfinite) return set_error(TM_ERR_NONFINITE, "tm_solve_doublet: non-finite value in the iteration");
       const bool progress = fin.iter > iters;
       iters = fin.iter;
-      if ((st = dtrue_residual(D, R, Y, bp, T, W, Z, &rr_true)) != TM_OK) return st;
+      if ((st = dtrue_residual(D, R, Y, bp, T, W, &rr_true)) != TM_OK) return st;
       ++updates;
       if (dverbose())
         fprintf(stderr, "[tm_solve_doublet] fp64 stage: iter %d true |r|/|b| %.3e\n", iters, std::sqrt(rr_true / bb));
@@ -368,14 +365,13 @@ static tm_status dcg(const DSolver& D, const tm_cg_params& P, const void* bp, do
   } else {
     const int sp = P.sloppy_prec;  // TM_F32 (checked by the caller)
     const size_t hs = 2 * D.S.hb[sp], h32 = 2 * D.S.hb[TM_F32];
-    void *rs = workspace(lat, 8, h32, &st), *xs = nullptr, *ps = nullptr, *Ts = nullptr, *Ws = nullptr, *Zs = nullptr;
+    void *rs = workspace(lat, 8, h32, &st), *xs = nullptr, *ps = nullptr, *Ts = nullptr, *Ws = nullptr;
     if (st == TM_OK) xs = workspace(lat, 9, h32, &st);
     if (st == TM_OK) ps = workspace(lat, 10, hs, &st);
     if (st == TM_OK) Ts = workspace(lat, 11, hs, &st);
     if (st == TM_OK) Ws = workspace(lat, 12, hs, &st);
-    if (st == TM_OK) Zs = workspace(lat, 13, hs, &st);
     if (st != TM_OK) return st;
-    DVecs v{sp, P.sloppy_link, xs, rs, ps, Ts, Ws, Zs};
+    DVecs v{sp, P.sloppy_link, xs, rs, ps, Ts, Ws};
     if ((st = cuda_check(cudaMemsetAsync(xs, 0, h32, s), "memset")) != TM_OK) return st;
     if ((st = dconvert(D, TM_F32, rs, TM_F64, R)) != TM_OK) return st;
     if ((st = dconvert(D, sp, ps, TM_F64, R)) != TM_OK) return st;
@@ -396,7 +392,7 @@ static tm_status dcg(const DSolver& D, const tm_cg_params& P, const void* bp, do
         iters = fin.iter;
         if ((st = daccumulate(D, Y, xs)) != TM_OK) return st;
       }
-      if ((st = dtrue_residual(D, R, Y, bp, T, W, Z, &rr_true)) != TM_OK) return st;
+      if ((st = dtrue_residual(D, R, Y, bp, T, W, &rr_true)) != TM_OK) return st;
       ++updates;
       if (dverbose())
         fprintf(stderr, "[tm_solve_doublet] sloppy stage: iter %d true |r|/|b| %.3e diverged %d\n", iters,
@@ -436,18 +432,14 @@ static tm_status dunpack(const DSolver& D, double* dst, const void* src, int par
   return TM_OK;
 }
 
-// (M_h in) on both parities from the half fields ie, io into oe, oo (FP64; T scratch)
-static tm_status dapply_M(const DSolver& D, void* oe, void* oo, const void* ie, const void* io, void* T) {
-  tm_lattice lat = D.S.lat;
-  DCoef m = dcoef_zero();  // D y - kappa z
+// (M_h in) on both parities from the half fields ie, io into oe, oo (FP64)
+static tm_status dapply_M(const DSolver& D, void* oe, void* oo, const void* ie, const void* io) {
+  DCoef m = dcoef_zero();  // D y - kappa H in
   set_D(m.P, D.mb, D.eb, 1.0);
-  set_I(m.Q, -lat->kappa);
-  const Reduce none{};
-  tm_status st;
-  if ((st = dhop(D, TM_F64, 18, 0, io, T)) != TM_OK) return st;
-  if ((st = dsite(D, TM_F64, 0, ie, T, oe, nullptr, m, none)) != TM_OK) return st;
-  if ((st = dhop(D, TM_F64, 18, 1, ie, T)) != TM_OK) return st;
-  return dsite(D, TM_F64, 0, io, T, oo, nullptr, m, none);
+  set_I(m.Q, -D.S.lat->kappa);
+  tm_status st = dhop(D, TM_F64, 18, 0, io, ie, oe, m);
+  if (st != TM_OK) return st;
+  return dhop(D, TM_F64, 18, 1, ie, io, oo, m);
 }
 
 static DSolver make_dsolver(tm_lattice lat, double mubar, double epsbar, cudaStream_t s) {
@@ -496,19 +488,18 @@ static tm_status dsolve_one(const DSolver& D, double* x, const double* b, const 
   DCoef dinv = dcoef_zero();
   set_Dinv(dinv.P, D.mb, D.eb, 1.0);
   if ((st = dsite(D, TM_F64, 0, be, nullptr, T, nullptr, dinv, none)) != TM_OK) return st;
-  if ((st = dhop(D, TM_F64, 18, 1, T, Z)) != TM_OK) return st;
   DCoef prep = dcoef_zero();
   set_I(prep.P, 1.0);
   set_I(prep.Q, lat->kappa);
   prep.swap = 1;
-  if ((st = dsite(D, TM_F64, 0, bo, Z, bp, nullptr, prep, none)) != TM_OK) return st;
+  if ((st = dhop(D, TM_F64, 18, 1, T, bo, bp, prep)) != TM_OK) return st;
   double bb = 0.0;
   if ((st = norm2_n(D.S, TM_F64, 2 * lat->geom.h, bp, &bb)) != TM_OK) return st;
   int iters = 0, updates = 0;
   bool converged = bb == 0.0;
   double rr_true = 0.0;
   if (!converged) {
-    if ((st = dcg(D, P, bp, bb, Y, R, Pv, T, W, Z, &iters, &updates, &converged, &rr_true)) != TM_OK) return st;
+    if ((st = dcg(D, P, bp, bb, Y, R, Pv, T, W, &iters, &updates, &converged, &rr_true)) != TM_OK) return st;
   } else if ((st = cuda_check(cudaMemsetAsync(Y, 0, hb2, D.S.s), "memset")) != TM_OK) {
     return st;
   }
@@ -516,23 +507,15 @@ static tm_status dsolve_one(const DSolver& D, double* x, const double* b, const 
   info->reliable_updates = updates;
   info->schur_rel_residual = bb > 0.0 ? std::sqrt(rr_true / bb) : 0.0;
   // x_o = Qhat_h Y = G (D Y - kappa^2 H_oe D^-1 H_eo Y)  -> W
-  const double k2 = lat->kappa * lat->kappa;
-  if ((st = dhop(D, TM_F64, 18, 0, Y, T)) != TM_OK) return st;
-  if ((st = dsite(D, TM_F64, 0, T, nullptr, T, nullptr, dinv, none)) != TM_OK) return st;
-  if ((st = dhop(D, TM_F64, 18, 1, T, Z)) != TM_OK) return st;
-  DCoef comb = dcoef_zero();
-  set_D(comb.P, D.mb, D.eb, 1.0);
-  set_I(comb.Q, -k2);
-  comb.swap = 1;
-  if ((st = dsite(D, TM_F64, 0, Y, Z, W, nullptr, comb, none)) != TM_OK) return st;
+  if ((st = dhop(D, TM_F64, 18, 0, Y, nullptr, T, co_dinv_hop(D))) != TM_OK) return st;
+  if ((st = dhop(D, TM_F64, 18, 1, T, Y, W, co_schur_g(D))) != TM_OK) return st;
   // x_e = D^-1 (b_e + kappa H_eo x_o)  -> Pv
-  if ((st = dhop(D, TM_F64, 18, 0, W, T)) != TM_OK) return st;
   DCoef rec = dcoef_zero();
   set_Dinv(rec.P, D.mb, D.eb, 1.0);
   set_Dinv(rec.Q, D.mb, D.eb, lat->kappa);
-  if ((st = dsite(D, TM_F64, 0, be, T, Pv, nullptr, rec, none)) != TM_OK) return st;
+  if ((st = dhop(D, TM_F64, 18, 0, W, be, Pv, rec)) != TM_OK) return st;
   // full residual ||b - M_h x|| / ||b|| in FP64
-  if ((st = dapply_M(D, R, Z, Pv, W, T)) != TM_OK) return st;  // (M x)_e -> R, (M x)_o -> Z
+  if ((st = dapply_M(D, R, Z, Pv, W)) != TM_OK) return st;  // (M x)_e -> R, (M x)_o -> Z
   DCoef diff = dcoef_zero();  // b - M x
   set_I(diff.P, 1.0);
   set_I(diff.Q, -1.0);
@@ -577,9 +560,9 @@ extern "C" tm_status tm_apply_Dh(tm_lattice lat, double* out, const double* in, 
   if (st != TM_OK) return st;
   const DSolver D = make_dsolver(lat, mubar, epsbar, s);
   const size_t hb2 = 2 * D.S.hb[TM_F64];
-  void* w[5];
-  for (int k = 0; k < 5; ++k) {
-    w[k] = workspace(lat, WS_APPLY_D + (k < 4 ? k : -1), hb2, &st);  // slots 22..25 and 21
+  void* w[4];
+  for (int k = 0; k < 4; ++k) {
+    w[k] = workspace(lat, WS_APPLY_D + k, hb2, &st);
     if (st != TM_OK) return st;
   }
   for (int r = 0; r < nrhs; ++r) {
@@ -587,7 +570,7 @@ extern "C" tm_status tm_apply_Dh(tm_lattice lat, double* out, const double* in, 
     double* orr = dout + (size_t)r * 2 * lat->V * 24;
     if ((st = dpack(D, w[0], ir, 0)) != TM_OK) return st;
     if ((st = dpack(D, w[1], ir, 1)) != TM_OK) return st;
-    if ((st = dapply_M(D, w[2], w[3], w[0], w[1], w[4])) != TM_OK) return st;
+    if ((st = dapply_M(D, w[2], w[3], w[0], w[1])) != TM_OK) return st;
     if ((st = dunpack(D, orr, w[2], 0)) != TM_OK) return st;
     if ((st = dunpack(D, orr, w[3], 1)) != TM_OK) return st;
   }

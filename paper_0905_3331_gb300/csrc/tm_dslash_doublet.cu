@@ -1,0 +1,184 @@
+// tm_dslash_doublet.cu -- the hopping term of the doublet operator (eq. Dh) for both flavours
+// at once, with the flavour-mixing site term in the epilogue.
+//
+// The hopping sum acts on each flavour alike (eq. eo0), so one thread takes both flavours of an
+// output site: per hop the link is loaded and reconstructed once and multiplies the projected
+// neighbour spinors of the two flavours (projection, adjoint for the backward hop and the
+// antiperiodic sign exactly as in the one-flavour kernel).  The epilogue forms
+//   out_f = [gamma5 tau1] ( sum_g P_fg y_g + Q_fg (H in)_g )
+// per chirality, which covers D^-1 H, gamma5 tau1 (D y - kappa^2 H in) of the Schur operator and
+// D y - kappa H in of the full operator, with the fused FP64 CG reductions.
+#include "tm_doublet.cuh"
+#include "tm_dslash.cuh"
+
+namespace tmq {
+
+template <int PREC, int NREAL, int MU, int S>
+__device__ __forceinline__ void dhop_dir(cpx<typename SpinorFmt<PREC>::real> acc[2][12], const char* in,
+                                         size_t stride, int h, int nbi, const char* slab, int link_index,
+                                         bool negate) {
+  typedef typename SpinorFmt<PREC>::real R;
+  typedef typename LinkStore<PREC>::type St;
+  constexpr int BYTES = NREAL * LinkStore<PREC>::size;
+  RawWords<BYTES> raw = load_raw<BYTES>(slab, h, link_index);
+  cpx<R> p0[12], p1[12];
+  SpinorFmt<PREC>::load(in, h, nbi, p0);
+  SpinorFmt<PREC>::load(in + stride, h, nbi, p1);
+  Mat3<R> U;
+  LinkRecon<R, St, NREAL>::unpack(raw, U);
+#pragma unroll
+  for (int f = 0; f < 2; ++f) {
+    cpx<R> h0[3], h1[3];
+    project<R, MU, S>(f == 0 ? p0 : p1, h0, h1);
+    if (MU == 0 && negate) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        h0[c] = R(-1) * h0[c];
+        h1[c] = R(-1) * h1[c];
+      }
+    }
+    cpx<R> u0[3], u1[3];
+    if (S > 0)
+      su3_mul2(U, h0, h1, u0, u1);
+    else
+      su3_adj_mul2(U, h0, h1, u0, u1);
+    accumulate<R, MU, S>(acc[f], u0, u1);
+  }
+}
+
+template <int PREC, int NREAL, bool HAS_Y, int MODE>
+__global__ void __launch_bounds__(HOP_NT) dhop_kernel(const Geom g, const int out_parity,
+                                                      const char* __restrict__ links, const char* in,
+                                                      size_t stride, char* out, size_t out_stride, const char* y,
+                                                      const DCoef co, const CGState* alpha_src, const Reduce red,
+                                                      const int* skip) {
+  typedef typename SpinorFmt<PREC>::real R;
+  __shared__ double sh[HOP_NT / 32];
+  if (skip != nullptr && *skip != 0) return;
+  const int cb = blockIdx.x * HOP_NT + threadIdx.x;
+  const bool active = cb < g.h;
+  double nrm = 0.0;
+  if (active) {
+    cpx<R> acc[2][12];
+#pragma unroll
+    for (int f = 0; f < 2; ++f)
+#pragma unroll
+      for (int k = 0; k < 12; ++k) acc[f][k] = mk<R>(R(0), R(0));
+    const SiteCoord c = site_of(g, cb, out_parity);
+    int nb[8];
+    neighbours(g, cb, c, nb);
+    const size_t slab = link_bytes(PREC, NREAL) * (size_t)g.h;
+    const char* lf = links + (size_t)(out_parity * 4) * slab;
+    const char* lo = links + (size_t)((1 - out_parity) * 4) * slab;
+    const bool tfwd = (c.t == g.T - 1), tbwd = (c.t == 0);
+    dhop_dir<PREC, NREAL, 0, +1>(acc, in, stride, g.h, nb[0], lf + 0 * slab, cb, tfwd);
+    dhop_dir<PREC, NREAL, 0, -1>(acc, in, stride, g.h, nb[4], lo + 0 * slab, nb[4], tbwd);
+    dhop_dir<PREC, NREAL, 1, +1>(acc, in, stride, g.h, nb[1], lf + 1 * slab, cb, false);
+    dhop_dir<PREC, NREAL, 1, -1>(acc, in, stride, g.h, nb[5], lo + 1 * slab, nb[5], false);
+    dhop_dir<PREC, NREAL, 2, +1>(acc, in, stride, g.h, nb[2], lf + 2 * slab, cb, false);
+    dhop_dir<PREC, NREAL, 2, -1>(acc, in, stride, g.h, nb[6], lo + 2 * slab, nb[6], false);
+    dhop_dir<PREC, NREAL, 3, +1>(acc, in, stride, g.h, nb[3], lf + 3 * slab, cb, false);
+    dhop_dir<PREC, NREAL, 3, -1>(acc, in, stride, g.h, nb[7], lo + 3 * slab, nb[7], false);
+    // epilogue, chirality by chirality
+    cpx<R> o[2][12];
+    if (HAS_Y) {
+      cpx<R> y0[12], y1[12];
+      SpinorFmt<PREC>::load(y, g.h, cb, y0);
+      SpinorFmt<PREC>::load(y + stride, g.h, cb, y1);
+#pragma unroll
+      for (int f = 0; f < 2; ++f)
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+          const int ch = k < 6 ? 0 : 1;
+          o[f][k] = mk<R>((R)co.P[ch][f][0][0], (R)co.P[ch][f][0][1]) * y0[k] +
+                    mk<R>((R)co.P[ch][f][1][0], (R)co.P[ch][f][1][1]) * y1[k] +
+                    mk<R>((R)co.Q[ch][f][0][0], (R)co.Q[ch][f][0][1]) * acc[0][k] +
+                    mk<R>((R)co.Q[ch][f][1][0], (R)co.Q[ch][f][1][1]) * acc[1][k];
+        }
+    } else {
+#pragma unroll
+      for (int f = 0; f < 2; ++f)
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+          const int ch = k < 6 ? 0 : 1;
+          o[f][k] = mk<R>((R)co.Q[ch][f][0][0], (R)co.Q[ch][f][0][1]) * acc[0][k] +
+                    mk<R>((R)co.Q[ch][f][1][0], (R)co.Q[ch][f][1][1]) * acc[1][k];
+        }
+    }
+    if (co.swap) {  // gamma5 tau1: swap the flavours, negate the lower spins
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        const cpx<R> t = o[0][k];
+        o[0][k] = k < 6 ? o[1][k] : mk<R>(-o[1][k].re, -o[1][k].im);
+        o[1][k] = k < 6 ? t : mk<R>(-t.re, -t.im);
+      }
+    }
+    if (MODE == 2) {
+      constexpr int PR = ResidPrec<PREC>::value;
+      typedef typename SpinorFmt<PR>::real RR;
+      const RR al = (RR)(alpha_src ? alpha_src->alpha : 1.0);
+#pragma unroll
+      for (int f = 0; f < 2; ++f) {
+        cpx<RR> r[12];
+        SpinorFmt<PR>::load(out + f * out_stride, g.h, cb, r);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+          r[k] = r[k] - al * mk<RR>((RR)o[f][k].re, (RR)o[f][k].im);
+          nrm += (double)r[k].re * (double)r[k].re + (double)r[k].im * (double)r[k].im;
+        }
+        SpinorFmt<PR>::store(out + f * out_stride, g.h, cb, r);
+      }
+    } else {
+#pragma unroll
+      for (int f = 0; f < 2; ++f) {
+        SpinorFmt<PREC>::store(out + f * out_stride, g.h, cb, o[f]);
+        if (MODE == 1)
+#pragma unroll
+          for (int k = 0; k < 12; ++k) nrm += (double)norm2(o[f][k]);
+      }
+    }
+  }
+  if (MODE >= 1) {
+    const double bs = block_sum<HOP_NT>(nrm, sh);
+    grid_reduce<HOP_NT>(red, 0, gridDim.x, blockIdx.x, bs, sh);
+  }
+}
+
+template <int PREC, int NREAL>
+static tm_status dhop_launch_t(tm_lattice lat, const DHopArgs& a, cudaStream_t s) {
+  const Geom& g = lat->geom;
+  const unsigned grid = (unsigned)((g.h + HOP_NT - 1) / HOP_NT);
+  const char* links = static_cast<const char*>(lat->links[PREC][link_index(NREAL)]);
+  const char* in = static_cast<const char*>(a.in);
+  const char* y = static_cast<const char*>(a.y);
+  char* out = static_cast<char*>(a.out);
+#define TM_DHOP_ARGS g, a.out_parity, links, in, a.stride, out, a.out_stride, y, a.co, a.alpha_src, a.red, a.skip
+  if (!a.y && a.mode == 0)
+    dhop_kernel<PREC, NREAL, false, 0><<<grid, HOP_NT, 0, s>>>(TM_DHOP_ARGS);
+  else if (a.y && a.mode == 0)
+    dhop_kernel<PREC, NREAL, true, 0><<<grid, HOP_NT, 0, s>>>(TM_DHOP_ARGS);
+  else if (a.y && a.mode == 1)
+    dhop_kernel<PREC, NREAL, true, 1><<<grid, HOP_NT, 0, s>>>(TM_DHOP_ARGS);
+  else if (a.y && a.mode == 2)
+    dhop_kernel<PREC, NREAL, true, 2><<<grid, HOP_NT, 0, s>>>(TM_DHOP_ARGS);
+  else
+    return set_error(TM_ERR_ARG, "doublet hopping: unsupported epilogue combination");
+#undef TM_DHOP_ARGS
+  count_launch();
+  return cuda_check(cudaGetLastError(), "doublet hopping kernel launch");
+}
+
+tm_status dhop_launch(tm_lattice lat, const DHopArgs& a, cudaStream_t s) {
+  tm_status st = ensure_links(lat, a.prec, a.nreal, s);
+  if (st != TM_OK) return st;
+  if (a.prec == TM_F64 && a.nreal == 18) return dhop_launch_t<TM_F64, 18>(lat, a, s);
+  if (a.prec == TM_F32) {
+    if (a.nreal == 18) return dhop_launch_t<TM_F32, 18>(lat, a, s);
+    if (a.nreal == 12) return dhop_launch_t<TM_F32, 12>(lat, a, s);
+    if (a.nreal == 8) return dhop_launch_t<TM_F32, 8>(lat, a, s);
+  }
+  return set_error(TM_ERR_UNSUPPORTED, "doublet hopping: storage %d with %d-real links is not built", a.prec,
+                   a.nreal);
+}
+
+}  // namespace tmq

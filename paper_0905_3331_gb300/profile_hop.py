@@ -8,6 +8,10 @@ It sets up the lattice (gauge copy), packs a Gaussian half field, runs
 tm_apply_hopping_eo `iters` times (alternating output parity) and reports the mean
 launch time from CUDA events (L2 flushed before each launch unless --warm), the
 algorithmic bytes and GB/s.
+
+With --doublet MUBAR,EPSBAR it instead runs `iters` doublet solves (tm_solve_doublet; FP64 for
+--form f64:18, reliable-update FP32 sloppy for f32:<links>) on two Gaussian flavour sources and
+reports the mean solve time -- a driver for captures of the two-flavour hopping kernel.
 """
 from __future__ import annotations
 
@@ -31,7 +35,11 @@ def main():
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--warm", action="store_true", help="do not flush L2 between launches")
     ap.add_argument("--tps", type=int, default=0, help="threads per site 1/2/4 (0: autotuned)")
+    ap.add_argument("--doublet", default=None, help="MUBAR,EPSBAR: time doublet solves instead")
+    ap.add_argument("--delta", type=float, default=0.001, help="reliable-update delta of the doublet solve")
     args = ap.parse_args()
+    if args.doublet:
+        return doublet(args)
     libbuild.build()
     prec = {"f64": 0, "f32": 1, "f16": 2, "df64": 3}[args.form.split(":")[0]]
     nreal = int(args.form.split(":")[1])
@@ -72,6 +80,39 @@ def main():
                       "gbs": per_site * h / t / 1e9,
                       "gflops": 1320 * args.nrhs * h / t / 1e9,
                       "l2": "warm" if args.warm else "flushed"}))
+    lat.close()
+
+
+def doublet(args):
+    import torch
+
+    from . import CG_FP64, CG_RELIABLE, Lattice, inputs
+    from . import build as libbuild
+    libbuild.build()
+    mubar, epsbar = (float(v) for v in args.doublet.split(","))
+    prec, nreal = args.form.split(":")
+    w = inputs.WORKLOADS[args.workload]
+    dev = torch.device("cuda:0")
+    lat = Lattice(w.T, w.L, w.kappa, w.mu)
+    lat.set_gauge(w.gauge())
+    b = torch.from_numpy(np.stack([w.source(0), w.source(1)])).to(dev)
+    x = torch.zeros_like(b)
+    kw = dict(mode=CG_FP64) if prec == "f64" else dict(mode=CG_RELIABLE, sloppy_link=int(nreal), delta=args.delta)
+    info = lat.solve_doublet(x, b, mubar, epsbar, **kw)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    times = []
+    for _ in range(args.iters):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = lat.solve_doublet(x, b, mubar, epsbar, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    print(json.dumps({"workload": w.name, "form": args.form, "doublet": [mubar, epsbar],
+                      "ms": statistics.mean(times) * 1e3, "iters": info.iters,
+                      "reliable_updates": info.reliable_updates,
+                      "true_rel_residual": info.true_rel_residual}))
     lat.close()
 
 
