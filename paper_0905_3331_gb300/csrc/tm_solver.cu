@@ -710,8 +710,10 @@ tm_status cg_normal(const Solver& S, const tm_cg_params& P, const void* bp, doub
   bool converged = false;
   double rr_true = bb;
   // starting residual R = b' - A X (X = 0 unless a guess is given)
+  bool w_valid = false;  // W = Qhat^{-f} X of the current X (K2 of the last FP64 residual)
   if (guess) {
     if ((st = true_residual(S, R, X, bp, T, W, &rr_true)) != TM_OK) return st;
+    w_valid = true;
   } else {
     if ((st = cuda_check(cudaMemsetAsync(X, 0, S.hb[TM_F64], s), "memset")) != TM_OK) return st;
     if ((st = cuda_check(cudaMemcpyAsync(R, bp, S.hb[TM_F64], cudaMemcpyDeviceToDevice, s), "copy")) != TM_OK)
@@ -730,11 +732,13 @@ tm_status cg_normal(const Solver& S, const tm_cg_params& P, const void* bp, doub
     while (!converged) {
       CGState fin;
       if ((st = run_stage(S, v, fresh_state(rr, stop2, P.max_iter, iters, 0.0), &fin)) != TM_OK) return st;
+      w_valid = false;
       trace_stage("fp64 stage", fin, bb);
       if (fin.nonfinite) return set_error(TM_ERR_NONFINITE, "tm_solve_cg: non-finite value in the iteration");
       const bool progress = fin.iter > iters;
       iters = fin.iter;
       if ((st = true_residual(S, R, X, bp, T, W, &rr_true)) != TM_OK) return st;
+      w_valid = true;
       ++updates;
       trace_update(updates, rr_true, bb);
       if (rr_true < stop2) {
@@ -768,6 +772,7 @@ tm_status cg_normal(const Solver& S, const tm_cg_params& P, const void* bp, doub
       CGState fin;
       const double stop_sw = std::fmax(P.tol * bb, stop2);
       if ((st = run_stage(S, v64, fresh_state(rr, stop_sw, P.max_iter, 0, 0.0), &fin)) != TM_OK) return st;
+      w_valid = false;
       trace_stage("fp64 stage (to sqrt(tol))", fin, bb);
       iters = fin.iter;
       if (fin.nonfinite) return set_error(TM_ERR_NONFINITE, "tm_solve_cg: non-finite value in the iteration");
@@ -788,8 +793,10 @@ tm_status cg_normal(const Solver& S, const tm_cg_params& P, const void* bp, doub
         const unsigned nbb = blas_blocks(lat->geom.h);
         accumulate_kernel<TM_F32><<<nbb, BNT, 0, s>>>(lat->geom.h, static_cast<char*>(X), static_cast<char*>(xs));
         count_launch();
+        w_valid = false;
       }
       if ((st = true_residual(S, R, X, bp, T, W, &rr_true)) != TM_OK) return st;
+      w_valid = true;
       ++updates;
       trace_update(updates, rr_true, bb);
       converged = rr_true < stop2;
@@ -834,6 +841,7 @@ tm_status cg_normal(const Solver& S, const tm_cg_params& P, const void* bp, doub
         const unsigned nbb = blas_blocks(lat->geom.h);
         accumulate_kernel<TM_F32><<<nbb, BNT, 0, s>>>(lat->geom.h, static_cast<char*>(X), static_cast<char*>(xs));
         count_launch();
+        w_valid = false;
       }
       if ((st = cuda_check(cudaGetLastError(), "accumulate kernel")) != TM_OK) return st;
       const void* rsrc = R;
@@ -844,6 +852,7 @@ tm_status cg_normal(const Solver& S, const tm_cg_params& P, const void* bp, doub
         rprec = TM_DF64;
       } else {
         if ((st = true_residual(S, R, X, bp, T, W, &rr_true)) != TM_OK) return st;
+        w_valid = true;
       }
       ++updates;
       trace_update(updates, rr_true, bb);
@@ -854,6 +863,7 @@ tm_status cg_normal(const Solver& S, const tm_cg_params& P, const void* bp, doub
         }
         // confirm in FP64; if the double-float residual was too optimistic, carry on in FP64
         if ((st = true_residual(S, R, X, bp, T, W, &rr_true)) != TM_OK) return st;
+        w_valid = true;
         ++updates;
         trace_update(updates, rr_true, bb);
         if (rr_true < stop2) {
@@ -875,6 +885,7 @@ tm_status cg_normal(const Solver& S, const tm_cg_params& P, const void* bp, doub
   res->updates = updates;
   res->converged = converged;
   res->rr_true = rr_true;
+  res->xo_in_W = w_valid;
   return TM_OK;
 }
 
@@ -915,8 +926,13 @@ static tm_status solve_one(tm_lattice lat, double* x, const double* b, const tm_
   info->reliable_updates = updates;
   info->schur_rel_residual = std::sqrt(rr_true / bb);
 
-  // ---- reconstruction and the FP64 residual of the full system
-  if ((st = reconstruct_check(S, X, be, bo, bfull, x, T, W, R, Pv, &info->true_rel_residual)) != TM_OK) return st;
+  // ---- reconstruction and the FP64 residual of the full system (x_o = Qhat^{-f} X is already in W
+  // when the last operation was the FP64 residual of the final X)
+  if (nr.xo_in_W)
+    st = reconstruct_xo(S, W, be, bo, bfull, x, T, R, Pv, &info->true_rel_residual);
+  else
+    st = reconstruct_check(S, X, be, bo, bfull, x, T, W, R, Pv, &info->true_rel_residual);
+  if (st != TM_OK) return st;
   info->status = converged ? TM_OK : TM_ERR_NOT_CONVERGED;
   if (!converged)
     return set_error(TM_ERR_NOT_CONVERGED, "tm_solve_cg: not converged after %d iterations (||r||/||b|| = %.3e)",

@@ -38,7 +38,8 @@ tm_status launch_accumulate(const Solver& S, void* X, void* xs);  // X (FP64) +=
 struct NormalResult {
   int iters, updates;
   bool converged;
-  double rr_true;  // ||bp - A X||^2, recomputed in FP64
+  double rr_true;   // ||bp - A X||^2, recomputed in FP64
+  bool xo_in_W;     // W holds Qhat^{-f} X for the final X (left by the last FP64 residual)
 };
 tm_status cg_normal(const Solver& S, const tm_cg_params& P, const void* bp, double bb, void* X, bool guess, void* R,
                     void* Pv, void* T, void* W, NormalResult* res);
