@@ -12,6 +12,9 @@ algorithmic bytes and GB/s.
 With --doublet MUBAR,EPSBAR it instead runs `iters` doublet solves (tm_solve_doublet; FP64 for
 --form f64:18, reliable-update FP32 sloppy for f32:<links>) on two Gaussian flavour sources and
 reports the mean solve time -- a driver for captures of the two-flavour hopping kernel.
+
+With --contract it runs `iters` meson contractions (tm_meson_contract) of 12 Gaussian
+propagators on the workload's lattice and reports the mean time, bytes and FP64 rate.
 """
 from __future__ import annotations
 
@@ -37,9 +40,12 @@ def main():
     ap.add_argument("--tps", type=int, default=0, help="threads per site 1/2/4 (0: autotuned)")
     ap.add_argument("--doublet", default=None, help="MUBAR,EPSBAR: time doublet solves instead")
     ap.add_argument("--delta", type=float, default=0.001, help="reliable-update delta of the doublet solve")
+    ap.add_argument("--contract", action="store_true", help="time meson contractions instead")
     args = ap.parse_args()
     if args.doublet:
         return doublet(args)
+    if args.contract:
+        return contract(args)
     libbuild.build()
     prec = {"f64": 0, "f32": 1, "f16": 2, "df64": 3}[args.form.split(":")[0]]
     nreal = int(args.form.split(":")[1])
@@ -80,6 +86,39 @@ def main():
                       "gbs": per_site * h / t / 1e9,
                       "gflops": 1320 * args.nrhs * h / t / 1e9,
                       "l2": "warm" if args.warm else "flushed"}))
+    lat.close()
+
+
+def contract(args):
+    import torch
+
+    from . import Lattice, inputs
+    from . import build as libbuild
+    libbuild.build()
+    w = inputs.WORKLOADS[args.workload]
+    dev = torch.device("cuda:0")
+    lat = Lattice(w.T, w.L, w.kappa, w.mu)
+    props = torch.from_numpy(inputs.gaussian_spinor(w.T, w.L, 7, shape_prefix=(12,))).to(dev)
+    out = torch.empty((w.T, 12, 12, 2), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)
+    lat.meson_contract(props, out)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    times = []
+    for _ in range(args.iters):
+        if not args.warm:
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lat.meson_contract(props, out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    t = statistics.mean(times)
+    nbytes = props.numel() * props.element_size()
+    flops = 78 * 12 * 8 * w.V
+    print(json.dumps({"workload": w.name, "contract_us": t * 1e6, "bytes": nbytes, "gbs": nbytes / t / 1e9,
+                      "fp64_tflops": flops / t / 1e12}))
     lat.close()
 
 
