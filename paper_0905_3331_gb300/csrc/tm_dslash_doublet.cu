@@ -8,6 +8,8 @@
 //   out_f = [gamma5 tau1] ( sum_g P_fg y_g + Q_fg (H in)_g )
 // per chirality, which covers D^-1 H, gamma5 tau1 (D y - kappa^2 H in) of the Schur operator and
 // D y - kappa H in of the full operator, with the fused FP64 CG reductions.
+#include <cstdlib>
+
 #include "tm_doublet.cuh"
 #include "tm_dslash.cuh"
 
@@ -144,25 +146,130 @@ __global__ void __launch_bounds__(HOP_NT) dhop_kernel(const Geom g, const int ou
   }
 }
 
+// The same operator with two threads per output site, one per flavour (adjacent lanes).  Both
+// lanes of a pair load the same link (one memory transaction serves the pair), each applies it
+// to its own flavour, and the epilogue takes the partner flavour's sums and site-local input
+// through warp shuffles.  Half the registers of the one-thread form and twice the threads.
+template <int PREC, int NREAL, bool HAS_Y, int MODE>
+__global__ void __launch_bounds__(HOP_NT) dhop2_kernel(const Geom g, const int out_parity,
+                                                       const char* __restrict__ links, const char* in,
+                                                       size_t stride, char* out, size_t out_stride, const char* y,
+                                                       const DCoef co, const CGState* alpha_src, const Reduce red,
+                                                       const int* skip) {
+  typedef typename SpinorFmt<PREC>::real R;
+  __shared__ double sh[HOP_NT / 32];
+  if (skip != nullptr && *skip != 0) return;
+  const int f = threadIdx.x & 1;
+  const int cb = blockIdx.x * (HOP_NT / 2) + (threadIdx.x >> 1);
+  const bool active = cb < g.h;
+  const char* inf = in + f * stride;
+  cpx<R> acc[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) acc[k] = mk<R>(R(0), R(0));
+  if (active) {
+    const SiteCoord c = site_of(g, cb, out_parity);
+    int nb[8];
+    neighbours(g, cb, c, nb);
+    const size_t slab = link_bytes(PREC, NREAL) * (size_t)g.h;
+    const char* lf = links + (size_t)(out_parity * 4) * slab;
+    const char* lo = links + (size_t)((1 - out_parity) * 4) * slab;
+    const bool tfwd = (c.t == g.T - 1), tbwd = (c.t == 0);
+    hop_dir<PREC, NREAL, 0, +1>(acc, inf, g.h, nb[0], lf + 0 * slab, cb, tfwd);
+    hop_dir<PREC, NREAL, 0, -1>(acc, inf, g.h, nb[4], lo + 0 * slab, nb[4], tbwd);
+    hop_dir<PREC, NREAL, 1, +1>(acc, inf, g.h, nb[1], lf + 1 * slab, cb, false);
+    hop_dir<PREC, NREAL, 1, -1>(acc, inf, g.h, nb[5], lo + 1 * slab, nb[5], false);
+    hop_dir<PREC, NREAL, 2, +1>(acc, inf, g.h, nb[2], lf + 2 * slab, cb, false);
+    hop_dir<PREC, NREAL, 2, -1>(acc, inf, g.h, nb[6], lo + 2 * slab, nb[6], false);
+    hop_dir<PREC, NREAL, 3, +1>(acc, inf, g.h, nb[3], lf + 3 * slab, cb, false);
+    hop_dir<PREC, NREAL, 3, -1>(acc, inf, g.h, nb[7], lo + 3 * slab, nb[7], false);
+  }
+  // epilogue, component by component: the partner lane's sum (and site-local input) of the same
+  // component comes through a shuffle (every lane takes part), the result overwrites acc[k].
+  // This lane writes flavour f; with the gamma5 tau1 swap its value is gamma5 (row 1 - f).
+  cpx<R> yv[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) yv[k] = mk<R>(R(0), R(0));
+  if (HAS_Y && active) SpinorFmt<PREC>::load(y + f * stride, g.h, cb, yv);
+  const int row = co.swap ? 1 - f : f;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    const int ch = k < 6 ? 0 : 1;
+    const cpx<R> ap = mk<R>(__shfl_xor_sync(0xffffffffu, acc[k].re, 1), __shfl_xor_sync(0xffffffffu, acc[k].im, 1));
+    cpx<R> v = mk<R>((R)co.Q[ch][row][f][0], (R)co.Q[ch][row][f][1]) * acc[k] +
+               mk<R>((R)co.Q[ch][row][1 - f][0], (R)co.Q[ch][row][1 - f][1]) * ap;
+    if (HAS_Y) {
+      const cpx<R> yp = mk<R>(__shfl_xor_sync(0xffffffffu, yv[k].re, 1), __shfl_xor_sync(0xffffffffu, yv[k].im, 1));
+      v = v + mk<R>((R)co.P[ch][row][f][0], (R)co.P[ch][row][f][1]) * yv[k] +
+          mk<R>((R)co.P[ch][row][1 - f][0], (R)co.P[ch][row][1 - f][1]) * yp;
+    }
+    acc[k] = (co.swap && k >= 6) ? mk<R>(-v.re, -v.im) : v;
+  }
+  double nrm = 0.0;
+  if (active) {
+    const cpx<R>* o = acc;
+    char* outf = out + f * out_stride;
+    if (MODE == 2) {
+      constexpr int PR = ResidPrec<PREC>::value;
+      typedef typename SpinorFmt<PR>::real RR;
+      const RR al = (RR)(alpha_src ? alpha_src->alpha : 1.0);
+      cpx<RR> r[12];
+      SpinorFmt<PR>::load(outf, g.h, cb, r);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        r[k] = r[k] - al * mk<RR>((RR)o[k].re, (RR)o[k].im);
+        nrm += (double)r[k].re * (double)r[k].re + (double)r[k].im * (double)r[k].im;
+      }
+      SpinorFmt<PR>::store(outf, g.h, cb, r);
+    } else {
+      SpinorFmt<PREC>::store(outf, g.h, cb, o);
+      if (MODE == 1)
+#pragma unroll
+        for (int k = 0; k < 12; ++k) nrm += (double)norm2(o[k]);
+    }
+  }
+  if (MODE >= 1) {
+    const double bs = block_sum<HOP_NT>(nrm, sh);
+    grid_reduce<HOP_NT>(red, 0, gridDim.x, blockIdx.x, bs, sh);
+  }
+}
+
+static int dhop_threads_per_site() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("TM_DHOP_TPS");
+    v = (e && *e == '1') ? 1 : 2;
+  }
+  return v;
+}
+
 template <int PREC, int NREAL>
 static tm_status dhop_launch_t(tm_lattice lat, const DHopArgs& a, cudaStream_t s) {
   const Geom& g = lat->geom;
-  const unsigned grid = (unsigned)((g.h + HOP_NT - 1) / HOP_NT);
   const char* links = static_cast<const char*>(lat->links[PREC][link_index(NREAL)]);
   const char* in = static_cast<const char*>(a.in);
   const char* y = static_cast<const char*>(a.y);
   char* out = static_cast<char*>(a.out);
+  const bool two = dhop_threads_per_site() == 2;
+  const unsigned grid = (unsigned)((g.h + (two ? HOP_NT / 2 : HOP_NT) - 1) / (two ? HOP_NT / 2 : HOP_NT));
 #define TM_DHOP_ARGS g, a.out_parity, links, in, a.stride, out, a.out_stride, y, a.co, a.alpha_src, a.red, a.skip
+#define TM_DHOP_LAUNCH(HY, MM)                                                       \
+  do {                                                                               \
+    if (two)                                                                         \
+      dhop2_kernel<PREC, NREAL, HY, MM><<<grid, HOP_NT, 0, s>>>(TM_DHOP_ARGS);       \
+    else                                                                             \
+      dhop_kernel<PREC, NREAL, HY, MM><<<grid, HOP_NT, 0, s>>>(TM_DHOP_ARGS);        \
+  } while (0)
   if (!a.y && a.mode == 0)
-    dhop_kernel<PREC, NREAL, false, 0><<<grid, HOP_NT, 0, s>>>(TM_DHOP_ARGS);
+    TM_DHOP_LAUNCH(false, 0);
   else if (a.y && a.mode == 0)
-    dhop_kernel<PREC, NREAL, true, 0><<<grid, HOP_NT, 0, s>>>(TM_DHOP_ARGS);
+    TM_DHOP_LAUNCH(true, 0);
   else if (a.y && a.mode == 1)
-    dhop_kernel<PREC, NREAL, true, 1><<<grid, HOP_NT, 0, s>>>(TM_DHOP_ARGS);
+    TM_DHOP_LAUNCH(true, 1);
   else if (a.y && a.mode == 2)
-    dhop_kernel<PREC, NREAL, true, 2><<<grid, HOP_NT, 0, s>>>(TM_DHOP_ARGS);
+    TM_DHOP_LAUNCH(true, 2);
   else
     return set_error(TM_ERR_ARG, "doublet hopping: unsupported epilogue combination");
+#undef TM_DHOP_LAUNCH
 #undef TM_DHOP_ARGS
   count_launch();
   return cuda_check(cudaGetLastError(), "doublet hopping kernel launch");
