@@ -20,7 +20,12 @@
 
 namespace tmq {
 
-constexpr int HOP_NT = 128;  // threads per block
+constexpr int HOP_NT = 128;  // threads per block of the batched and doublet hopping kernels
+// The one-flavour hopping kernel runs hop_spb(TPS) output sites per block with TPS threads each:
+// 64 sites (32 with 4 threads per site, whose partial sums would not fit the static shared
+// memory otherwise).  1024 blocks for 16^3 x 32 spread evenly over 152 SMs (6.7 per SM) where
+// 128-site blocks left a 3-vs-4-block imbalance.
+constexpr int hop_spb(int tps) { return tps == 4 ? 32 : 64; }
 
 template <typename R, int MU, int S>
 __device__ __forceinline__ void project(const cpx<R> p[12], cpx<R> h0[3], cpx<R> h1[3]) {
@@ -161,7 +166,7 @@ __device__ __forceinline__ void hop_part(cpx<typename SpinorFmt<PREC>::real> acc
 }
 
 template <int PREC, int NREAL, bool HAS_Y, int MODE, int TPS>
-__global__ void __launch_bounds__(HOP_NT) hop_kernel(const Geom g, const int out_parity,
+__global__ void __launch_bounds__(hop_spb(TPS) * TPS) hop_kernel(const Geom g, const int out_parity,
                                                      const char* __restrict__ links, const void* in,
                                                      size_t in_stride, void* out, size_t out_stride,
                                                      const void* y, size_t y_stride, const EpiCoef coef,
@@ -169,10 +174,11 @@ __global__ void __launch_bounds__(HOP_NT) hop_kernel(const Geom g, const int out
                                                      const Reduce red, const int* skip) {
   typedef typename SpinorFmt<PREC>::real R;
   typedef SpinorFmt<PREC> F;
-  constexpr int SPB = HOP_NT / TPS;         // sites per block
-  constexpr int WPP = (HOP_NT / 32) / TPS;  // warps per part
-  constexpr int STRIDE = 25;                // 24 reals per site, padded against bank conflicts
-  __shared__ double sh[HOP_NT / 32];
+  constexpr int SPB = hop_spb(TPS);        // sites per block
+  constexpr int NT = SPB * TPS;            // threads per block
+  constexpr int WPP = (NT / 32) / TPS;     // warps per part
+  constexpr int STRIDE = 25;               // 24 reals per site, padded against bank conflicts
+  __shared__ double sh[NT / 32];
   __shared__ R part_acc[TPS > 1 ? TPS * SPB * STRIDE : 1];
   __shared__ float part_max[(TPS > 1 && F::has_norm) ? TPS * SPB : 1];
   if (skip != nullptr && *skip != 0) return;
@@ -277,15 +283,15 @@ __global__ void __launch_bounds__(HOP_NT) hop_kernel(const Geom g, const int out
     }
   }
   if (MODE >= 1) {
-    const double bs = block_sum<HOP_NT>(nrm, sh);
-    grid_reduce<HOP_NT>(red, rhs, gridDim.x, blockIdx.x, bs, sh);
+    const double bs = block_sum<NT>(nrm, sh);
+    grid_reduce<NT>(red, rhs, gridDim.x, blockIdx.x, bs, sh);
   }
 }
 
 template <int PREC, int NREAL, int TPS>
 tm_status hop_launch_tps(tm_lattice lat, const HopArgs& a, cudaStream_t s) {
   const Geom& g = lat->geom;
-  constexpr int SPB = HOP_NT / TPS;
+  constexpr int SPB = hop_spb(TPS), NT = SPB * TPS;
   dim3 grid((g.h + SPB - 1) / SPB, a.nrhs);
   const char* links = static_cast<const char*>(lat->links[PREC][link_index(NREAL)]);
   const bool has_y = a.y != nullptr;
@@ -293,15 +299,15 @@ tm_status hop_launch_tps(tm_lattice lat, const HopArgs& a, cudaStream_t s) {
   g, a.out_parity, links, a.in, a.in_stride, a.out, a.out_stride, a.y, a.y_stride, a.coef, a.alpha_src, \
       a.alpha_sign, a.red, a.skip
   if (!has_y && a.mode == 0)
-    hop_kernel<PREC, NREAL, false, 0, TPS><<<grid, HOP_NT, 0, s>>>(TM_HOP_ARGS);
+    hop_kernel<PREC, NREAL, false, 0, TPS><<<grid, NT, 0, s>>>(TM_HOP_ARGS);
   else if (!has_y && a.mode == 1)
-    hop_kernel<PREC, NREAL, false, 1, TPS><<<grid, HOP_NT, 0, s>>>(TM_HOP_ARGS);
+    hop_kernel<PREC, NREAL, false, 1, TPS><<<grid, NT, 0, s>>>(TM_HOP_ARGS);
   else if (has_y && a.mode == 0)
-    hop_kernel<PREC, NREAL, true, 0, TPS><<<grid, HOP_NT, 0, s>>>(TM_HOP_ARGS);
+    hop_kernel<PREC, NREAL, true, 0, TPS><<<grid, NT, 0, s>>>(TM_HOP_ARGS);
   else if (has_y && a.mode == 1)
-    hop_kernel<PREC, NREAL, true, 1, TPS><<<grid, HOP_NT, 0, s>>>(TM_HOP_ARGS);
+    hop_kernel<PREC, NREAL, true, 1, TPS><<<grid, NT, 0, s>>>(TM_HOP_ARGS);
   else if (has_y && a.mode == 2)
-    hop_kernel<PREC, NREAL, true, 2, TPS><<<grid, HOP_NT, 0, s>>>(TM_HOP_ARGS);
+    hop_kernel<PREC, NREAL, true, 2, TPS><<<grid, NT, 0, s>>>(TM_HOP_ARGS);
   else
     return set_error(TM_ERR_ARG, "hopping: unsupported epilogue combination");
 #undef TM_HOP_ARGS
