@@ -99,6 +99,8 @@ def _configure(lib):
     lib.orc_bicgstab.argtypes = [P, P, I, D, D, I, P, P, P, D, I,
                                  ctypes.POINTER(I), ctypes.POINTER(D)]
     lib.orc_bicgstab.restype = I
+    lib.orc_mr.argtypes = [P, P, I, D, D, I, P, P, P, D, I, ctypes.POINTER(I), ctypes.POINTER(D)]
+    lib.orc_mr.restype = I
     lib.orc_eo_prepare.argtypes = [P, P, I, D, D, I, P, P, P]
     lib.orc_eo_reconstruct.argtypes = [P, P, I, D, D, I, P, P, P]
     lib.orc_solve.argtypes = [P, P, I, D, D, I, P, P, P, D, I, ctypes.POINTER(I),
@@ -304,6 +306,20 @@ def bicgstab(lat: Lattice, U, b, kappa: float, mu: float, f: int = 1, tol: float
     return CGResult(x, st == 0, it.value, rr.value)
 
 
+def mr(lat: Lattice, U, b, kappa: float, mu: float, f: int = 1, tol: float = 1e-10,
+       max_iter: int = 10000, x0=None) -> CGResult:
+    """Minimal residual iteration on Mhat^f X = b (odd-site vectors, eq. eo4; Sec. 4.4)."""
+    U = _c(U, lat.gauge_shape)
+    b = _c(b, lat.spinor_shape)
+    x = np.zeros_like(b) if x0 is None else _c(x0, lat.spinor_shape).copy()
+    it = ctypes.c_int(0)
+    rr = ctypes.c_double(0)
+    st = _load().orc_mr(_ptr(lat._dims()), _ptr(lat._theta()), int(lat.spread), kappa, mu, int(f),
+                        _ptr(U), _ptr(b), _ptr(x), tol, int(max_iter), ctypes.byref(it),
+                        ctypes.byref(rr))
+    return CGResult(x, st == 0, it.value, rr.value)
+
+
 def eo_prepare(lat: Lattice, U, phi, kappa: float, mu: float, f: int = 1) -> np.ndarray:
     """varphi_e = (M_ee)^-1 phi_e, varphi_o = phi_o - M_oe varphi_e (App. B.2)."""
     U = _c(U, lat.gauge_shape)
@@ -359,6 +375,19 @@ def solve_bicgstab(lat: Lattice, U, phi, kappa: float, mu: float, f: int = 1,
     odd = lat.parity_mask()[..., None, None]
     b = np.where(odd, varphi, 0)
     res = bicgstab(lat, U, b, kappa, mu, f, tol, max_iter)
+    psi = eo_reconstruct(lat, U, varphi, res.x, kappa, mu, f)
+    full = np.linalg.norm(phi - apply_M(lat, U, psi, kappa, mu, f)) / np.linalg.norm(phi)
+    return SolveResult(psi, res.converged, res.iters, res.relres, full)
+
+
+def solve_mr(lat: Lattice, U, phi, kappa: float, mu: float, f: int = 1, tol: float = 1e-10,
+             max_iter: int = 10000) -> SolveResult:
+    """M^f psi = phi by even/odd preconditioning (App. B.2) with MR on Mhat^f psi_o = varphi_o."""
+    U = _c(U, lat.gauge_shape)
+    phi = _c(phi, lat.spinor_shape)
+    varphi = eo_prepare(lat, U, phi, kappa, mu, f)
+    b = np.where(lat.parity_mask()[..., None, None], varphi, 0)
+    res = mr(lat, U, b, kappa, mu, f, tol, max_iter)
     psi = eo_reconstruct(lat, U, varphi, res.x, kappa, mu, f)
     full = np.linalg.norm(phi - apply_M(lat, U, psi, kappa, mu, f)) / np.linalg.norm(phi)
     return SolveResult(psi, res.converged, res.iters, res.relres, full)

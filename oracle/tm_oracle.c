@@ -506,6 +506,64 @@ done:
   return converged ? 0 : 1;
 }
 
+/* ------------------------------------------------------- minimal residual --- */
+/*
+ * Minimal residual iteration (MR; Saad 2003, the minimal residual method for general
+ * matrices), one of the solvers of Sec. 4.4, on the Schur operator Mhat^{f} of eq. eo4:
+ *   q = Mhat r;  alpha = <q, r> / <q, q>;  x += alpha r;  r -= alpha q
+ * (alpha minimises ||r - alpha q||).  Relative stopping test of Sec. 4.4 on the iterated
+ * residual, confirmed on the recomputed one (else the recursion restarts from it).  x holds
+ * the initial guess.  Returns 0 if converged, 1 otherwise.
+ */
+int orc_mr(const int dims[4], const double theta[4], int spread, double kappa, double mu, int f,
+           const cplx *U, const cplx *b, cplx *x, double tol, int max_iter, int *iters_out,
+           double *relres_out) {
+  geo_t g = make_geo(dims);
+  long n = 12 * g.V;
+  cplx *r = calloc(n, sizeof(cplx)), *q = calloc(n, sizeof(cplx));
+  double bb = norm2(n, b), stop2 = tol * tol * bb, rr = 0;
+  int converged = 0, k = 0;
+  if (bb == 0.0) {
+    for (long i = 0; i < n; ++i) x[i] = 0;
+    converged = 1;
+    goto done;
+  }
+  orc_schur(dims, theta, spread, kappa, mu, f, U, x, q, 0);
+  for (long i = 0; i < n; ++i) r[i] = b[i] - q[i];
+  rr = norm2(n, r);
+  while (k < max_iter) {
+    if (rr < stop2) { /* confirm on the recomputed residual */
+      orc_schur(dims, theta, spread, kappa, mu, f, U, x, q, 0);
+      for (long i = 0; i < n; ++i) r[i] = b[i] - q[i];
+      rr = norm2(n, r);
+      if (rr < stop2) {
+        converged = 1;
+        break;
+      }
+    }
+    orc_schur(dims, theta, spread, kappa, mu, f, U, r, q, 0); /* q = Mhat r */
+    double qq = norm2(n, q);
+    if (qq == 0.0) break;
+    cplx alpha = dot(n, q, r) / qq;
+    for (long i = 0; i < n; ++i) x[i] += alpha * r[i];
+    for (long i = 0; i < n; ++i) r[i] -= alpha * q[i];
+    rr = norm2(n, r);
+    ++k;
+  }
+  if (!converged && rr < stop2) { /* the last step reached the tolerance: confirm it */
+    orc_schur(dims, theta, spread, kappa, mu, f, U, x, q, 0);
+    for (long i = 0; i < n; ++i) r[i] = b[i] - q[i];
+    rr = norm2(n, r);
+    converged = rr < stop2;
+  }
+done:
+  if (iters_out) *iters_out = k;
+  if (relres_out) *relres_out = bb > 0 ? sqrt(rr / bb) : 0.0;
+  free(r);
+  free(q);
+  return converged ? 0 : 1;
+}
+
 /* ------------------------------------------- even/odd inversion (B.2) --- */
 /* Source preparation, first step of App. B.2:
  *   varphi_e = (M_ee^{f})^{-1} phi_e,   varphi_o = phi_o - M_oe varphi_e.

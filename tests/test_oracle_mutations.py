@@ -73,6 +73,9 @@ MUTATIONS = [
      "v - kappa * hop[(1 - f) * n + 12 * lex + 3 * s + a];"),
     ("doublet adjoint without the flavour swap", "  gamma5_apply(g.V, in + n, t1);\n  gamma5_apply(g.V, in, t1 + n);",
      "  gamma5_apply(g.V, in, t1);\n  gamma5_apply(g.V, in + n, t1 + n);"),
+    ("MR step length conjugated", "cplx alpha = dot(n, q, r) / qq;", "cplx alpha = dot(n, r, q) / qq;"),
+    ("MR solution update along q", "for (long i = 0; i < n; ++i) x[i] += alpha * r[i];\n    for (long i = 0; i < n; ++i) r[i] -= alpha * q[i];\n    rr = norm2(n, r);\n    ++k;",
+     "for (long i = 0; i < n; ++i) x[i] += alpha * q[i];\n    for (long i = 0; i < n; ++i) r[i] -= alpha * q[i];\n    rr = norm2(n, r);\n    ++k;"),
     ("tau2 typo", "{{0, -I}, {I, 0}},  /* tau^2  */", "{{0, I}, {-I, 0}},  /* tau^2  */"),
 ]
 
@@ -91,6 +94,8 @@ PIN_CALLS = [
     ("cg dense", lambda: pins.test_cg_on_normal_equations_matches_dense()),
     ("bicgstab = scipy", lambda: pins.test_bicgstab_iterates_match_scipy()),
     ("bicgstab dense", lambda: pins.test_bicgstab_solve_equals_dense_solve(2, 2)),
+    ("mr identity", lambda: pins.test_mr_is_exact_in_one_step_for_the_identity()),
+    ("mr monotone", lambda: pins.test_mr_residual_never_grows_and_solves_the_dense_system()),
     ("pauli", lambda: pins.test_pauli_matrices_algebra()),
     ("doublet eps 0", lambda: pins.test_doublet_without_splitting_is_two_twisted_flavours()),
     ("doublet free field", lambda: pins.test_doublet_free_field_spectrum()),

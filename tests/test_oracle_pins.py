@@ -600,3 +600,43 @@ def test_doublet_solve_equals_dense_solve(T, L):
     psi = np.linalg.solve(M, phi.reshape(-1))
     res = oracle.solve_Mh(lat, U, phi, kappa, mubar, epsbar, tol=1e-12)
     assert res.converged and rel(res.x.reshape(-1), psi) < 1e-10
+
+
+# ------------------------------------------------------ MR on Mhat (Sec. 4.4) ---
+def test_mr_is_exact_in_one_step_for_the_identity():
+    """kappa = 0, mu = 0: Mhat = 1, so the first MR step (alpha = <b, b>/<b, b> = 1) is exact."""
+    lat = Lattice.cubic(4, 2)
+    U = inputs.random_gauge(4, 2, 0.5, seed=121)
+    b = _odd(lat, 122)
+    res = oracle.mr(lat, U, b, 0.0, 0.0, tol=1e-14, max_iter=1)
+    assert res.iters == 1 and rel(res.x, b) < 1e-15 and res.converged
+
+
+def test_mr_residual_never_grows_and_solves_the_dense_system():
+    """Each MR step minimises ||r - alpha q|| over alpha, so the residual norm cannot grow; with
+    the spectrum of Mhat in Re > 0 (kappa 0.13) the iteration converges to the dense solution."""
+    lat = Lattice.cubic(4, 2)
+    U = inputs.random_gauge(4, 2, 0.5, seed=123)
+    kappa, mu = 0.13, 0.05
+    b = _odd(lat, 124)
+    last = np.inf
+    for k in range(1, 12):
+        res = oracle.mr(lat, U, b, kappa, mu, tol=1e-30, max_iter=k)
+        assert res.iters == k and res.relres <= last * (1 + 1e-12)
+        last = res.relres
+    assert last < 0.9
+    o = component_mask(lat, 1)
+    Mh = dense_from(lambda v: oracle.schur(lat, U, v, kappa, mu), lat, rows_mask=o, cols_mask=o)
+    res = oracle.mr(lat, U, b, kappa, mu, tol=1e-12, max_iter=5000)
+    assert res.converged and rel(res.x.reshape(-1)[o], np.linalg.solve(Mh, b.reshape(-1)[o])) < 1e-10
+
+
+def test_mr_solve_equals_dense_solve():
+    lat = Lattice.cubic(2, 2)
+    U = inputs.random_gauge(2, 2, 0.5, seed=125)
+    kappa, mu = 0.12, 0.05
+    phi = rand_spinor(lat, 126)
+    for f in (1, -1):
+        M = dense_from(lambda v: oracle.apply_M(lat, U, v, kappa, mu, f), lat)
+        res = oracle.solve_mr(lat, U, phi, kappa, mu, f, tol=1e-12, max_iter=5000)
+        assert res.converged and rel(res.psi.reshape(-1), np.linalg.solve(M, phi.reshape(-1))) < 1e-10
