@@ -447,10 +447,13 @@ def extra_measurements(args, dev, w, U, phi):
     lat.set_gauge(torch.from_numpy(U).to(dev))
     mixed = dict(mode=CG_RELIABLE, sloppy_prec=sp, sloppy_link=sl, delta=args.delta)
     rows = {}
+    mixed_mr = dict(mode=CG_RELIABLE, sloppy_link=sl, delta=args.delta)
     for name, fn, kw in (("cg_fp64", lat.solve_cg, dict(mode=CG_FP64)),
                          ("bicgstab_fp64", lat.solve_bicgstab, dict(mode=CG_FP64)),
+                         ("mr_fp64", lat.solve_mr, dict(mode=CG_FP64)),
                          ("cg_mixed", lat.solve_cg, mixed),
-                         ("bicgstab_mixed", lat.solve_bicgstab, mixed)):
+                         ("bicgstab_mixed", lat.solve_bicgstab, mixed),
+                         ("mr_mixed", lat.solve_mr, mixed_mr)):
         fn(x, b, tol=1e-10, **kw)  # warm-up
         t, infos = _timed(lambda: fn(x, b, tol=1e-10, **kw), 3, dev)
         rows[name] = {"solves_per_s": round(3 / t, 3), "iters": infos[-1].iters,

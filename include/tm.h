@@ -221,6 +221,17 @@ tm_status tm_solve_cg(tm_lattice lat, double *x, const double *b, int nrhs,
 tm_status tm_solve_bicgstab(tm_lattice lat, double *x, const double *b, int nrhs,
                             const tm_cg_params *params, tm_cg_info *info, void *stream);
 
+/* Solves M(f) x = b like tm_solve_bicgstab with the minimal residual iteration (MR, one of the
+ * solvers of Sec. 4.4) on the Schur system Mhat^f x_o = varphi_o of eq. eo4:
+ *   q = Mhat r,  alpha = <q, r> / <q, q>,  x += alpha r,  r -= alpha q
+ * (alpha minimises ||r - alpha q||; one Schur application per iteration).  Arguments, staging,
+ * nrhs, use_x0 and info as tm_solve_cg; params->mode TM_CG_FP64 or TM_CG_RELIABLE with
+ * sloppy_prec TM_F32 (18/12/8 links; r feeds the operator, so FP16 storage is not offered).
+ * Like BiCGstab it needs the spectrum of Mhat on one side of the origin (see tm_solve_bicgstab).
+ * Errors: as tm_solve_cg, plus TM_ERR_UNSUPPORTED for TM_CG_SQRT_EPS, TM_DF64 updates or FP16. */
+tm_status tm_solve_mr(tm_lattice lat, double *x, const double *b, int nrhs, const tm_cg_params *params,
+                      tm_cg_info *info, void *stream);
+
 /* One system of a batched solve: M(f; mu) x = b on the lattice `lat` (its gauge field and
  * kappa), with this system's own bare twisted mass mu (mu~ = 2 kappa mu). */
 typedef struct {

@@ -359,12 +359,110 @@ __global__ void __launch_bounds__(BNT) bi_rho_kernel(int h, const char* rh, cons
   }
 }
 
+// ------------------------------------------------------------ MR kernels ---
+// Minimal residual (MR) on Mhat: q = Mhat r (two hopping launches), then
+//   A  alpha = <q, r> / <q, q>
+//   U  x += alpha r;  r -= alpha q;  ||r||^2 and the tests (sets the loop condition)
+// r is the operator's input, so it is stored in the operator's format (FP64 or FP32).
+template <int P>
+__global__ void __launch_bounds__(BNT) mr_alpha_kernel(int h, const char* q, const char* r, BiState* st,
+                                                       double* partials, unsigned* counter) {
+  if (st->done) return;
+  typedef typename SpinorFmt<P>::real R;
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int i = blockIdx.x * BNT + threadIdx.x; i < h; i += gridDim.x * BNT) {
+    cpx<R> a[12], b[12];
+    SpinorFmt<P>::load(q, h, i, a);
+    SpinorFmt<P>::load(r, h, i, b);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {  // conj(q) r, |q|^2
+      const double qr = a[k].re, qi = a[k].im, rr_ = b[k].re, ri = b[k].im;
+      acc[0] += qr * rr_ + qi * ri;
+      acc[1] += qr * ri - qi * rr_;
+      acc[2] += qr * qr + qi * qi;
+    }
+  }
+  double tot[3];
+  if (!grid_sum<3>(acc, partials, counter, tot)) return;
+  BiState& S = *st;
+  if (!isfinite(tot[0]) || !isfinite(tot[1]) || !isfinite(tot[2])) {
+    S.nonfinite = 1;
+    S.done = 1;
+  } else if (!(tot[2] > 0.0)) {
+    S.breakdown = 1;
+    S.done = 1;
+  } else {
+    S.alpha_re = tot[0] / tot[2];
+    S.alpha_im = tot[1] / tot[2];
+  }
+}
+
+template <int P>
+__global__ void __launch_bounds__(BNT) mr_update_kernel(int h, char* x, char* r, const char* q, BiState* st,
+                                                        double* partials, unsigned* counter,
+                                                        cudaGraphConditionalHandle cond, int use_cond) {
+  BiState& S = *st;
+  if (S.done) {
+    if (use_cond && blockIdx.x == 0 && threadIdx.x == 0) {
+      S.loops += 1;
+      cudaGraphSetConditional(cond, 0u);
+    }
+    return;
+  }
+  typedef typename SpinorFmt<P>::real R;
+  const cpx<R> al = mk<R>((R)S.alpha_re, (R)S.alpha_im);
+  double acc[1] = {0.0};
+  for (int i = blockIdx.x * BNT + threadIdx.x; i < h; i += gridDim.x * BNT) {
+    cpx<R> xv[12], rv[12], qv[12];
+    SpinorFmt<P>::load(x, h, i, xv);
+    SpinorFmt<P>::load(r, h, i, rv);
+    SpinorFmt<P>::load(q, h, i, qv);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      xv[k] = xv[k] + al * rv[k];
+      rv[k] = rv[k] - al * qv[k];
+      acc[0] += (double)rv[k].re * (double)rv[k].re + (double)rv[k].im * (double)rv[k].im;
+    }
+    SpinorFmt<P>::store(x, h, i, xv);
+    SpinorFmt<P>::store(r, h, i, rv);
+  }
+  double tot[1];
+  if (!grid_sum<1>(acc, partials, counter, tot)) return;
+  S.iter += 1;
+  S.applied = S.iter;
+  const double rr = tot[0];
+  if (!isfinite(rr)) {
+    S.nonfinite = 1;
+    S.done = 1;
+  } else {
+    S.rr = rr;
+    if (rr < S.rr_min) S.rr_min = rr;
+    if (rr < S.stop2) {
+      S.converged = 1;
+      S.done = 1;
+    } else if (S.iter >= S.max_iter) {
+      S.done = 1;
+    } else if (S.delta2 > 0.0 && rr < S.delta2 * S.rr_ref) {
+      S.want_update = 1;
+      S.done = 1;
+    } else if (S.grow2 > 0.0 && rr > S.grow2 * S.rr_min) {
+      S.diverged = 1;
+      S.done = 1;
+    }
+  }
+  if (use_cond) {
+    S.loops += 1;
+    cudaGraphSetConditional(cond, (!S.done && S.loops < S.loop_cap) ? 1u : 0u);
+  }
+}
+
 // ------------------------------------------------------------------- host ---
 struct BiVecs {
+  int mr;     // 0 BiCGstab, 1 MR (then r^ = r and r is in the operator's format)
   int pp;     // operator storage precision (p, s, v, t, T)
   int nreal;  // link format
   int pr;     // precision of x, r, r^
-  void *x, *r, *rh, *p, *s, *v, *t, *T;
+  void *x, *r, *rh, *p, *s, *v, *t, *T;  // MR: v holds q = Mhat r
 };
 
 static unsigned* bi_counters(tm_lattice lat) { return lat->counters + 4; }
@@ -432,9 +530,30 @@ static void blas_step(const Solver& S, const BiVecs& v, BiState* st, int which, 
     launch_iteration_blas<TM_F32, TM_F16>(S, v, st, which, cond, use_cond);
 }
 
-// One BiCGstab iteration (eight kernels).
+static tm_status enqueue_mr_iteration(const Solver& S, const BiVecs& v, BiState* st,
+                                      cudaGraphConditionalHandle cond, int use_cond) {
+  tm_lattice lat = S.lat;
+  const int h = lat->geom.h;
+  const unsigned nb = blas_blocks(h);
+  unsigned* ctr = bi_counters(lat);
+  tm_status e = schur_apply(S, v.pp, v.nreal, v.r, v.T, v.v, &st->done);
+  if (e != TM_OK) return e;
+  char *x = (char*)v.x, *r = (char*)v.r, *q = (char*)v.v;
+  if (v.pp == TM_F64) {
+    mr_alpha_kernel<TM_F64><<<nb, BNT, 0, S.s>>>(h, q, r, st, lat->partials, ctr);
+    mr_update_kernel<TM_F64><<<nb, BNT, 0, S.s>>>(h, x, r, q, st, lat->partials, ctr + 1, cond, use_cond);
+  } else {
+    mr_alpha_kernel<TM_F32><<<nb, BNT, 0, S.s>>>(h, q, r, st, lat->partials, ctr);
+    mr_update_kernel<TM_F32><<<nb, BNT, 0, S.s>>>(h, x, r, q, st, lat->partials, ctr + 1, cond, use_cond);
+  }
+  count_launch(2);
+  return cuda_check(cudaGetLastError(), "MR kernels");
+}
+
+// One BiCGstab iteration (eight kernels), or one MR iteration (four).
 static tm_status enqueue_iteration(const Solver& S, const BiVecs& v, BiState* st, cudaGraphConditionalHandle cond,
                                    int use_cond) {
+  if (v.mr) return enqueue_mr_iteration(S, v, st, cond, use_cond);
   tm_status e;
   if ((e = schur_apply(S, v.pp, v.nreal, v.p, v.T, v.v, &st->done)) != TM_OK) return e;
   blas_step(S, v, st, 0);
@@ -449,7 +568,7 @@ static tm_status enqueue_iteration(const Solver& S, const BiVecs& v, BiState* st
 static tm_status bi_graph(const Solver& S, const BiVecs& v, BiState* dst, cudaGraphExec_t* out) {
   tm_lattice lat = S.lat;
   unsigned long long key[16] = {};
-  key[0] = 0xB1C6ull;
+  key[0] = v.mr ? 0x3A11ull : 0xB1C6ull;
   key[1] = (unsigned long long)v.pp | ((unsigned long long)v.nreal << 8) | ((unsigned long long)v.pr << 16) |
            ((unsigned long long)(S.f + 1) << 24);
   memcpy(&key[2], &lat->kappa, sizeof(double));
@@ -493,8 +612,8 @@ static tm_status run_bi_stage(const Solver& S, const BiVecs& v, BiState* dst, co
     if ((st = cuda_check(cudaMemcpyAsync(&hs, dst, sizeof(BiState), cudaMemcpyDeviceToHost, S.s), "state")) != TM_OK)
       return st;
     if ((st = cuda_check(cudaStreamSynchronize(S.s), "BiCGstab stage")) != TM_OK) return st;
-    count_launch(8u * (unsigned)hs.loops);
-    if (!hs.done) return set_error(TM_ERR_TIMEOUT, "tm_solve_bicgstab: stage loop reached its bound without finishing");
+    count_launch((v.mr ? 4u : 8u) * (unsigned)hs.loops);
+    if (!hs.done) return set_error(TM_ERR_TIMEOUT, "solver stage loop reached its bound without finishing");
   } else {
     if ((st = ensure_links(lat, v.pp, v.nreal, S.s)) != TM_OK) return st;
     for (;;) {
@@ -546,8 +665,23 @@ static bool bi_verbose() {
   return e && *e && *e != '0';
 }
 
+static tm_status solve_one_krylov(tm_lattice lat, double* x, const double* b, const tm_cg_params& P,
+                                  tm_cg_info* info, cudaStream_t s, bool mr);
+
 tm_status solve_one_bicgstab(tm_lattice lat, double* x, const double* b, const tm_cg_params& P, tm_cg_info* info,
                              cudaStream_t s) {
+  return solve_one_krylov(lat, x, b, P, info, s, false);
+}
+
+tm_status solve_one_mr(tm_lattice lat, double* x, const double* b, const tm_cg_params& P, tm_cg_info* info,
+                       cudaStream_t s) {
+  return solve_one_krylov(lat, x, b, P, info, s, true);
+}
+
+// BiCGstab (mr false) or MR (mr true) on Mhat^f x_o = varphi_o for one canonical full field.
+static tm_status solve_one_krylov(tm_lattice lat, double* x, const double* b, const tm_cg_params& P, tm_cg_info* info,
+                                  cudaStream_t s, bool mr) {
+  const char* nm = mr ? "tm_solve_mr" : "tm_solve_bicgstab";
   Solver S{lat, s, P.flavour, 2.0 * lat->kappa * lat->mu, {0, 0, 0, 0}};
   for (int p = 0; p < 4; ++p) S.hb[p] = spinor_bytes_per_site(p) * lat->h;
   tm_status st = TM_OK;
@@ -561,7 +695,7 @@ tm_status solve_one_bicgstab(tm_lattice lat, double* x, const double* b, const t
   double bb = 0.0, bfull = 0.0;
   if ((st = prepare_source(S, b, be, bo, B, T, &bb, &bfull)) != TM_OK) return st;
   if (!std::isfinite(bb) || !std::isfinite(bfull))
-    return set_error(TM_ERR_NONFINITE, "tm_solve_bicgstab: the source has non-finite entries");
+    return set_error(TM_ERR_NONFINITE, "%s: the source has non-finite entries", nm);
   // prepare_source gives gamma5 varphi_o; the Schur system wants varphi_o itself
   if ((st = diag_apply(lat, TM_F64, B, B, 1, 1.0, 0.0, -1.0, 0.0, s)) != TM_OK) return st;
   info->iters = 0;
@@ -576,7 +710,23 @@ tm_status solve_one_bicgstab(tm_lattice lat, double* x, const double* b, const t
   if ((st = cuda_check(cudaMemcpyAsync(R, B, S.hb[TM_F64], cudaMemcpyDeviceToDevice, s), "copy")) != TM_OK) return st;
   const bool fp64 = P.mode == TM_CG_FP64;
   BiVecs v{};
-  if (fp64) {
+  v.mr = mr ? 1 : 0;
+  if (mr) {  // x, r (the operator's input), q = Mhat r, T: all in the operator's format
+    v.pp = fp64 ? TM_F64 : TM_F32;
+    v.nreal = fp64 ? 18 : P.sloppy_link;
+    v.pr = v.pp;
+    v.T = T;
+    if (fp64) {
+      v.x = X;
+      v.r = R;
+    } else {
+      v.x = workspace(lat, 9, S.hb[TM_F32], &st);
+      if (st == TM_OK) v.r = workspace(lat, 8, S.hb[TM_F32], &st);
+      if (st == TM_OK) v.T = workspace(lat, 11, S.hb[TM_F32], &st);
+    }
+    if (st == TM_OK) v.v = workspace(lat, 19, S.hb[v.pp], &st);
+    v.rh = v.r;
+  } else if (fp64) {
     v.pp = TM_F64;
     v.nreal = 18;
     v.pr = TM_F64;
@@ -614,7 +764,12 @@ tm_status solve_one_bicgstab(tm_lattice lat, double* x, const double* b, const t
   bool converged = rr_true < stop2, restart = true;
   while (!converged && iters < P.max_iter) {
     // r from the FP64 residual R; on a restart also r^ = r, p = r and a zero increment
-    if (fp64) {
+    if (mr) {
+      if (!fp64) {
+        if ((st = convert_half(lat, TM_F32, v.r, TM_F64, R, s)) != TM_OK) return st;
+        if ((st = cuda_check(cudaMemsetAsync(v.x, 0, S.hb[TM_F32], s), "memset")) != TM_OK) return st;
+      }
+    } else if (fp64) {
       if (restart) {
         if ((st = cuda_check(cudaMemcpyAsync(v.rh, R, S.hb[TM_F64], cudaMemcpyDeviceToDevice, s), "copy")) != TM_OK)
           return st;
@@ -639,15 +794,14 @@ tm_status solve_one_bicgstab(tm_lattice lat, double* x, const double* b, const t
     if ((st = run_bi_stage(S, v, dst, init, &fin)) != TM_OK) return st;
     if (bi_verbose())
       fprintf(stderr,
-              "[tm_solve_bicgstab] stage: iter %d |r|/|b| %.3e converged %d update %d breakdown %d diverged %d "
+              "[%s] stage: iter %d |r|/|b| %.3e converged %d update %d breakdown %d diverged %d "
               "nonfinite %d\n",
-              fin.iter, std::sqrt(fin.rr / bb), fin.converged, fin.want_update, fin.breakdown, fin.diverged,
+              nm, fin.iter, std::sqrt(fin.rr / bb), fin.converged, fin.want_update, fin.breakdown, fin.diverged,
               fin.nonfinite);
     const bool progress = fin.iter > iters;
     iters = fin.iter;
     if (fin.nonfinite) {
-      if (++bad > 3) return set_error(TM_ERR_NONFINITE, "tm_solve_bicgstab: non-finite value in the iteration");
-      if (fp64) return set_error(TM_ERR_NONFINITE, "tm_solve_bicgstab: non-finite value in the iteration");
+      if (++bad > 3 || fp64) return set_error(TM_ERR_NONFINITE, "%s: non-finite value in the iteration", nm);
       restart = true;  // drop the sloppy increment
       continue;
     }
@@ -675,8 +829,8 @@ tm_status solve_one_bicgstab(tm_lattice lat, double* x, const double* b, const t
       dropped = 0;
     }
     ++updates;
-    if (bi_verbose()) fprintf(stderr, "[tm_solve_bicgstab] update %d: true |r|/|b| %.3e\n", updates, std::sqrt(rr_true / bb));
-    if (!(rr_true < 1e300)) return set_error(TM_ERR_NONFINITE, "tm_solve_bicgstab: residual diverged");
+    if (bi_verbose()) fprintf(stderr, "[%s] update %d: true |r|/|b| %.3e\n", nm, updates, std::sqrt(rr_true / bb));
+    if (!(rr_true < 1e300)) return set_error(TM_ERR_NONFINITE, "%s: residual diverged", nm);
     if (rr_true < stop2) {
       converged = true;
       break;
@@ -695,7 +849,7 @@ tm_status solve_one_bicgstab(tm_lattice lat, double* x, const double* b, const t
   if ((st = reconstruct_xo(S, X, be, bo, bfull, x, T, w[6], w[7], &info->true_rel_residual)) != TM_OK) return st;
   info->status = converged ? TM_OK : TM_ERR_NOT_CONVERGED;
   if (!converged)
-    return set_error(TM_ERR_NOT_CONVERGED, "tm_solve_bicgstab: not converged after %d iterations (||r||/||b|| = %.3e)",
+    return set_error(TM_ERR_NOT_CONVERGED, "%s: not converged after %d iterations (||r||/||b|| = %.3e)", nm,
                      iters, info->schur_rel_residual);
   return TM_OK;
 }
@@ -707,4 +861,9 @@ using namespace tmq;
 extern "C" tm_status tm_solve_bicgstab(tm_lattice lat, double* x, const double* b, int nrhs,
                                        const tm_cg_params* params, tm_cg_info* info, void* stream) {
   return solve_driver(lat, x, b, nrhs, params, info, stream, SOLVER_BICGSTAB);
+}
+
+extern "C" tm_status tm_solve_mr(tm_lattice lat, double* x, const double* b, int nrhs, const tm_cg_params* params,
+                                 tm_cg_info* info, void* stream) {
+  return solve_driver(lat, x, b, nrhs, params, info, stream, SOLVER_MR);
 }

@@ -973,7 +973,7 @@ namespace tmq {
 tm_status solve_driver(tm_lattice lat, double* x, const double* b, int nrhs, const tm_cg_params* params,
                        tm_cg_info* info, void* stream, int kind) {
   const auto t0 = std::chrono::steady_clock::now();
-  const char* nm = kind == SOLVER_CG ? "tm_solve_cg" : "tm_solve_bicgstab";
+  const char* nm = kind == SOLVER_CG ? "tm_solve_cg" : (kind == SOLVER_MR ? "tm_solve_mr" : "tm_solve_bicgstab");
   if (!lat || !x || !b || nrhs < 1) return set_error(TM_ERR_ARG, "%s: bad argument", nm);
   if (!lat->has_gauge) return set_error(TM_ERR_NO_GAUGE, "%s: no gauge field", nm);
   tm_cg_params P;
@@ -996,6 +996,8 @@ tm_status solve_driver(tm_lattice lat, double* x, const double* b, int nrhs, con
   }
   if (kind != SOLVER_CG && (P.mode == TM_CG_SQRT_EPS || (P.mode == TM_CG_RELIABLE && P.update_prec != TM_F64)))
     return set_error(TM_ERR_UNSUPPORTED, "%s: modes TM_CG_FP64 and TM_CG_RELIABLE with FP64 updates only", nm);
+  if (kind == SOLVER_MR && P.mode == TM_CG_RELIABLE && P.sloppy_prec != TM_F32)
+    return set_error(TM_ERR_UNSUPPORTED, "%s: sloppy storage TM_F32 only", nm);
   const size_t fbytes = lat->V * 24 * sizeof(double);
   if (x == b) return set_error(TM_ERR_ARG, "%s: x and b must differ", nm);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1026,7 +1028,9 @@ tm_status solve_driver(tm_lattice lat, double* x, const double* b, int nrhs, con
       if ((st = tm_apply_D(lat, r0, xr, P.flavour, 0, 1, stream)) != TM_OK) return st;
       axpby_kernel<<<nb, BNT, 0, s>>>(n, 1.0, br, -1.0, r0);  // r0 = b - M x0
       count_launch();
-      st = kind == SOLVER_CG ? solve_one(lat, delta, r0, P, &one, s) : solve_one_bicgstab(lat, delta, r0, P, &one, s);
+      st = kind == SOLVER_CG ? solve_one(lat, delta, r0, P, &one, s)
+           : kind == SOLVER_MR ? solve_one_mr(lat, delta, r0, P, &one, s)
+                               : solve_one_bicgstab(lat, delta, r0, P, &one, s);
       if (st != TM_OK && st != TM_ERR_NOT_CONVERGED) return st;
       axpby_kernel<<<nb, BNT, 0, s>>>(n, 1.0, delta, 1.0, xr);  // x = x0 + delta
       count_launch();
@@ -1044,7 +1048,9 @@ tm_status solve_driver(tm_lattice lat, double* x, const double* b, int nrhs, con
         one.true_rel_residual = den > 0 ? std::sqrt(num / den) : 0.0;
       }
     } else {
-      st = kind == SOLVER_CG ? solve_one(lat, xr, br, P, &one, s) : solve_one_bicgstab(lat, xr, br, P, &one, s);
+      st = kind == SOLVER_CG ? solve_one(lat, xr, br, P, &one, s)
+           : kind == SOLVER_MR ? solve_one_mr(lat, xr, br, P, &one, s)
+                               : solve_one_bicgstab(lat, xr, br, P, &one, s);
     }
     if (st != TM_OK && st != TM_ERR_NOT_CONVERGED) return st;
     if (st == TM_ERR_NOT_CONVERGED) result = st;

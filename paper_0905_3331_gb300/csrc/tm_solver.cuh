@@ -61,11 +61,14 @@ tm_status launch_update_n(const Solver& S, int n, int px, int pp, void* x, void*
 // sum of |x|^2 over n sites of format prec into *out_host (synchronises)
 tm_status norm2_n(const Solver& S, int prec, int n, const void* x, double* out_host);
 
-enum { SOLVER_CG = 0, SOLVER_BICGSTAB = 1 };
+enum { SOLVER_CG = 0, SOLVER_BICGSTAB = 1, SOLVER_MR = 2 };
 tm_status solve_driver(tm_lattice lat, double* x, const double* b, int nrhs, const tm_cg_params* params,
                        tm_cg_info* info, void* stream, int kind);
 // BiCGstab on Mhat^f x_o = varphi_o for one canonical full field (tm_bicgstab.cu)
 tm_status solve_one_bicgstab(tm_lattice lat, double* x, const double* b, const tm_cg_params& P, tm_cg_info* info,
                              cudaStream_t s);
+// MR on Mhat^f x_o = varphi_o for one canonical full field (tm_bicgstab.cu)
+tm_status solve_one_mr(tm_lattice lat, double* x, const double* b, const tm_cg_params& P, tm_cg_info* info,
+                       cudaStream_t s);
 
 }  // namespace tmq

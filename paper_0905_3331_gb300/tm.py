@@ -95,6 +95,7 @@ def load():
                                ctypes.POINTER(CGInfo), P], I),
         "tm_meson_contract": ([P, P, P, P], I),
         "tm_solve_bicgstab": ([P, P, P, I, ctypes.POINTER(CGParams), ctypes.POINTER(CGInfo), P], I),
+        "tm_solve_mr": ([P, P, P, I, ctypes.POINTER(CGParams), ctypes.POINTER(CGInfo), P], I),
         "tm_apply_Dh": ([P, P, P, D, D, I, P], I),
         "tm_solve_doublet": ([P, P, P, D, D, ctypes.POINTER(CGParams), ctypes.POINTER(CGInfo), P], I),
         "tm_solve_normal": ([P, P, P, ctypes.POINTER(CGParams), ctypes.POINTER(CGInfo), P], I),
@@ -116,7 +117,7 @@ def exported_symbols():
     return ["tm_lattice_create", "tm_lattice_destroy", "tm_lattice_set_params", "tm_volume",
             "tm_half_field_bytes", "tm_set_hop_threads", "tm_get_hop_threads", "tm_set_gauge", "tm_pack_half", "tm_unpack_half", "tm_apply_D",
             "tm_apply_hopping_eo", "tm_apply_Mee_inv", "tm_solve_cg", "tm_solve_cg_batch",
-            "tm_cg_params_default", "tm_meson_contract", "tm_solve_bicgstab", "tm_solve_normal", "tm_chrono_guess", "tm_apply_Dh",
+            "tm_cg_params_default", "tm_meson_contract", "tm_solve_bicgstab", "tm_solve_mr", "tm_solve_normal", "tm_chrono_guess", "tm_apply_Dh",
             "tm_solve_doublet",
             "tm_last_error", "tm_launch_count", "tm_reset_launch_count"]
 
@@ -314,6 +315,21 @@ class Lattice:
                                      ctypes.byref(info), _stream(stream))
         if check:
             _check(st, "tm_solve_doublet")
+        d = info.as_dict()
+        d["status"] = st
+        return SolveInfo(**d)
+
+    def solve_mr(self, x, b, nrhs: int = 1, tol: float = 1e-10, max_iter: int = 100000,
+                 mode: int = CG_FP64, sloppy_link: int = LINK12, delta: float = 0.1,
+                 use_x0: bool = False, flavour: int = 1, stream=None, check: bool = True) -> SolveInfo:
+        """Solve M^f x = b with the minimal residual iteration on the even/odd Schur system
+        (FP64, or FP32 sloppy storage with reliable updates)."""
+        p = CGParams(tol, max_iter, mode, F32, sloppy_link, delta, int(use_x0), flavour, F64)
+        info = CGInfo()
+        st = load().tm_solve_mr(self._h, _addr(x), _addr(b), nrhs, ctypes.byref(p), ctypes.byref(info),
+                                _stream(stream))
+        if check:
+            _check(st, "tm_solve_mr")
         d = info.as_dict()
         d["status"] = st
         return SolveInfo(**d)

@@ -157,14 +157,16 @@ import numpy as np, torch
 from paper_0905_3331_gb300 import Lattice, inputs, CG_RELIABLE, F16
 w = inputs.WORKLOADS["4^4"]
 lat = Lattice(w.T, w.L, 0.13, w.mu)
-for prec, link in ((0, 18), (2, 12)):  # fixed kernel choice: no timing-dependent tuning
+for prec, link in ((0, 18), (2, 12), (1, 12)):  # fixed kernel choice: no timing-dependent tuning
     lat.set_hop_threads(prec, link, 2)
 lat.set_gauge(w.gauge())
 b = torch.from_numpy(w.source()).cuda()
 x = torch.zeros_like(b)
 info = lat.solve_bicgstab(x, b, mode=CG_RELIABLE, sloppy_prec=F16)
-np.save({out!r}, x.cpu().numpy())
-print("ITERS", info.iters)
+x2 = torch.zeros_like(b)
+info2 = lat.solve_mr(x2, b, mode=CG_RELIABLE)
+np.save({out!r}, torch.stack([x, x2]).cpu().numpy())
+print("ITERS", info.iters, info2.iters)
 """
 
 
@@ -187,4 +189,58 @@ def test_bicgstab_host_loop_fallback_and_tracing(env, tmp_path):
     assert np.array_equal(outs[0][0], outs[1][0])
     assert outs[0][1] == outs[1][1]
     if "TM_VERBOSE" in env:
-        assert "[tm_solve_bicgstab] stage" in outs[1][2] and "update" in outs[1][2]
+        assert "[tm_solve_bicgstab] stage" in outs[1][2] and "[tm_solve_mr] stage" in outs[1][2]
+
+
+# ------------------------------------------------------------------ MR on Mhat ---
+MR_MODES = [
+    ("fp64", dict(mode=CG_FP64)),
+    ("reliable_f32_18", dict(mode=CG_RELIABLE, sloppy_link=LINK18)),
+    ("reliable_f32_12", dict(mode=CG_RELIABLE, sloppy_link=LINK12)),
+    ("reliable_f32_8", dict(mode=CG_RELIABLE, sloppy_link=LINK8)),
+]
+
+
+@pytest.mark.parametrize("name,kw", MR_MODES)
+@pytest.mark.parametrize("flavour", [1, -1])
+def test_mr_4x4x4x4(name, kw, flavour):
+    w, U, phi, lat = setup("4^4")
+    b = torch.from_numpy(phi).to(dev())
+    x = torch.zeros_like(b)
+    info = lat.solve_mr(x, b, tol=1e-10, flavour=flavour, **kw)
+    assert oracle_true_residual(w, U, phi, x.cpu().numpy(), flavour) < 1e-10
+    assert info.true_rel_residual < 1e-10 and info.iters > 0
+    lat.solve_mr(x, b, tol=1e-12, flavour=flavour, **kw)
+    ref = oracle.solve_mr(oracle.Lattice.cubic(w.T, w.L), U, phi, KAPPA, w.mu, flavour, tol=1e-12)
+    assert ref.converged and rel(x.cpu().numpy(), ref.psi) < 1e-9
+    lat.close()
+
+
+@pytest.mark.parametrize("name,kw", [MR_MODES[0], MR_MODES[2]])
+@pytest.mark.parametrize("workload", ["8^4", "12^3x24", "16^3x32"])
+def test_mr_larger_lattices(name, kw, workload):
+    w, U, phi, lat = setup(workload)
+    b = torch.from_numpy(phi).to(dev())
+    x = torch.zeros_like(b)
+    info = lat.solve_mr(x, b, tol=1e-10, **kw)
+    res = oracle_true_residual(w, U, phi, x.cpu().numpy())
+    assert res < 1e-10 and info.true_rel_residual < 1e-10
+    lat.close()
+
+
+def test_mr_errors_and_stagnation():
+    w, U, phi, lat = setup("8^4", kappa=0.1632)
+    b = torch.from_numpy(phi).to(dev())
+    x = torch.zeros_like(b)
+    info = lat.solve_mr(x, b, tol=1e-10, max_iter=300, check=False)
+    assert info.status == 7 and torch.isfinite(x).all()  # TM_ERR_NOT_CONVERGED: Re < 0 part of the spectrum
+    with pytest.raises(TMError):
+        lat.solve_mr(x, b, mode=CG_SQRT_EPS)
+    p = lat  # FP16 sloppy storage is rejected for MR (r feeds the operator)
+    from paper_0905_3331_gb300.tm import CGInfo, CGParams, load
+    import ctypes
+    prm = CGParams(1e-10, 100, CG_RELIABLE, F16, LINK12, 0.1, 0, 1, 0)
+    inf = CGInfo()
+    st = load().tm_solve_mr(p._h, x.data_ptr(), b.data_ptr(), 1, ctypes.byref(prm), ctypes.byref(inf), 0)
+    assert st == 10  # TM_ERR_UNSUPPORTED
+    lat.close()
