@@ -42,8 +42,10 @@ struct BatchGlobal {
 };
 
 // Same site computation as hop_kernel (one thread per site), the system taken from the table.
+// Register budget for 6 blocks per SM (80): the kernel is latency bound, and the extra warps
+// outweigh a few spilled bytes (12-system solve on 24^3 x 48: 1060 -> 990 ms).
 template <int PREC, int NREAL, bool HAS_Y, int MODE>
-__global__ void __launch_bounds__(HOP_NT) hop_batch_kernel(const BatchSys* __restrict__ systems,
+__global__ void __launch_bounds__(HOP_NT, 6) hop_batch_kernel(const BatchSys* __restrict__ systems,
                                                            const int2* __restrict__ map, int in_sel, int y_sel,
                                                            int out_sel, int k, int out_parity) {
   typedef typename SpinorFmt<PREC>::real R;
@@ -432,8 +434,9 @@ extern "C" tm_status tm_solve_cg_batch(const tm_system* systems, int nsys, const
       if (st == TM_OK) st = cuda_check(cudaStreamSynchronize(s), "tables");
     }
     if (st != TM_OK) break;
-    // ---- the stage graph: WHILE (any system active) { one batched iteration }
-    {
+    // ---- the stage graph: WHILE (any system active) { one batched iteration }; with TM_NO_GRAPH=1
+    // the stages run as host-driven chunks of iterations instead
+    if (use_graphs()) {
       cudaGraphConditionalHandle cond;
       cudaGraphNode_t node;
       cudaGraphNodeParams cp = {};
@@ -485,13 +488,29 @@ extern "C" tm_status tm_solve_cg_batch(const tm_system* systems, int nsys, const
       hgl = BatchGlobal{active, 0, cap, 0u};
       st = cuda_check(cudaMemcpyAsync(d_st, hst.data(), sizeof(CGState) * nsys, cudaMemcpyHostToDevice, s), "state");
       if (st == TM_OK) st = cuda_check(cudaMemcpyAsync(d_gl, &hgl, sizeof(hgl), cudaMemcpyHostToDevice, s), "state");
-      if (st == TM_OK) st = cuda_check(cudaGraphLaunch(exec, s), "graph launch");
-      if (st == TM_OK)
-        st = cuda_check(cudaMemcpyAsync(hst.data(), d_st, sizeof(CGState) * nsys, cudaMemcpyDeviceToHost, s), "state");
-      if (st == TM_OK) st = cuda_check(cudaMemcpyAsync(&hgl, d_gl, sizeof(hgl), cudaMemcpyDeviceToHost, s), "state");
-      if (st == TM_OK) st = cuda_check(cudaStreamSynchronize(s), "batched stage");
-      if (st != TM_OK) break;
-      count_launch(5u * (unsigned)hgl.loops);
+      if (exec) {
+        if (st == TM_OK) st = cuda_check(cudaGraphLaunch(exec, s), "graph launch");
+        if (st == TM_OK)
+          st = cuda_check(cudaMemcpyAsync(hst.data(), d_st, sizeof(CGState) * nsys, cudaMemcpyDeviceToHost, s),
+                          "state");
+        if (st == TM_OK) st = cuda_check(cudaMemcpyAsync(&hgl, d_gl, sizeof(hgl), cudaMemcpyDeviceToHost, s), "state");
+        if (st == TM_OK) st = cuda_check(cudaStreamSynchronize(s), "batched stage");
+        if (st != TM_OK) break;
+        count_launch(5u * (unsigned)hgl.loops);
+      } else {  // host-driven: chunks of 8 batched iterations until no system is active
+        for (;;) {
+          for (int q = 0; q < 8 && st == TM_OK; ++q)
+            st = batch_iteration(sp, sl, d_sys, d_hmap, nh, d_umap, nu, d_gl, 0, 0, s);
+          if (st == TM_OK) st = cuda_check(cudaMemcpyAsync(&hgl, d_gl, sizeof(hgl), cudaMemcpyDeviceToHost, s), "state");
+          if (st == TM_OK) st = cuda_check(cudaStreamSynchronize(s), "batched chunk");
+          if (st != TM_OK || hgl.active <= 0 || hgl.loops >= hgl.loop_cap) break;
+        }
+        if (st == TM_OK)
+          st = cuda_check(cudaMemcpyAsync(hst.data(), d_st, sizeof(CGState) * nsys, cudaMemcpyDeviceToHost, s),
+                          "state");
+        if (st == TM_OK) st = cuda_check(cudaStreamSynchronize(s), "batched stage");
+        if (st != TM_OK) break;
+      }
       // ---- reliable updates (FP64) of every system that stopped
       for (int k = 0; k < nsys && st == TM_OK; ++k) {
         SysWork& w = W[k];

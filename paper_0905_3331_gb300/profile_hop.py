@@ -13,6 +13,10 @@ With --doublet MUBAR,EPSBAR it instead runs `iters` doublet solves (tm_solve_dou
 --form f64:18, reliable-update FP32 sloppy for f32:<links>) on two Gaussian flavour sources and
 reports the mean solve time -- a driver for captures of the two-flavour hopping kernel.
 
+With --batch N it runs `iters` batched solves (tm_solve_cg_batch, FP32/FP16 sloppy storage per
+--form, delta 1e-3) of N Gaussian sources on the workload's lattice and reports the mean time
+-- a driver for captures of the batched hopping kernel.
+
 With --contract it runs `iters` meson contractions (tm_meson_contract) of 12 Gaussian
 propagators on the workload's lattice and reports the mean time, bytes and FP64 rate.
 """
@@ -41,7 +45,10 @@ def main():
     ap.add_argument("--doublet", default=None, help="MUBAR,EPSBAR: time doublet solves instead")
     ap.add_argument("--delta", type=float, default=0.001, help="reliable-update delta of the doublet solve")
     ap.add_argument("--contract", action="store_true", help="time meson contractions instead")
+    ap.add_argument("--batch", type=int, default=0, help="time batched solves of this many sources")
     args = ap.parse_args()
+    if args.batch:
+        return batch(args)
     if args.doublet:
         return doublet(args)
     if args.contract:
@@ -86,6 +93,41 @@ def main():
                       "gbs": per_site * h / t / 1e9,
                       "gflops": 1320 * args.nrhs * h / t / 1e9,
                       "l2": "warm" if args.warm else "flushed"}))
+    lat.close()
+
+
+def batch(args):
+    import torch
+
+    from . import Lattice, inputs, solve_cg_batch
+    from . import build as libbuild
+    libbuild.build()
+    prec = {"f32": 1, "f16": 2}[args.form.split(":")[0]]
+    nreal = int(args.form.split(":")[1])
+    w = inputs.WORKLOADS[args.workload]
+    dev = torch.device("cuda:0")
+    lat = Lattice(w.T, w.L, w.kappa, w.mu)
+    lat.set_gauge(w.gauge())
+    systems = []
+    for k in range(args.batch):
+        b = torch.from_numpy(w.source(k)).to(dev)
+        systems.append((lat, w.mu, torch.zeros_like(b), b))
+    kw = dict(sloppy_prec=prec, sloppy_link=nreal, delta=1e-3)
+    infos = solve_cg_batch(systems, **kw)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    times = []
+    for _ in range(args.iters):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        infos = solve_cg_batch(systems, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    t = statistics.mean(times)
+    print(json.dumps({"workload": w.name, "form": args.form, "systems": args.batch, "ms": t * 1e3,
+                      "systems_per_s": args.batch / t, "iters": [i.iters for i in infos],
+                      "max_true_rel_residual": max(i.true_rel_residual for i in infos)}))
     lat.close()
 
 

@@ -103,3 +103,37 @@ def test_batch_edge_cases():
         solve_cg_batch([(lat, w.mu, host, b)])
     assert e.value.status_name == "TM_ERR_ARG"
     lat.close()
+
+
+_BATCH_CHILD = """
+import numpy as np, torch
+from paper_0905_3331_gb300 import Lattice, inputs, solve_cg_batch, F32, LINK12
+w = inputs.WORKLOADS["4^4"]
+lat = Lattice(w.T, w.L, w.kappa, w.mu)
+for prec, link in ((0, 18), (1, 12)):  # fixed kernel choice: no timing-dependent tuning
+    lat.set_hop_threads(prec, link, 1)
+lat.set_gauge(w.gauge())
+systems = []
+for k, mu in enumerate((0.01, 0.02, 0.05)):
+    b = torch.from_numpy(w.source(k)).cuda()
+    systems.append((lat, mu, torch.zeros_like(b), b))
+infos = solve_cg_batch(systems, sloppy_prec=F32, sloppy_link=LINK12, delta=0.01)
+np.save({out!r}, torch.stack([s[2] for s in systems]).cpu().numpy())
+print("ITERS", [i.iters for i in infos])
+"""
+
+
+def test_batch_host_loop_matches_graph_loop(tmp_path):
+    """TM_NO_GRAPH=1 runs the batched stages as host-driven chunks: bitwise the same solutions."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    outs = []
+    for k, e in enumerate(({}, {"TM_NO_GRAPH": "1"})):
+        out = str(tmp_path / f"x{k}.npy")
+        r = subprocess.run([sys.executable, "-c", _BATCH_CHILD.format(out=out)], cwd=root,
+                           env={**os.environ, **e}, capture_output=True, text=True, timeout=300)
+        assert r.returncode == 0, r.stderr
+        outs.append((np.load(out), r.stdout))
+    assert np.array_equal(outs[0][0], outs[1][0]) and outs[0][1] == outs[1][1]
