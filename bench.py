@@ -32,7 +32,7 @@ METRIC = "Dslash GB/s & % HBM roofline; CG solves/sec to 1e-10 FP64 residual, mi
 HOP_FLOPS = 1320  # per output site per hopping application (8 hops x 168 flops - 24)
 # dram__bytes_read.sum + dram__bytes_write.sum of one hop_kernel<FP32, 12-real> launch on the
 # 16^3 x 32 lattice, ncu --set full capture (profiles/hop_f32_12_16x32_and_32x64_full.md)
-NCU_TRAFFIC = {("f32:12", "16^3x32"): 31488768.0}
+NCU_TRAFFIC = {("f32:12", "16^3x32"): 31492864.0}
 
 
 def hop_bytes_per_site(prec: int, nreal: int) -> int:
