@@ -187,6 +187,8 @@ __global__ void __launch_bounds__(hop_spb(TPS) * TPS, hop_min_blocks(PREC, TPS))
   __shared__ double sh[NT / 32];
   __shared__ R part_acc[TPS > 1 ? TPS * SPB * STRIDE : 1];
   __shared__ float part_max[(TPS > 1 && F::has_norm) ? TPS * SPB : 1];
+  pdl_wait();
+  pdl_allow();
   if (skip != nullptr && *skip != 0) return;
   const int rhs = blockIdx.y;
   const int warp = threadIdx.x >> 5;
@@ -305,15 +307,15 @@ tm_status hop_launch_tps(tm_lattice lat, const HopArgs& a, cudaStream_t s) {
   g, a.out_parity, links, a.in, a.in_stride, a.out, a.out_stride, a.y, a.y_stride, a.coef, a.alpha_src, \
       a.alpha_sign, a.red, a.skip
   if (!has_y && a.mode == 0)
-    hop_kernel<PREC, NREAL, false, 0, TPS><<<grid, NT, 0, s>>>(TM_HOP_ARGS);
+    launch_pdl(hop_kernel<PREC, NREAL, false, 0, TPS>, grid, dim3(NT), s, TM_HOP_ARGS);
   else if (!has_y && a.mode == 1)
-    hop_kernel<PREC, NREAL, false, 1, TPS><<<grid, NT, 0, s>>>(TM_HOP_ARGS);
+    launch_pdl(hop_kernel<PREC, NREAL, false, 1, TPS>, grid, dim3(NT), s, TM_HOP_ARGS);
   else if (has_y && a.mode == 0)
-    hop_kernel<PREC, NREAL, true, 0, TPS><<<grid, NT, 0, s>>>(TM_HOP_ARGS);
+    launch_pdl(hop_kernel<PREC, NREAL, true, 0, TPS>, grid, dim3(NT), s, TM_HOP_ARGS);
   else if (has_y && a.mode == 1)
-    hop_kernel<PREC, NREAL, true, 1, TPS><<<grid, NT, 0, s>>>(TM_HOP_ARGS);
+    launch_pdl(hop_kernel<PREC, NREAL, true, 1, TPS>, grid, dim3(NT), s, TM_HOP_ARGS);
   else if (has_y && a.mode == 2)
-    hop_kernel<PREC, NREAL, true, 2, TPS><<<grid, NT, 0, s>>>(TM_HOP_ARGS);
+    launch_pdl(hop_kernel<PREC, NREAL, true, 2, TPS>, grid, dim3(NT), s, TM_HOP_ARGS);
   else
     return set_error(TM_ERR_ARG, "hopping: unsupported epilogue combination");
 #undef TM_HOP_ARGS

@@ -831,8 +831,34 @@ __device__ __forceinline__ void grid_reduce(const Reduce& red, int sys, int nblo
   }
 }
 
+// ------------------------------------------------ programmatic dependent launch ---
+// A kernel launched with the programmatic-stream-serialization attribute may be scheduled while
+// its predecessor in the stream is still running: pdl_wait() holds its threads until the
+// predecessor has completed and its writes are visible, pdl_allow() lets the next kernel be
+// scheduled once every block of this one has called it.  Both are no-ops when the kernel was
+// launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_allow() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // -------------------------------------------------------------- host side ---
 void count_launch(unsigned n = 1);
+bool use_pdl();  // programmatic dependent launch of the iteration kernels (TM_PDL=1; off by default)
+
+// Launches `kernel` on `s` with the programmatic-stream-serialization attribute when use_pdl().
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = use_pdl() ? 1 : 0;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
 tm_status set_error(tm_status st, const char* fmt, ...);
 tm_status cuda_check(cudaError_t e, const char* what);
 

@@ -349,6 +349,17 @@ static tm_status tune_hop(tm_lattice lat, int prec, int nreal, cudaStream_t s) {
   return st;
 }
 
+// Off by default: measured on the 16^3 x 32 mixed solve, programmatic dependent launch of the
+// iteration kernels made the solve slower (123 vs 140 solves/s); TM_PDL=1 turns it on.
+bool use_pdl() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("TM_PDL");
+    v = (e && *e == '1') ? 1 : 0;
+  }
+  return v == 1;
+}
+
 void invalidate_graphs(tm_lattice lat) {
   for (int k = 0; k < 8; ++k) {
     if (lat->graphs[k].valid) {

@@ -53,6 +53,8 @@ template <int PX, int PP, int PR>
 __global__ void __launch_bounds__(BNT) cg_update_kernel(int h, char* x, char* p, const char* r, CGState* st,
                                                         unsigned* counter, cudaGraphConditionalHandle cond,
                                                         int use_cond) {
+  pdl_wait();
+  pdl_allow();
   CGState& S = st[0];
   const int iter = S.iter;
   if (iter == S.applied) {
@@ -271,11 +273,11 @@ tm_status launch_update_n(const Solver& S, int n, int px, int pp, void* x, void*
   const char* rc = static_cast<const char*>(r);
   unsigned* ctr = lat->counters + 2;
   if (px == TM_F64)
-    cg_update_kernel<TM_F64, TM_F64, TM_F64><<<nb, BNT, 0, S.s>>>(n, xc, pc, rc, state, ctr, cond, use_cond);
+    launch_pdl(cg_update_kernel<TM_F64, TM_F64, TM_F64>, dim3(nb), dim3(BNT), S.s, n, xc, pc, rc, state, ctr, cond, use_cond);
   else if (pp == TM_F32)
-    cg_update_kernel<TM_F32, TM_F32, TM_F32><<<nb, BNT, 0, S.s>>>(n, xc, pc, rc, state, ctr, cond, use_cond);
+    launch_pdl(cg_update_kernel<TM_F32, TM_F32, TM_F32>, dim3(nb), dim3(BNT), S.s, n, xc, pc, rc, state, ctr, cond, use_cond);
   else
-    cg_update_kernel<TM_F32, TM_F16, TM_F32><<<nb, BNT, 0, S.s>>>(n, xc, pc, rc, state, ctr, cond, use_cond);
+    launch_pdl(cg_update_kernel<TM_F32, TM_F16, TM_F32>, dim3(nb), dim3(BNT), S.s, n, xc, pc, rc, state, ctr, cond, use_cond);
   count_launch();
   return cuda_check(cudaGetLastError(), "CG update kernel");
 }
