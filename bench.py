@@ -582,7 +582,10 @@ def run_reference(args):
     from paper_0905_3331_gb300 import inputs
     w = inputs.WORKLOADS[args.workload]
     U, phi = w.gauge(), w.source()
-    iters = args.ref_iters
+    iters, how = args.ref_iters, "given"
+    if iters <= 0:  # first warm-up step: one complete oracle solve gives the iteration count
+        res = oracle.solve(oracle.Lattice.cubic(w.T, w.L), U, phi, w.kappa, w.mu, tol=1e-10)
+        iters, how = res.iters, "of the oracle's own complete FP64 solve to 1e-10"
     for _ in range(args.warmup):
         oracle_cg_rate(w, U, phi, 0.0)
     per_step = []
@@ -594,7 +597,8 @@ def run_reference(args):
     cb = {"value": round(value, 6), "unit": "solves/s", "cores": oracle.num_threads(),
           "kind": "oracle",
           "sample": f"each step: oracle FP64 CG on {w.name} timed for ~{args.ref_seconds} s, "
-                    f"extrapolated to {iters} iterations per solve"}
+                    f"extrapolated to {iters} iterations per solve ({how}), plus one source "
+                    "preparation and reconstruction"}
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "solves/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -628,8 +632,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the BiCGstab, chronological-guess and contraction measurements")
     ap.add_argument("--ref-seconds", type=float, default=8.0)
-    ap.add_argument("--ref-iters", type=int, default=1500,
-                    help="CG iterations per solve used to scale the reference arm's sample")
+    ap.add_argument("--ref-iters", type=int, default=0,
+                    help="CG iterations per solve used to scale the reference arm's sample (0: take them from one complete oracle solve)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the sloppy hopping kernel, if measured")
     args = ap.parse_args()
