@@ -170,7 +170,7 @@ print("ITERS", info.iters, info2.iters)
 """
 
 
-@pytest.mark.parametrize("env", [{"TM_NO_GRAPH": "1"}, {"TM_VERBOSE": "1"}])
+@pytest.mark.parametrize("env", [{"TM_NO_GRAPH": "1"}, {"TM_VERBOSE": "1"}, {"TM_PDL": "1"}])
 def test_bicgstab_host_loop_fallback_and_tracing(env, tmp_path):
     """The host-driven chunk loop (TM_NO_GRAPH=1) gives bitwise the solution of the graph loop
     (fixed-order sums); TM_VERBOSE=1 traces the stages.  Child processes read the environment

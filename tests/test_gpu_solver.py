@@ -191,10 +191,12 @@ print("ITERS", info.iters)
 """
 
 
-@pytest.mark.parametrize("env", [{"TM_NO_GRAPH": "1"}, {"TM_VERBOSE": "1"}])
+@pytest.mark.parametrize("env", [{"TM_NO_GRAPH": "1"}, {"TM_VERBOSE": "1"}, {"TM_PDL": "1"},
+                                 {"TM_PDL": "1", "TM_NO_GRAPH": "1"}])
 def test_host_loop_fallback_and_tracing(env, tmp_path):
-    """The host-driven stage loop (TM_NO_GRAPH=1) gives bitwise the same solution as the
-    CUDA-graph loop (all reductions have a fixed order); TM_VERBOSE=1 traces the stages."""
+    """The host-driven stage loop (TM_NO_GRAPH=1) and programmatic dependent launch (TM_PDL=1)
+    give bitwise the same solution as the CUDA-graph loop (all reductions have a fixed order);
+    TM_VERBOSE=1 traces the stages."""
     import os
     import subprocess
     import sys
@@ -257,4 +259,24 @@ def test_full_size_precision_forms(name, sloppy, link, delta):
     res = oracle_true_residual(w, U, phi, x.cpu().numpy())
     assert res < 1e-10 and info.true_rel_residual < 1e-10
     assert abs(res - info.true_rel_residual) < 1e-3 * res
+    lat.close()
+
+
+def test_bench_configuration_16x16x16x32():
+    """The solve bench.py times (16^3 x 32, FP32 storage, 12-real links, reliable updates at
+    delta 1e-5, host and device buffers): the oracle's M applied to the GPU solution gives a true
+    residual below 1e-10, and the reported residual agrees with it."""
+    w = inputs.WORKLOADS["16^3x32"]
+    U, phi = w.gauge(), w.source()
+    lat = Lattice(w.T, w.L, w.kappa, w.mu)
+    lat.set_gauge(U)
+    b = torch.from_numpy(phi).to(dev())
+    x = torch.zeros_like(b)
+    kw = dict(mode=CG_RELIABLE, sloppy_prec=F32, sloppy_link=LINK12, delta=1e-5)
+    info = lat.solve_cg(x, b, tol=1e-10, **kw)
+    res = oracle_true_residual(w, U, phi, x.cpu().numpy())
+    assert res < 1e-10 and abs(res - info.true_rel_residual) < 1e-3 * res
+    xh = np.zeros_like(phi)
+    lat.solve_cg(xh, phi, tol=1e-10, **kw)
+    assert np.array_equal(xh, x.cpu().numpy())
     lat.close()
