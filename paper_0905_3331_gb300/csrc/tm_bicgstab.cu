@@ -87,11 +87,19 @@ __device__ __forceinline__ bool grid_sum(double (&v)[N], double* partials, unsig
   __syncthreads();
   if (!last) return false;
   __threadfence();
-  const volatile double* parts = partials;
 #pragma unroll
   for (int k = 0; k < N; ++k) {
-    double x = 0.0;
-    for (int b = threadIdx.x; b < nb; b += BNT) x += parts[(size_t)k * nb + b];
+    double x = 0.0;  // partials b = t, t + BNT, ... in order, loads of a group of 8 issued together
+    for (int base = threadIdx.x; base < nb; base += 8 * BNT) {
+      double t[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int b = base + u * BNT;
+        t[u] = b < nb ? __ldcg(partials + (size_t)k * nb + b) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) x += t[u];
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
     __syncthreads();

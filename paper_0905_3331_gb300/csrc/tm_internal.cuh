@@ -820,9 +820,21 @@ __device__ __forceinline__ void grid_reduce(const Reduce& red, int sys, int nblo
   __syncthreads();
   if (!last) return;
   __threadfence();
+  // thread t adds partials t, t + NT, t + 2 NT, ... in that order; the loads of a group of 8
+  // are issued together (L2, bypassing L1, where the other blocks' partials are visible after
+  // their fence and this block's counter observation) so the tail pays one round trip per group
   double v = 0.0;
-  const volatile double* parts = red.partials + (size_t)sys * nblocks;
-  for (int k = threadIdx.x; k < nblocks; k += NT) v += parts[k];
+  const double* parts = red.partials + (size_t)sys * nblocks;
+  for (int base = threadIdx.x; base < nblocks; base += 8 * NT) {
+    double t[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int k = base + u * NT;
+      t[u] = k < nblocks ? __ldcg(parts + k) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v += t[u];
+  }
   __syncthreads();
   double tot = block_sum<NT>(v, sh);
   if (threadIdx.x == 0) {
