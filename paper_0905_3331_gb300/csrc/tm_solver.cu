@@ -31,6 +31,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <vector>
 
 #include "tm_internal.cuh"
 #include "tm_solver.cuh"
@@ -1015,7 +1016,24 @@ tm_status solve_driver(tm_lattice lat, double* x, const double* b, int nrhs, con
   tm_cg_info worst{};
   worst.status = TM_OK;
   tm_status result = TM_OK;
-  for (int r = 0; r < nrhs; ++r) {
+  // several right-hand sides in the reliable-update mode: solved together by the batched solver
+  // (their sloppy iterations share launches and link reads)
+  const bool batched = kind == SOLVER_CG && nrhs > 1 && P.mode == TM_CG_RELIABLE && P.update_prec == TM_F64 &&
+                       !P.use_x0;
+  if (batched) {
+    std::vector<tm_system> sys(nrhs);
+    std::vector<tm_cg_info> infos(nrhs);
+    for (int r = 0; r < nrhs; ++r)
+      sys[r] = tm_system{lat, lat->mu, P.flavour, dx + (size_t)r * lat->V * 24, db + (size_t)r * lat->V * 24};
+    st = tm_solve_cg_batch(sys.data(), nrhs, &P, infos.data(), stream);
+    if (st != TM_OK && st != TM_ERR_NOT_CONVERGED) return st;
+    result = st;
+    for (int r = 0; r < nrhs; ++r) {
+      if (r == 0 || infos[r].true_rel_residual > worst.true_rel_residual) worst = infos[r];
+      if (infos[r].iters > worst.iters) worst.iters = infos[r].iters;
+    }
+  }
+  for (int r = 0; r < (batched ? 0 : nrhs); ++r) {
     double* xr = dx + (size_t)r * lat->V * 24;
     const double* br = db + (size_t)r * lat->V * 24;
     tm_cg_info one{};

@@ -280,3 +280,25 @@ def test_bench_configuration_16x16x16x32():
     lat.solve_cg(xh, phi, tol=1e-10, **kw)
     assert np.array_equal(xh, x.cpu().numpy())
     lat.close()
+
+
+def test_multiple_rhs_reliable_mode_goes_through_the_batched_solver():
+    """nrhs = 3 in the reliable-update mode: solved together (tm_solve_cg_batch inside
+    tm_solve_cg); every solution meets the oracle-checked bar, device and host buffers alike."""
+    w = inputs.WORKLOADS["8^4"]
+    U = w.gauge()
+    phis = np.stack([w.source(k) for k in range(3)])
+    lat = Lattice(w.T, w.L, w.kappa, w.mu)
+    lat.set_gauge(U)
+    kw = dict(mode=CG_RELIABLE, sloppy_prec=F32, sloppy_link=LINK12, delta=1e-3)
+    b = torch.from_numpy(phis).to(dev())
+    x = torch.zeros_like(b)
+    info = lat.solve_cg(x, b, nrhs=3, flavour=-1, **kw)
+    xs = x.cpu().numpy()
+    for k in range(3):
+        assert oracle_true_residual(w, U, phis[k], xs[k], f=-1) < 1e-10
+    assert info.true_rel_residual < 1e-10
+    xh = np.zeros_like(phis)
+    lat.solve_cg(xh, phis, nrhs=3, flavour=-1, **kw)
+    assert np.array_equal(xh, xs)
+    lat.close()
