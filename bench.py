@@ -111,6 +111,15 @@ class ClockSampler:
 
 
 # -------------------------------------------------------- multi-rank logic ---
+def trimmed_mean(ts, frac: float = 0.1) -> float:
+    """Mean of the launch times without the lowest and highest `frac` (a stray launch that the
+    host or another process delays by 50-150 us would otherwise dominate a ~14 us average)."""
+    ts = sorted(ts)
+    k = int(len(ts) * frac)
+    core = ts[k:len(ts) - k] if len(ts) > 2 * k else ts
+    return statistics.mean(core)
+
+
 def reduce_max(v: float, world: int, device) -> float:
     """Max of a per-rank value over all ranks (the slowest rank's time)."""
     if world == 1:
@@ -240,7 +249,7 @@ def run_gpu(args):
                 e1.record(stream)
                 torch.cuda.synchronize()
                 ts.append(e0.elapsed_time(e1) / 1e3)
-            return statistics.mean(ts)
+            return trimmed_mean(ts)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for k in range(n):
@@ -275,11 +284,12 @@ def run_gpu(args):
                 "achieved": round(top["gbs_cold"], 1), "peak": peak, "unit": "GB/s",
                 "frac": round(top["gbs_cold"] / peak, 4),
                 "traffic": args.traffic, "peak_kind": peak_kind,
-                "timing": "per-launch CUDA events; before each launch L2 flushed (512 MB write) "
-                          "and cleaned (256 MB read)"}
+                "timing": "per-launch CUDA events, mean of the middle 80% of the launches; before each "
+                          "launch L2 flushed (512 MB write) and cleaned (256 MB read)"}
 
     batched = None if args.no_batched else batched_measurement(args, dev)
     extras = None if args.no_extras else extra_measurements(args, dev, w, U, phi)
+    precision = None if args.no_precision_form else precision_form_measurement(args, dev)
 
     n_units = args.steps * world
     value = whole_job_rate(args.steps, world, t_mixed)
@@ -308,6 +318,7 @@ def run_gpu(args):
         "gpu_launches": int(launches),
         "batched": batched,
         "solver_variants": extras,
+        "precision_form": precision,
         "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -330,7 +341,7 @@ def batched_measurement(args, dev):
     iterations, and the FP32 recursion drifts below delta ~ 1e-4 there."""
     import torch
 
-    from paper_0905_3331_gb300 import CG_RELIABLE, Lattice, inputs, solve_cg_batch
+    from paper_0905_3331_gb300 import CG_FP64, CG_RELIABLE, Lattice, inputs, solve_cg_batch
     sp, sl = parse_sloppy(args.sloppy)
     big = inputs.WORKLOADS["24^3x48"]
     lats, systems = [], []
@@ -357,6 +368,25 @@ def batched_measurement(args, dev):
     infos = solve_cg_batch(systems, **kw)
     torch.cuda.synchronize()
     t_batch = time.perf_counter() - t0
+    # the 12 point sources alone, batched, against one FP64 CG solve on the same lattice (the
+    # per-solve comparison of mixed batched CG with plain FP64 CG)
+    pts = systems[:12]
+    solve_cg_batch(pts, **kw)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    solve_cg_batch(pts, **kw)
+    torch.cuda.synchronize()
+    t_pts = time.perf_counter() - t0
+    lat0, _, x0, b0 = pts[0]
+    lat0.set_params(big.kappa, big.mu)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    i64 = lat0.solve_cg(x0, b0, tol=1e-10, mode=CG_FP64)
+    torch.cuda.synchronize()
+    t64 = time.perf_counter() - t0
+    point_sources = {"workload": f"12 point sources on {big.name}", "batched_s_per_solve": round(t_pts / 12, 4),
+                     "fp64_s_per_solve": round(t64, 4), "fp64_iters": i64.iters,
+                     "speedup_vs_fp64": round(t64 / (t_pts / 12), 2)}
     # meson contraction of the 12 point-source solutions (the correlators' building block)
     props = torch.stack([systems[k][2] for k in range(12)])
     Aout = torch.empty((big.T, 12, 12, 2), dtype=torch.float64, device=dev)
@@ -406,7 +436,65 @@ def batched_measurement(args, dev):
             "iters_batched": sum(i.iters for i in infos), "iters_unbatched": iters_single,
             "timing": "host wall clock around one synchronised call (batched) / the sum of "
                       "the single solves (unbatched)",
+            "point_sources": point_sources,
             "meson_contract": contraction}
+
+
+# -------------------------------------------------- the precision-form size ---
+def precision_form_measurement(args, dev):
+    """The 32^3 x 64 workload (eps 0.6, kappa 0.1615, mu 0.003): per-launch roofline of the
+    FP32 and FP16 hopping kernels with 12-real links (L2 flushed and cleaned before each launch)
+    and one reliable-update mixed solve against one FP64 CG solve, both to 1e-10."""
+    import numpy as np
+    import torch
+
+    from paper_0905_3331_gb300 import CG_FP64, CG_RELIABLE, F16, F32, LINK12, Lattice, inputs
+    w = inputs.WORKLOADS["32^3x64"]
+    U, phi = w.gauge(), w.source()
+    lat = Lattice(w.T, w.L, w.kappa, w.mu)
+    lat.set_gauge(torch.from_numpy(U).to(dev))
+    h = w.V // 2
+    peak, _ = peaks()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev)
+    clean = torch.ones(256 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+    half = torch.from_numpy(np.ascontiguousarray(phi.reshape(-1, 4, 3)[:h])).to(dev)
+    out = {"workload": f"{w.name} lattice, eps {w.eps}, kappa {w.kappa}, mu {w.mu}"}
+    for name, prec in (("f32_12", F32), ("f16_12", F16)):
+        nb = lat.half_field_bytes(prec)
+        din = torch.empty(nb, dtype=torch.uint8, device=dev)
+        dout = torch.empty(nb, dtype=torch.uint8, device=dev)
+        lat.pack_half(prec, din, half)
+        lat.apply_hopping_eo(1, dout, din, prec, LINK12)
+        ts = []
+        for k in range(10):
+            flush.zero_()
+            clean.sum()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lat.apply_hopping_eo(k & 1, dout, din, prec, LINK12)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        t = trimmed_mean(ts)
+        by = hop_bytes_per_site(prec, LINK12) * h
+        out[name] = {"us": round(t * 1e6, 2), "gbs": round(by / t / 1e9, 1), "frac_hbm": round(by / t / 1e9 / peak, 4),
+                     "bytes_per_site": hop_bytes_per_site(prec, LINK12)}
+    b = torch.from_numpy(phi).to(dev)
+    x = torch.zeros_like(b)
+    for name, kw in (("mixed_f32_12", dict(mode=CG_RELIABLE, sloppy_prec=F32, sloppy_link=LINK12,
+                                           delta=args.batched_delta)),
+                     ("fp64", dict(mode=CG_FP64))):
+        if name == "mixed_f32_12":
+            lat.solve_cg(x, b, tol=1e-10, **kw)  # warm-up (sloppy gauge copy, tuning, graphs)
+        t, infos = _timed(lambda: lat.solve_cg(x, b, tol=1e-10, **kw), 1, dev)
+        out[name] = {"s_per_solve": round(t, 4), "iters": infos[-1].iters,
+                     "true_rel_residual": infos[-1].true_rel_residual}
+    out["speedup_mixed_vs_fp64"] = round(out["fp64"]["s_per_solve"] / out["mixed_f32_12"]["s_per_solve"], 2)
+    out["timing"] = ("hopping: 10 launches, CUDA events, mean of the middle 80%, L2 flushed and cleaned "
+                     "before each; solves: CUDA events")
+    lat.close()
+    return out
 
 
 # ------------------------------------------------------ the other solvers ---
@@ -629,6 +717,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-solve measurement")
+    ap.add_argument("--no-precision-form", action="store_true",
+                    help="skip the 32^3x64 roofline and mixed-vs-FP64 solve measurement")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the BiCGstab, chronological-guess and contraction measurements")
     ap.add_argument("--ref-seconds", type=float, default=8.0)

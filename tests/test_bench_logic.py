@@ -55,3 +55,10 @@ def test_reference_arm_json_line():
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["higher_is_better"] is True
     assert line["metric"] == bench.METRIC and line["warmup"] == 3 and line["steps"] == 2
+
+
+def test_trimmed_mean_drops_stray_launches():
+    import bench
+    ts = [14.3e-6] * 18 + [148e-6, 14.1e-6]
+    assert abs(bench.trimmed_mean(ts) - 14.3e-6) < 1e-12
+    assert bench.trimmed_mean([2.0, 4.0]) == 3.0
