@@ -662,7 +662,7 @@ struct LinkRecon<R, S, 8> {
     sincospi_(thc, &sc, &cc);
     const cpx<R> a0 = mk<R>(ma0 * ca, ma0 * sa);
     const cpx<R> c0 = mk<R>(mc0 * cc, mc0 * sc);
-    const R invN = R(1) / N;
+    const R invN = recip_(N);
     // b1 = -(b0 conj(a0) a1 + conj(a2) conj(c0)) / N ;  b2 = (conj(a1) conj(c0) - a2 b0 conj(a0)) / N
     const cpx<R> b0ca0 = cjmul(a0, b0);  // conj(a0) b0
     const cpx<R> b1 = (-invN) * (b0ca0 * a1 + cj(a2 * c0));
@@ -675,8 +675,15 @@ struct LinkRecon<R, S, 8> {
     U.m[1][2] = b2;
     third_row(U);
   }
-  __device__ static __forceinline__ void sincospi_(float v, float* s, float* c) { sincospif(v, s, c); }
+  // Single precision (the reduced-precision operators): the fast hardware sine/cosine (absolute
+  // error ~4e-7 on |x| <= pi, far below FP16 storage and within the FP32 8-real parity bound)
+  // and the correctly rounded reciprocal; FP64 keeps the accurate library functions.
+  __device__ static __forceinline__ void sincospi_(float v, float* s, float* c) {
+    __sincosf(v * 3.14159265358979323846f, s, c);
+  }
   __device__ static __forceinline__ void sincospi_(double v, double* s, double* c) { sincospi(v, s, c); }
+  __device__ static __forceinline__ float recip_(float v) { return __frcp_rn(v); }
+  __device__ static __forceinline__ double recip_(double v) { return 1.0 / v; }
   __device__ static __forceinline__ void pack(RawWords<BYTES>& r, const Mat3<double>& U) {
     typedef RawGet<S, BYTES> G;
     G::put(r, 0, (S)U.m[0][1].re);
