@@ -457,7 +457,9 @@ extern "C" tm_status tm_solve_cg_batch(const tm_system* systems, int nsys, const
         st = cuda_check(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal),
                         "begin capture");
         if (st == TM_OK) {
-          tm_status st1 = batch_iteration(sp, sl, d_sys, d_hmap, nh, d_umap, nu, d_gl, cond, 1, cs);
+          tm_status st1 = TM_OK;
+          for (int u = 0; u < cg_unroll() && st1 == TM_OK; ++u)
+            st1 = batch_iteration(sp, sl, d_sys, d_hmap, nh, d_umap, nu, d_gl, cond, 1, cs);
           cudaGraph_t captured = nullptr;
           tm_status st2 = cuda_check(cudaStreamEndCapture(cs, &captured), "end capture");
           st = st1 != TM_OK ? st1 : st2;

@@ -261,7 +261,7 @@ tm_status ensure_links(tm_lattice lat, int prec, int nreal, cudaStream_t s) {
 
 // ---------------------------------------------------------------- autotuner ---
 // Picks the hopping kernel's threads per site (1, 2 or 4) for one storage form of this lattice
-// by timing each choice (one warm-up and three timed launches, CUDA events, fastest of three)
+// by timing each choice (CUDA events, fastest of several timed groups, candidates interleaved)
 // on scratch buffers.  TM_HOP_TPS=1|2|4 in the environment fixes the choice for every form;
 // tm_set_hop_threads fixes it for one form.  Runs when the form's gauge copy is built.
 static int env_tps() {
@@ -316,25 +316,28 @@ static tm_status tune_hop(tm_lattice lat, int prec, int nreal, cudaStream_t s) {
   upd.mode = 2;
   upd.alpha_sign = 1.0;
   upd.red = Reduce{lat->partials, lat->counters, lat->dscalars, nullptr, FIN_STORE};
+  // Rounds interleave the candidates so that a clock still ramping up after the gauge copy
+  // was built (or any other drift) slows every candidate alike; round 0 is the warm-up.  A
+  // group is two iterations' mix (8 launches); each candidate's score is its fastest group
+  // (five groups, three for FP64 storage, whose launches are ~10x longer).
   const int cands[3] = {1, 2, 4};
+  const int rounds = (prec == TM_F64) ? 4 : 6;
   float score[3] = {1e30f, 1e30f, 1e30f};
-  for (int c = 0; c < 3 && st == TM_OK; ++c) {
-    lat->hop_tps[prec][li] = cands[c];
-    float tmin = 1e30f;
-    for (int k = 0; k < 4 && st == TM_OK; ++k) {  // launch group 0 is the warm-up
+  for (int k = 0; k < rounds && st == TM_OK; ++k) {
+    for (int c = 0; c < 3 && st == TM_OK; ++c) {
+      lat->hop_tps[prec][li] = cands[c];
       st = cuda_check(cudaEventRecord(e0, s), "event");
-      for (int q = 0; q < 4 && st == TM_OK; ++q) {
+      for (int q = 0; q < 8 && st == TM_OK; ++q) {
         HopArgs a = (q & 1) ? upd : plain;
-        a.out_parity = q >> 1;
+        a.out_parity = (q >> 1) & 1;
         st = hop_launch_dispatch(lat, a, s);
       }
       if (st == TM_OK) st = cuda_check(cudaEventRecord(e1, s), "event");
       if (st == TM_OK) st = cuda_check(cudaEventSynchronize(e1), "tuner");
       float ms = 0.f;
       if (st == TM_OK) st = cuda_check(cudaEventElapsedTime(&ms, e0, e1), "event");
-      if (k > 0 && ms < tmin) tmin = ms;
+      if (k > 0 && ms < score[c]) score[c] = ms;
     }
-    score[c] = tmin;
   }
   int bi = 0;
   for (int c = 1; c < 3; ++c)

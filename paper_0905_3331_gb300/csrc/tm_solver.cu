@@ -314,9 +314,24 @@ bool use_graphs() {
   return v == 1;
 }
 
-// The CUDA graph of one CG stage: a WHILE conditional node whose body is one iteration
-// (K1..K4 and the update, which sets the loop condition from the device-side state).
-// Graphs are cached per lattice and stage (vectors, precision, flavour, kappa, mu).
+// Iterations per body of a solver graph's WHILE loop (TM_CG_UNROLL, 1..8, default 4).
+// Iterations after the stage is done within a body cost only empty launches (every kernel
+// skips on `done`, the update on iter == applied).  Measured on the 16^3 x 32 mixed CG solve:
+// each relaunch of the loop body costs ~4 us; 4 iterations per body gave 143 solves/s
+// against 138 with one.
+int cg_unroll() {
+  static int v = 0;
+  if (v == 0) {
+    const char* e = getenv("TM_CG_UNROLL");
+    int u = e && *e ? atoi(e) : 4;
+    v = u < 1 ? 1 : (u > 8 ? 8 : u);
+  }
+  return v;
+}
+
+// The CUDA graph of one CG stage: a WHILE conditional node whose body is cg_unroll()
+// iterations (K1..K4 and the update, which sets the loop condition from the device-side
+// state).  Graphs are cached per lattice and stage (vectors, precision, flavour, kappa, mu).
 static tm_status stage_graph(const Solver& S, const Stage& v, cudaGraphExec_t* out) {
   tm_lattice lat = S.lat;
   for (int k = 0; k < 8; ++k) {
@@ -354,8 +369,11 @@ static tm_status stage_graph(const Solver& S, const Stage& v, cudaGraphExec_t* o
     if (st == TM_OK) {
       Solver C = S;
       C.s = cs;
-      tm_status st1 = normal_apply(C, v.prec, v.nreal, v.p, v.T, v.W, v.r, lat->cgstate);
-      if (st1 == TM_OK) st1 = launch_update(C, v.px, v.prec, v.x, v.p, v.r, lat->cgstate, cond, 1);
+      tm_status st1 = TM_OK;
+      for (int u = 0; u < cg_unroll() && st1 == TM_OK; ++u) {
+        st1 = normal_apply(C, v.prec, v.nreal, v.p, v.T, v.W, v.r, lat->cgstate);
+        if (st1 == TM_OK) st1 = launch_update(C, v.px, v.prec, v.x, v.p, v.r, lat->cgstate, cond, 1);
+      }
       cudaGraph_t captured = nullptr;
       tm_status st2 = cuda_check(cudaStreamEndCapture(cs, &captured), "end capture");
       st = st1 != TM_OK ? st1 : st2;
@@ -426,7 +444,8 @@ tm_status aux_loop_graph(tm_lattice lat, const unsigned long long key[16], cudaS
     st = cuda_check(cudaStreamBeginCaptureToGraph(cs, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal),
                     "begin capture");
     if (st == TM_OK) {
-      tm_status st1 = body(cs, cond);
+      tm_status st1 = TM_OK;
+      for (int u = 0; u < cg_unroll() && st1 == TM_OK; ++u) st1 = body(cs, cond);
       cudaGraph_t captured = nullptr;
       tm_status st2 = cuda_check(cudaStreamEndCapture(cs, &captured), "end capture");
       st = st1 != TM_OK ? st1 : st2;

@@ -45,6 +45,7 @@ tm_status cg_normal(const Solver& S, const tm_cg_params& P, const void* bp, doub
                     void* Pv, void* T, void* W, NormalResult* res);
 
 bool use_graphs();  // CUDA-graph stage loops (TM_NO_GRAPH=1 selects host-driven chunks)
+int cg_unroll();    // iterations per body of a graph loop (TM_CG_UNROLL)
 
 // A cached CUDA graph whose only node is a WHILE conditional; its body is whatever `body`
 // enqueues on the capture stream (the body's last kernel sets the condition).  Graphs are
