@@ -30,9 +30,14 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Dslash GB/s & % HBM roofline; CG solves/sec to 1e-10 FP64 residual, mixed vs FP64"
 HOP_FLOPS = 1320  # per output site per hopping application (8 hops x 168 flops - 24)
-# dram__bytes_read.sum + dram__bytes_write.sum of one hop_kernel<FP32, 12-real> launch on the
-# 16^3 x 32 lattice, ncu --set full capture (profiles/hop_f32_12_16x32_and_32x64_full.md)
-NCU_TRAFFIC = {("f32:12", "16^3x32"): 31492864.0}
+# dram__bytes_read.sum + dram__bytes_write.sum of one hopping-kernel launch, from ncu captures
+# (profiles/), keyed by sloppy form, lattice and kernel choice (threads per site; 3 = the
+# software-pipelined one-thread kernel), each from an ncu --set full capture on 16^3 x 32:
+# plain (profiles/hop_f32_12_16x32_and_32x64_full.md), pipelined
+# (profiles/hop_f32_12_16x32_pipelined_full.md)
+NCU_TRAFFIC = {("f32:12", "16^3x32", 1): 31492864.0, ("f32:12", "16^3x32", 3): 31487744.0}
+HOP_VARIANT = {1: "1 thread per site", 2: "2 threads per site", 4: "4 threads per site",
+               3: "1 thread per site, pipelined loads"}
 
 
 def hop_bytes_per_site(prec: int, nreal: int) -> int:
@@ -277,10 +282,11 @@ def run_gpu(args):
     skey = args.sloppy.replace(":", "_")
     # DRAM bytes of one launch of the sloppy kernel from an ncu capture (profiles/), valid
     # while that kernel is unchanged; other forms or lattices report null
-    if args.traffic is None and (args.sloppy, w.name) in NCU_TRAFFIC:
-        args.traffic = NCU_TRAFFIC[(args.sloppy, w.name)]
     top = dslash[skey]
-    roofline = {"bound": "hbm", "kernel": f"hop_kernel ({args.sloppy} sloppy form)",
+    if args.traffic is None and (args.sloppy, w.name, top["threads_per_site"]) in NCU_TRAFFIC:
+        args.traffic = NCU_TRAFFIC[(args.sloppy, w.name, top["threads_per_site"])]
+    variant = HOP_VARIANT.get(top["threads_per_site"], str(top["threads_per_site"]))
+    roofline = {"bound": "hbm", "kernel": f"hop_kernel ({args.sloppy} sloppy form, {variant})",
                 "achieved": round(top["gbs_cold"], 1), "peak": peak, "unit": "GB/s",
                 "frac": round(top["gbs_cold"] / peak, 4),
                 "traffic": args.traffic, "peak_kind": peak_kind,

@@ -94,17 +94,15 @@ __device__ __forceinline__ void su3_adj_mul2(const Mat3<R>& U, const cpx<R> h0[3
 // One hop.  Forward (S = +1): link U_mu(x) from the output parity's slab at the output site.
 // Backward (S = -1): link U_mu(x - mu^) from the other parity's slab at the neighbour's index,
 // applied as its adjoint -- the same stored link serves both hops, so the operator keeps
-// gamma5-hermiticity exactly in every storage format.
+// gamma5-hermiticity exactly in every storage format.  hop_apply does the arithmetic on the
+// loaded link words and neighbour spinor (FP16: unscaled, with its per-site norm).
 template <int PREC, int NREAL, int MU, int S>
-__device__ __forceinline__ void hop_dir(cpx<typename SpinorFmt<PREC>::real> acc[12], const void* in, int h,
-                                        int nbi, const char* slab, int link_index, bool negate) {
+__device__ __forceinline__ void hop_apply(cpx<typename SpinorFmt<PREC>::real> acc[12],
+                                          const RawWords<NREAL * LinkStore<PREC>::size>& raw,
+                                          const cpx<typename SpinorFmt<PREC>::real> p[12],
+                                          typename SpinorFmt<PREC>::real scale, bool negate) {
   typedef typename SpinorFmt<PREC>::real R;
   typedef typename LinkStore<PREC>::type St;
-  constexpr int BYTES = NREAL * LinkStore<PREC>::size;
-  RawWords<BYTES> raw = load_raw<BYTES>(slab, h, link_index);
-  cpx<R> p[12];
-  R scale;
-  SpinorFmt<PREC>::load_unscaled(in, h, nbi, p, scale);
   cpx<R> h0[3], h1[3];
   project<R, MU, S>(p, h0, h1);
   if (SpinorFmt<PREC>::has_norm) {
@@ -130,6 +128,69 @@ __device__ __forceinline__ void hop_dir(cpx<typename SpinorFmt<PREC>::real> acc[
   else
     su3_adj_mul2(U, h0, h1, u0, u1);
   accumulate<R, MU, S>(acc, u0, u1);
+}
+
+template <int PREC, int NREAL, int MU, int S>
+__device__ __forceinline__ void hop_dir(cpx<typename SpinorFmt<PREC>::real> acc[12], const void* in, int h,
+                                        int nbi, const char* slab, int link_index, bool negate) {
+  typedef typename SpinorFmt<PREC>::real R;
+  constexpr int BYTES = NREAL * LinkStore<PREC>::size;
+  RawWords<BYTES> raw = load_raw<BYTES>(slab, h, link_index);
+  cpx<R> p[12];
+  R scale;
+  SpinorFmt<PREC>::load_unscaled(in, h, nbi, p, scale);
+  hop_apply<PREC, NREAL, MU, S>(acc, raw, p, scale, negate);
+}
+
+// Software-pipelined form (FP32 / FP16 storage, one thread per site): the link and spinor
+// words of the next hop are loaded before the current hop's arithmetic, so each thread keeps
+// two hops' loads in flight instead of waiting out eight load latencies one after another.
+// For lattices that fill less than a wave the launch time is this per-thread chain.
+template <int PREC, int NREAL>
+struct HopWords {
+  RawWords<NREAL * LinkStore<PREC>::size> link;
+  unsigned int sp[SpinorFmt<PREC>::bytes_per_site / 4];
+};
+
+template <int PREC, int NREAL>
+__device__ __forceinline__ void hop_fetch(HopWords<PREC, NREAL>& d, const char* in, int h, int nbi,
+                                          const char* slab, int link_index) {
+  d.link = load_raw<NREAL * LinkStore<PREC>::size>(slab, h, link_index);
+  SpinorFmt<PREC>::load_words(in, h, nbi, d.sp);
+}
+
+template <int PREC, int NREAL, int MU, int S>
+__device__ __forceinline__ void hop_finish(cpx<typename SpinorFmt<PREC>::real> acc[12],
+                                           const HopWords<PREC, NREAL>& d, bool negate) {
+  typedef typename SpinorFmt<PREC>::real R;
+  cpx<R> p[12];
+  R scale;
+  SpinorFmt<PREC>::unpack_words(d.sp, p, scale);
+  hop_apply<PREC, NREAL, MU, S>(acc, d.link, p, scale, negate);
+}
+
+template <int PREC, int NREAL>
+__device__ __forceinline__ void hop_all_pipelined(cpx<typename SpinorFmt<PREC>::real> acc[12], const Geom& g,
+                                                  int cb, const SiteCoord& c, const int nb[8], const char* inr,
+                                                  const char* lf, const char* lo, size_t slab) {
+  const bool tfwd = (c.t == g.T - 1), tbwd = (c.t == 0);
+  HopWords<PREC, NREAL> A, B;
+  hop_fetch(A, inr, g.h, nb[0], lf + 0 * slab, cb);
+  hop_fetch(B, inr, g.h, nb[4], lo + 0 * slab, nb[4]);
+  hop_finish<PREC, NREAL, 0, +1>(acc, A, tfwd);
+  hop_fetch(A, inr, g.h, nb[1], lf + 1 * slab, cb);
+  hop_finish<PREC, NREAL, 0, -1>(acc, B, tbwd);
+  hop_fetch(B, inr, g.h, nb[5], lo + 1 * slab, nb[5]);
+  hop_finish<PREC, NREAL, 1, +1>(acc, A, false);
+  hop_fetch(A, inr, g.h, nb[2], lf + 2 * slab, cb);
+  hop_finish<PREC, NREAL, 1, -1>(acc, B, false);
+  hop_fetch(B, inr, g.h, nb[6], lo + 2 * slab, nb[6]);
+  hop_finish<PREC, NREAL, 2, +1>(acc, A, false);
+  hop_fetch(A, inr, g.h, nb[3], lf + 3 * slab, cb);
+  hop_finish<PREC, NREAL, 2, -1>(acc, B, false);
+  hop_fetch(B, inr, g.h, nb[7], lo + 3 * slab, nb[7]);
+  hop_finish<PREC, NREAL, 3, +1>(acc, A, false);
+  hop_finish<PREC, NREAL, 3, -1>(acc, B, false);
 }
 
 // MODE 0: out = epi(hop).  MODE 1: same plus sum ||out||^2.
@@ -169,10 +230,17 @@ __device__ __forceinline__ void hop_part(cpx<typename SpinorFmt<PREC>::real> acc
 // per SM (80 per thread instead of 86-92).  The kernel is memory-latency bound and the extra
 // warps win over a few spilled bytes (FP32/12: 32^3 x 64 118 -> 113 us, 16^3 x 32 18.9 -> 17.6 us
 // per launch).  FP64 and double-float keep their full budget (~180 registers, ALU bound).
-constexpr int hop_min_blocks(int prec, int tps) { return (tps == 1 && (prec == TM_F32 || prec == TM_F16)) ? 12 : 1; }
+// The software-pipelined form holds two hops' words (72 more registers for FP32/12): a budget
+// for HOP_PIPE_BLOCKS blocks per SM.
+#ifndef HOP_PIPE_BLOCKS
+#define HOP_PIPE_BLOCKS 7
+#endif
+constexpr int hop_min_blocks(int prec, int tps, bool pipe) {
+  return pipe ? HOP_PIPE_BLOCKS : ((tps == 1 && (prec == TM_F32 || prec == TM_F16)) ? 12 : 1);
+}
 
-template <int PREC, int NREAL, bool HAS_Y, int MODE, int TPS>
-__global__ void __launch_bounds__(hop_spb(TPS) * TPS, hop_min_blocks(PREC, TPS)) hop_kernel(const Geom g, const int out_parity,
+template <int PREC, int NREAL, bool HAS_Y, int MODE, int TPS, bool PIPE>
+__global__ void __launch_bounds__(hop_spb(TPS) * TPS, hop_min_blocks(PREC, TPS, PIPE)) hop_kernel(const Geom g, const int out_parity,
                                                      const char* __restrict__ links, const void* in,
                                                      size_t in_stride, void* out, size_t out_stride,
                                                      const void* y, size_t y_stride, const EpiCoef coef,
@@ -207,7 +275,10 @@ __global__ void __launch_bounds__(hop_spb(TPS) * TPS, hop_min_blocks(PREC, TPS))
     const size_t slab = link_bytes(PREC, NREAL) * (size_t)g.h;
     const char* lf = links + (size_t)(out_parity * 4) * slab;        // U_mu(x), x of this parity
     const char* lo = links + (size_t)((1 - out_parity) * 4) * slab;  // U_mu(y), y of the other parity
-    hop_part<PREC, NREAL, TPS>(acc, g, cb, c, nb, inr, lf, lo, slab, part);
+    if constexpr (PIPE)
+      hop_all_pipelined<PREC, NREAL>(acc, g, cb, c, nb, inr, lf, lo, slab);
+    else
+      hop_part<PREC, NREAL, TPS>(acc, g, cb, c, nb, inr, lf, lo, slab, part);
   }
   // this thread's share of the site's storage blocks
   const int kb = (TPS == 1) ? 0 : F::CPB * ((F::NBLK * part) / TPS);
@@ -296,7 +367,7 @@ __global__ void __launch_bounds__(hop_spb(TPS) * TPS, hop_min_blocks(PREC, TPS))
   }
 }
 
-template <int PREC, int NREAL, int TPS>
+template <int PREC, int NREAL, int TPS, bool PIPE>
 tm_status hop_launch_tps(tm_lattice lat, const HopArgs& a, cudaStream_t s) {
   const Geom& g = lat->geom;
   constexpr int SPB = hop_spb(TPS), NT = SPB * TPS;
@@ -307,15 +378,15 @@ tm_status hop_launch_tps(tm_lattice lat, const HopArgs& a, cudaStream_t s) {
   g, a.out_parity, links, a.in, a.in_stride, a.out, a.out_stride, a.y, a.y_stride, a.coef, a.alpha_src, \
       a.alpha_sign, a.red, a.skip
   if (!has_y && a.mode == 0)
-    launch_pdl(hop_kernel<PREC, NREAL, false, 0, TPS>, grid, dim3(NT), s, TM_HOP_ARGS);
+    launch_pdl(hop_kernel<PREC, NREAL, false, 0, TPS, PIPE>, grid, dim3(NT), s, TM_HOP_ARGS);
   else if (!has_y && a.mode == 1)
-    launch_pdl(hop_kernel<PREC, NREAL, false, 1, TPS>, grid, dim3(NT), s, TM_HOP_ARGS);
+    launch_pdl(hop_kernel<PREC, NREAL, false, 1, TPS, PIPE>, grid, dim3(NT), s, TM_HOP_ARGS);
   else if (has_y && a.mode == 0)
-    launch_pdl(hop_kernel<PREC, NREAL, true, 0, TPS>, grid, dim3(NT), s, TM_HOP_ARGS);
+    launch_pdl(hop_kernel<PREC, NREAL, true, 0, TPS, PIPE>, grid, dim3(NT), s, TM_HOP_ARGS);
   else if (has_y && a.mode == 1)
-    launch_pdl(hop_kernel<PREC, NREAL, true, 1, TPS>, grid, dim3(NT), s, TM_HOP_ARGS);
+    launch_pdl(hop_kernel<PREC, NREAL, true, 1, TPS, PIPE>, grid, dim3(NT), s, TM_HOP_ARGS);
   else if (has_y && a.mode == 2)
-    launch_pdl(hop_kernel<PREC, NREAL, true, 2, TPS>, grid, dim3(NT), s, TM_HOP_ARGS);
+    launch_pdl(hop_kernel<PREC, NREAL, true, 2, TPS, PIPE>, grid, dim3(NT), s, TM_HOP_ARGS);
   else
     return set_error(TM_ERR_ARG, "hopping: unsupported epilogue combination");
 #undef TM_HOP_ARGS
@@ -327,11 +398,14 @@ template <int PREC, int NREAL>
 tm_status hop_launch_t(tm_lattice lat, const HopArgs& a, cudaStream_t s) {
   switch (lat->hop_tps[PREC][link_index(NREAL)]) {
     case 2:
-      return hop_launch_tps<PREC, NREAL, 2>(lat, a, s);
+      return hop_launch_tps<PREC, NREAL, 2, false>(lat, a, s);
     case 4:
-      return hop_launch_tps<PREC, NREAL, 4>(lat, a, s);
+      return hop_launch_tps<PREC, NREAL, 4, false>(lat, a, s);
+    case TM_HOP_PIPELINED:
+      if constexpr (PREC == TM_F32 || PREC == TM_F16) return hop_launch_tps<PREC, NREAL, 1, true>(lat, a, s);
+      return hop_launch_tps<PREC, NREAL, 1, false>(lat, a, s);
     default:
-      return hop_launch_tps<PREC, NREAL, 1>(lat, a, s);
+      return hop_launch_tps<PREC, NREAL, 1, false>(lat, a, s);
   }
 }
 

@@ -7,6 +7,6 @@
 namespace tmq {
 tm_status hop_launch_df64(tm_lattice lat, const HopArgs& a, cudaStream_t s) {
   if (a.nreal != 18) return set_error(TM_ERR_UNSUPPORTED, "double-float storage supports 18-real links only");
-  return hop_launch_tps<TM_DF64, 18, 1>(lat, a, s);
+  return hop_launch_tps<TM_DF64, 18, 1, false>(lat, a, s);
 }
 }  // namespace tmq

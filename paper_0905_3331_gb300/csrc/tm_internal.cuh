@@ -255,6 +255,24 @@ struct SpinorFmt<TM_F32> {
                                          (float)s[2 * k + 1].re, (float)s[2 * k + 1].im);
   }
   static constexpr int NBLK = 6, CPB = 2;
+  // The site's 24 words as loaded (software-pipelined hopping kernel), and their unpacking.
+  __device__ static __forceinline__ void load_words(const void* base, int h, int i, unsigned int w[24]) {
+    const uint4* p = static_cast<const uint4*>(base);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const uint4 v = __ldg(p + (size_t)k * h + i);
+      w[4 * k] = v.x;
+      w[4 * k + 1] = v.y;
+      w[4 * k + 2] = v.z;
+      w[4 * k + 3] = v.w;
+    }
+  }
+  template <typename R>
+  __device__ static __forceinline__ void unpack_words(const unsigned int w[24], cpx<R> s[12], R& scale) {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) s[k] = mk<R>((R)__uint_as_float(w[2 * k]), (R)__uint_as_float(w[2 * k + 1]));
+    scale = R(1);
+  }
   template <typename R>
   __device__ static __forceinline__ void load_range(const void* base, int h, int i, cpx<R> s[12], int kb, int ke) {
     const float4* p = static_cast<const float4*>(base);
@@ -298,6 +316,28 @@ struct SpinorFmt<TM_F16> {
       s[4 * k + 2] = mk<R>((R)c.x, (R)c.y);
       s[4 * k + 3] = mk<R>((R)d.x, (R)d.y);
     }
+  }
+  // The site's 12 words of halves and its norm as loaded (software-pipelined hopping kernel).
+  __device__ static __forceinline__ void load_words(const void* base, int h, int i, unsigned int w[13]) {
+    const uint4* p = static_cast<const uint4*>(base);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const uint4 v = __ldg(p + (size_t)k * h + i);
+      w[4 * k] = v.x;
+      w[4 * k + 1] = v.y;
+      w[4 * k + 2] = v.z;
+      w[4 * k + 3] = v.w;
+    }
+    w[12] = __ldg(reinterpret_cast<const unsigned int*>(p + (size_t)3 * h) + i);
+  }
+  template <typename R>
+  __device__ static __forceinline__ void unpack_words(const unsigned int w[13], cpx<R> s[12], R& scale) {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      const float2 a = h2f(w[k]);
+      s[k] = mk<R>((R)a.x, (R)a.y);
+    }
+    scale = (R)__uint_as_float(w[12]);
   }
   __device__ static __forceinline__ float2 h2f(unsigned int w) {
     __half2 hv = *reinterpret_cast<__half2*>(&w);
@@ -893,7 +933,7 @@ struct tm_lattice_s {
   bool has_gauge;
   double* U_canon;          // 72 V doubles, canonical copy on the device
   void* links[4][3];        // gauge copies [prec][0:18, 1:12, 2:8], built on demand
-  int hop_tps[4][3];        // threads per site of the hopping kernel per form (autotuned; 1, 2, 4)
+  int hop_tps[4][3];        // hopping kernel per form (autotuned): threads per site 1, 2, 4, or TM_HOP_PIPELINED
   int hop_tps_forced[4][3]; // set by tm_set_hop_threads: the tuner keeps hands off
   // work space
   void* ws[32];             // half-field buffers, allocated on demand

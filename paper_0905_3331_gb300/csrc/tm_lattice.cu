@@ -260,22 +260,25 @@ tm_status ensure_links(tm_lattice lat, int prec, int nreal, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------- autotuner ---
-// Picks the hopping kernel's threads per site (1, 2 or 4) for one storage form of this lattice
-// by timing each choice (CUDA events, fastest of several timed groups, candidates interleaved)
-// on scratch buffers.  TM_HOP_TPS=1|2|4 in the environment fixes the choice for every form;
-// tm_set_hop_threads fixes it for one form.  Runs when the form's gauge copy is built.
+// Picks the hopping kernel for one storage form of this lattice -- 1, 2 or 4 threads per site,
+// or one thread per site with software-pipelined loads (TM_HOP_PIPELINED) -- by timing each
+// choice (CUDA events, fastest of several timed groups, candidates interleaved) on scratch
+// buffers.  TM_HOP_TPS=1|2|3|4 in the environment fixes the choice for every form (3: the
+// pipelined kernel, FP64 falls back to 1); tm_set_hop_threads fixes it for one form.  Runs
+// when the form's gauge copy is built.
 static int env_tps() {
   const char* e = getenv("TM_HOP_TPS");
   if (!e) return 0;
   const int v = atoi(e);
-  return (v == 1 || v == 2 || v == 4) ? v : 0;
+  return (v == 1 || v == 2 || v == 4 || v == TM_HOP_PIPELINED) ? v : 0;
 }
 
-// Times the 1/2/4 threads-per-site kernels of one storage form on this lattice and keeps the
-// best.  The score is one CG iteration's mix: two plain launches (K1, K3) and two launches with
-// a site-local input, the residual update and the fused reduction (K2, K4).  More threads per
-// site must win by 10%: measured at 16^3 x 32, FP32 kernels with 2 threads per site ran at
-// their stand-alone speed in a host loop but 2.3x slower inside the CG stage graphs.
+// Times the kernel choices of one storage form on this lattice and keeps the best.  The score
+// is one CG iteration's mix: two plain launches (K1, K3) and two launches with a site-local
+// input, the residual update and the fused reduction (K2, K4).  More threads per site must
+// win by 10%: measured at 16^3 x 32, FP32 kernels with 2 threads per site ran at their
+// stand-alone speed in a host loop but 2.3x slower inside the CG stage graphs.  (They need
+// 116-144 registers a thread, so only 3-4 of their 128-thread blocks fit on an SM.)
 static tm_status tune_hop(tm_lattice lat, int prec, int nreal, cudaStream_t s) {
   const int li = link_index(nreal);
   if (lat->hop_tps_forced[prec][li]) return TM_OK;
@@ -284,7 +287,7 @@ static tm_status tune_hop(tm_lattice lat, int prec, int nreal, cudaStream_t s) {
     return TM_OK;
   }
   if (const int e = env_tps()) {
-    lat->hop_tps[prec][li] = e;
+    lat->hop_tps[prec][li] = (e == TM_HOP_PIPELINED && prec == TM_F64) ? 1 : e;
     return TM_OK;
   }
   const size_t hb = spinor_bytes_per_site(prec) * lat->h;
@@ -319,12 +322,15 @@ static tm_status tune_hop(tm_lattice lat, int prec, int nreal, cudaStream_t s) {
   // Rounds interleave the candidates so that a clock still ramping up after the gauge copy
   // was built (or any other drift) slows every candidate alike; round 0 is the warm-up.  A
   // group is two iterations' mix (8 launches); each candidate's score is its fastest group
-  // (five groups, three for FP64 storage, whose launches are ~10x longer).
-  const int cands[3] = {1, 2, 4};
+  // (five groups, three for FP64 storage, whose launches are ~10x longer).  Candidates: one
+  // thread per site, its software-pipelined form (FP32 / FP16 storage), 2 and 4 threads per site.
+  const int cands[4] = {1, TM_HOP_PIPELINED, 2, 4};
+  const bool has_pipe = (prec == TM_F32 || prec == TM_F16);
   const int rounds = (prec == TM_F64) ? 4 : 6;
-  float score[3] = {1e30f, 1e30f, 1e30f};
+  float score[4] = {1e30f, 1e30f, 1e30f, 1e30f};
   for (int k = 0; k < rounds && st == TM_OK; ++k) {
-    for (int c = 0; c < 3 && st == TM_OK; ++c) {
+    for (int c = 0; c < 4 && st == TM_OK; ++c) {
+      if (c == 1 && !has_pipe) continue;
       lat->hop_tps[prec][li] = cands[c];
       st = cuda_check(cudaEventRecord(e0, s), "event");
       for (int q = 0; q < 8 && st == TM_OK; ++q) {
@@ -339,9 +345,12 @@ static tm_status tune_hop(tm_lattice lat, int prec, int nreal, cudaStream_t s) {
       if (k > 0 && ms < score[c]) score[c] = ms;
     }
   }
-  int bi = 0;
-  for (int c = 1; c < 3; ++c)
-    if (score[c] < 0.9f * score[0] && score[c] < score[bi]) bi = c;
+  // The pipelined form must be 2% faster than the plain one, more threads per site 10% faster
+  // than the better of the two.
+  int bi = (has_pipe && score[1] < 0.98f * score[0]) ? 1 : 0;
+  const float base = score[bi];
+  for (int c = 2; c < 4; ++c)
+    if (score[c] < 0.9f * base && score[c] < score[bi]) bi = c;
   lat->hop_tps[prec][li] = cands[bi];
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
@@ -485,8 +494,11 @@ size_t tm_volume(tm_lattice lat) { return lat ? lat->V : 0; }
 tm_status tm_set_hop_threads(tm_lattice lat, tm_prec prec, tm_link link, int threads_per_site) {
   if (!lat || prec < TM_F64 || prec > TM_DF64 || (link != 18 && link != 12 && link != 8))
     return set_error(TM_ERR_ARG, "tm_set_hop_threads: bad argument");
-  if (threads_per_site != 0 && threads_per_site != 1 && threads_per_site != 2 && threads_per_site != 4)
-    return set_error(TM_ERR_ARG, "tm_set_hop_threads: threads_per_site must be 0 (tune), 1, 2 or 4");
+  if (threads_per_site != 0 && threads_per_site != 1 && threads_per_site != 2 && threads_per_site != 4 &&
+      threads_per_site != TM_HOP_PIPELINED)
+    return set_error(TM_ERR_ARG, "tm_set_hop_threads: threads_per_site must be 0 (tune), 1, 2, 4 or 3 (pipelined)");
+  if (threads_per_site == TM_HOP_PIPELINED && prec != TM_F32 && prec != TM_F16)
+    return set_error(TM_ERR_UNSUPPORTED, "tm_set_hop_threads: the pipelined kernel exists for FP32 and FP16 storage");
   const int li = link_index(link);
   invalidate_graphs(lat);  // captured graphs hold the previous kernel choice
   if (threads_per_site == 0) {

@@ -23,6 +23,7 @@ from . import build as _build
 F64, F32, F16, DF64 = 0, 1, 2, 3
 LINK18, LINK12, LINK8 = 18, 12, 8
 CG_FP64, CG_SQRT_EPS, CG_RELIABLE = 0, 1, 2
+HOP_PIPELINED = 3  # hopping-kernel choice: one thread per site, software-pipelined loads
 
 STATUS = {0: "TM_OK", 1: "TM_ERR_ARG", 2: "TM_ERR_ODD_EXTENT", 3: "TM_ERR_NO_GAUGE",
           4: "TM_ERR_NOT_SU3", 5: "TM_ERR_NONFINITE", 6: "TM_ERR_CUDA",
