@@ -81,6 +81,10 @@ class ClockSampler:
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
                  "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=self.file, stderr=subprocess.DEVNULL)
+            # nvidia-smi takes a moment to start: begin the timed region once it samples
+            t0 = time.time()
+            while time.time() - t0 < 3.0 and os.path.getsize(self.file.name) == 0:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
         return self
@@ -709,7 +713,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="16^3x32")

@@ -86,7 +86,8 @@ __global__ void __launch_bounds__(HOP_NT, 6) hop_batch_kernel(const BatchSys* __
 #pragma unroll
     for (int q = 0; q < 12; ++q) o[q] = ((q < 6) ? Du : Dl) * (cc * acc[q]);
   }
-  double nrm = 0.0;
+  typedef typename SiteSum<R>::type SR;
+  SR nrm = SR(0);
   void* outp = B.vec[out_sel];
   if (MODE == 2) {
     if (active) {
@@ -97,20 +98,20 @@ __global__ void __launch_bounds__(HOP_NT, 6) hop_batch_kernel(const BatchSys* __
 #pragma unroll
       for (int q = 0; q < 12; ++q) {
         r[q] = r[q] - al * o[q];
-        nrm += (double)norm2(r[q]);
+        nrm += (SR)norm2(r[q]);
       }
       SpinorFmt<PR>::store(outp, g.h, cb, r);
     }
   } else if (active) {
     if (MODE == 1) {
 #pragma unroll
-      for (int q = 0; q < 12; ++q) nrm += (double)norm2(o[q]);
+      for (int q = 0; q < 12; ++q) nrm += (SR)norm2(o[q]);
     }
     F::store(outp, g.h, cb, o);
   }
   if (MODE >= 1) {
     const Reduce red{B.partials, B.counters, nullptr, st, MODE == 1 ? FIN_CG_ALPHA : FIN_CG_RR};
-    const double bs = block_sum<HOP_NT>(nrm, sh);
+    const double bs = block_sum<HOP_NT>((double)nrm, sh);
     grid_reduce<HOP_NT>(red, 0, B.nblocks, m.y, bs, sh);
   }
 }
@@ -150,9 +151,7 @@ __global__ void __launch_bounds__(BNT) cg_update_batch_kernel(const BatchSys* __
   __syncthreads();
   if (threadIdx.x == 0) {
     if (work) {
-      __threadfence();
-      const unsigned prev = atomicAdd(B.counters + 1, 1u);
-      if (prev == (unsigned)B.nblocks_upd - 1) {
+      if (arrive_acq_rel(B.counters + 1) == (unsigned)B.nblocks_upd - 1) {
         S.applied = iter;
         B.counters[1] = 0u;
         if (S.done && !S.retired) {
@@ -164,9 +163,7 @@ __global__ void __launch_bounds__(BNT) cg_update_batch_kernel(const BatchSys* __
       S.retired = 1;
       atomicSub(&gl->active, 1);
     }
-    __threadfence();
-    const unsigned g = atomicAdd(&gl->counter, 1u);
-    if (g == gridDim.x - 1) {
+    if (arrive_acq_rel(&gl->counter) == gridDim.x - 1) {  // after this block's changes to `active`
       gl->counter = 0u;
       gl->loops += 1;
       const bool again = atomicAdd(&gl->active, 0) > 0 && gl->loops < gl->loop_cap;

@@ -80,13 +80,10 @@ __device__ __forceinline__ bool grid_sum(double (&v)[N], double* partials, unsig
       for (int w = 0; w < BNT / 32; ++w) s += sh[k][w];
       partials[(size_t)k * nb + blockIdx.x] = s;
     }
-    __threadfence();
-    const unsigned prev = atomicAdd(counter, 1u);
-    last = (prev == (unsigned)nb - 1);
+    last = (arrive_acq_rel(counter) == (unsigned)nb - 1);  // see grid_reduce
   }
   __syncthreads();
   if (!last) return false;
-  __threadfence();
 #pragma unroll
   for (int k = 0; k < N; ++k) {
     double x = 0.0;  // partials b = t, t + BNT, ... in order, loads of a group of 8 issued together
@@ -127,17 +124,22 @@ __global__ void __launch_bounds__(BNT) bi_alpha_kernel(int h, const char* rh, co
   if (st->done) return;
   typedef typename SpinorFmt<PR>::real RR;
   typedef typename SpinorFmt<PP>::real RP;
+  typedef typename SiteSum<RR>::type SR;
   double acc[2] = {0.0, 0.0};
   for (int i = blockIdx.x * BNT + threadIdx.x; i < h; i += gridDim.x * BNT) {
     cpx<RR> a[12];
     cpx<RP> b[12];
     SpinorFmt<PR>::load(rh, h, i, a);
     SpinorFmt<PP>::load(v, h, i, b);
+    SR l0 = SR(0), l1 = SR(0);
 #pragma unroll
     for (int k = 0; k < 12; ++k) {  // conj(a) b
-      acc[0] += (double)a[k].re * (double)b[k].re + (double)a[k].im * (double)b[k].im;
-      acc[1] += (double)a[k].re * (double)b[k].im - (double)a[k].im * (double)b[k].re;
+      const SR ar = (SR)a[k].re, ai = (SR)a[k].im, br = (SR)b[k].re, bi = (SR)b[k].im;
+      l0 += ar * br + ai * bi;
+      l1 += ar * bi - ai * br;
     }
+    acc[0] += (double)l0;
+    acc[1] += (double)l1;
   }
   double tot[2];
   if (!grid_sum<2>(acc, partials, counter, tot)) return;
@@ -179,18 +181,22 @@ __global__ void __launch_bounds__(BNT) bi_omega_kernel(int h, const char* s, con
                                                        double* partials, unsigned* counter) {
   if (st->done) return;
   typedef typename SpinorFmt<PP>::real RP;
+  typedef typename SiteSum<RP>::type SR;
   double acc[3] = {0.0, 0.0, 0.0};
   for (int i = blockIdx.x * BNT + threadIdx.x; i < h; i += gridDim.x * BNT) {
     cpx<RP> a[12], b[12];
     SpinorFmt<PP>::load(t, h, i, a);
     SpinorFmt<PP>::load(s, h, i, b);
+    SR l[3] = {SR(0), SR(0), SR(0)};
 #pragma unroll
     for (int k = 0; k < 12; ++k) {  // conj(t) s, |t|^2
-      const double tr = a[k].re, ti = a[k].im, sr = b[k].re, si = b[k].im;
-      acc[0] += tr * sr + ti * si;
-      acc[1] += tr * si - ti * sr;
-      acc[2] += tr * tr + ti * ti;
+      const SR tr = a[k].re, ti = a[k].im, sr = b[k].re, si = b[k].im;
+      l[0] += tr * sr + ti * si;
+      l[1] += tr * si - ti * sr;
+      l[2] += tr * tr + ti * ti;
     }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) acc[j] += (double)l[j];
   }
   double tot[3];
   if (!grid_sum<3>(acc, partials, counter, tot)) return;
@@ -216,8 +222,10 @@ __global__ void __launch_bounds__(BNT) bi_xr_kernel(int h, char* x, char* r, con
   typedef typename SpinorFmt<PP>::real RP;
   const cpx<RR> al = mk<RR>((RR)st->alpha_re, (RR)st->alpha_im);
   const cpx<RR> om = mk<RR>((RR)st->omega_re, (RR)st->omega_im);
+  typedef typename SiteSum<RR>::type SR;
   double acc[3] = {0.0, 0.0, 0.0};
   for (int i = blockIdx.x * BNT + threadIdx.x; i < h; i += gridDim.x * BNT) {
+    SR l[3] = {SR(0), SR(0), SR(0)};
     cpx<RR> xv[12], rv[12], hv[12];
     cpx<RP> pv[12], sv[12], tv[12];
     SpinorFmt<PR>::load(x, h, i, xv);
@@ -232,11 +240,13 @@ __global__ void __launch_bounds__(BNT) bi_xr_kernel(int h, char* x, char* r, con
       const cpx<RR> tk = mk<RR>((RR)tv[k].re, (RR)tv[k].im);
       xv[k] = xv[k] + al * pk + om * sk;
       rv[k] = sk - om * tk;
-      const double rr_ = rv[k].re, ri = rv[k].im, hr = hv[k].re, hi = hv[k].im;
-      acc[0] += hr * rr_ + hi * ri;
-      acc[1] += hr * ri - hi * rr_;
-      acc[2] += rr_ * rr_ + ri * ri;
+      const SR rr_ = rv[k].re, ri = rv[k].im, hr = hv[k].re, hi = hv[k].im;
+      l[0] += hr * rr_ + hi * ri;
+      l[1] += hr * ri - hi * rr_;
+      l[2] += rr_ * rr_ + ri * ri;
     }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) acc[j] += (double)l[j];
     SpinorFmt<PR>::store(x, h, i, xv);
     SpinorFmt<PR>::store(r, h, i, rv);
   }
@@ -317,9 +327,7 @@ __global__ void __launch_bounds__(BNT) bi_p_kernel(int h, char* p, const char* r
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned prev = atomicAdd(counter, 1u);
-    if (prev == gridDim.x - 1) {
+    if (arrive_acq_rel(counter) == gridDim.x - 1) {
       S.applied = iter;
       *counter = 0u;
       if (use_cond) {
@@ -336,18 +344,22 @@ template <int PR>
 __global__ void __launch_bounds__(BNT) bi_rho_kernel(int h, const char* rh, const char* r, BiState* st,
                                                      double* partials, unsigned* counter) {
   typedef typename SpinorFmt<PR>::real RR;
+  typedef typename SiteSum<RR>::type SR;
   double acc[3] = {0.0, 0.0, 0.0};
   for (int i = blockIdx.x * BNT + threadIdx.x; i < h; i += gridDim.x * BNT) {
     cpx<RR> a[12], b[12];
     SpinorFmt<PR>::load(rh, h, i, a);
     SpinorFmt<PR>::load(r, h, i, b);
+    SR l[3] = {SR(0), SR(0), SR(0)};
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-      const double ar = a[k].re, ai = a[k].im, br = b[k].re, bi = b[k].im;
-      acc[0] += ar * br + ai * bi;
-      acc[1] += ar * bi - ai * br;
-      acc[2] += br * br + bi * bi;
+      const SR ar = a[k].re, ai = a[k].im, br = b[k].re, bi = b[k].im;
+      l[0] += ar * br + ai * bi;
+      l[1] += ar * bi - ai * br;
+      l[2] += br * br + bi * bi;
     }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) acc[j] += (double)l[j];
   }
   double tot[3];
   if (!grid_sum<3>(acc, partials, counter, tot)) return;
@@ -377,18 +389,22 @@ __global__ void __launch_bounds__(BNT) mr_alpha_kernel(int h, const char* q, con
                                                        double* partials, unsigned* counter) {
   if (st->done) return;
   typedef typename SpinorFmt<P>::real R;
+  typedef typename SiteSum<R>::type SR;
   double acc[3] = {0.0, 0.0, 0.0};
   for (int i = blockIdx.x * BNT + threadIdx.x; i < h; i += gridDim.x * BNT) {
     cpx<R> a[12], b[12];
     SpinorFmt<P>::load(q, h, i, a);
     SpinorFmt<P>::load(r, h, i, b);
+    SR l[3] = {SR(0), SR(0), SR(0)};
 #pragma unroll
     for (int k = 0; k < 12; ++k) {  // conj(q) r, |q|^2
-      const double qr = a[k].re, qi = a[k].im, rr_ = b[k].re, ri = b[k].im;
-      acc[0] += qr * rr_ + qi * ri;
-      acc[1] += qr * ri - qi * rr_;
-      acc[2] += qr * qr + qi * qi;
+      const SR qr = a[k].re, qi = a[k].im, rr_ = b[k].re, ri = b[k].im;
+      l[0] += qr * rr_ + qi * ri;
+      l[1] += qr * ri - qi * rr_;
+      l[2] += qr * qr + qi * qi;
     }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) acc[j] += (double)l[j];
   }
   double tot[3];
   if (!grid_sum<3>(acc, partials, counter, tot)) return;
@@ -419,18 +435,21 @@ __global__ void __launch_bounds__(BNT) mr_update_kernel(int h, char* x, char* r,
   }
   typedef typename SpinorFmt<P>::real R;
   const cpx<R> al = mk<R>((R)S.alpha_re, (R)S.alpha_im);
+  typedef typename SiteSum<R>::type SR;
   double acc[1] = {0.0};
   for (int i = blockIdx.x * BNT + threadIdx.x; i < h; i += gridDim.x * BNT) {
     cpx<R> xv[12], rv[12], qv[12];
     SpinorFmt<P>::load(x, h, i, xv);
     SpinorFmt<P>::load(r, h, i, rv);
     SpinorFmt<P>::load(q, h, i, qv);
+    SR site = SR(0);
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
       xv[k] = xv[k] + al * rv[k];
       rv[k] = rv[k] - al * qv[k];
-      acc[0] += (double)rv[k].re * (double)rv[k].re + (double)rv[k].im * (double)rv[k].im;
+      site += (SR)norm2(rv[k]);
     }
+    acc[0] += (double)site;
     SpinorFmt<P>::store(x, h, i, xv);
     SpinorFmt<P>::store(r, h, i, rv);
   }

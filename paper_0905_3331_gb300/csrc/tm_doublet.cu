@@ -79,7 +79,9 @@ __global__ void __launch_bounds__(BNT) dsite_kernel(int h, const char* a, const 
   __shared__ double sh[BNT / 32];
   double acc = 0.0;
   const double al = MODE == 2 ? (alpha_src ? alpha_src->alpha : 1.0) : 0.0;
+  typedef typename SiteSum<R>::type SR;
   for (int i = blockIdx.x * BNT + threadIdx.x; i < h; i += gridDim.x * BNT) {
+    SR site = SR(0);
     cpx<R> va[2][12], vb[2][12], o[2][12];
 #pragma unroll
     for (int f = 0; f < 2; ++f) {
@@ -115,7 +117,7 @@ __global__ void __launch_bounds__(BNT) dsite_kernel(int h, const char* a, const 
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
           rv[k] = rv[k] - (RR)al * mk<RR>((RR)o[f][k].re, (RR)o[f][k].im);
-          acc += (double)rv[k].re * (double)rv[k].re + (double)rv[k].im * (double)rv[k].im;
+          site += (SR)norm2(rv[k]);
         }
         SpinorFmt<PR>::store(r + f * rstride, h, i, rv);
       }
@@ -126,9 +128,10 @@ __global__ void __launch_bounds__(BNT) dsite_kernel(int h, const char* a, const 
         if (MODE == 1)
 #pragma unroll
           for (int k = 0; k < 12; ++k)
-            acc += (double)o[f][k].re * (double)o[f][k].re + (double)o[f][k].im * (double)o[f][k].im;
+            site += (SR)norm2(o[f][k]);
       }
     }
+    acc += (double)site;
   }
   if (MODE != 0) {
     const double bs = block_sum<BNT>(acc, sh);

@@ -196,6 +196,9 @@ __device__ __forceinline__ void hop_all_pipelined(cpx<typename SpinorFmt<PREC>::
 // MODE 0: out = epi(hop).  MODE 1: same plus sum ||out||^2.
 // MODE 2: out buffer holds r (FP64 for FP64 storage, FP32 otherwise); r <- r - alpha * epi(hop),
 // plus sum ||r||^2.
+// MODE 3 (with y, FP64): out = D t with t = c hop + E y, plus sum ||t - M out||^2 with M the
+// inverse of D (coef.m): the residual of the site-diagonal solve M out = t that produced out,
+// from the hopping sum already in registers.
 //
 // TPS (threads per site) = 1, 2 or 4.  With TPS > 1 the 8 hops of a site are split over TPS
 // warps of the block (part q takes the directions q*4/TPS .. (q+1)*4/TPS - 1, both hops of
@@ -303,7 +306,8 @@ __global__ void __launch_bounds__(hop_spb(TPS) * TPS, hop_min_blocks(PREC, TPS, 
         acc[k] = sum;
       }
   }
-  double nrm = 0.0;
+  typedef typename SiteSum<R>::type SR;
+  SR nrm = SR(0);
   // epilogue: o_s = D_s (c acc_s + E_s y_s) on components [kb, ke)
   const R cc = (R)coef.c;
   const cpx<R> Du = mk<R>((R)coef.d_up_re, (R)coef.d_up_im), Dl = mk<R>((R)coef.d_lo_re, (R)coef.d_lo_im);
@@ -318,7 +322,12 @@ __global__ void __launch_bounds__(hop_spb(TPS) * TPS, hop_min_blocks(PREC, TPS, 
     for (int k = 0; k < 12; ++k) {
       const cpx<R> E = (k < 6) ? Eu : El;
       const cpx<R> D = (k < 6) ? Du : Dl;
-      o[k] = D * (cc * acc[k] + E * yv[k]);
+      const cpx<R> t = cc * acc[k] + E * yv[k];
+      o[k] = D * t;
+      if (MODE == 3 && k >= kb && k < ke) {
+        const cpx<R> M = (k < 6) ? mk<R>((R)coef.m_up_re, (R)coef.m_up_im) : mk<R>((R)coef.m_lo_re, (R)coef.m_lo_im);
+        nrm += (SR)norm2(t - M * o[k]);
+      }
     }
   } else {
 #pragma unroll
@@ -335,7 +344,7 @@ __global__ void __launch_bounds__(hop_spb(TPS) * TPS, hop_min_blocks(PREC, TPS, 
       for (int k = 0; k < 12; ++k)
         if (k >= kb && k < ke) {
           r[k] = r[k] - al * o[k];
-          nrm += (double)norm2(r[k]);
+          nrm += (SR)norm2(r[k]);
         }
       SpinorFmt<PR>::store_range(outr, g.h, cb, r, kb, ke, 0.f, false);
     }
@@ -356,13 +365,13 @@ __global__ void __launch_bounds__(hop_spb(TPS) * TPS, hop_min_blocks(PREC, TPS, 
       if (MODE == 1) {
 #pragma unroll
         for (int k = 0; k < 12; ++k)
-          if (k >= kb && k < ke) nrm += (double)norm2(o[k]);
+          if (k >= kb && k < ke) nrm += (SR)norm2(o[k]);
       }
       F::store_range(outr, g.h, cb, o, kb, ke, m, part == 0);
     }
   }
   if (MODE >= 1) {
-    const double bs = block_sum<NT>(nrm, sh);
+    const double bs = block_sum<NT>((double)nrm, sh);
     grid_reduce<NT>(red, rhs, gridDim.x, blockIdx.x, bs, sh);
   }
 }
@@ -387,7 +396,9 @@ tm_status hop_launch_tps(tm_lattice lat, const HopArgs& a, cudaStream_t s) {
     launch_pdl(hop_kernel<PREC, NREAL, true, 1, TPS, PIPE>, grid, dim3(NT), s, TM_HOP_ARGS);
   else if (has_y && a.mode == 2)
     launch_pdl(hop_kernel<PREC, NREAL, true, 2, TPS, PIPE>, grid, dim3(NT), s, TM_HOP_ARGS);
-  else
+  else if (has_y && a.mode == 3 && PREC == TM_F64) {
+    if constexpr (PREC == TM_F64) launch_pdl(hop_kernel<PREC, NREAL, true, 3, TPS, PIPE>, grid, dim3(NT), s, TM_HOP_ARGS);
+  } else
     return set_error(TM_ERR_ARG, "hopping: unsupported epilogue combination");
 #undef TM_HOP_ARGS
   count_launch();

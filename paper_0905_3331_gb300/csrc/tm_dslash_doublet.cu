@@ -59,7 +59,8 @@ __global__ void __launch_bounds__(HOP_NT) dhop_kernel(const Geom g, const int ou
   if (skip != nullptr && *skip != 0) return;
   const int cb = blockIdx.x * HOP_NT + threadIdx.x;
   const bool active = cb < g.h;
-  double nrm = 0.0;
+  typedef typename SiteSum<R>::type SR;
+  SR nrm = SR(0);
   if (active) {
     cpx<R> acc[2][12];
 #pragma unroll
@@ -126,7 +127,7 @@ __global__ void __launch_bounds__(HOP_NT) dhop_kernel(const Geom g, const int ou
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
           r[k] = r[k] - al * mk<RR>((RR)o[f][k].re, (RR)o[f][k].im);
-          nrm += (double)r[k].re * (double)r[k].re + (double)r[k].im * (double)r[k].im;
+          nrm += (SR)norm2(r[k]);
         }
         SpinorFmt<PR>::store(out + f * out_stride, g.h, cb, r);
       }
@@ -136,12 +137,12 @@ __global__ void __launch_bounds__(HOP_NT) dhop_kernel(const Geom g, const int ou
         SpinorFmt<PREC>::store(out + f * out_stride, g.h, cb, o[f]);
         if (MODE == 1)
 #pragma unroll
-          for (int k = 0; k < 12; ++k) nrm += (double)norm2(o[f][k]);
+          for (int k = 0; k < 12; ++k) nrm += (SR)norm2(o[f][k]);
       }
     }
   }
   if (MODE >= 1) {
-    const double bs = block_sum<HOP_NT>(nrm, sh);
+    const double bs = block_sum<HOP_NT>((double)nrm, sh);
     grid_reduce<HOP_NT>(red, 0, gridDim.x, blockIdx.x, bs, sh);
   }
 }
@@ -204,7 +205,8 @@ __global__ void __launch_bounds__(HOP_NT) dhop2_kernel(const Geom g, const int o
     }
     acc[k] = (co.swap && k >= 6) ? mk<R>(-v.re, -v.im) : v;
   }
-  double nrm = 0.0;
+  typedef typename SiteSum<R>::type SR;
+  SR nrm = SR(0);
   if (active) {
     const cpx<R>* o = acc;
     char* outf = out + f * out_stride;
@@ -217,18 +219,18 @@ __global__ void __launch_bounds__(HOP_NT) dhop2_kernel(const Geom g, const int o
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
         r[k] = r[k] - al * mk<RR>((RR)o[k].re, (RR)o[k].im);
-        nrm += (double)r[k].re * (double)r[k].re + (double)r[k].im * (double)r[k].im;
+        nrm += (SR)norm2(r[k]);
       }
       SpinorFmt<PR>::store(outf, g.h, cb, r);
     } else {
       SpinorFmt<PREC>::store(outf, g.h, cb, o);
       if (MODE == 1)
 #pragma unroll
-        for (int k = 0; k < 12; ++k) nrm += (double)norm2(o[k]);
+        for (int k = 0; k < 12; ++k) nrm += (SR)norm2(o[k]);
     }
   }
   if (MODE >= 1) {
-    const double bs = block_sum<HOP_NT>(nrm, sh);
+    const double bs = block_sum<HOP_NT>((double)nrm, sh);
     grid_reduce<HOP_NT>(red, 0, gridDim.x, blockIdx.x, bs, sh);
   }
 }

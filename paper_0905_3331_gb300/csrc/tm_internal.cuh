@@ -743,12 +743,13 @@ struct EpiCoef {
   double c;
   double d_up_re, d_up_im, d_lo_re, d_lo_im;
   double e_up_re, e_up_im, e_lo_re, e_lo_im;
+  double m_up_re, m_up_im, m_lo_re, m_lo_im;  // the inverse of D (residual epilogue, mode 3)
 };
 
 // Epilogue coefficient sets used by the operators (eq. eo0, eo2, eo3, App. B.2).
 EpiCoef epi_plain();                                    // out = H in
 EpiCoef epi_mdiag_inv_hop(double mut, int f);           // out = (M_ee^f)^-1 H in
-EpiCoef epi_scaled_minv(double mut, int f, double c);   // out = (M_ee^f)^-1 (c H in + y)
+EpiCoef epi_scaled_minv(double mut, int f, double c);   // out = (M_ee^f)^-1 (c H in + y); m = M_ee^f
 EpiCoef epi_full_M(double kappa, double mut, int f);    // out = (1 + i f mut g5) y - kappa H in
 EpiCoef epi_schur_q(double kappa, double mut, int f);   // out = g5 [(1 + i f mut g5) y - kappa^2 H in]
 EpiCoef epi_g5_y_plus(double c);                        // out = g5 (y + c H in)
@@ -836,6 +837,29 @@ __device__ __forceinline__ void fin_apply(const Reduce& red, int sys, double sum
   }
 }
 
+// A thread's own sum over its site's components, before the FP64 sum across threads and
+// blocks: FP32 when the terms are FP32 numbers (FP32 / FP16 storage), FP64 otherwise.  GB300
+// retires FP64 adds at ~1/60 of the FP32 rate; converting and adding a site's 24 terms in
+// FP64 cost more than the kernel's memory traffic (a 6 MB copy kernel with such a norm:
+// 8.9 us per launch against 2.8 us with the per-thread sum in FP32).
+template <typename R>
+struct SiteSum {
+  typedef double type;
+};
+template <>
+struct SiteSum<float> {
+  typedef float type;
+};
+
+// Arrival at a grid-wide counter: a device-scope atomic increment with release semantics (the
+// caller's earlier writes are visible to whoever observes the increment) and acquire semantics
+// (the caller sees the writes released by the increments before it).  Returns the old value.
+__device__ __forceinline__ unsigned arrive_acq_rel(unsigned* counter) {
+  unsigned prev;
+  asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(prev) : "l"(counter) : "memory");
+  return prev;
+}
+
 // Deterministic block sum of a double (fixed shuffle tree, then warps in order).
 template <int NT>
 __device__ __forceinline__ double block_sum(double v, double* sh) {
@@ -860,27 +884,26 @@ __device__ __forceinline__ void grid_reduce(const Reduce& red, int sys, int nblo
   __shared__ bool last;
   if (threadIdx.x == 0) {
     red.partials[(size_t)sys * nblocks + bid] = bsum;
-    __threadfence();
-    unsigned prev = atomicAdd(red.counters + sys, 1u);
-    last = (prev == (unsigned)nblocks - 1);
+    last = (arrive_acq_rel(red.counters + sys) == (unsigned)nblocks - 1);
   }
   __syncthreads();
   if (!last) return;
-  __threadfence();
-  // thread t adds partials t, t + NT, t + 2 NT, ... in that order; the loads of a group of 8
-  // are issued together (L2, bypassing L1, where the other blocks' partials are visible after
-  // their fence and this block's counter observation) so the tail pays one round trip per group
+  // thread t adds partials t, t + NT, t + 2 NT, ... in that order; the loads of a group of 16
+  // are issued together (L2, bypassing L1) so the tail pays one round trip per group.  Every
+  // other block's partial is visible here: its release increment precedes this block's
+  // acquiring one in the counter's modification order, and the barrier orders this block's
+  // threads after that acquire.
   double v = 0.0;
   const double* parts = red.partials + (size_t)sys * nblocks;
-  for (int base = threadIdx.x; base < nblocks; base += 8 * NT) {
-    double t[8];
+  for (int base = threadIdx.x; base < nblocks; base += 16 * NT) {
+    double t[16];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < 16; ++u) {
       const int k = base + u * NT;
       t[u] = k < nblocks ? __ldcg(parts + k) : 0.0;
     }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) v += t[u];
+    for (int u = 0; u < 16; ++u) v += t[u];
   }
   __syncthreads();
   double tot = block_sum<NT>(v, sh);

@@ -65,6 +65,9 @@ EpiCoef epi_scaled_minv(double mut, int f, double c) {  // (M_ee^f)^-1 (c H + y)
   EpiCoef e = epi_mdiag_inv_hop(mut, f);
   e.c = c;
   e.e_up_re = e.e_lo_re = 1.0;
+  e.m_up_re = e.m_lo_re = 1.0;  // M_ee^f = 1 + i f mut gamma5
+  e.m_up_im = f * mut;
+  e.m_lo_im = -f * mut;
   return e;
 }
 EpiCoef epi_full_M(double kappa, double mut, int f) {  // (1 + i f mut g5) y - kappa H

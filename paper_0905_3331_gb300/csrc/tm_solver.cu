@@ -84,9 +84,7 @@ __global__ void __launch_bounds__(BNT) cg_update_kernel(int h, char* x, char* p,
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
-    unsigned prev = atomicAdd(counter, 1u);
-    if (prev == gridDim.x - 1) {
+    if (arrive_acq_rel(counter) == gridDim.x - 1) {
       S.applied = iter;
       *counter = 0u;
       if (use_cond) {
@@ -102,27 +100,15 @@ template <int P>
 __global__ void __launch_bounds__(BNT) norm2_kernel(int h, const char* x, Reduce red) {
   __shared__ double sh[BNT / 32];
   typedef typename SpinorFmt<P>::real R;
+  typedef typename SiteSum<R>::type SR;
   double v = 0.0;
   for (int i = blockIdx.x * BNT + threadIdx.x; i < h; i += gridDim.x * BNT) {
     cpx<R> s[12];
     SpinorFmt<P>::load(x, h, i, s);
+    SR site = SR(0);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) v += (double)norm2(s[k]);
-  }
-  const double bs = block_sum<BNT>(v, sh);
-  grid_reduce<BNT>(red, 0, gridDim.x, blockIdx.x, bs, sh);
-}
-
-// sum ||a - b||^2 over FP64 half fields
-__global__ void __launch_bounds__(BNT) diffnorm2_kernel(int h, const char* a, const char* b, Reduce red) {
-  __shared__ double sh[BNT / 32];
-  double v = 0.0;
-  for (int i = blockIdx.x * BNT + threadIdx.x; i < h; i += gridDim.x * BNT) {
-    cpx<double> s[12], t[12];
-    SpinorFmt<TM_F64>::load(a, h, i, s);
-    SpinorFmt<TM_F64>::load(b, h, i, t);
-#pragma unroll
-    for (int k = 0; k < 12; ++k) v += norm2(s[k] - t[k]);
+    for (int k = 0; k < 12; ++k) site += (SR)norm2(s[k]);
+    v += (double)site;
   }
   const double bs = block_sum<BNT>(v, sh);
   grid_reduce<BNT>(red, 0, gridDim.x, blockIdx.x, bs, sh);
@@ -615,6 +601,9 @@ tm_status prepare_source(const Solver& S, const double* b, void* be, void* bo, v
   if ((st = pack_full_parity(lat, TM_F64, bo, b, 1, 0, s)) != TM_OK) return st;
   const double n = 1.0 / (1.0 + S.mut * S.mut);
   if ((st = diag_apply(lat, TM_F64, T, be, 1, n, -S.f * S.mut * n, n, S.f * S.mut * n, s)) != TM_OK) return st;
+  // ||b'||^2, ||b_e||^2, ||b_o||^2 into dscalars[0..2], read back with one synchronisation
+  const unsigned nb = blas_blocks(lat->geom.h);
+  if ((st = ensure_reduce(lat, std::max<size_t>(hop_grid_blocks(lat->h, 4), nb), 4)) != TM_OK) return st;
   HopArgs a{};
   a.prec = TM_F64;
   a.nreal = 18;
@@ -624,13 +613,22 @@ tm_status prepare_source(const Solver& S, const double* b, void* be, void* bo, v
   a.y = bo;
   a.out = bp;
   a.coef = epi_g5_y_plus(lat->kappa);
+  a.mode = 1;
+  a.red = Reduce{lat->partials, lat->counters, lat->dscalars, nullptr, FIN_STORE};
   if ((st = hop_launch(lat, a, s)) != TM_OK) return st;
-  double tmp = 0.0;
-  if ((st = norm2_half(S, TM_F64, bp, bb)) != TM_OK) return st;
-  if ((st = norm2_half(S, TM_F64, be, &tmp)) != TM_OK) return st;
-  *bfull = tmp;
-  if ((st = norm2_half(S, TM_F64, bo, &tmp)) != TM_OK) return st;
-  *bfull += tmp;
+  for (int k = 0; k < 2; ++k) {
+    const Reduce red{lat->partials, lat->counters, lat->dscalars + 1 + k, nullptr, FIN_STORE};
+    norm2_kernel<TM_F64><<<nb, BNT, 0, s>>>(lat->geom.h, static_cast<const char*>(k ? bo : be), red);
+    count_launch();
+  }
+  if ((st = cuda_check(cudaGetLastError(), "norm kernel")) != TM_OK) return st;
+  double* nn = reinterpret_cast<double*>(lat->flag_host);
+  if ((st = cuda_check(cudaMemcpyAsync(nn, lat->dscalars, 3 * sizeof(double), cudaMemcpyDeviceToHost, s),
+                       "readback")) != TM_OK)
+    return st;
+  if ((st = cuda_check(cudaStreamSynchronize(s), "synchronise")) != TM_OK) return st;
+  *bb = nn[0];
+  *bfull = nn[1] + nn[2];
   return TM_OK;
 }
 
@@ -659,12 +657,17 @@ tm_status reconstruct_check(const Solver& S, const void* X, const void* be, cons
 }
 
 // x_e = (M_ee^f)^-1 (b_e + kappa H_eo x_o) from the odd solution xo, written with xo to the
-// canonical field x; then ||b - M x|| / ||b|| in FP64 (T, R, Pv are FP64 scratch).
+// canonical field x; then ||b - M x|| / ||b|| in FP64 (T, R, Pv are FP64 scratch).  Two FP64
+// hopping launches: the first stores x_e and sums the even residual
+// ||b_e + kappa H_eo x_o - M_ee x_e||^2 from the same hopping sum; the second forms
+// (b - M x)_o = b_o - (M_oo x_o - kappa H_oe x_e) and its norm.  R is unused.
 tm_status reconstruct_xo(const Solver& S, const void* xo, const void* be, const void* bo, double bfull, double* x,
                          void* T, void* R, void* Pv, double* true_rel) {
+  (void)R;
   tm_lattice lat = S.lat;
   cudaStream_t s = S.s;
-  tm_status st;
+  tm_status st = ensure_reduce(lat, hop_grid_blocks(lat->h, 4), 4);
+  if (st != TM_OK) return st;
   void* W = const_cast<void*>(xo);
   HopArgs a{};
   a.prec = TM_F64;
@@ -675,36 +678,27 @@ tm_status reconstruct_xo(const Solver& S, const void* xo, const void* be, const 
   a.y = be;
   a.out = T;  // x_e
   a.coef = epi_scaled_minv(S.mut, S.f, lat->kappa);
+  a.mode = 3;
+  a.red = Reduce{lat->partials, lat->counters, lat->dscalars, nullptr, FIN_STORE};
   if ((st = hop_launch(lat, a, s)) != TM_OK) return st;
-  // (M x)_e into R, (M x)_o into Pv
+  if ((st = cuda_check(cudaMemcpyAsync(Pv, bo, S.hb[TM_F64], cudaMemcpyDeviceToDevice, s), "copy")) != TM_OK)
+    return st;
   a.coef = epi_full_M(lat->kappa, S.mut, S.f);
-  a.out_parity = 0;
-  a.in = W;
-  a.y = T;
-  a.out = R;
-  if ((st = hop_launch(lat, a, s)) != TM_OK) return st;
   a.out_parity = 1;
   a.in = T;
   a.y = W;
   a.out = Pv;
+  a.mode = 2;  // Pv -= 1 * (M x)_o
+  a.alpha_src = nullptr;
+  a.alpha_sign = 1.0;
+  a.red = Reduce{lat->partials, lat->counters, lat->dscalars + 1, nullptr, FIN_STORE};
   if ((st = hop_launch(lat, a, s)) != TM_OK) return st;
-  double rre = 0.0, rro = 0.0;
-  const unsigned nb = blas_blocks(lat->geom.h);
-  Reduce red{lat->partials, lat->counters, lat->dscalars, nullptr, FIN_STORE};
-  diffnorm2_kernel<<<nb, BNT, 0, s>>>(lat->geom.h, static_cast<const char*>(be), static_cast<const char*>(R), red);
-  count_launch();
-  if ((st = cuda_check(cudaMemcpyAsync(&lat->flag_host[0], lat->dscalars, sizeof(double), cudaMemcpyDeviceToHost, s),
+  double* rr = reinterpret_cast<double*>(lat->flag_host);
+  if ((st = cuda_check(cudaMemcpyAsync(rr, lat->dscalars, 2 * sizeof(double), cudaMemcpyDeviceToHost, s),
                        "readback")) != TM_OK)
     return st;
   if ((st = cuda_check(cudaStreamSynchronize(s), "synchronise")) != TM_OK) return st;
-  memcpy(&rre, &lat->flag_host[0], sizeof(double));
-  diffnorm2_kernel<<<nb, BNT, 0, s>>>(lat->geom.h, static_cast<const char*>(bo), static_cast<const char*>(Pv), red);
-  count_launch();
-  if ((st = cuda_check(cudaMemcpyAsync(&lat->flag_host[0], lat->dscalars, sizeof(double), cudaMemcpyDeviceToHost, s),
-                       "readback")) != TM_OK)
-    return st;
-  if ((st = cuda_check(cudaStreamSynchronize(s), "synchronise")) != TM_OK) return st;
-  memcpy(&rro, &lat->flag_host[0], sizeof(double));
+  const double rre = rr[0], rro = rr[1];
   *true_rel = bfull > 0.0 ? std::sqrt((rre + rro) / bfull) : 0.0;
   if ((st = unpack_full_parity(lat, TM_F64, x, T, 0, 0, s)) != TM_OK) return st;
   return unpack_full_parity(lat, TM_F64, x, W, 1, 0, s);
