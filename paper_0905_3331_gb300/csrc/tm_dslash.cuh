@@ -91,6 +91,179 @@ __device__ __forceinline__ void su3_adj_mul2(const Mat3<R>& U, const cpx<R> h0[3
   }
 }
 
+// ------------------------------------------------------------ direction pairs ---
+// The forward and backward hops of one direction mu reach the lower two spin components of the
+// output through the same fixed map P_mu (the +1 column of the table at the top) with opposite
+// signs: upper += u+ + u-, lower += P_mu (u+ - u-), u+- = U(+-) h(+-) the two-spinor results of
+// the hops.  So a pair forms s = u+ + u- by continuing the FMA chains of u+ with the backward
+// products, d = 2 u+ - s with one FMA per real, and adds s and P_mu d to the accumulator: 12 +
+// 12 adds per real pair instead of 2 x 24, and every colour row is one FMA chain (the product
+// form a*b + c*d + ... with separate multiplies and adds took 30% DMUL and 43% DADD of the FP64
+// pipe).  FP64 / FP32 / FP16 storage; double-float keeps the per-hop form (no fused FMA).
+template <typename R>
+__device__ __forceinline__ R fmadd(R a, R b, R c);
+template <>
+__device__ __forceinline__ float fmadd<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+template <>
+__device__ __forceinline__ double fmadd<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// u = U h for two colour vectors, each real part one chain
+template <typename R>
+__device__ __forceinline__ void su3_mul2_fma(const Mat3<R>& U, const cpx<R> h0[3], const cpx<R> h1[3], cpx<R> u0[3],
+                                             cpx<R> u1[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    R r0 = U.m[a][0].re * h0[0].re, i0 = U.m[a][0].re * h0[0].im;
+    R r1 = U.m[a][0].re * h1[0].re, i1 = U.m[a][0].re * h1[0].im;
+    r0 = fmadd(-U.m[a][0].im, h0[0].im, r0);
+    i0 = fmadd(U.m[a][0].im, h0[0].re, i0);
+    r1 = fmadd(-U.m[a][0].im, h1[0].im, r1);
+    i1 = fmadd(U.m[a][0].im, h1[0].re, i1);
+#pragma unroll
+    for (int b = 1; b < 3; ++b) {
+      r0 = fmadd(U.m[a][b].re, h0[b].re, r0);
+      r0 = fmadd(-U.m[a][b].im, h0[b].im, r0);
+      i0 = fmadd(U.m[a][b].re, h0[b].im, i0);
+      i0 = fmadd(U.m[a][b].im, h0[b].re, i0);
+      r1 = fmadd(U.m[a][b].re, h1[b].re, r1);
+      r1 = fmadd(-U.m[a][b].im, h1[b].im, r1);
+      i1 = fmadd(U.m[a][b].re, h1[b].im, i1);
+      i1 = fmadd(U.m[a][b].im, h1[b].re, i1);
+    }
+    u0[a] = mk<R>(r0, i0);
+    u1[a] = mk<R>(r1, i1);
+  }
+}
+
+// s = u + U^dag h for two colour vectors: the chains continue from u
+template <typename R>
+__device__ __forceinline__ void su3_adj_mul2_add(const Mat3<R>& U, const cpx<R> h0[3], const cpx<R> h1[3],
+                                                 const cpx<R> u0[3], const cpx<R> u1[3], cpx<R> s0[3],
+                                                 cpx<R> s1[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    R r0 = u0[a].re, i0 = u0[a].im, r1 = u1[a].re, i1 = u1[a].im;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {  // conj(U[b][a]) h[b]
+      r0 = fmadd(U.m[b][a].re, h0[b].re, r0);
+      r0 = fmadd(U.m[b][a].im, h0[b].im, r0);
+      i0 = fmadd(U.m[b][a].re, h0[b].im, i0);
+      i0 = fmadd(-U.m[b][a].im, h0[b].re, i0);
+      r1 = fmadd(U.m[b][a].re, h1[b].re, r1);
+      r1 = fmadd(U.m[b][a].im, h1[b].im, r1);
+      i1 = fmadd(U.m[b][a].re, h1[b].im, i1);
+      i1 = fmadd(-U.m[b][a].im, h1[b].re, i1);
+    }
+    s0[a] = mk<R>(r0, i0);
+    s1[a] = mk<R>(r1, i1);
+  }
+}
+
+// Projection of one hop's neighbour spinor with the FP16 per-site norm and the boundary sign.
+template <int PREC, int MU, int S>
+__device__ __forceinline__ void project_scaled(const cpx<typename SpinorFmt<PREC>::real> p[12],
+                                               typename SpinorFmt<PREC>::real scale, bool negate,
+                                               cpx<typename SpinorFmt<PREC>::real> h0[3],
+                                               cpx<typename SpinorFmt<PREC>::real> h1[3]) {
+  typedef typename SpinorFmt<PREC>::real R;
+  project<R, MU, S>(p, h0, h1);
+  if (SpinorFmt<PREC>::has_norm) {
+    const R f = (MU == 0 && negate) ? -scale : scale;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      h0[c] = f * h0[c];
+      h1[c] = f * h1[c];
+    }
+  } else if (MU == 0 && negate) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      h0[c] = mk<R>(-h0[c].re, -h0[c].im);
+      h1[c] = mk<R>(-h1[c].re, -h1[c].im);
+    }
+  }
+}
+
+// First half of a pair: u = U_mu(x) (1 + gamma_mu) in(x + mu^), projected.
+template <int PREC, int NREAL, int MU>
+__device__ __forceinline__ void pair_fwd(cpx<typename SpinorFmt<PREC>::real> u0[3],
+                                         cpx<typename SpinorFmt<PREC>::real> u1[3],
+                                         const RawWords<NREAL * LinkStore<PREC>::size>& raw,
+                                         const cpx<typename SpinorFmt<PREC>::real> p[12],
+                                         typename SpinorFmt<PREC>::real scale, bool negate) {
+  typedef typename SpinorFmt<PREC>::real R;
+  cpx<R> h0[3], h1[3];
+  project_scaled<PREC, MU, +1>(p, scale, negate, h0, h1);
+  Mat3<R> U;
+  LinkRecon<R, typename LinkStore<PREC>::type, NREAL>::unpack(raw, U);
+  su3_mul2_fma(U, h0, h1, u0, u1);
+}
+
+// Second half: the backward hop U_mu(x - mu^)^dag (1 - gamma_mu) in(x - mu^) completes the pair,
+// which is added to the accumulator (written, for the first pair of the accumulator).
+template <int PREC, int NREAL, int MU, bool FIRST>
+__device__ __forceinline__ void pair_bwd(cpx<typename SpinorFmt<PREC>::real> acc[12],
+                                         const cpx<typename SpinorFmt<PREC>::real> u0[3],
+                                         const cpx<typename SpinorFmt<PREC>::real> u1[3],
+                                         const RawWords<NREAL * LinkStore<PREC>::size>& raw,
+                                         const cpx<typename SpinorFmt<PREC>::real> p[12],
+                                         typename SpinorFmt<PREC>::real scale, bool negate) {
+  typedef typename SpinorFmt<PREC>::real R;
+  cpx<R> h0[3], h1[3];
+  project_scaled<PREC, MU, -1>(p, scale, negate, h0, h1);
+  Mat3<R> U;
+  LinkRecon<R, typename LinkStore<PREC>::type, NREAL>::unpack(raw, U);
+  cpx<R> s0[3], s1[3];
+  su3_adj_mul2_add(U, h0, h1, u0, u1, s0, s1);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const cpx<R> d0 = mk<R>(fmadd(R(2), u0[a].re, -s0[a].re), fmadd(R(2), u0[a].im, -s0[a].im));
+    const cpx<R> d1 = mk<R>(fmadd(R(2), u1[a].re, -s1[a].re), fmadd(R(2), u1[a].im, -s1[a].im));
+    cpx<R> l2, l3;  // P_mu d
+    if (MU == 0) {
+      l2 = mk<R>(-d0.re, -d0.im);
+      l3 = mk<R>(-d1.re, -d1.im);
+    } else if (MU == 1) {
+      l2 = times_i(d1);
+      l3 = times_i(d0);
+    } else if (MU == 2) {
+      l2 = d1;
+      l3 = mk<R>(-d0.re, -d0.im);
+    } else {
+      l2 = times_i(d0);
+      l3 = mk<R>(d1.im, -d1.re);  // -i d1
+    }
+    if (FIRST) {
+      acc[a] = s0[a];
+      acc[3 + a] = s1[a];
+      acc[6 + a] = l2;
+      acc[9 + a] = l3;
+    } else {
+      acc[a] = acc[a] + s0[a];
+      acc[3 + a] = acc[3 + a] + s1[a];
+      acc[6 + a] = acc[6 + a] + l2;
+      acc[9 + a] = acc[9 + a] + l3;
+    }
+  }
+}
+
+// Both hops of direction mu, loads then arithmetic.
+template <int PREC, int NREAL, int MU, bool FIRST>
+__device__ __forceinline__ void hop_pair(cpx<typename SpinorFmt<PREC>::real> acc[12], const void* in, int h,
+                                         int nbf, const char* slabf, int lif, bool negf, int nbb, const char* slabb,
+                                         int lib, bool negb) {
+  typedef typename SpinorFmt<PREC>::real R;
+  constexpr int BYTES = NREAL * LinkStore<PREC>::size;
+  const RawWords<BYTES> rf = load_raw<BYTES>(slabf, h, lif);
+  const RawWords<BYTES> rb = load_raw<BYTES>(slabb, h, lib);
+  cpx<R> p[12];
+  R scale;
+  SpinorFmt<PREC>::load_unscaled(in, h, nbf, p, scale);
+  cpx<R> u0[3], u1[3];
+  pair_fwd<PREC, NREAL, MU>(u0, u1, rf, p, scale, negf);
+  SpinorFmt<PREC>::load_unscaled(in, h, nbb, p, scale);
+  pair_bwd<PREC, NREAL, MU, FIRST>(acc, u0, u1, rb, p, scale, negb);
+}
+
 // One hop.  Forward (S = +1): link U_mu(x) from the output parity's slab at the output site.
 // Backward (S = -1): link U_mu(x - mu^) from the other parity's slab at the neighbour's index,
 // applied as its adjoint -- the same stored link serves both hops, so the operator keeps
@@ -159,38 +332,39 @@ __device__ __forceinline__ void hop_fetch(HopWords<PREC, NREAL>& d, const char* 
   SpinorFmt<PREC>::load_words(in, h, nbi, d.sp);
 }
 
-template <int PREC, int NREAL, int MU, int S>
-__device__ __forceinline__ void hop_finish(cpx<typename SpinorFmt<PREC>::real> acc[12],
-                                           const HopWords<PREC, NREAL>& d, bool negate) {
-  typedef typename SpinorFmt<PREC>::real R;
-  cpx<R> p[12];
-  R scale;
-  SpinorFmt<PREC>::unpack_words(d.sp, p, scale);
-  hop_apply<PREC, NREAL, MU, S>(acc, d.link, p, scale, negate);
-}
-
 template <int PREC, int NREAL>
 __device__ __forceinline__ void hop_all_pipelined(cpx<typename SpinorFmt<PREC>::real> acc[12], const Geom& g,
                                                   int cb, const SiteCoord& c, const int nb[8], const char* inr,
                                                   const char* lf, const char* lo, size_t slab) {
+  typedef typename SpinorFmt<PREC>::real R;
   const bool tfwd = (c.t == g.T - 1), tbwd = (c.t == 0);
-  HopWords<PREC, NREAL> A, B;
+  HopWords<PREC, NREAL> A, B;  // forward and backward hop of the current direction
+  cpx<R> u0[3], u1[3], p[12];
+  R scale;
   hop_fetch(A, inr, g.h, nb[0], lf + 0 * slab, cb);
   hop_fetch(B, inr, g.h, nb[4], lo + 0 * slab, nb[4]);
-  hop_finish<PREC, NREAL, 0, +1>(acc, A, tfwd);
+#define TM_PIPE_FWD(MU, NEG)                                \
+  SpinorFmt<PREC>::unpack_words(A.sp, p, scale);            \
+  pair_fwd<PREC, NREAL, MU>(u0, u1, A.link, p, scale, NEG);
+#define TM_PIPE_BWD(MU, FIRST, NEG)                         \
+  SpinorFmt<PREC>::unpack_words(B.sp, p, scale);            \
+  pair_bwd<PREC, NREAL, MU, FIRST>(acc, u0, u1, B.link, p, scale, NEG);
+  TM_PIPE_FWD(0, tfwd)
   hop_fetch(A, inr, g.h, nb[1], lf + 1 * slab, cb);
-  hop_finish<PREC, NREAL, 0, -1>(acc, B, tbwd);
+  TM_PIPE_BWD(0, true, tbwd)
   hop_fetch(B, inr, g.h, nb[5], lo + 1 * slab, nb[5]);
-  hop_finish<PREC, NREAL, 1, +1>(acc, A, false);
+  TM_PIPE_FWD(1, false)
   hop_fetch(A, inr, g.h, nb[2], lf + 2 * slab, cb);
-  hop_finish<PREC, NREAL, 1, -1>(acc, B, false);
+  TM_PIPE_BWD(1, false, false)
   hop_fetch(B, inr, g.h, nb[6], lo + 2 * slab, nb[6]);
-  hop_finish<PREC, NREAL, 2, +1>(acc, A, false);
+  TM_PIPE_FWD(2, false)
   hop_fetch(A, inr, g.h, nb[3], lf + 3 * slab, cb);
-  hop_finish<PREC, NREAL, 2, -1>(acc, B, false);
+  TM_PIPE_BWD(2, false, false)
   hop_fetch(B, inr, g.h, nb[7], lo + 3 * slab, nb[7]);
-  hop_finish<PREC, NREAL, 3, +1>(acc, A, false);
-  hop_finish<PREC, NREAL, 3, -1>(acc, B, false);
+  TM_PIPE_FWD(3, false)
+  TM_PIPE_BWD(3, false, false)
+#undef TM_PIPE_FWD
+#undef TM_PIPE_BWD
 }
 
 // MODE 0: out = epi(hop).  MODE 1: same plus sum ||out||^2.
@@ -211,21 +385,39 @@ __device__ __forceinline__ void hop_part(cpx<typename SpinorFmt<PREC>::real> acc
                                          const SiteCoord& c, const int nb[8], const char* inr, const char* lf,
                                          const char* lo, size_t slab, int part) {
   const bool tfwd = (c.t == g.T - 1), tbwd = (c.t == 0);
-  if (TPS == 1 || part == 0 || (TPS == 2 && part == 0)) {
-    hop_dir<PREC, NREAL, 0, +1>(acc, inr, g.h, nb[0], lf + 0 * slab, cb, tfwd);
-    hop_dir<PREC, NREAL, 0, -1>(acc, inr, g.h, nb[4], lo + 0 * slab, nb[4], tbwd);
-  }
-  if (TPS == 1 || (TPS == 2 && part == 0) || (TPS == 4 && part == 1)) {
-    hop_dir<PREC, NREAL, 1, +1>(acc, inr, g.h, nb[1], lf + 1 * slab, cb, false);
-    hop_dir<PREC, NREAL, 1, -1>(acc, inr, g.h, nb[5], lo + 1 * slab, nb[5], false);
-  }
-  if (TPS == 1 || (TPS == 2 && part == 1) || (TPS == 4 && part == 2)) {
-    hop_dir<PREC, NREAL, 2, +1>(acc, inr, g.h, nb[2], lf + 2 * slab, cb, false);
-    hop_dir<PREC, NREAL, 2, -1>(acc, inr, g.h, nb[6], lo + 2 * slab, nb[6], false);
-  }
-  if (TPS == 1 || (TPS == 2 && part == 1) || (TPS == 4 && part == 3)) {
-    hop_dir<PREC, NREAL, 3, +1>(acc, inr, g.h, nb[3], lf + 3 * slab, cb, false);
-    hop_dir<PREC, NREAL, 3, -1>(acc, inr, g.h, nb[7], lo + 3 * slab, nb[7], false);
+  if constexpr (PREC == TM_DF64) {  // per hop (no fused multiply-add for double-float)
+    if (TPS == 1 || part == 0 || (TPS == 2 && part == 0)) {
+      hop_dir<PREC, NREAL, 0, +1>(acc, inr, g.h, nb[0], lf + 0 * slab, cb, tfwd);
+      hop_dir<PREC, NREAL, 0, -1>(acc, inr, g.h, nb[4], lo + 0 * slab, nb[4], tbwd);
+    }
+    if (TPS == 1 || (TPS == 2 && part == 0) || (TPS == 4 && part == 1)) {
+      hop_dir<PREC, NREAL, 1, +1>(acc, inr, g.h, nb[1], lf + 1 * slab, cb, false);
+      hop_dir<PREC, NREAL, 1, -1>(acc, inr, g.h, nb[5], lo + 1 * slab, nb[5], false);
+    }
+    if (TPS == 1 || (TPS == 2 && part == 1) || (TPS == 4 && part == 2)) {
+      hop_dir<PREC, NREAL, 2, +1>(acc, inr, g.h, nb[2], lf + 2 * slab, cb, false);
+      hop_dir<PREC, NREAL, 2, -1>(acc, inr, g.h, nb[6], lo + 2 * slab, nb[6], false);
+    }
+    if (TPS == 1 || (TPS == 2 && part == 1) || (TPS == 4 && part == 3)) {
+      hop_dir<PREC, NREAL, 3, +1>(acc, inr, g.h, nb[3], lf + 3 * slab, cb, false);
+      hop_dir<PREC, NREAL, 3, -1>(acc, inr, g.h, nb[7], lo + 3 * slab, nb[7], false);
+    }
+  } else {
+    // direction pairs; the first pair of a part writes the accumulator
+    if (TPS == 1 || part == 0)
+      hop_pair<PREC, NREAL, 0, true>(acc, inr, g.h, nb[0], lf + 0 * slab, cb, tfwd, nb[4], lo + 0 * slab, nb[4], tbwd);
+    if (TPS == 1 || (TPS == 2 && part == 0))
+      hop_pair<PREC, NREAL, 1, false>(acc, inr, g.h, nb[1], lf + 1 * slab, cb, false, nb[5], lo + 1 * slab, nb[5], false);
+    if (TPS == 4 && part == 1)
+      hop_pair<PREC, NREAL, 1, true>(acc, inr, g.h, nb[1], lf + 1 * slab, cb, false, nb[5], lo + 1 * slab, nb[5], false);
+    if (TPS == 1)
+      hop_pair<PREC, NREAL, 2, false>(acc, inr, g.h, nb[2], lf + 2 * slab, cb, false, nb[6], lo + 2 * slab, nb[6], false);
+    if ((TPS == 2 && part == 1) || (TPS == 4 && part == 2))
+      hop_pair<PREC, NREAL, 2, true>(acc, inr, g.h, nb[2], lf + 2 * slab, cb, false, nb[6], lo + 2 * slab, nb[6], false);
+    if (TPS == 1 || (TPS == 2 && part == 1))
+      hop_pair<PREC, NREAL, 3, false>(acc, inr, g.h, nb[3], lf + 3 * slab, cb, false, nb[7], lo + 3 * slab, nb[7], false);
+    if (TPS == 4 && part == 3)
+      hop_pair<PREC, NREAL, 3, true>(acc, inr, g.h, nb[3], lf + 3 * slab, cb, false, nb[7], lo + 3 * slab, nb[7], false);
   }
 }
 
