@@ -32,10 +32,10 @@ METRIC = "Dslash GB/s & % HBM roofline; CG solves/sec to 1e-10 FP64 residual, mi
 HOP_FLOPS = 1320  # per output site per hopping application (8 hops x 168 flops - 24)
 # dram__bytes_read.sum + dram__bytes_write.sum of one hopping-kernel launch, from ncu captures
 # (profiles/), keyed by sloppy form, lattice and kernel choice (threads per site; 3 = the
-# software-pipelined one-thread kernel), each from an ncu --set full capture on 16^3 x 32:
-# plain (profiles/hop_f32_12_16x32_and_32x64_full.md), pipelined
-# (profiles/hop_f32_12_16x32_pipelined_full.md)
-NCU_TRAFFIC = {("f32:12", "16^3x32", 1): 31492864.0, ("f32:12", "16^3x32", 3): 31487744.0}
+# software-pipelined one-thread kernel), from ncu --set full captures of the current kernels:
+# pipelined on 16^3 x 32 (profiles/hop_f32_12_16x32_pipelined_full.md), plain on 32^3 x 64
+# (profiles/hop_f32_12_16x32_and_32x64_full.md)
+NCU_TRAFFIC = {("f32:12", "16^3x32", 3): 31485184.0, ("f32:12", "32^3x64", 1): 600914688.0}
 HOP_VARIANT = {1: "1 thread per site", 2: "2 threads per site", 4: "4 threads per site",
                3: "1 thread per site, pipelined loads"}
 

@@ -422,20 +422,29 @@ __device__ __forceinline__ void hop_part(cpx<typename SpinorFmt<PREC>::real> acc
 }
 
 // FP32 / FP16 storage with one thread per site: a register budget for 12 blocks of 64 threads
-// per SM (80 per thread instead of 86-92).  The kernel is memory-latency bound and the extra
-// warps win over a few spilled bytes (FP32/12: 32^3 x 64 118 -> 113 us, 16^3 x 32 18.9 -> 17.6 us
-// per launch).  FP64 and double-float keep their full budget (~180 registers, ALU bound).
+// per SM with 12-real links (80 per thread instead of 86-92).  The kernel is memory-latency
+// bound and the extra warps win over a few spilled bytes (FP32/12: 32^3 x 64 118 -> 113 us,
+// 16^3 x 32 18.9 -> 17.6 us per launch).  8- and 18-real links get 10 blocks (96 registers):
+// at 80 their direction pairs spilled 84-156 bytes (FP32/8 on 32^3 x 64: 115 -> 107 us with
+// 96, FP32/18: 157 -> 140 us).  FP64 and double-float keep their full budget (ALU bound).
 // The software-pipelined form holds two hops' words (72 more registers for FP32/12): a budget
 // for HOP_PIPE_BLOCKS blocks per SM.
 #ifndef HOP_PIPE_BLOCKS
 #define HOP_PIPE_BLOCKS 7
 #endif
-constexpr int hop_min_blocks(int prec, int tps, bool pipe) {
-  return pipe ? HOP_PIPE_BLOCKS : ((tps == 1 && (prec == TM_F32 || prec == TM_F16)) ? 12 : 1);
+#ifndef HOP_BLOCKS_12
+#define HOP_BLOCKS_12 12
+#endif
+#ifndef HOP_BLOCKS_OTHER
+#define HOP_BLOCKS_OTHER 10
+#endif
+constexpr int hop_min_blocks(int prec, int nreal, int tps, bool pipe) {
+  return pipe ? HOP_PIPE_BLOCKS
+              : ((tps == 1 && (prec == TM_F32 || prec == TM_F16)) ? (nreal == 12 ? HOP_BLOCKS_12 : HOP_BLOCKS_OTHER) : 1);
 }
 
 template <int PREC, int NREAL, bool HAS_Y, int MODE, int TPS, bool PIPE>
-__global__ void __launch_bounds__(hop_spb(TPS) * TPS, hop_min_blocks(PREC, TPS, PIPE)) hop_kernel(const Geom g, const int out_parity,
+__global__ void __launch_bounds__(hop_spb(TPS) * TPS, hop_min_blocks(PREC, NREAL, TPS, PIPE)) hop_kernel(const Geom g, const int out_parity,
                                                      const char* __restrict__ links, const void* in,
                                                      size_t in_stride, void* out, size_t out_stride,
                                                      const void* y, size_t y_stride, const EpiCoef coef,

@@ -348,9 +348,20 @@ static tm_status tune_hop(tm_lattice lat, int prec, int nreal, cudaStream_t s) {
       if (k > 0 && ms < score[c]) score[c] = ms;
     }
   }
-  // The pipelined form must be 2% faster than the plain one, more threads per site 10% faster
-  // than the better of the two.
-  int bi = (has_pipe && score[1] < 0.98f * score[0]) ? 1 : 0;
+  // Plain or pipelined: a difference above 3% decides; within 3% (the scores' repeat-to-repeat
+  // spread) the rule does, so that the choice is reproducible: the pipelined kernel where the
+  // plain one's grid fits in one wave (each thread's load latencies set the launch time there:
+  // 16^3 x 32 FP32/12 1.9% faster inside the mixed solve, 13% per cold launch), else the plain
+  // one.  More threads per site must be 10% faster than the better of the two.
+  int bi = 0;
+  if (has_pipe) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
+    const bool one_wave = lat->h <= (size_t)sms * HOP_BLOCKS_12 * hop_spb(1);
+    const float ratio = score[1] / score[0];
+    bi = ratio < 0.97f ? 1 : (ratio > 1.03f ? 0 : (one_wave ? 1 : 0));
+  }
   const float base = score[bi];
   for (int c = 2; c < 4; ++c)
     if (score[c] < 0.9f * base && score[c] < score[bi]) bi = c;
