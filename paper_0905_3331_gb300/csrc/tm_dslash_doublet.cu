@@ -15,36 +15,25 @@
 
 namespace tmq {
 
-template <int PREC, int NREAL, int MU, int S>
-__device__ __forceinline__ void dhop_dir(cpx<typename SpinorFmt<PREC>::real> acc[2][12], const char* in,
-                                         size_t stride, int h, int nbi, const char* slab, int link_index,
-                                         bool negate) {
+// Both hops of direction mu for both flavours: the one-flavour direction-pair arithmetic
+// (tm_dslash.cuh) per flavour, with the pair's two links loaded once for the two flavours.
+template <int PREC, int NREAL, int MU, bool FIRST>
+__device__ __forceinline__ void dhop_pair(cpx<typename SpinorFmt<PREC>::real> acc[2][12], const char* in,
+                                          size_t stride, int h, int nbf, const char* slabf, int lif, bool negf,
+                                          int nbb, const char* slabb, int lib, bool negb) {
   typedef typename SpinorFmt<PREC>::real R;
-  typedef typename LinkStore<PREC>::type St;
   constexpr int BYTES = NREAL * LinkStore<PREC>::size;
-  RawWords<BYTES> raw = load_raw<BYTES>(slab, h, link_index);
-  cpx<R> p0[12], p1[12];
-  SpinorFmt<PREC>::load(in, h, nbi, p0);
-  SpinorFmt<PREC>::load(in + stride, h, nbi, p1);
-  Mat3<R> U;
-  LinkRecon<R, St, NREAL>::unpack(raw, U);
+  const RawWords<BYTES> rf = load_raw<BYTES>(slabf, h, lif);
+  const RawWords<BYTES> rb = load_raw<BYTES>(slabb, h, lib);
 #pragma unroll
   for (int f = 0; f < 2; ++f) {
-    cpx<R> h0[3], h1[3];
-    project<R, MU, S>(f == 0 ? p0 : p1, h0, h1);
-    if (MU == 0 && negate) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        h0[c] = R(-1) * h0[c];
-        h1[c] = R(-1) * h1[c];
-      }
-    }
+    cpx<R> p[12];
+    R scale;
+    SpinorFmt<PREC>::load_unscaled(in + f * stride, h, nbf, p, scale);
     cpx<R> u0[3], u1[3];
-    if (S > 0)
-      su3_mul2(U, h0, h1, u0, u1);
-    else
-      su3_adj_mul2(U, h0, h1, u0, u1);
-    accumulate<R, MU, S>(acc[f], u0, u1);
+    pair_fwd<PREC, NREAL, MU>(u0, u1, rf, p, scale, negf);
+    SpinorFmt<PREC>::load_unscaled(in + f * stride, h, nbb, p, scale);
+    pair_bwd<PREC, NREAL, MU, FIRST>(acc[f], u0, u1, rb, p, scale, negb);
   }
 }
 
@@ -74,14 +63,10 @@ __global__ void __launch_bounds__(HOP_NT) dhop_kernel(const Geom g, const int ou
     const char* lf = links + (size_t)(out_parity * 4) * slab;
     const char* lo = links + (size_t)((1 - out_parity) * 4) * slab;
     const bool tfwd = (c.t == g.T - 1), tbwd = (c.t == 0);
-    dhop_dir<PREC, NREAL, 0, +1>(acc, in, stride, g.h, nb[0], lf + 0 * slab, cb, tfwd);
-    dhop_dir<PREC, NREAL, 0, -1>(acc, in, stride, g.h, nb[4], lo + 0 * slab, nb[4], tbwd);
-    dhop_dir<PREC, NREAL, 1, +1>(acc, in, stride, g.h, nb[1], lf + 1 * slab, cb, false);
-    dhop_dir<PREC, NREAL, 1, -1>(acc, in, stride, g.h, nb[5], lo + 1 * slab, nb[5], false);
-    dhop_dir<PREC, NREAL, 2, +1>(acc, in, stride, g.h, nb[2], lf + 2 * slab, cb, false);
-    dhop_dir<PREC, NREAL, 2, -1>(acc, in, stride, g.h, nb[6], lo + 2 * slab, nb[6], false);
-    dhop_dir<PREC, NREAL, 3, +1>(acc, in, stride, g.h, nb[3], lf + 3 * slab, cb, false);
-    dhop_dir<PREC, NREAL, 3, -1>(acc, in, stride, g.h, nb[7], lo + 3 * slab, nb[7], false);
+    dhop_pair<PREC, NREAL, 0, true>(acc, in, stride, g.h, nb[0], lf + 0 * slab, cb, tfwd, nb[4], lo + 0 * slab, nb[4], tbwd);
+    dhop_pair<PREC, NREAL, 1, false>(acc, in, stride, g.h, nb[1], lf + 1 * slab, cb, false, nb[5], lo + 1 * slab, nb[5], false);
+    dhop_pair<PREC, NREAL, 2, false>(acc, in, stride, g.h, nb[2], lf + 2 * slab, cb, false, nb[6], lo + 2 * slab, nb[6], false);
+    dhop_pair<PREC, NREAL, 3, false>(acc, in, stride, g.h, nb[3], lf + 3 * slab, cb, false, nb[7], lo + 3 * slab, nb[7], false);
     // epilogue, chirality by chirality
     cpx<R> o[2][12];
     if (HAS_Y) {
@@ -175,14 +160,11 @@ __global__ void __launch_bounds__(HOP_NT) dhop2_kernel(const Geom g, const int o
     const char* lf = links + (size_t)(out_parity * 4) * slab;
     const char* lo = links + (size_t)((1 - out_parity) * 4) * slab;
     const bool tfwd = (c.t == g.T - 1), tbwd = (c.t == 0);
-    hop_dir<PREC, NREAL, 0, +1>(acc, inf, g.h, nb[0], lf + 0 * slab, cb, tfwd);
-    hop_dir<PREC, NREAL, 0, -1>(acc, inf, g.h, nb[4], lo + 0 * slab, nb[4], tbwd);
-    hop_dir<PREC, NREAL, 1, +1>(acc, inf, g.h, nb[1], lf + 1 * slab, cb, false);
-    hop_dir<PREC, NREAL, 1, -1>(acc, inf, g.h, nb[5], lo + 1 * slab, nb[5], false);
-    hop_dir<PREC, NREAL, 2, +1>(acc, inf, g.h, nb[2], lf + 2 * slab, cb, false);
-    hop_dir<PREC, NREAL, 2, -1>(acc, inf, g.h, nb[6], lo + 2 * slab, nb[6], false);
-    hop_dir<PREC, NREAL, 3, +1>(acc, inf, g.h, nb[3], lf + 3 * slab, cb, false);
-    hop_dir<PREC, NREAL, 3, -1>(acc, inf, g.h, nb[7], lo + 3 * slab, nb[7], false);
+    // the one-flavour direction-pair arithmetic (tm_dslash.cuh) on this lane's flavour
+    hop_pair<PREC, NREAL, 0, true>(acc, inf, g.h, nb[0], lf + 0 * slab, cb, tfwd, nb[4], lo + 0 * slab, nb[4], tbwd);
+    hop_pair<PREC, NREAL, 1, false>(acc, inf, g.h, nb[1], lf + 1 * slab, cb, false, nb[5], lo + 1 * slab, nb[5], false);
+    hop_pair<PREC, NREAL, 2, false>(acc, inf, g.h, nb[2], lf + 2 * slab, cb, false, nb[6], lo + 2 * slab, nb[6], false);
+    hop_pair<PREC, NREAL, 3, false>(acc, inf, g.h, nb[3], lf + 3 * slab, cb, false, nb[7], lo + 3 * slab, nb[7], false);
   }
   // epilogue, component by component: the partner lane's sum (and site-local input) of the same
   // component comes through a shuffle (every lane takes part), the result overwrites acc[k].
