@@ -635,7 +635,7 @@ tm_status prepare_source(const Solver& S, const double* b, void* be, void* bo, v
 // x_o = Qhat^{-f} X, x_e = (M_ee^f)^-1 (b_e + kappa H_eo x_o) (eq. eo6, App. B.2), written to
 // the canonical field x; then ||b - M x|| / ||b|| in FP64 (R, Pv, T, W are FP64 scratch).
 tm_status reconstruct_check(const Solver& S, const void* X, const void* be, const void* bo, double bfull, double* x,
-                            void* T, void* W, void* R, void* Pv, double* true_rel) {
+                            void* T, void* W, void* R, void* Pv, double* true_rel, double* rr_odd) {
   tm_lattice lat = S.lat;
   tm_status st;
   HopArgs a{};
@@ -653,7 +653,7 @@ tm_status reconstruct_check(const Solver& S, const void* X, const void* be, cons
   a.out = W;  // x_o
   a.coef = epi_schur_q(lat->kappa, S.mut, -S.f);
   if ((st = hop_launch(lat, a, S.s)) != TM_OK) return st;
-  return reconstruct_xo(S, W, be, bo, bfull, x, T, R, Pv, true_rel);
+  return reconstruct_xo(S, W, be, bo, bfull, x, T, R, Pv, true_rel, rr_odd);
 }
 
 // x_e = (M_ee^f)^-1 (b_e + kappa H_eo x_o) from the odd solution xo, written with xo to the
@@ -662,7 +662,7 @@ tm_status reconstruct_check(const Solver& S, const void* X, const void* be, cons
 // ||b_e + kappa H_eo x_o - M_ee x_e||^2 from the same hopping sum; the second forms
 // (b - M x)_o = b_o - (M_oo x_o - kappa H_oe x_e) and its norm.  R is unused.
 tm_status reconstruct_xo(const Solver& S, const void* xo, const void* be, const void* bo, double bfull, double* x,
-                         void* T, void* R, void* Pv, double* true_rel) {
+                         void* T, void* R, void* Pv, double* true_rel, double* rr_odd) {
   (void)R;
   tm_lattice lat = S.lat;
   cudaStream_t s = S.s;
@@ -700,6 +700,7 @@ tm_status reconstruct_xo(const Solver& S, const void* xo, const void* be, const 
   if ((st = cuda_check(cudaStreamSynchronize(s), "synchronise")) != TM_OK) return st;
   const double rre = rr[0], rro = rr[1];
   *true_rel = bfull > 0.0 ? std::sqrt((rre + rro) / bfull) : 0.0;
+  if (rr_odd) *rr_odd = rro;
   if ((st = unpack_full_parity(lat, TM_F64, x, T, 0, 0, s)) != TM_OK) return st;
   return unpack_full_parity(lat, TM_F64, x, W, 1, 0, s);
 }
@@ -716,7 +717,7 @@ tm_status launch_accumulate(const Solver& S, void* X, void* xs) {
 // half fields (R, Pv, T, W work space); bb = ||bp||^2.  The result is converged when the
 // recomputed FP64 residual satisfies ||bp - A X||^2 < tol^2 bb.
 tm_status cg_normal(const Solver& S, const tm_cg_params& P, const void* bp, double bb, void* X, bool guess, void* R,
-                    void* Pv, void* T, void* W, NormalResult* res) {
+                    void* Pv, void* T, void* W, NormalResult* res, bool defer_final) {
   tm_lattice lat = S.lat;
   cudaStream_t s = S.s;
   tm_status st = TM_OK;
@@ -858,6 +859,16 @@ tm_status cg_normal(const Solver& S, const tm_cg_params& P, const void* bp, doub
         accumulate_kernel<TM_F32><<<nbb, BNT, 0, s>>>(lat->geom.h, static_cast<char*>(X), static_cast<char*>(xs));
         count_launch();
         w_valid = false;
+        if (defer_final && fin.converged && !dd_updates) {  // the caller confirms X in FP64
+          if ((st = cuda_check(cudaGetLastError(), "accumulate kernel")) != TM_OK) return st;
+          res->iters = iters;
+          res->updates = updates;
+          res->converged = false;
+          res->rr_true = fin.rr;
+          res->xo_in_W = false;
+          res->pending = true;
+          return TM_OK;
+        }
       }
       if ((st = cuda_check(cudaGetLastError(), "accumulate kernel")) != TM_OK) return st;
       const void* rsrc = R;
@@ -902,6 +913,7 @@ tm_status cg_normal(const Solver& S, const tm_cg_params& P, const void* bp, doub
   res->converged = converged;
   res->rr_true = rr_true;
   res->xo_in_W = w_valid;
+  res->pending = false;
   return TM_OK;
 }
 
@@ -933,18 +945,52 @@ static tm_status solve_one(tm_lattice lat, double* x, const double* b, const tm_
     info->status = TM_OK;
     return st;
   }
+  // Mixed modes defer the last confirmation: when a sloppy stage reaches the tolerance, X is
+  // confirmed by the reconstruction's FP64 residual of the full system, whose odd part
+  // ||(b - M x)_o|| = ||varphi_o - Mhat x_o|| = ||b' - A X|| up to the rounding of x_e (the even
+  // part vanishes but for that rounding).  That costs 4 FP64 hopping launches (x_o = Qhat^{-f} X,
+  // x_e, the odd residual) where recomputing b' - A X first would cost 6.  If the FP64 residual
+  // misses the tolerance the iteration continues from X (cg_normal recomputes b' - A X).
+  const bool defer = P.mode != TM_CG_FP64 && P.update_prec == TM_F64;
+  const double stop2 = P.tol * P.tol * bb;
   NormalResult nr{};
-  if ((st = cg_normal(S, P, bp, bb, X, false, R, Pv, T, W, &nr)) != TM_OK) return st;
-  const int iters = nr.iters, updates = nr.updates;
-  const bool converged = nr.converged;
-  const double rr_true = nr.rr_true;
+  if ((st = cg_normal(S, P, bp, bb, X, false, R, Pv, T, W, &nr, defer)) != TM_OK) return st;
+  int iters = nr.iters, updates = nr.updates;
+  bool converged = nr.converged;
+  double rr_true = nr.rr_true;
+  bool reconstructed = false;
+  while (nr.pending) {
+    double rro = 0.0;
+    if ((st = reconstruct_check(S, X, be, bo, bfull, x, T, W, R, Pv, &info->true_rel_residual, &rro)) != TM_OK)
+      return st;
+    ++updates;  // an FP64 residual recomputation
+    rr_true = rro;
+    if (verbose())
+      fprintf(stderr, "[tm_solve_cg] confirmation: FP64 |(b - M x)_o|/|b'| %.3e (%s)\n", std::sqrt(rro / bb),
+              rro < stop2 ? "converged" : "not confirmed, continuing");
+    if (rro < stop2) {
+      converged = true;
+      reconstructed = true;
+      break;
+    }
+    if (iters >= P.max_iter) break;
+    tm_cg_params Q = P;
+    Q.max_iter = P.max_iter - iters;
+    if ((st = cg_normal(S, Q, bp, bb, X, true, R, Pv, T, W, &nr, defer)) != TM_OK) return st;
+    iters += nr.iters;
+    updates += nr.updates;
+    converged = nr.converged;
+    rr_true = nr.rr_true;
+  }
   info->iters = iters;
   info->reliable_updates = updates;
   info->schur_rel_residual = std::sqrt(rr_true / bb);
 
   // ---- reconstruction and the FP64 residual of the full system (x_o = Qhat^{-f} X is already in W
   // when the last operation was the FP64 residual of the final X)
-  if (nr.xo_in_W)
+  if (reconstructed)
+    st = TM_OK;
+  else if (nr.xo_in_W)
     st = reconstruct_xo(S, W, be, bo, bfull, x, T, R, Pv, &info->true_rel_residual);
   else
     st = reconstruct_check(S, X, be, bo, bfull, x, T, W, R, Pv, &info->true_rel_residual);

@@ -29,20 +29,25 @@ tm_status true_residual(const Solver& S, void* r, const void* X, const void* bp,
 CGState fresh_state(double rr, double stop2, int max_iter, int iter0, double delta2, double growth = 0.0);
 tm_status prepare_source(const Solver& S, const double* b, void* be, void* bo, void* bp, void* T, double* bb,
                          double* bfull);
+// rr_odd (optional): ||(b - M x)_o||^2, the odd part of the full residual
 tm_status reconstruct_check(const Solver& S, const void* X, const void* be, const void* bo, double bfull, double* x,
-                            void* T, void* W, void* R, void* Pv, double* true_rel);
+                            void* T, void* W, void* R, void* Pv, double* true_rel, double* rr_odd = nullptr);
 tm_status reconstruct_xo(const Solver& S, const void* xo, const void* be, const void* bo, double bfull, double* x,
-                         void* T, void* R, void* Pv, double* true_rel);
+                         void* T, void* R, void* Pv, double* true_rel, double* rr_odd = nullptr);
 tm_status launch_accumulate(const Solver& S, void* X, void* xs);  // X (FP64) += xs (FP32); xs = 0
 
 struct NormalResult {
   int iters, updates;
   bool converged;
-  double rr_true;   // ||bp - A X||^2, recomputed in FP64
+  double rr_true;   // ||bp - A X||^2, recomputed in FP64 (the iterated one when `pending`)
   bool xo_in_W;     // W holds Qhat^{-f} X for the final X (left by the last FP64 residual)
+  bool pending;     // the last sloppy stage reached the tolerance; X is not yet confirmed in FP64
 };
+// With defer_final (mixed modes, FP64 updates), a sloppy stage that reaches the tolerance ends
+// the call with `pending` instead of an FP64 recomputation of bp - A X: the caller confirms X
+// through the FP64 residual of the full system, whose odd part is the same quantity.
 tm_status cg_normal(const Solver& S, const tm_cg_params& P, const void* bp, double bb, void* X, bool guess, void* R,
-                    void* Pv, void* T, void* W, NormalResult* res);
+                    void* Pv, void* T, void* W, NormalResult* res, bool defer_final = false);
 
 bool use_graphs();  // CUDA-graph stage loops (TM_NO_GRAPH=1 selects host-driven chunks)
 int cg_unroll();    // iterations per body of a graph loop (TM_CG_UNROLL)

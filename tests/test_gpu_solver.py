@@ -304,3 +304,40 @@ def test_multiple_rhs_reliable_mode_goes_through_the_batched_solver():
     lat.solve_cg(xh, phis, nrhs=3, flavour=-1, **kw)
     assert np.array_equal(xh, xs)
     lat.close()
+
+
+_SUBPROCESS_DRIFT = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, {root!r})
+from paper_0905_3331_gb300 import Lattice, inputs, CG_RELIABLE, F16, LINK8
+w = inputs.WORKLOADS["8^4"]
+lat = Lattice(w.T, w.L, w.kappa, w.mu)
+lat.set_gauge(w.gauge())
+b = torch.from_numpy(w.source()).cuda()
+x = torch.zeros_like(b)
+info = lat.solve_cg(x, b, mode=CG_RELIABLE, sloppy_prec=F16, sloppy_link=LINK8, delta=1e-12)
+np.save({out!r}, x.cpu().numpy())
+print("RES", info.true_rel_residual, info.schur_rel_residual, info.reliable_updates)
+"""
+
+
+def test_deferred_confirmation_falls_back(tmp_path):
+    """In the mixed modes the last sloppy stage's convergence is confirmed by the FP64 residual of
+    the full system.  With FP16 storage, 8-real links and no intermediate reliable update
+    (delta 1e-12) the iterated residual drifts away from the true one, the confirmation fails,
+    and the solve continues from X until the FP64 residual meets the bar (checked by the oracle)."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = str(tmp_path / "x.npy")
+    code = _SUBPROCESS_DRIFT.format(root=root, out=out)
+    r = subprocess.run([sys.executable, "-c", code], env={**os.environ, "TM_VERBOSE": "1"}, capture_output=True,
+                       text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    assert "not confirmed, continuing" in r.stderr
+    assert "confirmation" in r.stderr and "(converged)" in r.stderr
+    tr, sr, upd = r.stdout.split("RES")[1].split()
+    assert float(tr) < 1e-10 and float(sr) < 1e-10 and int(upd) >= 2
+    w = inputs.WORKLOADS["8^4"]
+    assert oracle_true_residual(w, w.gauge(), w.source(), np.load(out)) < 1e-10
