@@ -193,7 +193,9 @@ typedef struct {
   int iters;                 /* CG iterations performed (all precisions) */
   int reliable_updates;      /* FP64 residual recomputations inside the loop */
   double true_rel_residual;  /* ||b - M x|| / ||b|| on the full lattice, FP64, recomputed */
-  double schur_rel_residual; /* ||b_o - A X|| / ||b_o|| of the normal equations, FP64 */
+  double schur_rel_residual; /* ||b_o - A X|| / ||b_o|| of the normal equations, FP64 (mixed
+                                modes: the odd part of the FP64 full-system residual, which
+                                equals it up to the rounding of x_e) */
   double seconds;            /* wall time of the call */
   int status;                /* tm_status of the solve */
 } tm_cg_info;
