@@ -48,6 +48,14 @@ def hop_bytes_per_site(prec: int, nreal: int) -> int:
     return 2 * spinor + 8 * nreal * elem
 
 
+def hop_naive_bytes_per_site(prec: int, nreal: int) -> int:
+    """Bytes per output site without any neighbour reuse: eight neighbour spinors and eight links
+    read, one spinor written (the naive count, printed beside the algorithmic one)."""
+    spinor = {0: 192, 1: 96, 2: 52, 3: 192}[prec]
+    elem = {0: 8, 1: 4, 2: 2, 3: 8}[prec]
+    return 9 * spinor + 8 * nreal * elem
+
+
 def parse_sloppy(s: str):
     p, l = s.split(":")
     return {"f32": 1, "f16": 2}[p], int(l)
@@ -279,6 +287,7 @@ def run_gpu(args):
         dslash[name] = {"bytes_per_site": hop_bytes_per_site(prec, nreal),
                         "threads_per_site": lat.hop_threads(prec, nreal),
                         "us_cold": tc * 1e6, "gbs_cold": by / tc / 1e9,
+                        "gbs_naive_count_cold": hop_naive_bytes_per_site(prec, nreal) * h / tc / 1e9,
                         "frac_hbm_cold": by / tc / 1e9 / peak,
                         "gflops_cold": HOP_FLOPS * h / tc / 1e9,
                         "us_l2_resident": tw * 1e6, "gbs_l2_resident": by / tw / 1e9,
@@ -333,6 +342,7 @@ def run_gpu(args):
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(w, U, phi, infos64[-1].iters, args.cpu_seconds)
+        result["cpu_oracle_operator"] = cpu_oracle_operator(w, U, phi, dslash["f64_18"]["us_cold"])
     lat.close()
     if world > 1:
         import torch.distributed as dist
@@ -668,6 +678,28 @@ def cpu_baseline(w, U, phi, iters, seconds):
             "sample": f"oracle FP64 CG on {w.name}: {n} iterations timed ({t_it * 1e3:.1f} ms "
                       f"each), extrapolated to the {iters} iterations of the GPU FP64 CG, plus "
                       "one source preparation and reconstruction"}
+
+
+def cpu_oracle_operator(w, U, phi, gpu_us, seconds: float = 2.0):
+    """The oracle's H_oe (FP64, full 4x4 (1 +- gamma) matrices, OpenMP site loop) timed on the host
+    for about `seconds`, beside the FP64 GPU hopping kernel on the same lattice."""
+    import oracle
+    olat = oracle.Lattice.cubic(w.T, w.L)
+    oracle.hopping(olat, U, phi, out_parity=1)
+    n, t0 = 0, time.perf_counter()
+    while True:
+        oracle.hopping(olat, U, phi, out_parity=1)
+        n += 1
+        dt = time.perf_counter() - t0
+        if dt >= seconds:
+            break
+    per = dt / n
+    h = w.V // 2
+    return {"kernel": "oracle hopping H_oe, FP64", "workload": w.name, "applications": n,
+            "ms_per_application": round(per * 1e3, 3), "cores": oracle.num_threads(),
+            "gbs_algorithmic": round(hop_bytes_per_site(0, 18) * h / per / 1e9, 2),
+            "gflops": round(HOP_FLOPS * h / per / 1e9, 2),
+            "gpu_fp64_kernel_speedup": round(per / (gpu_us * 1e-6), 1)}
 
 
 def run_reference(args):
