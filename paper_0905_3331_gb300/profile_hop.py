@@ -43,7 +43,7 @@ def main():
     ap.add_argument("--warm", action="store_true", help="do not flush L2 between launches")
     ap.add_argument("--tps", type=int, default=0, help="threads per site 1/2/4 (0: autotuned)")
     ap.add_argument("--doublet", default=None, help="MUBAR,EPSBAR: time doublet solves instead")
-    ap.add_argument("--delta", type=float, default=0.001, help="reliable-update delta of the doublet solve")
+    ap.add_argument("--delta", type=float, default=0.001, help="reliable-update delta of the doublet and batched solves")
     ap.add_argument("--contract", action="store_true", help="time meson contractions instead")
     ap.add_argument("--batch", type=int, default=0, help="time batched solves of this many sources")
     args = ap.parse_args()
@@ -112,7 +112,7 @@ def batch(args):
     for k in range(args.batch):
         b = torch.from_numpy(w.source(k)).to(dev)
         systems.append((lat, w.mu, torch.zeros_like(b), b))
-    kw = dict(sloppy_prec=prec, sloppy_link=nreal, delta=1e-3)
+    kw = dict(sloppy_prec=prec, sloppy_link=nreal, delta=args.delta)
     infos = solve_cg_batch(systems, **kw)
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
