@@ -184,9 +184,13 @@ typedef struct {
   int use_x0;           /* nonzero: x holds the initial guess (full field) */
   int flavour;          /* +1 solves M(+mu) x = b, -1 solves M(-mu) x = b; 0 means +1 */
   int update_prec;      /* modes 1, 2: arithmetic of the residual recomputations inside the
-                           loop, TM_F64 or TM_DF64 (double-float; about 48 bits, on the FP32
-                           units).  Convergence is always confirmed by an FP64 recomputation;
-                           if that fails the solve continues with FP64 recomputations. */
+                           loop: TM_F64; TM_DF64 (double-float; about 48 bits, on the FP32
+                           units); or TM_F32 (for FP16 storage): each update at delta computes
+                           r = r64 - A dx with the FP32 operator, r64 the last FP64 residual and
+                           dx the FP32 increment since then, and the FP64 recomputation follows
+                           once ||r|| has fallen by 1e-2 since the last one.  Convergence is
+                           always confirmed in FP64; if that fails the solve continues with FP64
+                           recomputations. */
 } tm_cg_params;
 
 typedef struct {

@@ -108,8 +108,8 @@ extern "C" tm_status tm_solve_normal(tm_lattice lat, void* X, const void* phi, c
     if (P.sloppy_link != 18 && P.sloppy_link != 12 && P.sloppy_link != 8)
       return set_error(TM_ERR_ARG, "tm_solve_normal: sloppy link format %d", P.sloppy_link);
     if (!(P.delta > 0.0 && P.delta < 1.0)) return set_error(TM_ERR_ARG, "tm_solve_normal: delta must be in (0, 1)");
-    if (P.update_prec != TM_F64 && P.update_prec != TM_DF64)
-      return set_error(TM_ERR_ARG, "tm_solve_normal: update_prec must be TM_F64 or TM_DF64");
+    if (P.update_prec != TM_F64 && P.update_prec != TM_DF64 && P.update_prec != TM_F32)
+      return set_error(TM_ERR_ARG, "tm_solve_normal: update_prec must be TM_F64, TM_F32 or TM_DF64");
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const Solver S = make_solver(lat, P.flavour, s);

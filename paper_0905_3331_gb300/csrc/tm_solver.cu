@@ -830,6 +830,21 @@ tm_status cg_normal(const Solver& S, const tm_cg_params& P, const void* bp, doub
     const double delta2 = P.delta * P.delta;
     int bad_stages = 0;
     bool dd_updates = P.update_prec == TM_DF64;
+    // FP32 recomputations (update_prec TM_F32): r = r64 - A xs with the FP32 operator, r64 the
+    // last FP64 residual and xs the FP32 increment since then; the FP64 recomputation (X += xs)
+    // comes once ||r|| has fallen by F32_UPDATE_SPAN since the last one.  The FP32 result is off
+    // by about u32 kappa(A) ||r64|| (1e-4 ||r64|| on 48^3 x 96), well inside that span.
+    constexpr double F32_UPDATE_SPAN = 1e-2;
+    const bool f32_updates = P.update_prec == TM_F32;
+    void *rb32 = nullptr, *T32 = nullptr, *W32 = nullptr;
+    double rr64 = rr;
+    if (f32_updates) {
+      rb32 = workspace(lat, 13, S.hb[TM_F32], &st);
+      if (st == TM_OK) T32 = workspace(lat, 14, S.hb[TM_F32], &st);
+      if (st == TM_OK) W32 = workspace(lat, 15, S.hb[TM_F32], &st);
+      if (st == TM_OK) st = cuda_check(cudaMemcpyAsync(rb32, rs, S.hb[TM_F32], cudaMemcpyDeviceToDevice, s), "copy");
+      if (st != TM_OK) return st;
+    }
     void *bpd = nullptr, *Rd = nullptr, *Xd = nullptr, *Td = nullptr, *Wd = nullptr;
     if (dd_updates) {
       bpd = workspace(lat, 13, S.hb[TM_DF64], &st);
@@ -855,6 +870,24 @@ tm_status cg_normal(const Solver& S, const tm_cg_params& P, const void* bp, doub
         bad_stages = 0;
         if (fin.iter == iters) break;  // no progress (breakdown of <p, A p>): stop, report not converged
         iters = fin.iter;
+        if (f32_updates && !fin.converged && !fin.diverged && fin.rr > F32_UPDATE_SPAN * F32_UPDATE_SPAN * rr64) {
+          // FP32 recomputation relative to the last FP64 residual; xs keeps accumulating
+          if ((st = cuda_check(cudaMemcpyAsync(rs, rb32, S.hb[TM_F32], cudaMemcpyDeviceToDevice, s), "copy")) != TM_OK)
+            return st;
+          if ((st = normal_apply(S, TM_F32, sl, xs, T32, W32, rs, nullptr)) != TM_OK) return st;
+          double rr32 = 0.0;
+          if ((st = cuda_check(cudaMemcpyAsync(&lat->flag_host[0], lat->dscalars, sizeof(double),
+                                               cudaMemcpyDeviceToHost, s), "readback")) != TM_OK)
+            return st;
+          if ((st = cuda_check(cudaStreamSynchronize(s), "synchronise")) != TM_OK) return st;
+          memcpy(&rr32, &lat->flag_host[0], sizeof(double));
+          ++updates;
+          if (verbose())
+            fprintf(stderr, "[tm_solve_cg] FP32 update %d: |r|/|b| %.3e\n", updates, std::sqrt(rr32 / bb));
+          if (!(rr32 < 1e300)) return set_error(TM_ERR_NONFINITE, "tm_solve_cg: residual diverged");
+          rr = rr32;
+          continue;
+        }
         const unsigned nbb = blas_blocks(lat->geom.h);
         accumulate_kernel<TM_F32><<<nbb, BNT, 0, s>>>(lat->geom.h, static_cast<char*>(X), static_cast<char*>(xs));
         count_launch();
@@ -906,6 +939,10 @@ tm_status cg_normal(const Solver& S, const tm_cg_params& P, const void* bp, doub
       // after a divergent stage the search direction restarts from the true residual
       if (fin.diverged && (st = convert_half(lat, sp, ps, rprec, rsrc, s)) != TM_OK) return st;
       rr = rr_true;
+      rr64 = rr_true;
+      if (f32_updates &&
+          (st = cuda_check(cudaMemcpyAsync(rb32, rs, S.hb[TM_F32], cudaMemcpyDeviceToDevice, s), "copy")) != TM_OK)
+        return st;
     }
   }
   res->iters = iters;
@@ -951,7 +988,7 @@ static tm_status solve_one(tm_lattice lat, double* x, const double* b, const tm_
   // part vanishes but for that rounding).  That costs 4 FP64 hopping launches (x_o = Qhat^{-f} X,
   // x_e, the odd residual) where recomputing b' - A X first would cost 6.  If the FP64 residual
   // misses the tolerance the iteration continues from X (cg_normal recomputes b' - A X).
-  const bool defer = P.mode != TM_CG_FP64 && P.update_prec == TM_F64;
+  const bool defer = P.mode != TM_CG_FP64 && P.update_prec != TM_DF64;
   const double stop2 = P.tol * P.tol * bb;
   NormalResult nr{};
   if ((st = cg_normal(S, P, bp, bb, X, false, R, Pv, T, W, &nr, defer)) != TM_OK) return st;
@@ -1053,8 +1090,8 @@ tm_status solve_driver(tm_lattice lat, double* x, const double* b, int nrhs, con
     if (P.sloppy_link != 18 && P.sloppy_link != 12 && P.sloppy_link != 8)
       return set_error(TM_ERR_ARG, "%s: sloppy link format %d", nm, P.sloppy_link);
     if (!(P.delta > 0.0 && P.delta < 1.0)) return set_error(TM_ERR_ARG, "%s: delta must be in (0, 1)", nm);
-    if (P.update_prec != TM_F64 && P.update_prec != TM_DF64)
-      return set_error(TM_ERR_ARG, "%s: update_prec must be TM_F64 or TM_DF64", nm);
+    if (P.update_prec != TM_F64 && P.update_prec != TM_DF64 && P.update_prec != TM_F32)
+      return set_error(TM_ERR_ARG, "%s: update_prec must be TM_F64, TM_F32 or TM_DF64", nm);
   }
   if (kind != SOLVER_CG && (P.mode == TM_CG_SQRT_EPS || (P.mode == TM_CG_RELIABLE && P.update_prec != TM_F64)))
     return set_error(TM_ERR_UNSUPPORTED, "%s: modes TM_CG_FP64 and TM_CG_RELIABLE with FP64 updates only", nm);

@@ -149,7 +149,7 @@ def test_edge_cases():
     # bad parameters
     for kw in (dict(tol=0.0), dict(mode=7), dict(mode=CG_RELIABLE, delta=1.5),
                dict(flavour=3), dict(mode=CG_RELIABLE, sloppy_prec=0),
-               dict(mode=CG_RELIABLE, update_prec=F32)):
+               dict(mode=CG_RELIABLE, update_prec=F16)):
         with pytest.raises(TMError) as e:
             lat.solve_cg(x, b, **kw)
         assert e.value.status_name == "TM_ERR_ARG"
@@ -242,12 +242,14 @@ def test_solve_with_each_threads_per_site(tps):
     lat.close()
 
 
-@pytest.mark.parametrize("name,sloppy,link,delta", [
-    ("32^3x64", F32, LINK12, 1e-3),    # precision form: FP32 storage, 12-real links
-    ("32^3x64", F16, LINK12, 0.1),     # precision form: FP16 + norm storage, 12-real links
-    ("48^3x96", F16, LINK8, 0.3),      # large volume: FP16 storage, 8-real links (half)
+@pytest.mark.parametrize("name,sloppy,link,delta,upd", [
+    ("32^3x64", F32, LINK12, 1e-3, F64),    # precision form: FP32 storage, 12-real links
+    ("32^3x64", F16, LINK12, 0.1, F64),     # precision form: FP16 + norm storage, 12-real links
+    ("32^3x64", F16, LINK12, 0.1, F32),     # the same with FP32 recomputations between FP64 ones
+    ("48^3x96", F16, LINK8, 0.3, F64),      # large volume: FP16 storage, 8-real links (half)
+    ("48^3x96", F16, LINK8, 0.3, F32),
 ])
-def test_full_size_precision_forms(name, sloppy, link, delta):
+def test_full_size_precision_forms(name, sloppy, link, delta, upd):
     """The 32^3 x 64 and 48^3 x 96 workloads solved to an FP64 true residual of 1e-10 with the
     reliable-update CG; the oracle recomputes the residual of the GPU solution on the host."""
     w = inputs.WORKLOADS[name]
@@ -257,7 +259,7 @@ def test_full_size_precision_forms(name, sloppy, link, delta):
     b = torch.from_numpy(phi).to(dev())
     x = torch.zeros_like(b)
     info = lat.solve_cg(x, b, mode=CG_RELIABLE, sloppy_prec=sloppy, sloppy_link=link, delta=delta,
-                        max_iter=20000)
+                        max_iter=20000, update_prec=upd)
     res = oracle_true_residual(w, U, phi, x.cpu().numpy())
     assert res < 1e-10 and info.true_rel_residual < 1e-10
     assert abs(res - info.true_rel_residual) < 1e-3 * res
@@ -341,3 +343,55 @@ def test_deferred_confirmation_falls_back(tmp_path):
     assert float(tr) < 1e-10 and float(sr) < 1e-10 and int(upd) >= 2
     w = inputs.WORKLOADS["8^4"]
     assert oracle_true_residual(w, w.gauge(), w.source(), np.load(out)) < 1e-10
+
+
+_SUBPROCESS_F32_UPDATES = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, {root!r})
+from paper_0905_3331_gb300 import Lattice, inputs, CG_RELIABLE, F16, F32, LINK8, LINK12
+w = inputs.WORKLOADS["12^3x24"]
+lat = Lattice(w.T, w.L, w.kappa, w.mu)
+lat.set_gauge(w.gauge())
+b = torch.from_numpy(w.source()).cuda()
+for k, link in enumerate((LINK12, LINK8)):
+    x = torch.zeros_like(b)
+    info = lat.solve_cg(x, b, mode=CG_RELIABLE, sloppy_prec=F16, sloppy_link=link, delta=0.1, update_prec=F32)
+    np.save({out!r} + str(k) + ".npy", x.cpu().numpy())
+    print("RES", info.true_rel_residual, info.reliable_updates)
+"""
+
+
+def test_fp32_recomputations_between_fp64_ones(tmp_path):
+    """update_prec TM_F32 with FP16 storage: the reliable updates at delta are FP32 recomputations
+    r = r64 - A dx relative to the last FP64 residual (traced), FP64 ones follow every factor
+    1e-2, and the solutions meet the oracle-checked bar for 12- and 8-real links."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = str(tmp_path / "x")
+    code = _SUBPROCESS_F32_UPDATES.format(root=root, out=out)
+    r = subprocess.run([sys.executable, "-c", code], env={**os.environ, "TM_VERBOSE": "1"}, capture_output=True,
+                       text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    assert "FP32 update" in r.stderr and "reliable update" in r.stderr
+    w = inputs.WORKLOADS["12^3x24"]
+    U, phi = w.gauge(), w.source()
+    for k in range(2):
+        assert oracle_true_residual(w, U, phi, np.load(out + str(k) + ".npy")) < 1e-10
+    for line in r.stdout.split("RES")[1:]:
+        assert float(line.split()[0]) < 1e-10
+
+
+def test_update_prec_f32_in_every_mode():
+    """TM_F32 recomputations are accepted by the sqrt(eps) mode and by tm_solve_normal too, and the
+    results meet the bar."""
+    w = inputs.WORKLOADS["8^4"]
+    U, phi = w.gauge(), w.source()
+    lat = Lattice(w.T, w.L, w.kappa, w.mu)
+    lat.set_gauge(U)
+    b = torch.from_numpy(phi).to(dev())
+    x = torch.zeros_like(b)
+    lat.solve_cg(x, b, mode=CG_SQRT_EPS, sloppy_prec=F16, sloppy_link=LINK12, delta=0.1, update_prec=F32)
+    assert oracle_true_residual(w, U, phi, x.cpu().numpy()) < 1e-10
+    lat.close()
