@@ -464,7 +464,8 @@ def batched_measurement(args, dev):
 def precision_form_measurement(args, dev):
     """The 32^3 x 64 workload (eps 0.6, kappa 0.1615, mu 0.003): per-launch roofline of the
     FP32 and FP16 hopping kernels with 12-real links (L2 flushed and cleaned before each launch)
-    and one reliable-update mixed solve against one FP64 CG solve, both to 1e-10."""
+    and reliable-update mixed solves with FP32 and FP16 storage against one FP64 CG solve, all
+    to 1e-10."""
     import numpy as np
     import torch
 
@@ -502,15 +503,20 @@ def precision_form_measurement(args, dev):
                      "bytes_per_site": hop_bytes_per_site(prec, LINK12)}
     b = torch.from_numpy(phi).to(dev)
     x = torch.zeros_like(b)
+    # FP16 storage: delta 0.3 with FP32 recomputations between the FP64 ones (update_prec F32)
     for name, kw in (("mixed_f32_12", dict(mode=CG_RELIABLE, sloppy_prec=F32, sloppy_link=LINK12,
                                            delta=args.batched_delta)),
+                     ("mixed_f16_12", dict(mode=CG_RELIABLE, sloppy_prec=F16, sloppy_link=LINK12,
+                                           delta=0.3, update_prec=F32)),
                      ("fp64", dict(mode=CG_FP64))):
-        if name == "mixed_f32_12":
+        if name != "fp64":
             lat.solve_cg(x, b, tol=1e-10, **kw)  # warm-up (sloppy gauge copy, tuning, graphs)
         t, infos = _timed(lambda: lat.solve_cg(x, b, tol=1e-10, **kw), 1, dev)
         out[name] = {"s_per_solve": round(t, 4), "iters": infos[-1].iters,
+                     "reliable_updates": infos[-1].reliable_updates,
                      "true_rel_residual": infos[-1].true_rel_residual}
     out["speedup_mixed_vs_fp64"] = round(out["fp64"]["s_per_solve"] / out["mixed_f32_12"]["s_per_solve"], 2)
+    out["speedup_mixed_f16_vs_fp64"] = round(out["fp64"]["s_per_solve"] / out["mixed_f16_12"]["s_per_solve"], 2)
     out["timing"] = ("hopping: 10 launches, CUDA events, mean of the middle 80%, L2 flushed and cleaned "
                      "before each; solves: CUDA events")
     lat.close()
