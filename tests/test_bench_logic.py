@@ -62,3 +62,16 @@ def test_trimmed_mean_drops_stray_launches():
     ts = [14.3e-6] * 18 + [148e-6, 14.1e-6]
     assert abs(bench.trimmed_mean(ts) - 14.3e-6) < 1e-12
     assert bench.trimmed_mean([2.0, 4.0]) == 3.0
+
+
+def test_hopping_byte_counts():
+    """Algorithmic and naive bytes per output site of one half-lattice hopping application:
+    one input spinor, the 8 links and one output (algorithmic), eight neighbour spinors instead of
+    one (naive), for every storage form with 18/12/8-real links."""
+    import bench
+    F64, F32, F16 = 0, 1, 2
+    expect = {(F64, 18): (1536, 2880), (F64, 12): (1152, 2496), (F32, 18): (768, 1440),
+              (F32, 12): (576, 1248), (F16, 12): (296, 660), (F16, 8): (232, 596)}
+    for (prec, nreal), (alg, naive) in expect.items():
+        assert bench.hop_bytes_per_site(prec, nreal) == alg
+        assert bench.hop_naive_bytes_per_site(prec, nreal) == naive
