@@ -331,15 +331,18 @@ static bool dverbose() {
 }
 
 // CG on Qhat_h^2 y = bp (FP64 or reliable-update mixed precision); y starts at 0.
+// On return *xo_in_W says whether W holds Qhat_h Y of the final Y (left by the last FP64
+// residual, which forms it first): then it is x_o and the caller need not recompute it.
 static tm_status dcg(const DSolver& D, const tm_cg_params& P, const void* bp, double bb, void* Y, void* R, void* Pv,
-                     void* T, void* W, int* iters_out, int* updates_out, bool* conv_out, double* rr_out) {
+                     void* T, void* W, int* iters_out, int* updates_out, bool* conv_out, double* rr_out,
+                     bool* xo_in_W) {
   tm_lattice lat = D.S.lat;
   cudaStream_t s = D.S.s;
   const size_t hb64 = 2 * D.S.hb[TM_F64];
   tm_status st;
   const double stop2 = P.tol * P.tol * bb;
   int iters = 0, updates = 0, bad = 0;
-  bool converged = false;
+  bool converged = false, w_valid = false;
   double rr_true = bb;
   if ((st = cuda_check(cudaMemsetAsync(Y, 0, hb64, s), "memset")) != TM_OK) return st;
   if ((st = cuda_check(cudaMemcpyAsync(R, bp, hb64, cudaMemcpyDeviceToDevice, s), "copy")) != TM_OK) return st;
@@ -350,10 +353,12 @@ static tm_status dcg(const DSolver& D, const tm_cg_params& P, const void* bp, do
     while (!converged) {
       CGState fin;
       if ((st = run_dstage(D, v, fresh_state(rr, stop2, P.max_iter, iters, 0.0), &fin)) != TM_OK) return st;
+      w_valid = false;  // the stage updates Y in place
       if (fin.nonfinite) return set_error(TM_ERR_NONFINITE, "tm_solve_doublet: non-finite value in the iteration");
       const bool progress = fin.iter > iters;
       iters = fin.iter;
       if ((st = dtrue_residual(D, R, Y, bp, T, W, &rr_true)) != TM_OK) return st;
+      w_valid = true;
       ++updates;
       if (dverbose())
         fprintf(stderr, "[tm_solve_doublet] fp64 stage: iter %d true |r|/|b| %.3e\n", iters, std::sqrt(rr_true / bb));
@@ -394,8 +399,10 @@ static tm_status dcg(const DSolver& D, const tm_cg_params& P, const void* bp, do
         if (fin.iter == iters) break;
         iters = fin.iter;
         if ((st = daccumulate(D, Y, xs)) != TM_OK) return st;
+        w_valid = false;
       }
       if ((st = dtrue_residual(D, R, Y, bp, T, W, &rr_true)) != TM_OK) return st;
+      w_valid = true;
       ++updates;
       if (dverbose())
         fprintf(stderr, "[tm_solve_doublet] sloppy stage: iter %d true |r|/|b| %.3e diverged %d\n", iters,
@@ -414,6 +421,7 @@ static tm_status dcg(const DSolver& D, const tm_cg_params& P, const void* bp, do
   *updates_out = updates;
   *conv_out = converged;
   *rr_out = rr_true;
+  *xo_in_W = w_valid;
   return TM_OK;
 }
 
@@ -499,19 +507,23 @@ static tm_status dsolve_one(const DSolver& D, double* x, const double* b, const 
   double bb = 0.0;
   if ((st = norm2_n(D.S, TM_F64, 2 * lat->geom.h, bp, &bb)) != TM_OK) return st;
   int iters = 0, updates = 0;
-  bool converged = bb == 0.0;
+  bool converged = bb == 0.0, xo_in_W = false;
   double rr_true = 0.0;
   if (!converged) {
-    if ((st = dcg(D, P, bp, bb, Y, R, Pv, T, W, &iters, &updates, &converged, &rr_true)) != TM_OK) return st;
+    if ((st = dcg(D, P, bp, bb, Y, R, Pv, T, W, &iters, &updates, &converged, &rr_true, &xo_in_W)) != TM_OK)
+      return st;
   } else if ((st = cuda_check(cudaMemsetAsync(Y, 0, hb2, D.S.s), "memset")) != TM_OK) {
     return st;
   }
   info->iters = iters;
   info->reliable_updates = updates;
   info->schur_rel_residual = bb > 0.0 ? std::sqrt(rr_true / bb) : 0.0;
-  // x_o = Qhat_h Y = G (D Y - kappa^2 H_oe D^-1 H_eo Y)  -> W
-  if ((st = dhop(D, TM_F64, 18, 0, Y, nullptr, T, co_dinv_hop(D))) != TM_OK) return st;
-  if ((st = dhop(D, TM_F64, 18, 1, T, Y, W, co_schur_g(D))) != TM_OK) return st;
+  // x_o = Qhat_h Y = G (D Y - kappa^2 H_oe D^-1 H_eo Y)  -> W (already there after the last FP64
+  // residual of the final Y)
+  if (!xo_in_W) {
+    if ((st = dhop(D, TM_F64, 18, 0, Y, nullptr, T, co_dinv_hop(D))) != TM_OK) return st;
+    if ((st = dhop(D, TM_F64, 18, 1, T, Y, W, co_schur_g(D))) != TM_OK) return st;
+  }
   // x_e = D^-1 (b_e + kappa H_eo x_o)  -> Pv
   DCoef rec = dcoef_zero();
   set_Dinv(rec.P, D.mb, D.eb, 1.0);
