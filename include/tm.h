@@ -207,9 +207,12 @@ typedef struct {
 /* Solves M(f) x = b on the full lattice by even/odd preconditioning (App. B.2): source
  * preparation varphi_o = b_o - M_oe (M_ee)^{-1} b_e, CG on Qhat^f Qhat^-f X = gamma5 varphi_o
  * (eq. eo6), x_o = Qhat^-f X, x_e = (M_ee)^{-1}(b_e - M_eo x_o).  x, b: canonical full
- * fields, host or device, nrhs x 24 V doubles.  With mode TM_CG_RELIABLE, FP64 updates and no
- * initial guess, nrhs > 1 systems are solved together by tm_solve_cg_batch (shared launches);
- * otherwise one after another.  Synchronises
+ * fields, host or device, nrhs x 24 V doubles.  Convergence is decided by an FP64 residual:
+ * in the mixed modes, once a sloppy stage reaches tol, by the FP64 residual of the full
+ * system that the reconstruction computes (its odd part is ||b' - A X|| up to the rounding
+ * of x_e); if that misses tol the iteration continues.  With mode TM_CG_RELIABLE, FP64
+ * updates and no initial guess, nrhs > 1 systems are solved together by tm_solve_cg_batch
+ * (shared launches); otherwise one after another.  Synchronises
  * `stream` to fill `info` (may be NULL; with nrhs > 1 it describes the worst system).
  * Errors: TM_ERR_NOT_CONVERGED (x holds the last iterate), TM_ERR_NO_GAUGE, TM_ERR_ARG,
  * TM_ERR_NONFINITE, TM_ERR_CUDA, TM_ERR_OOM. */
