@@ -322,8 +322,8 @@ static tm_status tune_hop(tm_lattice lat, int prec, int nreal, cudaStream_t s) {
   upd.mode = 2;
   upd.alpha_sign = 1.0;
   upd.red = Reduce{lat->partials, lat->counters, lat->dscalars, nullptr, FIN_STORE};
-  // Rounds interleave the candidates so that a clock still ramping up after the gauge copy
-  // was built (or any other drift) slows every candidate alike; round 0 is the warm-up.  A
+  // Passes interleave the candidates so that a clock still ramping up after the gauge copy
+  // was built (or any other drift) slows every candidate alike; pass 0 is the warm-up.  A
   // group is two iterations' mix (8 launches); each candidate's score is its fastest group
   // (five groups, three for FP64 storage, whose launches are ~10x longer).  Candidates: one
   // thread per site, its software-pipelined form (FP32 / FP16 storage), 2 and 4 threads per site.

@@ -1,6 +1,6 @@
 """GPU even/odd CG against the CPU oracle (through the C ABI).
 
-The bar for every solve is the spec one: the FP64 true residual
+The bar for every solve: the FP64 true residual
 ||phi - M x|| / ||phi||, recomputed by the ORACLE's operator on the GPU solution,
 is below 1e-10.  On 4^4 the GPU solution is also compared with the oracle's own
 even/odd solve.
