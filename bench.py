@@ -30,6 +30,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Dslash GB/s & % HBM roofline; CG solves/sec to 1e-10 FP64 residual, mixed vs FP64"
 HOP_FLOPS = 1320  # per output site per hopping application (8 hops x 168 flops - 24)
+REF_TOTAL_SECONDS = 90.0  # host time of the reference arm's timed steps together
 # dram__bytes_read.sum + dram__bytes_write.sum of one hopping-kernel launch, from ncu captures
 # (profiles/), keyed by sloppy form, lattice and kernel choice (threads per site; 3 = the
 # software-pipelined one-thread kernel), from ncu --set full captures of the current kernels:
@@ -724,15 +725,18 @@ def run_reference(args):
         iters, how = res.iters, "of the oracle's own complete FP64 solve to 1e-10"
     for _ in range(args.warmup):
         oracle_cg_rate(w, U, phi, 0.0)
+    # each step's sample: --ref-seconds, shortened so that all steps together take about
+    # REF_TOTAL_SECONDS of host time
+    step_seconds = min(args.ref_seconds, max(0.5, REF_TOTAL_SECONDS / max(1, args.steps)))
     per_step = []
     for _ in range(args.steps):
-        t_it, n, t_fixed = oracle_cg_rate(w, U, phi, args.ref_seconds)
+        t_it, n, t_fixed = oracle_cg_rate(w, U, phi, step_seconds)
         per_step.append(t_it * iters + t_fixed)
     tot = sum(per_step)
     value = args.steps / tot
     cb = {"value": round(value, 6), "unit": "solves/s", "cores": oracle.num_threads(),
           "kind": "oracle",
-          "sample": f"each step: oracle FP64 CG on {w.name} timed for ~{args.ref_seconds} s, "
+          "sample": f"each step: oracle FP64 CG on {w.name} timed for ~{step_seconds:.2g} s, "
                     f"extrapolated to {iters} iterations per solve ({how}), plus one source "
                     "preparation and reconstruction"}
     print(json.dumps({
