@@ -333,9 +333,12 @@ static bool dverbose() {
 // CG on Qhat_h^2 y = bp (FP64 or reliable-update mixed precision); y starts at 0.
 // On return *xo_in_W says whether W holds Qhat_h Y of the final Y (left by the last FP64
 // residual, which forms it first): then it is x_o and the caller need not recompute it.
+// With `guess` Y holds a starting point (its FP64 residual is computed first).  With `defer`
+// (mixed mode) a sloppy stage that reaches the tolerance ends the call with *pending set and Y
+// accumulated but not confirmed in FP64: the caller confirms it through the reconstruction.
 static tm_status dcg(const DSolver& D, const tm_cg_params& P, const void* bp, double bb, void* Y, void* R, void* Pv,
                      void* T, void* W, int* iters_out, int* updates_out, bool* conv_out, double* rr_out,
-                     bool* xo_in_W) {
+                     bool* xo_in_W, bool guess = false, bool defer = false, bool* pending = nullptr) {
   tm_lattice lat = D.S.lat;
   cudaStream_t s = D.S.s;
   const size_t hb64 = 2 * D.S.hb[TM_F64];
@@ -344,12 +347,28 @@ static tm_status dcg(const DSolver& D, const tm_cg_params& P, const void* bp, do
   int iters = 0, updates = 0, bad = 0;
   bool converged = false, w_valid = false;
   double rr_true = bb;
-  if ((st = cuda_check(cudaMemsetAsync(Y, 0, hb64, s), "memset")) != TM_OK) return st;
-  if ((st = cuda_check(cudaMemcpyAsync(R, bp, hb64, cudaMemcpyDeviceToDevice, s), "copy")) != TM_OK) return st;
+  if (pending) *pending = false;
+  if (guess) {
+    if ((st = dtrue_residual(D, R, Y, bp, T, W, &rr_true)) != TM_OK) return st;
+    w_valid = true;
+    ++updates;
+    converged = rr_true < stop2;
+    if (converged || !(rr_true < 1e300)) {
+      *iters_out = 0;
+      *updates_out = updates;
+      *conv_out = converged;
+      *rr_out = rr_true;
+      *xo_in_W = true;
+      return converged ? TM_OK : set_error(TM_ERR_NONFINITE, "tm_solve_doublet: residual diverged");
+    }
+  } else {
+    if ((st = cuda_check(cudaMemsetAsync(Y, 0, hb64, s), "memset")) != TM_OK) return st;
+    if ((st = cuda_check(cudaMemcpyAsync(R, bp, hb64, cudaMemcpyDeviceToDevice, s), "copy")) != TM_OK) return st;
+  }
   if (P.mode == TM_CG_FP64) {
     if ((st = cuda_check(cudaMemcpyAsync(Pv, R, hb64, cudaMemcpyDeviceToDevice, s), "copy")) != TM_OK) return st;
     DVecs v{TM_F64, 18, Y, R, Pv, T, W};
-    double rr = bb;
+    double rr = rr_true;
     while (!converged) {
       CGState fin;
       if ((st = run_dstage(D, v, fresh_state(rr, stop2, P.max_iter, iters, 0.0), &fin)) != TM_OK) return st;
@@ -384,7 +403,7 @@ static tm_status dcg(const DSolver& D, const tm_cg_params& P, const void* bp, do
     if ((st = dconvert(D, TM_F32, rs, TM_F64, R)) != TM_OK) return st;
     if ((st = dconvert(D, sp, ps, TM_F64, R)) != TM_OK) return st;
     const double delta2 = P.delta * P.delta;
-    double rr = bb;
+    double rr = rr_true;
     while (!converged && iters < P.max_iter) {
       CGState fin;
       if ((st = run_dstage(D, v, fresh_state(rr, stop2, P.max_iter, iters, delta2, SLOPPY_GROWTH), &fin)) != TM_OK)
@@ -400,6 +419,15 @@ static tm_status dcg(const DSolver& D, const tm_cg_params& P, const void* bp, do
         iters = fin.iter;
         if ((st = daccumulate(D, Y, xs)) != TM_OK) return st;
         w_valid = false;
+        if (defer && pending && fin.converged) {
+          *iters_out = iters;
+          *updates_out = updates;
+          *conv_out = false;
+          *rr_out = fin.rr;
+          *xo_in_W = false;
+          *pending = true;
+          return TM_OK;
+        }
       }
       if ((st = dtrue_residual(D, R, Y, bp, T, W, &rr_true)) != TM_OK) return st;
       w_valid = true;
@@ -507,37 +535,66 @@ static tm_status dsolve_one(const DSolver& D, double* x, const double* b, const 
   double bb = 0.0;
   if ((st = norm2_n(D.S, TM_F64, 2 * lat->geom.h, bp, &bb)) != TM_OK) return st;
   int iters = 0, updates = 0;
-  bool converged = bb == 0.0, xo_in_W = false;
+  bool converged = bb == 0.0, xo_in_W = false, pending = false;
   double rr_true = 0.0;
+  const double stop2 = P.tol * P.tol * bb;
+  const bool defer = P.mode != TM_CG_FP64;
   if (!converged) {
-    if ((st = dcg(D, P, bp, bb, Y, R, Pv, T, W, &iters, &updates, &converged, &rr_true, &xo_in_W)) != TM_OK)
+    if ((st = dcg(D, P, bp, bb, Y, R, Pv, T, W, &iters, &updates, &converged, &rr_true, &xo_in_W, false, defer,
+                  &pending)) != TM_OK)
       return st;
   } else if ((st = cuda_check(cudaMemsetAsync(Y, 0, hb2, D.S.s), "memset")) != TM_OK) {
     return st;
   }
+  // x_o = Qhat_h Y (-> W), x_e = D^-1 (b_e + kappa H_eo x_o) (-> Pv) and the FP64 residual of the
+  // full system: its odd part ||(b - M x)_o|| = ||varphi_o - Mhat_h x_o|| = ||b' - Qhat_h^2 Y|| up
+  // to the rounding of x_e (G is unitary), so it also confirms a pending sloppy convergence.
+  double rfull = 0.0, rodd = 0.0;
+  for (;;) {
+    if (!xo_in_W) {
+      if ((st = dhop(D, TM_F64, 18, 0, Y, nullptr, T, co_dinv_hop(D))) != TM_OK) return st;
+      if ((st = dhop(D, TM_F64, 18, 1, T, Y, W, co_schur_g(D))) != TM_OK) return st;
+    }
+    DCoef rec = dcoef_zero();
+    set_Dinv(rec.P, D.mb, D.eb, 1.0);
+    set_Dinv(rec.Q, D.mb, D.eb, lat->kappa);
+    if ((st = dhop(D, TM_F64, 18, 0, W, be, Pv, rec)) != TM_OK) return st;
+    if ((st = dapply_M(D, R, Z, Pv, W)) != TM_OK) return st;  // (M x)_e -> R, (M x)_o -> Z
+    DCoef diff = dcoef_zero();  // b - M x
+    set_I(diff.P, 1.0);
+    set_I(diff.Q, -1.0);
+    if ((st = dsite(D, TM_F64, 0, be, R, R, nullptr, diff, none)) != TM_OK) return st;
+    if ((st = dsite(D, TM_F64, 0, bo, Z, Z, nullptr, diff, none)) != TM_OK) return st;
+    double reven = 0.0;
+    if ((st = norm2_n(D.S, TM_F64, 2 * lat->geom.h, R, &reven)) != TM_OK) return st;
+    if ((st = norm2_n(D.S, TM_F64, 2 * lat->geom.h, Z, &rodd)) != TM_OK) return st;
+    rfull = reven + rodd;
+    if (!pending) break;
+    ++updates;  // an FP64 residual recomputation
+    if (dverbose())
+      fprintf(stderr, "[tm_solve_doublet] confirmation: FP64 |(b - M x)_o|/|b'| %.3e\n", std::sqrt(rodd / bb));
+    if (rodd < stop2) {
+      converged = true;
+      rr_true = rodd;
+      break;
+    }
+    if (iters >= P.max_iter) {  // report not converged with this residual
+      rr_true = rodd;
+      break;
+    }
+    // not confirmed: continue from Y (its FP64 residual first)
+    tm_cg_params Q = P;
+    Q.max_iter = P.max_iter - iters;
+    int it2 = 0, up2 = 0;
+    if ((st = dcg(D, Q, bp, bb, Y, R, Pv, T, W, &it2, &up2, &converged, &rr_true, &xo_in_W, true, defer,
+                  &pending)) != TM_OK)
+      return st;
+    iters += it2;
+    updates += up2;
+  }
   info->iters = iters;
   info->reliable_updates = updates;
   info->schur_rel_residual = bb > 0.0 ? std::sqrt(rr_true / bb) : 0.0;
-  // x_o = Qhat_h Y = G (D Y - kappa^2 H_oe D^-1 H_eo Y)  -> W (already there after the last FP64
-  // residual of the final Y)
-  if (!xo_in_W) {
-    if ((st = dhop(D, TM_F64, 18, 0, Y, nullptr, T, co_dinv_hop(D))) != TM_OK) return st;
-    if ((st = dhop(D, TM_F64, 18, 1, T, Y, W, co_schur_g(D))) != TM_OK) return st;
-  }
-  // x_e = D^-1 (b_e + kappa H_eo x_o)  -> Pv
-  DCoef rec = dcoef_zero();
-  set_Dinv(rec.P, D.mb, D.eb, 1.0);
-  set_Dinv(rec.Q, D.mb, D.eb, lat->kappa);
-  if ((st = dhop(D, TM_F64, 18, 0, W, be, Pv, rec)) != TM_OK) return st;
-  // full residual ||b - M_h x|| / ||b|| in FP64
-  if ((st = dapply_M(D, R, Z, Pv, W)) != TM_OK) return st;  // (M x)_e -> R, (M x)_o -> Z
-  DCoef diff = dcoef_zero();  // b - M x
-  set_I(diff.P, 1.0);
-  set_I(diff.Q, -1.0);
-  if ((st = dsite(D, TM_F64, 0, be, R, R, nullptr, diff, none)) != TM_OK) return st;
-  if ((st = dsite(D, TM_F64, 0, bo, Z, Z, nullptr, diff, none)) != TM_OK) return st;
-  double rfull = 0.0;
-  if ((st = full_norm2_host(D, R, Z, &rfull)) != TM_OK) return st;
   info->true_rel_residual = std::sqrt(rfull / bfull);
   if ((st = dunpack(D, x, Pv, 0)) != TM_OK) return st;
   if ((st = dunpack(D, x, W, 1)) != TM_OK) return st;
