@@ -213,7 +213,8 @@ class Lattice:
         return int(load().tm_half_field_bytes(self._h, prec))
 
     def set_hop_threads(self, prec: int, link: int, threads_per_site: int):
-        """Fix the hopping kernel's threads per site (1, 2, 4) for one form; 0 re-tunes."""
+        """Fix the hopping kernel for one form: threads per site 1, 2 or 4, or HOP_PIPELINED (3,
+        one thread per site with software-pipelined loads; FP32 / FP16 storage); 0 re-tunes."""
         _check(load().tm_set_hop_threads(self._h, prec, link, threads_per_site),
                "tm_set_hop_threads")
 
@@ -265,6 +266,10 @@ class Lattice:
                  mode: int = CG_FP64, sloppy_prec: int = F32, sloppy_link: int = LINK12,
                  delta: float = 0.1, use_x0: bool = False, flavour: int = 1,
                  update_prec: int = F64, stream=None, check: bool = True) -> SolveInfo:
+        """tm_solve_cg: M(flavour) x = b to the relative residual tol (modes CG_FP64,
+        CG_SQRT_EPS, CG_RELIABLE).  update_prec is the arithmetic of the residual recomputations
+        inside the loop: F64, DF64, or F32 (FP32 recomputations relative to the last FP64 one,
+        for FP16 storage); convergence is always confirmed in FP64."""
         p = CGParams(tol, max_iter, mode, sloppy_prec, sloppy_link, delta, int(use_x0), flavour,
                      update_prec)
         info = CGInfo()
