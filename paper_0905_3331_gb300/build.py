@@ -7,6 +7,7 @@ The result lands in paper_0905_3331_gb300/_build/ (git-ignored).
 from __future__ import annotations
 
 import concurrent.futures as cf
+import fcntl
 import os
 import shutil
 import subprocess
@@ -50,10 +51,20 @@ def up_to_date() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """Compile every csrc/*.cu for sm_103a and link libtmqcd.so; returns its path."""
+    """Compile every csrc/*.cu for sm_103a and link libtmqcd.so; returns its path.  Processes
+    that build at the same time (the ranks of a multi-GPU launch) take turns through a lock
+    file; the later ones find the library up to date."""
     if not force and up_to_date():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
+    with open(os.path.join(BUILD, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        if not force and up_to_date():
+            return LIB
+        return _build_locked(verbose, extra_flags)
+
+
+def _build_locked(verbose: bool, extra_flags) -> str:
     cc = nvcc()
     objs = []
     cmds = []
