@@ -311,6 +311,35 @@ def test_even_odd_solve_equals_dense_solve(T, L):
     assert abs(res.relres_full * np.linalg.norm(phi) - res.relres_normal * bnorm) < 1e-13 * bnorm
 
 
+def test_reconstruction_residual_is_the_normal_residual_for_any_X():
+    """For any X on the odd sites, not only a solution: with x_o = Qhat^-f X and x_e reconstructed
+    as in App. B.2, the full residual phi - M x vanishes on the even sites (up to rounding), and
+    its odd part is gamma5 (b - Qhat^f Qhat^-f X) with b = gamma5 varphi_o (eq. eo6), for both
+    flavours.  A mixed solve relies on this when it confirms convergence through the
+    reconstruction's residual."""
+    T, L = 4, 4
+    lat = Lattice.cubic(T, L)
+    w = inputs.WORKLOADS["4^4"]
+    U = inputs.random_gauge(T, L, w.eps, seed=w.gauge_seed)
+    phi = inputs.gaussian_spinor(T, L, w.source_seed)
+    g5 = oracle.gamma(4)
+    odd = lat.parity_mask()[..., None, None]
+
+    def gamma5(v):
+        return np.einsum("ab,...bc->...ac", g5, v)
+
+    for f in (1, -1):
+        X = _odd(lat, 17 + f)
+        varphi = oracle.eo_prepare(lat, U, phi, w.kappa, w.mu, f)
+        b = np.where(odd, gamma5(varphi), 0)
+        xo = np.where(odd, oracle.schur(lat, U, X, w.kappa, w.mu, -f, gamma5=True), 0)
+        psi = oracle.eo_reconstruct(lat, U, varphi, xo, w.kappa, w.mu, f)
+        r = phi - oracle.apply_M(lat, U, psi, w.kappa, w.mu, f)
+        rn = b - oracle.normal_op(lat, U, X, w.kappa, w.mu, f)
+        assert np.linalg.norm(np.where(odd, 0, r)) < 1e-13 * np.linalg.norm(phi)
+        assert rel(np.where(odd, r, 0), np.where(odd, gamma5(rn), 0)) < 1e-12
+
+
 def test_cg_reaches_tolerance_on_4x4x4x4():
     """4^4 workload (kappa 0.160, mu 0.01, eps 0.3): CG stops with a true relative residual below 1e-10."""
     w = inputs.WORKLOADS["4^4"]
