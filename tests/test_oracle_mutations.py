@@ -159,3 +159,28 @@ def test_a_planted_mistake_in_the_chrono_guess_fails_a_pin(name, old, new, monke
         except Exception:
             failed.append(pin)
     assert failed, f"no pin caught: {name}"
+
+
+# The correlator trace is plain numpy in oracle/__init__.py too: a transposed or conjugated
+# Gamma, or the Gram matrix used transposed, must each fail the free-field correlator pin with
+# Gamma != 1 (a mistake that Gamma = 1 would never show).
+CORRELATOR_MUTATIONS = [
+    ("Gamma transposed", "big = np.kron(np.asarray(G, dtype=np.complex128), np.eye(3))",
+     "big = np.kron(np.asarray(G, dtype=np.complex128).T, np.eye(3))"),
+    ("Gamma conjugated", "big = np.kron(np.asarray(G, dtype=np.complex128), np.eye(3))",
+     "big = np.kron(np.conj(np.asarray(G, dtype=np.complex128)), np.eye(3))"),
+    ("Gram matrix transposed", "np.trace(A[t] @ big)", "np.trace(A[t].T @ big)"),
+]
+
+
+@pytest.mark.parametrize("name,old,new", CORRELATOR_MUTATIONS, ids=[m[0] for m in CORRELATOR_MUTATIONS])
+def test_a_planted_mistake_in_the_correlator_fails_its_pin(name, old, new, monkeypatch):
+    import inspect
+    import textwrap
+    src = textwrap.dedent(inspect.getsource(oracle.correlator))
+    assert src.count(old) == 1, f"mutation site not found: {old}"
+    ns = dict(vars(oracle))
+    exec(compile(src.replace(old, new), "<mutated correlator>", "exec"), ns)
+    monkeypatch.setattr(oracle, "correlator", ns["correlator"])
+    with pytest.raises(AssertionError):
+        pins.test_free_field_correlators_with_gamma_from_momentum_space()

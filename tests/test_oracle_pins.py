@@ -396,15 +396,47 @@ def test_sampled_sites_match_full_application():
     assert np.array_equal(part, full[sites])
 
 
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 2, 4)])
+def test_sampled_hopping_sites_match_full_hopping(dims):
+    """orc_hopping_sites (the checker of the sampled-site hopping parity on large lattices)
+    gives, at scattered sites of both parities, the rows of the full hopping sum H psi and of
+    its even/odd restrictions H_eo, H_oe: bit for bit, on a random gauge field and spinor."""
+    T, Lx, Ly, Lz = dims
+    lat = Lattice(T, Lx, Ly, Lz)
+    U = np.empty(lat.gauge_shape, dtype=np.complex128)
+    Uc = inputs.random_gauge(T, Lx, 0.5, seed=95) if Lx == Ly == Lz else None
+    if Uc is not None:
+        U[...] = Uc
+    else:  # random SU(3) links of a non-cubic lattice: QR of complex Gaussians, det fixed
+        rng = np.random.default_rng(95)
+        Z = rng.normal(size=lat.gauge_shape) + 1j * rng.normal(size=lat.gauge_shape)
+        Q, R = np.linalg.qr(Z)
+        d = np.diagonal(R, axis1=-2, axis2=-1)
+        Q = Q * (d / np.abs(d))[..., None, :]
+        U[...] = Q / np.linalg.det(Q)[..., None, None] ** (1 / 3)
+    rng = np.random.default_rng(96)
+    psi = rng.normal(size=lat.spinor_shape) + 1j * rng.normal(size=lat.spinor_shape)
+    full = oracle.hopping(lat, U, psi).reshape(lat.V, 4, 3)
+    sites = np.unique(np.concatenate([rng.integers(0, lat.V, 40), [0, 1, lat.V - 2, lat.V - 1]]))
+    odd = lat.parity_mask().reshape(-1)
+    assert odd[sites].any() and (~odd[sites]).any()
+    part = oracle.hopping_sites(lat, U, psi, sites)
+    assert np.array_equal(part, full[sites])
+    for p in (0, 1):  # H_{p,1-p}: the input on the other parity only
+        other = np.where(lat.parity_mask()[..., None, None] == (1 - p), psi, 0)
+        restricted = oracle.hopping(lat, U, other, out_parity=p).reshape(lat.V, 4, 3)
+        mine = sites[odd[sites] == p]
+        assert np.array_equal(oracle.hopping_sites(lat, U, other, mine), restricted[mine])
+
+
 # ------------------------------------------------------ correlators (Sec. 4.3) ---
-def test_free_field_pion_correlator_from_momentum_space():
-    """C_PP(t) = sum_x ||G(x,0)||^2 of the oracle's 12 point-source solves on a unit gauge field
-    equals the closed form G(x,0) = (1/V) sum_p e^{ipx} M(p)^-1, M(p) = (1 - 2k sum cos p)
-    + i mu~ g5 - 2ik sum g_mu sin p_mu (antiperiodic p_t), summed over each timeslice."""
-    T, L = 4, 4
+def _free_field_point_propagators(T, L, kappa, mu):
+    """The oracle's 12 point-source solves on a unit gauge field, and the closed form of the
+    same propagator from momentum space: G(x,0) = (1/V) sum_p e^{ipx} M(p)^-1 with
+    M(p) = (1 - 2k sum cos p) + i mu~ g5 - 2ik sum g_mu sin p_mu (antiperiodic p_t), as a
+    (T, L, L, L, 4, 4) array [..., sink spin, source spin] (the colour part is the identity)."""
     lat = Lattice.cubic(T, L)
     U = inputs.unit_gauge(T, L)
-    kappa, mu = 0.12, 0.05
     mut = 2 * kappa * mu
     props = []
     for s in range(4):
@@ -412,8 +444,6 @@ def test_free_field_pion_correlator_from_momentum_space():
             res = oracle.solve(lat, U, inputs.point_source(T, L, s, c), kappa, mu, tol=1e-13)
             assert res.converged
             props.append(res.psi)
-    A = oracle.meson_contract(np.stack(props))
-    C = oracle.correlator(A, np.eye(4)).real
     g = [oracle.gamma(k) for k in range(5)]
     P = free_field_momenta(lat)  # (p_t, p_x, p_y, p_z)
     t, z, y, x = np.indices((T, L, L, L))
@@ -424,11 +454,43 @@ def test_free_field_pion_correlator_from_momentum_space():
         phase = np.exp(1j * (p[0] * t + p[1] * x + p[2] * y + p[3] * z))
         G += phase[..., None, None] * np.linalg.inv(Mp)
     G /= lat.V
+    return np.stack(props), G
+
+
+def test_free_field_pion_correlator_from_momentum_space():
+    """C_PP(t) = sum_x ||G(x,0)||^2 of the oracle's 12 point-source solves on a unit gauge field
+    equals the closed form of the propagator from momentum space, summed over each timeslice."""
+    T, L = 4, 4
+    props, G = _free_field_point_propagators(T, L, 0.12, 0.05)
+    A = oracle.meson_contract(props)
+    C = oracle.correlator(A, np.eye(4)).real
     C_closed = 3 * (np.abs(G) ** 2).sum(axis=(1, 2, 3, 4, 5))  # colour identity: 3 copies
     assert np.allclose(C, C_closed, rtol=1e-9, atol=0)
     # the point-source propagator itself, spin block of colour 0, at every site
-    Gsolve = np.stack(props).reshape(4, 3, T, L, L, L, 4, 3)[:, 0, ..., 0]  # [s_src, ..., s_sink]
+    Gsolve = props.reshape(4, 3, T, L, L, L, 4, 3)[:, 0, ..., 0]  # [s_src, ..., s_sink]
     assert np.allclose(np.moveaxis(Gsolve, 0, -1), G, rtol=0, atol=1e-10)
+
+
+def test_free_field_correlators_with_gamma_from_momentum_space():
+    """C_PG(t) = sum_x tr[G(x,0)^dag G(x,0) Gamma gamma5] (Sec. 4.3) for Gamma != 1: the
+    axial (Gamma = gamma0 gamma5, C_PA), vector (Gamma = gamma0, C_PV) and a random complex
+    Gamma, against the closed-form propagator with the trace written out index by index:
+    tr[G^dag G X] = sum_{a,b,c} conj(G[a,b]) G[a,c] X[c,b] (a the sink spin; colour: 3 copies).
+    The random Gamma fails a transposed or conjugated Gamma, which gamma0 (real symmetric in
+    the basis of App. A) would not."""
+    T, L = 4, 4
+    props, G = _free_field_point_propagators(T, L, 0.12, 0.05)
+    A = oracle.meson_contract(props)
+    g = [oracle.gamma(k) for k in range(5)]
+    rng = np.random.default_rng(5)
+    gammas = {"PA": g[0] @ g[4], "PV": g[0],
+              "random": rng.normal(size=(4, 4)) + 1j * rng.normal(size=(4, 4))}
+    for name, Gam in gammas.items():
+        X = Gam @ g[4]
+        C = oracle.correlator(A, X)
+        C_closed = 3 * np.einsum("tzyxab,tzyxac,cb->t", G.conj(), G, X)
+        assert np.abs(C_closed).max() > 1e-6, name  # the pin has something to compare
+        assert np.allclose(C, C_closed, rtol=1e-9, atol=1e-13 * np.abs(C_closed).max()), name
 
 
 # ------------------------------------------- chronological guess (Sec. 4.2) ---
@@ -562,6 +624,70 @@ def dense_doublet(apply, lat):
         A[:, j] = apply(e).reshape(-1)
         flat[j] = 0.0
     return A
+
+
+def test_doublet_reconstruction_residual_is_the_normal_residual_for_any_Y():
+    """The doublet's even/odd form (the block elimination of App. B.1 with the site term
+    D = 1 + i mb g5 tau3 + eb tau1, Schur operator Mhat_h = D - kappa^2 H_oe D^-1 H_eo,
+    Qhat_h = G Mhat_h with G = g5 tau1): for ANY odd-site Y, x_o = Qhat_h Y and
+    x_e = D^-1 (b_e + kappa H_eo x_o) leave a full residual b - M_h x (the oracle's M_h of
+    eq. Dh, applied by its definition) that vanishes on the even sites, and whose odd part is
+    G (G varphi_o - Qhat_h^2 Y) with varphi_o = b_o + kappa H_oe D^-1 b_e.  A mixed doublet
+    solve relies on this when it confirms convergence through the reconstruction's residual.
+    D, D^-1 and G are built here as 8 x 8 matrices on (flavour, spin) from App. A's matrices."""
+    T, L = 4, 2
+    lat = Lattice.cubic(T, L)
+    U = inputs.random_gauge(T, L, 0.5, seed=111)
+    kappa, mubar, epsbar = 0.16, 0.15, 0.19
+    mb, eb = 2 * kappa * mubar, 2 * kappa * epsbar
+    g5 = oracle.gamma(4)
+    tau = [oracle.pauli(k) for k in range(4)]
+    D = np.eye(8) + 1j * mb * np.kron(tau[3], g5) + eb * np.kron(tau[1], np.eye(4))
+    Dinv = np.linalg.inv(D)
+    G = np.kron(tau[1], g5)
+
+    def site(Mat, v):  # Mat on the (flavour, spin) index of a doublet field
+        w = np.moveaxis(v, 0, -3)                       # (T, Lz, Ly, Lx, 2, 4, 3)
+        w = w.reshape(w.shape[:4] + (8, 3))
+        out = np.einsum("ab,...bc->...ac", Mat, w).reshape(w.shape[:4] + (2, 4, 3))
+        return np.moveaxis(out, -3, 0)
+
+    def hop(v, p):  # H_{p,1-p} on both flavours
+        return np.stack([oracle.hopping(lat, U, v[f], out_parity=p) for f in (0, 1)])
+
+    oddm = lat.parity_mask()[None, ..., None, None]
+    even = lambda v: np.where(oddm, 0, v)  # noqa: E731
+    odd = lambda v: np.where(oddm, v, 0)   # noqa: E731
+
+    def mhat(v):
+        return odd(site(D, v)) - kappa ** 2 * hop(even(site(Dinv, hop(v, 0))), 1)
+
+    def qhat(v):
+        return site(G, mhat(v))
+
+    b = _doublet(lat, 112)
+    varphi = odd(b) + kappa * hop(even(site(Dinv, even(b))), 1)
+    Y = odd(_doublet(lat, 114))
+    xo = qhat(Y)
+    xe = even(site(Dinv, even(b) + kappa * hop(xo, 0)))
+    r = b - oracle.apply_Mh(lat, U, xe + xo, kappa, mubar, epsbar)
+    assert np.linalg.norm(even(r)) < 1e-13 * np.linalg.norm(b)
+    expect = site(G, site(G, varphi) - qhat(qhat(Y)))
+    assert rel(odd(r), expect) < 1e-12
+    # and with Y the solution of Qhat_h^2 Y = G varphi_o, x solves M_h x = b
+    o = np.flatnonzero(np.broadcast_to(oddm, b.shape).reshape(-1))
+    n = len(o)
+    Q2 = np.empty((n, n), dtype=np.complex128)
+    e = np.zeros(b.shape, dtype=np.complex128)
+    for k, j in enumerate(o):
+        e.reshape(-1)[j] = 1.0
+        Q2[:, k] = qhat(qhat(e)).reshape(-1)[o]
+        e.reshape(-1)[j] = 0.0
+    Ys = np.zeros(b.shape, dtype=np.complex128)
+    Ys.reshape(-1)[o] = np.linalg.solve(Q2, site(G, varphi).reshape(-1)[o])
+    xo = qhat(Ys)
+    xe = even(site(Dinv, even(b) + kappa * hop(xo, 0)))
+    assert rel(oracle.apply_Mh(lat, U, xe + xo, kappa, mubar, epsbar), b) < 1e-12
 
 
 def test_pauli_matrices_algebra():
