@@ -364,11 +364,15 @@ void tm_cg_params_default(tm_cg_params *params);
  * those 64 MiB until the process exits.
  *   Limit: 4 x 192 x V/2 bytes of scratch must fit in 64 MiB, i.e. V = T L^3 <= 174762
  *          sites (16^3 x 32 fits, 24^3 x 48 does not); larger lattices get TM_ERR_ARG.
- *   in, out: canonical full fields in DEVICE memory of the lattice's device (host pointers
- *          get TM_ERR_ARG: staging them would need a buffer); nrhs x 24 V doubles; no overlap.
+ *   in, out: canonical full fields in DEVICE memory of the lattice's device, or managed
+ *          memory (host pointers, and device memory of another GPU, get TM_ERR_ARG: staging
+ *          them would need a buffer); nrhs x 24 V doubles; no overlap.
  *   Set-up: the first call on a device looks up the array's device address
- *          (cudaGetSymbolAddress, with that device current) and caches it; make that first
- *          call before any stream capture.
+ *          (cudaGetSymbolAddress, with that device current) and caches it for the rest of the
+ *          process; make that first call before any stream capture.  The cached address
+ *          belongs to the device's context at that time: after a cudaDeviceReset (which also
+ *          frees every lattice's device memory) this entry point must not be called again in
+ *          the same process.
  *   Sharing: every call uses the same array.  The array keeps the previous call's contents
  *          (each call writes every scratch byte it reads before reading it), and calls that
  *          overlap on the GPU -- on different streams, or from different host threads --

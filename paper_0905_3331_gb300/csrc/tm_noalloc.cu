@@ -44,6 +44,20 @@ static tm_status noalloc_scratch(void** out) {
   return TM_OK;
 }
 
+// True if p is memory that this call may hand to the lattice's kernels without staging:
+// device memory of the lattice's device, or managed memory (reachable from every device).
+// A pointer into another GPU's memory would be read over the interconnect with peer access,
+// and fault without it.
+static bool on_lattice_device(const void* p, int lattice_device) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == lattice_device;
+}
+
 }  // namespace tmq
 
 using namespace tmq;
@@ -73,6 +87,9 @@ extern "C" tm_status tm_apply_D_noalloc(tm_lattice lat, double* out, const doubl
   if (st != TM_OK) return st;
   if (dev != lat->device)
     return set_error(TM_ERR_ARG, "tm_apply_D_noalloc: current device %d is not the lattice's device %d", dev,
+                     lat->device);
+  if (!on_lattice_device(in, lat->device) || !on_lattice_device(out, lat->device))
+    return set_error(TM_ERR_ARG, "tm_apply_D_noalloc: in and out must be device memory of the lattice's device %d",
                      lat->device);
   void* base = nullptr;
   if ((st = noalloc_scratch(&base)) != TM_OK) return st;

@@ -11,6 +11,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle
 from paper_0905_3331_gb300 import Lattice, inputs, tm
 
 torch = pytest.importorskip("torch")
@@ -61,6 +62,52 @@ def test_noalloc_matches_apply_D_twice(T, L):
     lat.close()
 
 
+def test_noalloc_first_call_on_a_fresh_lattice_matches_the_oracle():
+    """The entry point as the first operator call on a freshly created lattice (no tm_apply_D
+    before it, so no lattice work space exists), for M and M^dag with two right-hand sides:
+    compared with the CPU oracle's M directly (M^dag = gamma5 M(-mu) gamma5), and the
+    device's free memory is the same before and after the call."""
+    lib, fn = _fn()
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream().cuda_stream
+    # the per-device set-up (the scratch array's address) happens on some earlier call; make
+    # one on another lattice so that this test also holds in a fresh process
+    warm = Lattice(4, 4, 0.16, 0.01)
+    warm.set_gauge(torch.from_numpy(inputs.unit_gauge(4, 4)).to(dev))
+    wx = torch.zeros(4 ** 4 * 12, dtype=torch.complex128, device=dev)
+    wy = torch.empty_like(wx)
+    assert fn(warm._h, wy.data_ptr(), wx.data_ptr(), 1, 0, 1, stream) == 0, lib.tm_last_error()
+    torch.cuda.synchronize()
+    warm.close()
+    T, L, kappa, mu = 8, 6, 0.1615, 0.003
+    U = inputs.random_gauge(T, L, 0.6, 3)
+    nrhs = 2
+    src_np = inputs.gaussian_spinor(T, L, 9, shape_prefix=(nrhs,))
+    lat = Lattice(T, L, kappa, mu)
+    lat.set_gauge(torch.from_numpy(U).to(dev))
+    src = torch.from_numpy(src_np).to(dev)
+    olat = oracle.Lattice.cubic(T, L)
+    g5 = np.diag([1.0, 1.0, -1.0, -1.0])
+    for dagger in (0, 1):
+        out = torch.full_like(src, float("nan"))
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info(dev)[0]
+        st = fn(lat._h, out.data_ptr(), src.data_ptr(), 1, dagger, nrhs, stream)
+        torch.cuda.synchronize()
+        assert st == 0, lib.tm_last_error()
+        assert torch.cuda.mem_get_info(dev)[0] == free0
+        got = out.cpu().numpy()
+        for r in range(nrhs):
+            if dagger:
+                v = np.einsum("ab,...bc->...ac", g5, src_np[r])
+                ref = np.einsum("ab,...bc->...ac", g5, oracle.apply_M(olat, U, v, kappa, -mu))
+            else:
+                ref = oracle.apply_M(olat, U, src_np[r], kappa, mu)
+            assert np.linalg.norm(got[r] - ref) / np.linalg.norm(ref) < 1e-13
+    lat.close()
+
+
 def test_noalloc_rejects_what_it_cannot_do():
     lib, fn = _fn()
     dev = torch.device("cuda:0")
@@ -76,4 +123,10 @@ def test_noalloc_rejects_what_it_cannot_do():
     host_out = np.zeros_like(host_in)
     assert fn(lat._h, host_out.ctypes.data, host_in.ctypes.data, 1, 0, 1, 0) == 1
     assert b"device memory" in lib.tm_last_error()
+    if torch.cuda.device_count() > 1:  # memory of another GPU is rejected, not read remotely
+        other = torch.zeros(4 ** 4 * 12, dtype=torch.complex128, device="cuda:1")
+        mine = torch.zeros_like(other, device=dev)
+        assert fn(lat._h, mine.data_ptr(), other.data_ptr(), 1, 0, 1, 0) == 1
+        assert b"lattice's device" in lib.tm_last_error()
+        assert fn(lat._h, other.data_ptr(), mine.data_ptr(), 1, 0, 1, 0) == 1
     lat.close()
