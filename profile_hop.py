@@ -2,7 +2,7 @@
 
 A small driver for timing and for ncu captures of a single kernel:
 
-  python -m paper_0905_3331_gb300.profile_hop --workload 32^3x64 --form f16:12 --iters 5
+  python profile_hop.py --workload 32^3x64 --form f16:12 --iters 5
 
 It sets up the lattice (gauge copy), packs a Gaussian half field, runs
 tm_apply_hopping_eo `iters` times (alternating output parity) and reports the mean
@@ -24,16 +24,20 @@ from __future__ import annotations
 
 import argparse
 import json
+import os
 import statistics
+import sys
 
 import numpy as np
+
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
 
 
 def main():
     import torch
 
-    from . import Lattice, inputs
-    from . import build as libbuild
+    from paper_0905_3331_gb300 import Lattice, inputs
+    from paper_0905_3331_gb300 import build as libbuild
 
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="32^3x64")
@@ -99,8 +103,8 @@ def main():
 def batch(args):
     import torch
 
-    from . import Lattice, inputs, solve_cg_batch
-    from . import build as libbuild
+    from paper_0905_3331_gb300 import Lattice, inputs, solve_cg_batch
+    from paper_0905_3331_gb300 import build as libbuild
     libbuild.build()
     prec = {"f32": 1, "f16": 2}[args.form.split(":")[0]]
     nreal = int(args.form.split(":")[1])
@@ -134,8 +138,8 @@ def batch(args):
 def contract(args):
     import torch
 
-    from . import Lattice, inputs
-    from . import build as libbuild
+    from paper_0905_3331_gb300 import Lattice, inputs
+    from paper_0905_3331_gb300 import build as libbuild
     libbuild.build()
     w = inputs.WORKLOADS[args.workload]
     dev = torch.device("cuda:0")
@@ -167,8 +171,8 @@ def contract(args):
 def doublet(args):
     import torch
 
-    from . import CG_FP64, CG_RELIABLE, Lattice, inputs
-    from . import build as libbuild
+    from paper_0905_3331_gb300 import CG_FP64, CG_RELIABLE, Lattice, inputs
+    from paper_0905_3331_gb300 import build as libbuild
     libbuild.build()
     mubar, epsbar = (float(v) for v in args.doublet.split(","))
     prec, nreal = args.form.split(":")
