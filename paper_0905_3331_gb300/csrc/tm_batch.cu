@@ -13,6 +13,8 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -213,6 +215,16 @@ static tm_status batch_iteration(int prec, int nreal, const BatchSys* d_sys, con
 }
 
 namespace {
+
+// TM_VERBOSE=1 traces the confirmation of each converged system
+bool batch_verbose() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("TM_VERBOSE");
+    v = (e && *e == '1') ? 1 : 0;
+  }
+  return v == 1;
+}
 
 struct SysWork {
   Solver S;
@@ -533,6 +545,7 @@ extern "C" tm_status tm_solve_cg_batch(const tm_system* systems, int nsys, const
           st = launch_accumulate(w.S, w.X, w.xs);
         }
         w.iters = c.iter;
+        bool missed = false;  // a converged stage whose confirmation failed
         if (st == TM_OK && !c.nonfinite && c.converged) {
           // confirm through the reconstruction's FP64 residual of the full system, whose odd part
           // is ||b' - A X|| up to the rounding of x_e (4 FP64 hopping launches instead of the
@@ -541,11 +554,15 @@ extern "C" tm_status tm_solve_cg_batch(const tm_system* systems, int nsys, const
           st = reconstruct_check(w.S, w.X, w.be, w.bo, w.bfull, w.x, L.T, L.W, L.R, L.Pv, &w.true_rel, &rro);
           if (st != TM_OK) break;
           ++w.updates;
+          if (batch_verbose())
+            fprintf(stderr, "[tm_solve_cg_batch] system %d confirmation: FP64 |(b - M x)_o|/|b'| %.3e (%s)\n", k,
+                    std::sqrt(rro / w.bb), rro < w.stop2 ? "converged" : "not confirmed, continuing");
           if (rro < w.stop2) {
             w.converged = w.reconstructed = true;
             w.rr = rro;
             continue;
           }
+          missed = true;
         }
         double rr_true = 0.0;
         if (st == TM_OK) st = true_residual(w.S, L.R, w.X, w.bp, L.T, L.W, &rr_true);
@@ -561,7 +578,11 @@ extern "C" tm_status tm_solve_cg_batch(const tm_system* systems, int nsys, const
           continue;
         }
         st = convert_half(w.lat, TM_F32, w.rs, TM_F64, L.R, s);
-        if (st == TM_OK && (c.diverged || c.nonfinite)) st = convert_half(w.lat, sp, w.ps, TM_F64, L.R, s);
+        // the search direction restarts from the true residual after a divergent or overflowed
+        // stage, and after a converged stage that the FP64 residual did not confirm: that stage's
+        // p is scaled to its (drifted) iterated residual, not to the true one
+        if (st == TM_OK && (c.diverged || c.nonfinite || missed))
+          st = convert_half(w.lat, sp, w.ps, TM_F64, L.R, s);
         w.rr = rr_true;
       }
       if (st != TM_OK) break;

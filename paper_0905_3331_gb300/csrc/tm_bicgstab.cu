@@ -853,7 +853,8 @@ static tm_status solve_one_krylov(tm_lattice lat, double* x, const double* b, co
         return st;
       ++updates;
       if (bi_verbose())
-        fprintf(stderr, "[%s] confirmation: FP64 |(b - M x)_o|/|b'| %.3e\n", nm, std::sqrt(rro / bb));
+        fprintf(stderr, "[%s] confirmation: FP64 |(b - M x)_o|/|b'| %.3e (%s)\n", nm, std::sqrt(rro / bb),
+                rro < stop2 ? "converged" : "not confirmed, continuing");
       if (rro < stop2) {
         rr_true = rro;
         converged = reconstructed = true;

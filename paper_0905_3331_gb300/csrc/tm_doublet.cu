@@ -572,7 +572,8 @@ static tm_status dsolve_one(const DSolver& D, double* x, const double* b, const 
     if (!pending) break;
     ++updates;  // an FP64 residual recomputation
     if (dverbose())
-      fprintf(stderr, "[tm_solve_doublet] confirmation: FP64 |(b - M x)_o|/|b'| %.3e\n", std::sqrt(rodd / bb));
+      fprintf(stderr, "[tm_solve_doublet] confirmation: FP64 |(b - M x)_o|/|b'| %.3e (%s)\n", std::sqrt(rodd / bb),
+              rodd < stop2 ? "converged" : "not confirmed, continuing");
     if (rodd < stop2) {
       converged = true;
       rr_true = rodd;
