@@ -347,6 +347,17 @@ tm_status tm_solve_doublet(tm_lattice lat, double *x, const double *b, double mu
  * Errors: TM_ERR_ARG, TM_ERR_CUDA. */
 tm_status tm_meson_contract(tm_lattice lat, const double *props, double *out, void *stream);
 
+/* Correlators from the timeslice Gram matrices of tm_meson_contract (Sec. 4.3): for each of
+ * ngamma 4 x 4 complex matrices X_g = Gamma_g gamma5 acting on source spin,
+ *   C[g][t] = tr[ A_t (X_g (x) 1_colour) ] = sum_{s, s', c} A[t][3s+c][3s'+c] X_g[s'][s],
+ * e.g. C_PP: X = 1;  C_PA (Gamma = gamma0 gamma5): X = gamma0;  C_PV (Gamma = gamma0): X = gamma0
+ * gamma5 (gamma matrices of App. A).  A: T x 12 x 12 complex doubles, the output of
+ * tm_meson_contract (host or device).  X: ngamma x 4 x 4 complex doubles, row-major X[s'][s]
+ * (host or device), 1 <= ngamma <= 1024.  C: ngamma x T complex doubles (host or device).  FP64;
+ * each entry is summed in a fixed order (deterministic).  Errors: TM_ERR_ARG, TM_ERR_CUDA. */
+tm_status tm_correlator(tm_lattice lat, const double *A, const double *X, int ngamma, double *C,
+                        void *stream);
+
 /* Fills params with the defaults: tol 1e-10, max_iter 100000, TM_CG_FP64, sloppy
  * TM_F32 / TM_LINK12, delta 0.1, use_x0 0, flavour +1, update_prec TM_F64. */
 void tm_cg_params_default(tm_cg_params *params);

@@ -5,7 +5,8 @@
 // where G(x,0) is the 12 x 12 spin-colour propagator (column j = the solution for the source
 // of spin-colour j).  This file computes the timeslice sums of its Gram matrix
 //   A_t[j][k] = sum_{x, x_t = t} <psi^(j)(x), psi^(k)(x)>   (conjugate on j),
-// from which every C_PG(t) follows as a 12 x 12 trace.  Deterministic two-pass FP64 sums.
+// from which every C_PG(t) follows as a 12 x 12 trace (tm_correlator, below).  Deterministic
+// two-pass FP64 sums.
 #include <algorithm>
 #include <cstdint>
 #include <vector>
@@ -96,9 +97,54 @@ __global__ void contract_finish_kernel(const double* __restrict__ partial, int n
   o[(k * 12 + j) * 2 + 1] = j == k ? im : -im;
 }
 
+// C[g][t] = tr[A_t (X_g (x) 1_colour)] = sum_{s, s', c} A_t[3s+c][3s'+c] X_g[s'][s]: one thread
+// per (g, t), the 48 complex products summed in the order s, s', c (FP64, deterministic).
+__global__ void correlator_kernel(const double* __restrict__ A, const double* __restrict__ X, int T, int ngamma,
+                                  double* __restrict__ C) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;  // (g, t)
+  if (i >= T * ngamma) return;
+  const int g = i / T, t = i % T;
+  const double* a = A + (size_t)t * 144 * 2;
+  const double* x = X + (size_t)g * 16 * 2;
+  double re = 0.0, im = 0.0;
+  for (int s = 0; s < 4; ++s)
+    for (int sp = 0; sp < 4; ++sp) {
+      const double xr = x[(sp * 4 + s) * 2], xi = x[(sp * 4 + s) * 2 + 1];
+      for (int c = 0; c < 3; ++c) {
+        const int jk = (3 * s + c) * 12 + (3 * sp + c);
+        const double ar = a[jk * 2], ai = a[jk * 2 + 1];
+        re = fma(ar, xr, fma(-ai, xi, re));
+        im = fma(ar, xi, fma(ai, xr, im));
+      }
+    }
+  C[(size_t)i * 2] = re;
+  C[(size_t)i * 2 + 1] = im;
+}
+
 }  // namespace tmq
 
 using namespace tmq;
+
+extern "C" tm_status tm_correlator(tm_lattice lat, const double* A, const double* X, int ngamma, double* C,
+                                   void* stream) {
+  if (!lat || !A || !X || !C || ngamma < 1 || ngamma > 1024)
+    return set_error(TM_ERR_ARG, "tm_correlator: NULL argument or ngamma not in 1..1024");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int T = lat->T;
+  tm_status st;
+  const double* dA = static_cast<const double*>(stage_in(lat, WS_STAGE_IN, A, (size_t)T * 144 * 2 * sizeof(double), s, &st));
+  if (st != TM_OK) return st;
+  const double* dX = static_cast<const double*>(stage_in(lat, WS_GAMMA, X, (size_t)ngamma * 16 * 2 * sizeof(double), s, &st));
+  if (st != TM_OK) return st;
+  const size_t out_bytes = (size_t)ngamma * T * 2 * sizeof(double);
+  double* dC = static_cast<double*>(stage_out(lat, WS_STAGE_OUT, C, out_bytes, &st));
+  if (st != TM_OK) return st;
+  const int n = T * ngamma;
+  correlator_kernel<<<(n + 127) / 128, 128, 0, s>>>(dA, dX, T, ngamma, dC);
+  count_launch();
+  if ((st = cuda_check(cudaGetLastError(), "tm_correlator")) != TM_OK) return st;
+  return stage_out_finish(C, dC, out_bytes, s);
+}
 
 extern "C" tm_status tm_meson_contract(tm_lattice lat, const double* props, double* out, void* stream) {
   if (!lat || !props || !out) return set_error(TM_ERR_ARG, "tm_meson_contract: NULL argument");

@@ -1036,8 +1036,8 @@ tm_status diag_apply(tm_lattice lat, int prec, void* out, const void* in, int nr
                      double dlr, double dli, cudaStream_t s);
 // Workspace slots: 0..17 CG solver, 22..25 tm_apply_D, 26 staged input, 27 staged output,
 // 28 initial-guess work space, 29 contraction partials, 30 chronological-guess scalars,
-// 31 BiCGstab state; 18..20 BiCGstab vectors.
-enum { WS_APPLY_D = 22, WS_STAGE_IN = 26, WS_STAGE_OUT = 27, WS_X0 = 28, WS_CHRONO = 30, WS_BISTATE = 31 };
+// 31 BiCGstab state; 18..20 BiCGstab vectors; 21 staged correlator matrices.
+enum { WS_GAMMA = 21, WS_APPLY_D = 22, WS_STAGE_IN = 26, WS_STAGE_OUT = 27, WS_X0 = 28, WS_CHRONO = 30, WS_BISTATE = 31 };
 // host-buffer staging through workspace slots
 const void* stage_in(tm_lattice lat, int slot, const void* src, size_t bytes, cudaStream_t s, tm_status* st);
 void* stage_out(tm_lattice lat, int slot, void* dst, size_t bytes, tm_status* st);

@@ -95,6 +95,7 @@ def load():
         "tm_solve_cg_batch": ([ctypes.POINTER(TmSystem), I, ctypes.POINTER(CGParams),
                                ctypes.POINTER(CGInfo), P], I),
         "tm_meson_contract": ([P, P, P, P], I),
+        "tm_correlator": ([P, P, P, I, P, P], I),
         "tm_solve_bicgstab": ([P, P, P, I, ctypes.POINTER(CGParams), ctypes.POINTER(CGInfo), P], I),
         "tm_solve_mr": ([P, P, P, I, ctypes.POINTER(CGParams), ctypes.POINTER(CGInfo), P], I),
         "tm_apply_Dh": ([P, P, P, D, D, I, P], I),
@@ -118,7 +119,7 @@ def exported_symbols():
     return ["tm_lattice_create", "tm_lattice_destroy", "tm_lattice_set_params", "tm_volume",
             "tm_half_field_bytes", "tm_set_hop_threads", "tm_get_hop_threads", "tm_set_gauge", "tm_pack_half", "tm_unpack_half", "tm_apply_D",
             "tm_apply_hopping_eo", "tm_apply_Mee_inv", "tm_solve_cg", "tm_solve_cg_batch",
-            "tm_cg_params_default", "tm_meson_contract", "tm_solve_bicgstab", "tm_solve_mr", "tm_solve_normal", "tm_chrono_guess", "tm_apply_Dh",
+            "tm_cg_params_default", "tm_meson_contract", "tm_correlator", "tm_solve_bicgstab", "tm_solve_mr", "tm_solve_normal", "tm_chrono_guess", "tm_apply_Dh",
             "tm_solve_doublet",
             "tm_last_error", "tm_launch_count", "tm_reset_launch_count"]
 
@@ -144,6 +145,16 @@ def _addr(buf) -> int:
             raise ValueError("tensor must be contiguous")
         return buf.data_ptr()
     raise TypeError(f"unsupported buffer type {type(buf)}")
+
+
+def _sync():
+    """Wait for the device (after a call that wrote a host buffer on a stream)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            torch.cuda.synchronize()
+    except ImportError:
+        pass
 
 
 def _stream(stream) -> int:
@@ -254,12 +265,7 @@ class Lattice:
         _check(load().tm_meson_contract(self._h, _addr(props), _addr(out), _stream(stream)),
                "tm_meson_contract")
         if isinstance(out, np.ndarray):
-            try:
-                import torch
-                if torch.cuda.is_available():
-                    torch.cuda.synchronize()
-            except ImportError:
-                pass
+            _sync()
         return out
 
     def solve_cg(self, x, b, nrhs: int = 1, tol: float = 1e-10, max_iter: int = 100000,
@@ -302,12 +308,7 @@ class Lattice:
         _check(load().tm_apply_Dh(self._h, _addr(out), _addr(inp), mubar, epsbar, nrhs,
                                   _stream(stream)), "tm_apply_Dh")
         if isinstance(out, np.ndarray):
-            try:
-                import torch
-                if torch.cuda.is_available():
-                    torch.cuda.synchronize()
-            except ImportError:
-                pass
+            _sync()
         return out
 
     def solve_doublet(self, x, b, mubar: float, epsbar: float, tol: float = 1e-10,
@@ -389,9 +390,30 @@ def solve_cg_batch(systems, tol: float = 1e-10, max_iter: int = 100000, sloppy_p
     return out
 
 
-def correlator(A, gamma_source_times_g5):
-    """C(t) = sum_{s, s', c} A[t][3s+c][3s'+c] G[s'][s] for G = Gamma gamma5 (4 x 4); A from
-    Lattice.meson_contract.  C_PP uses G = identity."""
-    A = np.asarray(A).reshape(-1, 4, 3, 4, 3)
-    G = np.asarray(gamma_source_times_g5)
-    return np.einsum("tacbc,ba->t", A, G)
+def correlator(lat, A, X, stream=None):
+    """C(t) = tr[A_t (X (x) 1_colour)] for X = Gamma gamma5 (4 x 4, or a stack (n, 4, 4)) on
+    source spin (tm_correlator); A from Lattice.meson_contract (host or device).  C_PP uses
+    X = identity.  Returns (T,) or (n, T) complex128 (numpy for host A, else on A's device)."""
+    if hasattr(X, "data_ptr"):  # a torch tensor (host or device)
+        import torch
+        Xa = X.contiguous()
+        if Xa.dtype != torch.complex128:
+            raise TypeError("X must be complex128")
+        single = Xa.dim() == 2
+        n = 1 if single else Xa.shape[0]
+    else:
+        Xa = np.ascontiguousarray(np.asarray(X, dtype=np.complex128))
+        single = Xa.ndim == 2
+        Xa = Xa.reshape(-1, 4, 4)
+        n = Xa.shape[0]
+    if isinstance(A, np.ndarray):
+        A = np.ascontiguousarray(A, dtype=np.complex128)
+        C = np.zeros((n, lat.T), dtype=np.complex128)
+    else:
+        import torch
+        C = torch.zeros((n, lat.T), dtype=torch.complex128, device=A.device)
+    _check(load().tm_correlator(lat._h, _addr(A), _addr(Xa), n, _addr(C), _stream(stream)),
+           "tm_correlator")
+    if isinstance(C, np.ndarray):
+        _sync()
+    return C[0] if single else C
