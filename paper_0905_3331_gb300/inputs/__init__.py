@@ -163,3 +163,36 @@ WORKLOADS = {
     "8^4": Workload("8^4", 8, 8, 0.5, 0.1632, 0.002),
     "12^3x24": Workload("12^3x24", 24, 12, 0.5, 0.1632, 0.002),
 }
+
+
+@dataclass(frozen=True)
+class BatchedSystem:
+    """One system of the batched workload: its lattice problem (gauge field and kappa from the
+    workload), its own bare twisted mass, and its source (a unit point source at the origin with
+    spin-colour index 3 s + c, or the workload's Gaussian source number `index`)."""
+    workload: Workload
+    mu: float
+    kind: str   # "point" or "gaussian"
+    index: int
+
+    def source(self) -> np.ndarray:
+        w = self.workload
+        if self.kind == "point":
+            return point_source(w.T, w.L, self.index // 3, self.index % 3)
+        return w.source(self.index)
+
+
+BATCHED_MU = (0.002, 0.005, 0.01)
+
+
+def batched_workload():
+    """The batched workload: the 12 spin-colour point sources of one propagator on 24^3 x 48
+    (eps 0.6, kappa 0.1615, mu 0.003), then the 8^4, 12^3 x 24 and 16^3 x 32 lattices (eps 0.5,
+    kappa 0.1632) with 4 Gaussian sources each for every mu in {0.002, 0.005, 0.01}: 48 systems
+    on 4 gauge fields."""
+    big = WORKLOADS["24^3x48"]
+    out = [BatchedSystem(big, big.mu, "point", j) for j in range(12)]
+    for name in ("8^4", "12^3x24", "16^3x32"):
+        for mu in BATCHED_MU:
+            out += [BatchedSystem(WORKLOADS[name], mu, "gaussian", k) for k in range(4)]
+    return out

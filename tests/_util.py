@@ -35,3 +35,12 @@ def rel(a, b):
     a = np.asarray(a).reshape(-1)
     b = np.asarray(b).reshape(-1)
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def site_rel_max(a, b):
+    """Largest per-site relative error: max over sites of ||a_x - b_x|| / ||b_x|| (the 12 complex
+    components of each site; arrays shaped (..., 4, 3)).  A wrong site or a wrong boundary slab
+    shows here even where the global 2-norm would hide it."""
+    a = np.asarray(a).reshape(-1, 12)
+    b = np.asarray(b).reshape(-1, 12)
+    return float((np.linalg.norm(a - b, axis=1) / np.maximum(np.linalg.norm(b, axis=1), 1e-300)).max())

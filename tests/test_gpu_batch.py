@@ -81,6 +81,35 @@ def test_twelve_point_sources_8x8x8x8():
     lat.close()
 
 
+@pytest.mark.parametrize("sloppy,delta", [((F32, LINK12), 1e-3), ((F16, LINK12), 0.1)])
+def test_batched_workload_at_full_size(sloppy, delta):
+    """The batched workload at full size in ONE batched solve: the 12 spin-colour point sources on
+    24^3 x 48 (eps 0.6, kappa 0.1615, mu 0.003) and the 8^4, 12^3 x 24 and 16^3 x 32 lattices
+    (eps 0.5, kappa 0.1632) with 4 Gaussian sources for each mu in {0.002, 0.005, 0.01} -- 48
+    systems on 4 gauge fields.  Every solution is checked with the ORACLE's M on the full lattice:
+    ||phi - M x|| / ||phi|| < 1e-10."""
+    defs = inputs.batched_workload()
+    lats, gauges = {}, {}
+    for d in defs:
+        w = d.workload
+        if w.name not in lats:
+            gauges[w.name] = w.gauge()
+            lats[w.name] = Lattice(w.T, w.L, w.kappa, w.mu)
+            lats[w.name].set_gauge(gauges[w.name])
+    systems = []
+    for d in defs:
+        b = torch.from_numpy(d.source()).to(dev())
+        systems.append((lats[d.workload.name], d.mu, torch.zeros_like(b), b))
+    infos = solve_cg_batch(systems, sloppy_prec=sloppy[0], sloppy_link=sloppy[1], delta=delta)
+    for d, (lat, mu, x, b), info in zip(defs, systems, infos):
+        w = d.workload
+        res = oracle_rel_residual(w.T, w.L, gauges[w.name], d.source(), x.cpu().numpy(), w.kappa, d.mu)
+        assert res < 1e-10, (w.name, d.mu, d.kind, d.index, res)
+        assert info.status == 0 and info.true_rel_residual < 1e-10
+    for lat in lats.values():
+        lat.close()
+
+
 def test_batch_edge_cases():
     w = inputs.WORKLOADS["4^4"]
     U = w.gauge()
