@@ -2,11 +2,15 @@
 """Benchmark: even/odd CG solves/s to an FP64 true residual of 1e-10 (mixed precision vs
 FP64) and the hopping kernel's bandwidth against the measured HBM roofline.
 
-Workload (default): the 16^3 x 32 lattice, random SU(3) links exp(i eps H) with eps = 0.5,
-kappa = 0.1632, mu = 0.004 (mu~ = 2 kappa mu), Gaussian source.  One step = one complete
-solve of M x = b through the C ABI: packing, source preparation, CG on Qhat+ Qhat- with the
-sloppy operator and FP64 reliable updates, reconstruction and the FP64 true-residual check.
-The L2 cache is flushed (a 512 MB write) before every step.
+Headline workload (default): the 48^3 x 96 lattice, random SU(3) links exp(i eps H) with
+eps = 0.6, kappa = 0.1615, mu = 0.0015 (mu~ = 2 kappa mu), Gaussian source -- the largest of
+the single-GPU workloads.  One step = one complete solve of M x = b through the C ABI: packing,
+source preparation, CG on Qhat+ Qhat- with the sloppy operator in FP16 storage with 8-real
+links and FP32 arithmetic, reliable updates (FP32 recomputations between FP64 ones),
+reconstruction and the FP64 true-residual check.  The L2 cache is flushed (a 512 MB write)
+before every step.  Beside the headline the line carries the 16^3 x 32 throughput baseline
+(FP64 and FP32 hopping kernels, FP64 CG), the 32^3 x 64 precision form, the batched workload
+and the other solvers as extra objects.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -31,12 +35,17 @@ sys.path.insert(0, ROOT)
 METRIC = "Dslash GB/s & % HBM roofline; CG solves/sec to 1e-10 FP64 residual, mixed vs FP64"
 HOP_FLOPS = 1320  # per output site per hopping application (8 hops x 168 flops - 24)
 REF_TOTAL_SECONDS = 90.0  # host time of the reference arm's timed steps together
-# dram__bytes_read.sum + dram__bytes_write.sum of one hopping-kernel launch, from ncu captures
-# (profiles/), keyed by sloppy form, lattice and kernel choice (threads per site; 3 = the
-# software-pipelined one-thread kernel), from ncu --set full captures of the current kernels:
-# pipelined on 16^3 x 32 (profiles/hop_f32_12_16x32_pipelined_full.md), plain on 32^3 x 64
-# (profiles/hop_f32_12_16x32_and_32x64_full.md)
-NCU_TRAFFIC = {("f32:12", "16^3x32", 3): 31485184.0, ("f32:12", "32^3x64", 1): 600914688.0}
+# Solver settings of the mixed solve per workload: sloppy storage:links, reliable-update delta and
+# the arithmetic of the residual recomputations between FP64 ones.  FP16 storage keeps the
+# iterated residual trustworthy over a factor ~0.3 only; FP32 storage over ~1e-5 on 16^3 x 32
+# (88 iterations) and ~1e-3 on the longer solves.
+SOLVER_DEFAULTS = {"48^3x96": ("f16:8", 0.3, "f32"), "32^3x64": ("f32:12", 1e-3, "f64"),
+                   "24^3x48": ("f32:12", 1e-3, "f64"), "16^3x32": ("f32:12", 1e-5, "f64")}
+# Iterations of the FP64 CG to 1e-10 on each workload's first Gaussian source, measured on GB300
+# by this library's FP64 CG (the same count the oracle's CG reaches up to rounding): the reference
+# arm extrapolates its bounded sample to them where one complete oracle solve would take longer
+# than the run may (48^3 x 96: about 50 minutes on 16 Grace cores).
+FP64_CG_ITERS = {"48^3x96": 522, "32^3x64": 437, "16^3x32": 88}
 HOP_VARIANT = {1: "1 thread per site", 2: "2 threads per site", 4: "4 threads per site",
                3: "1 thread per site, pipelined loads"}
 
@@ -60,6 +69,41 @@ def hop_naive_bytes_per_site(prec: int, nreal: int) -> int:
 def parse_sloppy(s: str):
     p, l = s.split(":")
     return {"f32": 1, "f16": 2}[p], int(l)
+
+
+def kernel_sources_hash(prec: int) -> str:
+    """Digest of the sources of the one-flavour hopping kernel in storage precision `prec` (the
+    kernel template, the shared device helpers and the precision's instantiation unit): an ncu
+    traffic figure is reported only while the kernel it was taken of is unchanged."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_0905_3331_gb300", "csrc")
+    unit = {0: "tm_dslash_f64.cu", 1: "tm_dslash_f32.cu", 2: "tm_dslash_f16.cu", 3: "tm_dslash_df64.cu"}[prec]
+    pair_unit = {1: "tm_dslash_pair_f32.cu", 2: "tm_dslash_pair_f16.cu"}.get(prec, unit)
+    h = hashlib.sha256()
+    for f in ("tm_dslash.cuh", "tm_dslash_pair.cuh", "tm_internal.cuh", unit, pair_unit):
+        path = os.path.join(csrc, f)
+        if os.path.exists(path):
+            with open(path, "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def ncu_traffic(form: str, lattice: str, variant: int, prec: int):
+    """DRAM bytes (read + write) of one launch of the hopping kernel from a committed ncu summary:
+    a line `bench-traffic: form=F lattice=L kernel=K sources=H bytes=N` in one of the files under
+    profiles/, for this form, lattice, kernel choice and the current kernel sources.  Returns
+    (bytes, file) or (None, None)."""
+    import glob
+    import re
+    want = kernel_sources_hash(prec)
+    pat = re.compile(r"bench-traffic: form=(\S+) lattice=(\S+) kernel=(\d+) sources=([0-9a-f]+) bytes=(\d+)")
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        with open(path) as fh:
+            for line in fh:
+                m = pat.search(line)
+                if m and (m.group(1), m.group(2), int(m.group(3)), m.group(4)) == (form, lattice, variant, want):
+                    return float(m.group(5)), os.path.relpath(path, ROOT)
+    return None, None
 
 
 def peaks():
@@ -155,12 +199,57 @@ def whole_job_rate(units_per_rank: int, world: int, t_max: float) -> float:
 
 
 # ------------------------------------------------------------------ GPU arm ---
+def hop_launch_time(lat, dev, prec, nreal, half, n, flush, clean, cold=True):
+    """Mean time of one tm_apply_hopping_eo launch on `lat` in (prec, nreal) storage, from per-launch
+    CUDA events on the launching stream.  Cold: before each launch L2 is flushed (512 MB write) and
+    cleaned (a read pass over another buffer twice the size of L2, so that the flush's dirty lines
+    are written back first: the cold state ncu measures in); mean of the middle 80% of launches.
+    Warm: n launches back to back."""
+    import torch
+    stream = torch.cuda.current_stream()
+    nb = lat.half_field_bytes(prec)
+    din = torch.empty(nb, dtype=torch.uint8, device=dev)
+    dout = torch.empty(nb, dtype=torch.uint8, device=dev)
+    lat.pack_half(prec, din, half)
+    lat.apply_hopping_eo(1, dout, din, prec, nreal)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if cold:
+        ts = []
+        for k in range(n):
+            flush.zero_()
+            clean.sum()
+            e0.record(stream)
+            lat.apply_hopping_eo(k & 1, dout, din, prec, nreal)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        return trimmed_mean(ts)
+    e0.record(stream)
+    for k in range(n):
+        lat.apply_hopping_eo(k & 1, dout, din, prec, nreal)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3 / n
+
+
+def hop_entry(prec, nreal, h, t_cold, t_warm, peak):
+    by = hop_bytes_per_site(prec, nreal) * h
+    e = {"bytes_per_site": hop_bytes_per_site(prec, nreal), "us_cold": t_cold * 1e6,
+         "gbs_cold": by / t_cold / 1e9,
+         "gbs_naive_count_cold": hop_naive_bytes_per_site(prec, nreal) * h / t_cold / 1e9,
+         "frac_hbm_cold": by / t_cold / 1e9 / peak, "gflops_cold": HOP_FLOPS * h / t_cold / 1e9}
+    if t_warm is not None:
+        e.update({"us_l2_resident": t_warm * 1e6, "gbs_l2_resident": by / t_warm / 1e9,
+                  "gflops_l2_resident": HOP_FLOPS * h / t_warm / 1e9})
+    return {k: (round(v, 4) if isinstance(v, float) else v) for k, v in e.items()}
+
+
 def run_gpu(args):
     import numpy as np
     import torch
 
-    from paper_0905_3331_gb300 import (CG_FP64, CG_RELIABLE, F32, F64, LINK18, Lattice, inputs,
-                                       launch_count)
+    from paper_0905_3331_gb300 import CG_FP64, CG_RELIABLE, F32, F64, Lattice, inputs, launch_count
     from paper_0905_3331_gb300 import build as libbuild
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -175,7 +264,12 @@ def run_gpu(args):
     libbuild.build()
 
     w = inputs.WORKLOADS[args.workload]
+    d_sloppy, d_delta, d_upd = SOLVER_DEFAULTS.get(w.name, ("f32:12", 1e-3, "f64"))
+    args.sloppy = args.sloppy or d_sloppy
+    args.delta = args.delta if args.delta is not None else d_delta
+    args.update_prec = args.update_prec or d_upd
     sp, sl = parse_sloppy(args.sloppy)
+    upd = {"f64": F64, "f32": F32}[args.update_prec]
     U = w.gauge()
     phi = w.source(rank)
     lat = Lattice(w.T, w.L, w.kappa, w.mu)
@@ -184,7 +278,7 @@ def run_gpu(args):
     x = torch.zeros_like(b)
     flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
-    mixed_kw = dict(mode=CG_RELIABLE, sloppy_prec=sp, sloppy_link=sl, delta=args.delta)
+    mixed_kw = dict(mode=CG_RELIABLE, sloppy_prec=sp, sloppy_link=sl, delta=args.delta, update_prec=upd)
 
     def barrier():
         if world > 1:
@@ -216,7 +310,7 @@ def run_gpu(args):
             total += ev[2 * k].elapsed_time(ev[2 * k + 1]) / 1e3
         return total, infos
 
-    # warm-up (allocations, gauge copies of every form used)
+    # warm-up (allocations, gauge copies of every form used, tuning, stage graphs)
     for _ in range(args.warmup):
         timed_solves(1, mixed_kw)
 
@@ -231,120 +325,79 @@ def run_gpu(args):
     t_mixed = max_over_ranks(t_mixed)
     worst_res = max(i.true_rel_residual for i in infos)
 
-    # ---- FP64 CG on the same system (the comparison the metric asks for)
-    timed_solves(1, dict(mode=CG_FP64))
+    # ---- FP64 CG on the same system (the comparison the metric asks for); its stage graphs are
+    # captured in the first solve, a few ms against seconds per solve at this size
     n64 = max(1, min(args.steps, args.fp64_steps))
     t64, infos64 = timed_solves(n64, dict(mode=CG_FP64))
     t64 = max_over_ranks(t64)
 
     # ---- end to end: same solve through the C ABI with pinned HOST buffers
+    n_e2e = max(1, min(args.steps, args.e2e_steps))
     timed_solves(1, mixed_kw, host=True)
-    t_e2e, _ = timed_solves(max(1, min(args.steps, 10)), mixed_kw, host=True)
-    n_e2e = max(1, min(args.steps, 10))
+    t_e2e, _ = timed_solves(n_e2e, mixed_kw, host=True)
     t_e2e = max_over_ranks(t_e2e)
 
-    # ---- hopping kernel: per-launch CUDA events, L2 flushed before each launch
-    def hop_time(prec, nreal, n, cold=True):
-        nb = lat.half_field_bytes(prec)
-        din = torch.empty(nb, dtype=torch.uint8, device=dev)
-        dout = torch.empty(nb, dtype=torch.uint8, device=dev)
-        half = torch.from_numpy(np.ascontiguousarray(
-            phi.reshape(-1, 4, 3)[: w.V // 2])).to(dev)
-        lat.pack_half(prec, din, half)
-        lat.apply_hopping_eo(1, dout, din, prec, nreal)
-        torch.cuda.synchronize()
-        if cold:
-            ts = []
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            for k in range(n):
-                # write flush, then a read pass over another buffer twice the size of L2: the
-                # flush's dirty lines are written back before the timed launch, which starts
-                # with L2 full of clean unrelated lines (the cold state ncu measures in)
-                flush.zero_()
-                clean.sum()
-                e0.record(stream)
-                lat.apply_hopping_eo(k & 1, dout, din, prec, nreal)
-                e1.record(stream)
-                torch.cuda.synchronize()
-                ts.append(e0.elapsed_time(e1) / 1e3)
-            return trimmed_mean(ts)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for k in range(n):
-            lat.apply_hopping_eo(k & 1, dout, din, prec, nreal)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / 1e3 / n
-
+    # ---- the sloppy hopping kernel of the headline solve, per launch, L2 flushed and cleaned
     h = w.V // 2
     peak, peak_kind = peaks()
     clean = torch.ones(256 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
-    dslash = {}
-    for name, (prec, nreal) in {"f64_18": (F64, 18), "f32_18": (F32, LINK18),
-                                f"{args.sloppy.replace(':', '_')}": (sp, sl)}.items():
-        tc = hop_time(prec, nreal, args.hop_iters)
-        tw = hop_time(prec, nreal, 1000, cold=False)
-        by = hop_bytes_per_site(prec, nreal) * h
-        dslash[name] = {"bytes_per_site": hop_bytes_per_site(prec, nreal),
-                        "threads_per_site": lat.hop_threads(prec, nreal),
-                        "us_cold": tc * 1e6, "gbs_cold": by / tc / 1e9,
-                        "gbs_naive_count_cold": hop_naive_bytes_per_site(prec, nreal) * h / tc / 1e9,
-                        "frac_hbm_cold": by / tc / 1e9 / peak,
-                        "gflops_cold": HOP_FLOPS * h / tc / 1e9,
-                        "us_l2_resident": tw * 1e6, "gbs_l2_resident": by / tw / 1e9,
-                        "gflops_l2_resident": HOP_FLOPS * h / tw / 1e9}
-    skey = args.sloppy.replace(":", "_")
-    # DRAM bytes of one launch of the sloppy kernel from an ncu capture (profiles/), valid
-    # while that kernel is unchanged; other forms or lattices report null
-    top = dslash[skey]
-    if args.traffic is None and (args.sloppy, w.name, top["threads_per_site"]) in NCU_TRAFFIC:
-        args.traffic = NCU_TRAFFIC[(args.sloppy, w.name, top["threads_per_site"])]
-    variant = HOP_VARIANT.get(top["threads_per_site"], str(top["threads_per_site"]))
-    roofline = {"bound": "hbm", "kernel": f"hop_kernel ({args.sloppy} sloppy form, {variant})",
+    half = torch.from_numpy(np.ascontiguousarray(phi.reshape(-1, 4, 3)[:h])).to(dev)
+    t_hop = hop_launch_time(lat, dev, sp, sl, half, args.hop_iters, flush, clean)
+    variant_id = lat.hop_threads(sp, sl)
+    top = hop_entry(sp, sl, h, t_hop, None, peak)
+    traffic, traffic_file = ncu_traffic(args.sloppy, w.name, variant_id, sp)
+    if args.traffic is not None:
+        traffic, traffic_file = args.traffic, "--traffic"
+    variant = HOP_VARIANT.get(variant_id, str(variant_id))
+    roofline = {"bound": "hbm", "kernel": f"hop_kernel ({args.sloppy} sloppy form, {variant}) on {w.name}",
                 "achieved": round(top["gbs_cold"], 1), "peak": peak, "unit": "GB/s",
-                "frac": round(top["gbs_cold"] / peak, 4),
-                "traffic": args.traffic, "peak_kind": peak_kind,
-                "timing": "per-launch CUDA events, mean of the middle 80% of the launches; before each "
-                          "launch L2 flushed (512 MB write) and cleaned (256 MB read)"}
-
-    batched = None if args.no_batched else batched_measurement(args, dev)
-    extras = None if args.no_extras else extra_measurements(args, dev, w, U, phi)
-    precision = None if args.no_precision_form else precision_form_measurement(args, dev)
+                "frac": round(top["gbs_cold"] / peak, 4), "traffic": traffic,
+                "traffic_source": traffic_file, "peak_kind": peak_kind,
+                "bytes_per_launch": hop_bytes_per_site(sp, sl) * h,
+                "us_per_launch": round(t_hop * 1e6, 3),
+                "timing": f"{args.hop_iters} launches, per-launch CUDA events, mean of the middle 80%; before "
+                          "each launch L2 flushed (512 MB write) and cleaned (256 MB read)"}
+    del half, clean
 
     n_units = args.steps * world
     value = whole_job_rate(args.steps, world, t_mixed)
     result = {
-        "metric": METRIC, "value": round(value, 3), "unit": "solves/s", "n_gpus": world,
+        "metric": METRIC, "value": round(value, 5), "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(t_mixed / args.steps * 1e3, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": f"{w.name} lattice, eps {w.eps}, kappa {w.kappa}, mu {w.mu}, "
-                               "Gaussian source; even/odd CG to FP64 true residual 1e-10",
-                   "lattice": w.name, "solver": f"reliable-update CG, sloppy {args.sloppy}, "
-                   f"delta {args.delta}", "l2": "flushed (512 MB write) before every step",
+        "dtype": "f16 storage, f32 arithmetic, f64 residuals" if sp == 2 else "f32+f64", "data": "synthetic",
+        "config": {"workload": f"{w.name} lattice (V = {w.V}), random SU(3) links eps {w.eps}, kappa {w.kappa}, "
+                               f"mu {w.mu}, Gaussian source; even/odd CG to FP64 true residual 1e-10",
+                   "lattice": w.name, "solver": f"reliable-update CG, sloppy {args.sloppy} (FP32 arithmetic), "
+                   f"delta {args.delta}, {args.update_prec.upper()} recomputations between FP64 ones",
+                   "l2": "flushed (512 MB write) before every step; inputs also larger than L2",
                    "parallelism": f"replicas x{world} (independent systems)"},
-        "mixed_cg": {"solves_per_s": round(value, 3), "iters": infos[-1].iters,
-                     "reliable_updates": infos[-1].reliable_updates,
+        "mixed_cg": {"solves_per_s": round(value, 5), "s_per_solve": round(t_mixed / args.steps, 4),
+                     "iters": infos[-1].iters, "reliable_updates": infos[-1].reliable_updates,
                      "true_rel_residual": worst_res},
-        "fp64_cg": {"solves_per_s": round(n64 * world / t64, 3), "iters": infos64[-1].iters,
-                    "true_rel_residual": infos64[-1].true_rel_residual},
+        "fp64_cg": {"solves_per_s": round(n64 * world / t64, 5), "s_per_solve": round(t64 / n64, 4),
+                    "iters": infos64[-1].iters, "true_rel_residual": infos64[-1].true_rel_residual},
         "speedup_mixed_vs_fp64": round((n_units / t_mixed) / (n64 * world / t64), 3),
-        "dslash": {k: {kk: (round(vv, 3) if isinstance(vv, float) else vv)
-                       for kk, vv in v.items()} for k, v in dslash.items()},
         "roofline": roofline,
-        "e2e": {"value": round(n_e2e * world / t_e2e, 3), "unit": "solves/s",
+        "e2e": {"value": round(n_e2e * world / t_e2e, 5), "unit": "solves/s",
                 "h2d_bytes_per_step": int(phi.nbytes), "d2h_bytes_per_step": int(phi.nbytes)},
         "gpu_launches": int(launches),
-        "batched": batched,
-        "solver_variants": extras,
-        "precision_form": precision,
         "clocks": clocks,
     }
+    lat.close()
+    del b, x
+    torch.cuda.empty_cache()
+    if not args.no_extras:
+        result["throughput_baseline"] = throughput_baseline(args, dev, flush)
+    if not args.no_precision_form:
+        result["precision_form"] = precision_form_measurement(args, dev)
+    if not args.no_batched:
+        result["batched"] = batched_measurement(args, dev)
+    if not args.no_extras:
+        result["solver_variants"] = extra_measurements(args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(w, U, phi, infos64[-1].iters, args.cpu_seconds)
-        result["cpu_oracle_operator"] = cpu_oracle_operator(w, U, phi, dslash["f64_18"]["us_cold"])
-    lat.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -352,78 +405,92 @@ def run_gpu(args):
         print(json.dumps(result))
 
 
-# --------------------------------------------------------------- batched ---
-def batched_measurement(args, dev):
-    """The batched workload: 12 spin-colour point sources on 24^3 x 48 (eps 0.6, kappa 0.1615,
-    mu 0.003) plus 8^4, 12^3 x 24 and 16^3 x 32 lattices (eps 0.5, kappa 0.1632) with 4
-    Gaussian sources for each mu in {0.002, 0.005, 0.01}: 48 systems in one batched solve,
-    against the same systems solved one at a time.  Same solver settings as the main line, except
-    the reliable-update delta (--batched-delta): the 24^3 x 48 systems run several hundred
-    iterations, and the FP32 recursion drifts below delta ~ 1e-4 there."""
+# ----------------------------------------------------- 16^3 x 32 baseline ---
+def throughput_baseline(args, dev, flush):
+    """The 16^3 x 32 throughput baseline (eps 0.5, kappa 0.1632, mu 0.004): the hopping operator
+    in FP64 and FP32 with 18-real links, 1000 applications back to back (L2-resident: the whole
+    working set fits in the 129 MB L2) and per launch with L2 flushed and cleaned; FP64 CG to 1e-10
+    on one Gaussian source; the mixed solve (FP32 storage, 12-real links, delta 1e-5); and the
+    oracle's FP64 hopping on the host beside the FP64 kernel."""
+    import numpy as np
     import torch
 
-    from paper_0905_3331_gb300 import CG_FP64, CG_RELIABLE, Lattice, inputs, solve_cg_batch
-    sp, sl = parse_sloppy(args.sloppy)
-    big = inputs.WORKLOADS["24^3x48"]
-    lats, systems = [], []
-    lat = Lattice(big.T, big.L, big.kappa, big.mu)
-    lat.set_gauge(big.gauge())
-    lats.append(lat)
-    for s in range(4):
-        for c in range(3):
-            b = torch.from_numpy(inputs.point_source(big.T, big.L, s, c)).to(dev)
-            systems.append((lat, big.mu, torch.zeros_like(b), b))
-    for name in ("8^4", "12^3x24", "16^3x32"):
-        w = inputs.WORKLOADS[name]
-        lat = Lattice(w.T, w.L, 0.1632, 0.002)
-        lat.set_gauge(inputs.random_gauge(w.T, w.L, 0.5, w.gauge_seed))
-        lats.append(lat)
-        for mu in (0.002, 0.005, 0.01):
-            for k in range(4):
-                b = torch.from_numpy(inputs.gaussian_spinor(w.T, w.L, 2 + k)).to(dev)
-                systems.append((lat, mu, torch.zeros_like(b), b))
-    kw = dict(sloppy_prec=sp, sloppy_link=sl, delta=args.batched_delta)
-    solve_cg_batch(systems, **kw)  # warm-up (gauge copies, allocations)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    infos = solve_cg_batch(systems, **kw)
-    torch.cuda.synchronize()
-    t_batch = time.perf_counter() - t0
-    # the 12 point sources alone, batched, against one FP64 CG solve on the same lattice (the
-    # per-solve comparison of mixed batched CG with plain FP64 CG)
+    from paper_0905_3331_gb300 import CG_FP64, CG_RELIABLE, F32, F64, Lattice, inputs
+    w = inputs.WORKLOADS["16^3x32"]
+    U, phi = w.gauge(), w.source()
+    lat = Lattice(w.T, w.L, w.kappa, w.mu)
+    lat.set_gauge(torch.from_numpy(U).to(dev))
+    h = w.V // 2
+    peak, _ = peaks()
+    clean = torch.ones(256 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+    half = torch.from_numpy(np.ascontiguousarray(phi.reshape(-1, 4, 3)[:h])).to(dev)
+    dslash = {}
+    for name, (prec, nreal) in {"f64_18": (F64, 18), "f32_18": (F32, 18), "f32_12": (F32, 12)}.items():
+        tc = hop_launch_time(lat, dev, prec, nreal, half, 200, flush, clean)
+        tw = hop_launch_time(lat, dev, prec, nreal, half, 1000, flush, clean, cold=False)
+        dslash[name] = {**hop_entry(prec, nreal, h, tc, tw, peak), "threads_per_site": lat.hop_threads(prec, nreal)}
+    b = torch.from_numpy(phi).to(dev)
+    x = torch.zeros_like(b)
+    out = {"workload": f"{w.name} lattice, eps {w.eps}, kappa {w.kappa}, mu {w.mu}, Gaussian source",
+           "dslash": dslash,
+           "dslash_timing": "cold: 200 launches, per-launch CUDA events, L2 flushed and cleaned before each, "
+                            "mean of the middle 80%; l2_resident: 1000 launches back to back"}
+    for name, kw, n in (("fp64_cg", dict(mode=CG_FP64), 3),
+                        ("mixed_cg_f32_12", dict(mode=CG_RELIABLE, sloppy_prec=F32, sloppy_link=12, delta=1e-5), 20)):
+        lat.solve_cg(x, b, tol=1e-10, **kw)  # warm-up (gauge copy, tuning, graphs)
+        t, infos = _timed(lambda: lat.solve_cg(x, b, tol=1e-10, **kw), n, dev)
+        out[name] = {"solves_per_s": round(n / t, 3), "iters": infos[-1].iters,
+                     "reliable_updates": infos[-1].reliable_updates,
+                     "true_rel_residual": infos[-1].true_rel_residual}
+    out["speedup_mixed_vs_fp64"] = round(out["mixed_cg_f32_12"]["solves_per_s"] / out["fp64_cg"]["solves_per_s"], 3)
+    lat.close()
+    if not args.no_cpu_baseline:
+        out["cpu_oracle_operator"] = cpu_oracle_operator(w, U, phi, dslash["f64_18"]["us_cold"])
+    return out
+
+
+# --------------------------------------------------------------- batched ---
+def batched_measurement(args, dev):
+    """The batched workload (12 spin-colour point sources on 24^3 x 48 plus 8^4, 12^3 x 24 and
+    16^3 x 32 lattices with 4 Gaussian sources for each mu in {0.002, 0.005, 0.01}: 48 systems on
+    4 gauge fields) in one batched solve, against the same systems solved one at a time; the 12
+    point sources alone against one FP64 CG solve on their lattice; and the meson contraction of
+    the 12 point-source solutions.  FP32 storage with 12-real links, delta --batched-delta (the
+    24^3 x 48 systems run several hundred iterations, and the FP32 recursion drifts below delta ~
+    1e-4 there).  CUDA events on the launching stream; L2 flushed before each timed call."""
+    import torch
+
+    from paper_0905_3331_gb300 import CG_FP64, CG_RELIABLE, F32, Lattice, inputs, solve_cg_batch
+    defs = inputs.batched_workload()
+    lats, systems = {}, []
+    for d in defs:
+        wl = d.workload
+        if wl.name not in lats:
+            lats[wl.name] = Lattice(wl.T, wl.L, wl.kappa, wl.mu)
+            lats[wl.name].set_gauge(wl.gauge())
+        b = torch.from_numpy(d.source()).to(dev)
+        systems.append((lats[wl.name], d.mu, torch.zeros_like(b), b))
+    kw = dict(sloppy_prec=F32, sloppy_link=12, delta=args.batched_delta)
+    solve_cg_batch(systems, **kw)  # warm-up (gauge copies, allocations, tuning)
+    t_batch, (infos,) = _timed(lambda: solve_cg_batch(systems, **kw), 1, dev)
     pts = systems[:12]
     solve_cg_batch(pts, **kw)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    solve_cg_batch(pts, **kw)
-    torch.cuda.synchronize()
-    t_pts = time.perf_counter() - t0
+    t_pts, _ = _timed(lambda: solve_cg_batch(pts, **kw), 1, dev)
+    big = defs[0].workload
     lat0, _, x0, b0 = pts[0]
     lat0.set_params(big.kappa, big.mu)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    i64 = lat0.solve_cg(x0, b0, tol=1e-10, mode=CG_FP64)
-    torch.cuda.synchronize()
-    t64 = time.perf_counter() - t0
+    x64 = torch.zeros_like(b0)
+    t64, (i64,) = _timed(lambda: lat0.solve_cg(x64, b0, tol=1e-10, mode=CG_FP64), 1, dev)
+    del x64
     point_sources = {"workload": f"12 point sources on {big.name}", "batched_s_per_solve": round(t_pts / 12, 4),
                      "fp64_s_per_solve": round(t64, 4), "fp64_iters": i64.iters,
                      "speedup_vs_fp64": round(t64 / (t_pts / 12), 2)}
     # meson contraction of the 12 point-source solutions (the correlators' building block)
     props = torch.stack([systems[k][2] for k in range(12)])
     Aout = torch.empty((big.T, 12, 12, 2), dtype=torch.float64, device=dev)
-    lats[0].meson_contract(props, Aout)
-    stream = torch.cuda.current_stream()
-    t_con = 0.0
-    flush = torch.empty(512 * 2 ** 20, dtype=torch.uint8, device=dev)
-    for _ in range(5):
-        flush.zero_()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        lats[0].meson_contract(props, Aout)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        t_con += e0.elapsed_time(e1) / 1e3 / 5
+    lat0.meson_contract(props, Aout)
+    t_con, _ = _timed(lambda: lat0.meson_contract(props, Aout), 5, dev)
+    t_con /= 5
     con_bytes = props.numel() * props.element_size() + Aout.numel() * Aout.element_size()
     hbm, _ = peaks()
     # FP64 flops: 78 hermitian pairs x 12 components x 8 flop per site (conj(a) b accumulated)
@@ -435,28 +502,23 @@ def batched_measurement(args, dev):
                    "flops": int(con_flops), "bound": "fp64 alu (about 3.3 flop per byte)",
                    "timing": "mean of 5 calls, CUDA events, L2 flushed before each"}
     del props
-    t_single = 0.0
-    iters_single = 0
+    t_single, iters_single = 0.0, 0
     for lat_, mu, x, b in systems:
         lat_.set_params(lat_.kappa, mu)
         x.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        info = lat_.solve_cg(x, b, mode=CG_RELIABLE, **kw)
-        torch.cuda.synchronize()
-        t_single += time.perf_counter() - t0
+        t, (info,) = _timed(lambda: lat_.solve_cg(x, b, mode=CG_RELIABLE, **kw), 1, dev)
+        t_single += t
         iters_single += info.iters
-    for lat_ in lats:
+    for lat_ in lats.values():
         lat_.close()
     n = len(systems)
     return {"workload": "12 point sources on 24^3x48 + {8^4, 12^3x24, 16^3x32} x 3 mu x 4 sources",
-            "delta": args.batched_delta, "systems": n, "systems_per_s": round(n / t_batch, 3),
-            "unbatched_systems_per_s": round(n / t_single, 3),
+            "sloppy": "f32:12", "delta": args.batched_delta, "systems": n,
+            "systems_per_s": round(n / t_batch, 3), "unbatched_systems_per_s": round(n / t_single, 3),
             "speedup": round(t_single / t_batch, 3),
             "max_true_rel_residual": max(i.true_rel_residual for i in infos),
             "iters_batched": sum(i.iters for i in infos), "iters_unbatched": iters_single,
-            "timing": "host wall clock around one synchronised call (batched) / the sum of "
-                      "the single solves (unbatched)",
+            "timing": "CUDA events around one batched call / the sum of the single solves, L2 flushed before each",
             "point_sources": point_sources,
             "meson_contract": contraction}
 
@@ -543,15 +605,17 @@ def _timed(fn, n, dev):
     return total, infos
 
 
-def extra_measurements(args, dev, w, U, phi):
-    """BiCGstab on Mhat against CG on the normal equations, the chronological guess along a
-    sequence of slowly varying sources, and the meson contraction.  Same gauge field and source
-    as the main line."""
+def extra_measurements(args, dev):
+    """On the 16^3 x 32 workload's gauge field and source: BiCGstab and MR on Mhat against CG on
+    the normal equations, the chronological guess along a sequence of slowly varying sources, and
+    the non-degenerate doublet solve (FP32 sloppy storage with 12-real links, delta 1e-5)."""
     import numpy as np
     import torch
 
-    from paper_0905_3331_gb300 import CG_FP64, CG_RELIABLE, F64, Lattice, inputs
-    sp, sl = parse_sloppy(args.sloppy)
+    from paper_0905_3331_gb300 import CG_FP64, CG_RELIABLE, F32, F64, Lattice, inputs
+    w = inputs.WORKLOADS["16^3x32"]
+    U, phi = w.gauge(), w.source()
+    sp, sl, delta = F32, 12, 1e-5
     out = {}
     b = torch.from_numpy(phi).to(dev)
     x = torch.zeros_like(b)
@@ -560,9 +624,9 @@ def extra_measurements(args, dev, w, U, phi):
     kb = 0.13
     lat = Lattice(w.T, w.L, kb, w.mu)
     lat.set_gauge(torch.from_numpy(U).to(dev))
-    mixed = dict(mode=CG_RELIABLE, sloppy_prec=sp, sloppy_link=sl, delta=args.delta)
+    mixed = dict(mode=CG_RELIABLE, sloppy_prec=sp, sloppy_link=sl, delta=delta)
     rows = {}
-    mixed_mr = dict(mode=CG_RELIABLE, sloppy_link=sl, delta=args.delta)
+    mixed_mr = dict(mode=CG_RELIABLE, sloppy_link=sl, delta=delta)
     for name, fn, kw in (("cg_fp64", lat.solve_cg, dict(mode=CG_FP64)),
                          ("bicgstab_fp64", lat.solve_bicgstab, dict(mode=CG_FP64)),
                          ("mr_fp64", lat.solve_mr, dict(mode=CG_FP64)),
@@ -582,7 +646,7 @@ def extra_measurements(args, dev, w, U, phi):
     lat.close()
     out["bicgstab"] = {"workload": f"{w.name} gauge field and source at kappa {kb} "
                                    "(spectrum of Mhat in Re > 0), mu " + str(w.mu),
-                       "sloppy": f"{args.sloppy}, delta {args.delta}", **rows,
+                       "sloppy": f"f32:{sl}, delta {delta}", **rows,
                        "timing": "3 solves each, CUDA events, L2 flushed before each"}
     # ---- chronological guess: 8 sources phi_k = phi + 0.02 k eta1 + 0.0005 k^2 eta2, normal
     # equations solved cold and from the guess of the last 4 solutions
@@ -624,7 +688,7 @@ def extra_measurements(args, dev, w, U, phi):
     xd = torch.zeros_like(bd)
     drows = {}
     for name, kw in (("fp64", dict(mode=CG_FP64)),
-                     ("mixed", dict(mode=CG_RELIABLE, sloppy_link=sl, delta=args.delta))):
+                     ("mixed", dict(mode=CG_RELIABLE, sloppy_link=sl, delta=delta))):
         lat.solve_doublet(xd, bd, 0.15, 0.19, tol=1e-10, **kw)  # warm-up
         t, infos = _timed(lambda: lat.solve_doublet(xd, bd, 0.15, 0.19, tol=1e-10, **kw), 3, dev)
         drows[name] = {"solves_per_s": round(3 / t, 3), "iters": infos[-1].iters,
@@ -636,7 +700,7 @@ def extra_measurements(args, dev, w, U, phi):
     lat.close()
     out["doublet"] = {"workload": f"{w.name} gauge field, mubar 0.15, epsbar 0.19, kappa {w.kappa}, two "
                                   "Gaussian flavour sources; even/odd CG to 1e-10",
-                      "sloppy": f"f32:{sl}, delta {args.delta}", **drows,
+                      "sloppy": f"f32:{sl}, delta {delta}", **drows,
                       "apply_Dh_ms": round(t / 5 * 1e3, 4),
                       "timing": "3 solves / 5 applications, CUDA events, L2 flushed before each"}
     out["chrono_guess"] = {"workload": f"{w.name}, 8 slowly varying sources, N_CSG = 4, FP64 CG on "
@@ -648,43 +712,59 @@ def extra_measurements(args, dev, w, U, phi):
 
 
 # -------------------------------------------------------------- CPU oracle ---
-def oracle_cg_rate(w, U, phi, seconds: float):
-    """Time the oracle's CG iterations (as it stands) on a bounded sample: returns
-    (seconds per iteration, iterations timed, seconds for prepare + reconstruct)."""
-    import numpy as np
+class OracleSample:
+    """The oracle's even/odd FP64 CG on one workload, as it stands, timed in bounded samples: the
+    source preparation and the reconstruction once (`fixed`), then CG iterations in samples of
+    about `seconds` (at least one iteration each).  The oracle's CG applies the operator once for
+    its initial residual and once more for the final check: one application (`t_A`, timed once) is
+    taken off each sample, and a solve is modelled as fixed + 2 t_A + iterations x (time per
+    iteration)."""
 
-    import oracle
-    lat = oracle.Lattice.cubic(w.T, w.L)
-    t0 = time.perf_counter()
-    varphi = oracle.eo_prepare(lat, U, phi, w.kappa, w.mu)
-    odd = lat.parity_mask()[..., None, None]
-    b = np.where(odd, varphi, 0) * np.array([1, 1, -1, -1])[:, None]
-    t_prep = time.perf_counter() - t0
-    n, t = 0, 0.0
-    k = 1
-    x = None
-    while n == 0 or t < seconds:
+    def __init__(self, w, U, phi):
+        import numpy as np
+
+        import oracle
+        self.w, self.U = w, U
+        self.lat = oracle.Lattice.cubic(w.T, w.L)
+        t0 = time.perf_counter()
+        varphi = oracle.eo_prepare(self.lat, U, phi, w.kappa, w.mu)
         t1 = time.perf_counter()
-        res = oracle.cg(lat, U, b, w.kappa, w.mu, tol=1e-30, max_iter=k, x0=x)
-        t += time.perf_counter() - t1
-        n += res.iters
-        x = res.x
-        k = min(2 * k, 64)
-    t2 = time.perf_counter()
-    oracle.eo_reconstruct(lat, U, varphi, np.where(odd, x, 0), w.kappa, w.mu)
-    t_rec = time.perf_counter() - t2
-    return t / n, n, t_prep + 2 * t_rec
+        odd = self.lat.parity_mask()[..., None, None]
+        self.b = np.where(odd, varphi, 0) * np.array([1, 1, -1, -1])[:, None]
+        t2 = time.perf_counter()
+        oracle.eo_reconstruct(self.lat, U, varphi, np.where(odd, self.b, 0), w.kappa, w.mu)
+        t3 = time.perf_counter()
+        oracle.normal_op(self.lat, U, self.b, w.kappa, w.mu)
+        self.t_A = time.perf_counter() - t3
+        # one preparation, one reconstruction (whose x_o = Qhat^- X costs as much again), and the
+        # CG's initial and final operator applications
+        self.fixed = (t1 - t0) + 2 * (t3 - t2) + 2 * self.t_A
+
+    def iterations(self, seconds: float):
+        """Runs CG iterations for about `seconds` (at least one); returns (seconds per iteration,
+        iterations run)."""
+        import oracle
+        w = self.w
+        n, t, k = 0, 0.0, 1
+        while n == 0 or t < seconds:
+            t1 = time.perf_counter()
+            res = oracle.cg(self.lat, self.U, self.b, w.kappa, w.mu, tol=1e-30, max_iter=k)
+            t += max(0.0, time.perf_counter() - t1 - self.t_A)
+            n += res.iters
+            k = min(2 * k, 64)
+        return t / n, n
 
 
 def cpu_baseline(w, U, phi, iters, seconds):
     import oracle
-    t_it, n, t_fixed = oracle_cg_rate(w, U, phi, seconds)
-    per_solve = t_it * iters + t_fixed
-    return {"value": round(1.0 / per_solve, 6), "unit": "solves/s", "cores": oracle.num_threads(),
+    smp = OracleSample(w, U, phi)
+    t_it, n = smp.iterations(seconds)
+    per_solve = t_it * iters + smp.fixed
+    return {"value": round(1.0 / per_solve, 8), "unit": "solves/s", "cores": oracle.num_threads(),
             "kind": "oracle",
-            "sample": f"oracle FP64 CG on {w.name}: {n} iterations timed ({t_it * 1e3:.1f} ms "
-                      f"each), extrapolated to the {iters} iterations of the GPU FP64 CG, plus "
-                      "one source preparation and reconstruction"}
+            "sample": f"oracle FP64 CG on {w.name}: {n} iterations timed ({t_it:.3f} s each), extrapolated "
+                      f"to the {iters} iterations of the GPU FP64 CG, plus one source preparation, "
+                      f"reconstruction and the CG's initial and final residuals ({smp.fixed:.2f} s, timed)"}
 
 
 def cpu_oracle_operator(w, U, phi, gpu_us, seconds: float = 2.0):
@@ -710,7 +790,8 @@ def cpu_oracle_operator(w, U, phi, gpu_us, seconds: float = 2.0):
 
 
 def run_reference(args):
-    """The reference arm: the CPU oracle as it stands, each step a bounded sample."""
+    """The reference arm: the CPU oracle as it stands, each step a bounded sample of the workload
+    (CG iterations), extrapolated to one complete solve."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -720,62 +801,70 @@ def run_reference(args):
     w = inputs.WORKLOADS[args.workload]
     U, phi = w.gauge(), w.source()
     iters, how = args.ref_iters, "given"
-    if iters <= 0:  # first warm-up step: one complete oracle solve gives the iteration count
+    if iters <= 0 and w.name in FP64_CG_ITERS:
+        iters, how = FP64_CG_ITERS[w.name], "of the FP64 CG to 1e-10 on this system, measured on GB300"
+    elif iters <= 0:  # small workloads: one complete oracle solve gives the iteration count
         res = oracle.solve(oracle.Lattice.cubic(w.T, w.L), U, phi, w.kappa, w.mu, tol=1e-10)
         iters, how = res.iters, "of the oracle's own complete FP64 solve to 1e-10"
+    smp = OracleSample(w, U, phi)
     for _ in range(args.warmup):
-        oracle_cg_rate(w, U, phi, 0.0)
+        smp.iterations(0.0)
     # each step's sample: --ref-seconds, shortened so that all steps together take about
-    # REF_TOTAL_SECONDS of host time
+    # REF_TOTAL_SECONDS of host time (at least one CG iteration per step)
     step_seconds = min(args.ref_seconds, max(0.5, REF_TOTAL_SECONDS / max(1, args.steps)))
-    per_step = []
+    per_step, n_it = [], 0
     for _ in range(args.steps):
-        t_it, n, t_fixed = oracle_cg_rate(w, U, phi, step_seconds)
-        per_step.append(t_it * iters + t_fixed)
+        t_it, n = smp.iterations(step_seconds)
+        n_it += n
+        per_step.append(t_it * iters + smp.fixed)
     tot = sum(per_step)
     value = args.steps / tot
-    cb = {"value": round(value, 6), "unit": "solves/s", "cores": oracle.num_threads(),
+    cb = {"value": round(value, 8), "unit": "solves/s", "cores": oracle.num_threads(),
           "kind": "oracle",
-          "sample": f"each step: oracle FP64 CG on {w.name} timed for ~{step_seconds:.2g} s, "
-                    f"extrapolated to {iters} iterations per solve ({how}), plus one source "
-                    "preparation and reconstruction"}
+          "sample": f"each step: oracle FP64 CG iterations on {w.name} for ~{step_seconds:.2g} s (at least one; "
+                    f"{n_it} in all), extrapolated to {iters} iterations per solve ({how}), plus one source "
+                    f"preparation, reconstruction and the CG's initial and final residuals ({smp.fixed:.2f} s, "
+                    "timed once)"}
     print(json.dumps({
-        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "solves/s",
+        "impl": "reference", "metric": METRIC, "value": round(value, 8), "unit": "solves/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(tot / args.steps * 1e3, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{w.name} lattice, eps {w.eps}, kappa {w.kappa}, mu {w.mu}, "
-                               "Gaussian source; even/odd CG to FP64 true residual 1e-10",
+        "config": {"workload": f"{w.name} lattice (V = {w.V}), random SU(3) links eps {w.eps}, kappa {w.kappa}, "
+                               f"mu {w.mu}, Gaussian source; even/odd CG to FP64 true residual 1e-10",
                    "lattice": w.name},
         "cpu_baseline": cb,
-        "e2e": {"value": round(value, 6), "unit": "solves/s", "h2d_bytes_per_step": 0,
+        "e2e": {"value": round(value, 8), "unit": "solves/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0}}))
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="16^3x32")
-    ap.add_argument("--sloppy", default="f32:12", help="sloppy storage:links, e.g. f32:12, f16:8")
-    ap.add_argument("--delta", type=float, default=1e-5,
-                    help="reliable-update delta of the main line (tuned for 16^3x32)")
+    ap.add_argument("--workload", default="48^3x96")
+    ap.add_argument("--sloppy", default=None, help="sloppy storage:links, e.g. f32:12, f16:8 (default per workload)")
+    ap.add_argument("--delta", type=float, default=None, help="reliable-update delta (default per workload)")
+    ap.add_argument("--update-prec", default=None, choices=["f64", "f32"],
+                    help="arithmetic of the residual recomputations between FP64 ones (default per workload)")
     ap.add_argument("--batched-delta", type=float, default=1e-3,
                     help="reliable-update delta of the batched measurement (24^3x48 systems)")
-    ap.add_argument("--fp64-steps", type=int, default=3)
-    ap.add_argument("--hop-iters", type=int, default=200)
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--hop-iters", type=int, default=50)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-solve measurement")
     ap.add_argument("--no-precision-form", action="store_true",
                     help="skip the 32^3x64 roofline and mixed-vs-FP64 solve measurement")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the BiCGstab, chronological-guess and contraction measurements")
+                    help="skip the 16^3x32 baseline and the BiCGstab, chronological-guess and doublet measurements")
     ap.add_argument("--ref-seconds", type=float, default=8.0)
     ap.add_argument("--ref-iters", type=int, default=0,
-                    help="CG iterations per solve used to scale the reference arm's sample (0: take them from one complete oracle solve)")
+                    help="CG iterations per solve used to scale the reference arm's sample (0: the table of "
+                         "measured FP64 CG counts, else one complete oracle solve)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="ncu dram bytes per launch of the sloppy hopping kernel, if measured")
     args = ap.parse_args()
