@@ -108,13 +108,16 @@ size_t tm_half_field_bytes(tm_lattice lat, tm_prec prec);
  * are added in a fixed order); more threads per site keep more memory requests in flight on
  * lattices too small to fill the GPU.  The value 3 (TM_HOP_PIPELINED, FP32 and FP16 storage
  * only) selects one thread per site whose loads of the next hop are issued before the current
- * hop's arithmetic.  By default the library times the choices when the form's gauge copy is
- * first built and keeps the fastest (the environment variable TM_HOP_TPS=1|2|3|4 overrides
- * that for every form).  tm_set_hop_threads fixes the choice (0 = tune again);
- * tm_get_hop_threads reports it.  Results for different choices agree to rounding; for one
- * fixed choice they are bitwise reproducible.  Errors: TM_ERR_ARG, TM_ERR_UNSUPPORTED (3 with
- * FP64 or double-float storage, 2 or 4 with double-float). */
+ * hop's arithmetic.  The value 5 (TM_HOP_PAIRED, FP32 and FP16 storage only) selects one thread
+ * per TWO sites whose FP32 arithmetic runs on packed pairs (one instruction for both sites).
+ * By default the library times the choices when the form's gauge copy is first built and keeps
+ * the fastest (the environment variable TM_HOP_TPS=1|2|3|4|5 overrides that for every form).
+ * tm_set_hop_threads fixes the choice (0 = tune again); tm_get_hop_threads reports it.
+ * Results for different choices agree to rounding; for one fixed choice they are bitwise
+ * reproducible.  Errors: TM_ERR_ARG, TM_ERR_UNSUPPORTED (3 or 5 with FP64 or double-float
+ * storage, 2 or 4 with double-float). */
 #define TM_HOP_PIPELINED 3
+#define TM_HOP_PAIRED 5
 tm_status tm_set_hop_threads(tm_lattice lat, tm_prec prec, tm_link link, int threads_per_site);
 int tm_get_hop_threads(tm_lattice lat, tm_prec prec, tm_link link);
 

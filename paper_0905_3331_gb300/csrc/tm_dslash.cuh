@@ -100,12 +100,6 @@ __device__ __forceinline__ void su3_adj_mul2(const Mat3<R>& U, const cpx<R> h0[3
 // 12 adds per real pair instead of 2 x 24, and every colour row is one FMA chain (the product
 // form a*b + c*d + ... with separate multiplies and adds took 30% DMUL and 43% DADD of the FP64
 // pipe).  FP64 / FP32 / FP16 storage; double-float keeps the per-hop form (no fused FMA).
-template <typename R>
-__device__ __forceinline__ R fmadd(R a, R b, R c);
-template <>
-__device__ __forceinline__ float fmadd<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-template <>
-__device__ __forceinline__ double fmadd<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
 
 // u = U h for two colour vectors, each real part one chain
 template <typename R>
@@ -577,6 +571,10 @@ __global__ void __launch_bounds__(hop_spb(TPS) * TPS, hop_min_blocks(PREC, NREAL
   }
 }
 
+// the two-sites-per-thread kernel (tm_dslash_pair.cuh), instantiated in its own units
+tm_status hop_pair_launch_f32(tm_lattice lat, const HopArgs& a, cudaStream_t s);
+tm_status hop_pair_launch_f16(tm_lattice lat, const HopArgs& a, cudaStream_t s);
+
 template <int PREC, int NREAL, int TPS, bool PIPE>
 tm_status hop_launch_tps(tm_lattice lat, const HopArgs& a, cudaStream_t s) {
   const Geom& g = lat->geom;
@@ -615,6 +613,10 @@ tm_status hop_launch_t(tm_lattice lat, const HopArgs& a, cudaStream_t s) {
       return hop_launch_tps<PREC, NREAL, 4, false>(lat, a, s);
     case TM_HOP_PIPELINED:
       if constexpr (PREC == TM_F32 || PREC == TM_F16) return hop_launch_tps<PREC, NREAL, 1, true>(lat, a, s);
+      return hop_launch_tps<PREC, NREAL, 1, false>(lat, a, s);
+    case TM_HOP_PAIRED:
+      if constexpr (PREC == TM_F32) return hop_pair_launch_f32(lat, a, s);
+      if constexpr (PREC == TM_F16) return hop_pair_launch_f16(lat, a, s);
       return hop_launch_tps<PREC, NREAL, 1, false>(lat, a, s);
     default:
       return hop_launch_tps<PREC, NREAL, 1, false>(lat, a, s);

@@ -70,6 +70,42 @@ __device__ __forceinline__ R norm2(cpx<R> a) {
   return a.re * a.re + a.im * a.im;
 }
 
+// Fused multiply-add a * b + c with one rounding, per arithmetic type.
+template <typename R>
+__device__ __forceinline__ R fmadd(R a, R b, R c);
+template <>
+__device__ __forceinline__ float fmadd<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+template <>
+__device__ __forceinline__ double fmadd<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// ------------------------------------------------------------ two-lane FP32 ---
+// A pair of FP32 numbers, one per lattice site, for kernels in which a thread computes two
+// output sites: every operation acts on both lanes with one packed FP32 instruction (sm_100 and
+// later), so the FP32 arithmetic of two sites costs the issue slots of one.  Each lane rounds as
+// the scalar operation would (IEEE round to nearest).
+struct f2 {
+  float2 v;
+  f2() = default;
+  __device__ __forceinline__ f2(float2 a) : v(a) {}
+  __device__ __forceinline__ f2(float a) : v(make_float2(a, a)) {}
+  __device__ __forceinline__ f2(int a) : v(make_float2((float)a, (float)a)) {}
+  __device__ __forceinline__ f2(float a, float b) : v(make_float2(a, b)) {}
+};
+__device__ __forceinline__ f2 operator-(f2 a) { return f2(make_float2(-a.v.x, -a.v.y)); }
+__device__ __forceinline__ f2 operator+(f2 a, f2 b) { return f2(__fadd2_rn(a.v, b.v)); }
+__device__ __forceinline__ f2 operator-(f2 a, f2 b) { return f2(__fadd2_rn(a.v, (-b).v)); }
+__device__ __forceinline__ f2 operator*(f2 a, f2 b) { return f2(__fmul2_rn(a.v, b.v)); }
+template <>
+__device__ __forceinline__ f2 fmadd<f2>(f2 a, f2 b, f2 c) { return f2(__ffma2_rn(a.v, b.v, c.v)); }
+// complex products of pairs as FMA chains (the scalar types get them from FMA contraction)
+__device__ __forceinline__ cpx<f2> operator*(cpx<f2> a, cpx<f2> b) {
+  return {fmadd(a.re, b.re, -(a.im * b.im)), fmadd(a.re, b.im, a.im * b.re)};
+}
+__device__ __forceinline__ cpx<f2> cjmul(cpx<f2> a, cpx<f2> b) {
+  return {fmadd(a.re, b.re, a.im * b.im), fmadd(a.re, b.im, -(a.im * b.re))};
+}
+__device__ __forceinline__ f2 norm2(cpx<f2> a) { return fmadd(a.re, a.re, a.im * a.im); }
+
 // ------------------------------------------------------------- double-float ---
 // A real number held as the unevaluated sum hi + lo of two FP32 numbers ("double-word"
 // arithmetic, Dekker 1971).  The building blocks are the error-free transformations TwoSum
@@ -632,12 +668,15 @@ template <typename R, typename S>
 struct LinkRecon<R, S, 18> {
   static constexpr int BYTES = 18 * (int)sizeof(S);
   __device__ static __forceinline__ void unpack(const RawWords<BYTES>& r, Mat3<R>& U) {
+    from_reals([&](int k) { return (R)RawGet<S, BYTES>::get(r, k); }, U);
+  }
+  // the matrix from its stored reals, get(k) = real number k (one site, or a pair of sites)
+  template <class Get>
+  __device__ static __forceinline__ void from_reals(Get get, Mat3<R>& U) {
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
-      for (int b = 0; b < 3; ++b)
-        U.m[a][b] = mk<R>((R)RawGet<S, BYTES>::get(r, 2 * (3 * a + b)),
-                          (R)RawGet<S, BYTES>::get(r, 2 * (3 * a + b) + 1));
+      for (int b = 0; b < 3; ++b) U.m[a][b] = mk<R>(get(2 * (3 * a + b)), get(2 * (3 * a + b) + 1));
   }
   __device__ static __forceinline__ void pack(RawWords<BYTES>& r, const Mat3<double>& U) {
 #pragma unroll
@@ -650,23 +689,43 @@ struct LinkRecon<R, S, 18> {
   }
 };
 
+// conj(a b - c d) as two FMA chains (the entries of row 3 = conj(row 1 x row 2))
+template <typename R>
+__device__ __forceinline__ cpx<R> cross_conj(cpx<R> a, cpx<R> b, cpx<R> c, cpx<R> d) {
+  R re = a.re * b.re;
+  re = fmadd(-a.im, b.im, re);
+  re = fmadd(-c.re, d.re, re);
+  re = fmadd(c.im, d.im, re);
+  R im = c.re * d.im;
+  im = fmadd(c.im, d.re, im);
+  im = fmadd(-a.re, b.im, im);
+  im = fmadd(-a.im, b.re, im);
+  return mk<R>(re, im);
+}
+template <>
+__device__ __forceinline__ cpx<dd> cross_conj<dd>(cpx<dd> a, cpx<dd> b, cpx<dd> c, cpx<dd> d) {
+  return cj(a * b - c * d);
+}
+
 template <typename R>
 __device__ __forceinline__ void third_row(Mat3<R>& U) {
-  U.m[2][0] = cj(U.m[0][1] * U.m[1][2] - U.m[0][2] * U.m[1][1]);
-  U.m[2][1] = cj(U.m[0][2] * U.m[1][0] - U.m[0][0] * U.m[1][2]);
-  U.m[2][2] = cj(U.m[0][0] * U.m[1][1] - U.m[0][1] * U.m[1][0]);
+  U.m[2][0] = cross_conj(U.m[0][1], U.m[1][2], U.m[0][2], U.m[1][1]);
+  U.m[2][1] = cross_conj(U.m[0][2], U.m[1][0], U.m[0][0], U.m[1][2]);
+  U.m[2][2] = cross_conj(U.m[0][0], U.m[1][1], U.m[0][1], U.m[1][0]);
 }
 
 template <typename R, typename S>
 struct LinkRecon<R, S, 12> {
   static constexpr int BYTES = 12 * (int)sizeof(S);
   __device__ static __forceinline__ void unpack(const RawWords<BYTES>& r, Mat3<R>& U) {
+    from_reals([&](int k) { return (R)RawGet<S, BYTES>::get(r, k); }, U);
+  }
+  template <class Get>
+  __device__ static __forceinline__ void from_reals(Get get, Mat3<R>& U) {
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
-      for (int b = 0; b < 3; ++b)
-        U.m[a][b] = mk<R>((R)RawGet<S, BYTES>::get(r, 2 * (3 * a + b)),
-                          (R)RawGet<S, BYTES>::get(r, 2 * (3 * a + b) + 1));
+      for (int b = 0; b < 3; ++b) U.m[a][b] = mk<R>(get(2 * (3 * a + b)), get(2 * (3 * a + b) + 1));
     third_row(U);
   }
   __device__ static __forceinline__ void pack(RawWords<BYTES>& r, const Mat3<double>& U) {
@@ -680,23 +739,41 @@ struct LinkRecon<R, S, 12> {
   }
 };
 
-template <typename R>
-__device__ __forceinline__ R sqrt_nonneg(R v) {
-  return sqrt(v > R(0) ? v : R(0));
+// Square root of a non-negative number (0 for a negative rounding residue), reciprocal and
+// sin/cos of pi v for the 8-real reconstruction.  FP64 uses the accurate library functions.  The
+// reduced-precision operators (FP32 arithmetic) use the hardware approximations: reciprocal
+// square root (v * rsqrt(v), a few ulp), reciprocal (2 ulp), sine/cosine (absolute error ~4e-7
+// on |x| <= pi), all far below FP16 storage and within the FP32 8-real parity bound; the IEEE
+// square root and reciprocal carry range checks and a slow path that cost ~190 instructions per
+// output site.
+__device__ __forceinline__ double sqrt_nn(double v) { return sqrt(v > 0.0 ? v : 0.0); }
+__device__ __forceinline__ float sqrt_nn(float v) { return v > 0.f ? v * rsqrtf(v) : 0.f; }
+__device__ __forceinline__ f2 sqrt_nn(f2 v) { return f2(sqrt_nn(v.v.x), sqrt_nn(v.v.y)); }
+__device__ __forceinline__ double recip_(double v) { return 1.0 / v; }
+__device__ __forceinline__ float recip_(float v) { return __fdividef(1.0f, v); }
+__device__ __forceinline__ f2 recip_(f2 v) { return f2(recip_(v.v.x), recip_(v.v.y)); }
+__device__ __forceinline__ void sincospi_(double v, double* s, double* c) { sincospi(v, s, c); }
+__device__ __forceinline__ void sincospi_(float v, float* s, float* c) { __sincosf(v * 3.14159265358979323846f, s, c); }
+__device__ __forceinline__ void sincospi_(f2 v, f2* s, f2* c) {
+  sincospi_(v.v.x, &s->v.x, &c->v.x);
+  sincospi_(v.v.y, &s->v.y, &c->v.y);
 }
 
 template <typename R, typename S>
 struct LinkRecon<R, S, 8> {
   static constexpr int BYTES = 8 * (int)sizeof(S);
   __device__ static __forceinline__ void unpack(const RawWords<BYTES>& r, Mat3<R>& U) {
-    typedef RawGet<S, BYTES> G;
-    const cpx<R> a1 = mk<R>((R)G::get(r, 0), (R)G::get(r, 1));
-    const cpx<R> a2 = mk<R>((R)G::get(r, 2), (R)G::get(r, 3));
-    const cpx<R> b0 = mk<R>((R)G::get(r, 4), (R)G::get(r, 5));
-    const R tha = (R)G::get(r, 6), thc = (R)G::get(r, 7);  // phases / pi
-    const R N = norm2(a1) + norm2(a2);                       // = 1 - |a0|^2
-    const R ma0 = sqrt_nonneg(R(1) - N);
-    const R mc0 = sqrt_nonneg(N - norm2(b0));                // = 1 - |a0|^2 - |b0|^2
+    from_reals([&](int k) { return (R)RawGet<S, BYTES>::get(r, k); }, U);
+  }
+  template <class Get>
+  __device__ static __forceinline__ void from_reals(Get get, Mat3<R>& U) {
+    const cpx<R> a1 = mk<R>(get(0), get(1));
+    const cpx<R> a2 = mk<R>(get(2), get(3));
+    const cpx<R> b0 = mk<R>(get(4), get(5));
+    const R tha = get(6), thc = get(7);    // phases / pi
+    const R N = norm2(a1) + norm2(a2);       // = 1 - |a0|^2
+    const R ma0 = sqrt_nn(R(1) - N);
+    const R mc0 = sqrt_nn(N - norm2(b0));    // = 1 - |a0|^2 - |b0|^2
     R sa, ca, sc, cc;
     sincospi_(tha, &sa, &ca);
     sincospi_(thc, &sc, &cc);
@@ -713,17 +790,11 @@ struct LinkRecon<R, S, 8> {
     U.m[1][0] = b0;
     U.m[1][1] = b1;
     U.m[1][2] = b2;
-    third_row(U);
+    // row 3 = conj(row 1 x row 2); its first entry is c0 itself
+    U.m[2][0] = c0;
+    U.m[2][1] = cross_conj(a2, b0, a0, b2);
+    U.m[2][2] = cross_conj(a0, b1, a1, b0);
   }
-  // Single precision (the reduced-precision operators): the fast hardware sine/cosine (absolute
-  // error ~4e-7 on |x| <= pi, far below FP16 storage and within the FP32 8-real parity bound)
-  // and the correctly rounded reciprocal; FP64 keeps the accurate library functions.
-  __device__ static __forceinline__ void sincospi_(float v, float* s, float* c) {
-    __sincosf(v * 3.14159265358979323846f, s, c);
-  }
-  __device__ static __forceinline__ void sincospi_(double v, double* s, double* c) { sincospi(v, s, c); }
-  __device__ static __forceinline__ float recip_(float v) { return __frcp_rn(v); }
-  __device__ static __forceinline__ double recip_(double v) { return 1.0 / v; }
   __device__ static __forceinline__ void pack(RawWords<BYTES>& r, const Mat3<double>& U) {
     typedef RawGet<S, BYTES> G;
     G::put(r, 0, (S)U.m[0][1].re);

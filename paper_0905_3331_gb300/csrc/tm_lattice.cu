@@ -273,7 +273,7 @@ static int env_tps() {
   const char* e = getenv("TM_HOP_TPS");
   if (!e) return 0;
   const int v = atoi(e);
-  return (v == 1 || v == 2 || v == 4 || v == TM_HOP_PIPELINED) ? v : 0;
+  return (v == 1 || v == 2 || v == 4 || v == TM_HOP_PIPELINED || v == TM_HOP_PAIRED) ? v : 0;
 }
 
 // Times the kernel choices of one storage form on this lattice and keeps the best.  The score
@@ -290,7 +290,7 @@ static tm_status tune_hop(tm_lattice lat, int prec, int nreal, cudaStream_t s) {
     return TM_OK;
   }
   if (const int e = env_tps()) {
-    lat->hop_tps[prec][li] = (e == TM_HOP_PIPELINED && prec == TM_F64) ? 1 : e;
+    lat->hop_tps[prec][li] = ((e == TM_HOP_PIPELINED || e == TM_HOP_PAIRED) && prec == TM_F64) ? 1 : e;
     return TM_OK;
   }
   const size_t hb = spinor_bytes_per_site(prec) * lat->h;
@@ -326,14 +326,15 @@ static tm_status tune_hop(tm_lattice lat, int prec, int nreal, cudaStream_t s) {
   // was built (or any other drift) slows every candidate alike; pass 0 is the warm-up.  A
   // group is two iterations' mix (8 launches); each candidate's score is its fastest group
   // (five groups, three for FP64 storage, whose launches are ~10x longer).  Candidates: one
-  // thread per site, its software-pipelined form (FP32 / FP16 storage), 2 and 4 threads per site.
-  const int cands[4] = {1, TM_HOP_PIPELINED, 2, 4};
+  // thread per site, its software-pipelined form (FP32 / FP16 storage), 2 and 4 threads per site,
+  // and two sites per thread with packed FP32 pairs (FP32 / FP16 storage).
+  const int cands[5] = {1, TM_HOP_PIPELINED, 2, 4, TM_HOP_PAIRED};
   const bool has_pipe = (prec == TM_F32 || prec == TM_F16);
   const int rounds = (prec == TM_F64) ? 4 : 6;
-  float score[4] = {1e30f, 1e30f, 1e30f, 1e30f};
+  float score[5] = {1e30f, 1e30f, 1e30f, 1e30f, 1e30f};
   for (int k = 0; k < rounds && st == TM_OK; ++k) {
-    for (int c = 0; c < 4 && st == TM_OK; ++c) {
-      if (c == 1 && !has_pipe) continue;
+    for (int c = 0; c < 5 && st == TM_OK; ++c) {
+      if ((c == 1 || c == 4) && !has_pipe) continue;
       lat->hop_tps[prec][li] = cands[c];
       st = cuda_check(cudaEventRecord(e0, s), "event");
       for (int q = 0; q < 8 && st == TM_OK; ++q) {
@@ -352,7 +353,8 @@ static tm_status tune_hop(tm_lattice lat, int prec, int nreal, cudaStream_t s) {
   // spread) the rule does, so that the choice is reproducible: the pipelined kernel where the
   // plain one's grid fits in one wave (each thread's load latencies set the launch time there:
   // 16^3 x 32 FP32/12 1.9% faster inside the mixed solve, 13% per cold launch), else the plain
-  // one.  More threads per site must be 10% faster than the better of the two.
+  // one.  The paired kernel must beat the better of the two by 3%; more threads per site must
+  // be 10% faster than the best so far.
   int bi = 0;
   if (has_pipe) {
     int dev = 0, sms = 0;
@@ -361,6 +363,7 @@ static tm_status tune_hop(tm_lattice lat, int prec, int nreal, cudaStream_t s) {
     const bool one_wave = lat->h <= (size_t)sms * HOP_BLOCKS_12 * hop_spb(1);
     const float ratio = score[1] / score[0];
     bi = ratio < 0.97f ? 1 : (ratio > 1.03f ? 0 : (one_wave ? 1 : 0));
+    if (score[4] < 0.97f * score[bi]) bi = 4;
   }
   const float base = score[bi];
   for (int c = 2; c < 4; ++c)
@@ -509,10 +512,13 @@ tm_status tm_set_hop_threads(tm_lattice lat, tm_prec prec, tm_link link, int thr
   if (!lat || prec < TM_F64 || prec > TM_DF64 || (link != 18 && link != 12 && link != 8))
     return set_error(TM_ERR_ARG, "tm_set_hop_threads: bad argument");
   if (threads_per_site != 0 && threads_per_site != 1 && threads_per_site != 2 && threads_per_site != 4 &&
-      threads_per_site != TM_HOP_PIPELINED)
-    return set_error(TM_ERR_ARG, "tm_set_hop_threads: threads_per_site must be 0 (tune), 1, 2, 4 or 3 (pipelined)");
-  if (threads_per_site == TM_HOP_PIPELINED && prec != TM_F32 && prec != TM_F16)
-    return set_error(TM_ERR_UNSUPPORTED, "tm_set_hop_threads: the pipelined kernel exists for FP32 and FP16 storage");
+      threads_per_site != TM_HOP_PIPELINED && threads_per_site != TM_HOP_PAIRED)
+    return set_error(TM_ERR_ARG,
+                     "tm_set_hop_threads: threads_per_site must be 0 (tune), 1, 2, 4, 3 (pipelined) or 5 (paired)");
+  if ((threads_per_site == TM_HOP_PIPELINED || threads_per_site == TM_HOP_PAIRED) && prec != TM_F32 &&
+      prec != TM_F16)
+    return set_error(TM_ERR_UNSUPPORTED,
+                     "tm_set_hop_threads: the pipelined and paired kernels exist for FP32 and FP16 storage");
   const int li = link_index(link);
   invalidate_graphs(lat);  // captured graphs hold the previous kernel choice
   if (threads_per_site == 0) {

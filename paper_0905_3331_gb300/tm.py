@@ -24,6 +24,7 @@ F64, F32, F16, DF64 = 0, 1, 2, 3
 LINK18, LINK12, LINK8 = 18, 12, 8
 CG_FP64, CG_SQRT_EPS, CG_RELIABLE = 0, 1, 2
 HOP_PIPELINED = 3  # hopping-kernel choice: one thread per site, software-pipelined loads
+HOP_PAIRED = 5     # hopping-kernel choice: two sites per thread, packed FP32 pairs
 
 STATUS = {0: "TM_OK", 1: "TM_ERR_ARG", 2: "TM_ERR_ODD_EXTENT", 3: "TM_ERR_NO_GAUGE",
           4: "TM_ERR_NOT_SU3", 5: "TM_ERR_NONFINITE", 6: "TM_ERR_CUDA",
@@ -224,8 +225,9 @@ class Lattice:
         return int(load().tm_half_field_bytes(self._h, prec))
 
     def set_hop_threads(self, prec: int, link: int, threads_per_site: int):
-        """Fix the hopping kernel for one form: threads per site 1, 2 or 4, or HOP_PIPELINED (3,
-        one thread per site with software-pipelined loads; FP32 / FP16 storage); 0 re-tunes."""
+        """Fix the hopping kernel for one form: threads per site 1, 2 or 4, HOP_PIPELINED (3,
+        one thread per site with software-pipelined loads) or HOP_PAIRED (5, two sites per thread
+        with packed FP32 pairs) -- the last two for FP32 / FP16 storage; 0 re-tunes."""
         _check(load().tm_set_hop_threads(self._h, prec, link, threads_per_site),
                "tm_set_hop_threads")
 
@@ -411,6 +413,7 @@ def correlator(lat, A, X, stream=None):
         C = np.zeros((n, lat.T), dtype=np.complex128)
     else:
         import torch
+        A = A.contiguous()
         C = torch.zeros((n, lat.T), dtype=torch.complex128, device=A.device)
     _check(load().tm_correlator(lat._h, _addr(A), _addr(Xa), n, _addr(C), _stream(stream)),
            "tm_correlator")

@@ -260,14 +260,15 @@ def test_full_size_sampled_sites(name, prec, link):
     lat.close()
 
 
-@pytest.mark.parametrize("tps", [1, 2, 4, 3])
+@pytest.mark.parametrize("tps", [1, 2, 4, 3, 5])
 @pytest.mark.parametrize("T,L", [(2, 2), (4, 6), (32, 16)])
 @pytest.mark.parametrize("prec,link", [(F64, 18), (F32, 18), (F32, 12), (F32, 8), (F16, 12), (F16, 8)])
 def test_hopping_each_threads_per_site(tps, T, L, prec, link):
-    """The 1-, 2- and 4-threads-per-site kernels and the software-pipelined one (3, FP32 / FP16
-    storage) all match the oracle (ragged tails included)."""
-    if tps == 3 and prec == F64:
-        pytest.skip("the pipelined kernel exists for FP32 and FP16 storage")
+    """The 1-, 2- and 4-threads-per-site kernels, the software-pipelined one (3) and the
+    two-sites-per-thread one with packed FP32 pairs (5; both FP32 / FP16 storage) all match the
+    oracle (ragged tails included: on 2^4 and 4 x 6^3 the second site of some threads is idle)."""
+    if tps in (3, 5) and prec == F64:
+        pytest.skip("the pipelined and paired kernels exist for FP32 and FP16 storage")
     lat = Lattice(T, L, 0.1632, 0.004)
     lat.set_hop_threads(prec, link, tps)
     U = inputs.random_gauge(T, L, 0.5, 1)
@@ -313,15 +314,17 @@ def test_double_float_link_formats():
     lat.close()
 
 
-def test_pipelined_matches_plain_kernel():
-    """The software-pipelined kernel does the plain one-thread kernel's arithmetic in the same
-    order: on a 16^3 x 32 field the two agree to FP32 rounding in every storage form."""
+@pytest.mark.parametrize("variant", [3, 5])
+def test_pipelined_and_paired_match_plain_kernel(variant):
+    """The software-pipelined kernel (3) and the paired one (5) do the plain one-thread kernel's
+    arithmetic (the paired kernel folds the epilogue's coefficients first): on a 16^3 x 32 field
+    they agree with it to FP32 rounding in every storage form."""
     T, L = 32, 16
     U = inputs.random_gauge(T, L, 0.5, 1)
     psi = inputs.gaussian_spinor(T, L, 8)
     for prec, link in ((F32, 18), (F32, 12), (F32, 8), (F16, 12), (F16, 8)):
         outs = []
-        for tps in (1, 3):
+        for tps in (1, variant):
             lat = Lattice(T, L, 0.1632, 0.004)
             lat.set_hop_threads(prec, link, tps)
             lat.set_gauge(U)

@@ -221,24 +221,45 @@ def test_host_loop_fallback_and_tracing(env, tmp_path):
     lat.close()
 
 
-@pytest.mark.parametrize("tps", [1, 2, 4, 3])
+@pytest.mark.parametrize("tps", [1, 2, 4, 3, 5])
 def test_solve_with_each_threads_per_site(tps):
-    """Every launch configuration of the hopping kernel (3: the software-pipelined one for the
-    FP32 / FP16 forms, FP64 then one thread per site) gives a solve that meets the bar."""
+    """Every launch configuration of the hopping kernel (3: the software-pipelined one, 5: two
+    sites per thread with packed FP32 pairs, both for the FP32 / FP16 forms, FP64 then one thread
+    per site) gives a solve that meets the bar."""
     w = inputs.WORKLOADS["4^4"]
     U, phi = w.gauge(), w.source()
     lat = Lattice(w.T, w.L, w.kappa, w.mu)
-    for prec, link in ((0, 18), (1, 12), (2, 12)):
-        lat.set_hop_threads(prec, link, 1 if (tps == 3 and prec == 0) else tps)
+    for prec, link in ((0, 18), (1, 12), (2, 12), (2, 8)):
+        lat.set_hop_threads(prec, link, 1 if (tps in (3, 5) and prec == 0) else tps)
     lat.set_gauge(U)
     b = torch.from_numpy(phi).to(dev())
     for kw in (dict(mode=CG_FP64), dict(mode=CG_RELIABLE, sloppy_prec=F32, sloppy_link=LINK12),
-               dict(mode=CG_RELIABLE, sloppy_prec=F16, sloppy_link=LINK12)):
+               dict(mode=CG_RELIABLE, sloppy_prec=F16, sloppy_link=LINK12),
+               dict(mode=CG_RELIABLE, sloppy_prec=F16, sloppy_link=LINK8, delta=0.3, update_prec=F32)):
         x = torch.zeros_like(b)
         lat.solve_cg(x, b, **kw)
         assert oracle_true_residual(w, U, phi, x.cpu().numpy()) < 1e-10
-    assert lat.hop_threads(0, 18) == (1 if tps == 3 else tps)
+    assert lat.hop_threads(0, 18) == (1 if tps in (3, 5) else tps)
     assert lat.hop_threads(1, 12) == tps
+    lat.close()
+
+
+@pytest.mark.parametrize("name", ["16^3x32", "48^3x96"])
+def test_paired_kernel_in_the_headline_solve(name):
+    """The headline solve (FP16 storage, 8-real links, delta 0.3, FP32 recomputations between FP64
+    ones) with the two-sites-per-thread hopping kernel: the oracle's residual of the GPU solution
+    is below 1e-10."""
+    w = inputs.WORKLOADS[name]
+    U, phi = w.gauge(), w.source()
+    lat = Lattice(w.T, w.L, w.kappa, w.mu)
+    lat.set_hop_threads(F16, LINK8, 5)
+    lat.set_hop_threads(F32, LINK8, 5)
+    lat.set_gauge(U)
+    b = torch.from_numpy(phi).to(dev())
+    x = torch.zeros_like(b)
+    info = lat.solve_cg(x, b, mode=CG_RELIABLE, sloppy_prec=F16, sloppy_link=LINK8, delta=0.3, update_prec=F32,
+                        max_iter=20000)
+    assert oracle_true_residual(w, U, phi, x.cpu().numpy()) < 1e-10 and info.true_rel_residual < 1e-10
     lat.close()
 
 
