@@ -19,6 +19,10 @@ With --batch N it runs `iters` batched solves (tm_solve_cg_batch, FP32/FP16 slop
 
 With --contract it runs `iters` meson contractions (tm_meson_contract) of 12 Gaussian
 propagators on the workload's lattice and reports the mean time, bytes and FP64 rate.
+
+With --fma-probe it compiles (nvcc, sm_103a) and runs a probe of the GPU's FMA rates: 8
+independent fma.rn.f64 / fma.rn.f32 / packed fma.rn.f32x2 chains per thread, 8 blocks of 256
+threads per SM, timed with CUDA events, best of 4 launches.
 """
 from __future__ import annotations
 
@@ -50,7 +54,10 @@ def main():
     ap.add_argument("--delta", type=float, default=0.001, help="reliable-update delta of the doublet and batched solves")
     ap.add_argument("--contract", action="store_true", help="time meson contractions instead")
     ap.add_argument("--batch", type=int, default=0, help="time batched solves of this many sources")
+    ap.add_argument("--fma-probe", action="store_true", help="measure the FP64 / FP32 FMA rates instead")
     args = ap.parse_args()
+    if args.fma_probe:
+        return fma_probe()
     if args.batch:
         return batch(args)
     if args.doublet:
@@ -199,6 +206,67 @@ def doublet(args):
                       "reliable_updates": info.reliable_updates,
                       "true_rel_residual": info.true_rel_residual}))
     lat.close()
+
+
+FMA_PROBE_SRC = r"""
+#include <cstdio>
+#include <cuda_runtime.h>
+typedef unsigned long long u64;
+template <typename T> __device__ __forceinline__ T fma_(T a, T b, T c);
+template <> __device__ __forceinline__ double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
+template <> __device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+template <> __device__ __forceinline__ float2 fma_(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+template <typename T> __device__ T seed(int k);
+template <> __device__ double seed<double>(int k) { return threadIdx.x * 1e-3 + k; }
+template <> __device__ float seed<float>(int k) { return threadIdx.x * 1e-3f + k; }
+template <> __device__ float2 seed<float2>(int k) { return make_float2(threadIdx.x * 1e-3f + k, k + 0.5f); }
+__device__ double sum_(double v) { return v; }
+__device__ double sum_(float v) { return v; }
+__device__ double sum_(float2 v) { return v.x + v.y; }
+template <typename T> __global__ void k(double* out, T a, T b, int iters) {
+  T x[8];
+  for (int j = 0; j < 8; ++j) x[j] = seed<T>(j);
+  for (int i = 0; i < iters; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = fma_(x[j], a, b);
+  double s = 0; for (int j = 0; j < 8; ++j) s += sum_(x[j]);
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+template <typename T> double rate(T a, T b, int iters, int lanes, double* out, int blocks) {
+  cudaEvent_t e0, e1; cudaEventCreate(&e0); cudaEventCreate(&e1);
+  float best = 1e30f;
+  for (int rep = 0; rep < 4; ++rep) {
+    float ms;
+    cudaEventRecord(e0); k<T><<<blocks, 256>>>(out, a, b, iters); cudaEventRecord(e1); cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) best = ms;
+  }
+  return 2.0 * 8 * lanes * iters * (double)blocks * 256 / best / 1e9;
+}
+int main() {
+  int sms = 0; cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+  const int blocks = sms * 8;
+  double* out; cudaMalloc(&out, sizeof(double) * blocks * 256);
+  const double f64 = rate<double>(0.999, 1e-3, 512, 1, out, blocks);
+  const double f32 = rate<float>(0.999f, 1e-3f, 4096, 1, out, blocks);
+  const double f32x2 = rate<float2>(make_float2(0.999f, 0.999f), make_float2(1e-3f, 1e-3f), 4096, 2, out, blocks);
+  printf("{\"fp64_fma_tflops\": %.4f, \"fp32_fma_tflops\": %.3f, \"fp32x2_fma_tflops\": %.3f, \"sms\": %d, \"error\": \"%s\"}\n",
+         f64, f32, f32x2, sms, cudaGetErrorString(cudaGetLastError()));
+  return 0;
+}
+"""
+
+
+def fma_probe():
+    import subprocess
+    import tempfile
+    from paper_0905_3331_gb300 import build as libbuild
+    with tempfile.TemporaryDirectory() as d:
+        src, exe = os.path.join(d, "fma_probe.cu"), os.path.join(d, "fma_probe")
+        with open(src, "w") as fh:
+            fh.write(FMA_PROBE_SRC)
+        subprocess.run([libbuild.nvcc(), *libbuild.ARCH, "-O3", src, "-o", exe], check=True)
+        print(subprocess.run([exe], check=True, capture_output=True, text=True).stdout.strip())
 
 
 if __name__ == "__main__":

@@ -14,9 +14,10 @@ against that site's own norm) to the same tolerance, so a single wrong site or b
 fails even where the global norm would hide it.  One exception, SITE_TOL below: FP16 storage
 with 8-real links.  That parametrisation obtains |c0| = sqrt(N - |b0|^2) (N = |a1|^2 + |a2|^2)
 from stored FP16 numbers, which loses relative accuracy on the links where |c0|^2 << N; a
-float64 emulation of the FP16/8 storage and reconstruction on the 16^3 x 32 field of these tests
-gives a global error of 6.6e-4 but a worst site of 1.3e-2 (99.99th percentile 9e-3), so its
-per-site bar is 5e-2 -- still far below the O(1) error of a wrong site.  FP32 storage with 8-real
+float64 emulation of the FP16/8 storage (the encoding's local search included) and
+reconstruction on the 16^3 x 32 field of these tests gives a global error of 3.9e-4 but a worst
+site of 1.5e-2 (99.99th percentile 6e-3), so its per-site bar is 5e-2 -- still far below the O(1)
+error of a wrong site.  FP32 storage with 8-real
 links meets the same conditioning with the error of the fast hardware sine/cosine (absolute
 ~3.6e-7) in place of FP16 rounding: measured worst site 1.7e-5 on 16^3 x 32 (global < 1e-5),
 per-site bar 1e-4.
