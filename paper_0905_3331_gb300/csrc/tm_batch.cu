@@ -16,6 +16,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
+#include <utility>
 #include <vector>
 
 #include "tm_dslash.cuh"
@@ -43,78 +45,130 @@ struct BatchGlobal {
   unsigned counter;  // update-kernel blocks arrived
 };
 
-// Same site computation as hop_kernel (one thread per site), the system taken from the table.
-// Register budget for 6 blocks per SM (80): the kernel is latency bound, and the extra warps
-// outweigh a few spilled bytes (12-system solve on 24^3 x 48: 1060 -> 990 ms).
-template <int PREC, int NREAL, bool HAS_Y, int MODE>
-__global__ void __launch_bounds__(HOP_NT, 6) hop_batch_kernel(const BatchSys* __restrict__ systems,
-                                                           const int2* __restrict__ map, int in_sel, int y_sel,
-                                                           int out_sel, int k, int out_parity) {
+// Up to 4 systems of one lattice whose hopping terms one block computes together.
+struct BatchGroup {
+  int n;       // systems in the group (1 .. K of the kernel)
+  int sys[4];  // their indices in the system table (the first one's geometry and links serve all)
+};
+
+// The hopping operator of K systems at once: thread = site, the K systems of the block's group
+// are its lanes.  Each of the 8 links of the site is loaded and reconstructed ONCE and applied to
+// the K systems' neighbour spinors (the same direction-pair arithmetic as hop_kernel, per lane),
+// so a link's bytes and its reconstruction are shared by K right-hand sides in registers.  Each
+// system keeps its own epilogue coefficients (its mu), output, CG state and reduction.  A system
+// that has stopped (its stage trigger, convergence) is skipped; the block returns when all of its
+// group have.  K = 1 is the one-system case.  Register budgets: 6 blocks of 128 per SM for K = 1
+// (80 registers; latency bound: 12-system solve on 24^3 x 48 1060 -> 990 ms), 4 for K = 2, 2 for
+// K = 4 (the accumulators of K spinors).
+template <int PREC, int NREAL, bool HAS_Y, int MODE, int K>
+__global__ void __launch_bounds__(HOP_NT, (K == 1 ? 6 : (K == 2 ? 4 : 2)))
+    hop_group_kernel(const BatchSys* __restrict__ systems, const BatchGroup* __restrict__ groups,
+                     const int2* __restrict__ map, int in_sel, int y_sel, int out_sel, int kk, int out_parity) {
   typedef typename SpinorFmt<PREC>::real R;
   typedef SpinorFmt<PREC> F;
+  typedef typename LinkStore<PREC>::type St;
+  constexpr int BYTES = NREAL * LinkStore<PREC>::size;
   __shared__ double sh[HOP_NT / 32];
   const int2 m = map[blockIdx.x];
-  const BatchSys& B = systems[m.x];
-  CGState* st = B.st;
-  if (st->done) return;
-  const Geom g = B.g;
+  const BatchGroup G = groups[m.x];
+  const BatchSys* S[K];
+  bool live[K];
+  bool any = false;
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
+    S[j] = systems + G.sys[j < G.n ? j : 0];
+    live[j] = j < G.n && !S[j]->st->done;
+    any = any || live[j];
+  }
+  if (!any) return;
+  const Geom g = S[0]->g;
   const int cb = m.y * HOP_NT + threadIdx.x;
   const bool active = cb < g.h;
-  cpx<R> acc[12];
+  cpx<R> acc[K][12];
 #pragma unroll
-  for (int q = 0; q < 12; ++q) acc[q] = mk<R>(R(0), R(0));
+  for (int j = 0; j < K; ++j)
+#pragma unroll
+    for (int q = 0; q < 12; ++q) acc[j][q] = mk<R>(R(0), R(0));
   if (active) {
     const SiteCoord c = site_of(g, cb, out_parity);
     int nb[8];
     neighbours(g, cb, c, nb);
     const size_t slab = link_bytes(PREC, NREAL) * (size_t)g.h;
-    const char* lf = B.links + (size_t)(out_parity * 4) * slab;
-    const char* lo = B.links + (size_t)((1 - out_parity) * 4) * slab;
-    hop_part<PREC, NREAL, 1>(acc, g, cb, c, nb, static_cast<const char*>(B.vec[in_sel]), lf, lo, slab, 0);
+    const char* lf = S[0]->links + (size_t)(out_parity * 4) * slab;
+    const char* lo = S[0]->links + (size_t)((1 - out_parity) * 4) * slab;
+    const bool tf = (c.t == g.T - 1), tb = (c.t == 0);
+#define TM_GROUP_DIR(MU, FIRST)                                                                     \
+  {                                                                                                 \
+    cpx<R> u0[K][3], u1[K][3], p[12];                                                               \
+    R scale;                                                                                        \
+    Mat3<R> U;                                                                                      \
+    LinkRecon<R, St, NREAL>::unpack(load_raw<BYTES>(lf + MU * slab, g.h, cb), U);                   \
+    _Pragma("unroll") for (int j = 0; j < K; ++j) if (live[j]) {                                    \
+      F::load_unscaled(S[j]->vec[in_sel], g.h, nb[MU], p, scale);                                   \
+      pair_fwd_mat<PREC, MU>(u0[j], u1[j], U, p, scale, MU == 0 && tf);                             \
+    }                                                                                               \
+    LinkRecon<R, St, NREAL>::unpack(load_raw<BYTES>(lo + MU * slab, g.h, nb[4 + MU]), U);           \
+    _Pragma("unroll") for (int j = 0; j < K; ++j) if (live[j]) {                                    \
+      F::load_unscaled(S[j]->vec[in_sel], g.h, nb[4 + MU], p, scale);                               \
+      pair_bwd_mat<PREC, MU, FIRST>(acc[j], u0[j], u1[j], U, p, scale, MU == 0 && tb);              \
+    }                                                                                               \
   }
-  const EpiCoef coef = B.coef[k];
-  const R cc = (R)coef.c;
-  const cpx<R> Du = mk<R>((R)coef.d_up_re, (R)coef.d_up_im), Dl = mk<R>((R)coef.d_lo_re, (R)coef.d_lo_im);
-  cpx<R> o[12];
-  if (HAS_Y) {
-    const cpx<R> Eu = mk<R>((R)coef.e_up_re, (R)coef.e_up_im), El = mk<R>((R)coef.e_lo_re, (R)coef.e_lo_im);
-    cpx<R> yv[12];
-#pragma unroll
-    for (int q = 0; q < 12; ++q) yv[q] = mk<R>(R(0), R(0));
-    if (active) F::load(B.vec[y_sel], g.h, cb, yv);
-#pragma unroll
-    for (int q = 0; q < 12; ++q) o[q] = ((q < 6) ? Du : Dl) * (cc * acc[q] + ((q < 6) ? Eu : El) * yv[q]);
-  } else {
-#pragma unroll
-    for (int q = 0; q < 12; ++q) o[q] = ((q < 6) ? Du : Dl) * (cc * acc[q]);
+    TM_GROUP_DIR(0, true)
+    TM_GROUP_DIR(1, false)
+    TM_GROUP_DIR(2, false)
+    TM_GROUP_DIR(3, false)
+#undef TM_GROUP_DIR
   }
-  typedef typename SiteSum<R>::type SR;
-  SR nrm = SR(0);
-  void* outp = B.vec[out_sel];
-  if (MODE == 2) {
-    if (active) {
-      const R al = (R)st->alpha;
-      constexpr int PR = ResidPrec<PREC>::value;
-      cpx<R> r[12];
-      SpinorFmt<PR>::load(outp, g.h, cb, r);
 #pragma unroll
-      for (int q = 0; q < 12; ++q) {
-        r[q] = r[q] - al * o[q];
-        nrm += (SR)norm2(r[q]);
+  for (int j = 0; j < K; ++j) {
+    if (!live[j]) continue;  // block-uniform
+    const BatchSys& B = *S[j];
+    CGState* st = B.st;
+    const EpiCoef coef = B.coef[kk];
+    const R cc = (R)coef.c;
+    const cpx<R> Du = mk<R>((R)coef.d_up_re, (R)coef.d_up_im), Dl = mk<R>((R)coef.d_lo_re, (R)coef.d_lo_im);
+    cpx<R> o[12];
+    if (HAS_Y) {
+      const cpx<R> Eu = mk<R>((R)coef.e_up_re, (R)coef.e_up_im), El = mk<R>((R)coef.e_lo_re, (R)coef.e_lo_im);
+      cpx<R> yv[12];
+#pragma unroll
+      for (int q = 0; q < 12; ++q) yv[q] = mk<R>(R(0), R(0));
+      if (active) F::load(B.vec[y_sel], g.h, cb, yv);
+#pragma unroll
+      for (int q = 0; q < 12; ++q) o[q] = ((q < 6) ? Du : Dl) * (cc * acc[j][q] + ((q < 6) ? Eu : El) * yv[q]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 12; ++q) o[q] = ((q < 6) ? Du : Dl) * (cc * acc[j][q]);
+    }
+    typedef typename SiteSum<R>::type SR;
+    SR nrm = SR(0);
+    void* outp = B.vec[out_sel];
+    if (MODE == 2) {
+      if (active) {
+        const R al = (R)st->alpha;
+        constexpr int PR = ResidPrec<PREC>::value;
+        cpx<R> r[12];
+        SpinorFmt<PR>::load(outp, g.h, cb, r);
+#pragma unroll
+        for (int q = 0; q < 12; ++q) {
+          r[q] = r[q] - al * o[q];
+          nrm += (SR)norm2(r[q]);
+        }
+        SpinorFmt<PR>::store(outp, g.h, cb, r);
       }
-      SpinorFmt<PR>::store(outp, g.h, cb, r);
-    }
-  } else if (active) {
-    if (MODE == 1) {
+    } else if (active) {
+      if (MODE == 1) {
 #pragma unroll
-      for (int q = 0; q < 12; ++q) nrm += (SR)norm2(o[q]);
+        for (int q = 0; q < 12; ++q) nrm += (SR)norm2(o[q]);
+      }
+      F::store(outp, g.h, cb, o);
     }
-    F::store(outp, g.h, cb, o);
-  }
-  if (MODE >= 1) {
-    const Reduce red{B.partials, B.counters, nullptr, st, MODE == 1 ? FIN_CG_ALPHA : FIN_CG_RR};
-    const double bs = block_sum<HOP_NT>((double)nrm, sh);
-    grid_reduce<HOP_NT>(red, 0, B.nblocks, m.y, bs, sh);
+    if (MODE >= 1) {
+      const Reduce red{B.partials, B.counters, nullptr, st, MODE == 1 ? FIN_CG_ALPHA : FIN_CG_RR};
+      const double bs = block_sum<HOP_NT>((double)nrm, sh);
+      grid_reduce<HOP_NT>(red, 0, B.nblocks, m.y, bs, sh);
+      __syncthreads();  // sh and the reduction's shared flag are reused by the next system
+    }
   }
 }
 
@@ -174,42 +228,57 @@ __global__ void __launch_bounds__(BNT) cg_update_batch_kernel(const BatchSys* __
   }
 }
 
-template <int PREC, int NREAL>
-static tm_status launch_hop_batch(const BatchSys* d_sys, const int2* d_map, int nblocks, int in_sel, int y_sel,
-                                  int out_sel, int k, int parity, int mode, bool has_y, cudaStream_t s) {
+template <int PREC, int NREAL, int K>
+static tm_status launch_hop_group(const BatchSys* d_sys, const BatchGroup* d_grp, const int2* d_map, int nblocks,
+                                  int in_sel, int y_sel, int out_sel, int kk, int parity, int mode, bool has_y,
+                                  cudaStream_t s) {
+#define TM_GARGS d_sys, d_grp, d_map, in_sel, y_sel, out_sel, kk, parity
   if (!has_y && mode == 0)
-    hop_batch_kernel<PREC, NREAL, false, 0><<<nblocks, HOP_NT, 0, s>>>(d_sys, d_map, in_sel, y_sel, out_sel, k, parity);
+    hop_group_kernel<PREC, NREAL, false, 0, K><<<nblocks, HOP_NT, 0, s>>>(TM_GARGS);
   else if (has_y && mode == 1)
-    hop_batch_kernel<PREC, NREAL, true, 1><<<nblocks, HOP_NT, 0, s>>>(d_sys, d_map, in_sel, y_sel, out_sel, k, parity);
+    hop_group_kernel<PREC, NREAL, true, 1, K><<<nblocks, HOP_NT, 0, s>>>(TM_GARGS);
   else
-    hop_batch_kernel<PREC, NREAL, true, 2><<<nblocks, HOP_NT, 0, s>>>(d_sys, d_map, in_sel, y_sel, out_sel, k, parity);
+    hop_group_kernel<PREC, NREAL, true, 2, K><<<nblocks, HOP_NT, 0, s>>>(TM_GARGS);
+#undef TM_GARGS
   count_launch();
   return cuda_check(cudaGetLastError(), "batched hopping kernel");
 }
 
-static tm_status hop_batch(int prec, int nreal, const BatchSys* d_sys, const int2* d_map, int nblocks, int in_sel,
-                           int y_sel, int out_sel, int k, int parity, int mode, bool has_y, cudaStream_t s) {
-#define TM_B(P, N) \
-  if (prec == P && nreal == N) return launch_hop_batch<P, N>(d_sys, d_map, nblocks, in_sel, y_sel, out_sel, k, parity, mode, has_y, s);
-  TM_B(TM_F32, 18) TM_B(TM_F32, 12) TM_B(TM_F32, 8) TM_B(TM_F16, 18) TM_B(TM_F16, 12) TM_B(TM_F16, 8)
+// The batched hopping launch of one sloppy form with K systems per group.
+struct GroupLaunch {
+  int prec, nreal, K;
+  const BatchSys* sys;
+  const BatchGroup* grp;
+  const int2* map;
+  int nblocks;
+};
+
+static tm_status hop_batch(const GroupLaunch& L, int in_sel, int y_sel, int out_sel, int kk, int parity, int mode,
+                           bool has_y, cudaStream_t s) {
+#define TM_B(P, N, KK)                                                                                    \
+  if (L.prec == P && L.nreal == N && L.K == KK)                                                          \
+    return launch_hop_group<P, N, KK>(L.sys, L.grp, L.map, L.nblocks, in_sel, y_sel, out_sel, kk, parity, mode, \
+                                      has_y, s);
+#define TM_BK(P, N) TM_B(P, N, 1) TM_B(P, N, 2) TM_B(P, N, 4)
+  TM_BK(TM_F32, 18) TM_BK(TM_F32, 12) TM_BK(TM_F32, 8) TM_BK(TM_F16, 18) TM_BK(TM_F16, 12) TM_BK(TM_F16, 8)
+#undef TM_BK
 #undef TM_B
   return set_error(TM_ERR_UNSUPPORTED, "batched solve: sloppy form not supported");
 }
 
 // One batched CG iteration: K1..K4 of every system, then the update.
-static tm_status batch_iteration(int prec, int nreal, const BatchSys* d_sys, const int2* d_hmap, int nh,
-                                 const int2* d_umap, int nu, BatchGlobal* d_gl, cudaGraphConditionalHandle cond,
-                                 int use_cond, cudaStream_t s) {
+static tm_status batch_iteration(const GroupLaunch& L, const int2* d_umap, int nu, BatchGlobal* d_gl,
+                                 cudaGraphConditionalHandle cond, int use_cond, cudaStream_t s) {
   tm_status st;
   // K1: T = (M_ee^-f)^-1 H_eo p ; K2: W = Qhat^-f p, <p,Ap> ; K3: T = (M_ee^f)^-1 H_eo W ; K4: r -= alpha Qhat^f W
-  if ((st = hop_batch(prec, nreal, d_sys, d_hmap, nh, 0, 0, 1, 0, 0, 0, false, s)) != TM_OK) return st;
-  if ((st = hop_batch(prec, nreal, d_sys, d_hmap, nh, 1, 0, 2, 1, 1, 1, true, s)) != TM_OK) return st;
-  if ((st = hop_batch(prec, nreal, d_sys, d_hmap, nh, 2, 0, 1, 2, 0, 0, false, s)) != TM_OK) return st;
-  if ((st = hop_batch(prec, nreal, d_sys, d_hmap, nh, 1, 2, 3, 3, 1, 2, true, s)) != TM_OK) return st;
-  if (prec == TM_F32)
-    cg_update_batch_kernel<TM_F32><<<nu, BNT, 0, s>>>(d_sys, d_umap, d_gl, cond, use_cond);
+  if ((st = hop_batch(L, 0, 0, 1, 0, 0, 0, false, s)) != TM_OK) return st;
+  if ((st = hop_batch(L, 1, 0, 2, 1, 1, 1, true, s)) != TM_OK) return st;
+  if ((st = hop_batch(L, 2, 0, 1, 2, 0, 0, false, s)) != TM_OK) return st;
+  if ((st = hop_batch(L, 1, 2, 3, 3, 1, 2, true, s)) != TM_OK) return st;
+  if (L.prec == TM_F32)
+    cg_update_batch_kernel<TM_F32><<<nu, BNT, 0, s>>>(L.sys, d_umap, d_gl, cond, use_cond);
   else
-    cg_update_batch_kernel<TM_F16><<<nu, BNT, 0, s>>>(d_sys, d_umap, d_gl, cond, use_cond);
+    cg_update_batch_kernel<TM_F16><<<nu, BNT, 0, s>>>(L.sys, d_umap, d_gl, cond, use_cond);
   count_launch();
   return cuda_check(cudaGetLastError(), "batched update kernel");
 }
@@ -248,6 +317,114 @@ struct LatWork {
   tm_lattice lat;
   void *R, *Pv, *T, *W;  // FP64 scratch for reliable updates and the final check
 };
+
+// Groups of up to K systems per lattice (in the order given) and the block map: for every
+// lattice, for every block of its sites, the blocks of its groups one after another.
+void build_groups(const std::vector<SysWork>& W, const std::vector<LatWork>& lats, int K,
+                  std::vector<BatchGroup>& grp, std::vector<int2>& map) {
+  grp.clear();
+  map.clear();
+  for (size_t li = 0; li < lats.size(); ++li) {
+    std::vector<int> mine;
+    const size_t g0 = grp.size();
+    for (size_t k = 0; k < W.size(); ++k)
+      if (W[k].lat_index == (int)li) mine.push_back((int)k);
+    for (size_t a = 0; a < mine.size(); a += K) {
+      BatchGroup G{};
+      G.n = (int)std::min<size_t>(K, mine.size() - a);
+      for (int j = 0; j < G.n; ++j) G.sys[j] = mine[a + j];
+      grp.push_back(G);
+    }
+    const int nbl = (int)hop_grid_blocks(lats[li].lat->h, 1);
+    for (int blk = 0; blk < nbl; ++blk)
+      for (size_t g = g0; g < grp.size(); ++g) map.push_back(make_int2((int)g, blk));
+  }
+}
+
+tm_status upload_groups(const std::vector<BatchGroup>& grp, const std::vector<int2>& map, GroupLaunch& L,
+                        cudaStream_t s) {
+  tm_status st = cuda_check(cudaMemcpyAsync(const_cast<BatchGroup*>(L.grp), grp.data(), sizeof(BatchGroup) * grp.size(),
+                                            cudaMemcpyHostToDevice, s),
+                            "table");
+  if (st == TM_OK)
+    st = cuda_check(cudaMemcpyAsync(const_cast<int2*>(L.map), map.data(), sizeof(int2) * map.size(),
+                                    cudaMemcpyHostToDevice, s),
+                    "table");
+  L.nblocks = (int)map.size();
+  return st;
+}
+
+// Systems per thread of the batched hopping kernel (K = 1, 2 or 4; the batch split of the
+// systems of each lattice into groups).  TM_BATCH_K=1|2|4 fixes it.  Otherwise the candidates up
+// to the largest number of systems on one lattice are timed on this batch's own vectors (a
+// plain application of the hopping operator to every system, CUDA events, the fastest of three
+// interleaved rounds of two launches each), and the fastest kept -- K > 1 must win by 3% -- and
+// remembered for later batches of the same signature (storage form, each lattice's extents and
+// number of systems).
+int env_batch_k() {
+  const char* e = getenv("TM_BATCH_K");
+  if (!e) return 0;
+  const int v = atoi(e);
+  return (v == 1 || v == 2 || v == 4) ? v : 0;
+}
+
+tm_status choose_batch_k(const std::vector<SysWork>& W, const std::vector<LatWork>& lats, int sp, int sl,
+                         GroupLaunch& L, cudaStream_t s) {
+  static std::mutex mu;
+  static std::vector<std::pair<std::vector<long long>, int>> cache;
+  std::vector<long long> sig = {sp, sl};
+  int most = 1;
+  for (size_t li = 0; li < lats.size(); ++li) {
+    int n = 0;
+    for (auto& w : W) n += (w.lat_index == (int)li);
+    most = std::max(most, n);
+    sig.push_back(lats[li].lat->T);
+    sig.push_back(lats[li].lat->L);
+    sig.push_back(n);
+  }
+  int K = env_batch_k();
+  if (K == 0) {
+    std::lock_guard<std::mutex> lock(mu);
+    for (auto& c : cache)
+      if (c.first == sig) K = c.second;
+  }
+  std::vector<BatchGroup> grp;
+  std::vector<int2> map;
+  tm_status st = TM_OK;
+  if (K == 0) {
+    const int cands[3] = {1, 2, 4};
+    float score[3] = {1e30f, 1e30f, 1e30f};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    st = cuda_check(cudaEventCreate(&e0), "event");
+    if (st == TM_OK) st = cuda_check(cudaEventCreate(&e1), "event");
+    for (int round = 0; round < 4 && st == TM_OK; ++round)
+      for (int c = 0; c < 3 && st == TM_OK; ++c) {
+        if (cands[c] > 1 && cands[c] > most) continue;
+        build_groups(W, lats, cands[c], grp, map);
+        L.K = cands[c];
+        if ((st = upload_groups(grp, map, L, s)) != TM_OK) break;
+        if ((st = cuda_check(cudaEventRecord(e0, s), "event")) != TM_OK) break;
+        for (int q = 0; q < 2 && st == TM_OK; ++q) st = hop_batch(L, 0, 0, 1, 0, q & 1, 0, false, s);
+        if (st == TM_OK) st = cuda_check(cudaEventRecord(e1, s), "event");
+        if (st == TM_OK) st = cuda_check(cudaEventSynchronize(e1), "tuner");
+        float ms = 0.f;
+        if (st == TM_OK) st = cuda_check(cudaEventElapsedTime(&ms, e0, e1), "event");
+        if (round > 0 && ms < score[c]) score[c] = ms;  // round 0 warms up
+      }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st != TM_OK) return st;
+    int bi = 0;
+    for (int c = 1; c < 3; ++c)
+      if (score[c] < 0.97f * score[bi]) bi = c;
+    K = cands[bi];
+    std::lock_guard<std::mutex> lock(mu);
+    cache.emplace_back(sig, K);
+  }
+  build_groups(W, lats, K, grp, map);
+  L.K = K;
+  return upload_groups(grp, map, L, s);
+}
 
 }  // namespace
 
@@ -326,18 +503,19 @@ extern "C" tm_status tm_solve_cg_batch(const tm_system* systems, int nsys, const
     for (int q = 0; q < 2; ++q) offs.push_back(add(96 * h));
     for (int q = 0; q < 3; ++q) offs.push_back(add(spinor_bytes_per_site(sp) * h));
   }
-  // device tables
-  int nh = 0, nu = 0;
+  // device tables (the block map has at most one entry per system and block of sites: K = 1)
+  int npart = 0, nu = 0;
   for (auto& w : W) {
-    nh += (int)hop_grid_blocks(w.lat->h, 1);
+    npart += (int)hop_grid_blocks(w.lat->h, 1);
     nu += (int)blas_blocks(w.lat->geom.h);
   }
   const size_t off_sys = add(sizeof(BatchSys) * nsys);
-  const size_t off_hmap = add(sizeof(int2) * nh);
+  const size_t off_grp = add(sizeof(BatchGroup) * nsys);
+  const size_t off_hmap = add(sizeof(int2) * npart);
   const size_t off_umap = add(sizeof(int2) * nu);
   const size_t off_state = add(sizeof(CGState) * nsys);
   const size_t off_gl = add(sizeof(BatchGlobal));
-  const size_t off_part = add(sizeof(double) * nh);
+  const size_t off_part = add(sizeof(double) * npart);
   const size_t off_ctr = add(sizeof(unsigned) * 2 * nsys);
   char* base = nullptr;
   if ((st = cuda_check(cudaMalloc(&base, total), "tm_solve_cg_batch: work space")) != TM_OK) return st;
@@ -369,7 +547,9 @@ extern "C" tm_status tm_solve_cg_batch(const tm_system* systems, int nsys, const
     }
   }
   BatchSys* d_sys = reinterpret_cast<BatchSys*>(base + off_sys);
+  BatchGroup* d_grp = reinterpret_cast<BatchGroup*>(base + off_grp);
   int2* d_hmap = reinterpret_cast<int2*>(base + off_hmap);
+  GroupLaunch GL{sp, sl, 1, d_sys, d_grp, d_hmap, 0};
   int2* d_umap = reinterpret_cast<int2*>(base + off_umap);
   CGState* d_st = reinterpret_cast<CGState*>(base + off_state);
   BatchGlobal* d_gl = reinterpret_cast<BatchGlobal*>(base + off_gl);
@@ -396,9 +576,11 @@ extern "C" tm_status tm_solve_cg_batch(const tm_system* systems, int nsys, const
       if (w.bfull == 0.0) w.converged = true;
     }
     if (st != TM_OK) break;
-    // ---- descriptor tables; blocks of systems on the same lattice interleaved site-block by site-block
+    // ---- descriptor tables; the blocks of the groups on one lattice interleaved site-block by
+    // site-block, so the K systems of a group share each link in registers and the groups of a
+    // lattice share it through L2
     {
-      std::vector<int2> hmap, umap;
+      std::vector<int2> umap;
       int pfirst = 0;
       std::vector<int> first(nsys);
       for (int k = 0; k < nsys; ++k) {
@@ -406,10 +588,6 @@ extern "C" tm_status tm_solve_cg_batch(const tm_system* systems, int nsys, const
         pfirst += (int)hop_grid_blocks(W[k].lat->h, 1);
       }
       for (size_t li = 0; li < lats.size(); ++li) {
-        const int nbl = (int)hop_grid_blocks(lats[li].lat->h, 1);
-        for (int blk = 0; blk < nbl; ++blk)
-          for (int k = 0; k < nsys; ++k)
-            if (W[k].lat_index == (int)li) hmap.push_back(make_int2(k, blk));
         const int nub = (int)blas_blocks(lats[li].lat->geom.h);
         for (int blk = 0; blk < nub; ++blk)
           for (int k = 0; k < nsys; ++k)
@@ -438,10 +616,13 @@ extern "C" tm_status tm_solve_cg_batch(const tm_system* systems, int nsys, const
       }
       st = cuda_check(cudaMemcpyAsync(d_sys, hsys.data(), sizeof(BatchSys) * nsys, cudaMemcpyHostToDevice, s), "table");
       if (st == TM_OK)
-        st = cuda_check(cudaMemcpyAsync(d_hmap, hmap.data(), sizeof(int2) * nh, cudaMemcpyHostToDevice, s), "table");
-      if (st == TM_OK)
         st = cuda_check(cudaMemcpyAsync(d_umap, umap.data(), sizeof(int2) * nu, cudaMemcpyHostToDevice, s), "table");
       if (st == TM_OK) st = cuda_check(cudaMemsetAsync(d_ctr, 0, sizeof(unsigned) * 2 * nsys, s), "memset");
+      // states with nothing stopped, for the tuner's launches
+      for (int k = 0; k < nsys && st == TM_OK; ++k) hst[k] = fresh_state(W[k].rr, W[k].stop2, P.max_iter, 0, 0.0, 0.0);
+      if (st == TM_OK)
+        st = cuda_check(cudaMemcpyAsync(d_st, hst.data(), sizeof(CGState) * nsys, cudaMemcpyHostToDevice, s), "state");
+      if (st == TM_OK) st = choose_batch_k(W, lats, sp, sl, GL, s);
       if (st == TM_OK) st = cuda_check(cudaStreamSynchronize(s), "tables");
     }
     if (st != TM_OK) break;
@@ -470,7 +651,7 @@ extern "C" tm_status tm_solve_cg_batch(const tm_system* systems, int nsys, const
         if (st == TM_OK) {
           tm_status st1 = TM_OK;
           for (int u = 0; u < cg_unroll() && st1 == TM_OK; ++u)
-            st1 = batch_iteration(sp, sl, d_sys, d_hmap, nh, d_umap, nu, d_gl, cond, 1, cs);
+            st1 = batch_iteration(GL, d_umap, nu, d_gl, cond, 1, cs);
           cudaGraph_t captured = nullptr;
           tm_status st2 = cuda_check(cudaStreamEndCapture(cs, &captured), "end capture");
           st = st1 != TM_OK ? st1 : st2;
@@ -513,7 +694,7 @@ extern "C" tm_status tm_solve_cg_batch(const tm_system* systems, int nsys, const
       } else {  // host-driven: chunks of 8 batched iterations until no system is active
         for (;;) {
           for (int q = 0; q < 8 && st == TM_OK; ++q)
-            st = batch_iteration(sp, sl, d_sys, d_hmap, nh, d_umap, nu, d_gl, 0, 0, s);
+            st = batch_iteration(GL, d_umap, nu, d_gl, 0, 0, s);
           if (st == TM_OK) st = cuda_check(cudaMemcpyAsync(&hgl, d_gl, sizeof(hgl), cudaMemcpyDeviceToHost, s), "state");
           if (st == TM_OK) st = cuda_check(cudaStreamSynchronize(s), "batched chunk");
           if (st != TM_OK || hgl.active <= 0 || hgl.loops >= hgl.loop_cap) break;

@@ -177,7 +177,72 @@ __device__ __forceinline__ void project_scaled(const cpx<typename SpinorFmt<PREC
   }
 }
 
-// First half of a pair: u = U_mu(x) (1 + gamma_mu) in(x + mu^), projected.
+// First half of a pair: u = U_mu(x) (1 + gamma_mu) in(x + mu^), projected, with the link given
+// as a matrix (pair_fwd below reconstructs it from its stored words first).
+template <int PREC, int MU>
+__device__ __forceinline__ void pair_fwd_mat(cpx<typename SpinorFmt<PREC>::real> u0[3],
+                                             cpx<typename SpinorFmt<PREC>::real> u1[3],
+                                             const Mat3<typename SpinorFmt<PREC>::real>& U,
+                                             const cpx<typename SpinorFmt<PREC>::real> p[12],
+                                             typename SpinorFmt<PREC>::real scale, bool negate) {
+  typedef typename SpinorFmt<PREC>::real R;
+  cpx<R> h0[3], h1[3];
+  project_scaled<PREC, MU, +1>(p, scale, negate, h0, h1);
+  su3_mul2_fma(U, h0, h1, u0, u1);
+}
+
+// ---- FP16 storage: the projection straight from the stored half words.  Each projected real
+// a +- b of two stored halves is one conversion of b and one mixed-precision add of a
+// (add/sub.rn.f32.f16: a half operand, FP32 result), not two conversions and an FP32 add: 12 FP32
+// pipe instructions per hop fewer.  The sum is exact in FP32 as in the converted form (two
+// halves), so the results are bitwise those of the converted projection.
+__device__ __forceinline__ unsigned short lo16(unsigned int w) { return (unsigned short)(w & 0xffffu); }
+__device__ __forceinline__ unsigned short hi16(unsigned int w) { return (unsigned short)(w >> 16); }
+__device__ __forceinline__ float cvt16(unsigned short a) { return __half2float(__ushort_as_half(a)); }
+__device__ __forceinline__ float hadd32(unsigned short a, float c) {
+  float d;
+  asm("add.rn.f32.f16 %0, %1, %2;" : "=f"(d) : "h"(a), "f"(c));
+  return d;
+}
+__device__ __forceinline__ float hsub32(unsigned short a, float c) {
+  float d;
+  asm("sub.rn.f32.f16 %0, %1, %2;" : "=f"(d) : "h"(a), "f"(c));
+  return d;
+}
+// a + q b for complex halves a, b (re low, im high) and q = +1 (Q 0), -1 (1), +i (2), -i (3)
+template <int Q>
+__device__ __forceinline__ cpx<float> padd16(unsigned int a, unsigned int b) {
+  if (Q == 0) return mk<float>(hadd32(lo16(a), cvt16(lo16(b))), hadd32(hi16(a), cvt16(hi16(b))));
+  if (Q == 1) return mk<float>(hsub32(lo16(a), cvt16(lo16(b))), hsub32(hi16(a), cvt16(hi16(b))));
+  if (Q == 2) return mk<float>(hsub32(lo16(a), cvt16(hi16(b))), hadd32(hi16(a), cvt16(lo16(b))));
+  return mk<float>(hadd32(lo16(a), cvt16(hi16(b))), hsub32(hi16(a), cvt16(lo16(b))));
+}
+// (1 + S gamma_MU) p projected (the table at the top), p the 12 half words of a site
+template <int MU, int S>
+__device__ __forceinline__ void project16(const unsigned int w[12], cpx<float> h0[3], cpx<float> h1[3]) {
+  constexpr int Q0 = MU == 0 || MU == 2 ? (S > 0 ? 1 : 0) : (S > 0 ? 3 : 2);
+  constexpr int Q1 = MU == 0 ? (S > 0 ? 1 : 0) : (MU == 1 ? (S > 0 ? 3 : 2) : (MU == 2 ? (S > 0 ? 0 : 1) : (S > 0 ? 2 : 3)));
+  constexpr int J0 = (MU == 0 || MU == 3) ? 6 : 9;  // partner of p0: p2 or p3
+  constexpr int J1 = (MU == 0 || MU == 3) ? 9 : 6;  // partner of p1: p3 or p2
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    h0[c] = padd16<Q0>(w[c], w[J0 + c]);
+    h1[c] = padd16<Q1>(w[3 + c], w[J1 + c]);
+  }
+}
+
+template <int MU, int S>
+__device__ __forceinline__ void project16_scaled(const unsigned int w[13], bool negate, cpx<float> h0[3], cpx<float> h1[3]) {
+  project16<MU, S>(w, h0, h1);
+  const float n = __uint_as_float(w[12]);
+  const float f = (MU == 0 && negate) ? -n : n;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    h0[c] = f * h0[c];
+    h1[c] = f * h1[c];
+  }
+}
+
 template <int PREC, int NREAL, int MU>
 __device__ __forceinline__ void pair_fwd(cpx<typename SpinorFmt<PREC>::real> u0[3],
                                          cpx<typename SpinorFmt<PREC>::real> u1[3],
@@ -185,27 +250,17 @@ __device__ __forceinline__ void pair_fwd(cpx<typename SpinorFmt<PREC>::real> u0[
                                          const cpx<typename SpinorFmt<PREC>::real> p[12],
                                          typename SpinorFmt<PREC>::real scale, bool negate) {
   typedef typename SpinorFmt<PREC>::real R;
-  cpx<R> h0[3], h1[3];
-  project_scaled<PREC, MU, +1>(p, scale, negate, h0, h1);
   Mat3<R> U;
   LinkRecon<R, typename LinkStore<PREC>::type, NREAL>::unpack(raw, U);
-  su3_mul2_fma(U, h0, h1, u0, u1);
+  pair_fwd_mat<PREC, MU>(u0, u1, U, p, scale, negate);
 }
 
 // Second half: the backward hop U_mu(x - mu^)^dag (1 - gamma_mu) in(x - mu^) completes the pair,
 // which is added to the accumulator (written, for the first pair of the accumulator).
-template <int PREC, int NREAL, int MU, bool FIRST>
-__device__ __forceinline__ void pair_bwd(cpx<typename SpinorFmt<PREC>::real> acc[12],
-                                         const cpx<typename SpinorFmt<PREC>::real> u0[3],
-                                         const cpx<typename SpinorFmt<PREC>::real> u1[3],
-                                         const RawWords<NREAL * LinkStore<PREC>::size>& raw,
-                                         const cpx<typename SpinorFmt<PREC>::real> p[12],
-                                         typename SpinorFmt<PREC>::real scale, bool negate) {
-  typedef typename SpinorFmt<PREC>::real R;
-  cpx<R> h0[3], h1[3];
-  project_scaled<PREC, MU, -1>(p, scale, negate, h0, h1);
-  Mat3<R> U;
-  LinkRecon<R, typename LinkStore<PREC>::type, NREAL>::unpack(raw, U);
+// The backward hop from its projected half spinor (h0, h1) onward.
+template <typename R, int MU, bool FIRST>
+__device__ __forceinline__ void pair_bwd_proj(cpx<R> acc[12], const cpx<R> u0[3], const cpx<R> u1[3], const Mat3<R>& U,
+                                              const cpx<R> h0[3], const cpx<R> h1[3]) {
   cpx<R> s0[3], s1[3];
   su3_adj_mul2_add(U, h0, h1, u0, u1, s0, s1);
 #pragma unroll
@@ -240,6 +295,32 @@ __device__ __forceinline__ void pair_bwd(cpx<typename SpinorFmt<PREC>::real> acc
   }
 }
 
+template <int PREC, int MU, bool FIRST>
+__device__ __forceinline__ void pair_bwd_mat(cpx<typename SpinorFmt<PREC>::real> acc[12],
+                                             const cpx<typename SpinorFmt<PREC>::real> u0[3],
+                                             const cpx<typename SpinorFmt<PREC>::real> u1[3],
+                                             const Mat3<typename SpinorFmt<PREC>::real>& U,
+                                             const cpx<typename SpinorFmt<PREC>::real> p[12],
+                                             typename SpinorFmt<PREC>::real scale, bool negate) {
+  typedef typename SpinorFmt<PREC>::real R;
+  cpx<R> h0[3], h1[3];
+  project_scaled<PREC, MU, -1>(p, scale, negate, h0, h1);
+  pair_bwd_proj<R, MU, FIRST>(acc, u0, u1, U, h0, h1);
+}
+
+template <int PREC, int NREAL, int MU, bool FIRST>
+__device__ __forceinline__ void pair_bwd(cpx<typename SpinorFmt<PREC>::real> acc[12],
+                                         const cpx<typename SpinorFmt<PREC>::real> u0[3],
+                                         const cpx<typename SpinorFmt<PREC>::real> u1[3],
+                                         const RawWords<NREAL * LinkStore<PREC>::size>& raw,
+                                         const cpx<typename SpinorFmt<PREC>::real> p[12],
+                                         typename SpinorFmt<PREC>::real scale, bool negate) {
+  typedef typename SpinorFmt<PREC>::real R;
+  Mat3<R> U;
+  LinkRecon<R, typename LinkStore<PREC>::type, NREAL>::unpack(raw, U);
+  pair_bwd_mat<PREC, MU, FIRST>(acc, u0, u1, U, p, scale, negate);
+}
+
 // Both hops of direction mu, loads then arithmetic.
 template <int PREC, int NREAL, int MU, bool FIRST>
 __device__ __forceinline__ void hop_pair(cpx<typename SpinorFmt<PREC>::real> acc[12], const void* in, int h,
@@ -249,13 +330,27 @@ __device__ __forceinline__ void hop_pair(cpx<typename SpinorFmt<PREC>::real> acc
   constexpr int BYTES = NREAL * LinkStore<PREC>::size;
   const RawWords<BYTES> rf = load_raw<BYTES>(slabf, h, lif);
   const RawWords<BYTES> rb = load_raw<BYTES>(slabb, h, lib);
-  cpx<R> p[12];
-  R scale;
-  SpinorFmt<PREC>::load_unscaled(in, h, nbf, p, scale);
   cpx<R> u0[3], u1[3];
-  pair_fwd<PREC, NREAL, MU>(u0, u1, rf, p, scale, negf);
-  SpinorFmt<PREC>::load_unscaled(in, h, nbb, p, scale);
-  pair_bwd<PREC, NREAL, MU, FIRST>(acc, u0, u1, rb, p, scale, negb);
+  if constexpr (PREC == TM_F16) {
+    unsigned int w[13];
+    cpx<float> h0[3], h1[3];
+    Mat3<float> U;
+    SpinorFmt<TM_F16>::load_words(in, h, nbf, w);
+    project16_scaled<MU, +1>(w, negf, h0, h1);
+    LinkRecon<float, __half, NREAL>::unpack(rf, U);
+    su3_mul2_fma(U, h0, h1, u0, u1);
+    SpinorFmt<TM_F16>::load_words(in, h, nbb, w);
+    project16_scaled<MU, -1>(w, negb, h0, h1);
+    LinkRecon<float, __half, NREAL>::unpack(rb, U);
+    pair_bwd_proj<float, MU, FIRST>(acc, u0, u1, U, h0, h1);
+  } else {
+    cpx<R> p[12];
+    R scale;
+    SpinorFmt<PREC>::load_unscaled(in, h, nbf, p, scale);
+    pair_fwd<PREC, NREAL, MU>(u0, u1, rf, p, scale, negf);
+    SpinorFmt<PREC>::load_unscaled(in, h, nbb, p, scale);
+    pair_bwd<PREC, NREAL, MU, FIRST>(acc, u0, u1, rb, p, scale, negb);
+  }
 }
 
 // One hop.  Forward (S = +1): link U_mu(x) from the output parity's slab at the output site.
@@ -337,12 +432,28 @@ __device__ __forceinline__ void hop_all_pipelined(cpx<typename SpinorFmt<PREC>::
   R scale;
   hop_fetch(A, inr, g.h, nb[0], lf + 0 * slab, cb);
   hop_fetch(B, inr, g.h, nb[4], lo + 0 * slab, nb[4]);
-#define TM_PIPE_FWD(MU, NEG)                                \
-  SpinorFmt<PREC>::unpack_words(A.sp, p, scale);            \
-  pair_fwd<PREC, NREAL, MU>(u0, u1, A.link, p, scale, NEG);
-#define TM_PIPE_BWD(MU, FIRST, NEG)                         \
-  SpinorFmt<PREC>::unpack_words(B.sp, p, scale);            \
-  pair_bwd<PREC, NREAL, MU, FIRST>(acc, u0, u1, B.link, p, scale, NEG);
+#define TM_PIPE_FWD(MU, NEG)                                                  \
+  if constexpr (PREC == TM_F16) {                                             \
+    cpx<float> h0[3], h1[3];                                                  \
+    Mat3<float> U;                                                            \
+    project16_scaled<MU, +1>(A.sp, NEG, h0, h1);                              \
+    LinkRecon<float, __half, NREAL>::unpack(A.link, U);                       \
+    su3_mul2_fma(U, h0, h1, u0, u1);                                          \
+  } else {                                                                    \
+    SpinorFmt<PREC>::unpack_words(A.sp, p, scale);                            \
+    pair_fwd<PREC, NREAL, MU>(u0, u1, A.link, p, scale, NEG);                 \
+  }
+#define TM_PIPE_BWD(MU, FIRST, NEG)                                           \
+  if constexpr (PREC == TM_F16) {                                             \
+    cpx<float> h0[3], h1[3];                                                  \
+    Mat3<float> U;                                                            \
+    project16_scaled<MU, -1>(B.sp, NEG, h0, h1);                              \
+    LinkRecon<float, __half, NREAL>::unpack(B.link, U);                       \
+    pair_bwd_proj<float, MU, FIRST>(acc, u0, u1, U, h0, h1);                  \
+  } else {                                                                    \
+    SpinorFmt<PREC>::unpack_words(B.sp, p, scale);                            \
+    pair_bwd<PREC, NREAL, MU, FIRST>(acc, u0, u1, B.link, p, scale, NEG);     \
+  }
   TM_PIPE_FWD(0, tfwd)
   hop_fetch(A, inr, g.h, nb[1], lf + 1 * slab, cb);
   TM_PIPE_BWD(0, true, tbwd)

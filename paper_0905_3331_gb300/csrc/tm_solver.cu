@@ -309,10 +309,21 @@ int cg_unroll() {
   static int v = 0;
   if (v == 0) {
     const char* e = getenv("TM_CG_UNROLL");
-    int u = e && *e ? atoi(e) : 4;
-    v = u < 1 ? 1 : (u > 8 ? 8 : u);
+    int u = e && *e ? atoi(e) : 0;
+    v = u < 0 ? 0 : (u > 8 ? 8 : u);
+    if (v == 0) v = -1;  // not set: by lattice size (cg_unroll_for)
   }
-  return v;
+  return v > 0 ? v : 4;
+}
+
+// The same for one lattice: without TM_CG_UNROLL, one iteration per body from a million sites
+// per parity on.  There an empty launch still schedules every block (~80 us for the 83 000 blocks
+// of 48^3 x 96 against ~4 us per relaunch of the body), and up to three per stage would be lost
+// to the four-iteration body.
+int cg_unroll_for(size_t h) {
+  const char* e = getenv("TM_CG_UNROLL");
+  if (e && *e) return cg_unroll();
+  return h >= ((size_t)1 << 20) ? 1 : 4;
 }
 
 // The CUDA graph of one CG stage: a WHILE conditional node whose body is cg_unroll()
@@ -356,7 +367,7 @@ static tm_status stage_graph(const Solver& S, const Stage& v, cudaGraphExec_t* o
       Solver C = S;
       C.s = cs;
       tm_status st1 = TM_OK;
-      for (int u = 0; u < cg_unroll() && st1 == TM_OK; ++u) {
+      for (int u = 0; u < cg_unroll_for(lat->h) && st1 == TM_OK; ++u) {
         st1 = normal_apply(C, v.prec, v.nreal, v.p, v.T, v.W, v.r, lat->cgstate);
         if (st1 == TM_OK) st1 = launch_update(C, v.px, v.prec, v.x, v.p, v.r, lat->cgstate, cond, 1);
       }

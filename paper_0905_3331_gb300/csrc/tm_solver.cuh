@@ -51,6 +51,7 @@ tm_status cg_normal(const Solver& S, const tm_cg_params& P, const void* bp, doub
 
 bool use_graphs();  // CUDA-graph stage loops (TM_NO_GRAPH=1 selects host-driven chunks)
 int cg_unroll();    // iterations per body of a graph loop (TM_CG_UNROLL)
+int cg_unroll_for(size_t h);  // the same for a lattice of h sites per parity
 
 // A cached CUDA graph whose only node is a WHILE conditional; its body is whatever `body`
 // enqueues on the capture stream (the body's last kernel sets the condition).  Graphs are
