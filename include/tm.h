@@ -265,12 +265,17 @@ typedef struct {
  * mixed-precision reliable-update CG of tm_solve_cg (params->mode must be TM_CG_RELIABLE;
  * FP32 or FP16 sloppy storage; FP64 updates), with the sloppy iterations of every system in
  * the same kernel launches -- blocks of systems that share a lattice interleaved so each
- * link is read from HBM once per iteration for all of them -- and each stage (iterations
- * until every system has reached its reliable-update trigger) one CUDA graph launch.  Every
- * system keeps its own CG scalars and stops on its own residual; infos[k] (may be NULL)
- * receives system k's result (seconds = the whole call).  Systems may share lattices and
- * differ in mu, flavour and source.  Synchronises `stream`.  Allocates its work space
- * (about 1.7 kB per site per system) for the duration of the call.
+ * link is read from HBM once per iteration for all of them.  The whole solve is ONE CUDA
+ * graph launch: a loop over the batched iteration, each followed, when some system has reached
+ * its reliable-update trigger (or its sloppy residual met tol, or it diverged or overflowed),
+ * by the FP64 reliable update of those systems in batched kernels (X += x, r = b' - A X in FP64)
+ * and the decision to finish or resume each.  A system is converged when that FP64 residual
+ * ||b' - A X|| / ||b'|| is below tol; the full-system FP64 residual is then computed once per
+ * system after the loop (true_rel_residual).  Every system keeps its own CG scalars and stops
+ * on its own residual; infos[k] (may be NULL) receives system k's result (seconds = the whole
+ * call).  Systems may share lattices and differ in mu, flavour and source.  Synchronises
+ * `stream`.  Allocates its work space (about 1.9 kB per odd site per system with FP32
+ * storage, plus 0.8 kB per odd site per lattice) for the duration of the call.
  * Errors: TM_ERR_NOT_CONVERGED (some systems; their x holds the last iterate), TM_ERR_ARG,
  * TM_ERR_UNSUPPORTED, TM_ERR_NO_GAUGE, TM_ERR_NONFINITE, TM_ERR_CUDA, TM_ERR_OOM. */
 tm_status tm_solve_cg_batch(const tm_system *systems, int nsys, const tm_cg_params *params,

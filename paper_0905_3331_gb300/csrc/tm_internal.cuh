@@ -848,8 +848,16 @@ struct CGState {
   int diverged;     // the stage ended because the iterated residual grew (restart p)
   int loops;        // graph loop: iteration bodies executed in this stage
   int loop_cap;     // graph loop: hard bound on loops (the loop always ends)
-  int retired;      // batched solves: this system no longer counts as active in the stage
-  int pad;
+  // batched solves, the FP64 service of a stopped system inside the solve's graph
+  int finished;     // the system is done for good (converged, failed or out of iterations)
+  int ok;           // converged: the FP64 residual met the tolerance
+  int serv_iter;    // iteration count at the last service (no progress since: breakdown)
+  int updates;      // FP64 residual recomputations
+  int missed;       // sloppy stages that reported convergence the FP64 residual did not confirm
+  int bad;          // stages dropped for a non-finite value
+  int rearm;        // set by the service for the systems it resumed (the conversions follow)
+  int restart;      // ... whose search direction restarts from the FP64 residual
+  double rr64;      // the last FP64 residual ||b' - A X||^2
 };
 
 // What the last block does with the sum of a reduction.

@@ -153,7 +153,7 @@ print("ITERS", [i.iters for i in infos])
 
 
 def test_batch_host_loop_matches_graph_loop(tmp_path):
-    """TM_NO_GRAPH=1 runs the batched stages as host-driven chunks: bitwise the same solutions."""
+    """TM_NO_GRAPH=1 runs the batched loop (iteration, FP64 service) from the host: bitwise the same solutions."""
     import os
     import subprocess
     import sys
