@@ -36,7 +36,7 @@ struct BatchSys {
   CGState* st;
   double* partials;    // reduction partials of this system (nblocks entries)
   unsigned* counters;  // [0] reductions, [1] update kernel
-  int nblocks;         // hopping blocks (HOP_NT sites each)
+  int nblocks;         // blocks of the hopping launch this table serves (hop_spb(TPS) sites each)
   int nblocks_upd;     // update-kernel blocks
   double* result;      // the FP64 service's ||b' - A X||^2 (reductions of kind FIN_STORE)
 };
@@ -47,195 +47,176 @@ struct BatchGlobal {
   int loop_cap;      // hard bound on loops
   unsigned counter;  // update-kernel blocks arrived
   int nsys;          // systems in the batch
-  int pad;
+  int services;      // executions of the FP64 service
   double delta2;     // reliable-update trigger of a resumed system
   double grow2;      // divergence guard of a resumed system
 };
 
-// Up to 4 systems of one lattice whose hopping terms one block computes together.
-struct BatchGroup {
-  int n;       // systems in the group (1 .. K of the kernel)
-  int sys[4];  // their indices in the system table (the first one's geometry and links serve all)
+// A work list: the live systems of the batch, compacted lattice by lattice and rebuilt inside the
+// graph whenever the set of running systems changes.  Virtual block v of a launch belongs to the
+// lattice li with start[li] <= v < start[li + 1]; there it is block (v - start[li]) / count[li] of
+// system items[base[li] + (v - start[li]) % count[li]], so the systems of one lattice take turns
+// block by block, read each link at about the same time and share it through L2.  Launches hold
+// as many blocks as the GPU keeps resident and walk the list with a stride: the blocks of stopped
+// and finished systems cost nothing.
+struct Plan {
+  int nlat;
+  const int* base;    // [nlat] first candidate (and item slot) of lattice li
+  const int* ncand;   // [nlat] candidates on lattice li
+  const int* blocks;  // [nlat] blocks per system on lattice li (of the launch the list serves)
+  int* start;         // [nlat + 1] first virtual block of lattice li; start[nlat] = the total
+  int* count;         // [nlat] live systems on lattice li
+  int* items;         // the live systems, lattice li's from base[li]
 };
 
-// The hopping operator of K systems at once: thread = site, the K systems of the block's group
-// are its lanes.  Each of the 8 links of the site is loaded and reconstructed ONCE and applied to
-// the K systems' neighbour spinors (the same direction-pair arithmetic as hop_kernel, per lane),
-// so a link's bytes and its reconstruction are shared by K right-hand sides in registers.  Each
-// system keeps its own epilogue coefficients (its mu), output, CG state and reduction.  A system
-// that has stopped (its stage trigger, convergence) is skipped; the block returns when all of its
-// group have.  K = 1 is the one-system case.  Register budgets: 6 blocks of 128 per SM for K = 1
-// (80 registers; latency bound: 12-system solve on 24^3 x 48 1060 -> 990 ms), 4 for K = 2, 2 for
-// K = 4 (the accumulators of K spinors).  SERV: the FP64 service of stopped systems (FP64 storage,
-// 18-real links): the live systems are those stopped and not finished, the residual update uses
-// alpha = 1 (r = b' - A X from r = b'), and the last reduction stores ||r||^2 in B.result.
-template <int PREC, int NREAL, bool HAS_Y, int MODE, int K, bool SERV = false>
-__global__ void __launch_bounds__(HOP_NT, (PREC == TM_F64 ? 1 : (K == 1 ? 6 : (K == 2 ? 4 : 2))))
-    hop_group_kernel(const BatchSys* __restrict__ systems, const BatchGroup* __restrict__ groups,
-                     const int2* __restrict__ map, int in_sel, int y_sel, int out_sel, int kk, int out_parity) {
-  typedef typename SpinorFmt<PREC>::real R;
-  typedef SpinorFmt<PREC> F;
-  typedef typename LinkStore<PREC>::type St;
-  constexpr int BYTES = NREAL * LinkStore<PREC>::size;
-  __shared__ double sh[HOP_NT / 32];
-  const int2 m = map[blockIdx.x];
-  const BatchGroup G = groups[m.x];
-  const BatchSys* S[K];
-  bool live[K];
-  bool any = false;
-#pragma unroll
-  for (int j = 0; j < K; ++j) {
-    S[j] = systems + G.sys[j < G.n ? j : 0];
-    const CGState* sj = S[j]->st;
-    live[j] = j < G.n && (SERV ? (sj->done && !sj->finished) : !sj->done);
-    any = any || live[j];
-  }
-  if (!any) return;
-  const Geom g = S[0]->g;
-  const int cb = m.y * HOP_NT + threadIdx.x;
-  const bool active = cb < g.h;
-  cpx<R> acc[K][12];
-#pragma unroll
-  for (int j = 0; j < K; ++j)
-#pragma unroll
-    for (int q = 0; q < 12; ++q) acc[j][q] = mk<R>(R(0), R(0));
-  if (active) {
-    const SiteCoord c = site_of(g, cb, out_parity);
-    int nb[8];
-    neighbours(g, cb, c, nb);
-    const size_t slab = link_bytes(PREC, NREAL) * (size_t)g.h;
-    const char* lf = S[0]->links + (size_t)(out_parity * 4) * slab;
-    const char* lo = S[0]->links + (size_t)((1 - out_parity) * 4) * slab;
-    const bool tf = (c.t == g.T - 1), tb = (c.t == 0);
-#define TM_GROUP_DIR(MU, FIRST)                                                                     \
-  {                                                                                                 \
-    cpx<R> u0[K][3], u1[K][3], p[12];                                                               \
-    R scale;                                                                                        \
-    Mat3<R> U;                                                                                      \
-    LinkRecon<R, St, NREAL>::unpack(load_raw<BYTES>(lf + MU * slab, g.h, cb), U);                   \
-    _Pragma("unroll") for (int j = 0; j < K; ++j) if (live[j]) {                                    \
-      F::load_unscaled(S[j]->vec[in_sel], g.h, nb[MU], p, scale);                                   \
-      pair_fwd_mat<PREC, MU>(u0[j], u1[j], U, p, scale, MU == 0 && tf);                             \
-    }                                                                                               \
-    LinkRecon<R, St, NREAL>::unpack(load_raw<BYTES>(lo + MU * slab, g.h, nb[4 + MU]), U);           \
-    _Pragma("unroll") for (int j = 0; j < K; ++j) if (live[j]) {                                    \
-      F::load_unscaled(S[j]->vec[in_sel], g.h, nb[4 + MU], p, scale);                               \
-      pair_bwd_mat<PREC, MU, FIRST>(acc[j], u0[j], u1[j], U, p, scale, MU == 0 && tb);              \
-    }                                                                                               \
-  }
-    TM_GROUP_DIR(0, true)
-    TM_GROUP_DIR(1, false)
-    TM_GROUP_DIR(2, false)
-    TM_GROUP_DIR(3, false)
-#undef TM_GROUP_DIR
-  }
-#pragma unroll
-  for (int j = 0; j < K; ++j) {
-    if (!live[j]) continue;  // block-uniform
-    const BatchSys& B = *S[j];
-    CGState* st = B.st;
-    const EpiCoef coef = B.coef[kk];
-    const R cc = (R)coef.c;
-    const cpx<R> Du = mk<R>((R)coef.d_up_re, (R)coef.d_up_im), Dl = mk<R>((R)coef.d_lo_re, (R)coef.d_lo_im);
-    cpx<R> o[12];
-    if (HAS_Y) {
-      const cpx<R> Eu = mk<R>((R)coef.e_up_re, (R)coef.e_up_im), El = mk<R>((R)coef.e_lo_re, (R)coef.e_lo_im);
-      cpx<R> yv[12];
-#pragma unroll
-      for (int q = 0; q < 12; ++q) yv[q] = mk<R>(R(0), R(0));
-      if (active) F::load(B.vec[y_sel], g.h, cb, yv);
-#pragma unroll
-      for (int q = 0; q < 12; ++q) o[q] = ((q < 6) ? Du : Dl) * (cc * acc[j][q] + ((q < 6) ? Eu : El) * yv[q]);
-    } else {
-#pragma unroll
-      for (int q = 0; q < 12; ++q) o[q] = ((q < 6) ? Du : Dl) * (cc * acc[j][q]);
-    }
-    typedef typename SiteSum<R>::type SR;
-    SR nrm = SR(0);
-    void* outp = B.vec[out_sel];
-    if (MODE == 2) {
-      if (active) {
-        const R al = SERV ? R(1) : (R)st->alpha;
-        constexpr int PR = ResidPrec<PREC>::value;
-        cpx<R> r[12];
-        SpinorFmt<PR>::load(outp, g.h, cb, r);
-#pragma unroll
-        for (int q = 0; q < 12; ++q) {
-          r[q] = r[q] - al * o[q];
-          nrm += (SR)norm2(r[q]);
-        }
-        SpinorFmt<PR>::store(outp, g.h, cb, r);
+// The four work lists of a batched solve: the running systems' hopping and update blocks, and the
+// FP64 service's for the systems that stopped.  The candidates are the positions in `order`.
+struct Plans {
+  Plan hop, upd, shop, supd;
+  const int* order;  // [nsys] system ids, lattice by lattice
+  CGState* states;   // [nsys] the systems' CG states
+};
+
+__device__ __forceinline__ int2 plan_item(const Plan& P, int v) {
+  int li = 0;
+  while (li + 1 < P.nlat && v >= P.start[li + 1]) ++li;
+  const int w = v - P.start[li];
+  const int c = P.count[li];
+  return make_int2(P.items[P.base[li] + w % c], w / c);
+}
+
+// Rebuilds a work list (one warp, all lanes): the candidates of a lattice are taken 32 at a time
+// and compacted with a ballot, one round of dependent loads per 32 candidates.
+__device__ void plan_build(const Plan& P, const int* order, const CGState* st, bool stopped) {
+  const unsigned lane = threadIdx.x & 31u;
+  int v = 0;
+  for (int li = 0; li < P.nlat; ++li) {
+    const int b0 = P.base[li], nc = P.ncand[li];
+    int n = 0;
+    for (int c0 = 0; c0 < nc; c0 += 32) {
+      const int c = c0 + (int)lane;
+      int id = -1;
+      if (c < nc) {
+        const int k = order[b0 + c];
+        const CGState& q = st[k];
+        if (stopped ? (q.done && !q.finished) : !q.done) id = k;
       }
-    } else if (active) {
-      if (MODE == 1) {
-#pragma unroll
-        for (int q = 0; q < 12; ++q) nrm += (SR)norm2(o[q]);
-      }
-      F::store(outp, g.h, cb, o);
+      const unsigned live = __ballot_sync(0xffffffffu, id >= 0);
+      if (id >= 0) P.items[b0 + n + __popc(live & ((1u << lane) - 1u))] = id;
+      n += __popc(live);
     }
-    if (MODE >= 1) {
-      const Reduce red{B.partials, B.counters, B.result, st, SERV ? FIN_STORE : (MODE == 1 ? FIN_CG_ALPHA : FIN_CG_RR)};
-      const double bs = block_sum<HOP_NT>((double)nrm, sh);
-      grid_reduce<HOP_NT>(red, 0, B.nblocks, m.y, bs, sh);
-      __syncthreads();  // sh and the reduction's shared flag are reused by the next system
+    if (lane == 0) {
+      P.start[li] = v;
+      P.count[li] = n;
     }
+    v += n * P.blocks[li];
+  }
+  if (lane == 0) P.start[P.nlat] = v;
+}
+
+// Work list w (0 hop, 1 upd: the running systems; 2 shop, 3 supd: the systems that stopped and are
+// not finished), rebuilt by one warp from the states as they stand.
+__device__ void plan_rebuild(const Plans& L, int w) {
+  const Plan& P = w == 0 ? L.hop : (w == 1 ? L.upd : (w == 2 ? L.shop : L.supd));
+  plan_build(P, L.order, L.states, w >= 2);
+}
+
+// All four (before the solve, and for the tuner); 4 warps.
+__global__ void plans_init_kernel(Plans L) {
+  const int w = threadIdx.x >> 5;
+  if (w < 4) plan_rebuild(L, w);
+}
+
+// The batched hopping kernel: the blocks of the listed systems, each computed by the hopping
+// kernels' own body (TPS threads per site, hop_spb(TPS) sites per block) on that system's fields,
+// epilogue coefficients (its mu), CG state and reduction.  serv = 0: the running systems, sloppy
+// storage; serv = 1: the FP64 service of stopped systems, where K4's residual update uses alpha = 1
+// (r = b' - A X from r = b') and the reduction stores ||r||^2 in B.result.  A system that stopped
+// since the list was built (a breakdown in K2) is skipped.
+#ifndef TM_BATCH_SPB1
+#define TM_BATCH_SPB1 64
+#endif
+constexpr int hop_batch_spb(int tps) { return tps == 1 ? TM_BATCH_SPB1 : hop_spb(tps); }
+constexpr int hop_batch_min_blocks(int prec, int nreal, int tps) {
+  return (tps == 1 && (prec == TM_F32 || prec == TM_F16)) ? 512 / hop_batch_spb(1) : 1;
+}
+
+template <int PREC, int NREAL, bool HAS_Y, int MODE, int TPS>
+__global__ void __launch_bounds__(hop_batch_spb(TPS) * TPS, hop_batch_min_blocks(PREC, NREAL, TPS))
+    hop_batch_kernel(const BatchSys* __restrict__ systems, const CGState* __restrict__ states, Plan plan, int serv,
+                     int in_sel, int y_sel, int out_sel, int kk, int out_parity) {
+  const int total = plan.start[plan.nlat];
+  for (int v = blockIdx.x; v < total; v += gridDim.x) {
+    const int2 m = plan_item(plan, v);
+    const CGState& S = states[m.x];
+    if (serv ? !(S.done && !S.finished) : S.done) continue;  // block-uniform
+    const BatchSys& B = systems[m.x];
+    const Reduce red{B.partials, B.counters, B.result, B.st, serv ? FIN_STORE : (MODE == 1 ? FIN_CG_ALPHA : FIN_CG_RR)};
+    hop_sites<PREC, NREAL, HAS_Y, MODE, TPS, false, ListBlock, hop_batch_spb(TPS)>(
+        B.g, out_parity, B.links, B.vec[in_sel], 0, B.vec[out_sel], 0, B.vec[y_sel], 0, B.coef[kk],
+        serv ? nullptr : B.st, 1.0, red, ListBlock{m.y, B.nblocks});
+    __syncthreads();  // the body's shared memory is reused by the next block
   }
 }
 
-// x += alpha p, p = r + beta p per system.  The last block of all sets the graph's conditions: the
-// loop runs again while a system is not finished (and below the loop cap), and the FP64 service
-// runs when a system has stopped (its reliable-update trigger, convergence of the sloppy residual,
-// divergence, a non-finite value, or its iteration bound).
+// x += alpha p, p = r + beta p per system.  The last block of all rebuilds the work lists (the
+// running systems for the next iteration, the stopped ones for the service) and sets the graph's
+// conditions: the loop runs again while a system is not finished (and below the loop cap), and
+// the FP64 service runs when a system has stopped (its reliable-update trigger, convergence of the
+// sloppy residual, divergence, a non-finite value, or its iteration bound).
 template <int PP>
-__global__ void __launch_bounds__(BNT) cg_update_batch_kernel(const BatchSys* __restrict__ systems,
-                                                              const int2* __restrict__ map, BatchGlobal* gl,
-                                                              cudaGraphConditionalHandle cond_loop,
+__global__ void __launch_bounds__(BNT) cg_update_batch_kernel(const BatchSys* __restrict__ systems, Plans L,
+                                                              BatchGlobal* gl, cudaGraphConditionalHandle cond_loop,
                                                               cudaGraphConditionalHandle cond_serv, int use_cond) {
   typedef typename SpinorFmt<PP>::real RP;
-  const int2 m = map[blockIdx.x];
-  const BatchSys& B = systems[m.x];
-  CGState& S = *B.st;
-  const int iter = S.iter;
-  const bool work = iter != S.applied;
-  if (work) {
-    const double alpha = S.alpha, beta = S.beta;
-    const int h = B.g.h;
-    char* x = static_cast<char*>(B.vec[4]);
-    char* p = static_cast<char*>(B.vec[0]);
-    const char* r = static_cast<const char*>(B.vec[3]);
-    for (int i = m.y * BNT + threadIdx.x; i < h; i += B.nblocks_upd * BNT) {
-      cpx<float> xv[12], rv[12];
-      cpx<RP> pv[12];
-      SpinorFmt<TM_F32>::load(x, h, i, xv);
-      SpinorFmt<PP>::load(p, h, i, pv);
-      SpinorFmt<TM_F32>::load(r, h, i, rv);
+  const int total = L.upd.start[L.upd.nlat];
+  for (int v = blockIdx.x; v < total; v += gridDim.x) {
+    const int2 m = plan_item(L.upd, v);
+    const BatchSys& B = systems[m.x];
+    CGState& S = L.states[m.x];
+    const int iter = S.iter;
+    const bool work = iter != S.applied;
+    if (work) {
+      const double alpha = S.alpha, beta = S.beta;
+      const int h = B.g.h;
+      char* x = static_cast<char*>(B.vec[4]);
+      char* p = static_cast<char*>(B.vec[0]);
+      const char* r = static_cast<const char*>(B.vec[3]);
+      for (int i = m.y * BNT + threadIdx.x; i < h; i += B.nblocks_upd * BNT) {
+        cpx<float> xv[12], rv[12];
+        cpx<RP> pv[12];
+        SpinorFmt<TM_F32>::load(x, h, i, xv);
+        SpinorFmt<PP>::load(p, h, i, pv);
+        SpinorFmt<TM_F32>::load(r, h, i, rv);
 #pragma unroll
-      for (int q = 0; q < 12; ++q) {
-        xv[q] = xv[q] + (float)alpha * mk<float>((float)pv[q].re, (float)pv[q].im);
-        pv[q] = rv[q] + (RP)beta * pv[q];
+        for (int q = 0; q < 12; ++q) {
+          xv[q] = xv[q] + (float)alpha * mk<float>((float)pv[q].re, (float)pv[q].im);
+          pv[q] = rv[q] + (RP)beta * pv[q];
+        }
+        SpinorFmt<TM_F32>::store(x, h, i, xv);
+        SpinorFmt<PP>::store(p, h, i, pv);
       }
-      SpinorFmt<TM_F32>::store(x, h, i, xv);
-      SpinorFmt<PP>::store(p, h, i, pv);
     }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    if (work && arrive_acq_rel(B.counters + 1) == (unsigned)B.nblocks_upd - 1) {
+    __syncthreads();  // every thread has read `applied` before the last block of the system sets it
+    if (threadIdx.x == 0 && work && arrive_acq_rel(B.counters + 1) == (unsigned)B.nblocks_upd - 1) {
       S.applied = iter;
       B.counters[1] = 0u;
     }
-    if (arrive_acq_rel(&gl->counter) == gridDim.x - 1) {  // every block's update of `applied` is visible
-      gl->counter = 0u;
-      gl->loops += 1;
-      int need = 0;
-      for (int k = 0; k < gl->nsys; ++k) {
-        const CGState& q = *systems[k].st;
-        need |= (q.done && !q.finished) ? 1 : 0;
-      }
-      if (use_cond) {
-        cudaGraphSetConditional(cond_serv, need ? 1u : 0u);
-        cudaGraphSetConditional(cond_loop, (gl->unfinished > 0 && gl->loops < gl->loop_cap) ? 1u : 0u);
-      }
+  }
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) last = arrive_acq_rel(&gl->counter) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  // the last block: every block's work is visible; warps 0..3 rebuild the four work lists
+  if ((threadIdx.x >> 5) < 4) plan_rebuild(L, threadIdx.x >> 5);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    gl->counter = 0u;
+    gl->loops += 1;
+    if (use_cond) {
+      cudaGraphSetConditional(cond_serv, L.supd.start[L.supd.nlat] > 0 ? 1u : 0u);
+      cudaGraphSetConditional(cond_loop, (gl->unfinished > 0 && gl->loops < gl->loop_cap) ? 1u : 0u);
     }
   }
 }
@@ -243,37 +224,41 @@ __global__ void __launch_bounds__(BNT) cg_update_batch_kernel(const BatchSys* __
 // ---- the FP64 service of the systems that stopped (all inside the solve's graph)
 // 1. X (FP64) += x_s (FP32; dropped after a non-finite value), x_s = 0; r (FP64) = b'.
 __global__ void __launch_bounds__(BNT) serv_begin_kernel(const BatchSys* __restrict__ sys, const BatchSys* __restrict__ sys64,
-                                                         const int2* __restrict__ map) {
-  const int2 m = map[blockIdx.x];
-  const BatchSys& B = sys[m.x];
-  const BatchSys& D = sys64[m.x];
-  const CGState& S = *B.st;
-  if (!S.done || S.finished) return;
-  const int h = B.g.h;
-  char* xs = static_cast<char*>(B.vec[4]);
-  char* X = static_cast<char*>(D.vec[0]);
-  char* R = static_cast<char*>(D.vec[3]);
-  const char* bp = static_cast<const char*>(D.vec[4]);
-  for (int i = m.y * BNT + threadIdx.x; i < h; i += B.nblocks_upd * BNT) {
-    cpx<double> a[12], b[12];
-    cpx<float> d[12];
-    SpinorFmt<TM_F32>::load(xs, h, i, d);
-    if (!S.nonfinite) {
-      SpinorFmt<TM_F64>::load(X, h, i, a);
+                                                         Plan supd) {
+  const int total = supd.start[supd.nlat];
+  for (int v = blockIdx.x; v < total; v += gridDim.x) {
+    const int2 m = plan_item(supd, v);
+    const BatchSys& B = sys[m.x];
+    const BatchSys& D = sys64[m.x];
+    const CGState& S = *B.st;
+    const int h = B.g.h;
+    char* xs = static_cast<char*>(B.vec[4]);
+    char* X = static_cast<char*>(D.vec[0]);
+    char* R = static_cast<char*>(D.vec[3]);
+    const char* bp = static_cast<const char*>(D.vec[4]);
+    for (int i = m.y * BNT + threadIdx.x; i < h; i += B.nblocks_upd * BNT) {
+      cpx<double> a[12], b[12];
+      cpx<float> d[12];
+      SpinorFmt<TM_F32>::load(xs, h, i, d);
+      if (!S.nonfinite) {
+        SpinorFmt<TM_F64>::load(X, h, i, a);
 #pragma unroll
-      for (int q = 0; q < 12; ++q) a[q] = a[q] + mk<double>((double)d[q].re, (double)d[q].im);
-      SpinorFmt<TM_F64>::store(X, h, i, a);
+        for (int q = 0; q < 12; ++q) a[q] = a[q] + mk<double>((double)d[q].re, (double)d[q].im);
+        SpinorFmt<TM_F64>::store(X, h, i, a);
+      }
+#pragma unroll
+      for (int q = 0; q < 12; ++q) d[q] = mk<float>(0.f, 0.f);
+      SpinorFmt<TM_F32>::store(xs, h, i, d);
+      SpinorFmt<TM_F64>::load(bp, h, i, b);
+      SpinorFmt<TM_F64>::store(R, h, i, b);
     }
-#pragma unroll
-    for (int q = 0; q < 12; ++q) d[q] = mk<float>(0.f, 0.f);
-    SpinorFmt<TM_F32>::store(xs, h, i, d);
-    SpinorFmt<TM_F64>::load(bp, h, i, b);
-    SpinorFmt<TM_F64>::store(R, h, i, b);
   }
 }
 
-// 3. The decision per stopped system, from its FP64 residual rr64 = ||b' - A X||^2 (one block).
-__global__ void serv_decide_kernel(const BatchSys* __restrict__ sys, BatchGlobal* gl) {
+// 3. The decision per stopped system, from its FP64 residual rr64 = ||b' - A X||^2 (one block);
+// then the running systems' work lists, with the resumed systems in them.
+__global__ void serv_decide_kernel(const BatchSys* __restrict__ sys, Plans L,
+                                   BatchGlobal* gl) {
   for (int k = threadIdx.x; k < gl->nsys; k += blockDim.x) {
     const BatchSys& B = sys[k];
     CGState& S = *B.st;
@@ -319,76 +304,98 @@ __global__ void serv_decide_kernel(const BatchSys* __restrict__ sys, BatchGlobal
     S.want_update = 0;
     S.diverged = 0;
   }
+  __syncthreads();
+  if ((threadIdx.x >> 5) < 2) plan_rebuild(L, threadIdx.x >> 5);
+  if (threadIdx.x == 0) gl->services += 1;
 }
 
 // 4. r_s (FP32) = r, and p = r (sloppy) for a restart, for the systems the decision resumed.
 template <int PP>
 __global__ void __launch_bounds__(BNT) serv_convert_kernel(const BatchSys* __restrict__ sys,
-                                                           const BatchSys* __restrict__ sys64,
-                                                           const int2* __restrict__ map) {
-  const int2 m = map[blockIdx.x];
-  const BatchSys& B = sys[m.x];
-  const CGState& S = *B.st;
-  if (!S.rearm) return;
-  const int h = B.g.h;
-  const char* R = static_cast<const char*>(sys64[m.x].vec[3]);
-  char* rs = static_cast<char*>(B.vec[3]);
-  char* ps = static_cast<char*>(B.vec[0]);
-  for (int i = m.y * BNT + threadIdx.x; i < h; i += B.nblocks_upd * BNT) {
-    cpx<double> a[12];
-    SpinorFmt<TM_F64>::load(R, h, i, a);
-    SpinorFmt<TM_F32>::store(rs, h, i, a);
-    if (S.restart) SpinorFmt<PP>::store(ps, h, i, a);
+                                                           const BatchSys* __restrict__ sys64, Plan supd) {
+  const int total = supd.start[supd.nlat];
+  for (int v = blockIdx.x; v < total; v += gridDim.x) {
+    const int2 m = plan_item(supd, v);
+    const BatchSys& B = sys[m.x];
+    const CGState& S = *B.st;
+    if (!S.rearm) continue;
+    const int h = B.g.h;
+    const char* R = static_cast<const char*>(sys64[m.x].vec[3]);
+    char* rs = static_cast<char*>(B.vec[3]);
+    char* ps = static_cast<char*>(B.vec[0]);
+    for (int i = m.y * BNT + threadIdx.x; i < h; i += B.nblocks_upd * BNT) {
+      cpx<double> a[12];
+      SpinorFmt<TM_F64>::load(R, h, i, a);
+      SpinorFmt<TM_F32>::store(rs, h, i, a);
+      if (S.restart) SpinorFmt<PP>::store(ps, h, i, a);
+    }
   }
 }
 
-template <int PREC, int NREAL, int K, bool SERV>
-static tm_status launch_hop_group(const BatchSys* d_sys, const BatchGroup* d_grp, const int2* d_map, int nblocks,
+// Blocks of a launch: as many as the GPU keeps resident (at most `cap`, the blocks of a full list).
+template <class Kern>
+static int resident_grid(Kern kern, int threads, int cap) {
+  int dev = 0, nsm = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, 0);
+  return std::max(1, std::min(cap, std::max(1, per) * std::max(1, nsm)));
+}
+
+template <int PREC, int NREAL, int TPS>
+static tm_status launch_hop_batch(const BatchSys* d_sys, const CGState* d_st, const Plan& plan, int cap, int serv,
                                   int in_sel, int y_sel, int out_sel, int kk, int parity, int mode, bool has_y,
                                   cudaStream_t s) {
-#define TM_GARGS d_sys, d_grp, d_map, in_sel, y_sel, out_sel, kk, parity
+  constexpr int NT = hop_batch_spb(TPS) * TPS;
+#define TM_GL(HY, MD)                                                                                  \
+  {                                                                                                    \
+    auto kern = hop_batch_kernel<PREC, NREAL, HY, MD, TPS>;                                            \
+    kern<<<resident_grid(kern, NT, cap), NT, 0, s>>>(d_sys, d_st, plan, serv, in_sel, y_sel, out_sel, kk, \
+                                                     parity);                                          \
+  }
   if (!has_y && mode == 0)
-    hop_group_kernel<PREC, NREAL, false, 0, K, SERV><<<nblocks, HOP_NT, 0, s>>>(TM_GARGS);
+    TM_GL(false, 0)
   else if (has_y && mode == 0)
-    hop_group_kernel<PREC, NREAL, true, 0, K, SERV><<<nblocks, HOP_NT, 0, s>>>(TM_GARGS);
+    TM_GL(true, 0)
   else if (has_y && mode == 1)
-    hop_group_kernel<PREC, NREAL, true, 1, K, SERV><<<nblocks, HOP_NT, 0, s>>>(TM_GARGS);
+    TM_GL(true, 1)
   else
-    hop_group_kernel<PREC, NREAL, true, 2, K, SERV><<<nblocks, HOP_NT, 0, s>>>(TM_GARGS);
-#undef TM_GARGS
+    TM_GL(true, 2)
+#undef TM_GL
   count_launch();
   return cuda_check(cudaGetLastError(), "batched hopping kernel");
 }
 
-// The batched hopping launch of one storage form with K systems per group (FP64 with K = 1 for the
-// service of stopped systems).
-struct GroupLaunch {
-  int prec, nreal, K;
+// The batched hopping launches of one storage form and TPS (FP64 with TPS 1 for the service of
+// stopped systems).
+struct BatchLaunch {
+  int prec, nreal, tps;
+  int serv;
   const BatchSys* sys;
-  const BatchGroup* grp;
-  const int2* map;
-  int nblocks;
+  const CGState* st;
+  Plan plan;
+  int cap;  // blocks of the full list
 };
 
-static tm_status hop_batch(const GroupLaunch& L, int in_sel, int y_sel, int out_sel, int kk, int parity, int mode,
+static tm_status hop_batch(const BatchLaunch& L, int in_sel, int y_sel, int out_sel, int kk, int parity, int mode,
                            bool has_y, cudaStream_t s) {
   if (L.prec == TM_F64)
-    return launch_hop_group<TM_F64, 18, 1, true>(L.sys, L.grp, L.map, L.nblocks, in_sel, y_sel, out_sel, kk, parity,
-                                                 mode, has_y, s);
-#define TM_B(P, N, KK)                                                                                    \
-  if (L.prec == P && L.nreal == N && L.K == KK)                                                          \
-    return launch_hop_group<P, N, KK, false>(L.sys, L.grp, L.map, L.nblocks, in_sel, y_sel, out_sel, kk, parity, \
-                                             mode, has_y, s);
-#define TM_BK(P, N) TM_B(P, N, 1) TM_B(P, N, 2) TM_B(P, N, 4)
-  TM_BK(TM_F32, 18) TM_BK(TM_F32, 12) TM_BK(TM_F32, 8) TM_BK(TM_F16, 18) TM_BK(TM_F16, 12) TM_BK(TM_F16, 8)
-#undef TM_BK
+    return launch_hop_batch<TM_F64, 18, 1>(L.sys, L.st, L.plan, L.cap, L.serv, in_sel, y_sel, out_sel, kk, parity, mode,
+                                           has_y, s);
+#define TM_B(P, N, T)                                                                                      \
+  if (L.prec == P && L.nreal == N && L.tps == T)                                                          \
+    return launch_hop_batch<P, N, T>(L.sys, L.st, L.plan, L.cap, L.serv, in_sel, y_sel, out_sel, kk, parity, mode, \
+                                     has_y, s);
+#define TM_BT(P, N) TM_B(P, N, 1) TM_B(P, N, 2) TM_B(P, N, 4)
+  TM_BT(TM_F32, 18) TM_BT(TM_F32, 12) TM_BT(TM_F32, 8) TM_BT(TM_F16, 18) TM_BT(TM_F16, 12) TM_BT(TM_F16, 8)
+#undef TM_BT
 #undef TM_B
   return set_error(TM_ERR_UNSUPPORTED, "batched solve: sloppy form not supported");
 }
 
-// One batched CG iteration: K1..K4 of every running system, then the update (which sets the graph
-// conditions).
-static tm_status batch_iteration(const GroupLaunch& L, const int2* d_umap, int nu, BatchGlobal* d_gl,
+// One batched CG iteration: K1..K4 of every running system, then the update (which rebuilds the
+// work lists and sets the graph conditions).
+static tm_status batch_iteration(const BatchLaunch& L, const Plans& plans, int ucap, BatchGlobal* d_gl,
                                  cudaGraphConditionalHandle cond_loop, cudaGraphConditionalHandle cond_serv,
                                  int use_cond, cudaStream_t s) {
   tm_status st;
@@ -397,21 +404,24 @@ static tm_status batch_iteration(const GroupLaunch& L, const int2* d_umap, int n
   if ((st = hop_batch(L, 1, 0, 2, 1, 1, 1, true, s)) != TM_OK) return st;
   if ((st = hop_batch(L, 2, 0, 1, 2, 0, 0, false, s)) != TM_OK) return st;
   if ((st = hop_batch(L, 1, 2, 3, 3, 1, 2, true, s)) != TM_OK) return st;
-  if (L.prec == TM_F32)
-    cg_update_batch_kernel<TM_F32><<<nu, BNT, 0, s>>>(L.sys, d_umap, d_gl, cond_loop, cond_serv, use_cond);
-  else
-    cg_update_batch_kernel<TM_F16><<<nu, BNT, 0, s>>>(L.sys, d_umap, d_gl, cond_loop, cond_serv, use_cond);
+  if (L.prec == TM_F32) {
+    auto kern = cg_update_batch_kernel<TM_F32>;
+    kern<<<resident_grid(kern, BNT, ucap), BNT, 0, s>>>(L.sys, plans, d_gl, cond_loop, cond_serv, use_cond);
+  } else {
+    auto kern = cg_update_batch_kernel<TM_F16>;
+    kern<<<resident_grid(kern, BNT, ucap), BNT, 0, s>>>(L.sys, plans, d_gl, cond_loop, cond_serv, use_cond);
+  }
   count_launch();
   return cuda_check(cudaGetLastError(), "batched update kernel");
 }
 
 // The FP64 service of the stopped systems: X += x_s, r = b' - A X in FP64 (the normal operator's four
 // hopping launches, K2 without its reduction, K4 storing ||r||^2), the decision, and the conversions
-// of the resumed systems.  Systems that did not stop skip every launch.
-static tm_status batch_service(const GroupLaunch& D, const BatchSys* d_sys, int sp, const int2* d_umap, int nu,
-                               BatchGlobal* d_gl, cudaStream_t s) {
+// of the resumed systems.  Each launch walks the stopped systems' work lists only.
+static tm_status batch_service(const BatchLaunch& D, const BatchSys* d_sys, int sp,
+                               const Plans& plans, int ucap, BatchGlobal* d_gl, cudaStream_t s) {
   tm_status st;
-  serv_begin_kernel<<<nu, BNT, 0, s>>>(d_sys, D.sys, d_umap);
+  serv_begin_kernel<<<resident_grid(serv_begin_kernel, BNT, ucap), BNT, 0, s>>>(d_sys, D.sys, plans.supd);
   count_launch();
   if ((st = cuda_check(cudaGetLastError(), "batched service")) != TM_OK) return st;
   // FP64 vectors: 0 X, 1 T, 2 W, 3 r
@@ -419,12 +429,15 @@ static tm_status batch_service(const GroupLaunch& D, const BatchSys* d_sys, int 
   if ((st = hop_batch(D, 1, 0, 2, 1, 1, 0, true, s)) != TM_OK) return st;
   if ((st = hop_batch(D, 2, 0, 1, 2, 0, 0, false, s)) != TM_OK) return st;
   if ((st = hop_batch(D, 1, 2, 3, 3, 1, 2, true, s)) != TM_OK) return st;
-  serv_decide_kernel<<<1, 128, 0, s>>>(d_sys, d_gl);
+  serv_decide_kernel<<<1, 128, 0, s>>>(d_sys, plans, d_gl);
   count_launch();
-  if (sp == TM_F32)
-    serv_convert_kernel<TM_F32><<<nu, BNT, 0, s>>>(d_sys, D.sys, d_umap);
-  else
-    serv_convert_kernel<TM_F16><<<nu, BNT, 0, s>>>(d_sys, D.sys, d_umap);
+  if (sp == TM_F32) {
+    auto kern = serv_convert_kernel<TM_F32>;
+    kern<<<resident_grid(kern, BNT, ucap), BNT, 0, s>>>(d_sys, D.sys, plans.supd);
+  } else {
+    auto kern = serv_convert_kernel<TM_F16>;
+    kern<<<resident_grid(kern, BNT, ucap), BNT, 0, s>>>(d_sys, D.sys, plans.supd);
+  }
   count_launch();
   return cuda_check(cudaGetLastError(), "batched service");
 }
@@ -462,80 +475,95 @@ struct LatWork {
   void *R, *Pv, *T, *W;  // FP64 scratch for reliable updates and the final check
 };
 
-// Groups of up to K systems per lattice (in the order given) and the block map: for every
-// lattice, for every block of its sites, the blocks of its groups one after another.
-void build_groups(const std::vector<SysWork>& W, const std::vector<LatWork>& lats, int K,
-                  std::vector<BatchGroup>& grp, std::vector<int2>& map) {
-  grp.clear();
-  map.clear();
-  for (size_t li = 0; li < lats.size(); ++li) {
-    std::vector<int> mine;
-    const size_t g0 = grp.size();
-    for (size_t k = 0; k < W.size(); ++k)
-      if (W[k].lat_index == (int)li) mine.push_back((int)k);
-    for (size_t a = 0; a < mine.size(); a += K) {
-      BatchGroup G{};
-      G.n = (int)std::min<size_t>(K, mine.size() - a);
-      for (int j = 0; j < G.n; ++j) G.sys[j] = mine[a + j];
-      grp.push_back(G);
+// The batch by lattice, and the device arrays of its work lists.  Device ints, in this order:
+// order[nsys]; per lattice sys_base, sys_cnt, hop_blk (blocks per system of the sloppy hopping
+// launch), upd_blk (of the update), shop_blk (of the FP64 service's hopping launch); then for each
+// of the four lists start[nlat + 1], count[nlat], items[nsys].
+struct BatchLayout {
+  static constexpr int NPER = 5;
+  int nlat = 0, nsys = 0;
+  std::vector<int> host;  // the static part (order and the per-lattice arrays)
+  int* dev = nullptr;
+  CGState* states = nullptr;
+  static size_t ints(int nlat, int nsys) { return (size_t)nsys + NPER * nlat + 4 * ((size_t)2 * nlat + 1 + nsys); }
+  int* at(int q) const { return dev + nsys + q * nlat; }        // q-th per-lattice array (device)
+  int& hat(int q, int li) { return host[nsys + q * nlat + li]; }  // ... and its host copy
+  Plans plans() const {
+    Plans L;
+    int* dyn = dev + nsys + NPER * nlat;
+    Plan* all[4] = {&L.hop, &L.upd, &L.shop, &L.supd};
+    const int blocks[4] = {2, 3, 4, 3};
+    for (int q = 0; q < 4; ++q) {
+      Plan& P = *all[q];
+      P.nlat = nlat;
+      P.base = at(0);
+      P.ncand = at(1);
+      P.blocks = at(blocks[q]);
+      P.start = dyn;
+      P.count = dyn + nlat + 1;
+      P.items = dyn + 2 * nlat + 1;
+      dyn += 2 * nlat + 1 + nsys;
     }
-    const int nbl = (int)hop_grid_blocks(lats[li].lat->h, 1);
-    for (int blk = 0; blk < nbl; ++blk)
-      for (size_t g = g0; g < grp.size(); ++g) map.push_back(make_int2((int)g, blk));
+    L.order = dev;
+    L.states = states;
+    return L;
   }
+  tm_status upload(cudaStream_t s) const {
+    tm_status st = cuda_check(cudaMemcpyAsync(dev, host.data(), sizeof(int) * host.size(), cudaMemcpyHostToDevice, s),
+                              "work lists");
+    if (st != TM_OK) return st;
+    plans_init_kernel<<<1, 128, 0, s>>>(plans());
+    count_launch();
+    return cuda_check(cudaGetLastError(), "work lists");
+  }
+};
+
+// The sloppy hopping launch's threads per site (1, 2 or 4; hop_spb(TPS) sites per block) for a
+// batch: sets the blocks per system in the layout and the system table, and uploads both.
+tm_status set_batch_tps(int tps, const std::vector<SysWork>& W, const std::vector<LatWork>& lats, BatchLayout& Y,
+                        std::vector<BatchSys>& hsys, BatchSys* d_sys, BatchLaunch& L, cudaStream_t s) {
+  const int spb = hop_batch_spb(tps);
+  for (int li = 0; li < Y.nlat; ++li) Y.hat(2, li) = (int)((lats[li].lat->h + spb - 1) / spb);
+  for (size_t k = 0; k < W.size(); ++k) hsys[k].nblocks = (int)((W[k].lat->h + spb - 1) / spb);
+  L.tps = tps;
+  tm_status st = cuda_check(
+      cudaMemcpyAsync(d_sys, hsys.data(), sizeof(BatchSys) * hsys.size(), cudaMemcpyHostToDevice, s), "table");
+  return st == TM_OK ? Y.upload(s) : st;
 }
 
-tm_status upload_groups(const std::vector<BatchGroup>& grp, const std::vector<int2>& map, GroupLaunch& L,
-                        cudaStream_t s) {
-  tm_status st = cuda_check(cudaMemcpyAsync(const_cast<BatchGroup*>(L.grp), grp.data(), sizeof(BatchGroup) * grp.size(),
-                                            cudaMemcpyHostToDevice, s),
-                            "table");
-  if (st == TM_OK)
-    st = cuda_check(cudaMemcpyAsync(const_cast<int2*>(L.map), map.data(), sizeof(int2) * map.size(),
-                                    cudaMemcpyHostToDevice, s),
-                    "table");
-  L.nblocks = (int)map.size();
-  return st;
-}
-
-// Systems per thread of the batched hopping kernel (K = 1, 2 or 4; the batch split of the
-// systems of each lattice into groups).  TM_BATCH_K=1|2|4 fixes it.  Otherwise the candidates up
-// to the largest number of systems on one lattice are timed on this batch's own vectors (a
-// plain application of the hopping operator to every system, CUDA events, the fastest of three
-// interleaved rounds of two launches each), and the fastest kept -- K > 1 must win by 3% -- and
-// remembered for later batches of the same signature (storage form, each lattice's extents and
-// number of systems).
-int env_batch_k() {
-  const char* e = getenv("TM_BATCH_K");
+// Threads per site of the batched hopping kernel.  TM_BATCH_TPS=1|2|4 fixes it.  Otherwise 1, 2
+// and 4 are timed on this batch's own vectors (a plain application of the hopping operator to
+// every system, CUDA events, the fastest of three interleaved rounds of two launches each) and
+// the fastest kept -- more threads per site must win by 3% -- and remembered for later batches of
+// the same signature (storage form, each lattice's extents and number of systems).
+int env_batch_tps() {
+  const char* e = getenv("TM_BATCH_TPS");
   if (!e) return 0;
   const int v = atoi(e);
   return (v == 1 || v == 2 || v == 4) ? v : 0;
 }
 
-tm_status choose_batch_k(const std::vector<SysWork>& W, const std::vector<LatWork>& lats, int sp, int sl,
-                         GroupLaunch& L, cudaStream_t s) {
+tm_status choose_batch_tps(const std::vector<SysWork>& W, const std::vector<LatWork>& lats, int sp, int sl,
+                           BatchLayout& Y, std::vector<BatchSys>& hsys, BatchSys* d_sys, BatchLaunch& L,
+                           cudaStream_t s) {
   static std::mutex mu;
   static std::vector<std::pair<std::vector<long long>, int>> cache;
   std::vector<long long> sig = {sp, sl};
-  int most = 1;
   for (size_t li = 0; li < lats.size(); ++li) {
     int n = 0;
     for (auto& w : W) n += (w.lat_index == (int)li);
-    most = std::max(most, n);
     sig.push_back(lats[li].lat->T);
     sig.push_back(lats[li].lat->L);
     sig.push_back(n);
   }
-  int K = env_batch_k();
-  if (K == 0) {
+  int tps = env_batch_tps();
+  if (tps == 0) {
     std::lock_guard<std::mutex> lock(mu);
     for (auto& c : cache)
-      if (c.first == sig) K = c.second;
+      if (c.first == sig) tps = c.second;
   }
-  std::vector<BatchGroup> grp;
-  std::vector<int2> map;
   tm_status st = TM_OK;
-  if (K == 0) {
+  if (tps == 0) {
     const int cands[3] = {1, 2, 4};
     float score[3] = {1e30f, 1e30f, 1e30f};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -543,10 +571,7 @@ tm_status choose_batch_k(const std::vector<SysWork>& W, const std::vector<LatWor
     if (st == TM_OK) st = cuda_check(cudaEventCreate(&e1), "event");
     for (int round = 0; round < 4 && st == TM_OK; ++round)
       for (int c = 0; c < 3 && st == TM_OK; ++c) {
-        if (cands[c] > 1 && cands[c] > most) continue;
-        build_groups(W, lats, cands[c], grp, map);
-        L.K = cands[c];
-        if ((st = upload_groups(grp, map, L, s)) != TM_OK) break;
+        if ((st = set_batch_tps(cands[c], W, lats, Y, hsys, d_sys, L, s)) != TM_OK) break;
         if ((st = cuda_check(cudaEventRecord(e0, s), "event")) != TM_OK) break;
         for (int q = 0; q < 2 && st == TM_OK; ++q) st = hop_batch(L, 0, 0, 1, 0, q & 1, 0, false, s);
         if (st == TM_OK) st = cuda_check(cudaEventRecord(e1, s), "event");
@@ -561,13 +586,11 @@ tm_status choose_batch_k(const std::vector<SysWork>& W, const std::vector<LatWor
     int bi = 0;
     for (int c = 1; c < 3; ++c)
       if (score[c] < 0.97f * score[bi]) bi = c;
-    K = cands[bi];
+    tps = cands[bi];
     std::lock_guard<std::mutex> lock(mu);
-    cache.emplace_back(sig, K);
+    cache.emplace_back(sig, tps);
   }
-  build_groups(W, lats, K, grp, map);
-  L.K = K;
-  return upload_groups(grp, map, L, s);
+  return set_batch_tps(tps, W, lats, Y, hsys, d_sys, L, s);
 }
 
 }  // namespace
@@ -647,19 +670,18 @@ extern "C" tm_status tm_solve_cg_batch(const tm_system* systems, int nsys, const
     for (int q = 0; q < 2; ++q) offs.push_back(add(96 * h));
     for (int q = 0; q < 3; ++q) offs.push_back(add(spinor_bytes_per_site(sp) * h));
   }
-  // device tables (a block map has at most one entry per system and block of sites: K = 1)
+  // device tables; npart bounds the blocks of a full hopping work list (32 sites per block at
+  // least) and so the reduction partials, nu is the blocks of a full update work list
   int npart = 0, nu = 0;
-  for (auto& w : W) {
-    npart += (int)hop_grid_blocks(w.lat->h, 1);
-    nu += (int)blas_blocks(w.lat->geom.h);
+  std::vector<int> first(nsys);
+  for (int k = 0; k < nsys; ++k) {
+    first[k] = npart;
+    npart += (int)((W[k].lat->h + 31) / 32);
+    nu += (int)blas_blocks(W[k].lat->geom.h);
   }
   const size_t off_sys = add(sizeof(BatchSys) * nsys);
   const size_t off_sys64 = add(sizeof(BatchSys) * nsys);
-  const size_t off_grp = add(sizeof(BatchGroup) * nsys);
-  const size_t off_grp1 = add(sizeof(BatchGroup) * nsys);
-  const size_t off_hmap = add(sizeof(int2) * npart);
-  const size_t off_hmap1 = add(sizeof(int2) * npart);
-  const size_t off_umap = add(sizeof(int2) * nu);
+  const size_t off_ints = add(sizeof(int) * BatchLayout::ints((int)lats.size(), nsys));
   const size_t off_state = add(sizeof(CGState) * nsys);
   const size_t off_gl = add(sizeof(BatchGlobal));
   const size_t off_part = add(sizeof(double) * npart);
@@ -701,13 +723,24 @@ extern "C" tm_status tm_solve_cg_batch(const tm_system* systems, int nsys, const
   }
   BatchSys* d_sys = reinterpret_cast<BatchSys*>(base + off_sys);
   BatchSys* d_sys64 = reinterpret_cast<BatchSys*>(base + off_sys64);
-  BatchGroup* d_grp = reinterpret_cast<BatchGroup*>(base + off_grp);
-  BatchGroup* d_grp1 = reinterpret_cast<BatchGroup*>(base + off_grp1);
-  int2* d_hmap = reinterpret_cast<int2*>(base + off_hmap);
-  int2* d_hmap1 = reinterpret_cast<int2*>(base + off_hmap1);
-  GroupLaunch GL{sp, sl, 1, d_sys, d_grp, d_hmap, 0};
-  GroupLaunch GD{TM_F64, 18, 1, d_sys64, d_grp1, d_hmap1, 0};
-  int2* d_umap = reinterpret_cast<int2*>(base + off_umap);
+  BatchLayout Y;
+  Y.nlat = (int)lats.size();
+  Y.nsys = nsys;
+  Y.dev = reinterpret_cast<int*>(base + off_ints);
+  Y.states = reinterpret_cast<CGState*>(base + off_state);
+  Y.host.assign((size_t)nsys + BatchLayout::NPER * Y.nlat, 0);
+  for (int li = 0, c = 0; li < Y.nlat; ++li) {  // order, sys_base, sys_cnt, hop_blk, upd_blk, shop_blk
+    Y.hat(0, li) = c;
+    for (int k = 0; k < nsys; ++k)
+      if (W[k].lat_index == li) Y.host[c++] = k;
+    Y.hat(1, li) = c - Y.hat(0, li);
+    Y.hat(2, li) = (int)((lats[li].lat->h + hop_batch_spb(1) - 1) / hop_batch_spb(1));
+    Y.hat(3, li) = (int)blas_blocks(lats[li].lat->geom.h);
+    Y.hat(4, li) = (int)((lats[li].lat->h + hop_batch_spb(1) - 1) / hop_batch_spb(1));
+  }
+  const Plans plans = Y.plans();
+  BatchLaunch GL{sp, sl, 1, 0, d_sys, plans.states, plans.hop, npart};
+  BatchLaunch GD{TM_F64, 18, 1, 1, d_sys64, plans.states, plans.shop, npart};
   CGState* d_st = reinterpret_cast<CGState*>(base + off_state);
   BatchGlobal* d_gl = reinterpret_cast<BatchGlobal*>(base + off_gl);
   double* d_part = reinterpret_cast<double*>(base + off_part);
@@ -715,6 +748,18 @@ extern "C" tm_status tm_solve_cg_batch(const tm_system* systems, int nsys, const
   double* d_res = reinterpret_cast<double*>(base + off_res);
   const double delta2 = P.delta * P.delta;
   int unfinished = 0;
+  // TM_VERBOSE=1: the host time of each phase (the stream synchronised at each mark)
+  char phases[256] = "";
+  auto tprev = std::chrono::steady_clock::now();
+  auto mark = [&](const char* name) {
+    if (!batch_verbose()) return;
+    cudaStreamSynchronize(s);
+    const auto now = std::chrono::steady_clock::now();
+    const size_t n = strlen(phases);
+    snprintf(phases + n, sizeof(phases) - n, " %s %.2f ms", name,
+             std::chrono::duration<double, std::milli>(now - tprev).count());
+    tprev = now;
+  };
 
   do {
     // ---- per system: source preparation (FP64), initial vectors
@@ -736,23 +781,9 @@ extern "C" tm_status tm_solve_cg_batch(const tm_system* systems, int nsys, const
       if (w.bfull == 0.0) w.converged = true;
     }
     if (st != TM_OK) break;
-    // ---- descriptor tables; the blocks of the groups on one lattice interleaved site-block by
-    // site-block, so the K systems of a group share each link in registers and the groups of a
-    // lattice share it through L2
+    mark("sources");
+    // ---- descriptor tables, groups and work lists
     {
-      std::vector<int2> umap;
-      int pfirst = 0;
-      std::vector<int> first(nsys);
-      for (int k = 0; k < nsys; ++k) {
-        first[k] = pfirst;
-        pfirst += (int)hop_grid_blocks(W[k].lat->h, 1);
-      }
-      for (size_t li = 0; li < lats.size(); ++li) {
-        const int nub = (int)blas_blocks(lats[li].lat->geom.h);
-        for (int blk = 0; blk < nub; ++blk)
-          for (int k = 0; k < nsys; ++k)
-            if (W[k].lat_index == (int)li) umap.push_back(make_int2(k, blk));
-      }
       for (int k = 0; k < nsys; ++k) {
         SysWork& w = W[k];
         BatchSys& B = hsys[k];
@@ -771,7 +802,7 @@ extern "C" tm_status tm_solve_cg_batch(const tm_system* systems, int nsys, const
         B.st = d_st + k;
         B.partials = d_part + first[k];
         B.counters = d_ctr + 2 * k;
-        B.nblocks = (int)hop_grid_blocks(w.lat->h, 1);
+        B.nblocks = (int)((w.lat->h + hop_batch_spb(1) - 1) / hop_batch_spb(1));  // the FP64 service's; the sloppy per TPS
         B.nblocks_upd = (int)blas_blocks(w.lat->geom.h);
         B.result = d_res + k;
         // the FP64 service's table: the FP64 gauge copy, X, T, W, r and b'
@@ -788,20 +819,12 @@ extern "C" tm_status tm_solve_cg_batch(const tm_system* systems, int nsys, const
       if (st == TM_OK)
         st = cuda_check(cudaMemcpyAsync(d_sys64, hsys64.data(), sizeof(BatchSys) * nsys, cudaMemcpyHostToDevice, s),
                         "table");
-      if (st == TM_OK)
-        st = cuda_check(cudaMemcpyAsync(d_umap, umap.data(), sizeof(int2) * nu, cudaMemcpyHostToDevice, s), "table");
       if (st == TM_OK) st = cuda_check(cudaMemsetAsync(d_ctr, 0, sizeof(unsigned) * 2 * nsys, s), "memset");
       // states with nothing stopped, for the tuner's launches
       for (int k = 0; k < nsys && st == TM_OK; ++k) hst[k] = fresh_state(W[k].rr, W[k].stop2, P.max_iter, 0, 0.0, 0.0);
       if (st == TM_OK)
         st = cuda_check(cudaMemcpyAsync(d_st, hst.data(), sizeof(CGState) * nsys, cudaMemcpyHostToDevice, s), "state");
-      if (st == TM_OK) st = choose_batch_k(W, lats, sp, sl, GL, s);
-      if (st == TM_OK) {  // the service's map: one system per group
-        std::vector<BatchGroup> g1;
-        std::vector<int2> m1;
-        build_groups(W, lats, 1, g1, m1);
-        st = upload_groups(g1, m1, GD, s);
-      }
+      if (st == TM_OK) st = choose_batch_tps(W, lats, sp, sl, Y, hsys, d_sys, GL, s);
       if (st == TM_OK) st = cuda_check(cudaStreamSynchronize(s), "tables");
     }
     if (st != TM_OK) break;
@@ -822,6 +845,11 @@ extern "C" tm_status tm_solve_cg_batch(const tm_system* systems, int nsys, const
     hgl = BatchGlobal{unfinished, 0, P.max_iter + 16, 0u, nsys, 0, delta2, SLOPPY_GROWTH * SLOPPY_GROWTH};
     st = cuda_check(cudaMemcpyAsync(d_st, hst.data(), sizeof(CGState) * nsys, cudaMemcpyHostToDevice, s), "state");
     if (st == TM_OK) st = cuda_check(cudaMemcpyAsync(d_gl, &hgl, sizeof(hgl), cudaMemcpyHostToDevice, s), "state");
+    if (st == TM_OK) {
+      plans_init_kernel<<<1, 128, 0, s>>>(plans);
+      count_launch();
+      st = cuda_check(cudaGetLastError(), "work lists");
+    }
     if (st != TM_OK) break;
     // ---- the solve: ONE graph launch, a WHILE loop over { batched iteration; IF (a system stopped)
     // { FP64 service } }.  With TM_NO_GRAPH=1 the same kernels run from the host in chunks of 8
@@ -855,7 +883,7 @@ extern "C" tm_status tm_solve_cg_batch(const tm_system* systems, int nsys, const
         st = cuda_check(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal),
                         "begin capture");
         if (st == TM_OK) {
-          tm_status st1 = batch_iteration(GL, d_umap, nu, d_gl, cond_loop, cond_serv, 1, cs);
+          tm_status st1 = batch_iteration(GL, plans, nu, d_gl, cond_loop, cond_serv, 1, cs);
           // the IF node after the iteration, added to the graph being captured
           if (st1 == TM_OK) {
             cudaStreamCaptureStatus cst;
@@ -885,13 +913,14 @@ extern "C" tm_status tm_solve_cg_batch(const tm_system* systems, int nsys, const
         st = cuda_check(cudaStreamBeginCaptureToGraph(cs, serv_body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal),
                         "begin capture");
         if (st == TM_OK) {
-          tm_status st1 = batch_service(GD, d_sys, sp, d_umap, nu, d_gl, cs);
+          tm_status st1 = batch_service(GD, d_sys, sp, plans, nu, d_gl, cs);
           cudaGraph_t captured = nullptr;
           tm_status st2 = cuda_check(cudaStreamEndCapture(cs, &captured), "end capture");
           st = st1 != TM_OK ? st1 : st2;
         }
       }
       if (st == TM_OK) st = cuda_check(cudaGraphInstantiate(&exec, graph, 0), "graph instantiate");
+      mark("tables+graph");
       tm_reset_launch_count();
       count_launch((unsigned)before);
       if (st == TM_OK) st = cuda_check(cudaGraphLaunch(exec, s), "graph launch");
@@ -900,12 +929,14 @@ extern "C" tm_status tm_solve_cg_batch(const tm_system* systems, int nsys, const
       if (st == TM_OK) st = cuda_check(cudaMemcpyAsync(&hgl, d_gl, sizeof(hgl), cudaMemcpyDeviceToHost, s), "state");
       if (st == TM_OK) st = cuda_check(cudaStreamSynchronize(s), "batched solve");
       if (st != TM_OK) break;
-      count_launch(5u * (unsigned)hgl.loops);
+      mark("solve");
+      count_launch(5u * (unsigned)hgl.loops + 7u * (unsigned)hgl.services);
     } else {
+      mark("tables");
       for (;;) {
         for (int q = 0; q < 8 && st == TM_OK; ++q) {
-          st = batch_iteration(GL, d_umap, nu, d_gl, 0, 0, 0, s);
-          if (st == TM_OK) st = batch_service(GD, d_sys, sp, d_umap, nu, d_gl, s);
+          st = batch_iteration(GL, plans, nu, d_gl, 0, 0, 0, s);
+          if (st == TM_OK) st = batch_service(GD, d_sys, sp, plans, nu, d_gl, s);
         }
         if (st == TM_OK) st = cuda_check(cudaMemcpyAsync(&hgl, d_gl, sizeof(hgl), cudaMemcpyDeviceToHost, s), "state");
         if (st == TM_OK) st = cuda_check(cudaStreamSynchronize(s), "batched chunk");
@@ -915,6 +946,7 @@ extern "C" tm_status tm_solve_cg_batch(const tm_system* systems, int nsys, const
         st = cuda_check(cudaMemcpyAsync(hst.data(), d_st, sizeof(CGState) * nsys, cudaMemcpyDeviceToHost, s), "state");
       if (st == TM_OK) st = cuda_check(cudaStreamSynchronize(s), "batched solve");
       if (st != TM_OK) break;
+      mark("solve");
     }
     for (int k = 0; k < nsys; ++k) {
       SysWork& w = W[k];
@@ -949,6 +981,9 @@ extern "C" tm_status tm_solve_cg_batch(const tm_system* systems, int nsys, const
       if (infos) infos[k] = info;
     }
     if (st == TM_OK) st = cuda_check(cudaStreamSynchronize(s), "synchronise");
+    mark("reconstruction");
+    if (batch_verbose())
+      fprintf(stderr, "[tm_solve_cg_batch] %d loops, %d FP64 services;%s\n", hgl.loops, hgl.services, phases);
   } while (false);
   if (exec) cudaGraphExecDestroy(exec);
   if (graph) cudaGraphDestroy(graph);

@@ -548,30 +548,46 @@ constexpr int hop_min_blocks(int prec, int nreal, int tps, bool pipe) {
               : ((tps == 1 && (prec == TM_F32 || prec == TM_F16)) ? (nreal == 12 ? HOP_BLOCKS_12 : HOP_BLOCKS_OTHER) : 1);
 }
 
-template <int PREC, int NREAL, bool HAS_Y, int MODE, int TPS, bool PIPE>
-__global__ void __launch_bounds__(hop_spb(TPS) * TPS, hop_min_blocks(PREC, NREAL, TPS, PIPE)) hop_kernel(const Geom g, const int out_parity,
-                                                     const char* __restrict__ links, const void* in,
-                                                     size_t in_stride, void* out, size_t out_stride,
-                                                     const void* y, size_t y_stride, const EpiCoef coef,
-                                                     const CGState* alpha_src, const double alpha_sign,
-                                                     const Reduce red, const int* skip) {
+// Which block of which right-hand side a block of the hopping kernel computes: the CUDA grid's
+// (block x of gridDim.x, right-hand side y), read where used like the kernel's own indices ...
+struct GridBlock {
+  __device__ __forceinline__ int bid() const { return blockIdx.x; }
+  __device__ __forceinline__ int nblocks() const { return gridDim.x; }
+  __device__ __forceinline__ int rhs() const { return blockIdx.y; }
+};
+// ... or a block of a batched solver's work list (right-hand side 0 of one system's fields)
+struct ListBlock {
+  int b, n;
+  __device__ __forceinline__ int bid() const { return b; }
+  __device__ __forceinline__ int nblocks() const { return n; }
+  __device__ __forceinline__ int rhs() const { return 0; }
+};
+
+// The body of the hopping kernels: output sites [bid SPB, (bid + 1) SPB) of right-hand side rhs
+// (fields at in + rhs in_stride, ...), block bid of nblocks (from B).  alpha (MODE 2): r -= alpha o
+// with alpha = alpha_sign * alpha_src[rhs].alpha, or alpha_sign without alpha_src; the norms of
+// MODE >= 1 go to the reduction red of system rhs.  Shared by hop_kernel and the batched solver's
+// kernel.  The field pointers are formed where they are used, as from a kernel's parameters, so
+// that they hold no registers across the hops.
+template <int PREC, int NREAL, bool HAS_Y, int MODE, int TPS, bool PIPE, class Blk, int SPB = hop_spb(TPS)>
+__device__ __forceinline__ void hop_sites(const Geom g, const int out_parity, const char* __restrict__ links,
+                                          const void* in, size_t in_stride, void* out, size_t out_stride,
+                                          const void* y, size_t y_stride, const EpiCoef coef,
+                                          const CGState* alpha_src, const double alpha_sign, const Reduce red,
+                                          const Blk B) {
   typedef typename SpinorFmt<PREC>::real R;
   typedef SpinorFmt<PREC> F;
-  constexpr int SPB = hop_spb(TPS);        // sites per block
-  constexpr int NT = SPB * TPS;            // threads per block
+  constexpr int NT = SPB * TPS;            // threads per block (SPB sites per block)
   constexpr int WPP = (NT / 32) / TPS;     // warps per part
   constexpr int STRIDE = 25;               // 24 reals per site, padded against bank conflicts
   __shared__ double sh[NT / 32];
   __shared__ R part_acc[TPS > 1 ? TPS * SPB * STRIDE : 1];
   __shared__ float part_max[(TPS > 1 && F::has_norm) ? TPS * SPB : 1];
-  pdl_wait();
-  pdl_allow();
-  if (skip != nullptr && *skip != 0) return;
-  const int rhs = blockIdx.y;
   const int warp = threadIdx.x >> 5;
   const int part = (TPS == 1) ? 0 : warp / WPP;
   const int sib = (TPS == 1) ? threadIdx.x : (warp % WPP) * 32 + (threadIdx.x & 31);
-  const int cb = blockIdx.x * SPB + sib;
+  const int rhs = B.rhs();
+  const int cb = B.bid() * SPB + sib;
   const bool active = cb < g.h;
   cpx<R> acc[12];
 #pragma unroll
@@ -688,8 +704,22 @@ __global__ void __launch_bounds__(hop_spb(TPS) * TPS, hop_min_blocks(PREC, NREAL
   }
   if (MODE >= 1) {
     const double bs = block_sum<NT>((double)nrm, sh);
-    grid_reduce<NT>(red, rhs, gridDim.x, blockIdx.x, bs, sh);
+    grid_reduce<NT>(red, rhs, B.nblocks(), B.bid(), bs, sh);
   }
+}
+
+template <int PREC, int NREAL, bool HAS_Y, int MODE, int TPS, bool PIPE>
+__global__ void __launch_bounds__(hop_spb(TPS) * TPS, hop_min_blocks(PREC, NREAL, TPS, PIPE)) hop_kernel(const Geom g, const int out_parity,
+                                                     const char* __restrict__ links, const void* in,
+                                                     size_t in_stride, void* out, size_t out_stride,
+                                                     const void* y, size_t y_stride, const EpiCoef coef,
+                                                     const CGState* alpha_src, const double alpha_sign,
+                                                     const Reduce red, const int* skip) {
+  pdl_wait();
+  pdl_allow();
+  if (skip != nullptr && *skip != 0) return;
+  hop_sites<PREC, NREAL, HAS_Y, MODE, TPS, PIPE>(g, out_parity, links, in, in_stride, out, out_stride, y, y_stride, coef,
+                                                 alpha_src, alpha_sign, red, GridBlock{});
 }
 
 // the two-sites-per-thread kernel (tm_dslash_pair.cuh), instantiated in its own units
