@@ -15,7 +15,8 @@ reports the mean solve time -- a driver for captures of the two-flavour hopping 
 
 With --batch N it runs `iters` batched solves (tm_solve_cg_batch, FP32/FP16 sloppy storage per
 --form, delta 1e-3) of N Gaussian sources on the workload's lattice and reports the mean time
--- a driver for captures of the batched hopping kernel.
+-- a driver for captures of the batched hopping kernel.  With --batch N --single the same N
+systems are solved one after another with tm_solve_cg (the same form and delta), for comparison.
 
 With --contract it runs `iters` meson contractions (tm_meson_contract) of 12 Gaussian
 propagators on the workload's lattice and reports the mean time, bytes and FP64 rate.
@@ -54,6 +55,7 @@ def main():
     ap.add_argument("--delta", type=float, default=0.001, help="reliable-update delta of the doublet and batched solves")
     ap.add_argument("--contract", action="store_true", help="time meson contractions instead")
     ap.add_argument("--batch", type=int, default=0, help="time batched solves of this many sources")
+    ap.add_argument("--single", action="store_true", help="with --batch: solve the sources one at a time")
     ap.add_argument("--fma-probe", action="store_true", help="measure the FP64 / FP32 FMA rates instead")
     args = ap.parse_args()
     if args.fma_probe:
@@ -110,7 +112,7 @@ def main():
 def batch(args):
     import torch
 
-    from paper_0905_3331_gb300 import Lattice, inputs, solve_cg_batch
+    from paper_0905_3331_gb300 import CG_RELIABLE, Lattice, inputs, solve_cg_batch
     from paper_0905_3331_gb300 import build as libbuild
     libbuild.build()
     prec = {"f32": 1, "f16": 2}[args.form.split(":")[0]]
@@ -124,19 +126,30 @@ def batch(args):
         b = torch.from_numpy(w.source(k)).to(dev)
         systems.append((lat, w.mu, torch.zeros_like(b), b))
     kw = dict(sloppy_prec=prec, sloppy_link=nreal, delta=args.delta)
-    infos = solve_cg_batch(systems, **kw)
+
+    def solve():
+        if not args.single:
+            return solve_cg_batch(systems, **kw)
+        out = []
+        for _, _, x, b in systems:
+            x.zero_()
+            out.append(lat.solve_cg(x, b, mode=CG_RELIABLE, **kw))
+        return out
+
+    infos = solve()
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
     times = []
     for _ in range(args.iters):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        infos = solve_cg_batch(systems, **kw)
+        infos = solve()
         e1.record(stream)
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1) / 1e3)
     t = statistics.mean(times)
-    print(json.dumps({"workload": w.name, "form": args.form, "systems": args.batch, "ms": t * 1e3,
+    print(json.dumps({"workload": w.name, "form": args.form, "systems": args.batch,
+                      "mode": "single" if args.single else "batched", "ms": t * 1e3,
                       "systems_per_s": args.batch / t, "iters": [i.iters for i in infos],
                       "max_true_rel_residual": max(i.true_rel_residual for i in infos)}))
     lat.close()
