@@ -50,6 +50,7 @@ def main():
     ap.add_argument("--iters", type=int, default=5)
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--warm", action="store_true", help="do not flush L2 between launches")
+    ap.add_argument("--parity", type=int, default=-1, help="output parity 0 or 1 (default: alternate)")
     ap.add_argument("--tps", type=int, default=0, help="threads per site 1/2/4 (0: autotuned)")
     ap.add_argument("--doublet", default=None, help="MUBAR,EPSBAR: time doublet solves instead")
     ap.add_argument("--delta", type=float, default=0.001, help="reliable-update delta of the doublet and batched solves")
@@ -92,7 +93,7 @@ def main():
         if not args.warm:
             flush.zero_()
         e0.record(stream)
-        lat.apply_hopping_eo(k & 1, dout, din, prec, nreal, nrhs=args.nrhs)
+        lat.apply_hopping_eo(k & 1 if args.parity < 0 else args.parity, dout, din, prec, nreal, nrhs=args.nrhs)
         e1.record(stream)
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1) / 1e3)
