@@ -633,17 +633,22 @@ __device__ __forceinline__ void hop_sites(const Geom g, const int out_parity, co
   // epilogue: o_s = D_s (c acc_s + E_s y_s) on components [kb, ke), evaluated as
   // (D_s c) acc_s + (D_s E_s) y_s with the two coefficients formed once in FP64 (24 multiplies
   // per site fewer); MODE 3 needs t = c acc + E y itself and keeps the factored form
+  constexpr bool F32A = sizeof(R) == 4;  // FP32 arithmetic: the host-folded FP32 coefficients
   const R cc = (R)coef.c;
   const cpx<R> Du = mk<R>((R)coef.d_up_re, (R)coef.d_up_im), Dl = mk<R>((R)coef.d_lo_re, (R)coef.d_lo_im);
-  const cpx<R> DCu = mk<R>((R)(coef.d_up_re * coef.c), (R)(coef.d_up_im * coef.c));
-  const cpx<R> DCl = mk<R>((R)(coef.d_lo_re * coef.c), (R)(coef.d_lo_im * coef.c));
+  const cpx<R> DCu = F32A ? mk<R>((R)coef.f_dcu_re, (R)coef.f_dcu_im)
+                          : mk<R>((R)(coef.d_up_re * coef.c), (R)(coef.d_up_im * coef.c));
+  const cpx<R> DCl = F32A ? mk<R>((R)coef.f_dcl_re, (R)coef.f_dcl_im)
+                          : mk<R>((R)(coef.d_lo_re * coef.c), (R)(coef.d_lo_im * coef.c));
   cpx<R> o[12];
   if (HAS_Y) {
     const cpx<R> Eu = mk<R>((R)coef.e_up_re, (R)coef.e_up_im), El = mk<R>((R)coef.e_lo_re, (R)coef.e_lo_im);
-    const cpx<R> DEu = mk<R>((R)(coef.d_up_re * coef.e_up_re - coef.d_up_im * coef.e_up_im),
-                             (R)(coef.d_up_re * coef.e_up_im + coef.d_up_im * coef.e_up_re));
-    const cpx<R> DEl = mk<R>((R)(coef.d_lo_re * coef.e_lo_re - coef.d_lo_im * coef.e_lo_im),
-                             (R)(coef.d_lo_re * coef.e_lo_im + coef.d_lo_im * coef.e_lo_re));
+    const cpx<R> DEu = F32A ? mk<R>((R)coef.f_deu_re, (R)coef.f_deu_im)
+                            : mk<R>((R)(coef.d_up_re * coef.e_up_re - coef.d_up_im * coef.e_up_im),
+                                    (R)(coef.d_up_re * coef.e_up_im + coef.d_up_im * coef.e_up_re));
+    const cpx<R> DEl = F32A ? mk<R>((R)coef.f_del_re, (R)coef.f_del_im)
+                            : mk<R>((R)(coef.d_lo_re * coef.e_lo_re - coef.d_lo_im * coef.e_lo_im),
+                                    (R)(coef.d_lo_re * coef.e_lo_im + coef.d_lo_im * coef.e_lo_re));
     cpx<R> yv[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) yv[k] = mk<R>(R(0), R(0));
@@ -668,7 +673,9 @@ __device__ __forceinline__ void hop_sites(const Geom g, const int out_parity, co
   char* outr = static_cast<char*>(out) + (size_t)rhs * out_stride;
   if (MODE == 2) {
     if (active) {
-      const R al = (R)(alpha_src ? alpha_sign * alpha_src[rhs].alpha : alpha_sign);
+      // (FP32 arithmetic: the sign, +-1, applied after the rounding, with the same result)
+      const R al = F32A ? (alpha_src ? (R)alpha_sign * (R)alpha_src[rhs].alpha : (R)alpha_sign)
+                        : (R)(alpha_src ? alpha_sign * alpha_src[rhs].alpha : alpha_sign);
       constexpr int PR = ResidPrec<PREC>::value;
       cpx<R> r[12];
       SpinorFmt<PR>::load_range(outr, g.h, cb, r, kb, ke);
@@ -703,7 +710,7 @@ __device__ __forceinline__ void hop_sites(const Geom g, const int out_parity, co
     }
   }
   if (MODE >= 1) {
-    const double bs = block_sum<NT>((double)nrm, sh);
+    const double bs = block_sum<NT>(nrm, sh);  // SR: FP32 for FP32 arithmetic
     grid_reduce<NT>(red, rhs, B.nblocks(), B.bid(), bs, sh);
   }
 }

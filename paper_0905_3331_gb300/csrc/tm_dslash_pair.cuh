@@ -160,15 +160,12 @@ __global__ void __launch_bounds__(PAIR_NT, HOP_PAIR_BLOCKS)
     for (int k = 0; k < 12; ++k) acc[k] = mk<f2>(f2(0.f), f2(0.f));
   }
   // epilogue o_s = D_s (c acc_s + E_s y_s) = (D_s c) acc_s + (D_s E_s) y_s, per chirality
-  const cpx<double> Du = mk<double>(coef.d_up_re, coef.d_up_im), Dl = mk<double>(coef.d_lo_re, coef.d_lo_im);
-  const cpx<f2> DCu = mk<f2>(f2((float)(Du.re * coef.c)), f2((float)(Du.im * coef.c)));
-  const cpx<f2> DCl = mk<f2>(f2((float)(Dl.re * coef.c)), f2((float)(Dl.im * coef.c)));
+  const cpx<f2> DCu = mk<f2>(f2(coef.f_dcu_re), f2(coef.f_dcu_im));  // folded on the host (epi_finish)
+  const cpx<f2> DCl = mk<f2>(f2(coef.f_dcl_re), f2(coef.f_dcl_im));
   cpx<f2> o[12];
   if (HAS_Y) {
-    const cpx<f2> DEu = mk<f2>(f2((float)(Du.re * coef.e_up_re - Du.im * coef.e_up_im)),
-                               f2((float)(Du.re * coef.e_up_im + Du.im * coef.e_up_re)));
-    const cpx<f2> DEl = mk<f2>(f2((float)(Dl.re * coef.e_lo_re - Dl.im * coef.e_lo_im)),
-                               f2((float)(Dl.re * coef.e_lo_im + Dl.im * coef.e_lo_re)));
+    const cpx<f2> DEu = mk<f2>(f2(coef.f_deu_re), f2(coef.f_deu_im));
+    const cpx<f2> DEl = mk<f2>(f2(coef.f_del_re), f2(coef.f_del_im));
     cpx<float> ya[12], yb[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) ya[k] = yb[k] = mk<float>(0.f, 0.f);
@@ -191,7 +188,7 @@ __global__ void __launch_bounds__(PAIR_NT, HOP_PAIR_BLOCKS)
   cpx<float> oa[12], ob[12];
   if (MODE == 2) {
     if (act_a) {
-      const f2 al((float)(alpha_src ? alpha_sign * alpha_src[rhs].alpha : alpha_sign));
+      const f2 al(alpha_src ? (float)alpha_sign * (float)alpha_src[rhs].alpha : (float)alpha_sign);
       constexpr int PR = ResidPrec<PREC>::value;
       cpx<float> ra[12], rb[12];
       SpinorFmt<PR>::load_range(outr, g.h, cba, ra, 0, 12);

@@ -815,7 +815,14 @@ struct EpiCoef {
   double d_up_re, d_up_im, d_lo_re, d_lo_im;
   double e_up_re, e_up_im, e_lo_re, e_lo_im;
   double m_up_re, m_up_im, m_lo_re, m_lo_im;  // the inverse of D (residual epilogue, mode 3)
+  // For the FP32 arithmetic of the FP32 / FP16 kernels: D c and D E formed in FP64 and rounded
+  // once, on the host (epi_finish).  GB300 runs FP64 and FP64 -> FP32 conversions at ~1/64 of the
+  // FP32 rate; forming these per thread kept the FP64 pipe 44% busy in the hopping launches with
+  // a y input (FP16/12 on 32^3 x 64).
+  float f_dcu_re, f_dcu_im, f_dcl_re, f_dcl_im;
+  float f_deu_re, f_deu_im, f_del_re, f_del_im;
 };
+EpiCoef epi_finish(EpiCoef e);  // fills the FP32 fields from the FP64 ones
 
 // Epilogue coefficient sets used by the operators (eq. eo0, eo2, eo3, App. B.2).
 EpiCoef epi_plain();                                    // out = H in
@@ -953,6 +960,28 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     for (int w = 0; w < NT / 32; ++w) s += sh[w];
   }
   return s;  // valid in thread 0
+}
+
+// The same for FP32 per-thread sums (FP32 / FP16 storage): the warp's shuffle tree in FP32, the
+// warps and everything after in FP64.  GB300 runs FP64 adds at ~1/64 of the FP32 rate; the FP64
+// tree cost 5 of them per thread.
+template <int NT>
+__device__ __forceinline__ double block_sum(float v, double* sh) {
+#ifdef TM_WARP_SUM_F64
+  return block_sum<NT>((double)v, sh);
+#else
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) sh[warp] = (double)v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int w = 0; w < NT / 32; ++w) s += sh[w];
+  }
+  return s;  // valid in thread 0
+#endif
 }
 
 // Called by every thread of every block with the block's contribution (valid in thread 0).

@@ -45,11 +45,22 @@ bool is_device_pointer(const void* p) {
 }
 
 // ------------------------------------------------------- epilogue coefficients ---
+EpiCoef epi_finish(EpiCoef e) {
+  e.f_dcu_re = (float)(e.d_up_re * e.c);
+  e.f_dcu_im = (float)(e.d_up_im * e.c);
+  e.f_dcl_re = (float)(e.d_lo_re * e.c);
+  e.f_dcl_im = (float)(e.d_lo_im * e.c);
+  e.f_deu_re = (float)(e.d_up_re * e.e_up_re - e.d_up_im * e.e_up_im);
+  e.f_deu_im = (float)(e.d_up_re * e.e_up_im + e.d_up_im * e.e_up_re);
+  e.f_del_re = (float)(e.d_lo_re * e.e_lo_re - e.d_lo_im * e.e_lo_im);
+  e.f_del_im = (float)(e.d_lo_re * e.e_lo_im + e.d_lo_im * e.e_lo_re);
+  return e;
+}
 EpiCoef epi_plain() {
   EpiCoef e{};
   e.c = 1.0;
   e.d_up_re = e.d_lo_re = 1.0;
-  return e;
+  return epi_finish(e);
 }
 EpiCoef epi_mdiag_inv_hop(double mut, int f) {  // (1 - i f mut g5) / (1 + mut^2) H
   EpiCoef e{};
@@ -59,7 +70,7 @@ EpiCoef epi_mdiag_inv_hop(double mut, int f) {  // (1 - i f mut g5) / (1 + mut^2
   e.d_up_im = -f * mut * n;
   e.d_lo_re = n;
   e.d_lo_im = f * mut * n;
-  return e;
+  return epi_finish(e);
 }
 EpiCoef epi_scaled_minv(double mut, int f, double c) {  // (M_ee^f)^-1 (c H + y)
   EpiCoef e = epi_mdiag_inv_hop(mut, f);
@@ -68,7 +79,7 @@ EpiCoef epi_scaled_minv(double mut, int f, double c) {  // (M_ee^f)^-1 (c H + y)
   e.m_up_re = e.m_lo_re = 1.0;  // M_ee^f = 1 + i f mut gamma5
   e.m_up_im = f * mut;
   e.m_lo_im = -f * mut;
-  return e;
+  return epi_finish(e);
 }
 EpiCoef epi_full_M(double kappa, double mut, int f) {  // (1 + i f mut g5) y - kappa H
   EpiCoef e{};
@@ -78,14 +89,14 @@ EpiCoef epi_full_M(double kappa, double mut, int f) {  // (1 + i f mut g5) y - k
   e.e_up_im = f * mut;
   e.e_lo_re = 1.0;
   e.e_lo_im = -f * mut;
-  return e;
+  return epi_finish(e);
 }
 EpiCoef epi_schur_q(double kappa, double mut, int f) {  // g5 [(1 + i f mut g5) y - kappa^2 H]
   EpiCoef e = epi_full_M(kappa * kappa, mut, f);
   e.c = -kappa * kappa;
   e.d_up_re = 1.0;
   e.d_lo_re = -1.0;
-  return e;
+  return epi_finish(e);
 }
 EpiCoef epi_g5_y_plus(double c) {  // g5 (y + c H)
   EpiCoef e{};
@@ -93,7 +104,7 @@ EpiCoef epi_g5_y_plus(double c) {  // g5 (y + c H)
   e.d_up_re = 1.0;
   e.d_lo_re = -1.0;
   e.e_up_re = e.e_lo_re = 1.0;
-  return e;
+  return epi_finish(e);
 }
 
 // ------------------------------------------------------------------ buffers ---
