@@ -77,9 +77,9 @@ __global__ void __launch_bounds__(BNT) dsite_kernel(int h, const char* a, const 
   constexpr int PR = ResidPrec<P>::value;
   typedef typename SpinorFmt<PR>::real RR;
   __shared__ double sh[BNT / 32];
-  double acc = 0.0;
-  const double al = MODE == 2 ? (alpha_src ? alpha_src->alpha : 1.0) : 0.0;
   typedef typename SiteSum<R>::type SR;
+  SR acc = SR(0);  // this thread's sites: FP32 for FP32 data (the warp tree too), FP64 after
+  const double al = MODE == 2 ? (alpha_src ? alpha_src->alpha : 1.0) : 0.0;
   for (int i = blockIdx.x * BNT + threadIdx.x; i < h; i += gridDim.x * BNT) {
     SR site = SR(0);
     cpx<R> va[2][12], vb[2][12], o[2][12];
@@ -96,8 +96,8 @@ __global__ void __launch_bounds__(BNT) dsite_kernel(int h, const char* a, const 
         cpx<R> s = mk<R>(R(0), R(0));
 #pragma unroll
         for (int g = 0; g < 2; ++g) {
-          if (a) s = s + mk<R>((R)co.P[c][f][g][0], (R)co.P[c][f][g][1]) * va[g][k];
-          if (b) s = s + mk<R>((R)co.Q[c][f][g][0], (R)co.Q[c][f][g][1]) * vb[g][k];
+          if (a) s = s + dco<R>(co.P[c][f][g], co.fP[c][f][g]) * va[g][k];
+          if (b) s = s + dco<R>(co.Q[c][f][g], co.fQ[c][f][g]) * vb[g][k];
         }
         o[f][k] = s;
       }
@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(BNT) dsite_kernel(int h, const char* a, const 
             site += (SR)norm2(o[f][k]);
       }
     }
-    acc += (double)site;
+    acc += site;
   }
   if (MODE != 0) {
     const double bs = block_sum<BNT>(acc, sh);
@@ -157,8 +157,9 @@ static tm_status dsite(const DSolver& D, int prec, int mode, const void* a, cons
   const char* bc = static_cast<const char*>(b);
   char* oc = static_cast<char*>(out);
   char* rc = static_cast<char*>(r);
+  const DCoef cf = dcoef_finish(co);
 #define DSITE_LAUNCH(PP, MM) \
-  dsite_kernel<PP, MM><<<nb, BNT, 0, D.S.s>>>(h, ac, bc, oc, st, rc, rst, co, red, skip, alpha_src)
+  dsite_kernel<PP, MM><<<nb, BNT, 0, D.S.s>>>(h, ac, bc, oc, st, rc, rst, cf, red, skip, alpha_src)
   if (mode != 0) return set_error(TM_ERR_ARG, "internal: doublet site kernel mode %d", mode);
   if (prec == TM_F64)
     DSITE_LAUNCH(TM_F64, 0);

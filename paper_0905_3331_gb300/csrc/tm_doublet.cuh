@@ -12,7 +12,27 @@ struct DCoef {
   double P[2][2][2][2];  // [chirality][f_out][f_in][re, im]
   double Q[2][2][2][2];
   int swap;
+  // the same rounded to FP32 once on the host (dcoef_finish), for the FP32 arithmetic of the
+  // reduced-precision kernels: GB300 converts FP64 to FP32 on its narrow FP64 pipe
+  float fP[2][2][2][2], fQ[2][2][2][2];
 };
+inline DCoef dcoef_finish(DCoef c) {
+  constexpr int N = (int)(sizeof(c.P) / sizeof(c.P[0][0][0][0]));
+  static_assert(sizeof(c.fP) / sizeof(c.fP[0][0][0][0]) == N && sizeof(c.Q) == sizeof(c.P), "coefficient sizes");
+  for (int i = 0; i < N; ++i) {
+    (&c.fP[0][0][0][0])[i] = (float)(&c.P[0][0][0][0])[i];
+    (&c.fQ[0][0][0][0])[i] = (float)(&c.Q[0][0][0][0])[i];
+  }
+  return c;
+}
+// A coefficient as a complex number of the kernel's arithmetic type.
+template <typename R>
+__device__ __forceinline__ cpx<R> dco(const double (&d)[2], const float (&f)[2]) {
+  if constexpr (sizeof(R) == 4)
+    return mk<R>(f[0], f[1]);
+  else
+    return mk<R>((R)d[0], (R)d[1]);
+}
 
 // One two-flavour hopping application with the flavour epilogue (z = H in):
 //   mode 0: out = epi;  1: out = epi, sum ||out||^2;  2: out (= r, FP64 for FP64 storage, FP32

@@ -78,10 +78,10 @@ __global__ void __launch_bounds__(HOP_NT) dhop_kernel(const Geom g, const int ou
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
           const int ch = k < 6 ? 0 : 1;
-          o[f][k] = mk<R>((R)co.P[ch][f][0][0], (R)co.P[ch][f][0][1]) * y0[k] +
-                    mk<R>((R)co.P[ch][f][1][0], (R)co.P[ch][f][1][1]) * y1[k] +
-                    mk<R>((R)co.Q[ch][f][0][0], (R)co.Q[ch][f][0][1]) * acc[0][k] +
-                    mk<R>((R)co.Q[ch][f][1][0], (R)co.Q[ch][f][1][1]) * acc[1][k];
+          o[f][k] = dco<R>(co.P[ch][f][0], co.fP[ch][f][0]) * y0[k] +
+                    dco<R>(co.P[ch][f][1], co.fP[ch][f][1]) * y1[k] +
+                    dco<R>(co.Q[ch][f][0], co.fQ[ch][f][0]) * acc[0][k] +
+                    dco<R>(co.Q[ch][f][1], co.fQ[ch][f][1]) * acc[1][k];
         }
     } else {
 #pragma unroll
@@ -89,8 +89,8 @@ __global__ void __launch_bounds__(HOP_NT) dhop_kernel(const Geom g, const int ou
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
           const int ch = k < 6 ? 0 : 1;
-          o[f][k] = mk<R>((R)co.Q[ch][f][0][0], (R)co.Q[ch][f][0][1]) * acc[0][k] +
-                    mk<R>((R)co.Q[ch][f][1][0], (R)co.Q[ch][f][1][1]) * acc[1][k];
+          o[f][k] = dco<R>(co.Q[ch][f][0], co.fQ[ch][f][0]) * acc[0][k] +
+                    dco<R>(co.Q[ch][f][1], co.fQ[ch][f][1]) * acc[1][k];
         }
     }
     if (co.swap) {  // gamma5 tau1: swap the flavours, negate the lower spins
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(HOP_NT) dhop_kernel(const Geom g, const int ou
     }
   }
   if (MODE >= 1) {
-    const double bs = block_sum<HOP_NT>((double)nrm, sh);
+    const double bs = block_sum<HOP_NT>(nrm, sh);
     grid_reduce<HOP_NT>(red, 0, gridDim.x, blockIdx.x, bs, sh);
   }
 }
@@ -178,12 +178,12 @@ __global__ void __launch_bounds__(HOP_NT) dhop2_kernel(const Geom g, const int o
   for (int k = 0; k < 12; ++k) {
     const int ch = k < 6 ? 0 : 1;
     const cpx<R> ap = mk<R>(__shfl_xor_sync(0xffffffffu, acc[k].re, 1), __shfl_xor_sync(0xffffffffu, acc[k].im, 1));
-    cpx<R> v = mk<R>((R)co.Q[ch][row][f][0], (R)co.Q[ch][row][f][1]) * acc[k] +
-               mk<R>((R)co.Q[ch][row][1 - f][0], (R)co.Q[ch][row][1 - f][1]) * ap;
+    cpx<R> v = dco<R>(co.Q[ch][row][f], co.fQ[ch][row][f]) * acc[k] +
+               dco<R>(co.Q[ch][row][1 - f], co.fQ[ch][row][1 - f]) * ap;
     if (HAS_Y) {
       const cpx<R> yp = mk<R>(__shfl_xor_sync(0xffffffffu, yv[k].re, 1), __shfl_xor_sync(0xffffffffu, yv[k].im, 1));
-      v = v + mk<R>((R)co.P[ch][row][f][0], (R)co.P[ch][row][f][1]) * yv[k] +
-          mk<R>((R)co.P[ch][row][1 - f][0], (R)co.P[ch][row][1 - f][1]) * yp;
+      v = v + dco<R>(co.P[ch][row][f], co.fP[ch][row][f]) * yv[k] +
+          dco<R>(co.P[ch][row][1 - f], co.fP[ch][row][1 - f]) * yp;
     }
     acc[k] = (co.swap && k >= 6) ? mk<R>(-v.re, -v.im) : v;
   }
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(HOP_NT) dhop2_kernel(const Geom g, const int o
     }
   }
   if (MODE >= 1) {
-    const double bs = block_sum<HOP_NT>((double)nrm, sh);
+    const double bs = block_sum<HOP_NT>(nrm, sh);
     grid_reduce<HOP_NT>(red, 0, gridDim.x, blockIdx.x, bs, sh);
   }
 }
@@ -235,7 +235,8 @@ static tm_status dhop_launch_t(tm_lattice lat, const DHopArgs& a, cudaStream_t s
   char* out = static_cast<char*>(a.out);
   const bool two = dhop_threads_per_site() == 2;
   const unsigned grid = (unsigned)((g.h + (two ? HOP_NT / 2 : HOP_NT) - 1) / (two ? HOP_NT / 2 : HOP_NT));
-#define TM_DHOP_ARGS g, a.out_parity, links, in, a.stride, out, a.out_stride, y, a.co, a.alpha_src, a.red, a.skip
+  const DCoef co = dcoef_finish(a.co);
+#define TM_DHOP_ARGS g, a.out_parity, links, in, a.stride, out, a.out_stride, y, co, a.alpha_src, a.red, a.skip
 #define TM_DHOP_LAUNCH(HY, MM)                                                       \
   do {                                                                               \
     if (two)                                                                         \

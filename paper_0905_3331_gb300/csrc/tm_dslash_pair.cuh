@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(PAIR_NT, HOP_PAIR_BLOCKS)
     if (act_b) F::store_range(outr, g.h, cbb, ob, 0, 12, mb, true);
   }
   if (MODE >= 1) {
-    const double bs = block_sum<PAIR_NT>((double)nrm, sh);
+    const double bs = block_sum<PAIR_NT>(nrm, sh);
     grid_reduce<PAIR_NT>(red, rhs, gridDim.x, blockIdx.x, bs, sh);
   }
 }
