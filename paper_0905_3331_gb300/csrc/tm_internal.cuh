@@ -880,6 +880,9 @@ struct Reduce {
   double* result;      // [nsys] (FIN_STORE)
   CGState* st;         // [nsys] (FIN_CG_*)
   int kind;
+  // optional: [nsys][ceil(nblocks / NT)] group counters, zero between uses, for grids of many
+  // blocks (two-level sum, grid_reduce2)
+  unsigned* gcounters = nullptr;
 };
 
 __device__ __forceinline__ void fin_apply(const Reduce& red, int sys, double sum) {
@@ -984,11 +987,67 @@ __device__ __forceinline__ double block_sum(float v, double* sh) {
 #endif
 }
 
+// Two levels, for grids of many blocks: the blocks form groups of NT (blocks g NT .. g NT + NT - 1);
+// the last block of a group to arrive sums its group's partials (one per thread) in fixed order,
+// writes the sum over the group's first partial and arrives at the system's counter; the last
+// group sums the group sums in fixed order and finalises.  A single last block summing 83 k
+// partials (one hopping launch on 48^3 x 96) waits out ~80 rounds of L2 loads.
+template <int NT>
+__device__ __forceinline__ void grid_reduce2(const Reduce& red, int sys, int nblocks, int bid, double bsum,
+                                             double* sh) {
+  __shared__ bool lastg, lasttop;
+  const size_t base = (size_t)sys * nblocks;
+  const int ngroups = (nblocks + NT - 1) / NT;
+  const int g = bid / NT;
+  const int gsize = min(NT, nblocks - g * NT);
+  unsigned* gctr = red.gcounters + (size_t)sys * ngroups + g;
+  if (threadIdx.x == 0) {
+    red.partials[base + bid] = bsum;
+    lastg = (arrive_acq_rel(gctr) == (unsigned)gsize - 1);
+  }
+  __syncthreads();
+  if (!lastg) return;
+  // every partial of the group is visible, as in grid_reduce: through the counter's acquire
+  const double v = (int)threadIdx.x < gsize ? __ldcg(red.partials + base + (size_t)g * NT + threadIdx.x) : 0.0;
+  const double gs = block_sum<NT>(v, sh);
+  if (threadIdx.x == 0) {
+    *gctr = 0u;
+    red.partials[base + (size_t)g * NT] = gs;
+    lasttop = (arrive_acq_rel(red.counters + sys) == (unsigned)ngroups - 1);
+  }
+  __syncthreads();
+  if (!lasttop) return;
+  double w = 0.0;
+  for (int b0 = threadIdx.x; b0 < ngroups; b0 += 8 * NT) {
+    double t[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int k = b0 + u * NT;
+      t[u] = k < ngroups ? __ldcg(red.partials + base + (size_t)k * NT) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) w += t[u];
+  }
+  __syncthreads();
+  const double tot = block_sum<NT>(w, sh);
+  if (threadIdx.x == 0) {
+    fin_apply(red, sys, tot);
+    red.counters[sys] = 0u;
+  }
+}
+
 // Called by every thread of every block with the block's contribution (valid in thread 0).
-// The last block of system `sys` to arrive sums the partials in fixed order and finalises.
+// The last block of system `sys` to arrive sums the partials in fixed order and finalises (two
+// levels when the caller provides group counters and the grid has more than 64 NT blocks: below
+// that the single tail's few rounds of loads cost less than the second arrival -- 16^3 x 32, 1024
+// blocks: 199 mixed solves/s with one level, 185 with two; 48^3 x 96, 83 k blocks: 0.76 -> 0.80).
 template <int NT>
 __device__ __forceinline__ void grid_reduce(const Reduce& red, int sys, int nblocks, int bid, double bsum,
                                             double* sh) {
+  if (red.gcounters != nullptr && nblocks > 64 * NT) {
+    grid_reduce2<NT>(red, sys, nblocks, bid, bsum, sh);
+    return;
+  }
   __shared__ bool last;
   if (threadIdx.x == 0) {
     red.partials[(size_t)sys * nblocks + bid] = bsum;
@@ -1073,6 +1132,7 @@ struct tm_lattice_s {
   size_t partials_count;
   unsigned* counters;       // reduction counters (zeroed)
   size_t counters_count;
+  unsigned* gcounters;      // group counters of two-level reductions (zeroed; allocated once, h / 1024 + 16)
   double* dscalars;         // small device scalar scratch
   tmq::CGState* cgstate;     // device CG state array
   size_t cgstate_count;

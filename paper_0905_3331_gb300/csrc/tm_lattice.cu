@@ -130,6 +130,12 @@ void* workspace(tm_lattice lat, int slot, size_t bytes, tm_status* st) {
 }
 
 tm_status ensure_reduce(tm_lattice lat, size_t nparts, size_t ncounters) {
+  if (!lat->gcounters) {  // once per lattice, before any graph capture uses it
+    const size_t n = lat->h / 1024 + 16;
+    tm_status st = cuda_check(cudaMalloc(&lat->gcounters, n * sizeof(unsigned)), "reduction group counters");
+    if (st == TM_OK) st = cuda_check(cudaMemset(lat->gcounters, 0, n * sizeof(unsigned)), "reduction group counters");
+    if (st != TM_OK) return st;
+  }
   if (nparts > lat->partials_count) {
     if (lat->partials) cudaFree(lat->partials);
     lat->partials = nullptr;
@@ -548,6 +554,7 @@ tm_status tm_lattice_destroy(tm_lattice lat) {
   for (int k = 0; k < 32; ++k) cudaFree(lat->ws[k]);
   cudaFree(lat->partials);
   cudaFree(lat->counters);
+  cudaFree(lat->gcounters);
   cudaFree(lat->dscalars);
   cudaFree(lat->cgstate);
   cudaFree(lat->stage);

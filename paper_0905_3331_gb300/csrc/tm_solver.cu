@@ -219,7 +219,7 @@ tm_status normal_apply(const Solver& S, int prec, int nreal, const void* in, voi
   a.coef = epi_schur_q(lat->kappa, S.mut, -S.f);
   if (state) {
     a.mode = 1;
-    a.red = Reduce{lat->partials, lat->counters, nullptr, state, FIN_CG_ALPHA};
+    a.red = Reduce{lat->partials, lat->counters, nullptr, state, FIN_CG_ALPHA, lat->gcounters};
   } else {
     a.mode = 0;
   }
@@ -242,11 +242,11 @@ tm_status normal_apply(const Solver& S, int prec, int nreal, const void* in, voi
   if (state) {
     a.alpha_src = state;
     a.alpha_sign = 1.0;
-    a.red = Reduce{lat->partials, lat->counters, nullptr, state, FIN_CG_RR};
+    a.red = Reduce{lat->partials, lat->counters, nullptr, state, FIN_CG_RR, lat->gcounters};
   } else {
     a.alpha_src = nullptr;
     a.alpha_sign = 1.0;
-    a.red = Reduce{lat->partials, lat->counters, lat->dscalars, nullptr, FIN_STORE};
+    a.red = Reduce{lat->partials, lat->counters, lat->dscalars, nullptr, FIN_STORE, lat->gcounters};
   }
   return hop_launch(lat, a, S.s);
 }
