@@ -22,72 +22,16 @@
 #include <utility>
 #include <vector>
 
-#include "tm_dslash.cuh"
+#include "tm_batch.cuh"
 #include "tm_solver.cuh"
 
 namespace tmq {
 
-// Per-system descriptor (device memory).
-struct BatchSys {
-  Geom g;
-  const char* links;   // sloppy gauge copy of the system's lattice
-  EpiCoef coef[4];     // epilogues of K1..K4 (this system's mu)
-  void* vec[5];        // 0 p, 1 T, 2 W (sloppy storage), 3 r, 4 x increment (FP32)
-  CGState* st;
-  double* partials;    // reduction partials of this system (nblocks entries)
-  unsigned* counters;  // [0] reductions, [1] update kernel
-  int nblocks;         // blocks of the hopping launch this table serves (hop_spb(TPS) sites each)
-  int nblocks_upd;     // update-kernel blocks
-  double* result;      // the FP64 service's ||b' - A X||^2 (reductions of kind FIN_STORE)
-};
-
-struct BatchGlobal {
-  int unfinished;    // systems not yet done for good
-  int loops;         // iterations executed (bodies of the graph loop)
-  int loop_cap;      // hard bound on loops
-  unsigned counter;  // update-kernel blocks arrived
-  int nsys;          // systems in the batch
-  int services;      // executions of the FP64 service
-  double delta2;     // reliable-update trigger of a resumed system
-  double grow2;      // divergence guard of a resumed system
-};
-
-// A work list: the live systems of the batch, compacted lattice by lattice and rebuilt inside the
-// graph whenever the set of running systems changes.  Virtual block v of a launch belongs to the
-// lattice li with start[li] <= v < start[li + 1]; there it is block (v - start[li]) / count[li] of
-// system items[base[li] + (v - start[li]) % count[li]], so the systems of one lattice take turns
-// block by block, read each link at about the same time and share it through L2.  Launches hold
-// as many blocks as the GPU keeps resident and walk the list with a stride: the blocks of stopped
-// and finished systems cost nothing.
-struct Plan {
-  int nlat;
-  const int* base;    // [nlat] first candidate (and item slot) of lattice li
-  const int* ncand;   // [nlat] candidates on lattice li
-  const int* blocks;  // [nlat] blocks per system on lattice li (of the launch the list serves)
-  int* start;         // [nlat + 1] first virtual block of lattice li; start[nlat] = the total
-  int* count;         // [nlat] live systems on lattice li
-  int* items;         // the live systems, lattice li's from base[li]
-};
-
-// The four work lists of a batched solve: the running systems' hopping and update blocks, and the
-// FP64 service's for the systems that stopped.  The candidates are the positions in `order`.
-struct Plans {
-  Plan hop, upd, shop, supd;
-  const int* order;  // [nsys] system ids, lattice by lattice
-  CGState* states;   // [nsys] the systems' CG states
-};
-
-__device__ __forceinline__ int2 plan_item(const Plan& P, int v) {
-  int li = 0;
-  while (li + 1 < P.nlat && v >= P.start[li + 1]) ++li;
-  const int w = v - P.start[li];
-  const int c = P.count[li];
-  return make_int2(P.items[P.base[li] + w % c], w / c);
-}
-
 // Rebuilds a work list (one warp, all lanes): the candidates of a lattice are taken 32 at a time
 // and compacted with a ballot, one round of dependent loads per 32 candidates.
-__device__ void plan_build(const Plan& P, const int* order, const CGState* st, bool stopped) {
+// Candidates: the positions in `order` (systems; groups == nullptr), or the group ids.
+__device__ void plan_build(const Plan& P, const int* order, const CGState* st, bool stopped,
+                           const BatchGroup* groups = nullptr) {
   const unsigned lane = threadIdx.x & 31u;
   int v = 0;
   for (int li = 0; li < P.nlat; ++li) {
@@ -96,7 +40,11 @@ __device__ void plan_build(const Plan& P, const int* order, const CGState* st, b
     for (int c0 = 0; c0 < nc; c0 += 32) {
       const int c = c0 + (int)lane;
       int id = -1;
-      if (c < nc) {
+      if (c < nc && groups) {  // a group runs while one of its systems does
+        const BatchGroup G = groups[b0 + c];
+        for (int j = 0; j < G.n; ++j)
+          if (!st[G.sys[j]].done) id = b0 + c;
+      } else if (c < nc) {
         const int k = order[b0 + c];
         const CGState& q = st[k];
         if (stopped ? (q.done && !q.finished) : !q.done) id = k;
@@ -115,8 +63,13 @@ __device__ void plan_build(const Plan& P, const int* order, const CGState* st, b
 }
 
 // Work list w (0 hop, 1 upd: the running systems; 2 shop, 3 supd: the systems that stopped and are
-// not finished), rebuilt by one warp from the states as they stand.
+// not finished; 4 ghop: the running groups), rebuilt by one warp from the states as they stand.
+constexpr int NPLANS = 5;
 __device__ void plan_rebuild(const Plans& L, int w) {
+  if (w == 4) {
+    plan_build(L.ghop, L.order, L.states, false, L.groups);
+    return;
+  }
   const Plan& P = w == 0 ? L.hop : (w == 1 ? L.upd : (w == 2 ? L.shop : L.supd));
   plan_build(P, L.order, L.states, w >= 2);
 }
@@ -124,7 +77,7 @@ __device__ void plan_rebuild(const Plans& L, int w) {
 // All four (before the solve, and for the tuner); 4 warps.
 __global__ void plans_init_kernel(Plans L) {
   const int w = threadIdx.x >> 5;
-  if (w < 4) plan_rebuild(L, w);
+  if (w < NPLANS) plan_rebuild(L, w);
 }
 
 // The batched hopping kernel: the blocks of the listed systems, each computed by the hopping
@@ -209,7 +162,7 @@ __global__ void __launch_bounds__(BNT) cg_update_batch_kernel(const BatchSys* __
   __syncthreads();
   if (!last) return;
   // the last block: every block's work is visible; warps 0..3 rebuild the four work lists
-  if ((threadIdx.x >> 5) < 4) plan_rebuild(L, threadIdx.x >> 5);
+  if ((threadIdx.x >> 5) < NPLANS) plan_rebuild(L, threadIdx.x >> 5);
   __syncthreads();
   if (threadIdx.x == 0) {
     gl->counter = 0u;
@@ -305,7 +258,8 @@ __global__ void serv_decide_kernel(const BatchSys* __restrict__ sys, Plans L,
     S.diverged = 0;
   }
   __syncthreads();
-  if ((threadIdx.x >> 5) < 2) plan_rebuild(L, threadIdx.x >> 5);
+  const int w = threadIdx.x >> 5;  // the running systems' lists (hop, upd, ghop)
+  if (w < 2 || w == 4) plan_rebuild(L, w);
   if (threadIdx.x == 0) gl->services += 1;
 }
 
@@ -332,16 +286,6 @@ __global__ void __launch_bounds__(BNT) serv_convert_kernel(const BatchSys* __res
   }
 }
 
-// Blocks of a launch: as many as the GPU keeps resident (at most `cap`, the blocks of a full list).
-template <class Kern>
-static int resident_grid(Kern kern, int threads, int cap) {
-  int dev = 0, nsm = 0, per = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, 0);
-  return std::max(1, std::min(cap, std::max(1, per) * std::max(1, nsm)));
-}
-
 template <int PREC, int NREAL, int TPS>
 static tm_status launch_hop_batch(const BatchSys* d_sys, const CGState* d_st, const Plan& plan, int cap, int serv,
                                   int in_sel, int y_sel, int out_sel, int kk, int parity, int mode, bool has_y,
@@ -366,8 +310,8 @@ static tm_status launch_hop_batch(const BatchSys* d_sys, const CGState* d_st, co
   return cuda_check(cudaGetLastError(), "batched hopping kernel");
 }
 
-// The batched hopping launches of one storage form and TPS (FP64 with TPS 1 for the service of
-// stopped systems).
+// The batched hopping launches of one storage form: TPS threads per site (K = 1), or K = 2, 4
+// systems per thread over the groups (FP64 with TPS 1 for the service of stopped systems).
 struct BatchLaunch {
   int prec, nreal, tps;
   int serv;
@@ -375,10 +319,16 @@ struct BatchLaunch {
   const CGState* st;
   Plan plan;
   int cap;  // blocks of the full list
+  int K;                    // systems per thread
+  const BatchGroup* grp;    // the groups (K > 1)
+  Plan gplan;               // their work list
 };
 
 static tm_status hop_batch(const BatchLaunch& L, int in_sel, int y_sel, int out_sel, int kk, int parity, int mode,
                            bool has_y, cudaStream_t s) {
+  if (L.K > 1)
+    return launch_hop_group(L.prec, L.nreal, L.K, L.sys, L.grp, L.st, L.gplan, L.cap, in_sel, y_sel, out_sel, kk,
+                            parity, mode, has_y, s);
   if (L.prec == TM_F64)
     return launch_hop_batch<TM_F64, 18, 1>(L.sys, L.st, L.plan, L.cap, L.serv, in_sel, y_sel, out_sel, kk, parity, mode,
                                            has_y, s);
@@ -429,7 +379,7 @@ static tm_status batch_service(const BatchLaunch& D, const BatchSys* d_sys, int 
   if ((st = hop_batch(D, 1, 0, 2, 1, 1, 0, true, s)) != TM_OK) return st;
   if ((st = hop_batch(D, 2, 0, 1, 2, 0, 0, false, s)) != TM_OK) return st;
   if ((st = hop_batch(D, 1, 2, 3, 3, 1, 2, true, s)) != TM_OK) return st;
-  serv_decide_kernel<<<1, 128, 0, s>>>(d_sys, plans, d_gl);
+  serv_decide_kernel<<<1, 32 * NPLANS, 0, s>>>(d_sys, plans, d_gl);
   count_launch();
   if (sp == TM_F32) {
     auto kern = serv_convert_kernel<TM_F32>;
@@ -477,27 +427,31 @@ struct LatWork {
 
 // The batch by lattice, and the device arrays of its work lists.  Device ints, in this order:
 // order[nsys]; per lattice sys_base, sys_cnt, hop_blk (blocks per system of the sloppy hopping
-// launch), upd_blk (of the update), shop_blk (of the FP64 service's hopping launch); then for each
-// of the four lists start[nlat + 1], count[nlat], items[nsys].
+// launch), upd_blk (of the update), shop_blk (of the FP64 service's hopping launch), grp_base,
+// grp_cnt (the groups of K systems), ghop_blk (blocks per group); then for each of the five lists
+// start[nlat + 1], count[nlat], items[nsys].
 struct BatchLayout {
-  static constexpr int NPER = 5;
+  static constexpr int NPER = 8;
   int nlat = 0, nsys = 0;
   std::vector<int> host;  // the static part (order and the per-lattice arrays)
   int* dev = nullptr;
   CGState* states = nullptr;
-  static size_t ints(int nlat, int nsys) { return (size_t)nsys + NPER * nlat + 4 * ((size_t)2 * nlat + 1 + nsys); }
+  BatchGroup* groups = nullptr;  // device, nsys entries at most
+  static size_t ints(int nlat, int nsys) {
+    return (size_t)nsys + NPER * nlat + NPLANS * ((size_t)2 * nlat + 1 + nsys);
+  }
   int* at(int q) const { return dev + nsys + q * nlat; }        // q-th per-lattice array (device)
   int& hat(int q, int li) { return host[nsys + q * nlat + li]; }  // ... and its host copy
   Plans plans() const {
     Plans L;
     int* dyn = dev + nsys + NPER * nlat;
-    Plan* all[4] = {&L.hop, &L.upd, &L.shop, &L.supd};
-    const int blocks[4] = {2, 3, 4, 3};
-    for (int q = 0; q < 4; ++q) {
+    Plan* all[NPLANS] = {&L.hop, &L.upd, &L.shop, &L.supd, &L.ghop};
+    const int blocks[NPLANS] = {2, 3, 4, 3, 7};
+    for (int q = 0; q < NPLANS; ++q) {
       Plan& P = *all[q];
       P.nlat = nlat;
-      P.base = at(0);
-      P.ncand = at(1);
+      P.base = at(q == 4 ? 5 : 0);   // the groups' lists: grp_base, grp_cnt
+      P.ncand = at(q == 4 ? 6 : 1);
       P.blocks = at(blocks[q]);
       P.start = dyn;
       P.count = dyn + nlat + 1;
@@ -506,72 +460,109 @@ struct BatchLayout {
     }
     L.order = dev;
     L.states = states;
+    L.groups = groups;
     return L;
   }
   tm_status upload(cudaStream_t s) const {
     tm_status st = cuda_check(cudaMemcpyAsync(dev, host.data(), sizeof(int) * host.size(), cudaMemcpyHostToDevice, s),
                               "work lists");
     if (st != TM_OK) return st;
-    plans_init_kernel<<<1, 128, 0, s>>>(plans());
+    plans_init_kernel<<<1, 32 * NPLANS, 0, s>>>(plans());
     count_launch();
     return cuda_check(cudaGetLastError(), "work lists");
   }
 };
 
-// The sloppy hopping launch's threads per site (1, 2 or 4; hop_spb(TPS) sites per block) for a
-// batch: sets the blocks per system in the layout and the system table, and uploads both.
-tm_status set_batch_tps(int tps, const std::vector<SysWork>& W, const std::vector<LatWork>& lats, BatchLayout& Y,
-                        std::vector<BatchSys>& hsys, BatchSys* d_sys, BatchLaunch& L, cudaStream_t s) {
-  const int spb = hop_batch_spb(tps);
-  for (int li = 0; li < Y.nlat; ++li) Y.hat(2, li) = (int)((lats[li].lat->h + spb - 1) / spb);
+// The batch split of the sloppy hopping launch: K = 1 with TPS threads per site (1, 2 or 4;
+// hop_batch_spb(TPS) sites per block), or K = 2, 4 systems per thread (HOP_NT sites per block) over
+// groups of K systems of one lattice.  Sets the blocks per system (and group) in the layout and
+// the system table, builds the groups, and uploads them.
+tm_status set_batch_split(int K, int tps, const std::vector<SysWork>& W, const std::vector<LatWork>& lats,
+                          BatchLayout& Y, std::vector<BatchSys>& hsys, BatchSys* d_sys, BatchLaunch& L,
+                          cudaStream_t s) {
+  const int spb = K > 1 ? HOP_NT : hop_batch_spb(tps);
+  std::vector<BatchGroup> grp;
+  for (int li = 0; li < Y.nlat; ++li) {
+    const int nbl = (int)((lats[li].lat->h + spb - 1) / spb);
+    Y.hat(2, li) = nbl;
+    Y.hat(7, li) = nbl;
+    Y.hat(5, li) = (int)grp.size();
+    const int first = Y.hat(0, li), n = Y.hat(1, li);
+    for (int a = 0; a < n; a += K) {  // the lattice's systems in order, K to a group
+      BatchGroup G{};
+      G.n = std::min(K, n - a);
+      for (int j = 0; j < G.n; ++j) G.sys[j] = Y.host[first + a + j];
+      grp.push_back(G);
+    }
+    Y.hat(6, li) = (int)grp.size() - Y.hat(5, li);
+  }
   for (size_t k = 0; k < W.size(); ++k) hsys[k].nblocks = (int)((W[k].lat->h + spb - 1) / spb);
-  L.tps = tps;
+  L.tps = K > 1 ? 1 : tps;
+  L.K = K;
   tm_status st = cuda_check(
       cudaMemcpyAsync(d_sys, hsys.data(), sizeof(BatchSys) * hsys.size(), cudaMemcpyHostToDevice, s), "table");
+  if (st == TM_OK)
+    st = cuda_check(cudaMemcpyAsync(Y.groups, grp.data(), sizeof(BatchGroup) * grp.size(), cudaMemcpyHostToDevice, s),
+                    "groups");
   return st == TM_OK ? Y.upload(s) : st;
 }
 
-// Threads per site of the batched hopping kernel.  TM_BATCH_TPS=1|2|4 fixes it.  Otherwise 1, 2
-// and 4 are timed on this batch's own vectors (a plain application of the hopping operator to
-// every system, CUDA events, the fastest of three interleaved rounds of two launches each) and
-// the fastest kept -- more threads per site must win by 3% -- and remembered for later batches of
-// the same signature (storage form, each lattice's extents and number of systems).
-int env_batch_tps() {
-  const char* e = getenv("TM_BATCH_TPS");
+// The batch split of the batched hopping kernel.  TM_BATCH_TPS=1|2|4 fixes one system per thread
+// with that many threads per site, TM_BATCH_K=2|4 that many systems per thread.  Otherwise the
+// candidates -- (K = 1; 1, 2, 4 threads per site), K = 2, K = 4 (up to the most systems on one
+// lattice) -- are timed on this batch's own vectors (a plain application of the hopping operator
+// to every system, CUDA events, the fastest of three interleaved rounds of two launches each) and
+// the fastest kept (another candidate must win by 3% over one thread per site and K = 1), and
+// remembered for later batches of the same signature (storage form, each lattice's extents and
+// number of systems).
+int env_batch(const char* name, bool allow2, bool allow4) {
+  const char* e = getenv(name);
   if (!e) return 0;
   const int v = atoi(e);
-  return (v == 1 || v == 2 || v == 4) ? v : 0;
+  return (v == 1 || (v == 2 && allow2) || (v == 4 && allow4)) ? v : 0;
 }
 
-tm_status choose_batch_tps(const std::vector<SysWork>& W, const std::vector<LatWork>& lats, int sp, int sl,
-                           BatchLayout& Y, std::vector<BatchSys>& hsys, BatchSys* d_sys, BatchLaunch& L,
-                           cudaStream_t s) {
+tm_status choose_batch_split(const std::vector<SysWork>& W, const std::vector<LatWork>& lats, int sp, int sl,
+                             BatchLayout& Y, std::vector<BatchSys>& hsys, BatchSys* d_sys, BatchLaunch& L,
+                             cudaStream_t s) {
   static std::mutex mu;
-  static std::vector<std::pair<std::vector<long long>, int>> cache;
+  static std::vector<std::pair<std::vector<long long>, std::pair<int, int>>> cache;
   std::vector<long long> sig = {sp, sl};
+  int most = 1;
   for (size_t li = 0; li < lats.size(); ++li) {
     int n = 0;
     for (auto& w : W) n += (w.lat_index == (int)li);
+    most = std::max(most, n);
     sig.push_back(lats[li].lat->T);
     sig.push_back(lats[li].lat->L);
     sig.push_back(n);
   }
-  int tps = env_batch_tps();
-  if (tps == 0) {
+  int K = 0, tps = 0;
+  if (const int ek = env_batch("TM_BATCH_K", true, true)) {
+    K = ek;
+    tps = 1;
+  } else if (const int et = env_batch("TM_BATCH_TPS", true, true)) {
+    K = 1;
+    tps = et;
+  } else {
     std::lock_guard<std::mutex> lock(mu);
     for (auto& c : cache)
-      if (c.first == sig) tps = c.second;
+      if (c.first == sig) {
+        K = c.second.first;
+        tps = c.second.second;
+      }
   }
   tm_status st = TM_OK;
-  if (tps == 0) {
-    const int cands[3] = {1, 2, 4};
-    float score[3] = {1e30f, 1e30f, 1e30f};
+  if (K == 0) {
+    const int candK[5] = {1, 1, 1, 2, 4}, candT[5] = {1, 2, 4, 1, 1};
+    float score[5] = {1e30f, 1e30f, 1e30f, 1e30f, 1e30f};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     st = cuda_check(cudaEventCreate(&e0), "event");
     if (st == TM_OK) st = cuda_check(cudaEventCreate(&e1), "event");
     for (int round = 0; round < 4 && st == TM_OK; ++round)
-      for (int c = 0; c < 3 && st == TM_OK; ++c) {
-        if ((st = set_batch_tps(cands[c], W, lats, Y, hsys, d_sys, L, s)) != TM_OK) break;
+      for (int c = 0; c < 5 && st == TM_OK; ++c) {
+        if (candK[c] > most) continue;
+        if ((st = set_batch_split(candK[c], candT[c], W, lats, Y, hsys, d_sys, L, s)) != TM_OK) break;
         if ((st = cuda_check(cudaEventRecord(e0, s), "event")) != TM_OK) break;
         for (int q = 0; q < 2 && st == TM_OK; ++q) st = hop_batch(L, 0, 0, 1, 0, q & 1, 0, false, s);
         if (st == TM_OK) st = cuda_check(cudaEventRecord(e1, s), "event");
@@ -584,13 +575,20 @@ tm_status choose_batch_tps(const std::vector<SysWork>& W, const std::vector<LatW
     if (e1) cudaEventDestroy(e1);
     if (st != TM_OK) return st;
     int bi = 0;
-    for (int c = 1; c < 3; ++c)
-      if (score[c] < 0.97f * score[bi]) bi = c;
-    tps = cands[bi];
+    for (int c = 1; c < 5; ++c)
+      if (score[c] < 0.97f * score[0] && score[c] < score[bi]) bi = c;
+    K = candK[bi];
+    tps = candT[bi];
+    if (batch_verbose())
+      fprintf(stderr,
+              "[tm_solve_cg_batch] split tuner (ms for two launches): K1/TPS1 %.3f, K1/TPS2 %.3f, K1/TPS4 %.3f, "
+              "K2 %.3f, K4 %.3f -> K%d TPS%d\n",
+              score[0], score[1], score[2], score[3] < 1e29f ? score[3] : 0.f, score[4] < 1e29f ? score[4] : 0.f,
+              K, tps);
     std::lock_guard<std::mutex> lock(mu);
-    cache.emplace_back(sig, tps);
+    cache.emplace_back(sig, std::make_pair(K, tps));
   }
-  return set_batch_tps(tps, W, lats, Y, hsys, d_sys, L, s);
+  return set_batch_split(K, tps, W, lats, Y, hsys, d_sys, L, s);
 }
 
 }  // namespace
@@ -682,6 +680,7 @@ extern "C" tm_status tm_solve_cg_batch(const tm_system* systems, int nsys, const
   const size_t off_sys = add(sizeof(BatchSys) * nsys);
   const size_t off_sys64 = add(sizeof(BatchSys) * nsys);
   const size_t off_ints = add(sizeof(int) * BatchLayout::ints((int)lats.size(), nsys));
+  const size_t off_grp = add(sizeof(BatchGroup) * nsys);
   const size_t off_state = add(sizeof(CGState) * nsys);
   const size_t off_gl = add(sizeof(BatchGlobal));
   const size_t off_part = add(sizeof(double) * npart);
@@ -728,6 +727,7 @@ extern "C" tm_status tm_solve_cg_batch(const tm_system* systems, int nsys, const
   Y.nsys = nsys;
   Y.dev = reinterpret_cast<int*>(base + off_ints);
   Y.states = reinterpret_cast<CGState*>(base + off_state);
+  Y.groups = reinterpret_cast<BatchGroup*>(base + off_grp);
   Y.host.assign((size_t)nsys + BatchLayout::NPER * Y.nlat, 0);
   for (int li = 0, c = 0; li < Y.nlat; ++li) {  // order, sys_base, sys_cnt, hop_blk, upd_blk, shop_blk
     Y.hat(0, li) = c;
@@ -739,8 +739,8 @@ extern "C" tm_status tm_solve_cg_batch(const tm_system* systems, int nsys, const
     Y.hat(4, li) = (int)((lats[li].lat->h + hop_batch_spb(1) - 1) / hop_batch_spb(1));
   }
   const Plans plans = Y.plans();
-  BatchLaunch GL{sp, sl, 1, 0, d_sys, plans.states, plans.hop, npart};
-  BatchLaunch GD{TM_F64, 18, 1, 1, d_sys64, plans.states, plans.shop, npart};
+  BatchLaunch GL{sp, sl, 1, 0, d_sys, plans.states, plans.hop, npart, 1, Y.groups, plans.ghop};
+  BatchLaunch GD{TM_F64, 18, 1, 1, d_sys64, plans.states, plans.shop, npart, 1, nullptr, plans.ghop};
   CGState* d_st = reinterpret_cast<CGState*>(base + off_state);
   BatchGlobal* d_gl = reinterpret_cast<BatchGlobal*>(base + off_gl);
   double* d_part = reinterpret_cast<double*>(base + off_part);
@@ -824,7 +824,7 @@ extern "C" tm_status tm_solve_cg_batch(const tm_system* systems, int nsys, const
       for (int k = 0; k < nsys && st == TM_OK; ++k) hst[k] = fresh_state(W[k].rr, W[k].stop2, P.max_iter, 0, 0.0, 0.0);
       if (st == TM_OK)
         st = cuda_check(cudaMemcpyAsync(d_st, hst.data(), sizeof(CGState) * nsys, cudaMemcpyHostToDevice, s), "state");
-      if (st == TM_OK) st = choose_batch_tps(W, lats, sp, sl, Y, hsys, d_sys, GL, s);
+      if (st == TM_OK) st = choose_batch_split(W, lats, sp, sl, Y, hsys, d_sys, GL, s);
       if (st == TM_OK) st = cuda_check(cudaStreamSynchronize(s), "tables");
     }
     if (st != TM_OK) break;
@@ -846,7 +846,7 @@ extern "C" tm_status tm_solve_cg_batch(const tm_system* systems, int nsys, const
     st = cuda_check(cudaMemcpyAsync(d_st, hst.data(), sizeof(CGState) * nsys, cudaMemcpyHostToDevice, s), "state");
     if (st == TM_OK) st = cuda_check(cudaMemcpyAsync(d_gl, &hgl, sizeof(hgl), cudaMemcpyHostToDevice, s), "state");
     if (st == TM_OK) {
-      plans_init_kernel<<<1, 128, 0, s>>>(plans);
+      plans_init_kernel<<<1, 32 * NPLANS, 0, s>>>(plans);
       count_launch();
       st = cuda_check(cudaGetLastError(), "work lists");
     }

@@ -152,8 +152,10 @@ print("ITERS", [i.iters for i in infos])
 """
 
 
-def test_batch_host_loop_matches_graph_loop(tmp_path):
-    """TM_NO_GRAPH=1 runs the batched loop (iteration, FP64 service) from the host: bitwise the same solutions."""
+@pytest.mark.parametrize("split", [("TM_BATCH_TPS", "1"), ("TM_BATCH_K", "2")])
+def test_batch_host_loop_matches_graph_loop(tmp_path, split):
+    """TM_NO_GRAPH=1 runs the batched loop (iteration, FP64 service) from the host: bitwise the same
+    solutions, for a fixed batch split (the tuner's choice depends on timing)."""
     import os
     import subprocess
     import sys
@@ -162,7 +164,61 @@ def test_batch_host_loop_matches_graph_loop(tmp_path):
     for k, e in enumerate(({}, {"TM_NO_GRAPH": "1"})):
         out = str(tmp_path / f"x{k}.npy")
         r = subprocess.run([sys.executable, "-c", _BATCH_CHILD.format(out=out)], cwd=root,
-                           env={**os.environ, **e}, capture_output=True, text=True, timeout=300)
+                           env={**os.environ, **e, split[0]: split[1]}, capture_output=True, text=True, timeout=300)
         assert r.returncode == 0, r.stderr
         outs.append((np.load(out), r.stdout))
     assert np.array_equal(outs[0][0], outs[1][0]) and outs[0][1] == outs[1][1]
+
+
+_SPLIT_CHILD = """
+import sys, numpy as np, torch
+from paper_0905_3331_gb300 import Lattice, inputs, solve_cg_batch, F16, F32, LINK8, LINK12
+specs = [(4, 4, 0.3, 0.160, 11), (6, 4, 0.5, 0.1632, 12)]
+lats = []
+for T, L, eps, kappa, seed in specs:
+    lat = Lattice(T, L, kappa, 0.01)
+    lat.set_gauge(inputs.random_gauge(T, L, eps, seed))
+    lats.append(lat)
+systems = []
+for li, (T, L, eps, kappa, seed) in enumerate(specs):
+    for k, mu in enumerate((0.002, 0.005, 0.01, 0.02, 0.05)):  # 5 systems a lattice: a ragged last group
+        b = torch.from_numpy(inputs.gaussian_spinor(T, L, 200 + 10 * li + k)).cuda()
+        systems.append((lats[li], mu, torch.zeros_like(b), b, 1 if k % 2 == 0 else -1))
+for prec, link in ((F32, LINK12), (F16, LINK8)):
+    for s in systems:
+        s[2].zero_()
+    infos = solve_cg_batch(systems, sloppy_prec=prec, sloppy_link=link, delta=0.1)
+    np.savez({out!r}.replace(".npy", "_%d_%d.npz" % (prec, link)), *[s[2].cpu().numpy() for s in systems])
+    print("ITERS", prec, link, [i.iters for i in infos])
+"""
+
+
+@pytest.mark.parametrize("split", [("TM_BATCH_K", "2"), ("TM_BATCH_K", "4"), ("TM_BATCH_TPS", "2"),
+                                   ("TM_BATCH_TPS", "4")])
+def test_every_batch_split_solves_to_the_oracle(tmp_path, split):
+    """Each batch split the tuner can pick -- K = 2 or 4 systems per thread (groups of one lattice,
+    a ragged last group), or one system per thread with 2 or 4 threads per site -- forced through
+    the environment, on two lattices with five systems each (both flavours), FP32/12 and FP16/8:
+    every solution meets the oracle's residual bar."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = str(tmp_path / "x.npy")
+    r = subprocess.run([sys.executable, "-c", _SPLIT_CHILD.format(out=out)], cwd=root,
+                       env={**os.environ, split[0]: split[1], "TM_VERBOSE": "1"}, capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stderr[-4000:]
+    specs = [(4, 4, 0.3, 0.160, 11), (6, 4, 0.5, 0.1632, 12)]
+    for prec, link in ((F32, LINK12), (F16, 8)):
+        z = np.load(out.replace(".npy", "_%d_%d.npz" % (prec, link)))
+        xs = [z["arr_%d" % i] for i in range(len(z.files))]
+        n = 0
+        for li, (T, L, eps, kappa, seed) in enumerate(specs):
+            U = inputs.random_gauge(T, L, eps, seed)
+            for k, mu in enumerate((0.002, 0.005, 0.01, 0.02, 0.05)):
+                phi = inputs.gaussian_spinor(T, L, 200 + 10 * li + k)
+                f = 1 if k % 2 == 0 else -1
+                res = oracle_rel_residual(T, L, U, phi, xs[n], kappa, mu, f)
+                assert res < 1e-10, (split, prec, link, li, mu, res)
+                n += 1
