@@ -273,8 +273,11 @@ typedef struct {
  * ||b' - A X|| / ||b'|| is below tol; the full-system FP64 residual is then computed once per
  * system after the loop (true_rel_residual).  Every system keeps its own CG scalars and stops
  * on its own residual; infos[k] (may be NULL) receives system k's result (seconds = the whole
- * call).  Systems may share lattices and differ in mu, flavour and source.  Synchronises
- * `stream`.  Allocates its work space (about 1.9 kB per odd site per system with FP32
+ * call).  Systems may share lattices and differ in mu, flavour and source.  The hopping
+ * launches' split -- one system per thread with 1, 2 or 4 threads per site, or 2 or 4 systems
+ * of one lattice per thread sharing each link -- is timed on the batch's own vectors at the
+ * first call of a batch shape and cached (TM_BATCH_TPS=1|2|4 or TM_BATCH_K=2|4 in the
+ * environment fixes it).  Synchronises `stream`.  Allocates its work space (about 1.9 kB per odd site per system with FP32
  * storage, plus 0.8 kB per odd site per lattice) for the duration of the call.
  * Errors: TM_ERR_NOT_CONVERGED (some systems; their x holds the last iterate), TM_ERR_ARG,
  * TM_ERR_UNSUPPORTED, TM_ERR_NO_GAUGE, TM_ERR_NONFINITE, TM_ERR_CUDA, TM_ERR_OOM. */
