@@ -5,10 +5,12 @@ FP64) and the hopping kernel's bandwidth against the measured HBM roofline.
 Headline workload (default): the 48^3 x 96 lattice, random SU(3) links exp(i eps H) with
 eps = 0.6, kappa = 0.1615, mu = 0.0015 (mu~ = 2 kappa mu), Gaussian source -- the largest of
 the single-GPU workloads.  One step = one complete solve of M x = b through the C ABI: packing,
-source preparation, CG on Qhat+ Qhat- with the sloppy operator in FP16 storage with 12-real
-links and FP32 arithmetic, reliable updates (FP32 recomputations between FP64 ones),
+source preparation, CG on Qhat+ Qhat- with the sloppy operator in FP16 storage with 8-real
+links (the workload's named form) and FP32 arithmetic, reliable updates (FP32 recomputations
+between FP64 ones),
 reconstruction and the FP64 true-residual check.  The L2 cache is flushed (a 512 MB write)
-before every step.  Beside the headline the line carries the 16^3 x 32 throughput baseline
+before every step.  Beside the headline the line carries the same solve with 12-real links
+(`link_form_12`, the faster form on GB300), the 16^3 x 32 throughput baseline
 (FP64 and FP32 hopping kernels, FP64 CG), the 32^3 x 64 precision form, the batched workload
 and the other solvers as extra objects.
 
@@ -38,16 +40,17 @@ REF_TOTAL_SECONDS = 90.0  # host time of the reference arm's timed steps togethe
 # Solver settings of the mixed solve per workload: sloppy storage:links, reliable-update delta and
 # the arithmetic of the residual recomputations between FP64 ones.  FP16 storage keeps the
 # iterated residual trustworthy over a factor ~0.3 only; FP32 storage over ~1e-5 on 16^3 x 32
-# (88 iterations) and ~1e-3 on the longer solves.  On 48^3 x 96 FP16 with 12-real links is the
-# fastest form: its hopping kernel is bound by the FP32 pipe like the 8-real one's, with fewer
-# operations per site (no 8-real reconstruction), so its extra 64 bytes a site cost nothing
-# (1.39 s per solve, 528 iterations, at delta 0.2 against 1.45 s for FP16/8).
-SOLVER_DEFAULTS = {"48^3x96": ("f16:12", 0.2, "f32"), "32^3x64": ("f32:12", 1e-3, "f64"),
+# (88 iterations) and ~1e-3 on the longer solves.  48^3 x 96 is named with 8-real links; the
+# 12-real form is measured beside it (LINK_FORM_12): both kernels are bound by the FP32 pipe and
+# the 12-real one does fewer operations per site (no 8-real reconstruction), so its 64 more bytes
+# a site cost nothing.
+SOLVER_DEFAULTS = {"48^3x96": ("f16:8", 0.3, "f32"), "32^3x64": ("f32:12", 1e-3, "f64"),
                    "24^3x48": ("f32:12", 1e-3, "f64"), "16^3x32": ("f32:12", 1e-5, "f64")}
 # Iterations of the FP64 CG to 1e-10 on each workload's first Gaussian source, measured on GB300
 # by this library's FP64 CG (the same count the oracle's CG reaches up to rounding): the reference
 # arm extrapolates its bounded sample to them where one complete oracle solve would take longer
 # than the run may (48^3 x 96: about 50 minutes on 16 Grace cores).
+LINK_FORM_12_DELTA = 0.2  # FP16/12 on 48^3 x 96: delta 0.2 0.719, 0.3 0.717, 0.5 0.702 solves/s
 FP64_CG_ITERS = {"48^3x96": 522, "32^3x64": 437, "16^3x32": 88}
 HOP_VARIANT = {1: "1 thread per site", 2: "2 threads per site", 4: "4 threads per site",
                3: "1 thread per site, pipelined loads"}
@@ -369,6 +372,30 @@ def run_gpu(args):
                            if back_to_back else "") +
                           f"cold: {args.hop_iters} launches, per-launch CUDA events, mean of the middle 80%, before "
                           "each launch L2 flushed (512 MB write) and cleaned (256 MB read)"}
+    # ---- the same solve with 12-real links (where the headline form has 8), timed the same way
+    link12 = None
+    if sl == 8 and not args.no_link_form:
+        kw12 = dict(mixed_kw, sloppy_link=12, delta=LINK_FORM_12_DELTA)
+        timed_solves(1, kw12)
+        n12 = max(1, min(args.steps, 3))
+        t12, inf12 = timed_solves(n12, kw12)
+        t12 = max_over_ranks(t12)
+        t12_hop = hop_launch_time(lat, dev, sp, 12, half, args.hop_iters, flush, clean, cold=False)
+        b12 = hop_bytes_per_site(sp, 12) * h
+        tr12, tr12_file = ncu_traffic(f"f{16 if sp == 2 else 32}:12", w.name, lat.hop_threads(sp, 12), sp)
+        link12 = {"sloppy": f"{'f16' if sp == 2 else 'f32'}:12", "delta": LINK_FORM_12_DELTA,
+                  "solves_per_s": round(n12 * world / t12, 5), "s_per_solve": round(t12 / n12, 4),
+                  "iters": inf12[-1].iters, "reliable_updates": inf12[-1].reliable_updates,
+                  "true_rel_residual": max(i.true_rel_residual for i in inf12),
+                  "speedup_vs_fp64": round((n12 * world / t12) / (n64 * world / t64), 3),
+                  "roofline": {"bound": "hbm", "kernel": f"hop_kernel ({'f16' if sp == 2 else 'f32'}:12, "
+                               f"{HOP_VARIANT.get(lat.hop_threads(sp, 12), '?')}) on {w.name}",
+                               "achieved": round(b12 / t12_hop / 1e9, 1), "peak": peak, "unit": "GB/s",
+                               "frac": round(b12 / t12_hop / 1e9 / peak, 4), "traffic": tr12,
+                               "traffic_source": tr12_file, "bytes_per_launch": b12,
+                               "us_per_launch": round(t12_hop * 1e6, 3),
+                               "timing": f"{args.hop_iters} launches back to back, CUDA events around them"},
+                  "timing": f"{n12} solves after one warm-up, CUDA events, L2 flushed before each"}
     del half, clean
 
     n_units = args.steps * world
@@ -397,6 +424,8 @@ def run_gpu(args):
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
+    if link12 is not None:
+        result["link_form_12"] = link12
     lat.close()
     del b, x
     torch.cuda.empty_cache()
@@ -869,6 +898,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-solve measurement")
+    ap.add_argument("--no-link-form", action="store_true",
+                    help="skip the 12-real-link solve beside an 8-real headline")
     ap.add_argument("--no-precision-form", action="store_true",
                     help="skip the 32^3x64 roofline and mixed-vs-FP64 solve measurement")
     ap.add_argument("--no-extras", action="store_true",
