@@ -59,17 +59,19 @@ constexpr int CHUNK_BI = 8;  // iterations per host check without graphs
 // ------------------------------------------------------- multi-value sums ---
 // Every block adds its N values; the last block to arrive sums the per-block partials in
 // fixed order and returns true in thread 0 with the totals in tot[].
-template <int N>
-__device__ __forceinline__ bool grid_sum(double (&v)[N], double* partials, unsigned* counter, double (&tot)[N]) {
+// T: the per-thread sums' type (FP32 for FP32 data: the warp's shuffle tree in FP32, then FP64 --
+// GB300 runs FP64 adds and conversions at ~1/64 of the FP32 rate).
+template <int N, typename T>
+__device__ __forceinline__ bool grid_sum(T (&v)[N], double* partials, unsigned* counter, double (&tot)[N]) {
   __shared__ double sh[N][BNT / 32];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < N; ++k) {
-    double x = v[k];
+    T x = v[k];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
-    if (lane == 0) sh[k][warp] = x;
+    if (lane == 0) sh[k][warp] = (double)x;
   }
   __syncthreads();
   const int nb = gridDim.x;
@@ -125,7 +127,7 @@ __global__ void __launch_bounds__(BNT) bi_alpha_kernel(int h, const char* rh, co
   typedef typename SpinorFmt<PR>::real RR;
   typedef typename SpinorFmt<PP>::real RP;
   typedef typename SiteSum<RR>::type SR;
-  double acc[2] = {0.0, 0.0};
+  SR acc[2] = {};  // FP32 for FP32 data (the warp tree too), FP64 from the warps on
   for (int i = blockIdx.x * BNT + threadIdx.x; i < h; i += gridDim.x * BNT) {
     cpx<RR> a[12];
     cpx<RP> b[12];
@@ -138,8 +140,8 @@ __global__ void __launch_bounds__(BNT) bi_alpha_kernel(int h, const char* rh, co
       l0 += ar * br + ai * bi;
       l1 += ar * bi - ai * br;
     }
-    acc[0] += (double)l0;
-    acc[1] += (double)l1;
+    acc[0] += l0;
+    acc[1] += l1;
   }
   double tot[2];
   if (!grid_sum<2>(acc, partials, counter, tot)) return;
@@ -182,7 +184,7 @@ __global__ void __launch_bounds__(BNT) bi_omega_kernel(int h, const char* s, con
   if (st->done) return;
   typedef typename SpinorFmt<PP>::real RP;
   typedef typename SiteSum<RP>::type SR;
-  double acc[3] = {0.0, 0.0, 0.0};
+  SR acc[3] = {};  // FP32 for FP32 data (the warp tree too), FP64 from the warps on
   for (int i = blockIdx.x * BNT + threadIdx.x; i < h; i += gridDim.x * BNT) {
     cpx<RP> a[12], b[12];
     SpinorFmt<PP>::load(t, h, i, a);
@@ -196,7 +198,7 @@ __global__ void __launch_bounds__(BNT) bi_omega_kernel(int h, const char* s, con
       l[2] += tr * tr + ti * ti;
     }
 #pragma unroll
-    for (int j = 0; j < 3; ++j) acc[j] += (double)l[j];
+    for (int j = 0; j < 3; ++j) acc[j] += l[j];
   }
   double tot[3];
   if (!grid_sum<3>(acc, partials, counter, tot)) return;
@@ -223,7 +225,7 @@ __global__ void __launch_bounds__(BNT) bi_xr_kernel(int h, char* x, char* r, con
   const cpx<RR> al = mk<RR>((RR)st->alpha_re, (RR)st->alpha_im);
   const cpx<RR> om = mk<RR>((RR)st->omega_re, (RR)st->omega_im);
   typedef typename SiteSum<RR>::type SR;
-  double acc[3] = {0.0, 0.0, 0.0};
+  SR acc[3] = {};  // FP32 for FP32 data (the warp tree too), FP64 from the warps on
   for (int i = blockIdx.x * BNT + threadIdx.x; i < h; i += gridDim.x * BNT) {
     SR l[3] = {SR(0), SR(0), SR(0)};
     cpx<RR> xv[12], rv[12], hv[12];
@@ -246,7 +248,7 @@ __global__ void __launch_bounds__(BNT) bi_xr_kernel(int h, char* x, char* r, con
       l[2] += rr_ * rr_ + ri * ri;
     }
 #pragma unroll
-    for (int j = 0; j < 3; ++j) acc[j] += (double)l[j];
+    for (int j = 0; j < 3; ++j) acc[j] += l[j];
     SpinorFmt<PR>::store(x, h, i, xv);
     SpinorFmt<PR>::store(r, h, i, rv);
   }
@@ -345,7 +347,7 @@ __global__ void __launch_bounds__(BNT) bi_rho_kernel(int h, const char* rh, cons
                                                      double* partials, unsigned* counter) {
   typedef typename SpinorFmt<PR>::real RR;
   typedef typename SiteSum<RR>::type SR;
-  double acc[3] = {0.0, 0.0, 0.0};
+  SR acc[3] = {};  // FP32 for FP32 data (the warp tree too), FP64 from the warps on
   for (int i = blockIdx.x * BNT + threadIdx.x; i < h; i += gridDim.x * BNT) {
     cpx<RR> a[12], b[12];
     SpinorFmt<PR>::load(rh, h, i, a);
@@ -359,7 +361,7 @@ __global__ void __launch_bounds__(BNT) bi_rho_kernel(int h, const char* rh, cons
       l[2] += br * br + bi * bi;
     }
 #pragma unroll
-    for (int j = 0; j < 3; ++j) acc[j] += (double)l[j];
+    for (int j = 0; j < 3; ++j) acc[j] += l[j];
   }
   double tot[3];
   if (!grid_sum<3>(acc, partials, counter, tot)) return;
@@ -390,7 +392,7 @@ __global__ void __launch_bounds__(BNT) mr_alpha_kernel(int h, const char* q, con
   if (st->done) return;
   typedef typename SpinorFmt<P>::real R;
   typedef typename SiteSum<R>::type SR;
-  double acc[3] = {0.0, 0.0, 0.0};
+  SR acc[3] = {};  // FP32 for FP32 data (the warp tree too), FP64 from the warps on
   for (int i = blockIdx.x * BNT + threadIdx.x; i < h; i += gridDim.x * BNT) {
     cpx<R> a[12], b[12];
     SpinorFmt<P>::load(q, h, i, a);
@@ -404,7 +406,7 @@ __global__ void __launch_bounds__(BNT) mr_alpha_kernel(int h, const char* q, con
       l[2] += qr * qr + qi * qi;
     }
 #pragma unroll
-    for (int j = 0; j < 3; ++j) acc[j] += (double)l[j];
+    for (int j = 0; j < 3; ++j) acc[j] += l[j];
   }
   double tot[3];
   if (!grid_sum<3>(acc, partials, counter, tot)) return;
@@ -436,7 +438,7 @@ __global__ void __launch_bounds__(BNT) mr_update_kernel(int h, char* x, char* r,
   typedef typename SpinorFmt<P>::real R;
   const cpx<R> al = mk<R>((R)S.alpha_re, (R)S.alpha_im);
   typedef typename SiteSum<R>::type SR;
-  double acc[1] = {0.0};
+  SR acc[1] = {};  // FP32 for FP32 data (the warp tree too), FP64 from the warps on
   for (int i = blockIdx.x * BNT + threadIdx.x; i < h; i += gridDim.x * BNT) {
     cpx<R> xv[12], rv[12], qv[12];
     SpinorFmt<P>::load(x, h, i, xv);
@@ -449,7 +451,7 @@ __global__ void __launch_bounds__(BNT) mr_update_kernel(int h, char* x, char* r,
       rv[k] = rv[k] - al * qv[k];
       site += (SR)norm2(rv[k]);
     }
-    acc[0] += (double)site;
+    acc[0] += site;
     SpinorFmt<P>::store(x, h, i, xv);
     SpinorFmt<P>::store(r, h, i, rv);
   }
