@@ -74,7 +74,7 @@ __device__ void plan_rebuild(const Plans& L, int w) {
   plan_build(P, L.order, L.states, w >= 2);
 }
 
-// All four (before the solve, and for the tuner); 4 warps.
+// All five (before the solve, and for the tuner); one warp each.
 __global__ void plans_init_kernel(Plans L) {
   const int w = threadIdx.x >> 5;
   if (w < NPLANS) plan_rebuild(L, w);
@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(BNT) cg_update_batch_kernel(const BatchSys* __
   if (threadIdx.x == 0) last = arrive_acq_rel(&gl->counter) == gridDim.x - 1;
   __syncthreads();
   if (!last) return;
-  // the last block: every block's work is visible; warps 0..3 rebuild the four work lists
+  // the last block: every block's work is visible; warps 0..4 rebuild the five work lists
   if ((threadIdx.x >> 5) < NPLANS) plan_rebuild(L, threadIdx.x >> 5);
   __syncthreads();
   if (threadIdx.x == 0) {
