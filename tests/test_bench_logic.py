@@ -75,3 +75,31 @@ def test_hopping_byte_counts():
     for (prec, nreal), (alg, naive) in expect.items():
         assert bench.hop_bytes_per_site(prec, nreal) == alg
         assert bench.hop_naive_bytes_per_site(prec, nreal) == naive
+
+
+def test_traffic_lines_of_the_committed_profiles():
+    """Each `bench-traffic:` line under profiles/ names a known form and lattice, a kernel choice
+    and a 12-digit source digest, and its DRAM bytes lie within 10% of the algorithmic bytes of one
+    launch of that form on that lattice (so a figure the bench reports as roofline.traffic is one
+    launch's worth); the headline form's line is found by ncu_traffic when its digest is current."""
+    import glob
+    import re
+    import bench
+    from paper_0905_3331_gb300 import inputs
+    pat = re.compile(r"bench-traffic: form=(\S+) lattice=(\S+) kernel=(\d+) sources=([0-9a-f]+) bytes=(\d+)")
+    found = 0
+    for path in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        for line in open(path):
+            m = pat.search(line)
+            if not m:
+                continue
+            found += 1
+            form, lattice, kernel, digest, nbytes = m.groups()
+            prec, nreal = bench.parse_sloppy(form)
+            w = inputs.WORKLOADS[lattice]
+            alg = bench.hop_bytes_per_site(prec, nreal) * (w.V // 2)
+            assert len(digest) == 12 and int(kernel) in (1, 2, 3, 4, 5)
+            assert abs(int(nbytes) - alg) < 0.1 * alg, (path, form, lattice, nbytes, alg)
+            if digest == bench.kernel_sources_hash(prec):
+                assert bench.ncu_traffic(form, lattice, int(kernel), prec)[0] == float(nbytes)
+    assert found >= 1
