@@ -222,3 +222,33 @@ def test_every_batch_split_solves_to_the_oracle(tmp_path, split):
                 res = oracle_rel_residual(T, L, U, phi, xs[n], kappa, mu, f)
                 assert res < 1e-10, (split, prec, link, li, mu, res)
                 n += 1
+
+
+def test_batch_of_forty_systems_on_one_lattice():
+    """40 systems on one lattice: the work lists compact their candidates 32 at a time (two
+    ballots on this lattice), and with 4 systems per thread the ten groups fill one list too.
+    Every solution meets the oracle's bar."""
+    import os
+    w = inputs.WORKLOADS["4^4"]
+    U = w.gauge()
+    lat = Lattice(w.T, w.L, w.kappa, w.mu)
+    lat.set_gauge(U)
+    systems, phis = [], []
+    for k in range(40):
+        phi = inputs.gaussian_spinor(w.T, w.L, 500 + k)
+        b = torch.from_numpy(phi).to(dev())
+        systems.append((lat, 0.005 + 0.001 * (k % 7), torch.zeros_like(b), b, 1 if k % 3 else -1))
+        phis.append(phi)
+    for split in (None, "4"):
+        if split:
+            os.environ["TM_BATCH_K"] = split
+        try:
+            for s in systems:
+                s[2].zero_()
+            infos = solve_cg_batch(systems, sloppy_prec=F32, sloppy_link=LINK12, delta=0.1)
+        finally:
+            os.environ.pop("TM_BATCH_K", None)
+        for (lat_, mu, x, b, f), phi, info in zip(systems, phis, infos):
+            res = oracle_rel_residual(w.T, w.L, U, phi, x.cpu().numpy(), w.kappa, mu, f)
+            assert res < 1e-10 and info.status == 0, (split, mu, f, res)
+    lat.close()
