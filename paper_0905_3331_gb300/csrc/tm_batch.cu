@@ -3,9 +3,11 @@
 // Systems may differ in source, twisted mass and lattice (geometry and gauge field).  Every
 // system runs the mixed-precision reliable-update CG of tm_solver.cu, but the sloppy
 // iterations of all systems go through the same kernels: one launch of K1..K4 and of the
-// update covers every system, its blocks mapped to (system, block of sites) by a table, with
-// the blocks of systems that share a lattice interleaved so that each link is fetched from
-// HBM once and served to the other systems from L2.  Each system keeps its own device-side
+// update covers every running system, its blocks mapped to (system, block of sites) by a work
+// list rebuilt inside the graph, with the blocks of systems that share a lattice interleaved so
+// that each link is fetched from HBM once and served to the other systems from L2.  The hopping
+// launches run the single-system kernel's body per system (1, 2 or 4 threads per site) or K = 2,
+// 4 systems per thread (tm_batch_group.cu), as a tuner picks per batch shape.  Each system keeps its own device-side
 // CG state and reductions.  The whole solve is one CUDA graph launch: a WHILE node over one
 // batched iteration followed by an IF node that runs the FP64 service -- the reliable update of
 // every system that stopped in that iteration (its trigger, convergence of the sloppy residual,
