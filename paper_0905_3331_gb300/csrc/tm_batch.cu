@@ -88,16 +88,12 @@ __global__ void plans_init_kernel(Plans L) {
 // storage; serv = 1: the FP64 service of stopped systems, where K4's residual update uses alpha = 1
 // (r = b' - A X from r = b') and the reduction stores ||r||^2 in B.result.  A system that stopped
 // since the list was built (a breakdown in K2) is skipped.
-#ifndef TM_BATCH_SPB1
-#define TM_BATCH_SPB1 64
-#endif
-constexpr int hop_batch_spb(int tps) { return tps == 1 ? TM_BATCH_SPB1 : hop_spb(tps); }
 constexpr int hop_batch_min_blocks(int prec, int nreal, int tps) {
-  return (tps == 1 && (prec == TM_F32 || prec == TM_F16)) ? 512 / hop_batch_spb(1) : 1;
+  return (tps == 1 && (prec == TM_F32 || prec == TM_F16)) ? 512 / hop_spb(1) : 1;  // 8 blocks of 64 (128 registers)
 }
 
 template <int PREC, int NREAL, bool HAS_Y, int MODE, int TPS>
-__global__ void __launch_bounds__(hop_batch_spb(TPS) * TPS, hop_batch_min_blocks(PREC, NREAL, TPS))
+__global__ void __launch_bounds__(hop_spb(TPS) * TPS, hop_batch_min_blocks(PREC, NREAL, TPS))
     hop_batch_kernel(const BatchSys* __restrict__ systems, const CGState* __restrict__ states, Plan plan, int serv,
                      int in_sel, int y_sel, int out_sel, int kk, int out_parity) {
   const int total = plan.start[plan.nlat];
@@ -107,7 +103,7 @@ __global__ void __launch_bounds__(hop_batch_spb(TPS) * TPS, hop_batch_min_blocks
     if (serv ? !(S.done && !S.finished) : S.done) continue;  // block-uniform
     const BatchSys& B = systems[m.x];
     const Reduce red{B.partials, B.counters, B.result, B.st, serv ? FIN_STORE : (MODE == 1 ? FIN_CG_ALPHA : FIN_CG_RR)};
-    hop_sites<PREC, NREAL, HAS_Y, MODE, TPS, false, ListBlock, hop_batch_spb(TPS)>(
+    hop_sites<PREC, NREAL, HAS_Y, MODE, TPS, false, ListBlock, hop_spb(TPS)>(
         B.g, out_parity, B.links, B.vec[in_sel], 0, B.vec[out_sel], 0, B.vec[y_sel], 0, B.coef[kk],
         serv ? nullptr : B.st, 1.0, red, ListBlock{m.y, B.nblocks});
     __syncthreads();  // the body's shared memory is reused by the next block
@@ -292,7 +288,7 @@ template <int PREC, int NREAL, int TPS>
 static tm_status launch_hop_batch(const BatchSys* d_sys, const CGState* d_st, const Plan& plan, int cap, int serv,
                                   int in_sel, int y_sel, int out_sel, int kk, int parity, int mode, bool has_y,
                                   cudaStream_t s) {
-  constexpr int NT = hop_batch_spb(TPS) * TPS;
+  constexpr int NT = hop_spb(TPS) * TPS;
 #define TM_GL(HY, MD)                                                                                  \
   {                                                                                                    \
     auto kern = hop_batch_kernel<PREC, NREAL, HY, MD, TPS>;                                            \
@@ -476,13 +472,13 @@ struct BatchLayout {
 };
 
 // The batch split of the sloppy hopping launch: K = 1 with TPS threads per site (1, 2 or 4;
-// hop_batch_spb(TPS) sites per block), or K = 2, 4 systems per thread (HOP_NT sites per block) over
+// hop_spb(TPS) sites per block), or K = 2, 4 systems per thread (HOP_NT sites per block) over
 // groups of K systems of one lattice.  Sets the blocks per system (and group) in the layout and
 // the system table, builds the groups, and uploads them.
 tm_status set_batch_split(int K, int tps, const std::vector<SysWork>& W, const std::vector<LatWork>& lats,
                           BatchLayout& Y, std::vector<BatchSys>& hsys, BatchSys* d_sys, BatchLaunch& L,
                           cudaStream_t s) {
-  const int spb = K > 1 ? HOP_NT : hop_batch_spb(tps);
+  const int spb = K > 1 ? HOP_NT : hop_spb(tps);
   std::vector<BatchGroup> grp;
   for (int li = 0; li < Y.nlat; ++li) {
     const int nbl = (int)((lats[li].lat->h + spb - 1) / spb);
@@ -736,9 +732,9 @@ extern "C" tm_status tm_solve_cg_batch(const tm_system* systems, int nsys, const
     for (int k = 0; k < nsys; ++k)
       if (W[k].lat_index == li) Y.host[c++] = k;
     Y.hat(1, li) = c - Y.hat(0, li);
-    Y.hat(2, li) = (int)((lats[li].lat->h + hop_batch_spb(1) - 1) / hop_batch_spb(1));
+    Y.hat(2, li) = (int)((lats[li].lat->h + hop_spb(1) - 1) / hop_spb(1));
     Y.hat(3, li) = (int)blas_blocks(lats[li].lat->geom.h);
-    Y.hat(4, li) = (int)((lats[li].lat->h + hop_batch_spb(1) - 1) / hop_batch_spb(1));
+    Y.hat(4, li) = (int)((lats[li].lat->h + hop_spb(1) - 1) / hop_spb(1));
   }
   const Plans plans = Y.plans();
   BatchLaunch GL{sp, sl, 1, 0, d_sys, plans.states, plans.hop, npart, 1, Y.groups, plans.ghop};
@@ -804,7 +800,7 @@ extern "C" tm_status tm_solve_cg_batch(const tm_system* systems, int nsys, const
         B.st = d_st + k;
         B.partials = d_part + first[k];
         B.counters = d_ctr + 2 * k;
-        B.nblocks = (int)((w.lat->h + hop_batch_spb(1) - 1) / hop_batch_spb(1));  // the FP64 service's; the sloppy per TPS
+        B.nblocks = (int)((w.lat->h + hop_spb(1) - 1) / hop_spb(1));  // the FP64 service's; the sloppy per TPS
         B.nblocks_upd = (int)blas_blocks(w.lat->geom.h);
         B.result = d_res + k;
         // the FP64 service's table: the FP64 gauge copy, X, T, W, r and b'
