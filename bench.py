@@ -854,10 +854,12 @@ def run_reference(args):
     # REF_TOTAL_SECONDS of host time (at least one CG iteration per step)
     step_seconds = min(args.ref_seconds, max(0.5, REF_TOTAL_SECONDS / max(1, args.steps)))
     per_step, n_it = [], 0
+    t_host = time.perf_counter()
     for _ in range(args.steps):
         t_it, n = smp.iterations(step_seconds)
         n_it += n
         per_step.append(t_it * iters + smp.fixed)
+    t_host = time.perf_counter() - t_host
     tot = sum(per_step)
     value = args.steps / tot
     cb = {"value": round(value, 8), "unit": "solves/s", "cores": oracle.num_threads(),
@@ -875,6 +877,8 @@ def run_reference(args):
                                f"mu {w.mu}, Gaussian source; even/odd CG to FP64 true residual 1e-10",
                    "lattice": w.name},
         "cpu_baseline": cb,
+        # ms_per_step is the modelled time of one complete solve; the host time a step's sample took:
+        "sample_ms_per_step": round(t_host / max(1, args.steps) * 1e3, 3),
         "e2e": {"value": round(value, 8), "unit": "solves/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0}}))
 

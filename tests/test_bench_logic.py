@@ -55,6 +55,7 @@ def test_reference_arm_json_line():
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["higher_is_better"] is True
     assert line["metric"] == bench.METRIC and line["warmup"] == 3 and line["steps"] == 2
+    assert 0 < line["sample_ms_per_step"] < 60e3  # the bounded sample, not the modelled solve
 
 
 def test_trimmed_mean_drops_stray_launches():
