@@ -69,3 +69,63 @@ def test_cg_params_defaults(lib):
 def test_launch_counter(lib):
     lib.tm_reset_launch_count()
     assert lib.tm_launch_count() == 0
+
+
+def test_every_entry_point_rejects_a_null_lattice_on_the_host(lib):
+    """Each compute entry point checks its arguments before any CUDA call: a NULL lattice (or
+    field) is TM_ERR_ARG with a message naming the function, on a machine without a GPU."""
+    ERR_ARG = 1
+    calls = {
+        "tm_apply_D": lambda: lib.tm_apply_D(None, None, None, 1, 0, 1, None),
+        "tm_apply_hopping_eo": lambda: lib.tm_apply_hopping_eo(None, 0, None, None, 0, 18, 1, None),
+        "tm_apply_Mee_inv": lambda: lib.tm_apply_Mee_inv(None, None, None, 1, 0, 1, None),
+        "tm_pack_half": lambda: lib.tm_pack_half(None, 0, None, None, 1, None),
+        "tm_unpack_half": lambda: lib.tm_unpack_half(None, 0, None, None, 1, None),
+        "tm_set_gauge": lambda: lib.tm_set_gauge(None, None, None),
+        "tm_lattice_set_params": lambda: lib.tm_lattice_set_params(None, 0.16, 0.01),
+        "tm_solve_cg": lambda: lib.tm_solve_cg(None, None, None, 1, None, None, None),
+        "tm_solve_bicgstab": lambda: lib.tm_solve_bicgstab(None, None, None, 1, None, None, None),
+        "tm_solve_mr": lambda: lib.tm_solve_mr(None, None, None, 1, None, None, None),
+        "tm_solve_normal": lambda: lib.tm_solve_normal(None, None, None, None, None, None),
+        "tm_chrono_guess": lambda: lib.tm_chrono_guess(None, None, None, 0, None, 1, None),
+        "tm_apply_Dh": lambda: lib.tm_apply_Dh(None, None, None, 0.15, 0.19, 1, None),
+        "tm_solve_doublet": lambda: lib.tm_solve_doublet(None, None, None, 0.15, 0.19, None, None, None),
+        "tm_meson_contract": lambda: lib.tm_meson_contract(None, None, None, None),
+        "tm_correlator": lambda: lib.tm_correlator(None, None, None, 1, None, None),
+        "tm_solve_cg_batch": lambda: lib.tm_solve_cg_batch(None, 0, None, None, None),
+    }
+    for name, call in calls.items():
+        assert call() == ERR_ARG, name
+        assert name.encode() in lib.tm_last_error(), (name, lib.tm_last_error())
+    fn = lib.tm_apply_D_noalloc
+    fn.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int] * 3 + [ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    assert fn(None, None, None, 1, 0, 1, None) == ERR_ARG
+    assert b"tm_apply_D_noalloc" in lib.tm_last_error()
+
+
+def test_batched_solver_checks_its_parameters_on_the_host(lib):
+    """tm_solve_cg_batch rejects parameters it does not support before it reads a system: the
+    mode (reliable updates only), the sloppy storage (FP32 or FP16) and link form (18/12/8), tol,
+    max_iter, delta, and initial guesses."""
+    ERR_ARG, UNSUPPORTED = 1, 10
+    systems = (tm.TmSystem * 2)()
+
+    def run(**kw):
+        p = tm.CGParams()
+        lib.tm_cg_params_default(ctypes.byref(p))
+        p.mode = 2  # TM_CG_RELIABLE
+        for k, v in kw.items():
+            setattr(p, k, v)
+        return lib.tm_solve_cg_batch(systems, 2, ctypes.byref(p), None, None), lib.tm_last_error()
+
+    assert run(mode=0) == (UNSUPPORTED, b"tm_solve_cg_batch: mode must be TM_CG_RELIABLE")
+    assert run(sloppy_prec=0)[0] == ERR_ARG
+    assert run(sloppy_link=9)[0] == ERR_ARG
+    assert run(tol=0.0)[0] == ERR_ARG
+    assert run(max_iter=0)[0] == ERR_ARG
+    assert run(delta=1.0)[0] == ERR_ARG
+    assert run(use_x0=1)[0] == UNSUPPORTED
+    # parameters accepted: the first system's NULL members are the next error
+    st, msg = run()
+    assert st == ERR_ARG and b"system 0 has a NULL member" in msg
