@@ -111,8 +111,10 @@ size_t tm_half_field_bytes(tm_lattice lat, tm_prec prec);
  * hop's arithmetic.  The value 5 (TM_HOP_PAIRED, FP32 and FP16 storage only) selects one thread
  * per TWO sites whose FP32 arithmetic runs on packed pairs (one instruction for both sites).
  * By default the library times the choices when the form's gauge copy is first built and keeps
- * the fastest (the environment variable TM_HOP_TPS=1|2|3|4|5 overrides that for every form).
- * tm_set_hop_threads fixes the choice (0 = tune again); tm_get_hop_threads reports it.
+ * the fastest, for the rest of the process, for every lattice of the same extents on the same
+ * device (the environment variable TM_HOP_TPS=1|2|3|4|5 overrides that for every form).
+ * tm_set_hop_threads fixes the choice (0 = time again if the form's gauge copy exists, and
+ * keep the new choice for later lattices of these extents); tm_get_hop_threads reports it.
  * Results for different choices agree to rounding; for one fixed choice they are bitwise
  * reproducible.  Errors: TM_ERR_ARG, TM_ERR_UNSUPPORTED (3 or 5 with FP64 or double-float
  * storage, 2 or 4 with double-float). */

@@ -9,6 +9,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
+#include <vector>
 
 #include "tm_dslash.cuh"
 #include "tm_internal.cuh"
@@ -285,7 +287,7 @@ __global__ void build_links_kernel(Geom g, const double* __restrict__ U, char* _
   }
 }
 
-static tm_status tune_hop(tm_lattice lat, int prec, int nreal, cudaStream_t s);
+static tm_status tune_hop(tm_lattice lat, int prec, int nreal, cudaStream_t s, bool retime = false);
 
 template <typename S, int NREAL>
 static void launch_build(tm_lattice lat, char* out, cudaStream_t s) {
@@ -335,7 +337,10 @@ tm_status ensure_links(tm_lattice lat, int prec, int nreal, cudaStream_t s) {
 // choice (CUDA events, fastest of several timed groups, candidates interleaved) on scratch
 // buffers.  TM_HOP_TPS=1|2|3|4 in the environment fixes the choice for every form (3: the
 // pipelined kernel, FP64 falls back to 1); tm_set_hop_threads fixes it for one form.  Runs
-// when the form's gauge copy is built.
+// when the form's gauge copy is built.  A choice is kept for the rest of the process by device,
+// extents and storage form (it depends on the launch shape, not on the field's values): a later
+// lattice of the same shape takes it without timing again, and tm_set_hop_threads(..., 0) times
+// again and replaces it.
 static int env_tps() {
   const char* e = getenv("TM_HOP_TPS");
   if (!e) return 0;
@@ -343,13 +348,20 @@ static int env_tps() {
   return (v == 1 || v == 2 || v == 4 || v == TM_HOP_PIPELINED || v == TM_HOP_PAIRED) ? v : 0;
 }
 
+// The choices made so far in this process.
+struct TuneChoice {
+  int device, T, L, prec, nreal, tps;
+};
+static std::mutex g_tune_mu;
+static std::vector<TuneChoice> g_tune_choices;
+
 // Times the kernel choices of one storage form on this lattice and keeps the best.  The score
 // is one CG iteration's mix: two plain launches (K1, K3) and two launches with a site-local
 // input, the residual update and the fused reduction (K2, K4).  More threads per site must
 // win by 10%: measured at 16^3 x 32, FP32 kernels with 2 threads per site ran at their
 // stand-alone speed in a host loop but 2.3x slower inside the CG stage graphs.  (They need
 // 116-144 registers a thread, so only 3-4 of their 128-thread blocks fit on an SM.)
-static tm_status tune_hop(tm_lattice lat, int prec, int nreal, cudaStream_t s) {
+static tm_status tune_hop(tm_lattice lat, int prec, int nreal, cudaStream_t s, bool retime) {
   const int li = link_index(nreal);
   if (lat->hop_tps_forced[prec][li]) return TM_OK;
   if (prec == TM_DF64) {  // built with one thread per site only
@@ -359,6 +371,14 @@ static tm_status tune_hop(tm_lattice lat, int prec, int nreal, cudaStream_t s) {
   if (const int e = env_tps()) {
     lat->hop_tps[prec][li] = ((e == TM_HOP_PIPELINED || e == TM_HOP_PAIRED) && prec == TM_F64) ? 1 : e;
     return TM_OK;
+  }
+  if (!retime) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (const TuneChoice& c : g_tune_choices)
+      if (c.device == lat->device && c.T == lat->T && c.L == lat->L && c.prec == prec && c.nreal == nreal) {
+        lat->hop_tps[prec][li] = c.tps;
+        return TM_OK;
+      }
   }
   const size_t hb = spinor_bytes_per_site(prec) * lat->h;
   const int pr = (prec == TM_F64) ? TM_F64 : TM_F32;
@@ -436,6 +456,16 @@ static tm_status tune_hop(tm_lattice lat, int prec, int nreal, cudaStream_t s) {
   for (int c = 2; c < 4; ++c)
     if (score[c] < 0.9f * base && score[c] < score[bi]) bi = c;
   lat->hop_tps[prec][li] = cands[bi];
+  if (st == TM_OK) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    bool found = false;
+    for (TuneChoice& c : g_tune_choices)
+      if (c.device == lat->device && c.T == lat->T && c.L == lat->L && c.prec == prec && c.nreal == nreal) {
+        c.tps = cands[bi];
+        found = true;
+      }
+    if (!found) g_tune_choices.push_back(TuneChoice{lat->device, lat->T, lat->L, prec, nreal, cands[bi]});
+  }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   cudaFree(din);
@@ -591,7 +621,7 @@ tm_status tm_set_hop_threads(tm_lattice lat, tm_prec prec, tm_link link, int thr
   invalidate_graphs(lat);  // captured graphs hold the previous kernel choice
   if (threads_per_site == 0) {
     lat->hop_tps_forced[prec][li] = 0;
-    if (lat->links[prec][li]) return tune_hop(lat, prec, link, nullptr);
+    if (lat->links[prec][li]) return tune_hop(lat, prec, link, nullptr, true);
     return TM_OK;
   }
   if (prec == TM_DF64 && threads_per_site != 1)
